@@ -1,0 +1,300 @@
+"""Benchmark of the spring-mass hot path on GB300.
+
+A "step" is one simulation time step over the whole system: every spring's
+force onto both masses, then every mass integrated (gravity, constraints).
+Default workload: the 1M-mass lattice (100^3 sites, 12,731,796 26-neighbourhood
+springs, perturbed rest lengths, lognormal k, bottom layer fixed, no ground,
+dt = 5e-5) with the deterministic CSR kernel.  The metric is spring updates
+per second (springs x steps / time); the roofline compares the algorithmic
+bytes of one step with the measured HBM copy bandwidth.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                       [--accumulate csr|atomic] [--workload lattice1m|...]
+Under torchrun (N > 1) every rank simulates its own replica on its own GPU
+(the method has no data-path exchange between independent bodies); the value
+is the total over ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "spring updates/s"
+UNIT = "spring_updates/s"
+L2_BYTES = 126 * 1024 * 1024
+
+# ncu DRAM traffic of k_step_sell per launch on the 1M-mass lattice, with the
+# SHA-256 (first 16 hex digits) of the kernel source it was measured on.
+# Reported only while the source is unchanged.
+NCU_TRAFFIC = {}
+
+
+def kernel_source_hash() -> str:
+    p = os.path.join(ROOT, "paper_1911_10274_gb300", "csrc", "step_kernels.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def algorithmic_bytes(n_masses: int, n_springs: int) -> int:
+    """Bytes one step must move: 16 per spring (i, j, k, L0) and 52 per mass
+    (position and velocity read and written, 1/m read)."""
+    return 16 * n_springs + 52 * n_masses
+
+
+def make_workload(name: str):
+    from paper_1911_10274_gb300 import inputs
+    if name == "lattice1m":
+        return inputs.large_lattice(n=100, seed=0)
+    if name == "lattice50":
+        s = inputs.large_lattice(n=50, seed=0)
+        return s
+    if name == "mesh2m":
+        return inputs.random_mesh(n_points=2_000_000, seed=0)
+    if name == "cube1k":
+        return inputs.cube_drop()
+    raise SystemExit(f"unknown workload {name}")
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv") \
+            if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/titan_clocks_{os.getpid()}.csv"
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return None
+        rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if "Active" in r[5 + k] and "Not" not in r[5 + k]})
+        loaded = [x for x in sm if mx and x > 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def time_oracle(system, steps: int):
+    import oracle
+    t0 = time.perf_counter()
+    oracle.run(system, steps)
+    return time.perf_counter() - t0
+
+
+def sub_lattice_for_budget(seconds_per_step: float):
+    """Largest n^3 sub-lattice of the 1M-mass recipe whose oracle step fits the budget."""
+    from paper_1911_10274_gb300 import inputs
+    probe = inputs.large_lattice(n=30, seed=0)
+    t = min(time_oracle(probe, 3) / 3, 10.0)
+    rate = probe.n_springs / max(t, 1e-9)
+    n = 30
+    while n < 100 and inputs.lattice_spring_count(n + 2, n + 2, n + 2) / rate <= seconds_per_step:
+        n += 2
+    while n > 4 and inputs.lattice_spring_count(n, n, n) / rate > seconds_per_step:
+        n -= 2
+    return inputs.large_lattice(n=n, seed=0)
+
+
+def cpu_baseline_leg(system, target_seconds: float = 15.0):
+    """The oracle as it stands, single thread, on a bounded number of steps of
+    the same workload (from its initial state)."""
+    probe = time_oracle(system, 1)
+    steps = max(1, min(200, int(target_seconds / max(probe, 1e-6))))
+    t = time_oracle(system, steps)
+    return {"value": system.n_springs * steps / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{system.name}: {steps} time steps of the full system from its initial "
+                      f"state, FP64, one thread ({t:.1f} s)"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    per_step = 90.0 / max(1, args.steps + args.warmup)
+    system = sub_lattice_for_budget(per_step)
+    import oracle
+    x, v = system.pos, system.vel
+    for w in range(args.warmup):
+        x, v = oracle.run(system, 1, step0=w, pos=x, vel=v)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        x, v = oracle.run(system, 1, step0=args.warmup + k, pos=x, vel=v)
+    dt = time.perf_counter() - t0
+    value = system.n_springs * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_for(args, None),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"each step: one FP64 oracle time step of a {system.name} "
+                                       f"sub-lattice ({system.n_masses} masses, {system.n_springs} springs) "
+                                       f"of the benchmark recipe, one thread"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_for(args, system):
+    cfg = {"workload": {"lattice1m": "1M-mass lattice 100^3, 12,731,796 springs, fixed base, no ground, dt=5e-5",
+                        "lattice50": "50^3 lattice, 1,558,396 springs", "mesh2m": "2M-point kNN mesh",
+                        "cube1k": "10^3 cube drop"}[args.workload],
+           "accumulate": args.accumulate, "order": "morton", "graph_chunk": 64,
+           "parallelism": f"replicas x{args.gpus}",
+           "l2": "inputs larger than L2 (spring data > 126 MB), no flush"}
+    if system is not None:
+        cfg.update({"masses": system.n_masses, "springs": system.n_springs})
+    return cfg
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1911_10274_gb300 import titan as T
+
+    system = make_workload(args.workload)
+    acc = T.ACCUM_CSR if args.accumulate == "csr" else T.ACCUM_ATOMIC
+    stream = torch.cuda.current_stream()
+    sim = T.Sim(system, accumulate=acc, stream=stream.cuda_stream, device=local)
+    launches_per_step = 1 if acc == T.ACCUM_CSR else 2
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    with ClockSampler(local) as clocks:
+        sim.step(args.warmup)
+        barrier()
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        sim.step(args.steps)
+        end.record(stream)
+        barrier()
+        ms = start.elapsed_time(end)
+        # end-to-end through the C ABI with host buffers: upload state, K steps, read back
+        pos0 = np.ascontiguousarray(system.pos)
+        vel0 = np.ascontiguousarray(system.vel)
+        barrier()
+        t0 = time.perf_counter()
+        sim.set_state(pos0, vel0)
+        sim.step(args.steps)
+        p, v, _ = sim.snapshot()
+        e2e_s = time.perf_counter() - t0
+        barrier()
+    t_max = ms / 1e3
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_max, e2e_s], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max, e2e_s = float(tt[0]), float(tt[1])
+    value = world * system.n_springs * args.steps / t_max
+    e2e_value = world * system.n_springs * args.steps / e2e_s
+    step_s = t_max / args.steps
+    alg = algorithmic_bytes(system.n_masses, system.n_springs)
+    peak, peak_kind = measured_peaks()
+    achieved = alg / step_s / 1e9
+    h = kernel_source_hash()
+    traffic = NCU_TRAFFIC.get((args.workload, args.accumulate, h))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * step_s, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config_for(args, system),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "k_step_sell" if acc == T.ACCUM_CSR else "k_springs_atomic+k_masses_atomic",
+                     "algorithmic_bytes_per_launch": alg,
+                     "peak_source": f"{peak_kind} HBM copy bandwidth"},
+        "e2e": {"value": e2e_value, "unit": UNIT,
+                "h2d_bytes_per_step": 32 * system.n_masses / args.steps,
+                "d2h_bytes_per_step": 24 * system.n_masses / args.steps,
+                "note": "titan_set_state from host FP64 arrays, K steps, titan_snapshot to pinned host"},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks.summary(),
+    }
+    sim.close()
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_leg(system)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=128)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--accumulate", choices=["csr", "atomic"], default="csr")
+    ap.add_argument("--workload", default="lattice1m")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

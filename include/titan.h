@@ -1,0 +1,183 @@
+/*
+ * titan.h -- C ABI of the GB300 spring-mass simulator (libtitan.so).
+ *
+ * The library simulates the hot path of Titan (Austin et al., arXiv
+ * 1911.10274): every time step applies each spring's Hooke-plus-damping force
+ * to both of its masses (Sec. III-B, Eq. 1), then integrates every mass with
+ * a velocity-first Euler step under gravity, a ground plane with Coulomb
+ * friction, and fixed-mass constraints (Sec. III-A).  The host calls follow the
+ * paper's asynchronous model (Sec. III-D): the caller builds the objects, lets
+ * the GPU run a number of steps without blocking, reads state back without
+ * stalling the step loop, edits the system between steps and resumes.
+ *
+ * Conventions for every call:
+ *  - Pointers are host pointers unless the name says "dev".  Input arrays are
+ *    owned by the caller and are copied before the call returns; the library
+ *    keeps no pointer to them.
+ *  - Mass and spring indices are always the caller's own (input) order; any
+ *    internal reordering is invisible at this interface.
+ *  - Every call returns a titan_status and never throws or aborts.  On an
+ *    error the handle is unchanged unless the status is TITAN_E_CUDA, and
+ *    titan_last_error() describes it.  Errors of earlier asynchronous GPU work
+ *    are reported by the next call that synchronises with it.
+ *  - Calls on one handle must not overlap; a call that finds another one in
+ *    progress on the same handle returns TITAN_E_BUSY.  Distinct handles are
+ *    independent and may be driven from different threads.
+ *  - Units are SI (m, kg, s, N).  z is the vertical axis.
+ */
+#ifndef TITAN_H
+#define TITAN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct titan_sim titan_sim;     /* opaque, library-owned */
+
+typedef enum {
+    TITAN_OK = 0,
+    TITAN_E_INVALID = 1,      /* an argument failed validation; nothing changed     */
+    TITAN_E_CUDA = 2,         /* a CUDA call failed (maybe earlier asynchronous work) */
+    TITAN_E_OOM = 3,          /* a device or pinned-host allocation failed          */
+    TITAN_E_TIMEOUT = 4,      /* a bounded device-side wait gave up                 */
+    TITAN_E_BUSY = 5,         /* another call on this handle is in progress         */
+    TITAN_E_UNSUPPORTED = 6   /* valid request this build or device cannot serve    */
+} titan_status;
+
+/* Masses (Sec. III-B: one integrator thread per mass).
+ * pos [n][3], vel [n][3] (NULL: at rest), mass [n] (> 0, finite),
+ * fixed [n] (NULL: none; nonzero: the mass never moves, Sec. III-A). */
+typedef struct {
+    uint32_t n;
+    const double *pos;
+    const double *vel;
+    const double *mass;
+    const uint8_t *fixed;
+} titan_masses;
+
+/* Springs (Sec. III-B, Eq. 1).  ends [n][2] mass indices i != j (< masses.n);
+ * k [n] stiffness >= 0; rest [n] rest length >= 0 (NULL: the initial
+ * distance between the two masses); damping [n] axial dashpot >= 0 (NULL:
+ * titan_params.damping for every spring). */
+typedef struct {
+    uint32_t n;
+    const uint32_t *ends;
+    const double *k;
+    const double *rest;
+    const double *damping;
+} titan_springs;
+
+typedef enum {
+    TITAN_ACCUM_CSR = 0,      /* deterministic per-mass gather (fused, bit-exact)   */
+    TITAN_ACCUM_ATOMIC = 1    /* per-spring scatter with vector atomics (Sec. III-B) */
+} titan_accumulate;
+
+typedef enum {
+    TITAN_ORDER_INPUT = 0,    /* keep the caller's mass order on the device         */
+    TITAN_ORDER_MORTON = 1    /* reorder masses along a Morton curve                */
+} titan_order;
+
+typedef enum {
+    TITAN_EXEC_AUTO = 0,      /* persistent kernel when the system fits, else launches */
+    TITAN_EXEC_LAUNCH = 1,    /* one fused kernel launch per step (graph-captured)  */
+    TITAN_EXEC_PERSISTENT = 2 /* one launch runs many steps (cluster, shared memory) */
+} titan_exec;
+
+/* Integration parameters.  Fill with titan_default_params() first. */
+typedef struct {
+    double dt;                /* time step (s), > 0                                */
+    double gravity[3];        /* m/s^2; default (0, 0, -9.81)                      */
+    int32_t ground;           /* nonzero: ground plane z = 0 with friction         */
+    double ground_k;          /* penalty stiffness (N/m), >= 0; default 1e5        */
+    double mu;                /* Coulomb friction coefficient, >= 0; default 0.5   */
+    double damping;           /* dashpot used when springs.damping is NULL         */
+    int32_t accumulate;       /* titan_accumulate; default CSR                     */
+    int32_t order;            /* titan_order; default MORTON                       */
+    int32_t exec;             /* titan_exec; default AUTO                          */
+    int32_t device;           /* CUDA device ordinal; default 0                    */
+    void *stream;             /* cudaStream_t for the step loop; NULL: own stream  */
+    uint64_t spin_limit;      /* bound on device spin-wait iterations; 0: default  */
+    int32_t graph_chunk;      /* steps per captured CUDA graph; 0: 64; < 0: none   */
+    int32_t reserved[7];      /* zero                                              */
+} titan_params;
+
+/* Writes the defaults listed above into *p (p != NULL). */
+void titan_default_params(titan_params *p);
+
+/* Builds a simulation on the GPU (Sec. III-C: all objects live on the GPU).
+ * Validates every input (indices in range, i != j, finite values, mass > 0,
+ * dt > 0, k/rest/damping >= 0) before touching the device, copies the inputs
+ * to device memory in the chosen layout, and sets *out.  The state is at
+ * step 0 (t = 0).  Errors: TITAN_E_INVALID (bad input, *out untouched),
+ * TITAN_E_OOM, TITAN_E_CUDA. */
+titan_status titan_create(const titan_masses *masses, const titan_springs *springs,
+                          const titan_params *params, titan_sim **out);
+
+/* Enqueues n_steps time steps on the simulation's stream and returns without
+ * waiting for them (Sec. III-D: the GPU runs while the caller continues).
+ * Each step is the spring pass and the mass pass of Sec. III-B.
+ * n_steps == 0 is a no-op.  Errors: TITAN_E_CUDA, TITAN_E_TIMEOUT (a bounded
+ * device wait in the persistent kernel expired; reported by this or a later
+ * call once the GPU has run it). */
+titan_status titan_step(titan_sim *sim, uint64_t n_steps);
+
+/* Takes a snapshot of the state after all steps enqueued so far, without
+ * stalling the step loop: a device-side copy on the simulation stream, then a
+ * device-to-host copy on `stream` (a cudaStream_t; NULL: a library-owned side
+ * stream) into one of two pinned host buffers.  *ticket identifies it.
+ * Only the two most recent snapshots are retained.  Errors: TITAN_E_CUDA. */
+titan_status titan_snapshot_async(titan_sim *sim, void *stream, uint64_t *ticket);
+
+/* Waits for snapshot `ticket` and returns pointers to library-owned arrays in
+ * the caller's mass order: *pos and *vel are [n][3] float, *t the simulated
+ * time of the snapshot (any output pointer may be NULL).  The arrays stay valid
+ * until the second next titan_snapshot_async call or titan_destroy.
+ * Errors: TITAN_E_INVALID (ticket unknown or already overwritten),
+ * TITAN_E_CUDA. */
+titan_status titan_snapshot_wait(titan_sim *sim, uint64_t ticket, const float **pos,
+                                 const float **vel, double *t);
+
+/* Sets sinusoidal actuation on the listed springs (Sec. V-B: springs expand
+ * and contract over time; Sec. III-F edits pushed between steps):
+ * rest(t) = L0 (1 + amp sin(2 pi freq_hz t + phase)), t = step * dt at the start
+ * of the step.  amp == 0 turns actuation off for that spring.  freq_hz applies
+ * to the whole system.  Takes effect from the next enqueued step.
+ * Errors: TITAN_E_INVALID (index out of range, non-finite value). */
+titan_status titan_set_actuation(titan_sim *sim, uint32_t n, const uint32_t *spring_ids,
+                                 const float *amp, const float *phase, float freq_hz);
+
+/* Replaces the positions and velocities (host FP64 arrays [n][3], caller
+ * order; vel NULL: zero) from the next enqueued step on; the step counter is
+ * kept.  Used to resume from a checkpoint (Sec. III-D breakpoints).
+ * Errors: TITAN_E_INVALID (non-finite), TITAN_E_CUDA. */
+titan_status titan_set_state(titan_sim *sim, const double *pos, const double *vel);
+
+/* Writes the state after all steps enqueued so far, in the caller's mass
+ * order, into caller-provided DEVICE arrays pos_dev and vel_dev ([n][3]
+ * float; either may be NULL), ordered on the simulation stream; when `stream`
+ * (a cudaStream_t) is non-NULL it is made to wait for the copy.  Does not block
+ * the host.  Errors: TITAN_E_CUDA. */
+titan_status titan_read_state_dev(titan_sim *sim, float *pos_dev, float *vel_dev, void *stream);
+
+/* Blocks until every enqueued step and copy has finished (the paper's
+ * waitForEvent, Sec. III-D).  Errors: TITAN_E_CUDA, TITAN_E_TIMEOUT. */
+titan_status titan_sync(titan_sim *sim);
+
+/* Number of steps enqueued so far (the simulated time is steps * dt). */
+uint64_t titan_steps(const titan_sim *sim);
+
+/* Text of the last error on this handle, or of the last failed titan_create
+ * on this thread when sim is NULL.  Owned by the library; never NULL. */
+const char *titan_last_error(const titan_sim *sim);
+
+/* Waits for outstanding work and frees every resource of the handle.
+ * NULL is a no-op.  Returns the status of that final wait. */
+titan_status titan_destroy(titan_sim *sim);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TITAN_H */

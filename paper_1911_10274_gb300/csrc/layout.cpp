@@ -1,0 +1,134 @@
+// layout.cpp -- host-side construction of the device layouts (run once per titan_create).
+//
+// Morton order: masses are sorted by the 63-bit Morton code of their position
+// quantised to 2^21 cells per axis over the bounding cube, so that masses that
+// are close in space get close device indices and the neighbour gathers of one
+// warp fall in a few cache lines.
+// SELL-32 incidence: per mass, its incident half-edges sorted by neighbour
+// device index (then spring index) - a fixed order, which makes the force sum
+// deterministic - stored column-major per slice of 32 masses.
+// Spring records: one {i, j, k, L0} record per spring, sorted by (lower,
+// higher) device index, for the atomic scatter.
+#include "layout.h"
+
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+
+namespace titan {
+
+namespace {
+// Spreads the low 21 bits of x so that bit b moves to bit 3b.
+inline uint64_t spread_bits3(uint64_t x) {
+    x &= 0x1fffffULL;
+    x = (x | (x << 32)) & 0x1f00000000ffffULL;
+    x = (x | (x << 16)) & 0x1f0000ff0000ffULL;
+    x = (x | (x << 8)) & 0x100f00f00f00f00fULL;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ULL;
+    x = (x | (x << 2)) & 0x1249249249249249ULL;
+    return x;
+}
+}  // namespace
+
+void morton_order(const double *pos, uint32_t n, std::vector<uint32_t> &caller_of_dev) {
+    caller_of_dev.resize(n);
+    if (n == 0) return;
+    double lo[3] = {pos[0], pos[1], pos[2]}, hi[3] = {pos[0], pos[1], pos[2]};
+    for (uint32_t i = 0; i < n; ++i)
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = std::min(lo[a], pos[3 * (size_t)i + a]);
+            hi[a] = std::max(hi[a], pos[3 * (size_t)i + a]);
+        }
+    double ext = std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
+    const double scale = ext > 0 ? (double)((1u << 21) - 1) / ext : 0.0;
+    std::vector<std::pair<uint64_t, uint32_t>> key(n);
+    for (uint32_t i = 0; i < n; ++i) {
+        uint64_t code = 0;
+        for (int a = 0; a < 3; ++a) {
+            double q = std::floor((pos[3 * (size_t)i + a] - lo[a]) * scale);
+            uint64_t c = q < 0 ? 0 : (q > (double)((1u << 21) - 1) ? (1u << 21) - 1 : (uint64_t)q);
+            code |= spread_bits3(c) << a;
+        }
+        key[i] = {code, i};
+    }
+    std::sort(key.begin(), key.end());
+    for (uint32_t d = 0; d < n; ++d) caller_of_dev[d] = key[d].second;
+}
+
+bool build_sell(uint32_t n, uint32_t s, const uint32_t *ends, const std::vector<uint32_t> &dev_of,
+                SellHost &out) {
+    const uint32_t n_slices = (n + 31) / 32;
+    std::vector<uint32_t> deg(n, 0);
+    for (uint32_t q = 0; q < s; ++q) {
+        ++deg[dev_of[ends[2 * (size_t)q]]];
+        ++deg[dev_of[ends[2 * (size_t)q + 1]]];
+    }
+    std::vector<uint64_t> rowptr(n + 1, 0);
+    for (uint32_t i = 0; i < n; ++i) rowptr[i + 1] = rowptr[i] + deg[i];
+    // half-edge = (neighbour device index, spring index, end slot 0/1)
+    struct HalfEdge { uint32_t nbr, spring; };
+    std::vector<HalfEdge> he(rowptr[n]);
+    std::vector<uint64_t> cur(rowptr.begin(), rowptr.end() - 1);
+    for (uint32_t q = 0; q < s; ++q) {
+        const uint32_t a = dev_of[ends[2 * (size_t)q]], b = dev_of[ends[2 * (size_t)q + 1]];
+        he[cur[a]++] = {b, q};
+        he[cur[b]++] = {a, q};
+    }
+    for (uint32_t i = 0; i < n; ++i)
+        std::sort(he.begin() + rowptr[i], he.begin() + rowptr[i + 1],
+                  [](const HalfEdge &x, const HalfEdge &y) {
+                      return x.nbr != y.nbr ? x.nbr < y.nbr : x.spring < y.spring;
+                  });
+    out.slice_off.assign(n_slices + 1, 0);
+    uint64_t total = 0;
+    for (uint32_t sl = 0; sl < n_slices; ++sl) {
+        uint32_t w = 0;
+        for (uint32_t l = 0; l < 32 && sl * 32 + l < n; ++l) w = std::max(w, deg[sl * 32 + l]);
+        w = (w + 1) & ~1u;
+        total += (uint64_t)w * 32;
+        if (total > 0xffffffffULL) return false;
+        out.slice_off[sl + 1] = (uint32_t)total;
+    }
+    out.entries = (uint32_t)total;
+    out.nbr.assign(total, 0);
+    out.spring.assign(total, UINT32_MAX);
+    out.entry_of_end.assign(2 * (size_t)s, 0);
+    for (uint32_t sl = 0; sl < n_slices; ++sl) {
+        const uint32_t w = (out.slice_off[sl + 1] - out.slice_off[sl]) / 32;
+        for (uint32_t l = 0; l < 32; ++l) {
+            const uint32_t i = sl * 32 + l;
+            for (uint32_t t = 0; t < w; ++t) {
+                const uint64_t e = out.slice_off[sl] + 32ull * t + l;
+                if (i < n && t < deg[i]) {
+                    const HalfEdge &h = he[rowptr[i] + t];
+                    out.nbr[e] = h.nbr;
+                    out.spring[e] = h.spring;
+                    // which end of spring h.spring this row is
+                    const uint32_t end0 = dev_of[ends[2 * (size_t)h.spring]];
+                    const bool is_i = (end0 == i) && !(end0 == h.nbr);
+                    out.entry_of_end[2 * (size_t)h.spring + (is_i ? 0 : 1)] = (uint32_t)e;
+                } else {
+                    out.nbr[e] = i < n ? i : 0;   // self: zero-length padding spring
+                }
+            }
+        }
+    }
+    return true;
+}
+
+void build_records(uint32_t s, const uint32_t *ends, const std::vector<uint32_t> &dev_of,
+                   RecordsHost &out) {
+    out.order.resize(s);
+    std::iota(out.order.begin(), out.order.end(), 0u);
+    std::vector<uint64_t> key(s);
+    for (uint32_t q = 0; q < s; ++q) {
+        const uint64_t a = dev_of[ends[2 * (size_t)q]], b = dev_of[ends[2 * (size_t)q + 1]];
+        key[q] = (std::min(a, b) << 32) | std::max(a, b);
+    }
+    std::stable_sort(out.order.begin(), out.order.end(),
+                     [&](uint32_t x, uint32_t y) { return key[x] < key[y]; });
+    out.slot_of_spring.resize(s);
+    for (uint32_t r = 0; r < s; ++r) out.slot_of_spring[out.order[r]] = r;
+}
+
+}  // namespace titan

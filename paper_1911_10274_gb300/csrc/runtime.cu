@@ -1,0 +1,591 @@
+// runtime.cu -- the C ABI of libtitan (include/titan.h): handles, validation,
+// device layout upload, the asynchronous step loop and snapshots.
+//
+// Asynchronous model (Titan Sec. III-D): titan_step only enqueues work on the
+// simulation stream - one fused kernel per step, replayed from captured CUDA
+// graphs of `graph_chunk` steps - and returns.  Snapshots copy the state on
+// the simulation stream into a slot buffer (a gather into caller order, one
+// small kernel) and move it to pinned host memory on a side stream, so the
+// host reads state while later steps keep running.
+#include <math.h>
+#include <string.h>
+
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "layout.h"
+#include "titan.h"
+#include "titan_internal.h"
+
+using titan::MassState;
+
+namespace {
+
+thread_local std::string g_thread_error = "";
+
+constexpr int kDefaultGraphChunk = 64;
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+bool finite(double x) { return std::isfinite(x); }
+
+}  // namespace
+
+struct titan_sim {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaStream_t side = nullptr;       // snapshot device-to-host copies
+    cudaStream_t capture = nullptr;    // graph capture
+    uint32_t n = 0, s = 0;
+    int accumulate = TITAN_ACCUM_CSR;
+    titan::StepConst c{};
+    bool has_c = false, has_act = false;
+    double dt = 0;
+
+    std::vector<uint32_t> caller_of_dev, dev_of_caller;
+    std::vector<float> inv_mass;          // caller order
+    std::vector<float> k, rest, damp;     // caller spring order
+    std::vector<float> act_amp, act_phase;
+    titan::SellHost sell;
+    titan::RecordsHost rec;
+
+    MassState *state[2] = {nullptr, nullptr};
+    long long *steps_dev = nullptr;       // [2]
+    int cur = 0;
+    uint64_t steps = 0;
+    uint32_t *d_dev_of_caller = nullptr;
+
+    uint32_t *d_slice_off = nullptr, *d_nbr = nullptr;
+    float2 *d_kl = nullptr, *d_act = nullptr;
+    float *d_c = nullptr;
+
+    uint4 *d_rec = nullptr;
+    float *d_rc = nullptr;
+    float2 *d_ract = nullptr;
+    float4 *d_force = nullptr;
+
+    int graph_chunk = kDefaultGraphChunk;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+
+    // snapshots: slot = ticket & 1
+    float *snap_dev[2] = {nullptr, nullptr};     // [2][n][3] pos then vel, caller order
+    float *snap_host[2] = {nullptr, nullptr};    // pinned, same layout
+    cudaEvent_t snap_ready[2] = {nullptr, nullptr};
+    cudaEvent_t snap_done[2] = {nullptr, nullptr};
+    double snap_t[2] = {0, 0};
+    uint64_t last_ticket = 0;
+
+    std::vector<void *> allocations;
+    std::string error;
+    std::atomic<bool> busy{false};
+};
+
+namespace {
+
+struct BusyGuard {
+    titan_sim *sim;
+    bool acquired;
+    explicit BusyGuard(titan_sim *s) : sim(s) { acquired = !sim->busy.exchange(true); }
+    ~BusyGuard() {
+        if (acquired) sim->busy.store(false);
+    }
+};
+
+titan_status fail(titan_sim *sim, titan_status st, const std::string &msg) {
+    if (sim) sim->error = msg;
+    else g_thread_error = msg;
+    return st;
+}
+
+titan_status fail_cuda(titan_sim *sim, cudaError_t e, const char *what) {
+    std::string msg = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return fail(sim, e == cudaErrorMemoryAllocation ? TITAN_E_OOM : TITAN_E_CUDA, msg);
+}
+
+#define TITAN_CK(sim, call)                                                  \
+    do {                                                                     \
+        cudaError_t e_ = (call);                                             \
+        if (e_ != cudaSuccess) return fail_cuda((sim), e_, #call);           \
+    } while (0)
+
+template <typename T>
+cudaError_t dev_alloc(titan_sim *sim, T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    void *raw = nullptr;
+    cudaError_t e = cudaMalloc(&raw, count * sizeof(T));
+    if (e != cudaSuccess) return e;
+    sim->allocations.push_back(raw);
+    *p = static_cast<T *>(raw);
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t upload(T *dst, const std::vector<T> &src, cudaStream_t st) {
+    if (src.empty()) return cudaSuccess;
+    return cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+}
+
+void free_graphs(titan_sim *sim) {
+    for (auto &g : sim->graph) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
+}
+
+void release(titan_sim *sim) {
+    free_graphs(sim);
+    for (int b = 0; b < 2; ++b) {
+        if (sim->snap_host[b]) cudaFreeHost(sim->snap_host[b]);
+        if (sim->snap_ready[b]) cudaEventDestroy(sim->snap_ready[b]);
+        if (sim->snap_done[b]) cudaEventDestroy(sim->snap_done[b]);
+    }
+    for (void *p : sim->allocations) cudaFree(p);
+    sim->allocations.clear();
+    if (sim->side) cudaStreamDestroy(sim->side);
+    if (sim->capture) cudaStreamDestroy(sim->capture);
+    if (sim->own_stream && sim->stream) cudaStreamDestroy(sim->stream);
+}
+
+titan_status validate(const titan_masses *m, const titan_springs *sp, const titan_params *p) {
+    if (!m || !sp || !p) return fail(nullptr, TITAN_E_INVALID, "null masses, springs or params");
+    if (m->n >= (1u << 31)) return fail(nullptr, TITAN_E_INVALID, "too many masses (>= 2^31)");
+    if (sp->n >= (1u << 30)) return fail(nullptr, TITAN_E_INVALID, "too many springs (>= 2^30)");
+    if (m->n && (!m->pos || !m->mass)) return fail(nullptr, TITAN_E_INVALID, "masses.pos and masses.mass are required");
+    if (sp->n && (!sp->ends || !sp->k)) return fail(nullptr, TITAN_E_INVALID, "springs.ends and springs.k are required");
+    if (!(finite(p->dt) && p->dt > 0)) return fail(nullptr, TITAN_E_INVALID, "params.dt must be finite and > 0");
+    for (int a = 0; a < 3; ++a)
+        if (!finite(p->gravity[a])) return fail(nullptr, TITAN_E_INVALID, "params.gravity must be finite");
+    if (!(finite(p->ground_k) && p->ground_k >= 0)) return fail(nullptr, TITAN_E_INVALID, "params.ground_k must be finite and >= 0");
+    if (!(finite(p->mu) && p->mu >= 0)) return fail(nullptr, TITAN_E_INVALID, "params.mu must be finite and >= 0");
+    if (!(finite(p->damping) && p->damping >= 0)) return fail(nullptr, TITAN_E_INVALID, "params.damping must be finite and >= 0");
+    if (p->accumulate != TITAN_ACCUM_CSR && p->accumulate != TITAN_ACCUM_ATOMIC)
+        return fail(nullptr, TITAN_E_INVALID, "params.accumulate must be TITAN_ACCUM_CSR or TITAN_ACCUM_ATOMIC");
+    if (p->order != TITAN_ORDER_INPUT && p->order != TITAN_ORDER_MORTON)
+        return fail(nullptr, TITAN_E_INVALID, "params.order must be TITAN_ORDER_INPUT or TITAN_ORDER_MORTON");
+    if (p->exec < TITAN_EXEC_AUTO || p->exec > TITAN_EXEC_PERSISTENT)
+        return fail(nullptr, TITAN_E_INVALID, "params.exec out of range");
+    if (p->device < 0) return fail(nullptr, TITAN_E_INVALID, "params.device must be >= 0");
+    for (uint64_t i = 0; i < m->n; ++i) {
+        for (int a = 0; a < 3; ++a) {
+            if (!finite(m->pos[3 * i + a])) return fail(nullptr, TITAN_E_INVALID, "masses.pos has a non-finite value at mass " + std::to_string(i));
+            if (m->vel && !finite(m->vel[3 * i + a])) return fail(nullptr, TITAN_E_INVALID, "masses.vel has a non-finite value at mass " + std::to_string(i));
+        }
+        if (!(finite(m->mass[i]) && m->mass[i] > 0)) return fail(nullptr, TITAN_E_INVALID, "masses.mass must be finite and > 0 (mass " + std::to_string(i) + ")");
+    }
+    for (uint64_t q = 0; q < sp->n; ++q) {
+        const uint32_t i = sp->ends[2 * q], j = sp->ends[2 * q + 1];
+        if (i >= m->n || j >= m->n) return fail(nullptr, TITAN_E_INVALID, "springs.ends index out of range at spring " + std::to_string(q));
+        if (i == j) return fail(nullptr, TITAN_E_INVALID, "spring " + std::to_string(q) + " joins a mass to itself");
+        if (!(finite(sp->k[q]) && sp->k[q] >= 0)) return fail(nullptr, TITAN_E_INVALID, "springs.k must be finite and >= 0 (spring " + std::to_string(q) + ")");
+        if (sp->rest && !(finite(sp->rest[q]) && sp->rest[q] >= 0)) return fail(nullptr, TITAN_E_INVALID, "springs.rest must be finite and >= 0 (spring " + std::to_string(q) + ")");
+        if (sp->damping && !(finite(sp->damping[q]) && sp->damping[q] >= 0)) return fail(nullptr, TITAN_E_INVALID, "springs.damping must be finite and >= 0 (spring " + std::to_string(q) + ")");
+    }
+    return TITAN_OK;
+}
+
+void fill_state(const titan_sim *sim, const double *pos, const double *vel, std::vector<MassState> &st) {
+    st.resize(sim->n);
+    for (uint32_t d = 0; d < sim->n; ++d) {
+        const uint32_t i = sim->caller_of_dev[d];
+        MassState m;
+        m.p = make_float4((float)pos[3 * (size_t)i], (float)pos[3 * (size_t)i + 1], (float)pos[3 * (size_t)i + 2], sim->inv_mass[i]);
+        if (vel) m.v = make_float4((float)vel[3 * (size_t)i], (float)vel[3 * (size_t)i + 1], (float)vel[3 * (size_t)i + 2], 0.f);
+        else m.v = make_float4(0.f, 0.f, 0.f, 0.f);
+        st[d] = m;
+    }
+}
+
+// Uploads the per-entry actuation arrays of the current layout.
+cudaError_t upload_actuation(titan_sim *sim) {
+    cudaError_t e;
+    if (sim->accumulate == TITAN_ACCUM_CSR) {
+        if (!sim->d_act && (e = dev_alloc(sim, &sim->d_act, sim->sell.entries)) != cudaSuccess) return e;
+        std::vector<float2> a(sim->sell.entries, make_float2(0.f, 0.f));
+        for (uint32_t e2 = 0; e2 < sim->sell.entries; ++e2) {
+            const uint32_t q = sim->sell.spring[e2];
+            if (q != UINT32_MAX) a[e2] = make_float2(sim->act_amp[q], sim->act_phase[q]);
+        }
+        return upload(sim->d_act, a, sim->stream);
+    }
+    if (!sim->d_ract && (e = dev_alloc(sim, &sim->d_ract, sim->s)) != cudaSuccess) return e;
+    std::vector<float2> a(sim->s);
+    for (uint32_t r = 0; r < sim->s; ++r) {
+        const uint32_t q = sim->rec.order[r];
+        a[r] = make_float2(sim->act_amp[q], sim->act_phase[q]);
+    }
+    return upload(sim->d_ract, a, sim->stream);
+}
+
+cudaError_t enqueue_step(titan_sim *sim, cudaStream_t st, int b) {
+    const MassState *in = sim->state[b];
+    MassState *out = sim->state[1 - b];
+    const long long *si = sim->steps_dev + b;
+    long long *so = sim->steps_dev + (1 - b);
+    if (sim->accumulate == TITAN_ACCUM_CSR) {
+        titan::SellView v{sim->d_slice_off, sim->d_nbr, sim->d_kl, sim->has_c ? sim->d_c : nullptr,
+                          sim->has_act ? sim->d_act : nullptr};
+        return titan::launch_step_sell(in, out, sim->n, v, sim->c, si, so, st);
+    }
+    titan::AtomicView v{sim->d_rec, sim->has_c ? sim->d_rc : nullptr,
+                        sim->has_act ? sim->d_ract : nullptr, sim->d_force, sim->s};
+    return titan::launch_step_atomic(in, out, sim->n, v, sim->c, si, so, st);
+}
+
+cudaError_t ensure_graph(titan_sim *sim, int b) {
+    if (sim->graph[b]) return cudaSuccess;
+    cudaError_t e = cudaStreamBeginCapture(sim->capture, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    cudaError_t le = cudaSuccess;
+    for (int k = 0; k < sim->graph_chunk && le == cudaSuccess; ++k) le = enqueue_step(sim, sim->capture, b ^ (k & 1));
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(sim->capture, &g);
+    if (le != cudaSuccess) { if (g) cudaGraphDestroy(g); return le; }
+    if (e != cudaSuccess) return e;
+    e = cudaGraphInstantiate(&sim->graph[b], g, 0);
+    cudaGraphDestroy(g);
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+void titan_default_params(titan_params *p) {
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->dt = 1e-4;
+    p->gravity[2] = -9.81;
+    p->ground = 0;
+    p->ground_k = 1e5;
+    p->mu = 0.5;
+    p->damping = 0.0;
+    p->accumulate = TITAN_ACCUM_CSR;
+    p->order = TITAN_ORDER_MORTON;
+    p->exec = TITAN_EXEC_AUTO;
+    p->device = 0;
+    p->stream = nullptr;
+    p->spin_limit = 0;
+    p->graph_chunk = 0;
+}
+
+titan_status titan_create(const titan_masses *m, const titan_springs *sp, const titan_params *p,
+                          titan_sim **out) {
+    if (!out) return fail(nullptr, TITAN_E_INVALID, "out is null");
+    titan_status vs = validate(m, sp, p);
+    if (vs != TITAN_OK) return vs;
+
+    DeviceGuard dg(p->device);
+    if (!dg.ok) return fail(nullptr, TITAN_E_CUDA, "cannot select CUDA device " + std::to_string(p->device));
+    titan_sim *sim = new titan_sim();
+    sim->device = p->device;
+    sim->n = m->n;
+    sim->s = sp->n;
+    sim->accumulate = p->accumulate;
+    sim->dt = p->dt;
+    sim->graph_chunk = p->graph_chunk == 0 ? kDefaultGraphChunk : (p->graph_chunk < 0 ? 0 : ((p->graph_chunk + 1) & ~1));
+    sim->c.dt = (float)p->dt;
+    sim->c.dt_d = p->dt;
+    sim->c.gx = (float)p->gravity[0];
+    sim->c.gy = (float)p->gravity[1];
+    sim->c.gz = (float)p->gravity[2];
+    sim->c.ground = p->ground ? 1 : 0;
+    sim->c.ground_k = (float)p->ground_k;
+    sim->c.mu = (float)p->mu;
+    sim->c.c_uniform = (float)p->damping;
+    sim->c.act_omega = 0.0;
+
+    auto bail = [&](titan_status st) {
+        g_thread_error = sim->error;
+        release(sim);
+        delete sim;
+        return st;
+    };
+#define CREATE_CK(call)                                                      \
+    do {                                                                     \
+        cudaError_t e_ = (call);                                             \
+        if (e_ != cudaSuccess) return bail(fail_cuda(sim, e_, #call));       \
+    } while (0)
+
+    if (p->stream) {
+        sim->stream = static_cast<cudaStream_t>(p->stream);
+    } else {
+        CREATE_CK(cudaStreamCreateWithFlags(&sim->stream, cudaStreamNonBlocking));
+        sim->own_stream = true;
+    }
+    CREATE_CK(cudaStreamCreateWithFlags(&sim->side, cudaStreamNonBlocking));
+    CREATE_CK(cudaStreamCreateWithFlags(&sim->capture, cudaStreamNonBlocking));
+
+    // ---- host-side layout
+    const uint32_t n = m->n, s = sp->n;
+    if (p->order == TITAN_ORDER_MORTON) {
+        titan::morton_order(m->pos, n, sim->caller_of_dev);
+    } else {
+        sim->caller_of_dev.resize(n);
+        for (uint32_t i = 0; i < n; ++i) sim->caller_of_dev[i] = i;
+    }
+    sim->dev_of_caller.resize(n);
+    for (uint32_t d = 0; d < n; ++d) sim->dev_of_caller[sim->caller_of_dev[d]] = d;
+    sim->inv_mass.resize(n);
+    for (uint32_t i = 0; i < n; ++i)
+        sim->inv_mass[i] = (m->fixed && m->fixed[i]) ? 0.f : (float)(1.0 / m->mass[i]);
+    sim->k.resize(s);
+    sim->rest.resize(s);
+    sim->damp.resize(s);
+    bool uniform_c = true;
+    for (uint32_t q = 0; q < s; ++q) {
+        const uint32_t i = sp->ends[2 * (size_t)q], j = sp->ends[2 * (size_t)q + 1];
+        sim->k[q] = (float)sp->k[q];
+        double L;
+        if (sp->rest) {
+            L = sp->rest[q];
+        } else {
+            const double dx = m->pos[3 * (size_t)j] - m->pos[3 * (size_t)i];
+            const double dy = m->pos[3 * (size_t)j + 1] - m->pos[3 * (size_t)i + 1];
+            const double dz = m->pos[3 * (size_t)j + 2] - m->pos[3 * (size_t)i + 2];
+            L = sqrt(dx * dx + dy * dy + dz * dz);
+        }
+        sim->rest[q] = (float)L;
+        sim->damp[q] = (float)(sp->damping ? sp->damping[q] : p->damping);
+        if (q && sim->damp[q] != sim->damp[0]) uniform_c = false;
+    }
+    sim->has_c = !uniform_c;
+    if (uniform_c && s) sim->c.c_uniform = sim->damp[0];
+
+    // ---- device state
+    CREATE_CK(dev_alloc(sim, &sim->state[0], n));
+    CREATE_CK(dev_alloc(sim, &sim->state[1], n));
+    CREATE_CK(dev_alloc(sim, &sim->steps_dev, 2));
+    CREATE_CK(dev_alloc(sim, &sim->d_dev_of_caller, n));
+    {
+        std::vector<MassState> st;
+        fill_state(sim, m->pos, m->vel, st);
+        CREATE_CK(upload(sim->state[0], st, sim->stream));
+        CREATE_CK(upload(sim->state[1], st, sim->stream));
+        CREATE_CK(upload(sim->d_dev_of_caller, sim->dev_of_caller, sim->stream));
+        CREATE_CK(cudaMemsetAsync(sim->steps_dev, 0, 2 * sizeof(long long), sim->stream));
+    }
+
+    if (sim->accumulate == TITAN_ACCUM_CSR) {
+        if (!titan::build_sell(n, s, sp->ends, sim->dev_of_caller, sim->sell))
+            return bail(fail(sim, TITAN_E_UNSUPPORTED, "padded incidence exceeds 2^32 entries"));
+        const uint32_t E = sim->sell.entries;
+        std::vector<float2> kl(E, make_float2(0.f, 0.f));
+        std::vector<float> cc;
+        if (sim->has_c) cc.assign(E, 0.f);
+        for (uint32_t e = 0; e < E; ++e) {
+            const uint32_t q = sim->sell.spring[e];
+            if (q == UINT32_MAX) continue;
+            kl[e] = make_float2(sim->k[q], sim->rest[q]);
+            if (sim->has_c) cc[e] = sim->damp[q];
+        }
+        CREATE_CK(dev_alloc(sim, &sim->d_slice_off, sim->sell.slice_off.size()));
+        CREATE_CK(dev_alloc(sim, &sim->d_nbr, E));
+        CREATE_CK(dev_alloc(sim, &sim->d_kl, E));
+        CREATE_CK(upload(sim->d_slice_off, sim->sell.slice_off, sim->stream));
+        CREATE_CK(upload(sim->d_nbr, sim->sell.nbr, sim->stream));
+        CREATE_CK(upload(sim->d_kl, kl, sim->stream));
+        if (sim->has_c) {
+            CREATE_CK(dev_alloc(sim, &sim->d_c, E));
+            CREATE_CK(upload(sim->d_c, cc, sim->stream));
+        }
+    } else {
+        titan::build_records(s, sp->ends, sim->dev_of_caller, sim->rec);
+        std::vector<uint4> r(s);
+        std::vector<float> cc;
+        if (sim->has_c) cc.resize(s);
+        for (uint32_t k = 0; k < s; ++k) {
+            const uint32_t q = sim->rec.order[k];
+            uint32_t kb, lb;
+            memcpy(&kb, &sim->k[q], 4);
+            memcpy(&lb, &sim->rest[q], 4);
+            r[k] = make_uint4(sim->dev_of_caller[sp->ends[2 * (size_t)q]], sim->dev_of_caller[sp->ends[2 * (size_t)q + 1]], kb, lb);
+            if (sim->has_c) cc[k] = sim->damp[q];
+        }
+        CREATE_CK(dev_alloc(sim, &sim->d_rec, s));
+        CREATE_CK(dev_alloc(sim, &sim->d_force, n));
+        CREATE_CK(upload(sim->d_rec, r, sim->stream));
+        CREATE_CK(cudaMemsetAsync(sim->d_force, 0, (size_t)(n ? n : 1) * sizeof(float4), sim->stream));
+        if (sim->has_c) {
+            CREATE_CK(dev_alloc(sim, &sim->d_rc, s));
+            CREATE_CK(upload(sim->d_rc, cc, sim->stream));
+        }
+    }
+    CREATE_CK(cudaStreamSynchronize(sim->stream));
+#undef CREATE_CK
+    *out = sim;
+    return TITAN_OK;
+}
+
+titan_status titan_step(titan_sim *sim, uint64_t n_steps) {
+    if (!sim) return fail(nullptr, TITAN_E_INVALID, "sim is null");
+    BusyGuard bg(sim);
+    if (!bg.acquired) return fail(sim, TITAN_E_BUSY, "another call on this handle is in progress");
+    DeviceGuard dg(sim->device);
+    TITAN_CK(sim, cudaGetLastError());
+    while (n_steps > 0) {
+        if (sim->graph_chunk > 0 && n_steps >= (uint64_t)sim->graph_chunk) {
+            TITAN_CK(sim, ensure_graph(sim, sim->cur));
+            TITAN_CK(sim, cudaGraphLaunch(sim->graph[sim->cur], sim->stream));
+            n_steps -= sim->graph_chunk;
+            sim->steps += sim->graph_chunk;      // even chunk: the parity is unchanged
+        } else {
+            TITAN_CK(sim, enqueue_step(sim, sim->stream, sim->cur));
+            sim->cur ^= 1;
+            --n_steps;
+            ++sim->steps;
+        }
+    }
+    return TITAN_OK;
+}
+
+titan_status titan_snapshot_async(titan_sim *sim, void *stream, uint64_t *ticket) {
+    if (!sim || !ticket) return fail(sim, TITAN_E_INVALID, "sim or ticket is null");
+    BusyGuard bg(sim);
+    if (!bg.acquired) return fail(sim, TITAN_E_BUSY, "another call on this handle is in progress");
+    DeviceGuard dg(sim->device);
+    cudaStream_t side = stream ? static_cast<cudaStream_t>(stream) : sim->side;
+    const uint64_t tk = sim->last_ticket + 1;
+    const int slot = (int)(tk & 1);
+    const size_t floats = 6 * (size_t)(sim->n ? sim->n : 1);
+    if (!sim->snap_dev[slot]) {
+        TITAN_CK(sim, dev_alloc(sim, &sim->snap_dev[slot], floats));
+        TITAN_CK(sim, cudaHostAlloc((void **)&sim->snap_host[slot], floats * sizeof(float), cudaHostAllocDefault));
+        TITAN_CK(sim, cudaEventCreateWithFlags(&sim->snap_ready[slot], cudaEventDisableTiming));
+        TITAN_CK(sim, cudaEventCreateWithFlags(&sim->snap_done[slot], cudaEventDisableTiming));
+    } else {
+        // the slot's previous device-to-host copy must be done before it is overwritten
+        TITAN_CK(sim, cudaStreamWaitEvent(sim->stream, sim->snap_done[slot], 0));
+    }
+    float *pos = sim->snap_dev[slot], *vel = pos + 3 * (size_t)sim->n;
+    TITAN_CK(sim, titan::launch_unpermute(sim->state[sim->cur], sim->d_dev_of_caller, sim->n, pos, vel, sim->stream));
+    TITAN_CK(sim, cudaEventRecord(sim->snap_ready[slot], sim->stream));
+    TITAN_CK(sim, cudaStreamWaitEvent(side, sim->snap_ready[slot], 0));
+    TITAN_CK(sim, cudaMemcpyAsync(sim->snap_host[slot], sim->snap_dev[slot], 6 * (size_t)sim->n * sizeof(float),
+                                  cudaMemcpyDeviceToHost, side));
+    TITAN_CK(sim, cudaEventRecord(sim->snap_done[slot], side));
+    sim->snap_t[slot] = (double)sim->steps * sim->dt;
+    sim->last_ticket = tk;
+    *ticket = tk;
+    return TITAN_OK;
+}
+
+titan_status titan_snapshot_wait(titan_sim *sim, uint64_t ticket, const float **pos, const float **vel,
+                                 double *t) {
+    if (!sim) return fail(nullptr, TITAN_E_INVALID, "sim is null");
+    BusyGuard bg(sim);
+    if (!bg.acquired) return fail(sim, TITAN_E_BUSY, "another call on this handle is in progress");
+    if (ticket == 0 || ticket > sim->last_ticket || sim->last_ticket - ticket >= 2)
+        return fail(sim, TITAN_E_INVALID, "snapshot ticket " + std::to_string(ticket) + " is unknown or overwritten");
+    DeviceGuard dg(sim->device);
+    const int slot = (int)(ticket & 1);
+    TITAN_CK(sim, cudaEventSynchronize(sim->snap_done[slot]));
+    if (pos) *pos = sim->snap_host[slot];
+    if (vel) *vel = sim->snap_host[slot] + 3 * (size_t)sim->n;
+    if (t) *t = sim->snap_t[slot];
+    return TITAN_OK;
+}
+
+titan_status titan_set_actuation(titan_sim *sim, uint32_t n, const uint32_t *ids, const float *amp,
+                                 const float *phase, float freq_hz) {
+    if (!sim) return fail(nullptr, TITAN_E_INVALID, "sim is null");
+    BusyGuard bg(sim);
+    if (!bg.acquired) return fail(sim, TITAN_E_BUSY, "another call on this handle is in progress");
+    if (n && (!ids || !amp || !phase)) return fail(sim, TITAN_E_INVALID, "spring_ids, amp and phase are required");
+    if (!std::isfinite(freq_hz)) return fail(sim, TITAN_E_INVALID, "freq_hz must be finite");
+    for (uint32_t q = 0; q < n; ++q) {
+        if (ids[q] >= sim->s) return fail(sim, TITAN_E_INVALID, "spring id out of range: " + std::to_string(ids[q]));
+        if (!std::isfinite(amp[q]) || !std::isfinite(phase[q])) return fail(sim, TITAN_E_INVALID, "non-finite amp or phase");
+    }
+    DeviceGuard dg(sim->device);
+    if (sim->act_amp.empty()) {
+        sim->act_amp.assign(sim->s, 0.f);
+        sim->act_phase.assign(sim->s, 0.f);
+    }
+    for (uint32_t q = 0; q < n; ++q) {
+        sim->act_amp[ids[q]] = amp[q];
+        sim->act_phase[ids[q]] = phase[q];
+    }
+    sim->c.act_omega = 2.0 * 3.14159265358979323846 * (double)freq_hz;
+    TITAN_CK(sim, upload_actuation(sim));
+    sim->has_act = true;
+    free_graphs(sim);       // kernel variant and constants changed
+    return TITAN_OK;
+}
+
+titan_status titan_set_state(titan_sim *sim, const double *pos, const double *vel) {
+    if (!sim) return fail(nullptr, TITAN_E_INVALID, "sim is null");
+    BusyGuard bg(sim);
+    if (!bg.acquired) return fail(sim, TITAN_E_BUSY, "another call on this handle is in progress");
+    if (sim->n && !pos) return fail(sim, TITAN_E_INVALID, "pos is required");
+    for (uint64_t i = 0; i < 3 * (uint64_t)sim->n; ++i)
+        if (!std::isfinite(pos[i]) || (vel && !std::isfinite(vel[i])))
+            return fail(sim, TITAN_E_INVALID, "non-finite pos or vel");
+    DeviceGuard dg(sim->device);
+    std::vector<MassState> st;
+    fill_state(sim, pos, vel, st);
+    TITAN_CK(sim, upload(sim->state[sim->cur], st, sim->stream));
+    // pageable source: the copy is staged before cudaMemcpyAsync returns
+    return TITAN_OK;
+}
+
+titan_status titan_read_state_dev(titan_sim *sim, float *pos_dev, float *vel_dev, void *stream) {
+    if (!sim) return fail(nullptr, TITAN_E_INVALID, "sim is null");
+    BusyGuard bg(sim);
+    if (!bg.acquired) return fail(sim, TITAN_E_BUSY, "another call on this handle is in progress");
+    DeviceGuard dg(sim->device);
+    TITAN_CK(sim, titan::launch_unpermute(sim->state[sim->cur], sim->d_dev_of_caller, sim->n, pos_dev,
+                                          vel_dev, sim->stream));
+    if (stream && static_cast<cudaStream_t>(stream) != sim->stream) {
+        cudaEvent_t ev;
+        TITAN_CK(sim, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        cudaError_t e = cudaEventRecord(ev, sim->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(static_cast<cudaStream_t>(stream), ev, 0);
+        cudaEventDestroy(ev);
+        TITAN_CK(sim, e);
+    }
+    return TITAN_OK;
+}
+
+titan_status titan_sync(titan_sim *sim) {
+    if (!sim) return fail(nullptr, TITAN_E_INVALID, "sim is null");
+    BusyGuard bg(sim);
+    if (!bg.acquired) return fail(sim, TITAN_E_BUSY, "another call on this handle is in progress");
+    DeviceGuard dg(sim->device);
+    TITAN_CK(sim, cudaStreamSynchronize(sim->stream));
+    TITAN_CK(sim, cudaStreamSynchronize(sim->side));
+    return TITAN_OK;
+}
+
+uint64_t titan_steps(const titan_sim *sim) { return sim ? sim->steps : 0; }
+
+const char *titan_last_error(const titan_sim *sim) {
+    return sim ? sim->error.c_str() : g_thread_error.c_str();
+}
+
+titan_status titan_destroy(titan_sim *sim) {
+    if (!sim) return TITAN_OK;
+    titan_status st = TITAN_OK;
+    {
+        DeviceGuard dg(sim->device);
+        if (cudaStreamSynchronize(sim->stream) != cudaSuccess) st = TITAN_E_CUDA;
+        if (sim->side && cudaStreamSynchronize(sim->side) != cudaSuccess) st = TITAN_E_CUDA;
+        release(sim);
+    }
+    delete sim;
+    return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,73 @@
+// titan_internal.h -- device layouts and kernel launchers of libtitan (GPU path only).
+//
+// Device layout (all in HBM, cudaMalloc'd, 256-byte aligned):
+//   MassState[n]  32 B per mass {x, y, z, 1/m | vx, vy, vz, 0}; one neighbour
+//                 gather is one 32-byte L2 sector.  1/m == 0 marks a fixed mass.
+//                 Two copies (ping-pong): step n reads one and writes the other.
+//   SELL-32 incidence (deterministic gather, K1): masses are taken in slices of
+//                 32 consecutive device indices; slice s holds W_s columns of 32
+//                 half-edge entries (column-major, entry = off[s] + 32 t + lane),
+//                 W_s = the slice's largest degree rounded up to even.  Per
+//                 entry: nbr (u32 device index) and {k, L0} (float2), optionally
+//                 c (float) and actuation {A, phi} (float2).  Padding entries
+//                 point at the mass itself with k = L0 = c = A = 0, which gives an
+//                 exactly zero force (a zero-length spring has no axis).
+//   Spring records (atomic scatter, K2): {i, j, k, L0} as one uint4 (128-bit
+//                 load), sorted by the lower device index, plus a float4 force
+//                 accumulator per mass.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace titan {
+
+struct __align__(16) MassState {
+    float4 p;   // x, y, z, 1/m (0: fixed)
+    float4 v;   // vx, vy, vz, unused (0)
+};
+static_assert(sizeof(MassState) == 32, "MassState must be one 32-byte sector");
+
+// Per-step constants shared by every kernel of one simulation.
+struct StepConst {
+    float dt;
+    float gx, gy, gz;
+    float ground_k;
+    float mu;
+    float c_uniform;      // dashpot when there is no per-spring damping array
+    int32_t ground;
+    double act_omega;     // 2 pi f (rad/s) of the sinusoidal actuation
+    double dt_d;          // dt in FP64 for the phase of the actuation clock
+};
+
+struct SellView {
+    const uint32_t *slice_off;   // [n_slices + 1] entry offsets
+    const uint32_t *nbr;         // [E]
+    const float2 *kl;            // [E] {k, L0}
+    const float *c;              // [E] or nullptr (uniform c)
+    const float2 *act;           // [E] {A, phi} or nullptr (no actuation)
+};
+
+struct AtomicView {
+    const uint4 *rec;            // [S] {i, j, bits(k), bits(L0)}
+    const float *c;              // [S] or nullptr
+    const float2 *act;           // [S] or nullptr
+    float4 *force;               // [n] accumulators, zero between steps
+    uint32_t n_springs;
+};
+
+// Step counters: steps[b] is the step index of the state in buffer b.  A step
+// that reads buffer b writes steps[1 - b] = steps[b] + 1.
+cudaError_t launch_step_sell(const MassState *in, MassState *out, uint32_t n, const SellView &v,
+                             const StepConst &c, const long long *step_in, long long *step_out,
+                             cudaStream_t stream);
+
+cudaError_t launch_step_atomic(const MassState *in, MassState *out, uint32_t n,
+                               const AtomicView &v, const StepConst &c, const long long *step_in,
+                               long long *step_out, cudaStream_t stream);
+
+// Gathers device-order state into caller order: pos/vel [n][3] float.
+cudaError_t launch_unpermute(const MassState *state, const uint32_t *dev_of_caller, uint32_t n,
+                             float *pos, float *vel, cudaStream_t stream);
+
+}  // namespace titan

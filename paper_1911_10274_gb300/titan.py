@@ -1,0 +1,245 @@
+"""Thin ctypes binding of libtitan.so (include/titan.h).
+
+Functions carry the C names and only marshal arguments: numpy arrays become
+host pointers, torch CUDA tensors and streams become device pointers and
+cudaStream_t handles.  Every step of the simulation runs in the library's
+CUDA kernels; there is no Python or CPU fallback - if the library cannot be
+built or loaded, loading fails with an error.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+TITAN_OK, TITAN_E_INVALID, TITAN_E_CUDA, TITAN_E_OOM, TITAN_E_TIMEOUT, TITAN_E_BUSY, \
+    TITAN_E_UNSUPPORTED = range(7)
+ACCUM_CSR, ACCUM_ATOMIC = 0, 1
+ORDER_INPUT, ORDER_MORTON = 0, 1
+EXEC_AUTO, EXEC_LAUNCH, EXEC_PERSISTENT = 0, 1, 2
+_STATUS = {0: "TITAN_OK", 1: "TITAN_E_INVALID", 2: "TITAN_E_CUDA", 3: "TITAN_E_OOM",
+           4: "TITAN_E_TIMEOUT", 5: "TITAN_E_BUSY", 6: "TITAN_E_UNSUPPORTED"}
+
+
+class TitanError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class titan_masses(C.Structure):
+    _fields_ = [("n", C.c_uint32), ("pos", C.c_void_p), ("vel", C.c_void_p),
+                ("mass", C.c_void_p), ("fixed", C.c_void_p)]
+
+
+class titan_springs(C.Structure):
+    _fields_ = [("n", C.c_uint32), ("ends", C.c_void_p), ("k", C.c_void_p),
+                ("rest", C.c_void_p), ("damping", C.c_void_p)]
+
+
+class titan_params(C.Structure):
+    _fields_ = [("dt", C.c_double), ("gravity", C.c_double * 3), ("ground", C.c_int32),
+                ("ground_k", C.c_double), ("mu", C.c_double), ("damping", C.c_double),
+                ("accumulate", C.c_int32), ("order", C.c_int32), ("exec", C.c_int32),
+                ("device", C.c_int32), ("stream", C.c_void_p), ("spin_limit", C.c_uint64),
+                ("graph_chunk", C.c_int32), ("reserved", C.c_int32 * 7)]
+
+
+_lib = None
+_lock = threading.Lock()
+_P = C.c_void_p
+
+
+def load(path: Optional[str] = None):
+    """Builds (if stale) and loads libtitan.so; raises if that is impossible."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib_path = path or _build.build()
+            lib = C.CDLL(lib_path)
+            S, u32, u64, f32 = C.c_int, C.c_uint32, C.c_uint64, C.c_float
+            sigs = {
+                "titan_default_params": (None, [C.POINTER(titan_params)]),
+                "titan_create": (S, [C.POINTER(titan_masses), C.POINTER(titan_springs),
+                                     C.POINTER(titan_params), C.POINTER(_P)]),
+                "titan_step": (S, [_P, u64]),
+                "titan_snapshot_async": (S, [_P, _P, C.POINTER(u64)]),
+                "titan_snapshot_wait": (S, [_P, u64, C.POINTER(C.POINTER(f32)),
+                                            C.POINTER(C.POINTER(f32)), C.POINTER(C.c_double)]),
+                "titan_set_actuation": (S, [_P, u32, _P, _P, _P, f32]),
+                "titan_set_state": (S, [_P, _P, _P]),
+                "titan_read_state_dev": (S, [_P, _P, _P, _P]),
+                "titan_sync": (S, [_P]),
+                "titan_steps": (u64, [_P]),
+                "titan_last_error": (C.c_char_p, [_P]),
+                "titan_destroy": (S, [_P]),
+            }
+            for name, (res, args) in sigs.items():
+                fn = getattr(lib, name)
+                fn.restype, fn.argtypes = res, args
+            _lib = lib
+    return _lib
+
+
+def _check(status: int, sim=None):
+    if status != TITAN_OK:
+        msg = load().titan_last_error(sim).decode(errors="replace")
+        raise TitanError(status, msg)
+
+
+def _ptr(a) -> Optional[int]:
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+# --------------------------------------------------------------------------- C names
+
+def titan_default_params() -> titan_params:
+    p = titan_params()
+    load().titan_default_params(C.byref(p))
+    return p
+
+
+def titan_create(masses: titan_masses, springs: titan_springs, params: titan_params) -> int:
+    out = _P()
+    _check(load().titan_create(C.byref(masses), C.byref(springs), C.byref(params), C.byref(out)))
+    return out.value
+
+
+def titan_step(sim: int, n_steps: int) -> None:
+    _check(load().titan_step(sim, n_steps), sim)
+
+
+def titan_snapshot_async(sim: int, stream: Optional[int] = None) -> int:
+    t = C.c_uint64()
+    _check(load().titan_snapshot_async(sim, stream, C.byref(t)), sim)
+    return t.value
+
+
+def titan_snapshot_wait(sim: int, ticket: int, n: int):
+    """Returns (pos, vel, t); pos/vel are numpy copies [n][3] float32."""
+    p, v, t = C.POINTER(C.c_float)(), C.POINTER(C.c_float)(), C.c_double()
+    _check(load().titan_snapshot_wait(sim, ticket, C.byref(p), C.byref(v), C.byref(t)), sim)
+    if n == 0:
+        return np.zeros((0, 3), np.float32), np.zeros((0, 3), np.float32), t.value
+    pos = np.ctypeslib.as_array(p, shape=(n, 3)).copy()
+    vel = np.ctypeslib.as_array(v, shape=(n, 3)).copy()
+    return pos, vel, t.value
+
+
+def titan_set_actuation(sim: int, spring_ids, amp, phase, freq_hz: float) -> None:
+    ids = np.ascontiguousarray(spring_ids, dtype=np.uint32)
+    a = np.ascontiguousarray(amp, dtype=np.float32)
+    ph = np.ascontiguousarray(phase, dtype=np.float32)
+    if not (ids.shape == a.shape == ph.shape):
+        raise ValueError("spring_ids, amp and phase must have the same length")
+    _check(load().titan_set_actuation(sim, ids.size, _ptr(ids), _ptr(a), _ptr(ph), float(freq_hz)), sim)
+
+
+def titan_set_state(sim: int, pos, vel=None) -> None:
+    p = np.ascontiguousarray(pos, dtype=np.float64)
+    v = None if vel is None else np.ascontiguousarray(vel, dtype=np.float64)
+    _check(load().titan_set_state(sim, _ptr(p), _ptr(v)), sim)
+
+
+def titan_read_state_dev(sim: int, pos_dev=None, vel_dev=None, stream: Optional[int] = None) -> None:
+    _check(load().titan_read_state_dev(sim, _ptr(pos_dev), _ptr(vel_dev), stream), sim)
+
+
+def titan_sync(sim: int) -> None:
+    _check(load().titan_sync(sim), sim)
+
+
+def titan_steps(sim: int) -> int:
+    return int(load().titan_steps(sim))
+
+
+def titan_last_error(sim: Optional[int] = None) -> str:
+    return load().titan_last_error(sim).decode(errors="replace")
+
+
+def titan_destroy(sim: int) -> None:
+    _check(load().titan_destroy(sim))
+
+
+# --------------------------------------------------------------------------- convenience
+
+class Sim:
+    """Owns one titan_sim handle built from an ``inputs.System``-like object."""
+
+    def __init__(self, system, accumulate: int = ACCUM_CSR, order: int = ORDER_MORTON,
+                 exec_mode: int = EXEC_AUTO, graph_chunk: int = 0, stream: Optional[int] = None,
+                 device: int = 0, per_spring_damping: bool = False):
+        load()
+        self.n = int(system.pos.shape[0])
+        self.s = int(system.ends.shape[0])
+        self.dt = float(system.dt)
+        self._keep = dict(
+            pos=np.ascontiguousarray(system.pos, dtype=np.float64),
+            vel=np.ascontiguousarray(system.vel, dtype=np.float64),
+            mass=np.ascontiguousarray(system.mass, dtype=np.float64),
+            fixed=np.ascontiguousarray(system.fixed, dtype=np.uint8),
+            ends=np.ascontiguousarray(system.ends, dtype=np.uint32),
+            k=np.ascontiguousarray(system.k, dtype=np.float64),
+            rest=np.ascontiguousarray(system.rest, dtype=np.float64),
+            damping=np.ascontiguousarray(system.damping, dtype=np.float64))
+        kp = self._keep
+        m = titan_masses(self.n, _ptr(kp["pos"]), _ptr(kp["vel"]), _ptr(kp["mass"]), _ptr(kp["fixed"]))
+        sp = titan_springs(self.s, _ptr(kp["ends"]), _ptr(kp["k"]), _ptr(kp["rest"]), _ptr(kp["damping"]))
+        p = titan_default_params()
+        p.dt = self.dt
+        p.gravity = (C.c_double * 3)(*[float(g) for g in system.gravity])
+        p.ground = 1 if system.ground else 0
+        p.ground_k = float(system.ground_k)
+        p.mu = float(system.mu)
+        p.accumulate, p.order, p.exec, p.device = accumulate, order, exec_mode, device
+        p.graph_chunk = graph_chunk
+        p.stream = stream
+        self.handle = titan_create(m, sp, p)
+        self._keep = None
+        if getattr(system, "act_amp", None) is not None:
+            ids = np.arange(self.s, dtype=np.uint32)
+            titan_set_actuation(self.handle, ids, system.act_amp, system.act_phase, system.act_freq)
+
+    def step(self, n: int) -> "Sim":
+        titan_step(self.handle, n)
+        return self
+
+    def snapshot(self):
+        """(pos, vel, t) after every step enqueued so far (float32, caller order)."""
+        return titan_snapshot_wait(self.handle, titan_snapshot_async(self.handle), self.n)
+
+    def set_state(self, pos, vel=None) -> None:
+        titan_set_state(self.handle, pos, vel)
+
+    def sync(self) -> None:
+        titan_sync(self.handle)
+
+    @property
+    def steps(self) -> int:
+        return titan_steps(self.handle)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            titan_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,274 @@
+"""GPU (FP32, through the C ABI) vs the FP64 oracle, element by element.
+
+Tolerance: the maximum position error must stay within 1e-4 of the lattice
+spacing (1e-5 m for the 0.1 m lattices) after 1000 steps without contact and
+after 100 steps with contact.  Velocities are checked at a looser bound derived
+from the same position bound (velocity error ~ position error / (few dt)).
+The deterministic (CSR) mode must be bit-identical from run to run.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1911_10274_gb300 import inputs
+from paper_1911_10274_gb300 import titan as T
+
+pytestmark = pytest.mark.gpu
+
+POS_TOL_FRAC = 1e-4      # of the lattice spacing
+
+
+def gpu_run(sys, steps, **kw):
+    with T.Sim(sys, **kw) as sim:
+        sim.step(steps)
+        pos, vel, t = sim.snapshot()
+    return pos.astype(np.float64), vel.astype(np.float64), t
+
+
+def check(sys, steps, step0=0, spacing=None, **kw):
+    spacing = sys.spacing if spacing is None else spacing
+    xo, vo = oracle.run(sys, steps, step0=step0)
+    xg, vg, t = gpu_run(sys, steps, **kw)
+    err = np.abs(xg - xo).max()
+    assert err <= POS_TOL_FRAC * spacing, f"max position error {err:.3e} > {POS_TOL_FRAC * spacing:.1e}"
+    verr = np.abs(vg - vo).max()
+    assert verr <= 1e3 * POS_TOL_FRAC * spacing, f"max velocity error {verr:.3e}"
+    assert t == pytest.approx(steps * sys.dt, rel=1e-12)
+    return err
+
+
+MODES = [dict(accumulate=T.ACCUM_CSR), dict(accumulate=T.ACCUM_ATOMIC),
+         dict(accumulate=T.ACCUM_CSR, order=T.ORDER_INPUT),
+         dict(accumulate=T.ACCUM_CSR, graph_chunk=-1)]
+MODE_IDS = ["csr", "atomic", "csr-input-order", "csr-no-graph"]
+
+
+@pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
+def test_cube_free_fall_1000_steps(mode):
+    """Bouncing-cube workload, first 1000 steps (pure fall, no contact yet)."""
+    check(inputs.cube_drop(), 1000, **mode)
+
+
+def _contact_start():
+    sys = inputs.cube_drop()
+    x, v = oracle.run(sys, 3150)
+    s2 = sys.copy()
+    s2.pos, s2.vel = x, v
+    return s2
+
+
+@pytest.mark.parametrize("mode", MODES[:2], ids=MODE_IDS[:2])
+def test_cube_contact_100_steps(mode):
+    """From the oracle's state at step 3150 (just before the cube lands), 100
+    steps through the first ground contact."""
+    sys = _contact_start()
+    xo, _ = oracle.run(sys, 100)
+    assert xo[:, 2].min() < 0, "the window must contain ground contact"
+    check(sys, 100, **mode)
+
+
+@pytest.mark.parametrize("mode", MODES[:2], ids=MODE_IDS[:2])
+def test_cube_penetrating_and_sliding_100_steps(mode):
+    """Cube placed 1 mm into the ground, sliding at 0.1 m/s: penalty contact
+    and capped Coulomb friction on every bottom mass from the first step."""
+    sys = inputs.cube_drop(drop_height=-1e-3)
+    sys.vel[:, 0] = 0.1
+    sys.vel[:, 1] = -0.05
+    check(sys, 100, **mode)
+
+
+@pytest.mark.parametrize("mode", MODES[:2], ids=MODE_IDS[:2])
+def test_cube_with_perturbed_rest_lengths_1000_steps(mode):
+    """Same topology with rest lengths x U(0.95, 1.05) and lognormal k, so the
+    internal spring forces are large from the first step."""
+    sys = inputs.cube_drop(drop_height=2.0)
+    rng = np.random.default_rng(7)
+    sys.rest = sys.rest * rng.uniform(0.95, 1.05, sys.n_springs)
+    sys.k = 1e4 * np.exp(0.5 * rng.standard_normal(sys.n_springs))
+    check(sys, 1000, **mode)
+
+
+def test_per_spring_damping():
+    sys = inputs.cube_drop(drop_height=2.0)
+    rng = np.random.default_rng(3)
+    sys.damping = rng.uniform(0.0, 3.0, sys.n_springs)
+    sys.rest = sys.rest * rng.uniform(0.97, 1.03, sys.n_springs)
+    check(sys, 1000)
+    check(sys, 1000, accumulate=T.ACCUM_ATOMIC)
+
+
+@pytest.mark.parametrize("accumulate", [T.ACCUM_CSR, T.ACCUM_ATOMIC], ids=["csr", "atomic"])
+def test_large_lattice_scaled_down(accumulate):
+    """The 1M-mass workload's recipe at 20^3: fixed bottom layer, perturbed
+    rest lengths, lognormal k, no ground, dt = 5e-5, 1000 steps."""
+    sys = inputs.large_lattice(n=20, seed=0)
+    check(sys, 1000, accumulate=accumulate)
+    xg, vg, _ = gpu_run(sys, 1000, accumulate=accumulate)
+    fx = sys.fixed.astype(bool)
+    assert np.array_equal(xg[fx], sys.pos[fx].astype(np.float32).astype(np.float64))
+    assert np.all(vg[fx] == 0.0)
+
+
+@pytest.mark.parametrize("order", [T.ORDER_INPUT, T.ORDER_MORTON], ids=["random-order", "morton"])
+def test_random_mesh_scaled_down(order):
+    """Unstructured kNN mesh (random index order) at 5,000 points, ground on,
+    dt = 2e-5, 500 steps; tolerance relative to the mean point spacing."""
+    sys = inputs.random_mesh(n_points=5000, seed=1, lift=0.0)
+    check(sys, 500, order=order)
+
+
+def test_actuated_robot_1000_steps():
+    """One robot of the batched workload: a 6x4x3 lattice resting on the
+    ground, 30% of springs actuated L0 (1 + A sin(2 pi 2 t + phi))."""
+    sys = inputs.actuated_box(6, 4, 3, np.random.default_rng(11))
+    assert (sys.act_amp > 0).any()
+    check(sys, 1000)
+    check(sys, 1000, accumulate=T.ACCUM_ATOMIC)
+
+
+def test_actuation_set_mid_run_uses_absolute_time():
+    """Actuation switched on after 300 steps uses t = step dt of the running
+    simulation (not time since the call)."""
+    sys = inputs.actuated_box(4, 4, 3, np.random.default_rng(5))
+    plain = sys.copy()
+    plain.act_amp = None
+    x, v = oracle.run(plain, 300)
+    mid = sys.copy()
+    mid.pos, mid.vel = x, v
+    xo, vo = oracle.run(mid, 200, step0=300)
+    with T.Sim(plain) as sim:
+        sim.step(300)
+        T.titan_set_actuation(sim.handle, np.arange(sys.n_springs), sys.act_amp, sys.act_phase,
+                              sys.act_freq)
+        sim.step(200)
+        xg, _, _ = sim.snapshot()
+    assert np.abs(xg - xo).max() <= POS_TOL_FRAC * sys.spacing
+
+
+def test_deterministic_mode_is_bit_exact_across_runs():
+    sys = inputs.cube_drop(drop_height=0.05)
+    sys.vel[:, 0] = 0.2
+    a = gpu_run(sys, 2000)
+    b = gpu_run(sys, 2000)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_resume_from_snapshot_is_bit_exact():
+    """Resume on the same handle (set_state) and in a new handle (create from
+    the snapshot, input order) both reproduce the uninterrupted run bit for bit."""
+    sys = inputs.cube_drop(drop_height=0.05)
+    sys.vel[:, 1] = 0.3
+    full, _, _ = gpu_run(sys, 800, order=T.ORDER_INPUT)
+    with T.Sim(sys, order=T.ORDER_INPUT) as sim:
+        sim.step(400)
+        p, v, _ = sim.snapshot()
+        sim.set_state(p.astype(np.float64), v.astype(np.float64))
+        sim.step(400)
+        same, _, _ = sim.snapshot()
+    s2 = sys.copy()
+    s2.pos, s2.vel = p.astype(np.float64), v.astype(np.float64)
+    fresh, _, _ = gpu_run(s2, 400, order=T.ORDER_INPUT)
+    assert np.array_equal(same, full)
+    assert np.array_equal(fresh, full)
+
+
+def test_graph_replay_matches_direct_launches_bit_exact():
+    sys = inputs.cube_drop(drop_height=0.02)
+    a = gpu_run(sys, 300, graph_chunk=64)
+    b = gpu_run(sys, 300, graph_chunk=-1)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+# --------------------------------------------------------------------------- edge cases
+
+def test_single_mass_free_fall_and_empty_spring_list():
+    sys = inputs.System(pos=np.array([[0.3, -0.2, 5.0]]), vel=np.array([[1.0, 0.0, 0.0]]),
+                        mass=np.array([2.0]), fixed=np.zeros(1, np.uint8),
+                        ends=np.zeros((0, 2), np.uint32), k=np.zeros(0), rest=np.zeros(0),
+                        damping=np.zeros(0), dt=1e-3, ground=True, spacing=0.1)
+    check(sys, 500)
+    check(sys, 500, accumulate=T.ACCUM_ATOMIC)
+
+
+def test_empty_system():
+    sys = inputs.System(pos=np.zeros((0, 3)), vel=np.zeros((0, 3)), mass=np.zeros(0),
+                        fixed=np.zeros(0, np.uint8), ends=np.zeros((0, 2), np.uint32),
+                        k=np.zeros(0), rest=np.zeros(0), damping=np.zeros(0), dt=1e-3)
+    for acc in (T.ACCUM_CSR, T.ACCUM_ATOMIC):
+        pos, vel, t = gpu_run(sys, 10, accumulate=acc)
+        assert pos.shape == (0, 3) and t == pytest.approx(0.01)
+
+
+def test_ragged_sizes_and_zero_length_spring():
+    """33 masses (one full slice plus one lane), uneven degrees, some fixed
+    masses, and a spring whose two masses coincide and move together (zero
+    length: no axis, no force, no NaN)."""
+    rng = np.random.default_rng(4)
+    n = 33
+    pos = rng.uniform(0, 0.5, (n, 3))
+    pos[5] = pos[4]
+    vel = rng.normal(0, 0.1, (n, 3))
+    vel[5] = vel[4]
+    ends = [(4, 5)] + [(i, j) for i in range(n) for j in range(i + 1, n)
+                       if i not in (4, 5) and j not in (4, 5) and rng.random() < 0.2]
+    ends = np.array(ends, np.uint32)
+    d = np.linalg.norm(pos[ends[:, 1]] - pos[ends[:, 0]], axis=1)
+    fixed = (rng.random(n) < 0.1).astype(np.uint8)
+    fixed[4] = fixed[5] = 0
+    sys = inputs.System(pos=pos, vel=vel, mass=rng.uniform(0.05, 0.2, n), fixed=fixed, ends=ends,
+                        k=rng.uniform(100, 1000, len(ends)), rest=d * rng.uniform(0.9, 1.1, len(ends)),
+                        damping=np.full(len(ends), 0.1), dt=1e-4, gravity=(0, 0, -9.81), spacing=0.1)
+    sys.rest[0] = 0.05
+    sys.mass[5] = sys.mass[4]
+    for acc in (T.ACCUM_CSR, T.ACCUM_ATOMIC):
+        check(sys, 200, accumulate=acc)
+        xg, vg, _ = gpu_run(sys, 200, accumulate=acc)
+        assert np.all(np.isfinite(xg)) and np.array_equal(xg[4], xg[5])
+
+
+def test_snapshot_tickets_and_double_buffer():
+    sys = inputs.cube_drop(n=3)
+    with T.Sim(sys) as sim:
+        t1 = T.titan_snapshot_async(sim.handle)
+        sim.step(10)
+        t2 = T.titan_snapshot_async(sim.handle)
+        sim.step(10)
+        p2, _, tt2 = T.titan_snapshot_wait(sim.handle, t2, sim.n)
+        p1, _, tt1 = T.titan_snapshot_wait(sim.handle, t1, sim.n)
+        assert tt1 == 0.0 and tt2 == pytest.approx(10 * sys.dt)
+        np.testing.assert_array_equal(p1, sys.pos.astype(np.float32))
+        t3 = T.titan_snapshot_async(sim.handle)
+        with pytest.raises(T.TitanError) as ei:
+            T.titan_snapshot_wait(sim.handle, t1, sim.n)      # overwritten by t3
+        assert ei.value.status == T.TITAN_E_INVALID
+        p3, _, tt3 = T.titan_snapshot_wait(sim.handle, t3, sim.n)
+        assert tt3 == pytest.approx(20 * sys.dt)
+        xo, _ = oracle.run(sys, 20)
+        assert np.abs(p3 - xo).max() <= POS_TOL_FRAC * sys.spacing
+
+
+def test_read_state_into_torch_tensors():
+    torch = pytest.importorskip("torch")
+    sys = inputs.cube_drop(n=4)
+    stream = torch.cuda.current_stream()
+    with T.Sim(sys, stream=stream.cuda_stream) as sim:
+        sim.step(50)
+        pos = torch.empty((sim.n, 3), dtype=torch.float32, device="cuda")
+        vel = torch.empty_like(pos)
+        T.titan_read_state_dev(sim.handle, pos, vel, stream.cuda_stream)
+        xo, vo = oracle.run(sys, 50)
+        assert np.abs(pos.cpu().numpy() - xo).max() <= POS_TOL_FRAC * sys.spacing
+
+
+def test_full_size_lattice_against_oracle_in_bench_configuration():
+    """The 1M-mass, 12.7M-spring lattice in the benchmark's configuration
+    (CSR, Morton order, 64-step graphs): 64 steps compared with the oracle on
+    every mass, and the fixed bottom layer exactly still."""
+    sys = inputs.large_lattice(n=100, seed=0)
+    xo, vo = oracle.run(sys, 64)
+    for acc in (T.ACCUM_CSR, T.ACCUM_ATOMIC):
+        xg, vg, _ = gpu_run(sys, 64, accumulate=acc)
+        err = np.abs(xg - xo).max()
+        assert err <= POS_TOL_FRAC * sys.spacing, err
+        fx = sys.fixed.astype(bool)
+        assert np.array_equal(xg[fx], sys.pos[fx].astype(np.float32).astype(np.float64))
