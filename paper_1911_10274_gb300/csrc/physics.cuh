@@ -1,0 +1,65 @@
+// physics.cuh -- the arithmetic of one spring and one mass, shared by every
+// kernel of the GPU path (Titan Sec. III-B, Eq. 1; Sec. III-A constraints).
+#pragma once
+
+#include "titan_internal.h"
+
+namespace titan {
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+// Phase of the actuation clock at step `step`: 2 pi f t mod 2 pi with
+// t = step dt, formed in FP64 so that long runs keep full FP32 phase accuracy.
+__device__ __forceinline__ float clock_phase(const StepConst &c, long long step) {
+    double ph = c.act_omega * ((double)step * c.dt_d);
+    ph -= kTwoPi * floor(ph / kTwoPi);
+    return (float)ph;
+}
+
+// Force on the mass at (p, v) from one spring to the mass at (q, w):
+// accumulates f u into (fx, fy, fz).  A zero-length spring contributes 0.
+__device__ __forceinline__ void spring_force(const float4 &p, const float4 &v, const float4 &q,
+                                             const float4 &w, float k, float L, float c,
+                                             float &fx, float &fy, float &fz) {
+    const float dx = q.x - p.x, dy = q.y - p.y, dz = q.z - p.z;
+    const float l2 = dx * dx + dy * dy + dz * dz;
+    const float l = sqrtf(l2);
+    const float inv = l2 > 0.f ? 1.0f / l : 0.f;
+    const float ux = dx * inv, uy = dy * inv, uz = dz * inv;
+    const float rate = (w.x - v.x) * ux + (w.y - v.y) * uy + (w.z - v.z) * uz;
+    const float f = k * (l - L) + c * rate;
+    fx += f * ux;
+    fy += f * uy;
+    fz += f * uz;
+}
+
+// The mass pass for one mass: gravity, ground contact with capped Coulomb
+// friction, velocity-first Euler, fixed-mass constraint.
+template <bool GROUND>
+__device__ __forceinline__ void integrate(const float4 &p, const float4 &v, float fx, float fy,
+                                          float fz, const StepConst &c, MassState *out) {
+    const float im = p.w;
+    float4 xn, vn;
+    if (im == 0.f) {
+        xn = p;
+        vn = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+        float ax = fx * im + c.gx, ay = fy * im + c.gy, az = fz * im + c.gz;
+        if (GROUND && p.z < 0.f) {
+            const float an = c.ground_k * (-p.z) * im;       // normal force / m
+            az += an;
+            const float vt = sqrtf(v.x * v.x + v.y * v.y);
+            if (vt > 0.f) {
+                const float fr = fminf(c.mu * an, vt / c.dt);  // |friction| / m, capped
+                ax -= fr * (v.x / vt);
+                ay -= fr * (v.y / vt);
+            }
+        }
+        vn = make_float4(v.x + ax * c.dt, v.y + ay * c.dt, v.z + az * c.dt, 0.f);
+        xn = make_float4(p.x + vn.x * c.dt, p.y + vn.y * c.dt, p.z + vn.z * c.dt, im);
+    }
+    out->p = xn;
+    out->v = vn;
+}
+
+}  // namespace titan

@@ -25,6 +25,7 @@ namespace {
 thread_local std::string g_thread_error = "";
 
 constexpr int kDefaultGraphChunk = 64;
+constexpr uint32_t kDefaultSpinLimit = 1u << 22;
 
 struct DeviceGuard {
     int prev = -1;
@@ -77,6 +78,9 @@ struct titan_sim {
     float4 *d_force = nullptr;
 
     int graph_chunk = kDefaultGraphChunk;
+    int kernel_variant = 0;
+    uint32_t spin_limit = kDefaultSpinLimit;
+    int *d_err = nullptr;                 // device error flag (bounded waits)
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
 
     // snapshots: slot = ticket & 1
@@ -178,6 +182,7 @@ titan_status validate(const titan_masses *m, const titan_springs *sp, const tita
     if (p->exec < TITAN_EXEC_AUTO || p->exec > TITAN_EXEC_PERSISTENT)
         return fail(nullptr, TITAN_E_INVALID, "params.exec out of range");
     if (p->device < 0) return fail(nullptr, TITAN_E_INVALID, "params.device must be >= 0");
+    if (p->kernel_variant < 0 || p->kernel_variant > 1) return fail(nullptr, TITAN_E_INVALID, "params.kernel_variant must be 0 or 1");
     for (uint64_t i = 0; i < m->n; ++i) {
         for (int a = 0; a < 3; ++a) {
             if (!finite(m->pos[3 * i + a])) return fail(nullptr, TITAN_E_INVALID, "masses.pos has a non-finite value at mass " + std::to_string(i));
@@ -236,12 +241,25 @@ cudaError_t enqueue_step(titan_sim *sim, cudaStream_t st, int b) {
     long long *so = sim->steps_dev + (1 - b);
     if (sim->accumulate == TITAN_ACCUM_CSR) {
         titan::SellView v{sim->d_slice_off, sim->d_nbr, sim->d_kl, sim->has_c ? sim->d_c : nullptr,
-                          sim->has_act ? sim->d_act : nullptr};
+                          sim->has_act ? sim->d_act : nullptr, sim->kernel_variant, sim->spin_limit,
+                          sim->d_err};
         return titan::launch_step_sell(in, out, sim->n, v, sim->c, si, so, st);
     }
     titan::AtomicView v{sim->d_rec, sim->has_c ? sim->d_rc : nullptr,
                         sim->has_act ? sim->d_ract : nullptr, sim->d_force, sim->s};
     return titan::launch_step_atomic(in, out, sim->n, v, sim->c, si, so, st);
+}
+
+// Reads (and clears) the device error flag set by bounded waits that expired.
+// The caller has synchronised the simulation stream.
+titan_status check_device_error(titan_sim *sim) {
+    int flag = 0;
+    TITAN_CK(sim, cudaMemcpy(&flag, sim->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        TITAN_CK(sim, cudaMemset(sim->d_err, 0, sizeof(int)));
+        return fail(sim, TITAN_E_TIMEOUT, "a bounded device wait expired; the affected steps did not complete");
+    }
+    return TITAN_OK;
 }
 
 cudaError_t ensure_graph(titan_sim *sim, int b) {
@@ -306,6 +324,9 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
     sim->c.mu = (float)p->mu;
     sim->c.c_uniform = (float)p->damping;
     sim->c.act_omega = 0.0;
+    sim->kernel_variant = p->kernel_variant;
+    sim->spin_limit = p->spin_limit == 0 ? kDefaultSpinLimit
+                                         : (uint32_t)(p->spin_limit > 0xffffffffull ? 0xffffffffull : p->spin_limit);
 
     auto bail = [&](titan_status st) {
         g_thread_error = sim->error;
@@ -368,6 +389,8 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
     CREATE_CK(dev_alloc(sim, &sim->state[0], n));
     CREATE_CK(dev_alloc(sim, &sim->state[1], n));
     CREATE_CK(dev_alloc(sim, &sim->steps_dev, 2));
+    CREATE_CK(dev_alloc(sim, &sim->d_err, 1));
+    CREATE_CK(cudaMemsetAsync(sim->d_err, 0, sizeof(int), sim->stream));
     CREATE_CK(dev_alloc(sim, &sim->d_dev_of_caller, n));
     {
         std::vector<MassState> st;
@@ -492,6 +515,10 @@ titan_status titan_snapshot_wait(titan_sim *sim, uint64_t ticket, const float **
     DeviceGuard dg(sim->device);
     const int slot = (int)(ticket & 1);
     TITAN_CK(sim, cudaEventSynchronize(sim->snap_done[slot]));
+    {
+        titan_status es = check_device_error(sim);
+        if (es != TITAN_OK) return es;
+    }
     if (pos) *pos = sim->snap_host[slot];
     if (vel) *vel = sim->snap_host[slot] + 3 * (size_t)sim->n;
     if (t) *t = sim->snap_t[slot];
@@ -566,7 +593,7 @@ titan_status titan_sync(titan_sim *sim) {
     DeviceGuard dg(sim->device);
     TITAN_CK(sim, cudaStreamSynchronize(sim->stream));
     TITAN_CK(sim, cudaStreamSynchronize(sim->side));
-    return TITAN_OK;
+    return check_device_error(sim);
 }
 
 uint64_t titan_steps(const titan_sim *sim) { return sim ? sim->steps : 0; }

@@ -14,68 +14,16 @@
 // K2 (k_springs_atomic + k_masses_atomic) is the paper's default scatter: one
 // thread per spring adds f u to both masses with vector atomics, then one
 // thread per mass integrates and clears the accumulator.
+#include <atomic>
+
+#include "physics.cuh"
+#include "ptx.cuh"
 #include "titan_internal.h"
 
 namespace titan {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr double kTwoPi = 6.283185307179586476925286766559;
-
-
-// Phase of the actuation clock at step `step`: 2 pi f t mod 2 pi with
-// t = step dt, formed in FP64 so that long runs keep full FP32 phase accuracy.
-__device__ __forceinline__ float clock_phase(const StepConst &c, long long step) {
-    double ph = c.act_omega * ((double)step * c.dt_d);
-    ph -= kTwoPi * floor(ph / kTwoPi);
-    return (float)ph;
-}
-
-// Force on the mass at (p, v) from one spring to the mass at (q, w):
-// accumulates f u into (fx, fy, fz).  A zero-length spring contributes 0.
-__device__ __forceinline__ void spring_force(const float4 &p, const float4 &v, const float4 &q,
-                                             const float4 &w, float k, float L, float c,
-                                             float &fx, float &fy, float &fz) {
-    const float dx = q.x - p.x, dy = q.y - p.y, dz = q.z - p.z;
-    const float l2 = dx * dx + dy * dy + dz * dz;
-    const float l = sqrtf(l2);
-    const float inv = l2 > 0.f ? 1.0f / l : 0.f;
-    const float ux = dx * inv, uy = dy * inv, uz = dz * inv;
-    const float rate = (w.x - v.x) * ux + (w.y - v.y) * uy + (w.z - v.z) * uz;
-    const float f = k * (l - L) + c * rate;
-    fx += f * ux;
-    fy += f * uy;
-    fz += f * uz;
-}
-
-// The mass pass for one mass: gravity, ground contact with capped Coulomb
-// friction, velocity-first Euler, fixed-mass constraint.
-template <bool GROUND>
-__device__ __forceinline__ void integrate(const float4 &p, const float4 &v, float fx, float fy,
-                                          float fz, const StepConst &c, MassState *out) {
-    const float im = p.w;
-    float4 xn, vn;
-    if (im == 0.f) {
-        xn = p;
-        vn = make_float4(0.f, 0.f, 0.f, 0.f);
-    } else {
-        float ax = fx * im + c.gx, ay = fy * im + c.gy, az = fz * im + c.gz;
-        if (GROUND && p.z < 0.f) {
-            const float an = c.ground_k * (-p.z) * im;       // normal force / m
-            az += an;
-            const float vt = sqrtf(v.x * v.x + v.y * v.y);
-            if (vt > 0.f) {
-                const float fr = fminf(c.mu * an, vt / c.dt);  // |friction| / m, capped
-                ax -= fr * (v.x / vt);
-                ay -= fr * (v.y / vt);
-            }
-        }
-        vn = make_float4(v.x + ax * c.dt, v.y + ay * c.dt, v.z + az * c.dt, 0.f);
-        xn = make_float4(p.x + vn.x * c.dt, p.y + vn.y * c.dt, p.z + vn.z * c.dt, im);
-    }
-    out->p = xn;
-    out->v = vn;
-}
 
 template <bool HAS_C, bool HAS_ACT, bool GROUND>
 __global__ void __launch_bounds__(kThreads)
@@ -116,6 +64,141 @@ k_step_sell(const MassState *__restrict__ in, MassState *__restrict__ out, uint3
         spring_force(p, v, q1, w1, a1.x, L1, c1, fx, fy, fz);
     }
     integrate<GROUND>(p, v, fx, fy, fz, c, out + i);
+}
+
+// K1, TMA-staged form.  One warp owns one SELL slice (32 masses).  Lane 0
+// streams the slice's half-edge columns into a per-warp ring of shared-memory
+// stages with 1-D bulk copies (TMA), kStagesK1 chunks of kChunkCols columns
+// ahead, each stage guarded by an mbarrier; the warp computes from shared
+// memory while later chunks are in flight, so DRAM streaming no longer waits
+// on the neighbour gathers.  Every mbarrier wait is bounded by spin_limit
+// polls; on expiry the warp records the error in *err, waits (bounded) for its
+// copies in flight and leaves its masses unwritten.
+constexpr int kWarpsK1 = 4;
+constexpr int kChunkCols = 8;
+constexpr int kStagesK1 = 2;
+constexpr int kChunkEntries = kChunkCols * 32;
+
+template <bool HAS_C, bool HAS_ACT>
+constexpr int entry_bytes() { return 12 + (HAS_C ? 4 : 0) + (HAS_ACT ? 8 : 0); }
+
+template <bool HAS_C, bool HAS_ACT>
+constexpr int staged_smem_bytes() { return kWarpsK1 * kStagesK1 * kChunkEntries * entry_bytes<HAS_C, HAS_ACT>(); }
+
+template <bool HAS_C, bool HAS_ACT, bool GROUND>
+__global__ void __launch_bounds__(kWarpsK1 * 32)
+k_step_sell_staged(const MassState *__restrict__ in, MassState *__restrict__ out, uint32_t n,
+                   uint32_t n_slices, const uint32_t *__restrict__ slice_off,
+                   const uint32_t *__restrict__ nbr, const float2 *__restrict__ kl,
+                   const float *__restrict__ cc, const float2 *__restrict__ act, StepConst c,
+                   const long long *__restrict__ step_in, long long *__restrict__ step_out,
+                   uint32_t spin_limit, int *__restrict__ err) {
+    constexpr int EB = entry_bytes<HAS_C, HAS_ACT>();
+    constexpr uint32_t FULL = 0xffffffffu;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t bars[kWarpsK1][kStagesK1];
+
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t sl = blockIdx.x * kWarpsK1 + w;
+    long long step = 0;
+    if (HAS_ACT) step = *step_in;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *step_out = *step_in + 1;
+    if (sl >= n_slices) return;                 // whole warp; no CTA-wide barrier follows
+
+    // stage s of this warp: [kl float2 | act float2 | nbr u32 | c float] x kChunkEntries
+    unsigned char *wbase = smem + (size_t)w * kStagesK1 * kChunkEntries * EB;
+    auto st_kl = [&](int s) { return reinterpret_cast<float2 *>(wbase + (size_t)s * kChunkEntries * EB); };
+    auto st_act = [&](int s) { return reinterpret_cast<float2 *>(wbase + (size_t)s * kChunkEntries * EB + kChunkEntries * 8); };
+    auto st_nbr = [&](int s) {
+        return reinterpret_cast<uint32_t *>(wbase + (size_t)s * kChunkEntries * EB + kChunkEntries * (HAS_ACT ? 16 : 8));
+    };
+    auto st_c = [&](int s) {
+        return reinterpret_cast<float *>(wbase + (size_t)s * kChunkEntries * EB + kChunkEntries * (HAS_ACT ? 20 : 12));
+    };
+
+    const uint32_t e0 = __ldg(slice_off + sl);
+    const uint32_t width = (__ldg(slice_off + sl + 1) - e0) >> 5;
+    const uint32_t n_chunks = (width + kChunkCols - 1) / kChunkCols;
+
+    if (lane == 0) {
+        for (int s = 0; s < kStagesK1; ++s) ptx::mbar_init(&bars[w][s], 1);
+        ptx::fence_mbar_init();
+    }
+    __syncwarp();
+
+    auto issue = [&](uint32_t ch) {            // lane 0 only
+        const int s = ch % kStagesK1;
+        const uint32_t cols = min((uint32_t)kChunkCols, width - ch * kChunkCols);
+        const uint32_t ne = cols * 32, eb = e0 + ch * kChunkEntries;
+        ptx::mbar_arrive_expect_tx(&bars[w][s], ne * EB);
+        ptx::bulk_g2s(st_kl(s), kl + eb, ne * 8, &bars[w][s]);
+        if (HAS_ACT) ptx::bulk_g2s(st_act(s), act + eb, ne * 8, &bars[w][s]);
+        ptx::bulk_g2s(st_nbr(s), nbr + eb, ne * 4, &bars[w][s]);
+        if (HAS_C) ptx::bulk_g2s(st_c(s), cc + eb, ne * 4, &bars[w][s]);
+    };
+    uint32_t issued = 0;
+    if (lane == 0)
+        for (; issued < n_chunks && issued < (uint32_t)kStagesK1; ++issued) issue(issued);
+    issued = __shfl_sync(FULL, issued, 0);
+
+    const uint32_t i = sl * 32 + lane;
+    const bool valid = i < n;
+    float4 p = make_float4(0.f, 0.f, 0.f, 0.f), v = p;
+    if (valid) {
+        p = __ldg(&in[i].p);
+        v = __ldg(&in[i].v);
+    }
+    const float ph = HAS_ACT ? clock_phase(c, step) : 0.f;
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+
+    for (uint32_t ch = 0; ch < n_chunks; ++ch) {
+        const int s = ch % kStagesK1;
+        const uint32_t parity = (ch / kStagesK1) & 1;
+        bool done = false;
+        for (uint32_t it = 0; it < spin_limit; ++it) {
+            done = ptx::mbar_try_wait(&bars[w][s], parity);
+            if (__all_sync(FULL, done)) break;
+        }
+        if (!__all_sync(FULL, done)) {
+            if (lane == 0) {
+                atomicExch(err, 1);
+                for (uint32_t k = ch; k < issued; ++k)
+                    ptx::mbar_wait_bounded(&bars[w][k % kStagesK1], (k / kStagesK1) & 1, spin_limit);
+            }
+            __syncwarp();
+            return;
+        }
+        const uint32_t cols = min((uint32_t)kChunkCols, width - ch * kChunkCols);
+        if (valid) {
+            const float2 *skl = st_kl(s);
+            const uint32_t *snb = st_nbr(s);
+            for (uint32_t t = 0; t < cols; t += 2) {
+                const uint32_t a = t * 32 + lane, b = a + 32;
+                const uint32_t j0 = snb[a], j1 = snb[b];
+                const float2 a0 = skl[a], a1 = skl[b];
+                float c0 = c.c_uniform, c1 = c.c_uniform;
+                if (HAS_C) { c0 = st_c(s)[a]; c1 = st_c(s)[b]; }
+                float L0 = a0.y, L1 = a1.y;
+                if (HAS_ACT) {
+                    const float2 s0 = st_act(s)[a], s1 = st_act(s)[b];
+                    L0 = a0.y * (1.f + s0.x * sinf(ph + s0.y));
+                    L1 = a1.y * (1.f + s1.x * sinf(ph + s1.y));
+                }
+                const float4 q0 = __ldg(&in[j0].p), w0 = __ldg(&in[j0].v);
+                const float4 q1 = __ldg(&in[j1].p), w1 = __ldg(&in[j1].v);
+                spring_force(p, v, q0, w0, a0.x, L0, c0, fx, fy, fz);
+                spring_force(p, v, q1, w1, a1.x, L1, c1, fx, fy, fz);
+            }
+        }
+        __syncwarp();
+        if (lane == 0 && issued < n_chunks) {
+            ptx::fence_proxy_async_smem();
+            issue(issued);
+            ++issued;
+        }
+        issued = __shfl_sync(FULL, issued, 0);
+    }
+    if (valid) integrate<GROUND>(p, v, fx, fy, fz, c, out + i);
 }
 
 template <bool HAS_C, bool HAS_ACT>
@@ -178,19 +261,48 @@ inline unsigned blocks_for(uint64_t n) { return (unsigned)((n + kThreads - 1) / 
 cudaError_t launch_step_sell(const MassState *in, MassState *out, uint32_t n, const SellView &v,
                              const StepConst &c, const long long *step_in, long long *step_out,
                              cudaStream_t stream) {
-    const unsigned g = n ? blocks_for(n) : 1;
     const bool hc = v.c != nullptr, ha = v.act != nullptr, gr = c.ground != 0;
+    if (v.variant == 1) {
+        const unsigned g = n ? blocks_for(n) : 1;
 #define TITAN_SELL(HC, HA, GR)                                                                   \
     k_step_sell<HC, HA, GR><<<g, kThreads, 0, stream>>>(in, out, n, v.slice_off, v.nbr, v.kl,  \
                                                         v.c, v.act, c, step_in, step_out)
-    if (hc) {
-        if (ha) { if (gr) TITAN_SELL(true, true, true); else TITAN_SELL(true, true, false); }
-        else    { if (gr) TITAN_SELL(true, false, true); else TITAN_SELL(true, false, false); }
-    } else {
-        if (ha) { if (gr) TITAN_SELL(false, true, true); else TITAN_SELL(false, true, false); }
-        else    { if (gr) TITAN_SELL(false, false, true); else TITAN_SELL(false, false, false); }
-    }
+        if (hc) {
+            if (ha) { if (gr) TITAN_SELL(true, true, true); else TITAN_SELL(true, true, false); }
+            else    { if (gr) TITAN_SELL(true, false, true); else TITAN_SELL(true, false, false); }
+        } else {
+            if (ha) { if (gr) TITAN_SELL(false, true, true); else TITAN_SELL(false, true, false); }
+            else    { if (gr) TITAN_SELL(false, false, true); else TITAN_SELL(false, false, false); }
+        }
 #undef TITAN_SELL
+        return cudaGetLastError();
+    }
+    const uint32_t n_slices = (n + 31) / 32;
+    const unsigned g = n_slices ? (n_slices + kWarpsK1 - 1) / kWarpsK1 : 1;
+#define TITAN_STAGED(HC, HA, GR)                                                                 \
+    do {                                                                                         \
+        auto kern = k_step_sell_staged<HC, HA, GR>;                                              \
+        constexpr int bytes = staged_smem_bytes<HC, HA>();                                       \
+        static std::atomic<uint64_t> attr_set{0};                                                \
+        int dev_ = 0;                                                                            \
+        cudaGetDevice(&dev_);                                                                    \
+        const uint64_t bit_ = 1ull << (dev_ & 63);                                               \
+        if (!(attr_set.load() & bit_)) {                                                         \
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); \
+            if (e != cudaSuccess) return e;                                                      \
+            attr_set.fetch_or(bit_);                                                             \
+        }                                                                                        \
+        kern<<<g, kWarpsK1 * 32, bytes, stream>>>(in, out, n, n_slices, v.slice_off, v.nbr, v.kl, \
+                                                  v.c, v.act, c, step_in, step_out, v.spin_limit, v.err); \
+    } while (0)
+    if (hc) {
+        if (ha) { if (gr) TITAN_STAGED(true, true, true); else TITAN_STAGED(true, true, false); }
+        else    { if (gr) TITAN_STAGED(true, false, true); else TITAN_STAGED(true, false, false); }
+    } else {
+        if (ha) { if (gr) TITAN_STAGED(false, true, true); else TITAN_STAGED(false, true, false); }
+        else    { if (gr) TITAN_STAGED(false, false, true); else TITAN_STAGED(false, false, false); }
+    }
+#undef TITAN_STAGED
     return cudaGetLastError();
 }
 

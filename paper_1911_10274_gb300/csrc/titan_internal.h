@@ -46,6 +46,9 @@ struct SellView {
     const float2 *kl;            // [E] {k, L0}
     const float *c;              // [E] or nullptr (uniform c)
     const float2 *act;           // [E] {A, phi} or nullptr (no actuation)
+    int variant;                 // 0: TMA-staged stream (default), 1: direct loads
+    uint32_t spin_limit;         // bound on mbarrier polls
+    int *err;                    // set to 1 when a bounded wait expires
 };
 
 struct AtomicView {

@@ -47,7 +47,8 @@ class titan_params(C.Structure):
                 ("ground_k", C.c_double), ("mu", C.c_double), ("damping", C.c_double),
                 ("accumulate", C.c_int32), ("order", C.c_int32), ("exec", C.c_int32),
                 ("device", C.c_int32), ("stream", C.c_void_p), ("spin_limit", C.c_uint64),
-                ("graph_chunk", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("graph_chunk", C.c_int32), ("kernel_variant", C.c_int32),
+                ("reserved", C.c_int32 * 6)]
 
 
 _lib = None
@@ -177,7 +178,7 @@ class Sim:
 
     def __init__(self, system, accumulate: int = ACCUM_CSR, order: int = ORDER_MORTON,
                  exec_mode: int = EXEC_AUTO, graph_chunk: int = 0, stream: Optional[int] = None,
-                 device: int = 0, per_spring_damping: bool = False):
+                 device: int = 0, kernel_variant: int = 0):
         load()
         self.n = int(system.pos.shape[0])
         self.s = int(system.ends.shape[0])
@@ -202,6 +203,7 @@ class Sim:
         p.mu = float(system.mu)
         p.accumulate, p.order, p.exec, p.device = accumulate, order, exec_mode, device
         p.graph_chunk = graph_chunk
+        p.kernel_variant = kernel_variant
         p.stream = stream
         self.handle = titan_create(m, sp, p)
         self._keep = None

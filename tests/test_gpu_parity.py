@@ -38,9 +38,10 @@ def check(sys, steps, step0=0, spacing=None, **kw):
 
 
 MODES = [dict(accumulate=T.ACCUM_CSR), dict(accumulate=T.ACCUM_ATOMIC),
+         dict(accumulate=T.ACCUM_CSR, kernel_variant=1),
          dict(accumulate=T.ACCUM_CSR, order=T.ORDER_INPUT),
          dict(accumulate=T.ACCUM_CSR, graph_chunk=-1)]
-MODE_IDS = ["csr", "atomic", "csr-input-order", "csr-no-graph"]
+MODE_IDS = ["csr", "atomic", "csr-direct-loads", "csr-input-order", "csr-no-graph"]
 
 
 @pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
@@ -57,7 +58,7 @@ def _contact_start():
     return s2
 
 
-@pytest.mark.parametrize("mode", MODES[:2], ids=MODE_IDS[:2])
+@pytest.mark.parametrize("mode", MODES[:3], ids=MODE_IDS[:3])
 def test_cube_contact_100_steps(mode):
     """From the oracle's state at step 3150 (just before the cube lands), 100
     steps through the first ground contact."""
@@ -67,7 +68,7 @@ def test_cube_contact_100_steps(mode):
     check(sys, 100, **mode)
 
 
-@pytest.mark.parametrize("mode", MODES[:2], ids=MODE_IDS[:2])
+@pytest.mark.parametrize("mode", MODES[:3], ids=MODE_IDS[:3])
 def test_cube_penetrating_and_sliding_100_steps(mode):
     """Cube placed 1 mm into the ground, sliding at 0.1 m/s: penalty contact
     and capped Coulomb friction on every bottom mass from the first step."""
@@ -77,7 +78,7 @@ def test_cube_penetrating_and_sliding_100_steps(mode):
     check(sys, 100, **mode)
 
 
-@pytest.mark.parametrize("mode", MODES[:2], ids=MODE_IDS[:2])
+@pytest.mark.parametrize("mode", MODES[:3], ids=MODE_IDS[:3])
 def test_cube_with_perturbed_rest_lengths_1000_steps(mode):
     """Same topology with rest lengths x U(0.95, 1.05) and lognormal k, so the
     internal spring forces are large from the first step."""
@@ -170,6 +171,16 @@ def test_resume_from_snapshot_is_bit_exact():
     fresh, _, _ = gpu_run(s2, 400, order=T.ORDER_INPUT)
     assert np.array_equal(same, full)
     assert np.array_equal(fresh, full)
+
+
+def test_staged_and_direct_csr_kernels_agree_bit_exact():
+    """The TMA-staged and the direct-load CSR kernels sum the same entries in
+    the same order: identical trajectories."""
+    sys = inputs.cube_drop(drop_height=0.02)
+    sys.vel[:, 0] = 0.3
+    a = gpu_run(sys, 500, kernel_variant=0)
+    b = gpu_run(sys, 500, kernel_variant=1)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
 
 
 def test_graph_replay_matches_direct_launches_bit_exact():
@@ -266,8 +277,9 @@ def test_full_size_lattice_against_oracle_in_bench_configuration():
     every mass, and the fixed bottom layer exactly still."""
     sys = inputs.large_lattice(n=100, seed=0)
     xo, vo = oracle.run(sys, 64)
-    for acc in (T.ACCUM_CSR, T.ACCUM_ATOMIC):
-        xg, vg, _ = gpu_run(sys, 64, accumulate=acc)
+    for mode in (dict(accumulate=T.ACCUM_CSR), dict(accumulate=T.ACCUM_CSR, kernel_variant=1),
+                 dict(accumulate=T.ACCUM_ATOMIC)):
+        xg, vg, _ = gpu_run(sys, 64, **mode)
         err = np.abs(xg - xo).max()
         assert err <= POS_TOL_FRAC * sys.spacing, err
         fx = sys.fixed.astype(bool)
