@@ -101,7 +101,7 @@ typedef struct {
     void *stream;             /* cudaStream_t for the step loop; NULL: own stream  */
     uint64_t spin_limit;      /* bound on device spin-wait iterations; 0: default  */
     int32_t graph_chunk;      /* steps per captured CUDA graph; 0: 64; < 0: none   */
-    int32_t kernel_variant;   /* CSR kernel: 0 TMA-staged stream (default), 1 direct loads */
+    int32_t kernel_variant;   /* CSR kernel: 0 bulk-prefetched (default), 1 direct loads, 2 smem-staged */
     int32_t reserved[6];      /* zero                                              */
 } titan_params;
 

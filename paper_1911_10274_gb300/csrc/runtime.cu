@@ -182,7 +182,7 @@ titan_status validate(const titan_masses *m, const titan_springs *sp, const tita
     if (p->exec < TITAN_EXEC_AUTO || p->exec > TITAN_EXEC_PERSISTENT)
         return fail(nullptr, TITAN_E_INVALID, "params.exec out of range");
     if (p->device < 0) return fail(nullptr, TITAN_E_INVALID, "params.device must be >= 0");
-    if (p->kernel_variant < 0 || p->kernel_variant > 1) return fail(nullptr, TITAN_E_INVALID, "params.kernel_variant must be 0 or 1");
+    if (p->kernel_variant < 0 || p->kernel_variant > 2) return fail(nullptr, TITAN_E_INVALID, "params.kernel_variant must be 0, 1 or 2");
     for (uint64_t i = 0; i < m->n; ++i) {
         for (int a = 0; a < 3; ++a) {
             if (!finite(m->pos[3 * i + a])) return fail(nullptr, TITAN_E_INVALID, "masses.pos has a non-finite value at mass " + std::to_string(i));

@@ -66,6 +66,76 @@ k_step_sell(const MassState *__restrict__ in, MassState *__restrict__ out, uint3
     integrate<GROUND>(p, v, fx, fy, fz, c, out + i);
 }
 
+// K1, default form.  One thread per mass, one warp per SELL slice.  At entry
+// lane 0 asks the TMA engine to prefetch the slice's whole half-edge stream
+// (all columns of every array) into L2 in one bulk request per array, so the
+// DRAM latency is paid once per slice instead of once per column; the loop
+// then loads each column one iteration ahead of its use (register double
+// buffering), overlapping the L2 latency of the stream with the neighbour
+// gathers of the current column.
+template <bool HAS_C, bool HAS_ACT, bool GROUND>
+__global__ void __launch_bounds__(kThreads)
+k_step_sell_pf(const MassState *__restrict__ in, MassState *__restrict__ out, uint32_t n,
+               const uint32_t *__restrict__ slice_off, const uint32_t *__restrict__ nbr,
+               const float2 *__restrict__ kl, const float *__restrict__ cc,
+               const float2 *__restrict__ act, StepConst c, const long long *__restrict__ step_in,
+               long long *__restrict__ step_out) {
+    const uint32_t i = blockIdx.x * kThreads + threadIdx.x;
+    long long step = 0;
+    if (HAS_ACT) step = *step_in;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *step_out = *step_in + 1;
+    const uint32_t sl = i >> 5, lane = i & 31;
+    const uint32_t n_slices = (n + 31) >> 5;
+    if (sl >= n_slices) return;
+    const uint32_t e0 = __ldg(slice_off + sl);
+    const uint32_t width = (__ldg(slice_off + sl + 1) - e0) >> 5;   // even, warp-uniform
+    if (lane == 0 && width) {
+        const uint32_t ne = width * 32;
+        ptx::bulk_prefetch_l2(kl + e0, ne * 8);
+        ptx::bulk_prefetch_l2(nbr + e0, ne * 4);
+        if (HAS_C) ptx::bulk_prefetch_l2(cc + e0, ne * 4);
+        if (HAS_ACT) ptx::bulk_prefetch_l2(act + e0, ne * 8);
+    }
+    if (i >= n) return;
+
+    const float4 p = __ldg(&in[i].p);
+    const float4 v = __ldg(&in[i].v);
+    const float ph = HAS_ACT ? clock_phase(c, step) : 0.f;
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+    if (width) {
+        uint32_t e = e0 + lane;
+        uint32_t nj0 = __ldcs(nbr + e), nj1 = __ldcs(nbr + e + 32);
+        float2 na0 = __ldcs(kl + e), na1 = __ldcs(kl + e + 32);
+        float nc0 = c.c_uniform, nc1 = c.c_uniform;
+        float2 ns0 = make_float2(0.f, 0.f), ns1 = ns0;
+        if (HAS_C) { nc0 = __ldcs(cc + e); nc1 = __ldcs(cc + e + 32); }
+        if (HAS_ACT) { ns0 = __ldcs(act + e); ns1 = __ldcs(act + e + 32); }
+        for (uint32_t t = 0; t < width; t += 2) {
+            const uint32_t j0 = nj0, j1 = nj1;
+            const float2 a0 = na0, a1 = na1;
+            const float c0 = nc0, c1 = nc1;
+            const float2 s0 = ns0, s1 = ns1;
+            const float4 q0 = __ldg(&in[j0].p), w0 = __ldg(&in[j0].v);
+            const float4 q1 = __ldg(&in[j1].p), w1 = __ldg(&in[j1].v);
+            if (t + 2 < width) {
+                e += 64;
+                nj0 = __ldcs(nbr + e); nj1 = __ldcs(nbr + e + 32);
+                na0 = __ldcs(kl + e); na1 = __ldcs(kl + e + 32);
+                if (HAS_C) { nc0 = __ldcs(cc + e); nc1 = __ldcs(cc + e + 32); }
+                if (HAS_ACT) { ns0 = __ldcs(act + e); ns1 = __ldcs(act + e + 32); }
+            }
+            float L0 = a0.y, L1 = a1.y;
+            if (HAS_ACT) {
+                L0 = a0.y * (1.f + s0.x * sinf(ph + s0.y));
+                L1 = a1.y * (1.f + s1.x * sinf(ph + s1.y));
+            }
+            spring_force(p, v, q0, w0, a0.x, L0, c0, fx, fy, fz);
+            spring_force(p, v, q1, w1, a1.x, L1, c1, fx, fy, fz);
+        }
+    }
+    integrate<GROUND>(p, v, fx, fy, fz, c, out + i);
+}
+
 // K1, TMA-staged form.  One warp owns one SELL slice (32 masses).  Lane 0
 // streams the slice's half-edge columns into a per-warp ring of shared-memory
 // stages with 1-D bulk copies (TMA), kStagesK1 chunks of kChunkCols columns
@@ -262,11 +332,17 @@ cudaError_t launch_step_sell(const MassState *in, MassState *out, uint32_t n, co
                              const StepConst &c, const long long *step_in, long long *step_out,
                              cudaStream_t stream) {
     const bool hc = v.c != nullptr, ha = v.act != nullptr, gr = c.ground != 0;
-    if (v.variant == 1) {
+    if (v.variant == 0 || v.variant == 1) {
         const unsigned g = n ? blocks_for(n) : 1;
 #define TITAN_SELL(HC, HA, GR)                                                                   \
-    k_step_sell<HC, HA, GR><<<g, kThreads, 0, stream>>>(in, out, n, v.slice_off, v.nbr, v.kl,  \
-                                                        v.c, v.act, c, step_in, step_out)
+    do {                                                                                         \
+        if (v.variant == 0)                                                                      \
+            k_step_sell_pf<HC, HA, GR><<<g, kThreads, 0, stream>>>(in, out, n, v.slice_off, v.nbr, \
+                                                                 v.kl, v.c, v.act, c, step_in, step_out); \
+        else                                                                                     \
+            k_step_sell<HC, HA, GR><<<g, kThreads, 0, stream>>>(in, out, n, v.slice_off, v.nbr, v.kl, \
+                                                                v.c, v.act, c, step_in, step_out); \
+    } while (0)
         if (hc) {
             if (ha) { if (gr) TITAN_SELL(true, true, true); else TITAN_SELL(true, true, false); }
             else    { if (gr) TITAN_SELL(true, false, true); else TITAN_SELL(true, false, false); }

@@ -46,7 +46,7 @@ struct SellView {
     const float2 *kl;            // [E] {k, L0}
     const float *c;              // [E] or nullptr (uniform c)
     const float2 *act;           // [E] {A, phi} or nullptr (no actuation)
-    int variant;                 // 0: TMA-staged stream (default), 1: direct loads
+    int variant;                 // 0: bulk L2 prefetch (default), 1: direct loads, 2: smem-staged
     uint32_t spin_limit;         // bound on mbarrier polls
     int *err;                    // set to 1 when a bounded wait expires
 };

@@ -39,9 +39,10 @@ def check(sys, steps, step0=0, spacing=None, **kw):
 
 MODES = [dict(accumulate=T.ACCUM_CSR), dict(accumulate=T.ACCUM_ATOMIC),
          dict(accumulate=T.ACCUM_CSR, kernel_variant=1),
+         dict(accumulate=T.ACCUM_CSR, kernel_variant=2),
          dict(accumulate=T.ACCUM_CSR, order=T.ORDER_INPUT),
          dict(accumulate=T.ACCUM_CSR, graph_chunk=-1)]
-MODE_IDS = ["csr", "atomic", "csr-direct-loads", "csr-input-order", "csr-no-graph"]
+MODE_IDS = ["csr", "atomic", "csr-direct-loads", "csr-smem-staged", "csr-input-order", "csr-no-graph"]
 
 
 @pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
@@ -58,7 +59,7 @@ def _contact_start():
     return s2
 
 
-@pytest.mark.parametrize("mode", MODES[:3], ids=MODE_IDS[:3])
+@pytest.mark.parametrize("mode", MODES[:4], ids=MODE_IDS[:4])
 def test_cube_contact_100_steps(mode):
     """From the oracle's state at step 3150 (just before the cube lands), 100
     steps through the first ground contact."""
@@ -68,7 +69,7 @@ def test_cube_contact_100_steps(mode):
     check(sys, 100, **mode)
 
 
-@pytest.mark.parametrize("mode", MODES[:3], ids=MODE_IDS[:3])
+@pytest.mark.parametrize("mode", MODES[:4], ids=MODE_IDS[:4])
 def test_cube_penetrating_and_sliding_100_steps(mode):
     """Cube placed 1 mm into the ground, sliding at 0.1 m/s: penalty contact
     and capped Coulomb friction on every bottom mass from the first step."""
@@ -78,7 +79,7 @@ def test_cube_penetrating_and_sliding_100_steps(mode):
     check(sys, 100, **mode)
 
 
-@pytest.mark.parametrize("mode", MODES[:3], ids=MODE_IDS[:3])
+@pytest.mark.parametrize("mode", MODES[:4], ids=MODE_IDS[:4])
 def test_cube_with_perturbed_rest_lengths_1000_steps(mode):
     """Same topology with rest lengths x U(0.95, 1.05) and lognormal k, so the
     internal spring forces are large from the first step."""
@@ -173,14 +174,15 @@ def test_resume_from_snapshot_is_bit_exact():
     assert np.array_equal(fresh, full)
 
 
-def test_staged_and_direct_csr_kernels_agree_bit_exact():
-    """The TMA-staged and the direct-load CSR kernels sum the same entries in
-    the same order: identical trajectories."""
+def test_csr_kernel_variants_agree_bit_exact():
+    """The three CSR kernels (bulk-prefetched, direct, smem-staged) sum the
+    same entries in the same order: identical trajectories."""
     sys = inputs.cube_drop(drop_height=0.02)
     sys.vel[:, 0] = 0.3
     a = gpu_run(sys, 500, kernel_variant=0)
-    b = gpu_run(sys, 500, kernel_variant=1)
-    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    for var in (1, 2):
+        b = gpu_run(sys, 500, kernel_variant=var)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
 
 
 def test_graph_replay_matches_direct_launches_bit_exact():
@@ -278,7 +280,7 @@ def test_full_size_lattice_against_oracle_in_bench_configuration():
     sys = inputs.large_lattice(n=100, seed=0)
     xo, vo = oracle.run(sys, 64)
     for mode in (dict(accumulate=T.ACCUM_CSR), dict(accumulate=T.ACCUM_CSR, kernel_variant=1),
-                 dict(accumulate=T.ACCUM_ATOMIC)):
+                 dict(accumulate=T.ACCUM_CSR, kernel_variant=2), dict(accumulate=T.ACCUM_ATOMIC)):
         xg, vg, _ = gpu_run(sys, 64, **mode)
         err = np.abs(xg - xo).max()
         assert err <= POS_TOL_FRAC * sys.spacing, err
