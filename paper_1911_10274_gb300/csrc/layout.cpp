@@ -4,9 +4,14 @@
 // quantised to 2^21 cells per axis over the bounding cube, so that masses that
 // are close in space get close device indices and the neighbour gathers of one
 // warp fall in a few cache lines.
-// SELL-32 incidence: per mass, its incident half-edges sorted by neighbour
-// device index (then spring index) - a fixed order, which makes the force sum
-// deterministic - stored column-major per slice of 32 masses.
+// SELL-32 incidence: per mass, its incident half-edges in a fixed order (which
+// makes the force sum deterministic), stored column-major per slice of 32
+// masses.  The order is by the direction class of the spring seen from the
+// mass (each component of the initial unit vector rounded to -1/0/+1, 26
+// classes), then by neighbour index: in a lattice, column t of a slice is then
+// the same lattice direction for every interior mass, so the 32 neighbour
+// gathers of one column hit a compact, shifted block of consecutive states
+// (few cache lines) instead of 32 unrelated ones.
 // Spring records: one {i, j, k, L0} record per spring, sorted by (lower,
 // higher) device index, for the atomic scatter.
 #include "layout.h"
@@ -55,8 +60,24 @@ void morton_order(const double *pos, uint32_t n, std::vector<uint32_t> &caller_o
     for (uint32_t d = 0; d < n; ++d) caller_of_dev[d] = key[d].second;
 }
 
-bool build_sell(uint32_t n, uint32_t s, const uint32_t *ends, const std::vector<uint32_t> &dev_of,
-                SellHost &out) {
+namespace {
+// Direction class 0..26 of d (13 for a zero vector): each component of d/|d|
+// mapped to 0/1/2 for below -0.38 / within / above +0.38.
+uint32_t direction_class(const double *a, const double *b) {
+    const double d[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+    const double l = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    if (!(l > 0)) return 13;
+    uint32_t c = 0, m = 1;
+    for (int k = 0; k < 3; ++k, m *= 3) {
+        const double u = d[k] / l;
+        c += m * (u > 0.38 ? 2u : (u < -0.38 ? 0u : 1u));
+    }
+    return c;
+}
+}  // namespace
+
+bool build_sell(uint32_t n, uint32_t s, const uint32_t *ends, const double *pos,
+                const std::vector<uint32_t> &dev_of, SellHost &out) {
     const uint32_t n_slices = (n + 31) / 32;
     std::vector<uint32_t> deg(n, 0);
     for (uint32_t q = 0; q < s; ++q) {
@@ -66,17 +87,20 @@ bool build_sell(uint32_t n, uint32_t s, const uint32_t *ends, const std::vector<
     std::vector<uint64_t> rowptr(n + 1, 0);
     for (uint32_t i = 0; i < n; ++i) rowptr[i + 1] = rowptr[i] + deg[i];
     // half-edge = (neighbour device index, spring index, end slot 0/1)
-    struct HalfEdge { uint32_t nbr, spring; };
+    struct HalfEdge { uint32_t key, nbr, spring; };
     std::vector<HalfEdge> he(rowptr[n]);
     std::vector<uint64_t> cur(rowptr.begin(), rowptr.end() - 1);
     for (uint32_t q = 0; q < s; ++q) {
-        const uint32_t a = dev_of[ends[2 * (size_t)q]], b = dev_of[ends[2 * (size_t)q + 1]];
-        he[cur[a]++] = {b, q};
-        he[cur[b]++] = {a, q};
+        const uint32_t ci = ends[2 * (size_t)q], cj = ends[2 * (size_t)q + 1];
+        const uint32_t a = dev_of[ci], b = dev_of[cj];
+        const uint32_t kab = direction_class(pos + 3 * (size_t)ci, pos + 3 * (size_t)cj);
+        he[cur[a]++] = {kab, b, q};
+        he[cur[b]++] = {26u - kab, a, q};      // the opposite direction
     }
     for (uint32_t i = 0; i < n; ++i)
         std::sort(he.begin() + rowptr[i], he.begin() + rowptr[i + 1],
                   [](const HalfEdge &x, const HalfEdge &y) {
+                      if (x.key != y.key) return x.key < y.key;
                       return x.nbr != y.nbr ? x.nbr < y.nbr : x.spring < y.spring;
                   });
     out.slice_off.assign(n_slices + 1, 0);

@@ -19,8 +19,9 @@ struct SellHost {
 };
 
 // Returns false if the padded incidence does not fit 32-bit entry offsets.
-bool build_sell(uint32_t n, uint32_t s, const uint32_t *ends, const std::vector<uint32_t> &dev_of,
-                SellHost &out);
+// pos: caller-order positions [n][3], used only to order each row by direction.
+bool build_sell(uint32_t n, uint32_t s, const uint32_t *ends, const double *pos,
+                const std::vector<uint32_t> &dev_of, SellHost &out);
 
 struct RecordsHost {
     std::vector<uint32_t> order;            // [S] record r holds caller spring order[r]

@@ -8,6 +8,14 @@ namespace titan {
 
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 
+// One 256-bit read-only load of a mass's whole 32-byte state (sm_100+ vector
+// width): one L1 request per neighbour gather instead of two.
+__device__ __forceinline__ void load_state(const MassState *m, float4 &p, float4 &v) {
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(p.x), "=f"(p.y), "=f"(p.z), "=f"(p.w), "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+        : "l"(m));
+}
+
 // Phase of the actuation clock at step `step`: 2 pi f t mod 2 pi with
 // t = step dt, formed in FP64 so that long runs keep full FP32 phase accuracy.
 __device__ __forceinline__ float clock_phase(const StepConst &c, long long step) {

@@ -402,7 +402,7 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
     }
 
     if (sim->accumulate == TITAN_ACCUM_CSR) {
-        if (!titan::build_sell(n, s, sp->ends, sim->dev_of_caller, sim->sell))
+        if (!titan::build_sell(n, s, sp->ends, m->pos, sim->dev_of_caller, sim->sell))
             return bail(fail(sim, TITAN_E_UNSUPPORTED, "padded incidence exceeds 2^32 entries"));
         const uint32_t E = sim->sell.entries;
         std::vector<float2> kl(E, make_float2(0.f, 0.f));

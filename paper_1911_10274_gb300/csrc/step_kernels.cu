@@ -58,8 +58,9 @@ k_step_sell(const MassState *__restrict__ in, MassState *__restrict__ out, uint3
             L0 = a0.y * (1.f + s0.x * sinf(ph + s0.y));
             L1 = a1.y * (1.f + s1.x * sinf(ph + s1.y));
         }
-        const float4 q0 = __ldg(&in[j0].p), w0 = __ldg(&in[j0].v);
-        const float4 q1 = __ldg(&in[j1].p), w1 = __ldg(&in[j1].v);
+        float4 q0, w0, q1, w1;
+        load_state(in + j0, q0, w0);
+        load_state(in + j1, q1, w1);
         spring_force(p, v, q0, w0, a0.x, L0, c0, fx, fy, fz);
         spring_force(p, v, q1, w1, a1.x, L1, c1, fx, fy, fz);
     }
@@ -115,8 +116,9 @@ k_step_sell_pf(const MassState *__restrict__ in, MassState *__restrict__ out, ui
             const float2 a0 = na0, a1 = na1;
             const float c0 = nc0, c1 = nc1;
             const float2 s0 = ns0, s1 = ns1;
-            const float4 q0 = __ldg(&in[j0].p), w0 = __ldg(&in[j0].v);
-            const float4 q1 = __ldg(&in[j1].p), w1 = __ldg(&in[j1].v);
+            float4 q0, w0, q1, w1;
+            load_state(in + j0, q0, w0);
+            load_state(in + j1, q1, w1);
             if (t + 2 < width) {
                 e += 64;
                 nj0 = __ldcs(nbr + e); nj1 = __ldcs(nbr + e + 32);
@@ -254,8 +256,9 @@ k_step_sell_staged(const MassState *__restrict__ in, MassState *__restrict__ out
                     L0 = a0.y * (1.f + s0.x * sinf(ph + s0.y));
                     L1 = a1.y * (1.f + s1.x * sinf(ph + s1.y));
                 }
-                const float4 q0 = __ldg(&in[j0].p), w0 = __ldg(&in[j0].v);
-                const float4 q1 = __ldg(&in[j1].p), w1 = __ldg(&in[j1].v);
+                float4 q0, w0, q1, w1;
+                load_state(in + j0, q0, w0);
+                load_state(in + j1, q1, w1);
                 spring_force(p, v, q0, w0, a0.x, L0, c0, fx, fy, fz);
                 spring_force(p, v, q1, w1, a1.x, L1, c1, fx, fy, fz);
             }
@@ -287,8 +290,9 @@ k_springs_atomic(const MassState *__restrict__ in, const uint4 *__restrict__ rec
         L = L * (1.f + a.x * sinf(clock_phase(c, *step_in) + a.y));
     }
     const float cs = HAS_C ? __ldcs(cc + s) : c.c_uniform;
-    const float4 p = __ldg(&in[r.x].p), v = __ldg(&in[r.x].v);
-    const float4 q = __ldg(&in[r.y].p), w = __ldg(&in[r.y].v);
+    float4 p, v, q, w;
+    load_state(in + r.x, p, v);
+    load_state(in + r.y, q, w);
     float fx = 0.f, fy = 0.f, fz = 0.f;
     spring_force(p, v, q, w, k, L, cs, fx, fy, fz);
     atomicAdd(force + r.x, make_float4(fx, fy, fz, 0.f));
