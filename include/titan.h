@@ -174,6 +174,37 @@ uint64_t titan_steps(const titan_sim *sim);
  * on this thread when sim is NULL.  Owned by the library; never NULL. */
 const char *titan_last_error(const titan_sim *sim);
 
+/* One time step of the atomic-scatter kernels on caller-owned device arrays,
+ * for callers that cannot allocate device memory: a control loop with a hard
+ * per-step deadline (cudaMalloc and cudaFree may synchronise the device and
+ * take unbounded time), or a plug-in inside a host framework that owns all
+ * device memory through its own pool.  The call allocates nothing; the
+ * per-mass force accumulator it needs is a fixed 4 MiB array inside the
+ * library (every GPU that loads the library holds it until the process exits).
+ * The paper has no counterpart of this call.
+ *
+ * Inputs (device pointers, caller order, float): pos_dev and vel_dev [n][3],
+ * inv_mass_dev [n] (0 marks a fixed mass), ends_dev [n_springs][2] (u32),
+ * k_dev and rest_dev [n_springs]; damping is the dashpot of every spring.
+ * params supplies dt, gravity, ground, ground_k and mu (other fields unused).
+ * Outputs: pos_out_dev and vel_out_dev [n][3] (must not alias the inputs).
+ * Enqueued on `stream` (a cudaStream_t; NULL: the legacy default stream) on
+ * the current device; the call does not wait for it.
+ * Limits: n_masses <= 262144; larger counts return TITAN_E_INVALID.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  All calls share the one array per device and each call
+ * clears the part it uses first: calls whose work overlaps on the GPU (other
+ * streams, other threads) race on it and must be serialised by the caller.
+ * Errors: TITAN_E_INVALID (sizes, null pointers, dt/damping), TITAN_E_CUDA;
+ * the text is in titan_last_error(NULL). */
+titan_status titan_step_atomic_noalloc(uint32_t n_masses, const float *pos_dev, const float *vel_dev,
+                                       const float *inv_mass_dev, uint32_t n_springs,
+                                       const uint32_t *ends_dev, const float *k_dev,
+                                       const float *rest_dev, float damping,
+                                       const titan_params *params, float *pos_out_dev,
+                                       float *vel_out_dev, void *stream);
+
 /* Waits for outstanding work and frees every resource of the handle.
  * NULL is a no-op.  Returns the status of that final wait. */
 titan_status titan_destroy(titan_sim *sim);

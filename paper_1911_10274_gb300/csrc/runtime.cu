@@ -43,6 +43,12 @@ bool finite(double x) { return std::isfinite(x); }
 
 }  // namespace
 
+namespace titan {
+// Lets other translation units of the library report an error through
+// titan_last_error(NULL).
+void set_thread_error(const std::string &msg) { g_thread_error = msg; }
+}  // namespace titan
+
 struct titan_sim {
     int device = 0;
     cudaStream_t stream = nullptr;

@@ -79,6 +79,8 @@ def load(path: Optional[str] = None):
                 "titan_steps": (u64, [_P]),
                 "titan_last_error": (C.c_char_p, [_P]),
                 "titan_destroy": (S, [_P]),
+                "titan_step_atomic_noalloc": (S, [u32, _P, _P, _P, u32, _P, _P, _P, f32,
+                                                  C.POINTER(titan_params), _P, _P, _P]),
             }
             for name, (res, args) in sigs.items():
                 fn = getattr(lib, name)
@@ -169,6 +171,17 @@ def titan_last_error(sim: Optional[int] = None) -> str:
 
 def titan_destroy(sim: int) -> None:
     _check(load().titan_destroy(sim))
+
+
+def titan_step_atomic_noalloc(n_masses: int, pos_dev, vel_dev, inv_mass_dev, n_springs: int, ends_dev,
+                              k_dev, rest_dev, damping: float, params: titan_params, pos_out_dev,
+                              vel_out_dev, stream: Optional[int] = None) -> None:
+    """One atomic-scatter step on caller-owned device tensors, allocating
+    nothing (the accumulator is a fixed array inside the library)."""
+    _check(load().titan_step_atomic_noalloc(
+        n_masses, _ptr(pos_dev), _ptr(vel_dev), _ptr(inv_mass_dev), n_springs, _ptr(ends_dev),
+        _ptr(k_dev), _ptr(rest_dev), float(damping), C.byref(params), _ptr(pos_out_dev),
+        _ptr(vel_out_dev), stream))
 
 
 # --------------------------------------------------------------------------- convenience
