@@ -77,7 +77,8 @@ typedef enum {
 
 typedef enum {
     TITAN_ORDER_INPUT = 0,    /* keep the caller's mass order on the device         */
-    TITAN_ORDER_MORTON = 1    /* reorder masses along a Morton curve                */
+    TITAN_ORDER_MORTON = 1    /* spatial order: 4x4x2 grid tiles when the masses sit on a
+                                 grid (pitch = shortest spring), else a Morton curve */
 } titan_order;
 
 typedef enum {
@@ -101,7 +102,10 @@ typedef struct {
     void *stream;             /* cudaStream_t for the step loop; NULL: own stream  */
     uint64_t spin_limit;      /* bound on device spin-wait iterations; 0: default  */
     int32_t graph_chunk;      /* steps per captured CUDA graph; 0: 64; < 0: none   */
-    int32_t kernel_variant;   /* CSR kernel: 0 bulk-prefetched (default), 1 direct loads, 2 smem-staged */
+    int32_t kernel_variant;   /* CSR kernel: 0 auto (halo tables in shared memory when they
+                                 fit, else 3), 1 direct loads, 2 TMA-staged stream,
+                                 3 bulk L2 prefetch, 4 halo (TITAN_E_UNSUPPORTED if the
+                                 tables do not fit)                                   */
     int32_t reserved[6];      /* zero                                              */
 } titan_params;
 

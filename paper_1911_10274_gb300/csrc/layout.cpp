@@ -60,6 +60,43 @@ void morton_order(const double *pos, uint32_t n, std::vector<uint32_t> &caller_o
     for (uint32_t d = 0; d < n; ++d) caller_of_dev[d] = key[d].second;
 }
 
+bool grid_tile_order(const double *pos, uint32_t n, double h, std::vector<uint32_t> &caller_of_dev) {
+    caller_of_dev.clear();
+    if (n == 0 || !(h > 0) || !std::isfinite(h)) return false;
+    double lo[3] = {pos[0], pos[1], pos[2]};
+    for (uint32_t i = 0; i < n; ++i)
+        for (int a = 0; a < 3; ++a) lo[a] = std::min(lo[a], pos[3 * (size_t)i + a]);
+    struct Key { uint64_t tile; uint32_t lane, idx; };
+    std::vector<Key> key(n);
+    for (uint32_t i = 0; i < n; ++i) {
+        uint64_t c[3];
+        for (int a = 0; a < 3; ++a) {
+            const double q = (pos[3 * (size_t)i + a] - lo[a]) / h;
+            const double r = std::nearbyint(q);
+            if (std::fabs(q - r) > 1e-3 || r > (double)((1u << 22) - 1)) return false;
+            c[a] = (uint64_t)r;
+        }
+        const uint64_t tile = spread_bits3(c[0] >> 2) | (spread_bits3(c[1] >> 2) << 1) | (spread_bits3(c[2] >> 1) << 2);
+        key[i] = {tile, (uint32_t)((c[0] & 3) + 4 * (c[1] & 3) + 16 * (c[2] & 1)), i};
+    }
+    std::sort(key.begin(), key.end(), [](const Key &a, const Key &b) {
+        return a.tile != b.tile ? a.tile < b.tile : (a.lane != b.lane ? a.lane < b.lane : a.idx < b.idx);
+    });
+    uint64_t tiles = 0;
+    for (uint32_t k = 0; k < n; ++k) {
+        if (k && key[k].tile == key[k - 1].tile && key[k].lane == key[k - 1].lane) return false;  // shared cell
+        if (k == 0 || key[k].tile != key[k - 1].tile) ++tiles;
+    }
+    if (tiles * 32 >= (1ull << 31)) return false;
+    caller_of_dev.assign(tiles * 32, UINT32_MAX);
+    uint64_t t = 0;
+    for (uint32_t k = 0; k < n; ++k) {
+        if (k && key[k].tile != key[k - 1].tile) ++t;
+        caller_of_dev[t * 32 + key[k].lane] = key[k].idx;
+    }
+    return true;
+}
+
 namespace {
 // Direction class 0..26 of d (13 for a zero vector): each component of d/|d|
 // mapped to 0/1/2 for below -0.38 / within / above +0.38.
@@ -137,6 +174,131 @@ bool build_sell(uint32_t n, uint32_t s, const uint32_t *ends, const double *pos,
             }
         }
     }
+    return true;
+}
+
+bool build_halo(uint32_t n, const SellHost &sell, uint32_t max_slots, bool grid_colours, HaloHost &out) {
+    const uint32_t n_blocks = (n + kHaloBlock - 1) / kHaloBlock;
+    const uint32_t slices_per_block = kHaloBlock / 32;
+    const uint32_t n_slices = (n + 31) / 32;
+    out.nbr_slot.assign(sell.entries, 0);
+    out.own_slot.assign(n, 0);
+    out.ext_off.assign(n_blocks + 1, 0);
+    out.ext_idx.clear();
+    out.ext_slot.clear();
+    out.max_table = 0;
+    uint64_t groups = 0, wavefronts = 0;
+
+    std::vector<uint32_t> local(n, UINT32_MAX);      // table entry of a device mass in the current block
+    std::vector<uint32_t> entries;                    // device index per table entry
+    std::vector<std::vector<uint32_t>> groups_of;     // access groups touching each entry
+    std::vector<std::vector<uint32_t>> group_members; // entries per access group (distinct)
+    std::vector<int> color;
+    for (uint32_t b = 0; b < n_blocks; ++b) {
+        const uint32_t m0 = b * kHaloBlock, m1 = std::min(n, m0 + kHaloBlock);
+        entries.clear();
+        for (uint32_t m = m0; m < m1; ++m) { local[m] = (uint32_t)entries.size(); entries.push_back(m); }
+        const uint32_t own = (uint32_t)entries.size();
+        group_members.clear();
+        // access groups: (slice, column, half-warp) -> distinct entries read
+        for (uint32_t w = 0; w < slices_per_block; ++w) {
+            const uint32_t sl = b * slices_per_block + w;
+            if (sl >= n_slices) break;
+            const uint32_t e0 = sell.slice_off[sl], width = (sell.slice_off[sl + 1] - e0) / 32;
+            for (uint32_t t = 0; t < width; ++t)
+                for (uint32_t h = 0; h < 2; ++h) {
+                    std::vector<uint32_t> g;
+                    for (uint32_t l = 16 * h; l < 16 * h + 16; ++l) {
+                        if (sl * 32 + l >= n) continue;
+                        const uint32_t j = sell.nbr[e0 + 32 * t + l];
+                        if (local[j] == UINT32_MAX) { local[j] = (uint32_t)entries.size(); entries.push_back(j); }
+                        g.push_back(local[j]);
+                    }
+                    std::sort(g.begin(), g.end());
+                    g.erase(std::unique(g.begin(), g.end()), g.end());
+                    if (g.size() > 1) group_members.push_back(std::move(g));
+                }
+        }
+        // the own-state writes: one group per half-warp of own masses
+        for (uint32_t h = 0; 16 * h < own; ++h) {
+            std::vector<uint32_t> g;
+            for (uint32_t l = 16 * h; l < std::min(own, 16 * h + 16); ++l) g.push_back(l);
+            if (g.size() > 1) group_members.push_back(std::move(g));
+        }
+        const uint32_t T = (uint32_t)entries.size();
+        groups_of.assign(T, {});
+        for (uint32_t gi = 0; gi < group_members.size(); ++gi)
+            for (uint32_t e : group_members[gi]) groups_of[e].push_back(gi);
+        // greedy colouring, most-constrained entries first; ties go to the least-used colour
+        std::vector<uint32_t> order(T);
+        std::iota(order.begin(), order.end(), 0u);
+        std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
+            return groups_of[x].size() > groups_of[y].size();
+        });
+        color.assign(T, -1);
+        std::vector<uint32_t> used(16, 0);
+        if (grid_colours) {
+            for (uint32_t e = 0; e < T; ++e) { color[e] = (int)(entries[e] & 15); ++used[color[e]]; }
+            order.clear();
+        }
+        for (uint32_t e : order) {
+            uint32_t cost[16] = {0};
+            for (uint32_t gi : groups_of[e])
+                for (uint32_t o : group_members[gi])
+                    if (o != e && color[o] >= 0) ++cost[color[o]];
+            int best = 0;
+            for (int c = 1; c < 16; ++c)
+                if (cost[c] < cost[best] || (cost[c] == cost[best] && used[c] < used[best])) best = c;
+            color[e] = best;
+            ++used[best];
+        }
+        uint32_t rows = 0;
+        for (int c = 0; c < 16; ++c) rows = std::max(rows, used[c]);
+        const uint32_t table = 16 * rows;
+        if (table > max_slots) {
+            for (uint32_t e = 0; e < T; ++e) local[entries[e]] = UINT32_MAX;
+            return false;
+        }
+        out.max_table = std::max(out.max_table, table);
+        std::vector<uint32_t> next_row(16, 0), slot(T);
+        for (uint32_t e = 0; e < T; ++e) slot[e] = 16 * next_row[color[e]]++ + (uint32_t)color[e];
+        for (uint32_t m = m0; m < m1; ++m) out.own_slot[m] = (uint16_t)slot[local[m]];
+        for (uint32_t e = own; e < T; ++e) {
+            out.ext_idx.push_back(entries[e]);
+            out.ext_slot.push_back((uint16_t)slot[e]);
+        }
+        out.ext_off[b + 1] = (uint32_t)out.ext_idx.size();
+        for (uint32_t w = 0; w < slices_per_block; ++w) {
+            const uint32_t sl = b * slices_per_block + w;
+            if (sl >= n_slices) break;
+            const uint32_t e0 = sell.slice_off[sl], e1 = sell.slice_off[sl + 1];
+            for (uint32_t e = e0; e < e1; ++e) {
+                const uint32_t l = (e - e0) % 32;
+                const uint32_t j = (sl * 32 + l < n) ? sell.nbr[e] : m0;
+                out.nbr_slot[e] = (uint16_t)slot[local[j]];
+            }
+            // conflict statistics: wavefronts per half-warp access
+            const uint32_t width = (e1 - e0) / 32;
+            for (uint32_t t = 0; t < width; ++t)
+                for (uint32_t h = 0; h < 2; ++h) {
+                    uint32_t per_bank[16] = {0};
+                    std::vector<uint32_t> seen;
+                    for (uint32_t l = 16 * h; l < 16 * h + 16; ++l) {
+                        if (sl * 32 + l >= n) continue;
+                        const uint32_t sslot = out.nbr_slot[e0 + 32 * t + l];
+                        if (std::find(seen.begin(), seen.end(), sslot) != seen.end()) continue;
+                        seen.push_back(sslot);
+                        ++per_bank[sslot % 16];
+                    }
+                    uint32_t ways = 1;
+                    for (int c = 0; c < 16; ++c) ways = std::max(ways, per_bank[c]);
+                    wavefronts += ways;
+                    ++groups;
+                }
+        }
+        for (uint32_t e = 0; e < T; ++e) local[entries[e]] = UINT32_MAX;
+    }
+    out.conflict_ways = groups ? (double)wavefronts / (double)groups : 1.0;
     return true;
 }
 

@@ -10,7 +10,9 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -26,6 +28,7 @@ thread_local std::string g_thread_error = "";
 
 constexpr int kDefaultGraphChunk = 64;
 constexpr uint32_t kDefaultSpinLimit = 1u << 22;
+constexpr uint32_t kHaloMaxSlots = 4096;     // 96 KiB of shared memory per CTA
 
 struct DeviceGuard {
     int prev = -1;
@@ -56,6 +59,8 @@ struct titan_sim {
     cudaStream_t side = nullptr;       // snapshot device-to-host copies
     cudaStream_t capture = nullptr;    // graph capture
     uint32_t n = 0, s = 0;
+    uint32_t n_dev = 0;                   // device slots (>= n: grid-tile order leaves holes)
+    bool grid_order = false;
     int accumulate = TITAN_ACCUM_CSR;
     titan::StepConst c{};
     bool has_c = false, has_act = false;
@@ -66,7 +71,9 @@ struct titan_sim {
     std::vector<float> k, rest, damp;     // caller spring order
     std::vector<float> act_amp, act_phase;
     titan::SellHost sell;
+    titan::HaloHost halo;
     titan::RecordsHost rec;
+    int csr_kernel = 0;                   // resolved: 1 direct, 2 smem-staged, 3 bulk-prefetch, 4 halo
 
     MassState *state[2] = {nullptr, nullptr};
     long long *steps_dev = nullptr;       // [2]
@@ -75,6 +82,8 @@ struct titan_sim {
     uint32_t *d_dev_of_caller = nullptr;
 
     uint32_t *d_slice_off = nullptr, *d_nbr = nullptr;
+    uint16_t *d_nslot = nullptr, *d_own_slot = nullptr, *d_ext_slot = nullptr;
+    uint32_t *d_ext_off = nullptr, *d_ext_idx = nullptr;
     float2 *d_kl = nullptr, *d_act = nullptr;
     float *d_c = nullptr;
 
@@ -188,7 +197,7 @@ titan_status validate(const titan_masses *m, const titan_springs *sp, const tita
     if (p->exec < TITAN_EXEC_AUTO || p->exec > TITAN_EXEC_PERSISTENT)
         return fail(nullptr, TITAN_E_INVALID, "params.exec out of range");
     if (p->device < 0) return fail(nullptr, TITAN_E_INVALID, "params.device must be >= 0");
-    if (p->kernel_variant < 0 || p->kernel_variant > 2) return fail(nullptr, TITAN_E_INVALID, "params.kernel_variant must be 0, 1 or 2");
+    if (p->kernel_variant < 0 || p->kernel_variant > 4) return fail(nullptr, TITAN_E_INVALID, "params.kernel_variant must be 0..4");
     for (uint64_t i = 0; i < m->n; ++i) {
         for (int a = 0; a < 3; ++a) {
             if (!finite(m->pos[3 * i + a])) return fail(nullptr, TITAN_E_INVALID, "masses.pos has a non-finite value at mass " + std::to_string(i));
@@ -208,10 +217,16 @@ titan_status validate(const titan_masses *m, const titan_springs *sp, const tita
 }
 
 void fill_state(const titan_sim *sim, const double *pos, const double *vel, std::vector<MassState> &st) {
-    st.resize(sim->n);
-    for (uint32_t d = 0; d < sim->n; ++d) {
+    st.resize(sim->n_dev);
+    for (uint32_t d = 0; d < sim->n_dev; ++d) {
         const uint32_t i = sim->caller_of_dev[d];
         MassState m;
+        if (i == UINT32_MAX) {            // hole: a fixed, unconnected slot
+            m.p = make_float4(0.f, 0.f, 0.f, 0.f);
+            m.v = make_float4(0.f, 0.f, 0.f, 0.f);
+            st[d] = m;
+            continue;
+        }
         m.p = make_float4((float)pos[3 * (size_t)i], (float)pos[3 * (size_t)i + 1], (float)pos[3 * (size_t)i + 2], sim->inv_mass[i]);
         if (vel) m.v = make_float4((float)vel[3 * (size_t)i], (float)vel[3 * (size_t)i + 1], (float)vel[3 * (size_t)i + 2], 0.f);
         else m.v = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -247,13 +262,18 @@ cudaError_t enqueue_step(titan_sim *sim, cudaStream_t st, int b) {
     long long *so = sim->steps_dev + (1 - b);
     if (sim->accumulate == TITAN_ACCUM_CSR) {
         titan::SellView v{sim->d_slice_off, sim->d_nbr, sim->d_kl, sim->has_c ? sim->d_c : nullptr,
-                          sim->has_act ? sim->d_act : nullptr, sim->kernel_variant, sim->spin_limit,
-                          sim->d_err};
-        return titan::launch_step_sell(in, out, sim->n, v, sim->c, si, so, st);
+                          sim->has_act ? sim->d_act : nullptr, 0, sim->spin_limit, sim->d_err};
+        if (sim->csr_kernel == 4) {
+            titan::HaloView h{sim->d_nslot, sim->d_own_slot, sim->d_ext_off, sim->d_ext_idx,
+                              sim->d_ext_slot, sim->halo.max_table};
+            return titan::launch_step_halo(in, out, sim->n_dev, v, h, sim->c, si, so, st);
+        }
+        v.variant = sim->csr_kernel == 3 ? 0 : sim->csr_kernel;   // launcher: 0 prefetch, 1 direct, 2 staged
+        return titan::launch_step_sell(in, out, sim->n_dev, v, sim->c, si, so, st);
     }
     titan::AtomicView v{sim->d_rec, sim->has_c ? sim->d_rc : nullptr,
                         sim->has_act ? sim->d_ract : nullptr, sim->d_force, sim->s};
-    return titan::launch_step_atomic(in, out, sim->n, v, sim->c, si, so, st);
+    return titan::launch_step_atomic(in, out, sim->n_dev, v, sim->c, si, so, st);
 }
 
 // Reads (and clears) the device error flag set by bounded waits that expired.
@@ -358,13 +378,28 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
     // ---- host-side layout
     const uint32_t n = m->n, s = sp->n;
     if (p->order == TITAN_ORDER_MORTON) {
-        titan::morton_order(m->pos, n, sim->caller_of_dev);
+        // masses on a grid (pitch = shortest spring) get the grid-tile order, others Morton
+        double h = INFINITY;
+        for (uint32_t q = 0; q < s; ++q) {
+            const uint32_t i = sp->ends[2 * (size_t)q], j = sp->ends[2 * (size_t)q + 1];
+            double d2 = 0;
+            for (int a = 0; a < 3; ++a) {
+                const double d = m->pos[3 * (size_t)j + a] - m->pos[3 * (size_t)i + a];
+                d2 += d * d;
+            }
+            if (d2 > 0) h = std::min(h, std::sqrt(d2));
+        }
+        sim->grid_order = s > 0 && titan::grid_tile_order(m->pos, n, h, sim->caller_of_dev) &&
+                          sim->caller_of_dev.size() <= 2 * (size_t)n + 4096;
+        if (!sim->grid_order) titan::morton_order(m->pos, n, sim->caller_of_dev);
     } else {
         sim->caller_of_dev.resize(n);
         for (uint32_t i = 0; i < n; ++i) sim->caller_of_dev[i] = i;
     }
+    sim->n_dev = (uint32_t)sim->caller_of_dev.size();
     sim->dev_of_caller.resize(n);
-    for (uint32_t d = 0; d < n; ++d) sim->dev_of_caller[sim->caller_of_dev[d]] = d;
+    for (uint32_t d = 0; d < sim->n_dev; ++d)
+        if (sim->caller_of_dev[d] != UINT32_MAX) sim->dev_of_caller[sim->caller_of_dev[d]] = d;
     sim->inv_mass.resize(n);
     for (uint32_t i = 0; i < n; ++i)
         sim->inv_mass[i] = (m->fixed && m->fixed[i]) ? 0.f : (float)(1.0 / m->mass[i]);
@@ -392,8 +427,9 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
     if (uniform_c && s) sim->c.c_uniform = sim->damp[0];
 
     // ---- device state
-    CREATE_CK(dev_alloc(sim, &sim->state[0], n));
-    CREATE_CK(dev_alloc(sim, &sim->state[1], n));
+    const uint32_t nd = sim->n_dev;
+    CREATE_CK(dev_alloc(sim, &sim->state[0], nd));
+    CREATE_CK(dev_alloc(sim, &sim->state[1], nd));
     CREATE_CK(dev_alloc(sim, &sim->steps_dev, 2));
     CREATE_CK(dev_alloc(sim, &sim->d_err, 1));
     CREATE_CK(cudaMemsetAsync(sim->d_err, 0, sizeof(int), sim->stream));
@@ -408,8 +444,17 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
     }
 
     if (sim->accumulate == TITAN_ACCUM_CSR) {
-        if (!titan::build_sell(n, s, sp->ends, m->pos, sim->dev_of_caller, sim->sell))
+        if (!titan::build_sell(nd, s, sp->ends, m->pos, sim->dev_of_caller, sim->sell))
             return bail(fail(sim, TITAN_E_UNSUPPORTED, "padded incidence exceeds 2^32 entries"));
+        const int want = p->kernel_variant;
+        sim->csr_kernel = want == 0 ? 4 : want;
+        if (sim->csr_kernel == 4 &&
+            !titan::build_halo(nd, sim->sell, kHaloMaxSlots, sim->grid_order, sim->halo)) {
+            if (want == 4)
+                return bail(fail(sim, TITAN_E_UNSUPPORTED, "a block's neighbourhood table exceeds " +
+                                                               std::to_string(kHaloMaxSlots) + " slots"));
+            sim->csr_kernel = 3;
+        }
         const uint32_t E = sim->sell.entries;
         std::vector<float2> kl(E, make_float2(0.f, 0.f));
         std::vector<float> cc;
@@ -421,11 +466,25 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
             if (sim->has_c) cc[e] = sim->damp[q];
         }
         CREATE_CK(dev_alloc(sim, &sim->d_slice_off, sim->sell.slice_off.size()));
-        CREATE_CK(dev_alloc(sim, &sim->d_nbr, E));
         CREATE_CK(dev_alloc(sim, &sim->d_kl, E));
         CREATE_CK(upload(sim->d_slice_off, sim->sell.slice_off, sim->stream));
-        CREATE_CK(upload(sim->d_nbr, sim->sell.nbr, sim->stream));
         CREATE_CK(upload(sim->d_kl, kl, sim->stream));
+        if (sim->csr_kernel == 4) {
+            const titan::HaloHost &h = sim->halo;
+            CREATE_CK(dev_alloc(sim, &sim->d_nslot, E));
+            CREATE_CK(dev_alloc(sim, &sim->d_own_slot, nd));
+            CREATE_CK(dev_alloc(sim, &sim->d_ext_off, h.ext_off.size()));
+            CREATE_CK(dev_alloc(sim, &sim->d_ext_idx, h.ext_idx.size()));
+            CREATE_CK(dev_alloc(sim, &sim->d_ext_slot, h.ext_slot.size()));
+            CREATE_CK(upload(sim->d_nslot, h.nbr_slot, sim->stream));
+            CREATE_CK(upload(sim->d_own_slot, h.own_slot, sim->stream));
+            CREATE_CK(upload(sim->d_ext_off, h.ext_off, sim->stream));
+            CREATE_CK(upload(sim->d_ext_idx, h.ext_idx, sim->stream));
+            CREATE_CK(upload(sim->d_ext_slot, h.ext_slot, sim->stream));
+        } else {
+            CREATE_CK(dev_alloc(sim, &sim->d_nbr, E));
+            CREATE_CK(upload(sim->d_nbr, sim->sell.nbr, sim->stream));
+        }
         if (sim->has_c) {
             CREATE_CK(dev_alloc(sim, &sim->d_c, E));
             CREATE_CK(upload(sim->d_c, cc, sim->stream));
@@ -444,9 +503,9 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
             if (sim->has_c) cc[k] = sim->damp[q];
         }
         CREATE_CK(dev_alloc(sim, &sim->d_rec, s));
-        CREATE_CK(dev_alloc(sim, &sim->d_force, n));
+        CREATE_CK(dev_alloc(sim, &sim->d_force, nd));
         CREATE_CK(upload(sim->d_rec, r, sim->stream));
-        CREATE_CK(cudaMemsetAsync(sim->d_force, 0, (size_t)(n ? n : 1) * sizeof(float4), sim->stream));
+        CREATE_CK(cudaMemsetAsync(sim->d_force, 0, (size_t)(nd ? nd : 1) * sizeof(float4), sim->stream));
         if (sim->has_c) {
             CREATE_CK(dev_alloc(sim, &sim->d_rc, s));
             CREATE_CK(upload(sim->d_rc, cc, sim->stream));

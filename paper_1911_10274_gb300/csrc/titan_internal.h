@@ -51,6 +51,15 @@ struct SellView {
     int *err;                    // set to 1 when a bounded wait expires
 };
 
+struct HaloView {
+    const uint16_t *nslot;       // [E] neighbour slot in the block's table
+    const uint16_t *own_slot;    // [n] slot of each mass in its block's table
+    const uint32_t *ext_off;     // [n_blocks + 1]
+    const uint32_t *ext_idx;     // external entries: device index
+    const uint16_t *ext_slot;    //                   and slot
+    uint32_t table_slots;        // slots per block table (shared memory = 24 B each)
+};
+
 struct AtomicView {
     const uint4 *rec;            // [S] {i, j, bits(k), bits(L0)}
     const float *c;              // [S] or nullptr
@@ -64,6 +73,11 @@ struct AtomicView {
 cudaError_t launch_step_sell(const MassState *in, MassState *out, uint32_t n, const SellView &v,
                              const StepConst &c, const long long *step_in, long long *step_out,
                              cudaStream_t stream);
+
+// Halo form of the fused CSR step (see step_kernels.cu).
+cudaError_t launch_step_halo(const MassState *in, MassState *out, uint32_t n, const SellView &v,
+                             const HaloView &h, const StepConst &c, const long long *step_in,
+                             long long *step_out, cudaStream_t stream);
 
 cudaError_t launch_step_atomic(const MassState *in, MassState *out, uint32_t n,
                                const AtomicView &v, const StepConst &c, const long long *step_in,

@@ -40,9 +40,12 @@ def check(sys, steps, step0=0, spacing=None, **kw):
 MODES = [dict(accumulate=T.ACCUM_CSR), dict(accumulate=T.ACCUM_ATOMIC),
          dict(accumulate=T.ACCUM_CSR, kernel_variant=1),
          dict(accumulate=T.ACCUM_CSR, kernel_variant=2),
+         dict(accumulate=T.ACCUM_CSR, kernel_variant=3),
+         dict(accumulate=T.ACCUM_CSR, kernel_variant=4),
          dict(accumulate=T.ACCUM_CSR, order=T.ORDER_INPUT),
          dict(accumulate=T.ACCUM_CSR, graph_chunk=-1)]
-MODE_IDS = ["csr", "atomic", "csr-direct-loads", "csr-smem-staged", "csr-input-order", "csr-no-graph"]
+MODE_IDS = ["csr", "atomic", "csr-direct-loads", "csr-tma-staged", "csr-bulk-prefetch", "csr-halo",
+            "csr-input-order", "csr-no-graph"]
 
 
 @pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
@@ -59,7 +62,7 @@ def _contact_start():
     return s2
 
 
-@pytest.mark.parametrize("mode", MODES[:4], ids=MODE_IDS[:4])
+@pytest.mark.parametrize("mode", MODES[:6], ids=MODE_IDS[:6])
 def test_cube_contact_100_steps(mode):
     """From the oracle's state at step 3150 (just before the cube lands), 100
     steps through the first ground contact."""
@@ -69,7 +72,7 @@ def test_cube_contact_100_steps(mode):
     check(sys, 100, **mode)
 
 
-@pytest.mark.parametrize("mode", MODES[:4], ids=MODE_IDS[:4])
+@pytest.mark.parametrize("mode", MODES[:6], ids=MODE_IDS[:6])
 def test_cube_penetrating_and_sliding_100_steps(mode):
     """Cube placed 1 mm into the ground, sliding at 0.1 m/s: penalty contact
     and capped Coulomb friction on every bottom mass from the first step."""
@@ -79,7 +82,7 @@ def test_cube_penetrating_and_sliding_100_steps(mode):
     check(sys, 100, **mode)
 
 
-@pytest.mark.parametrize("mode", MODES[:4], ids=MODE_IDS[:4])
+@pytest.mark.parametrize("mode", MODES[:6], ids=MODE_IDS[:6])
 def test_cube_with_perturbed_rest_lengths_1000_steps(mode):
     """Same topology with rest lengths x U(0.95, 1.05) and lognormal k, so the
     internal spring forces are large from the first step."""
@@ -112,11 +115,28 @@ def test_large_lattice_scaled_down(accumulate):
 
 
 @pytest.mark.parametrize("order", [T.ORDER_INPUT, T.ORDER_MORTON], ids=["random-order", "morton"])
-def test_random_mesh_scaled_down(order):
+@pytest.mark.parametrize("variant", [0, 3], ids=["auto", "bulk-prefetch"])
+def test_random_mesh_scaled_down(order, variant):
     """Unstructured kNN mesh (random index order) at 5,000 points, ground on,
-    dt = 2e-5, 500 steps; tolerance relative to the mean point spacing."""
+    dt = 2e-5, 500 steps; tolerance relative to the mean point spacing.  Not
+    on a grid: Morton order and greedily coloured halo tables."""
     sys = inputs.random_mesh(n_points=5000, seed=1, lift=0.0)
-    check(sys, 500, order=order)
+    check(sys, 500, order=order, kernel_variant=variant)
+
+
+def test_lattice_with_holes_in_grid_tiles():
+    """A 10 x 7 x 5 lattice does not fill whole 4 x 4 x 2 tiles: the grid-tile
+    order leaves empty device slots that must stay inert."""
+    pos = inputs.lattice_points(10, 7, 5, 0.1, (0.0, 0.0, 0.3))
+    ends = inputs.lattice_springs(10, 7, 5)
+    d = np.linalg.norm(pos[ends[:, 1]] - pos[ends[:, 0]], axis=1)
+    rng = np.random.default_rng(9)
+    sys = inputs.System(pos=pos, vel=rng.normal(0, 0.05, pos.shape), mass=np.full(len(pos), 0.1),
+                        fixed=np.zeros(len(pos), np.uint8), ends=ends, k=np.full(len(ends), 1e4),
+                        rest=d * rng.uniform(0.97, 1.03, len(d)), damping=np.full(len(ends), 1.0),
+                        dt=1e-4, ground=True, spacing=0.1)
+    for var in (0, 4, 3):
+        check(sys, 1000, kernel_variant=var)
 
 
 def test_actuated_robot_1000_steps():
@@ -175,12 +195,12 @@ def test_resume_from_snapshot_is_bit_exact():
 
 
 def test_csr_kernel_variants_agree_bit_exact():
-    """The three CSR kernels (bulk-prefetched, direct, smem-staged) sum the
+    """The CSR kernels (halo, bulk-prefetched, direct, TMA-staged) sum the
     same entries in the same order: identical trajectories."""
     sys = inputs.cube_drop(drop_height=0.02)
     sys.vel[:, 0] = 0.3
     a = gpu_run(sys, 500, kernel_variant=0)
-    for var in (1, 2):
+    for var in (1, 2, 3, 4):
         b = gpu_run(sys, 500, kernel_variant=var)
         assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
 
@@ -280,7 +300,8 @@ def test_full_size_lattice_against_oracle_in_bench_configuration():
     sys = inputs.large_lattice(n=100, seed=0)
     xo, vo = oracle.run(sys, 64)
     for mode in (dict(accumulate=T.ACCUM_CSR), dict(accumulate=T.ACCUM_CSR, kernel_variant=1),
-                 dict(accumulate=T.ACCUM_CSR, kernel_variant=2), dict(accumulate=T.ACCUM_ATOMIC)):
+                 dict(accumulate=T.ACCUM_CSR, kernel_variant=2), dict(accumulate=T.ACCUM_CSR, kernel_variant=3),
+                 dict(accumulate=T.ACCUM_ATOMIC)):
         xg, vg, _ = gpu_run(sys, 64, **mode)
         err = np.abs(xg - xo).max()
         assert err <= POS_TOL_FRAC * sys.spacing, err
