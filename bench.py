@@ -31,6 +31,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "spring updates/s"
+CSR_KERNELS = ["auto (halo tables in shared memory)", "direct-loads", "tma-staged", "bulk-l2-prefetch", "halo"]
+CSR_KERNEL_NAMES = ["k_step_halo", "k_step_sell", "k_step_sell_staged", "k_step_sell_pf", "k_step_halo"]
 UNIT = "spring_updates/s"
 L2_BYTES = 126 * 1024 * 1024
 
@@ -190,7 +192,7 @@ def config_for(args, system):
                         "lattice50": "50^3 lattice, 1,558,396 springs", "mesh2m": "2M-point kNN mesh",
                         "cube1k": "10^3 cube drop"}[args.workload],
            "accumulate": args.accumulate, "order": "morton", "graph_chunk": 64,
-           "csr_kernel": ["bulk-l2-prefetch", "direct-loads", "smem-staged"][args.kernel_variant],
+           "csr_kernel": CSR_KERNELS[args.kernel_variant],
            "parallelism": f"replicas x{args.gpus}",
            "l2": "inputs larger than L2 (spring data > 126 MB), no flush"}
     if system is not None:
@@ -261,7 +263,7 @@ def run_ours(args):
         "config": config_for(args, system),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": ["k_step_sell_pf", "k_step_sell", "k_step_sell_staged"][args.kernel_variant]
+                     "kernel": CSR_KERNEL_NAMES[args.kernel_variant]
                      if acc == T.ACCUM_CSR else "k_springs_atomic+k_masses_atomic",
                      "algorithmic_bytes_per_launch": alg,
                      "peak_source": f"{peak_kind} HBM copy bandwidth"},
@@ -291,7 +293,7 @@ def main():
     ap.add_argument("--accumulate", choices=["csr", "atomic"], default="csr")
     ap.add_argument("--workload", default="lattice1m")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel-variant", type=int, default=0, help="CSR kernel: 0 bulk L2 prefetch, 1 direct loads, 2 smem-staged")
+    ap.add_argument("--kernel-variant", type=int, default=0, help="CSR kernel: 0 auto, 1 direct loads, 2 TMA-staged, 3 bulk L2 prefetch, 4 halo")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -31,8 +31,10 @@ __device__ __forceinline__ void spring_force(const float4 &p, const float4 &v, c
                                              float &fx, float &fy, float &fz) {
     const float dx = q.x - p.x, dy = q.y - p.y, dz = q.z - p.z;
     const float l2 = dx * dx + dy * dy + dz * dz;
-    const float l = sqrtf(l2);
-    const float inv = l2 > 0.f ? 1.0f / l : 0.f;
+    // one reciprocal square root gives both 1/l and l = l2 / l; its error
+    // (a few ulp) is below the rounding of the FP32 positions themselves
+    const float inv = l2 > 0.f ? rsqrtf(l2) : 0.f;
+    const float l = l2 * inv;
     const float ux = dx * inv, uy = dy * inv, uz = dz * inv;
     const float rate = (w.x - v.x) * ux + (w.y - v.y) * uy + (w.z - v.z) * uz;
     const float f = k * (l - L) + c * rate;

@@ -151,7 +151,7 @@ k_step_sell_pf(const MassState *__restrict__ in, MassState *__restrict__ out, ui
 constexpr int kHaloThreads = 256;
 
 template <bool HAS_C, bool HAS_ACT, bool GROUND>
-__global__ void __launch_bounds__(kHaloThreads)
+__global__ void __launch_bounds__(kHaloThreads, 6)
 k_step_halo(const MassState *__restrict__ in, MassState *__restrict__ out, uint32_t n,
             const uint32_t *__restrict__ slice_off, const uint16_t *__restrict__ nslot,
             const float2 *__restrict__ kl, const float *__restrict__ cc,
@@ -498,6 +498,11 @@ cudaError_t launch_step_halo(const MassState *in, MassState *out, uint32_t n, co
         auto kern = k_step_halo<HC, HA, GR>;                                                     \
         if (bytes > 48 * 1024) {                                                                 \
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes); \
+            if (e != cudaSuccess) return e;                                                      \
+        }                                                                                        \
+        {                                                                                        \
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, \
+                                                 (int)cudaSharedmemCarveoutMaxShared);            \
             if (e != cudaSuccess) return e;                                                      \
         }                                                                                        \
         kern<<<g, kHaloThreads, bytes, stream>>>(in, out, n, v.slice_off, h.nslot, v.kl, v.c, v.act, \
