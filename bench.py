@@ -31,8 +31,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "spring updates/s"
-CSR_KERNELS = ["auto (halo tables in shared memory)", "direct-loads", "tma-staged", "bulk-l2-prefetch", "halo"]
-CSR_KERNEL_NAMES = ["k_step_halo", "k_step_sell", "k_step_sell_staged", "k_step_sell_pf", "k_step_halo"]
+CSR_KERNELS = ["auto (halo table + TMA-staged stream)", "direct-loads", "tma-staged", "bulk-l2-prefetch",
+               "halo", "halo+tma"]
+CSR_KERNEL_NAMES = ["k_step_halo_tma", "k_step_sell", "k_step_sell_staged", "k_step_sell_pf", "k_step_halo",
+                    "k_step_halo_tma"]
 UNIT = "spring_updates/s"
 L2_BYTES = 126 * 1024 * 1024
 
@@ -293,7 +295,7 @@ def main():
     ap.add_argument("--accumulate", choices=["csr", "atomic"], default="csr")
     ap.add_argument("--workload", default="lattice1m")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel-variant", type=int, default=0, help="CSR kernel: 0 auto, 1 direct loads, 2 TMA-staged, 3 bulk L2 prefetch, 4 halo")
+    ap.add_argument("--kernel-variant", type=int, default=0, help="CSR kernel: 0 auto, 1 direct loads, 2 TMA-staged, 3 bulk L2 prefetch, 4 halo, 5 halo+TMA")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

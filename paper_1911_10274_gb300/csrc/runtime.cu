@@ -29,6 +29,7 @@ thread_local std::string g_thread_error = "";
 constexpr int kDefaultGraphChunk = 64;
 constexpr uint32_t kDefaultSpinLimit = 1u << 22;
 constexpr uint32_t kHaloMaxSlots = 4096;     // 96 KiB of shared memory per CTA
+constexpr size_t kHaloTmaMaxSmem = 112 * 1024;  // two CTAs per SM
 
 struct DeviceGuard {
     int prev = -1;
@@ -73,7 +74,8 @@ struct titan_sim {
     titan::SellHost sell;
     titan::HaloHost halo;
     titan::RecordsHost rec;
-    int csr_kernel = 0;                   // resolved: 1 direct, 2 smem-staged, 3 bulk-prefetch, 4 halo
+    int csr_kernel = 0;                   // resolved: 1 direct, 2 smem-staged, 3 bulk-prefetch, 4 halo, 5 halo+TMA
+    uint32_t halo_w_max = 0;              // staged columns per slice (halo+TMA kernel)
 
     MassState *state[2] = {nullptr, nullptr};
     long long *steps_dev = nullptr;       // [2]
@@ -197,7 +199,7 @@ titan_status validate(const titan_masses *m, const titan_springs *sp, const tita
     if (p->exec < TITAN_EXEC_AUTO || p->exec > TITAN_EXEC_PERSISTENT)
         return fail(nullptr, TITAN_E_INVALID, "params.exec out of range");
     if (p->device < 0) return fail(nullptr, TITAN_E_INVALID, "params.device must be >= 0");
-    if (p->kernel_variant < 0 || p->kernel_variant > 4) return fail(nullptr, TITAN_E_INVALID, "params.kernel_variant must be 0..4");
+    if (p->kernel_variant < 0 || p->kernel_variant > 5) return fail(nullptr, TITAN_E_INVALID, "params.kernel_variant must be 0..5");
     for (uint64_t i = 0; i < m->n; ++i) {
         for (int a = 0; a < 3; ++a) {
             if (!finite(m->pos[3 * i + a])) return fail(nullptr, TITAN_E_INVALID, "masses.pos has a non-finite value at mass " + std::to_string(i));
@@ -263,9 +265,12 @@ cudaError_t enqueue_step(titan_sim *sim, cudaStream_t st, int b) {
     if (sim->accumulate == TITAN_ACCUM_CSR) {
         titan::SellView v{sim->d_slice_off, sim->d_nbr, sim->d_kl, sim->has_c ? sim->d_c : nullptr,
                           sim->has_act ? sim->d_act : nullptr, 0, sim->spin_limit, sim->d_err};
-        if (sim->csr_kernel == 4) {
+        if (sim->csr_kernel == 4 || sim->csr_kernel == 5) {
             titan::HaloView h{sim->d_nslot, sim->d_own_slot, sim->d_ext_off, sim->d_ext_idx,
                               sim->d_ext_slot, sim->halo.max_table};
+            if (sim->csr_kernel == 5)
+                return titan::launch_step_halo_tma(in, out, sim->n_dev, v, h, sim->halo_w_max, sim->c, si,
+                                                   so, st);
             return titan::launch_step_halo(in, out, sim->n_dev, v, h, sim->c, si, so, st);
         }
         v.variant = sim->csr_kernel == 3 ? 0 : sim->csr_kernel;   // launcher: 0 prefetch, 1 direct, 2 staged
@@ -274,6 +279,23 @@ cudaError_t enqueue_step(titan_sim *sim, cudaStream_t st, int b) {
     titan::AtomicView v{sim->d_rec, sim->has_c ? sim->d_rc : nullptr,
                         sim->has_act ? sim->d_ract : nullptr, sim->d_force, sim->s};
     return titan::launch_step_atomic(in, out, sim->n_dev, v, sim->c, si, so, st);
+}
+
+// Staged columns per slice for the halo+TMA kernel: every slice if two CTAs
+// per SM still fit, else the widest width that does (wider slices read their
+// columns from global memory).  False if not even two columns fit.
+bool choose_halo_width(titan_sim *sim) {
+    uint32_t w_max = 0;
+    for (size_t sl = 0; sl + 1 < sim->sell.slice_off.size(); ++sl)
+        w_max = std::max(w_max, (sim->sell.slice_off[sl + 1] - sim->sell.slice_off[sl]) / 32);
+    w_max = std::max(2u, (w_max + 1) & ~1u);
+    auto bytes = [&](uint32_t w) {
+        return titan::halo_tma_smem_bytes(sim->halo.max_table, w, sim->has_c, sim->has_act);
+    };
+    while (w_max > 2 && bytes(w_max) > kHaloTmaMaxSmem) w_max -= 2;
+    if (bytes(w_max) > kHaloTmaMaxSmem) return false;
+    sim->halo_w_max = w_max;
+    return true;
 }
 
 // Reads (and clears) the device error flag set by bounded waits that expired.
@@ -447,13 +469,18 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
         if (!titan::build_sell(nd, s, sp->ends, m->pos, sim->dev_of_caller, sim->sell))
             return bail(fail(sim, TITAN_E_UNSUPPORTED, "padded incidence exceeds 2^32 entries"));
         const int want = p->kernel_variant;
-        sim->csr_kernel = want == 0 ? 4 : want;
-        if (sim->csr_kernel == 4 &&
+        sim->csr_kernel = want == 0 ? 5 : want;
+        if ((sim->csr_kernel == 4 || sim->csr_kernel == 5) &&
             !titan::build_halo(nd, sim->sell, kHaloMaxSlots, sim->grid_order, sim->halo)) {
-            if (want == 4)
+            if (want == 4 || want == 5)
                 return bail(fail(sim, TITAN_E_UNSUPPORTED, "a block's neighbourhood table exceeds " +
                                                                std::to_string(kHaloMaxSlots) + " slots"));
             sim->csr_kernel = 3;
+        }
+        if (sim->csr_kernel == 5 && !choose_halo_width(sim)) {
+            if (want == 5)
+                return bail(fail(sim, TITAN_E_UNSUPPORTED, "the halo+TMA kernel's shared memory does not fit"));
+            sim->csr_kernel = 4;
         }
         const uint32_t E = sim->sell.entries;
         std::vector<float2> kl(E, make_float2(0.f, 0.f));
@@ -469,7 +496,7 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
         CREATE_CK(dev_alloc(sim, &sim->d_kl, E));
         CREATE_CK(upload(sim->d_slice_off, sim->sell.slice_off, sim->stream));
         CREATE_CK(upload(sim->d_kl, kl, sim->stream));
-        if (sim->csr_kernel == 4) {
+        if (sim->csr_kernel == 4 || sim->csr_kernel == 5) {
             const titan::HaloHost &h = sim->halo;
             CREATE_CK(dev_alloc(sim, &sim->d_nslot, E));
             CREATE_CK(dev_alloc(sim, &sim->d_own_slot, nd));
@@ -613,6 +640,7 @@ titan_status titan_set_actuation(titan_sim *sim, uint32_t n, const uint32_t *ids
     sim->c.act_omega = 2.0 * 3.14159265358979323846 * (double)freq_hz;
     TITAN_CK(sim, upload_actuation(sim));
     sim->has_act = true;
+    if (sim->csr_kernel == 5 && !choose_halo_width(sim)) sim->csr_kernel = 4;   // larger entries
     free_graphs(sim);       // kernel variant and constants changed
     return TITAN_OK;
 }

@@ -239,6 +239,135 @@ k_step_halo(const MassState *__restrict__ in, MassState *__restrict__ out, uint3
     integrate<GROUND>(p, v, fx, fy, fz, c, out + i);
 }
 
+// K1, halo + TMA form.  As k_step_halo, but the half-edge stream of each
+// warp's slice (all columns of every array) is copied into shared memory by
+// the TMA engine (1-D bulk copies on one mbarrier per warp), issued before the
+// halo fill so the DRAM transfer overlaps it; the hot loop then reads only
+// shared memory.  Slices wider than the staging buffer (w_max columns) read
+// their columns from global memory instead.  The mbarrier wait is bounded by
+// spin_limit polls; on expiry the warp records the error in *err, waits
+// (bounded) for its copies and leaves its masses unwritten.
+template <bool HAS_C, bool HAS_ACT>
+constexpr int halo_entry_bytes() { return 10 + (HAS_C ? 4 : 0) + (HAS_ACT ? 8 : 0); }
+
+template <bool HAS_C, bool HAS_ACT, bool GROUND>
+__global__ void __launch_bounds__(kHaloThreads, 2)
+k_step_halo_tma(const MassState *__restrict__ in, MassState *__restrict__ out, uint32_t n,
+                const uint32_t *__restrict__ slice_off, const uint16_t *__restrict__ nslot,
+                const float2 *__restrict__ kl, const float *__restrict__ cc,
+                const float2 *__restrict__ act, const uint16_t *__restrict__ own_slot,
+                const uint32_t *__restrict__ ext_off, const uint32_t *__restrict__ ext_idx,
+                const uint16_t *__restrict__ ext_slot, uint32_t table_slots, uint32_t w_max,
+                StepConst c, const long long *__restrict__ step_in, long long *__restrict__ step_out,
+                uint32_t spin_limit, int *__restrict__ err) {
+    constexpr uint32_t FULL = 0xffffffffu;
+    constexpr int EB = halo_entry_bytes<HAS_C, HAS_ACT>();
+    extern __shared__ __align__(16) unsigned char hsm[];
+    __shared__ uint64_t bars[kHaloThreads / 32];
+    float2 *tA = reinterpret_cast<float2 *>(hsm);
+    float2 *tB = tA + table_slots, *tC = tB + table_slots;
+    const uint32_t b = blockIdx.x, tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    const uint32_t i = b * kHaloThreads + tid, sl = i >> 5;
+    const uint32_t n_slices = (n + 31) >> 5;
+    // per-warp staging buffer: [kl float2 | act float2 | c float | slot u16] x (w_max * 32)
+    const size_t per_warp = (size_t)w_max * 32 * EB;
+    unsigned char *wb = hsm + (size_t)3 * table_slots * sizeof(float2) + (size_t)w * per_warp;
+    float2 *s_kl = reinterpret_cast<float2 *>(wb);
+    float2 *s_act = reinterpret_cast<float2 *>(wb + (size_t)w_max * 32 * 8);
+    float *s_c = reinterpret_cast<float *>(wb + (size_t)w_max * 32 * (HAS_ACT ? 16 : 8));
+    uint16_t *s_slot = reinterpret_cast<uint16_t *>(wb + (size_t)w_max * 32 * (8 + (HAS_ACT ? 8 : 0) + (HAS_C ? 4 : 0)));
+
+    long long step = 0;
+    if (HAS_ACT) step = *step_in;
+    if (b == 0 && tid == 0) *step_out = *step_in + 1;
+
+    const bool warp_live = sl < n_slices;                    // warp-uniform
+    uint32_t e0 = 0, width = 0;
+    if (warp_live) {
+        e0 = __ldg(slice_off + sl);
+        width = (__ldg(slice_off + sl + 1) - e0) >> 5;
+    }
+    const bool staged = warp_live && width > 0 && width <= w_max;
+    if (staged && lane == 0) {
+        const uint32_t ne = width * 32;
+        ptx::mbar_init(&bars[w], 1);
+        ptx::fence_mbar_init();
+        ptx::mbar_arrive_expect_tx(&bars[w], ne * EB);
+        ptx::bulk_g2s(s_kl, kl + e0, ne * 8, &bars[w]);
+        if (HAS_ACT) ptx::bulk_g2s(s_act, act + e0, ne * 8, &bars[w]);
+        if (HAS_C) ptx::bulk_g2s(s_c, cc + e0, ne * 4, &bars[w]);
+        ptx::bulk_g2s(s_slot, nslot + e0, ne * 2, &bars[w]);
+    }
+    const bool valid = i < n;
+    float4 p = make_float4(0.f, 0.f, 0.f, 0.f), v = p;
+    if (valid) {
+        load_state(in + i, p, v);
+        const uint32_t s = own_slot[i];
+        tA[s] = make_float2(p.x, p.y);
+        tB[s] = make_float2(p.z, v.x);
+        tC[s] = make_float2(v.y, v.z);
+    }
+    const uint32_t h0 = __ldg(ext_off + b), h1 = __ldg(ext_off + b + 1);
+    for (uint32_t h = h0 + tid; h < h1; h += kHaloThreads) {
+        float4 q, ww;
+        load_state(in + __ldg(ext_idx + h), q, ww);
+        const uint32_t s = __ldg(ext_slot + h);
+        tA[s] = make_float2(q.x, q.y);
+        tB[s] = make_float2(q.z, ww.x);
+        tC[s] = make_float2(ww.y, ww.z);
+    }
+    __syncthreads();                    // also publishes the mbarrier initialisation
+    if (!warp_live) return;
+    if (staged) {
+        bool done = false;
+        for (uint32_t it = 0; it < spin_limit; ++it) {
+            done = ptx::mbar_try_wait(&bars[w], 0);
+            if (__all_sync(FULL, done)) break;
+        }
+        if (!__all_sync(FULL, done)) {
+            if (lane == 0) {
+                atomicExch(err, 1);
+                ptx::mbar_wait_bounded(&bars[w], 0, spin_limit);
+            }
+            __syncwarp();
+            return;
+        }
+    }
+    if (!valid) return;
+
+    const float ph = HAS_ACT ? clock_phase(c, step) : 0.f;
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+    for (uint32_t t = 0; t < width; t += 2) {
+        const uint32_t a = t * 32 + lane, bb = a + 32;
+        uint32_t j0, j1;
+        float2 a0, a1, s0 = make_float2(0.f, 0.f), s1 = s0;
+        float c0 = c.c_uniform, c1 = c.c_uniform;
+        if (staged) {
+            j0 = s_slot[a]; j1 = s_slot[bb];
+            a0 = s_kl[a]; a1 = s_kl[bb];
+            if (HAS_C) { c0 = s_c[a]; c1 = s_c[bb]; }
+            if (HAS_ACT) { s0 = s_act[a]; s1 = s_act[bb]; }
+        } else {
+            j0 = __ldcs(nslot + e0 + a); j1 = __ldcs(nslot + e0 + bb);
+            a0 = __ldcs(kl + e0 + a); a1 = __ldcs(kl + e0 + bb);
+            if (HAS_C) { c0 = __ldcs(cc + e0 + a); c1 = __ldcs(cc + e0 + bb); }
+            if (HAS_ACT) { s0 = __ldcs(act + e0 + a); s1 = __ldcs(act + e0 + bb); }
+        }
+        const float2 qa0 = tA[j0], qb0 = tB[j0], qc0 = tC[j0];
+        const float2 qa1 = tA[j1], qb1 = tB[j1], qc1 = tC[j1];
+        float L0 = a0.y, L1 = a1.y;
+        if (HAS_ACT) {
+            L0 = a0.y * (1.f + s0.x * sinf(ph + s0.y));
+            L1 = a1.y * (1.f + s1.x * sinf(ph + s1.y));
+        }
+        spring_force(p, v, make_float4(qa0.x, qa0.y, qb0.x, 0.f), make_float4(qb0.y, qc0.x, qc0.y, 0.f),
+                     a0.x, L0, c0, fx, fy, fz);
+        spring_force(p, v, make_float4(qa1.x, qa1.y, qb1.x, 0.f), make_float4(qb1.y, qc1.x, qc1.y, 0.f),
+                     a1.x, L1, c1, fx, fy, fz);
+    }
+    integrate<GROUND>(p, v, fx, fy, fz, c, out + i);
+}
+
 // K1, TMA-staged form.  One warp owns one SELL slice (32 masses).  Lane 0
 // streams the slice's half-edge columns into a per-warp ring of shared-memory
 // stages with 1-D bulk copies (TMA), kStagesK1 chunks of kChunkCols columns
@@ -518,6 +647,42 @@ cudaError_t launch_step_halo(const MassState *in, MassState *out, uint32_t n, co
     }
 #undef TITAN_HALO
     return cudaGetLastError();
+}
+
+cudaError_t launch_step_halo_tma(const MassState *in, MassState *out, uint32_t n, const SellView &v,
+                                 const HaloView &h, uint32_t w_max, const StepConst &c,
+                                 const long long *step_in, long long *step_out, cudaStream_t stream) {
+    const bool hc = v.c != nullptr, ha = v.act != nullptr, gr = c.ground != 0;
+    const unsigned g = n ? (n + kHaloThreads - 1) / kHaloThreads : 1;
+#define TITAN_HTMA(HC, HA, GR)                                                                   \
+    do {                                                                                         \
+        auto kern = k_step_halo_tma<HC, HA, GR>;                                                 \
+        const size_t bytes = (size_t)3 * h.table_slots * sizeof(float2) +                         \
+                             (size_t)(kHaloThreads / 32) * w_max * 32 * halo_entry_bytes<HC, HA>(); \
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes); \
+        if (e != cudaSuccess) return e;                                                          \
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,           \
+                                 (int)cudaSharedmemCarveoutMaxShared);                            \
+        if (e != cudaSuccess) return e;                                                          \
+        kern<<<g, kHaloThreads, bytes, stream>>>(in, out, n, v.slice_off, h.nslot, v.kl, v.c, v.act, \
+                                                 h.own_slot, h.ext_off, h.ext_idx, h.ext_slot,   \
+                                                 h.table_slots, w_max, c, step_in, step_out,     \
+                                                 v.spin_limit, v.err);                           \
+    } while (0)
+    if (hc) {
+        if (ha) { if (gr) TITAN_HTMA(true, true, true); else TITAN_HTMA(true, true, false); }
+        else    { if (gr) TITAN_HTMA(true, false, true); else TITAN_HTMA(true, false, false); }
+    } else {
+        if (ha) { if (gr) TITAN_HTMA(false, true, true); else TITAN_HTMA(false, true, false); }
+        else    { if (gr) TITAN_HTMA(false, false, true); else TITAN_HTMA(false, false, false); }
+    }
+#undef TITAN_HTMA
+    return cudaGetLastError();
+}
+
+size_t halo_tma_smem_bytes(uint32_t table_slots, uint32_t w_max, bool has_c, bool has_act) {
+    return (size_t)3 * table_slots * sizeof(float2) +
+           (size_t)(kHaloThreads / 32) * w_max * 32 * (10 + (has_c ? 4 : 0) + (has_act ? 8 : 0));
 }
 
 cudaError_t launch_step_atomic(const MassState *in, MassState *out, uint32_t n,

@@ -42,10 +42,11 @@ MODES = [dict(accumulate=T.ACCUM_CSR), dict(accumulate=T.ACCUM_ATOMIC),
          dict(accumulate=T.ACCUM_CSR, kernel_variant=2),
          dict(accumulate=T.ACCUM_CSR, kernel_variant=3),
          dict(accumulate=T.ACCUM_CSR, kernel_variant=4),
+         dict(accumulate=T.ACCUM_CSR, kernel_variant=5),
          dict(accumulate=T.ACCUM_CSR, order=T.ORDER_INPUT),
          dict(accumulate=T.ACCUM_CSR, graph_chunk=-1)]
 MODE_IDS = ["csr", "atomic", "csr-direct-loads", "csr-tma-staged", "csr-bulk-prefetch", "csr-halo",
-            "csr-input-order", "csr-no-graph"]
+            "csr-halo-tma", "csr-input-order", "csr-no-graph"]
 
 
 @pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
@@ -62,7 +63,7 @@ def _contact_start():
     return s2
 
 
-@pytest.mark.parametrize("mode", MODES[:6], ids=MODE_IDS[:6])
+@pytest.mark.parametrize("mode", MODES[:7], ids=MODE_IDS[:7])
 def test_cube_contact_100_steps(mode):
     """From the oracle's state at step 3150 (just before the cube lands), 100
     steps through the first ground contact."""
@@ -72,7 +73,7 @@ def test_cube_contact_100_steps(mode):
     check(sys, 100, **mode)
 
 
-@pytest.mark.parametrize("mode", MODES[:6], ids=MODE_IDS[:6])
+@pytest.mark.parametrize("mode", MODES[:7], ids=MODE_IDS[:7])
 def test_cube_penetrating_and_sliding_100_steps(mode):
     """Cube placed 1 mm into the ground, sliding at 0.1 m/s: penalty contact
     and capped Coulomb friction on every bottom mass from the first step."""
@@ -82,7 +83,7 @@ def test_cube_penetrating_and_sliding_100_steps(mode):
     check(sys, 100, **mode)
 
 
-@pytest.mark.parametrize("mode", MODES[:6], ids=MODE_IDS[:6])
+@pytest.mark.parametrize("mode", MODES[:7], ids=MODE_IDS[:7])
 def test_cube_with_perturbed_rest_lengths_1000_steps(mode):
     """Same topology with rest lengths x U(0.95, 1.05) and lognormal k, so the
     internal spring forces are large from the first step."""
@@ -115,7 +116,7 @@ def test_large_lattice_scaled_down(accumulate):
 
 
 @pytest.mark.parametrize("order", [T.ORDER_INPUT, T.ORDER_MORTON], ids=["random-order", "morton"])
-@pytest.mark.parametrize("variant", [0, 3], ids=["auto", "bulk-prefetch"])
+@pytest.mark.parametrize("variant", [0, 4, 3], ids=["auto", "halo", "bulk-prefetch"])
 def test_random_mesh_scaled_down(order, variant):
     """Unstructured kNN mesh (random index order) at 5,000 points, ground on,
     dt = 2e-5, 500 steps; tolerance relative to the mean point spacing.  Not
@@ -135,7 +136,7 @@ def test_lattice_with_holes_in_grid_tiles():
                         fixed=np.zeros(len(pos), np.uint8), ends=ends, k=np.full(len(ends), 1e4),
                         rest=d * rng.uniform(0.97, 1.03, len(d)), damping=np.full(len(ends), 1.0),
                         dt=1e-4, ground=True, spacing=0.1)
-    for var in (0, 4, 3):
+    for var in (0, 5, 4, 3):
         check(sys, 1000, kernel_variant=var)
 
 
@@ -200,7 +201,7 @@ def test_csr_kernel_variants_agree_bit_exact():
     sys = inputs.cube_drop(drop_height=0.02)
     sys.vel[:, 0] = 0.3
     a = gpu_run(sys, 500, kernel_variant=0)
-    for var in (1, 2, 3, 4):
+    for var in (1, 2, 3, 4, 5):
         b = gpu_run(sys, 500, kernel_variant=var)
         assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
 
@@ -301,7 +302,7 @@ def test_full_size_lattice_against_oracle_in_bench_configuration():
     xo, vo = oracle.run(sys, 64)
     for mode in (dict(accumulate=T.ACCUM_CSR), dict(accumulate=T.ACCUM_CSR, kernel_variant=1),
                  dict(accumulate=T.ACCUM_CSR, kernel_variant=2), dict(accumulate=T.ACCUM_CSR, kernel_variant=3),
-                 dict(accumulate=T.ACCUM_ATOMIC)):
+                 dict(accumulate=T.ACCUM_CSR, kernel_variant=4), dict(accumulate=T.ACCUM_ATOMIC)):
         xg, vg, _ = gpu_run(sys, 64, **mode)
         err = np.abs(xg - xo).max()
         assert err <= POS_TOL_FRAC * sys.spacing, err
