@@ -31,9 +31,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "spring updates/s"
-CSR_KERNELS = ["auto (halo table + TMA-staged stream)", "direct-loads", "tma-staged", "bulk-l2-prefetch",
+CSR_KERNELS = ["auto (halo table in shared memory)", "direct-loads", "tma-staged", "bulk-l2-prefetch",
                "halo", "halo+tma"]
-CSR_KERNEL_NAMES = ["k_step_halo_tma", "k_step_sell", "k_step_sell_staged", "k_step_sell_pf", "k_step_halo",
+CSR_KERNEL_NAMES = ["k_step_halo", "k_step_sell", "k_step_sell_staged", "k_step_sell_pf", "k_step_halo",
                     "k_step_halo_tma"]
 UNIT = "spring_updates/s"
 L2_BYTES = 126 * 1024 * 1024

@@ -76,6 +76,7 @@ struct titan_sim {
     titan::RecordsHost rec;
     int csr_kernel = 0;                   // resolved: 1 direct, 2 smem-staged, 3 bulk-prefetch, 4 halo, 5 halo+TMA
     uint32_t halo_w_max = 0;              // staged columns per slice (halo+TMA kernel)
+    uint32_t halo_ahead = 0;              // L2 prefetch distance in blocks (halo kernel)
 
     MassState *state[2] = {nullptr, nullptr};
     long long *steps_dev = nullptr;       // [2]
@@ -267,7 +268,7 @@ cudaError_t enqueue_step(titan_sim *sim, cudaStream_t st, int b) {
                           sim->has_act ? sim->d_act : nullptr, 0, sim->spin_limit, sim->d_err};
         if (sim->csr_kernel == 4 || sim->csr_kernel == 5) {
             titan::HaloView h{sim->d_nslot, sim->d_own_slot, sim->d_ext_off, sim->d_ext_idx,
-                              sim->d_ext_slot, sim->halo.max_table};
+                              sim->d_ext_slot, sim->halo.max_table, sim->halo_ahead};
             if (sim->csr_kernel == 5)
                 return titan::launch_step_halo_tma(in, out, sim->n_dev, v, h, sim->halo_w_max, sim->c, si,
                                                    so, st);
@@ -469,7 +470,7 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
         if (!titan::build_sell(nd, s, sp->ends, m->pos, sim->dev_of_caller, sim->sell))
             return bail(fail(sim, TITAN_E_UNSUPPORTED, "padded incidence exceeds 2^32 entries"));
         const int want = p->kernel_variant;
-        sim->csr_kernel = want == 0 ? 5 : want;
+        sim->csr_kernel = want == 0 ? 4 : want;
         if ((sim->csr_kernel == 4 || sim->csr_kernel == 5) &&
             !titan::build_halo(nd, sim->sell, kHaloMaxSlots, sim->grid_order, sim->halo)) {
             if (want == 4 || want == 5)
@@ -497,6 +498,10 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
         CREATE_CK(upload(sim->d_slice_off, sim->sell.slice_off, sim->stream));
         CREATE_CK(upload(sim->d_kl, kl, sim->stream));
         if (sim->csr_kernel == 4 || sim->csr_kernel == 5) {
+            // prefetch about half a wave ahead: a wave is (SMs x 6) resident CTAs
+            int sms = 0;
+            CREATE_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
+            sim->halo_ahead = (uint32_t)std::max(1, sms * 6 / 2);
             const titan::HaloHost &h = sim->halo;
             CREATE_CK(dev_alloc(sim, &sim->d_nslot, E));
             CREATE_CK(dev_alloc(sim, &sim->d_own_slot, nd));

@@ -141,14 +141,28 @@ k_step_sell_pf(const MassState *__restrict__ in, MassState *__restrict__ out, ui
 // K1, halo form (the default when the neighbourhood tables fit).  One CTA
 // per block of kHaloThreads consecutive device masses.  The CTA first copies
 // the state of every mass its half-edges touch - its own masses and the
-// external halo - into a shared-memory table (three float2 arrays: (x, y),
-// (z, vx), (vy, vz)), then each thread runs its SELL row reading neighbours
-// from that table through 16-bit slots.  Each neighbour state is fetched from
-// global memory once per block instead of once per half-edge, and the slots
-// are coloured so that a half-warp's 8-byte table reads fall in distinct
-// banks.  The half-edge stream (u16 slot + {k, L0}, 10 bytes) is prefetched
-// into L2 by one TMA bulk request per warp and array.
+// external halo - into a shared-memory table (a float4 (x, y, z, vx) and a
+// float2 (vy, vz) per slot), then each thread runs its SELL row reading
+// neighbours from that table through 16-bit slots.  Each neighbour state is
+// fetched from global memory once per block instead of once per half-edge, and
+// the slots are coloured so that a quarter-warp's 16-byte and a half-warp's
+// 8-byte table reads fall in distinct banks.  The half-edge stream (u16 slot
+// + {k, L0}, 10 bytes) is brought into L2 by TMA bulk prefetches issued
+// `ahead` blocks in advance (the first `ahead` blocks prefetch their own), so
+// the loop's stream loads hit L2 while DRAM streams the blocks to come.
 constexpr int kHaloThreads = 256;
+
+template <bool HAS_C, bool HAS_ACT>
+__device__ __forceinline__ void prefetch_slice(const uint32_t *slice_off, uint32_t sl, const uint16_t *nslot,
+                                               const float2 *kl, const float *cc, const float2 *act) {
+    const uint32_t e0 = __ldg(slice_off + sl);
+    const uint32_t ne = __ldg(slice_off + sl + 1) - e0;
+    if (!ne) return;
+    ptx::bulk_prefetch_l2(kl + e0, ne * 8);
+    ptx::bulk_prefetch_l2(nslot + e0, ne * 2);
+    if (HAS_C) ptx::bulk_prefetch_l2(cc + e0, ne * 4);
+    if (HAS_ACT) ptx::bulk_prefetch_l2(act + e0, ne * 8);
+}
 
 template <bool HAS_C, bool HAS_ACT, bool GROUND>
 __global__ void __launch_bounds__(kHaloThreads, 6)
@@ -157,46 +171,42 @@ k_step_halo(const MassState *__restrict__ in, MassState *__restrict__ out, uint3
             const float2 *__restrict__ kl, const float *__restrict__ cc,
             const float2 *__restrict__ act, const uint16_t *__restrict__ own_slot,
             const uint32_t *__restrict__ ext_off, const uint32_t *__restrict__ ext_idx,
-            const uint16_t *__restrict__ ext_slot, uint32_t table_slots, StepConst c,
+            const uint16_t *__restrict__ ext_slot, uint32_t table_slots, uint32_t ahead, StepConst c,
             const long long *__restrict__ step_in, long long *__restrict__ step_out) {
-    extern __shared__ float2 tab[];
-    float2 *tA = tab, *tB = tab + table_slots, *tC = tab + 2 * table_slots;
+    extern __shared__ float4 tab4[];
+    float4 *tA = tab4;
+    float2 *tB = reinterpret_cast<float2 *>(tab4 + table_slots);
     const uint32_t b = blockIdx.x, tid = threadIdx.x;
     const uint32_t i = b * kHaloThreads + tid;
-    const uint32_t lane = tid & 31, sl = i >> 5;
+    const uint32_t lane = tid & 31, sl = i >> 5, w = tid >> 5;
+    const uint32_t n_slices = (n + 31) >> 5;
     long long step = 0;
     if (HAS_ACT) step = *step_in;
     if (b == 0 && tid == 0) *step_out = *step_in + 1;
     const bool valid = i < n;
 
+    if (lane == 0) {
+        if (b < ahead && sl < n_slices) prefetch_slice<HAS_C, HAS_ACT>(slice_off, sl, nslot, kl, cc, act);
+        const uint32_t sl_next = (b + ahead) * (kHaloThreads / 32) + w;
+        if (ahead && sl_next < n_slices) prefetch_slice<HAS_C, HAS_ACT>(slice_off, sl_next, nslot, kl, cc, act);
+    }
     uint32_t e0 = 0, width = 0;
+    float4 p = make_float4(0.f, 0.f, 0.f, 0.f), v = p;
     if (valid) {
         e0 = __ldg(slice_off + sl);
         width = (__ldg(slice_off + sl + 1) - e0) >> 5;
-        if (lane == 0 && width) {
-            const uint32_t ne = width * 32;
-            ptx::bulk_prefetch_l2(kl + e0, ne * 8);
-            ptx::bulk_prefetch_l2(nslot + e0, ne * 2);
-            if (HAS_C) ptx::bulk_prefetch_l2(cc + e0, ne * 4);
-            if (HAS_ACT) ptx::bulk_prefetch_l2(act + e0, ne * 8);
-        }
-    }
-    float4 p = make_float4(0.f, 0.f, 0.f, 0.f), v = p;
-    if (valid) {
         load_state(in + i, p, v);
         const uint32_t s = own_slot[i];
-        tA[s] = make_float2(p.x, p.y);
-        tB[s] = make_float2(p.z, v.x);
-        tC[s] = make_float2(v.y, v.z);
+        tA[s] = make_float4(p.x, p.y, p.z, v.x);
+        tB[s] = make_float2(v.y, v.z);
     }
     const uint32_t h0 = __ldg(ext_off + b), h1 = __ldg(ext_off + b + 1);
     for (uint32_t h = h0 + tid; h < h1; h += kHaloThreads) {
-        float4 q, w;
-        load_state(in + __ldg(ext_idx + h), q, w);
+        float4 q, ww;
+        load_state(in + __ldg(ext_idx + h), q, ww);
         const uint32_t s = __ldg(ext_slot + h);
-        tA[s] = make_float2(q.x, q.y);
-        tB[s] = make_float2(q.z, w.x);
-        tC[s] = make_float2(w.y, w.z);
+        tA[s] = make_float4(q.x, q.y, q.z, ww.x);
+        tB[s] = make_float2(ww.y, ww.z);
     }
     __syncthreads();
     if (!valid) return;
@@ -223,17 +233,15 @@ k_step_halo(const MassState *__restrict__ in, MassState *__restrict__ out, uint3
                 if (HAS_C) { nc0 = __ldcs(cc + e); nc1 = __ldcs(cc + e + 32); }
                 if (HAS_ACT) { ns0 = __ldcs(act + e); ns1 = __ldcs(act + e + 32); }
             }
-            const float2 qa0 = tA[j0], qb0 = tB[j0], qc0 = tC[j0];
-            const float2 qa1 = tA[j1], qb1 = tB[j1], qc1 = tC[j1];
+            const float4 qa0 = tA[j0], qa1 = tA[j1];
+            const float2 qb0 = tB[j0], qb1 = tB[j1];
             float L0 = a0.y, L1 = a1.y;
             if (HAS_ACT) {
                 L0 = a0.y * (1.f + s0.x * sinf(ph + s0.y));
                 L1 = a1.y * (1.f + s1.x * sinf(ph + s1.y));
             }
-            spring_force(p, v, make_float4(qa0.x, qa0.y, qb0.x, 0.f), make_float4(qb0.y, qc0.x, qc0.y, 0.f),
-                         a0.x, L0, c0, fx, fy, fz);
-            spring_force(p, v, make_float4(qa1.x, qa1.y, qb1.x, 0.f), make_float4(qb1.y, qc1.x, qc1.y, 0.f),
-                         a1.x, L1, c1, fx, fy, fz);
+            spring_force(p, v, qa0, make_float4(qa0.w, qb0.x, qb0.y, 0.f), a0.x, L0, c0, fx, fy, fz);
+            spring_force(p, v, qa1, make_float4(qa1.w, qb1.x, qb1.y, 0.f), a1.x, L1, c1, fx, fy, fz);
         }
     }
     integrate<GROUND>(p, v, fx, fy, fz, c, out + i);
@@ -621,7 +629,7 @@ cudaError_t launch_step_halo(const MassState *in, MassState *out, uint32_t n, co
                              long long *step_out, cudaStream_t stream) {
     const bool hc = v.c != nullptr, ha = v.act != nullptr, gr = c.ground != 0;
     const unsigned g = n ? (n + kHaloThreads - 1) / kHaloThreads : 1;
-    const size_t bytes = (size_t)3 * h.table_slots * sizeof(float2);
+    const size_t bytes = (size_t)h.table_slots * (sizeof(float4) + sizeof(float2));
 #define TITAN_HALO(HC, HA, GR)                                                                   \
     do {                                                                                         \
         auto kern = k_step_halo<HC, HA, GR>;                                                     \
@@ -636,7 +644,7 @@ cudaError_t launch_step_halo(const MassState *in, MassState *out, uint32_t n, co
         }                                                                                        \
         kern<<<g, kHaloThreads, bytes, stream>>>(in, out, n, v.slice_off, h.nslot, v.kl, v.c, v.act, \
                                                  h.own_slot, h.ext_off, h.ext_idx, h.ext_slot,   \
-                                                 h.table_slots, c, step_in, step_out);           \
+                                                 h.table_slots, h.ahead, c, step_in, step_out);  \
     } while (0)
     if (hc) {
         if (ha) { if (gr) TITAN_HALO(true, true, true); else TITAN_HALO(true, true, false); }

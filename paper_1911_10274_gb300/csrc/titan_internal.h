@@ -58,6 +58,7 @@ struct HaloView {
     const uint32_t *ext_idx;     // external entries: device index
     const uint16_t *ext_slot;    //                   and slot
     uint32_t table_slots;        // slots per block table (shared memory = 24 B each)
+    uint32_t ahead;              // blocks between a CTA and the block whose stream it prefetches
 };
 
 struct AtomicView {
