@@ -498,10 +498,7 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
         CREATE_CK(upload(sim->d_slice_off, sim->sell.slice_off, sim->stream));
         CREATE_CK(upload(sim->d_kl, kl, sim->stream));
         if (sim->csr_kernel == 4 || sim->csr_kernel == 5) {
-            // prefetch about half a wave ahead: a wave is (SMs x 6) resident CTAs
-            int sms = 0;
-            CREATE_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
-            sim->halo_ahead = (uint32_t)std::max(1, sms * 6 / 2);
+            sim->halo_ahead = 0;    // each warp prefetches its own slice
             const titan::HaloHost &h = sim->halo;
             CREATE_CK(dev_alloc(sim, &sim->d_nslot, E));
             CREATE_CK(dev_alloc(sim, &sim->d_own_slot, nd));

@@ -147,9 +147,9 @@ k_step_sell_pf(const MassState *__restrict__ in, MassState *__restrict__ out, ui
 // fetched from global memory once per block instead of once per half-edge, and
 // the slots are coloured so that a quarter-warp's 16-byte and a half-warp's
 // 8-byte table reads fall in distinct banks.  The half-edge stream (u16 slot
-// + {k, L0}, 10 bytes) is brought into L2 by TMA bulk prefetches issued
-// `ahead` blocks in advance (the first `ahead` blocks prefetch their own), so
-// the loop's stream loads hit L2 while DRAM streams the blocks to come.
+// + {k, L0}, 10 bytes) is brought into L2 by TMA bulk prefetches: of the
+// warp's own slice (ahead = 0, the default: prefetching further ahead was
+// measured to lose lines to L2 eviction), or `ahead` blocks in advance.
 constexpr int kHaloThreads = 256;
 
 template <bool HAS_C, bool HAS_ACT>
@@ -186,7 +186,9 @@ k_step_halo(const MassState *__restrict__ in, MassState *__restrict__ out, uint3
     const bool valid = i < n;
 
     if (lane == 0) {
-        if (b < ahead && sl < n_slices) prefetch_slice<HAS_C, HAS_ACT>(slice_off, sl, nslot, kl, cc, act);
+        if (b < ahead || ahead == 0) {
+            if (sl < n_slices) prefetch_slice<HAS_C, HAS_ACT>(slice_off, sl, nslot, kl, cc, act);
+        }
         const uint32_t sl_next = (b + ahead) * (kHaloThreads / 32) + w;
         if (ahead && sl_next < n_slices) prefetch_slice<HAS_C, HAS_ACT>(slice_off, sl_next, nslot, kl, cc, act);
     }
