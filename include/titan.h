@@ -214,6 +214,68 @@ titan_status titan_step_atomic_noalloc(uint32_t n_masses, const float *pos_dev, 
  * NULL is a no-op.  Returns the status of that final wait. */
 titan_status titan_destroy(titan_sim *sim);
 
+/* ------------------------------------------------------------------ batches
+ * Many independent systems (robots) advanced together: the paper's parallel
+ * robots and agents (Sec. I; Sec. V-B, 100 worms simulated at once).  Each
+ * system is owned by one thread-block cluster whose shared memory holds its
+ * state and springs for a whole rollout; all clusters of one size run in one
+ * persistent launch, and the launches of a rollout form one CUDA graph.
+ * Systems keep their own mass order; masses of different systems never
+ * interact. */
+typedef struct titan_batch titan_batch;
+
+/* Sinusoidal actuation of one system's springs (Sec. V-B):
+ * rest(t) = L0 (1 + amp[s] sin(2 pi freq_hz t + phase[s])); amp NULL: none. */
+typedef struct {
+    const double *amp;
+    const double *phase;
+    double freq_hz;
+} titan_actuation;
+
+/* Builds a batch of n_systems systems (masses[r], springs[r], act[r]; act
+ * may be NULL).  params supplies dt, gravity, ground, ground_k, mu, damping
+ * (uniform: per-spring damping returns TITAN_E_UNSUPPORTED), device, stream
+ * and spin_limit.  Every system must fit a cluster of 8 CTAs (about 30,000
+ * springs); all actuated systems share one frequency.  Errors:
+ * TITAN_E_INVALID, TITAN_E_UNSUPPORTED, TITAN_E_OOM, TITAN_E_CUDA. */
+titan_status titan_batch_create(uint32_t n_systems, const titan_masses *masses,
+                                const titan_springs *springs, const titan_actuation *act,
+                                const titan_params *params, titan_batch **out);
+
+/* Enqueues a rollout of n_steps (< 2^32) steps of every system and returns
+ * without waiting.  The actuation clock continues across rollouts. */
+titan_status titan_batch_rollout(titan_batch *b, uint64_t n_steps);
+
+/* Times each launch group with 128, 256 and 512 threads per CTA over a
+ * probe_steps rollout (0: 50) and keeps the fastest.  The state is unchanged. */
+titan_status titan_batch_autotune(titan_batch *b, uint32_t probe_steps);
+
+/* Restores every system's initial state and the step counter to 0. */
+titan_status titan_batch_reset(titan_batch *b);
+
+/* Waits for the batch's work; TITAN_E_TIMEOUT if a bounded wait expired. */
+titan_status titan_batch_sync(titan_batch *b);
+
+/* Copies system `system`'s current positions and velocities ([n][3] float,
+ * its own mass order; either may be NULL) to host memory.  Waits. */
+titan_status titan_batch_read(titan_batch *b, uint32_t system, float *pos, float *vel);
+
+/* Writes every system's centroid ([n_systems][3] float, host) after the
+ * enqueued work.  Waits. */
+titan_status titan_batch_centroids(titan_batch *b, float *out);
+
+/* Number of launch groups (one per cluster size) and, per group, its cluster
+ * size, threads per CTA and CTA count. */
+uint32_t titan_batch_groups(const titan_batch *b);
+titan_status titan_batch_info(const titan_batch *b, uint32_t group, uint32_t *cluster,
+                              uint32_t *threads, uint32_t *ctas);
+
+/* Text of the last error on this batch ("" if none). */
+const char *titan_batch_last_error(const titan_batch *b);
+
+/* Waits and frees the batch.  NULL is a no-op. */
+titan_status titan_batch_destroy(titan_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

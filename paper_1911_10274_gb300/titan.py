@@ -51,6 +51,10 @@ class titan_params(C.Structure):
                 ("reserved", C.c_int32 * 6)]
 
 
+class titan_actuation(C.Structure):
+    _fields_ = [("amp", C.c_void_p), ("phase", C.c_void_p), ("freq_hz", C.c_double)]
+
+
 _lib = None
 _lock = threading.Lock()
 _P = C.c_void_p
@@ -81,6 +85,19 @@ def load(path: Optional[str] = None):
                 "titan_destroy": (S, [_P]),
                 "titan_step_atomic_noalloc": (S, [u32, _P, _P, _P, u32, _P, _P, _P, f32,
                                                   C.POINTER(titan_params), _P, _P, _P]),
+                "titan_batch_create": (S, [u32, C.POINTER(titan_masses), C.POINTER(titan_springs),
+                                           C.POINTER(titan_actuation), C.POINTER(titan_params),
+                                           C.POINTER(_P)]),
+                "titan_batch_rollout": (S, [_P, u64]),
+                "titan_batch_autotune": (S, [_P, u32]),
+                "titan_batch_reset": (S, [_P]),
+                "titan_batch_sync": (S, [_P]),
+                "titan_batch_read": (S, [_P, u32, _P, _P]),
+                "titan_batch_centroids": (S, [_P, _P]),
+                "titan_batch_groups": (u32, [_P]),
+                "titan_batch_info": (S, [_P, u32, C.POINTER(u32), C.POINTER(u32), C.POINTER(u32)]),
+                "titan_batch_last_error": (C.c_char_p, [_P]),
+                "titan_batch_destroy": (S, [_P]),
             }
             for name, (res, args) in sigs.items():
                 fn = getattr(lib, name)
@@ -182,6 +199,115 @@ def titan_step_atomic_noalloc(n_masses: int, pos_dev, vel_dev, inv_mass_dev, n_s
         n_masses, _ptr(pos_dev), _ptr(vel_dev), _ptr(inv_mass_dev), n_springs, _ptr(ends_dev),
         _ptr(k_dev), _ptr(rest_dev), float(damping), C.byref(params), _ptr(pos_out_dev),
         _ptr(vel_out_dev), stream))
+
+
+def _bcheck(status: int, batch=None):
+    if status != TITAN_OK:
+        lib = load()
+        msg = (lib.titan_batch_last_error(batch) if batch else lib.titan_last_error(None))
+        raise TitanError(status, msg.decode(errors="replace"))
+
+
+def _params_from(system, device=0, stream=None):
+    p = titan_default_params()
+    p.dt = float(system.dt)
+    p.gravity = (C.c_double * 3)(*[float(g) for g in system.gravity])
+    p.ground = 1 if system.ground else 0
+    p.ground_k = float(system.ground_k)
+    p.mu = float(system.mu)
+    p.device = device
+    p.stream = stream
+    return p
+
+
+class Batch:
+    """Many independent systems advanced together (titan_batch_* calls).
+
+    All systems share dt, gravity, ground parameters and one uniform damping
+    (taken from the first system) and one actuation frequency."""
+
+    def __init__(self, systems, device: int = 0, stream: Optional[int] = None):
+        load()
+        self.n = len(systems)
+        self.sizes = [int(sy.pos.shape[0]) for sy in systems]
+        keep, ms, ss, acts = [], [], [], []
+        damping = float(systems[0].damping[0]) if systems and len(systems[0].damping) else 0.0
+        for sy in systems:
+            d = dict(pos=np.ascontiguousarray(sy.pos, np.float64), vel=np.ascontiguousarray(sy.vel, np.float64),
+                     mass=np.ascontiguousarray(sy.mass, np.float64),
+                     fixed=np.ascontiguousarray(sy.fixed, np.uint8),
+                     ends=np.ascontiguousarray(sy.ends, np.uint32), k=np.ascontiguousarray(sy.k, np.float64),
+                     rest=np.ascontiguousarray(sy.rest, np.float64))
+            if len(sy.damping) and not np.all(sy.damping == damping):
+                raise ValueError("a batch uses one uniform damping")
+            ms.append(titan_masses(sy.n_masses, _ptr(d["pos"]), _ptr(d["vel"]), _ptr(d["mass"]), _ptr(d["fixed"])))
+            ss.append(titan_springs(sy.n_springs, _ptr(d["ends"]), _ptr(d["k"]), _ptr(d["rest"]), None))
+            if getattr(sy, "act_amp", None) is not None:
+                d["amp"] = np.ascontiguousarray(sy.act_amp, np.float64)
+                d["phase"] = np.ascontiguousarray(sy.act_phase, np.float64)
+                acts.append(titan_actuation(_ptr(d["amp"]), _ptr(d["phase"]), float(sy.act_freq)))
+            else:
+                acts.append(titan_actuation(None, None, 0.0))
+            keep.append(d)
+        p = _params_from(systems[0], device, stream)
+        p.damping = damping
+        M = (titan_masses * max(1, self.n))(*ms)
+        S = (titan_springs * max(1, self.n))(*ss)
+        A = (titan_actuation * max(1, self.n))(*acts)
+        out = _P()
+        _bcheck(load().titan_batch_create(self.n, M, S, A, C.byref(p), C.byref(out)))
+        self.handle = out.value
+
+    def rollout(self, n_steps: int) -> "Batch":
+        _bcheck(load().titan_batch_rollout(self.handle, n_steps), self.handle)
+        return self
+
+    def autotune(self, probe_steps: int = 50) -> None:
+        _bcheck(load().titan_batch_autotune(self.handle, probe_steps), self.handle)
+
+    def reset(self) -> None:
+        _bcheck(load().titan_batch_reset(self.handle), self.handle)
+
+    def sync(self) -> None:
+        _bcheck(load().titan_batch_sync(self.handle), self.handle)
+
+    def read(self, r: int):
+        n = self.sizes[r]
+        pos = np.empty((n, 3), np.float32)
+        vel = np.empty((n, 3), np.float32)
+        _bcheck(load().titan_batch_read(self.handle, r, _ptr(pos), _ptr(vel)), self.handle)
+        return pos, vel
+
+    def centroids(self) -> np.ndarray:
+        out = np.empty((self.n, 3), np.float32)
+        _bcheck(load().titan_batch_centroids(self.handle, _ptr(out)), self.handle)
+        return out
+
+    def groups(self):
+        lib = load()
+        res = []
+        for g in range(lib.titan_batch_groups(self.handle)):
+            cl, th, ct = C.c_uint32(), C.c_uint32(), C.c_uint32()
+            _bcheck(lib.titan_batch_info(self.handle, g, C.byref(cl), C.byref(th), C.byref(ct)), self.handle)
+            res.append(dict(cluster=cl.value, threads=th.value, ctas=ct.value))
+        return res
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            _bcheck(load().titan_batch_destroy(self.handle))
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # --------------------------------------------------------------------------- convenience

@@ -100,3 +100,18 @@ def test_null_handle_calls_are_rejected():
     assert lib.titan_destroy(None) == T.TITAN_OK
     assert lib.titan_steps(None) == 0
     assert isinstance(T.titan_last_error(None), str)
+
+
+def test_batch_create_validates_before_touching_the_device():
+    sy = inputs.actuated_box(3, 3, 3, np.random.default_rng(0))
+    bad = sy.copy()
+    bad.ends = bad.ends.copy()
+    bad.ends[0, 1] = 500
+    with pytest.raises(T.TitanError) as ei:
+        T.Batch([sy, bad])
+    assert ei.value.status == T.TITAN_E_INVALID and "system 1" in str(ei.value)
+    other = sy.copy()
+    other.act_freq = 3.0
+    with pytest.raises(T.TitanError) as ei:
+        T.Batch([sy, other])
+    assert ei.value.status == T.TITAN_E_UNSUPPORTED
