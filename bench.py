@@ -202,6 +202,51 @@ def config_for(args, system):
     return cfg
 
 
+def batched_leg(stream_handle, device, n_robots=4096, steps=2000, plain_robots=32, plain_steps=200):
+    """Batched actuated robots (a, b, c ~ U{3..12}, 30% of springs actuated,
+    ground contact): one rollout of `steps` steps for all robots in the
+    persistent cluster launches, against plain per-robot launches (one kernel
+    launch per robot per step) timed on a subset and expressed per rollout."""
+    import torch
+    from paper_1911_10274_gb300 import inputs
+    from paper_1911_10274_gb300 import titan as T
+    robots = inputs.robot_batch(n_robots, seed=0)
+    springs = sum(r.n_springs for r in robots)
+    with T.Batch(robots, device=device, stream=stream_handle) as b:
+        b.autotune(50)
+        times = []
+        for _ in range(3):
+            b.reset()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            b.rollout(steps)
+            b.sync()
+            times.append(time.perf_counter() - t0)
+        groups = b.groups()
+    t = min(times)
+    sims = [T.Sim(r, graph_chunk=-1, device=device) for r in robots[:plain_robots]]
+    for sm in sims:
+        sm.step(10)
+    for sm in sims:
+        sm.sync()
+    t0 = time.perf_counter()
+    for _ in range(plain_steps):
+        for sm in sims:
+            T.titan_step(sm.handle, 1)
+    for sm in sims:
+        sm.sync()
+    per_robot_step = (time.perf_counter() - t0) / (plain_steps * len(sims))
+    for sm in sims:
+        sm.close()
+    plain = 1.0 / (per_robot_step * steps)
+    return {"workload": f"{n_robots} actuated lattice robots, a,b,c ~ U{{3..12}}, {springs} springs, "
+                        f"{steps}-step rollouts, ground contact, dt=1e-4",
+            "rollouts_per_s": n_robots / t, "plain_rollouts_per_s": plain, "speedup": n_robots / t / plain,
+            "spring_updates_per_s": springs * steps / t, "rollout_s": t,
+            "plain": f"one launch per robot per step, {plain_robots} robots x {plain_steps} steps",
+            "launch_groups": groups}
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_env()
@@ -277,6 +322,8 @@ def run_ours(args):
         "clocks": clocks.summary(),
     }
     sim.close()
+    if not args.no_batched:
+        line["batched"] = batched_leg(stream.cuda_stream, local)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_leg(system)
     if rank == 0:
@@ -295,6 +342,7 @@ def main():
     ap.add_argument("--accumulate", choices=["csr", "atomic"], default="csr")
     ap.add_argument("--workload", default="lattice1m")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-robots leg")
     ap.add_argument("--kernel-variant", type=int, default=0, help="CSR kernel: 0 auto, 1 direct loads, 2 TMA-staged, 3 bulk L2 prefetch, 4 halo, 5 halo+TMA")
     args = ap.parse_args()
     if args.warmup < 3:
