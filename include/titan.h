@@ -168,6 +168,28 @@ titan_status titan_set_state(titan_sim *sim, const double *pos, const double *ve
  * the host.  Errors: TITAN_E_CUDA. */
 titan_status titan_read_state_dev(titan_sim *sim, float *pos_dev, float *vel_dev, void *stream);
 
+/* Sets the step counter (the simulated time is steps * dt; the actuation
+ * clock reads it) for the steps enqueued from now on.  Errors: TITAN_E_CUDA. */
+titan_status titan_set_step(titan_sim *sim, uint64_t step);
+
+/* Reverse-mode derivative of a rollout (gradient-based design of actuated
+ * robots; the paper's Sec. III-F shape and actuation optimisation done with
+ * gradients).  From the current state and step, runs n_steps ordinary steps
+ * (the simulation advances as titan_step would), keeping the state every
+ * `every` steps (0: 50), then recomputes each segment from its checkpoint and
+ * reverses it, accumulating
+ *   grad_amp_dev[s]   = dJ / dA_s,    grad_phase_dev[s] = dJ / dphi_s
+ * for J = sum_i seed_pos[i] . x_T[i] + seed_vel[i] . v_T[i] (x_T, v_T: the
+ * state after the rollout).  All arrays are DEVICE float arrays in caller
+ * order: seed_pos_dev and seed_vel_dev [n][3] (seed_vel_dev may be NULL),
+ * gradients [n_springs] (overwritten).  Requires CSR accumulation and
+ * actuation set with titan_set_actuation.  At the kinks of contact and
+ * friction the derivative of the branch the forward step took is used.
+ * Enqueued on the simulation stream.  Errors: TITAN_E_INVALID,
+ * TITAN_E_UNSUPPORTED (atomic accumulation), TITAN_E_OOM, TITAN_E_CUDA. */
+titan_status titan_adjoint(titan_sim *sim, uint64_t n_steps, uint32_t every, const float *seed_pos_dev,
+                           const float *seed_vel_dev, float *grad_amp_dev, float *grad_phase_dev);
+
 /* Blocks until every enqueued step and copy has finished (the paper's
  * waitForEvent, Sec. III-D).  Errors: TITAN_E_CUDA, TITAN_E_TIMEOUT. */
 titan_status titan_sync(titan_sim *sim);

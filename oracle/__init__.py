@@ -62,6 +62,9 @@ def _bind(lib):
     lib.titan_oracle_mass_update.restype = None
     lib.titan_oracle_rest_length.argtypes = [P, C.c_int64, C.c_double]
     lib.titan_oracle_rest_length.restype = C.c_double
+    lib.titan_oracle_adjoint.argtypes = [P, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_void_p,
+                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.titan_oracle_adjoint.restype = C.c_int
     return lib
 
 
@@ -163,3 +166,32 @@ def rest_length(sys, s: int, t: float, act_mode=None, worm=None) -> float:
     lib = _load()
     b = _Bound(sys, act_mode, worm)
     return lib.titan_oracle_rest_length(C.byref(b.struct), int(s), float(t))
+
+
+def adjoint(sys, n_steps: int, seed_x, seed_v=None, step0: int = 0, pos=None, vel=None):
+    """Reverse-mode gradient of J = <seed_x, x_T> + <seed_v, v_T> with respect
+    to the actuation amplitudes and phases of every spring.
+    Returns (grad_amp, grad_phase, x_T, v_T)."""
+    lib = _load()
+    b = _Bound(sys, 1, None)
+    x0 = _f64(sys.pos if pos is None else pos)
+    v0 = _f64(sys.vel if vel is None else vel)
+    sx = _f64(seed_x)
+    sv = None if seed_v is None else _f64(seed_v)
+    ga = np.zeros(sys.n_springs)
+    gb = np.zeros(sys.n_springs)
+    xT = np.empty_like(x0)
+    vT = np.empty_like(v0)
+    rc = lib.titan_oracle_adjoint(C.byref(b.struct), x0.ctypes.data, v0.ctypes.data, int(step0), int(n_steps),
+                                  sx.ctypes.data, None if sv is None else sv.ctypes.data,
+                                  ga.ctypes.data, gb.ctypes.data, xT.ctypes.data, vT.ctypes.data)
+    if rc != 0:
+        raise RuntimeError("oracle adjoint failed (needs sinusoidal actuation)")
+    return ga, gb, xT, vT
+
+
+def centroid_x_seed(n: int) -> np.ndarray:
+    """Seed for J = mean_i x_T[i, 0] (the centroid's x position)."""
+    s = np.zeros((n, 3))
+    s[:, 0] = 1.0 / n
+    return s

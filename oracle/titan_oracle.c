@@ -159,3 +159,150 @@ void titan_oracle_run(const oracle_system *sys, double *x, double *v, int64_t st
         titan_oracle_mass_update(sys, x, v, F);
     }
 }
+
+/* ------------------------------------------------------------------ adjoint
+ * Reverse-mode derivative of one rollout, used to pin the GPU adjoint.
+ * Objective J = sum_i seed_x[i] . x_T[i] + seed_v[i] . v_T[i] after n_steps
+ * steps from (x0, v0) at step index step0.  Outputs dJ/dA_s and dJ/dphi_s for
+ * the sinusoidal actuation (mode 1) of every spring.  The reverse sweep walks
+ * the time steps backwards; within a step it undoes the mass pass (mass by
+ * mass) and then the spring pass (spring by spring, in reverse input order).
+ * At the kinks (contact on/off, capped/uncapped friction, l = 0) it uses the
+ * branch the forward step took.  Every forward state is kept (no
+ * checkpointing: the oracle is for small systems).  Returns 0, or -1 if
+ * actuation is not mode 1 or memory runs out. */
+#include <stdlib.h>
+
+static void adjoint_mass_pass(const oracle_system *sys, const double *x, const double *v,
+                              const double *xb_out, const double *vb_out,
+                              double *xb, double *vb, double *Fb)
+{
+    const double dt = sys->dt;
+    for (int64_t i = 0; i < sys->n_masses; ++i) {
+        const double *xi = x + 3 * i, *vi = v + 3 * i;
+        double *xbi = xb + 3 * i, *vbi = vb + 3 * i, *Fbi = Fb + 3 * i;
+        if (sys->fixed && sys->fixed[i]) {
+            /* x' = x, v' = 0: only the position adjoint passes through */
+            for (int c = 0; c < 3; ++c) { xbi[c] = xb_out[3 * i + c]; vbi[c] = 0.0; Fbi[c] = 0.0; }
+            continue;
+        }
+        const double m = sys->mass[i];
+        double vtot[3], ab[3];
+        for (int c = 0; c < 3; ++c) {
+            /* x' = x + v' dt  ->  dJ/dv' gains dt dJ/dx'; v' = v + a dt */
+            vtot[c] = vb_out[3 * i + c] + dt * xb_out[3 * i + c];
+            xbi[c] = xb_out[3 * i + c];
+            vbi[c] = vtot[c];
+            ab[c] = dt * vtot[c];
+            Fbi[c] = ab[c] / m;          /* a = F / m + g + contact */
+        }
+        if (sys->ground && xi[2] < 0.0) {
+            const double kgm = sys->ground_k / m;      /* a_z += kg (-z) / m */
+            xbi[2] += -kgm * ab[2];
+            const double vt = sqrt(vi[0] * vi[0] + vi[1] * vi[1]);
+            if (vt > 0.0) {
+                const double w[2] = {vi[0] / vt, vi[1] / vt};
+                /* the forward step's branch: capped iff m vt / dt < mu Fn */
+                const double Fn = sys->ground_k * (-xi[2]);
+                const int capped = m * vt / dt < sys->mu * Fn;
+                const double fr = capped ? vt / dt : sys->mu * Fn / m;     /* |friction| / m */
+                /* a_t -= fr w */
+                const double frb = -(ab[0] * w[0] + ab[1] * w[1]);
+                const double wb[2] = {-fr * ab[0], -fr * ab[1]};
+                double vtb = 0.0;
+                if (!capped) xbi[2] += -(sys->mu * sys->ground_k / m) * frb;
+                else vtb += frb / dt;
+                const double wdot = wb[0] * w[0] + wb[1] * w[1];
+                for (int c = 0; c < 2; ++c) vbi[c] += (wb[c] - wdot * w[c]) / vt + vtb * w[c];
+            }
+        }
+    }
+}
+
+static void adjoint_spring_pass(const oracle_system *sys, const double *x, const double *v, int64_t step,
+                                const double *Fb, double *xb, double *vb, double *ga, double *gb)
+{
+    const double t = (double)step * sys->dt;
+    for (int64_t s = sys->n_springs - 1; s >= 0; --s) {
+        const int64_t i = sys->ends[2 * s + 0];
+        const int64_t j = sys->ends[2 * s + 1];
+        double d[3], dv[3];
+        for (int a = 0; a < 3; ++a) {
+            d[a] = x[3 * j + a] - x[3 * i + a];
+            dv[a] = v[3 * j + a] - v[3 * i + a];
+        }
+        const double len = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        if (len == 0.0) continue;
+        double u[3], g[3];
+        for (int a = 0; a < 3; ++a) {
+            u[a] = d[a] / len;
+            g[a] = Fb[3 * i + a] - Fb[3 * j + a];     /* F_i += f u, F_j -= f u */
+        }
+        const double L = titan_oracle_rest_length(sys, s, t);
+        const double rate = dv[0] * u[0] + dv[1] * u[1] + dv[2] * u[2];
+        const double f = sys->k[s] * (len - L) + sys->damping[s] * rate;
+        const double fb = g[0] * u[0] + g[1] * u[1] + g[2] * u[2];
+        double ub[3];
+        for (int a = 0; a < 3; ++a) ub[a] = f * g[a];
+        const double lenb = sys->k[s] * fb;
+        const double Lb = -sys->k[s] * fb;
+        const double rateb = sys->damping[s] * fb;
+        for (int a = 0; a < 3; ++a) {
+            vb[3 * j + a] += rateb * u[a];
+            vb[3 * i + a] -= rateb * u[a];
+            ub[a] += rateb * dv[a];
+        }
+        const double udot = ub[0] * u[0] + ub[1] * u[1] + ub[2] * u[2];
+        for (int a = 0; a < 3; ++a) {
+            const double db = (ub[a] - udot * u[a]) / len + lenb * u[a];
+            xb[3 * j + a] += db;
+            xb[3 * i + a] -= db;
+        }
+        /* L = L0 (1 + A sin(2 pi f t + phi)) */
+        const double th = 2.0 * kPi * sys->act_freq * t + sys->act_b[s];
+        ga[s] += Lb * sys->rest[s] * sin(th);
+        gb[s] += Lb * sys->rest[s] * sys->act_a[s] * cos(th);
+    }
+}
+
+int titan_oracle_adjoint(const oracle_system *sys, const double *x0, const double *v0, int64_t step0,
+                         int64_t n_steps, const double *seed_x, const double *seed_v,
+                         double *grad_a, double *grad_b, double *x_T, double *v_T)
+{
+    if (sys->act_mode != 1 || !sys->act_a) return -1;
+    const size_t n3 = 3 * (size_t)sys->n_masses;
+    double *X = (double *)malloc(sizeof(double) * n3 * (size_t)(n_steps + 1));
+    double *V = (double *)malloc(sizeof(double) * n3 * (size_t)(n_steps + 1));
+    double *F = (double *)malloc(sizeof(double) * n3);
+    double *xb = (double *)malloc(sizeof(double) * n3), *vb = (double *)malloc(sizeof(double) * n3);
+    double *xb2 = (double *)malloc(sizeof(double) * n3), *vb2 = (double *)malloc(sizeof(double) * n3);
+    if (!X || !V || !F || !xb || !vb || !xb2 || !vb2) {
+        free(X); free(V); free(F); free(xb); free(vb); free(xb2); free(vb2);
+        return -1;
+    }
+    memcpy(X, x0, sizeof(double) * n3);
+    memcpy(V, v0, sizeof(double) * n3);
+    for (int64_t n = 0; n < n_steps; ++n) {
+        memcpy(X + n3 * (n + 1), X + n3 * n, sizeof(double) * n3);
+        memcpy(V + n3 * (n + 1), V + n3 * n, sizeof(double) * n3);
+        titan_oracle_spring_forces(sys, X + n3 * (n + 1), V + n3 * (n + 1), step0 + n, F);
+        titan_oracle_mass_update(sys, X + n3 * (n + 1), V + n3 * (n + 1), F);
+    }
+    if (x_T) memcpy(x_T, X + n3 * n_steps, sizeof(double) * n3);
+    if (v_T) memcpy(v_T, V + n3 * n_steps, sizeof(double) * n3);
+    for (size_t k = 0; k < n3; ++k) {
+        xb[k] = seed_x ? seed_x[k] : 0.0;
+        vb[k] = seed_v ? seed_v[k] : 0.0;
+    }
+    memset(grad_a, 0, sizeof(double) * (size_t)sys->n_springs);
+    memset(grad_b, 0, sizeof(double) * (size_t)sys->n_springs);
+    for (int64_t n = n_steps - 1; n >= 0; --n) {
+        const double *x = X + n3 * n, *v = V + n3 * n;
+        adjoint_mass_pass(sys, x, v, xb, vb, xb2, vb2, F);
+        adjoint_spring_pass(sys, x, v, step0 + n, F, xb2, vb2, grad_a, grad_b);
+        double *tx = xb; xb = xb2; xb2 = tx;
+        double *tv = vb; vb = vb2; vb2 = tv;
+    }
+    free(X); free(V); free(F); free(xb); free(vb); free(xb2); free(vb2);
+    return 0;
+}

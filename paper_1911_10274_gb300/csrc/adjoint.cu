@@ -1,0 +1,284 @@
+// adjoint.cu -- reverse-mode derivative of a rollout with respect to the
+// actuation amplitudes and phases (gradient-based design of actuated robots).
+//
+// Forward: the ordinary step (Titan Sec. III-B, Eq. 1; Sec. III-A contact,
+// friction and constraints) with L = L0 (1 + A sin(2 pi f t + phi)).  The
+// rollout runs forward once, keeping the state every `every` steps
+// (checkpoints); then, segment by segment from the last, the segment's states
+// are recomputed from its checkpoint and the step is reversed one step at a
+// time.  Reversing a step takes two kernels:
+//   k_adj_mass   - per mass: the adjoint of x' = x + v' dt, v' = v + a dt and
+//                  a = F/m + g + contact/friction (the branch the forward step
+//                  took at each kink), giving dJ/dF and the direct terms of
+//                  dJ/dx, dJ/dv;
+//   k_adj_spring - per mass, gathering its SELL row in the forward's fixed
+//                  order: each spring's adjoint seen from this end (both ends
+//                  compute the same spring scalars), added to this mass only;
+//                  the half-edge of the spring's first end also adds dJ/dA and
+//                  dJ/dphi to the spring's gradient (one owner: no atomics,
+//                  a fixed summation order).
+#include <math.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "physics.cuh"
+#include "sim_internal.h"
+
+namespace {
+
+constexpr int kT = 256;
+constexpr uint32_t kOwner = 0x80000000u;
+constexpr uint32_t kNoSpring = 0xffffffffu;
+
+template <bool GROUND>
+__global__ void __launch_bounds__(kT)
+k_adj_mass(const MassState *__restrict__ X, const float4 *__restrict__ xbo, const float4 *__restrict__ vbo,
+           float4 *__restrict__ xb, float4 *__restrict__ vb, float4 *__restrict__ Fb, uint32_t n,
+           titan::StepConst c) {
+    const uint32_t i = blockIdx.x * kT + threadIdx.x;
+    if (i >= n) return;
+    const float4 p = X[i].p, v = X[i].v;
+    const float4 xo = xbo[i], vo = vbo[i];
+    const float im = p.w;
+    if (im == 0.f) {                       // fixed: x' = x, v' = 0
+        xb[i] = make_float4(xo.x, xo.y, xo.z, 0.f);
+        vb[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        Fb[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
+    const float dt = c.dt;
+    const float vtx = vo.x + dt * xo.x, vty = vo.y + dt * xo.y, vtz = vo.z + dt * xo.z;
+    float4 x_b = make_float4(xo.x, xo.y, xo.z, 0.f);
+    float4 v_b = make_float4(vtx, vty, vtz, 0.f);
+    const float abx = dt * vtx, aby = dt * vty, abz = dt * vtz;
+    Fb[i] = make_float4(abx * im, aby * im, abz * im, 0.f);
+    if (GROUND && p.z < 0.f) {
+        x_b.z += -c.ground_k * im * abz;                   // a_z += kg (-z) / m
+        const float vt = sqrtf(v.x * v.x + v.y * v.y);
+        if (vt > 0.f) {
+            const float an = c.ground_k * (-p.z) * im;
+            const bool capped = vt / c.dt < c.mu * an;      // the forward's fminf choice
+            const float fr = capped ? vt / c.dt : c.mu * an;
+            const float wx = v.x / vt, wy = v.y / vt;
+            const float frb = -(abx * wx + aby * wy);      // a_t -= fr w
+            const float wbx = -fr * abx, wby = -fr * aby;
+            float vtb = 0.f;
+            if (!capped) x_b.z += -c.mu * c.ground_k * im * frb;
+            else vtb = frb / c.dt;
+            const float wdot = wbx * wx + wby * wy;
+            v_b.x += (wbx - wdot * wx) / vt + vtb * wx;
+            v_b.y += (wby - wdot * wy) / vt + vtb * wy;
+        }
+    }
+    xb[i] = x_b;
+    vb[i] = v_b;
+}
+
+template <bool HAS_C>
+__global__ void __launch_bounds__(kT)
+k_adj_spring(const MassState *__restrict__ X, const float4 *__restrict__ Fb, float4 *__restrict__ xb,
+             float4 *__restrict__ vb, uint32_t n, const uint32_t *__restrict__ slice_off,
+             const uint32_t *__restrict__ nbr, const uint32_t *__restrict__ spring,
+             const float2 *__restrict__ kl, const float2 *__restrict__ act, const float *__restrict__ cc,
+             titan::StepConst c, long long step, float *__restrict__ grad_amp, float *__restrict__ grad_phase) {
+    const uint32_t i = blockIdx.x * kT + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t sl = i >> 5, lane = i & 31;
+    const uint32_t e0 = slice_off[sl];
+    const uint32_t width = (slice_off[sl + 1] - e0) >> 5;
+    const float4 p = X[i].p, v = X[i].v;
+    const float4 Fi = Fb[i];
+    float4 x_b = xb[i], v_b = vb[i];
+    const float ph = titan::clock_phase(c, step);
+    for (uint32_t t = 0; t < width; ++t) {
+        const uint32_t e = e0 + 32 * t + lane;
+        const uint32_t spr = spring[e];
+        if (spr == kNoSpring) continue;                   // padding entry
+        const uint32_t j = nbr[e];
+        const float4 q = X[j].p, w = X[j].v;
+        const float dx = q.x - p.x, dy = q.y - p.y, dz = q.z - p.z;
+        const float l2 = dx * dx + dy * dy + dz * dz;
+        if (!(l2 > 0.f)) continue;                          // zero length: no force
+        const float inv = rsqrtf(l2);
+        const float l = l2 * inv;
+        const float ux = dx * inv, uy = dy * inv, uz = dz * inv;
+        const float2 a = kl[e], s = act[e];
+        const float k = a.x;
+        float sn, cs;
+        sincosf(ph + s.y, &sn, &cs);
+        const float L = a.y * (1.f + s.x * sn);
+        const float cd = HAS_C ? cc[e] : c.c_uniform;
+        const float dvx = w.x - v.x, dvy = w.y - v.y, dvz = w.z - v.z;
+        const float rate = dvx * ux + dvy * uy + dvz * uz;
+        const float f = k * (l - L) + cd * rate;
+        const float4 Fj = Fb[j];
+        const float gx = Fi.x - Fj.x, gy = Fi.y - Fj.y, gz = Fi.z - Fj.z;
+        const float fb = gx * ux + gy * uy + gz * uz;
+        const float lb = k * fb, Lb = -k * fb, rb = cd * fb;
+        float ubx = f * gx + rb * dvx, uby = f * gy + rb * dvy, ubz = f * gz + rb * dvz;
+        v_b.x -= rb * ux; v_b.y -= rb * uy; v_b.z -= rb * uz;
+        const float udot = ubx * ux + uby * uy + ubz * uz;
+        x_b.x -= (ubx - udot * ux) * inv + lb * ux;
+        x_b.y -= (uby - udot * uy) * inv + lb * uy;
+        x_b.z -= (ubz - udot * uz) * inv + lb * uz;
+        if (spr & kOwner) {
+            const uint32_t sid = spr & ~kOwner;
+            grad_amp[sid] += Lb * a.y * sn;
+            grad_phase[sid] += Lb * a.y * s.x * cs;
+        }
+    }
+    xb[i] = x_b;
+    vb[i] = v_b;
+}
+
+__global__ void k_adj_seed(const float *__restrict__ seed_pos, const float *__restrict__ seed_vel,
+                           const uint32_t *__restrict__ dev_of_caller, uint32_t n, float4 *__restrict__ xb,
+                           float4 *__restrict__ vb) {
+    const uint32_t i = blockIdx.x * kT + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t d = dev_of_caller[i];
+    xb[d] = make_float4(seed_pos[3 * (size_t)i], seed_pos[3 * (size_t)i + 1], seed_pos[3 * (size_t)i + 2], 0.f);
+    if (seed_vel)
+        vb[d] = make_float4(seed_vel[3 * (size_t)i], seed_vel[3 * (size_t)i + 1], seed_vel[3 * (size_t)i + 2], 0.f);
+}
+
+titan_status afail(titan_sim *sim, titan_status st, const std::string &msg) {
+    sim->error = msg;
+    return st;
+}
+
+#define ADJ_CK(call)                                                                               \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) {                                                                   \
+            st_ = afail(sim, e_ == cudaErrorMemoryAllocation ? TITAN_E_OOM : TITAN_E_CUDA,         \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                        \
+            goto done;                                                                             \
+        }                                                                                          \
+    } while (0)
+
+}  // namespace
+
+extern "C" titan_status titan_adjoint(titan_sim *sim, uint64_t n_steps, uint32_t every,
+                                      const float *seed_pos_dev, const float *seed_vel_dev,
+                                      float *grad_amp_dev, float *grad_phase_dev) {
+    if (!sim) return TITAN_E_INVALID;
+    if (sim->busy.exchange(true)) return afail(sim, TITAN_E_BUSY, "another call on this handle is in progress");
+    titan_status st_ = TITAN_OK;
+    int prev = -1;
+    const uint32_t nd = sim->n_dev, S = sim->s;
+    const size_t state_bytes = (size_t)std::max(nd, 1u) * sizeof(MassState);
+    const size_t vec_bytes = (size_t)std::max(nd, 1u) * sizeof(float4);
+    cudaStream_t s = sim->stream;
+    MassState *ckpt = nullptr, *seg = nullptr;
+    float4 *xb[2] = {nullptr, nullptr}, *vb[2] = {nullptr, nullptr}, *Fb = nullptr;
+    long long *seg_steps = nullptr;
+    uint64_t n_seg = 0;
+    int cur = 0;
+    if (sim->accumulate != TITAN_ACCUM_CSR) { st_ = afail(sim, TITAN_E_UNSUPPORTED, "the adjoint needs the CSR (deterministic) accumulation"); goto out; }
+    if (!sim->has_act) { st_ = afail(sim, TITAN_E_INVALID, "the adjoint differentiates the actuation: call titan_set_actuation first"); goto out; }
+    if (!seed_pos_dev || (S && (!grad_amp_dev || !grad_phase_dev))) { st_ = afail(sim, TITAN_E_INVALID, "null seed or gradient array"); goto out; }
+    if (every == 0) every = 50;
+    cudaGetDevice(&prev);
+    if (cudaSetDevice(sim->device) != cudaSuccess) { st_ = afail(sim, TITAN_E_CUDA, "cannot select the device"); goto out; }
+    {
+        // per-entry neighbour and spring ownership for the reverse gather (built once)
+        if (!sim->d_adj_spring) {
+            std::vector<uint32_t> spr(sim->sell.entries, kNoSpring);
+            for (uint32_t e = 0; e < sim->sell.entries; ++e)
+                if (sim->sell.spring[e] != UINT32_MAX) spr[e] = sim->sell.spring[e];
+            for (uint32_t q = 0; q < S; ++q) spr[sim->sell.entry_of_end[2 * (size_t)q]] |= kOwner;
+            void *p1 = nullptr;
+            ADJ_CK(cudaMalloc(&p1, std::max<size_t>(spr.size(), 1) * 4));
+            sim->allocations.push_back(p1);
+            sim->d_adj_spring = static_cast<uint32_t *>(p1);
+            ADJ_CK(cudaMemcpy(sim->d_adj_spring, spr.data(), spr.size() * 4, cudaMemcpyHostToDevice));
+            if (!sim->d_nbr) {
+                void *p2 = nullptr;
+                ADJ_CK(cudaMalloc(&p2, std::max<size_t>(sim->sell.nbr.size(), 1) * 4));
+                sim->allocations.push_back(p2);
+                sim->d_nbr = static_cast<uint32_t *>(p2);
+                ADJ_CK(cudaMemcpy(sim->d_nbr, sim->sell.nbr.data(), sim->sell.nbr.size() * 4, cudaMemcpyHostToDevice));
+            }
+        }
+        n_seg = (n_steps + every - 1) / every;
+        const unsigned gm = (nd + kT - 1) / kT;
+        ADJ_CK(cudaMallocAsync((void **)&ckpt, state_bytes * (n_seg + 1), s));
+        ADJ_CK(cudaMallocAsync((void **)&seg, state_bytes * (every + 1), s));
+        for (int b = 0; b < 2; ++b) {
+            ADJ_CK(cudaMallocAsync((void **)&xb[b], vec_bytes, s));
+            ADJ_CK(cudaMallocAsync((void **)&vb[b], vec_bytes, s));
+        }
+        ADJ_CK(cudaMallocAsync((void **)&Fb, vec_bytes, s));
+        ADJ_CK(cudaMallocAsync((void **)&seg_steps, sizeof(long long) * (every + 1), s));
+        const uint64_t step0 = sim->steps;
+        // forward rollout through the ordinary step, keeping checkpoints
+        ADJ_CK(cudaMemcpyAsync(ckpt, sim->state[sim->cur], state_bytes, cudaMemcpyDeviceToDevice, s));
+        for (uint64_t g = 0; g < n_seg; ++g) {
+            const uint64_t len = std::min<uint64_t>(every, n_steps - g * every);
+            for (uint64_t k = 0; k < len; ++k) {
+                ADJ_CK(titan::enqueue_sim_step(sim, s, sim->cur));
+                sim->cur ^= 1;
+                ++sim->steps;
+            }
+            ADJ_CK(cudaMemcpyAsync(ckpt + (g + 1) * nd, sim->state[sim->cur], state_bytes, cudaMemcpyDeviceToDevice, s));
+        }
+        // seed dJ/dx_T, dJ/dv_T in device order; gradients start at zero
+        ADJ_CK(cudaMemsetAsync(xb[0], 0, vec_bytes, s));
+        ADJ_CK(cudaMemsetAsync(vb[0], 0, vec_bytes, s));
+        if (sim->n) {
+            k_adj_seed<<<(sim->n + kT - 1) / kT, kT, 0, s>>>(seed_pos_dev, seed_vel_dev, sim->d_dev_of_caller,
+                                                             sim->n, xb[0], vb[0]);
+            ADJ_CK(cudaGetLastError());
+        }
+        if (S) {
+            ADJ_CK(cudaMemsetAsync(grad_amp_dev, 0, (size_t)S * 4, s));
+            ADJ_CK(cudaMemsetAsync(grad_phase_dev, 0, (size_t)S * 4, s));
+        }
+        titan::SellView v{sim->d_slice_off, sim->d_nbr, sim->d_kl, sim->has_c ? sim->d_c : nullptr, sim->d_act, 1,
+                          sim->spin_limit, sim->d_err};
+        for (uint64_t g = n_seg; g-- > 0;) {
+            const uint64_t len = std::min<uint64_t>(every, n_steps - g * every);
+            const long long first = (long long)(step0 + g * every);
+            ADJ_CK(cudaMemcpyAsync(seg, ckpt + g * nd, state_bytes, cudaMemcpyDeviceToDevice, s));
+            ADJ_CK(cudaMemcpyAsync(seg_steps, &first, sizeof(long long), cudaMemcpyHostToDevice, s));
+            for (uint64_t k = 0; k < len; ++k)
+                ADJ_CK(titan::launch_step_sell(seg + k * nd, seg + (k + 1) * nd, nd, v, sim->c, seg_steps + k,
+                                               seg_steps + k + 1, s));
+            for (uint64_t k = len; k-- > 0;) {
+                const MassState *X = seg + k * nd;
+                if (sim->c.ground)
+                    k_adj_mass<true><<<gm, kT, 0, s>>>(X, xb[cur], vb[cur], xb[cur ^ 1], vb[cur ^ 1], Fb, nd, sim->c);
+                else
+                    k_adj_mass<false><<<gm, kT, 0, s>>>(X, xb[cur], vb[cur], xb[cur ^ 1], vb[cur ^ 1], Fb, nd, sim->c);
+                ADJ_CK(cudaGetLastError());
+                const long long stepk = first + (long long)k;
+                if (sim->has_c)
+                    k_adj_spring<true><<<gm, kT, 0, s>>>(X, Fb, xb[cur ^ 1], vb[cur ^ 1], nd, sim->d_slice_off, sim->d_nbr,
+                                                         sim->d_adj_spring, sim->d_kl, sim->d_act, sim->d_c, sim->c,
+                                                         stepk, grad_amp_dev, grad_phase_dev);
+                else
+                    k_adj_spring<false><<<gm, kT, 0, s>>>(X, Fb, xb[cur ^ 1], vb[cur ^ 1], nd, sim->d_slice_off, sim->d_nbr,
+                                                          sim->d_adj_spring, sim->d_kl, sim->d_act, sim->d_c, sim->c,
+                                                          stepk, grad_amp_dev, grad_phase_dev);
+                ADJ_CK(cudaGetLastError());
+                cur ^= 1;
+            }
+        }
+    }
+done:
+    if (ckpt) cudaFreeAsync(ckpt, s);
+    if (seg) cudaFreeAsync(seg, s);
+    for (int b = 0; b < 2; ++b) {
+        if (xb[b]) cudaFreeAsync(xb[b], s);
+        if (vb[b]) cudaFreeAsync(vb[b], s);
+    }
+    if (Fb) cudaFreeAsync(Fb, s);
+    if (seg_steps) cudaFreeAsync(seg_steps, s);
+    if (prev >= 0) cudaSetDevice(prev);
+out:
+    sim->busy.store(false);
+    return st_;
+}

@@ -17,17 +17,15 @@
 #include <vector>
 
 #include "layout.h"
+#include "sim_internal.h"
 #include "titan.h"
 #include "titan_internal.h"
 
-using titan::MassState;
 
 namespace {
 
 thread_local std::string g_thread_error = "";
 
-constexpr int kDefaultGraphChunk = 64;
-constexpr uint32_t kDefaultSpinLimit = 1u << 22;
 constexpr uint32_t kHaloMaxSlots = 4096;     // 96 KiB of shared memory per CTA
 constexpr size_t kHaloTmaMaxSmem = 112 * 1024;  // two CTAs per SM
 
@@ -53,66 +51,6 @@ namespace titan {
 void set_thread_error(const std::string &msg) { g_thread_error = msg; }
 }  // namespace titan
 
-struct titan_sim {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    cudaStream_t side = nullptr;       // snapshot device-to-host copies
-    cudaStream_t capture = nullptr;    // graph capture
-    uint32_t n = 0, s = 0;
-    uint32_t n_dev = 0;                   // device slots (>= n: grid-tile order leaves holes)
-    bool grid_order = false;
-    int accumulate = TITAN_ACCUM_CSR;
-    titan::StepConst c{};
-    bool has_c = false, has_act = false;
-    double dt = 0;
-
-    std::vector<uint32_t> caller_of_dev, dev_of_caller;
-    std::vector<float> inv_mass;          // caller order
-    std::vector<float> k, rest, damp;     // caller spring order
-    std::vector<float> act_amp, act_phase;
-    titan::SellHost sell;
-    titan::HaloHost halo;
-    titan::RecordsHost rec;
-    int csr_kernel = 0;                   // resolved: 1 direct, 2 smem-staged, 3 bulk-prefetch, 4 halo, 5 halo+TMA
-    uint32_t halo_w_max = 0;              // staged columns per slice (halo+TMA kernel)
-    uint32_t halo_ahead = 0;              // L2 prefetch distance in blocks (halo kernel)
-
-    MassState *state[2] = {nullptr, nullptr};
-    long long *steps_dev = nullptr;       // [2]
-    int cur = 0;
-    uint64_t steps = 0;
-    uint32_t *d_dev_of_caller = nullptr;
-
-    uint32_t *d_slice_off = nullptr, *d_nbr = nullptr;
-    uint16_t *d_nslot = nullptr, *d_own_slot = nullptr, *d_ext_slot = nullptr;
-    uint32_t *d_ext_off = nullptr, *d_ext_idx = nullptr;
-    float2 *d_kl = nullptr, *d_act = nullptr;
-    float *d_c = nullptr;
-
-    uint4 *d_rec = nullptr;
-    float *d_rc = nullptr;
-    float2 *d_ract = nullptr;
-    float4 *d_force = nullptr;
-
-    int graph_chunk = kDefaultGraphChunk;
-    int kernel_variant = 0;
-    uint32_t spin_limit = kDefaultSpinLimit;
-    int *d_err = nullptr;                 // device error flag (bounded waits)
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
-
-    // snapshots: slot = ticket & 1
-    float *snap_dev[2] = {nullptr, nullptr};     // [2][n][3] pos then vel, caller order
-    float *snap_host[2] = {nullptr, nullptr};    // pinned, same layout
-    cudaEvent_t snap_ready[2] = {nullptr, nullptr};
-    cudaEvent_t snap_done[2] = {nullptr, nullptr};
-    double snap_t[2] = {0, 0};
-    uint64_t last_ticket = 0;
-
-    std::vector<void *> allocations;
-    std::string error;
-    std::atomic<bool> busy{false};
-};
 
 namespace {
 
@@ -310,6 +248,12 @@ titan_status check_device_error(titan_sim *sim) {
     }
     return TITAN_OK;
 }
+
+}  // namespace
+
+cudaError_t titan::enqueue_sim_step(titan_sim *sim, cudaStream_t st, int b) { return enqueue_step(sim, st, b); }
+
+namespace {
 
 cudaError_t ensure_graph(titan_sim *sim, int b) {
     if (sim->graph[b]) return cudaSuccess;
@@ -678,6 +622,17 @@ titan_status titan_read_state_dev(titan_sim *sim, float *pos_dev, float *vel_dev
         cudaEventDestroy(ev);
         TITAN_CK(sim, e);
     }
+    return TITAN_OK;
+}
+
+titan_status titan_set_step(titan_sim *sim, uint64_t step) {
+    if (!sim) return fail(nullptr, TITAN_E_INVALID, "sim is null");
+    BusyGuard bg(sim);
+    if (!bg.acquired) return fail(sim, TITAN_E_BUSY, "another call on this handle is in progress");
+    DeviceGuard dg(sim->device);
+    const long long v[2] = {(long long)step, (long long)step};
+    TITAN_CK(sim, cudaMemcpyAsync(sim->steps_dev, v, sizeof(v), cudaMemcpyHostToDevice, sim->stream));
+    sim->steps = step;
     return TITAN_OK;
 }
 

@@ -85,6 +85,8 @@ def load(path: Optional[str] = None):
                 "titan_destroy": (S, [_P]),
                 "titan_step_atomic_noalloc": (S, [u32, _P, _P, _P, u32, _P, _P, _P, f32,
                                                   C.POINTER(titan_params), _P, _P, _P]),
+                "titan_set_step": (S, [_P, u64]),
+                "titan_adjoint": (S, [_P, u64, u32, _P, _P, _P, _P]),
                 "titan_batch_create": (S, [u32, C.POINTER(titan_masses), C.POINTER(titan_springs),
                                            C.POINTER(titan_actuation), C.POINTER(titan_params),
                                            C.POINTER(_P)]),
@@ -172,6 +174,16 @@ def titan_set_state(sim: int, pos, vel=None) -> None:
 
 def titan_read_state_dev(sim: int, pos_dev=None, vel_dev=None, stream: Optional[int] = None) -> None:
     _check(load().titan_read_state_dev(sim, _ptr(pos_dev), _ptr(vel_dev), stream), sim)
+
+
+def titan_set_step(sim: int, step: int) -> None:
+    _check(load().titan_set_step(sim, step), sim)
+
+
+def titan_adjoint(sim: int, n_steps: int, every: int, seed_pos_dev, seed_vel_dev, grad_amp_dev,
+                  grad_phase_dev) -> None:
+    _check(load().titan_adjoint(sim, n_steps, every, _ptr(seed_pos_dev), _ptr(seed_vel_dev),
+                                _ptr(grad_amp_dev), _ptr(grad_phase_dev)), sim)
 
 
 def titan_sync(sim: int) -> None:
@@ -384,3 +396,103 @@ class Sim:
             self.close()
         except Exception:
             pass
+
+
+# --------------------------------------------------------------------------- differentiable rollouts
+
+def union_system(systems):
+    """Concatenates independent systems into one (block-diagonal) system.
+    Returns (system, mass_offsets, spring_offsets)."""
+    from .inputs import System
+    mo = np.cumsum([0] + [sy.n_masses for sy in systems])
+    so = np.cumsum([0] + [sy.n_springs for sy in systems])
+    cat = lambda f: np.concatenate([getattr(sy, f) for sy in systems])
+    ends = np.concatenate([sy.ends.astype(np.int64) + mo[r] for r, sy in enumerate(systems)]).astype(np.uint32)
+    s0 = systems[0]
+    amp = np.concatenate([sy.act_amp if sy.act_amp is not None else np.zeros(sy.n_springs) for sy in systems])
+    ph = np.concatenate([sy.act_phase if sy.act_phase is not None else np.zeros(sy.n_springs) for sy in systems])
+    u = System(pos=cat("pos"), vel=cat("vel"), mass=cat("mass"), fixed=cat("fixed"), ends=ends, k=cat("k"),
+               rest=cat("rest"), damping=cat("damping"), dt=s0.dt, gravity=s0.gravity, ground=s0.ground,
+               ground_k=s0.ground_k, mu=s0.mu, act_amp=amp, act_phase=ph, act_freq=s0.act_freq,
+               spacing=s0.spacing, name="union")
+    return u, mo, so
+
+
+class CentroidRollout:
+    """Centroid x-displacement of each of several robots after an n_steps
+    rollout, as a differentiable function of every spring's actuation
+    amplitude and phase (concatenated over the robots, robot by robot).
+
+    ``__call__(amp, phase)`` takes CUDA float32 tensors and returns a tensor
+    of per-robot displacements; gradients flow back through the library's
+    adjoint (titan_adjoint) with checkpoints every ``every`` steps."""
+
+    def __init__(self, robots, n_steps: int, every: int = 50, device: int = 0):
+        import torch
+        self.system, self.mass_off, self.spring_off = union_system(robots)
+        self.n_steps, self.every = int(n_steps), int(every)
+        self.n_robots = len(robots)
+        self.robot_of_mass = np.repeat(np.arange(self.n_robots), np.diff(self.mass_off))
+        self.counts = np.diff(self.mass_off).astype(np.float64)
+        self.freq = float(self.system.act_freq)
+        self.device = device
+        self.sim = Sim(self.system, device=device)
+        self.pos0 = np.ascontiguousarray(self.system.pos)
+        self.vel0 = np.ascontiguousarray(self.system.vel)
+        self.x0 = np.array([self.pos0[self.mass_off[r]:self.mass_off[r + 1], 0].mean()
+                            for r in range(self.n_robots)])
+        self._fn = None
+        self._torch = torch
+
+    def _prepare(self, amp, phase):
+        T_ = self._torch
+        titan_set_actuation(self.sim.handle, np.arange(self.system.n_springs, dtype=np.uint32),
+                            amp.detach().float().cpu().numpy(), phase.detach().float().cpu().numpy(), self.freq)
+        titan_set_step(self.sim.handle, 0)
+        self.sim.set_state(self.pos0, self.vel0)
+
+    def forward(self, amp, phase):
+        T_ = self._torch
+        self._prepare(amp, phase)
+        self.sim.step(self.n_steps)
+        pos = T_.empty((self.system.n_masses, 3), dtype=T_.float32, device=f"cuda:{self.device}")
+        titan_read_state_dev(self.sim.handle, pos, None, None)
+        self.sim.sync()
+        idx = T_.as_tensor(self.robot_of_mass, device=pos.device)
+        sums = T_.zeros(self.n_robots, dtype=T_.float64, device=pos.device).index_add_(0, idx, pos[:, 0].double())
+        cnt = T_.as_tensor(self.counts, device=pos.device)
+        return (sums / cnt - T_.as_tensor(self.x0, device=pos.device)).float()
+
+    def gradients(self, amp, phase, grad_out):
+        """dJ/dA and dJ/dphi for the objective sum_r grad_out[r] * J_r."""
+        T_ = self._torch
+        self._prepare(amp, phase)
+        dev = f"cuda:{self.device}"
+        w = (grad_out.detach().double().cpu().numpy() / self.counts)[self.robot_of_mass]
+        seed = T_.zeros((self.system.n_masses, 3), dtype=T_.float32, device=dev)
+        seed[:, 0] = T_.as_tensor(w, dtype=T_.float32, device=dev)
+        ga = T_.empty(self.system.n_springs, dtype=T_.float32, device=dev)
+        gp = T_.empty_like(ga)
+        titan_adjoint(self.sim.handle, self.n_steps, self.every, seed, None, ga, gp)
+        self.sim.sync()
+        return ga, gp
+
+    def __call__(self, amp, phase):
+        if self._fn is None:
+            torch = self._torch
+            engine = self
+
+            class _Fn(torch.autograd.Function):
+                @staticmethod
+                def forward(ctx, a, p):
+                    ctx.save_for_backward(a, p)
+                    return engine.forward(a, p)
+
+                @staticmethod
+                def backward(ctx, g):
+                    a, p = ctx.saved_tensors
+                    ga, gp = engine.gradients(a, p, g)
+                    return ga.to(a.dtype), gp.to(p.dtype)
+
+            self._fn = _Fn
+        return self._fn.apply(amp, phase)

@@ -1,0 +1,126 @@
+"""The GPU adjoint (titan_adjoint, FP32) against the FP64 oracle's adjoint and
+FP64 central finite differences (h = 1e-6) of the oracle's rollout.
+
+Tolerance: 1e-3 relative, normwise over the gradient vector (max absolute
+error <= 1e-3 x the largest gradient entry), the bar the benchmark target sets
+for the adjoint."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1911_10274_gb300 import inputs
+from paper_1911_10274_gb300 import titan as T
+
+pytestmark = pytest.mark.gpu
+REL = 1e-3
+
+
+def _robot(dims=(5, 3, 3), seed=4, ground=True, all_actuated=False):
+    rng = np.random.default_rng(seed)
+    sy = inputs.actuated_box(*dims, rng)
+    if all_actuated:
+        sy.act_amp = rng.uniform(0.02, 0.2, sy.n_springs)
+        sy.act_phase = rng.uniform(0, 2 * np.pi, sy.n_springs)
+    sy.ground = ground
+    if not ground:
+        sy.gravity = (0.0, 0.0, 0.0)
+    return sy
+
+
+def _gpu_adjoint(sy, steps, seed, every=50, **kw):
+    import torch
+    with T.Sim(sy, **kw) as sim:
+        s = torch.as_tensor(seed, dtype=torch.float32, device="cuda")
+        ga = torch.empty(sy.n_springs, dtype=torch.float32, device="cuda")
+        gp = torch.empty_like(ga)
+        T.titan_adjoint(sim.handle, steps, every, s, None, ga, gp)
+        sim.sync()
+        x, _, t = sim.snapshot()
+    return ga.cpu().numpy().astype(np.float64), gp.cpu().numpy().astype(np.float64), x, t
+
+
+def _close(g, ref):
+    scale = np.abs(ref).max()
+    assert scale > 0
+    err = np.abs(g - ref).max()
+    assert err <= REL * scale, f"max error {err:.3e} vs {REL} x {scale:.3e}"
+
+
+@pytest.mark.parametrize("ground", [False, True], ids=["floating", "on-ground"])
+def test_adjoint_matches_oracle_adjoint(ground):
+    sy = _robot(ground=ground, all_actuated=not ground)
+    steps = 200
+    rng = np.random.default_rng(0)
+    seed = rng.standard_normal((sy.n_masses, 3)) if not ground else oracle.centroid_x_seed(sy.n_masses)
+    ga, gp, xg, t = _gpu_adjoint(sy, steps, seed)
+    ra, rp, xo, _ = oracle.adjoint(sy, steps, seed)
+    _close(ga, ra)
+    _close(gp, rp)
+    assert np.abs(xg - xo).max() <= 1e-4 * sy.spacing      # the rollout itself advanced the state
+    assert t == pytest.approx(steps * sy.dt)
+
+
+def test_adjoint_matches_central_differences_on_the_benchmark_objective():
+    """Centroid x-displacement after 200 steps, checkpoint every 50, robot on
+    the ground: the GPU gradient against FP64 central differences."""
+    sy = _robot(dims=(6, 4, 3), seed=9)
+    steps = 200
+    seed = oracle.centroid_x_seed(sy.n_masses)
+    ga, gp, _, _ = _gpu_adjoint(sy, steps, seed, every=50)
+    ra, rp, _, _ = oracle.adjoint(sy, steps, seed)
+    scale_a, scale_p = np.abs(ra).max(), np.abs(rp).max()
+    rng = np.random.default_rng(2)
+    for s in rng.choice(np.flatnonzero(sy.act_amp > 0), 6, replace=False):
+        for which, g, scale in (("amp", ga, scale_a), ("phase", gp, scale_p)):
+            def J(delta):
+                alt = sy.copy()
+                arr = (alt.act_amp if which == "amp" else alt.act_phase).copy()
+                arr[s] += delta
+                if which == "amp":
+                    alt.act_amp = arr
+                else:
+                    alt.act_phase = arr
+                x, _ = oracle.run(alt, steps)
+                return float((seed * x).sum())
+            fd = (J(1e-6) - J(-1e-6)) / 2e-6
+            assert abs(g[s] - fd) <= REL * scale, (which, s, g[s], fd)
+
+
+def test_checkpoint_interval_does_not_change_the_result():
+    sy = _robot(dims=(4, 4, 3), seed=3)
+    seed = oracle.centroid_x_seed(sy.n_masses)
+    a = _gpu_adjoint(sy, 120, seed, every=50)
+    for every in (7, 120, 1):
+        b = _gpu_adjoint(sy, 120, seed, every=every)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_adjoint_runs_in_every_csr_kernel_configuration():
+    sy = _robot(dims=(4, 3, 3), seed=6)
+    seed = oracle.centroid_x_seed(sy.n_masses)
+    ref = _gpu_adjoint(sy, 100, seed)
+    for kw in (dict(kernel_variant=3), dict(kernel_variant=1), dict(order=T.ORDER_INPUT)):
+        g = _gpu_adjoint(sy, 100, seed, **kw)
+        _close(g[0], ref[0])
+        _close(g[1], ref[1])
+
+
+def test_torch_autograd_function_over_several_robots():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(12)
+    robots = [inputs.actuated_box(a, b, c, rng) for a, b, c in [(3, 3, 3), (5, 4, 3), (4, 3, 5)]]
+    steps = 200
+    f = T.CentroidRollout(robots, steps, every=50)
+    amp = torch.tensor(f.system.act_amp, dtype=torch.float32, device="cuda", requires_grad=True)
+    ph = torch.tensor(f.system.act_phase, dtype=torch.float32, device="cuda", requires_grad=True)
+    J = f(amp, ph)
+    assert J.shape == (3,)
+    w = torch.tensor([1.0, -2.0, 0.5], device="cuda")
+    (J * w).sum().backward()
+    for r, sy in enumerate(robots):
+        xo, _ = oracle.run(sy, steps)
+        assert float(J[r]) == pytest.approx(xo[:, 0].mean() - sy.pos[:, 0].mean(), abs=1e-5)
+        ra, rp, _, _ = oracle.adjoint(sy, steps, oracle.centroid_x_seed(sy.n_masses))
+        s0, s1 = f.spring_off[r], f.spring_off[r + 1]
+        _close(amp.grad[s0:s1].cpu().numpy() / float(w[r]), ra)
+        _close(ph.grad[s0:s1].cpu().numpy() / float(w[r]), rp)

@@ -9,6 +9,7 @@ close to it.
 import pytest
 
 import oracle
+import test_oracle_adjoint as adj_pins
 import test_oracle_pins as pins
 
 # (name, text in titan_oracle.c, replacement)
@@ -37,24 +38,35 @@ MUTANTS = [
     ("actuation phase sign", "* t + sys->act_b[s]", "* t - sys->act_b[s]"),
     ("actuation 2 pi dropped", "2.0 * kPi * sys->act_freq * t", "sys->act_freq * t"),
     ("actuation time off by one step", "(double)step * sys->dt", "(double)(step + 1) * sys->dt"),
+    ("adjoint: dashpot sign", "vb[3 * j + a] += rateb * u[a];", "vb[3 * j + a] -= rateb * u[a];"),
+    ("adjoint: friction branch", "if (!capped) xbi[2] +=", "if (capped) xbi[2] +="),
+    ("adjoint: phase derivative", "sys->act_a[s] * cos(th);", "sys->act_a[s] * sin(th);"),
+    ("adjoint: velocity passes dt", "vtot[c] = vb_out[3 * i + c] + dt * xb_out[3 * i + c];",
+     "vtot[c] = vb_out[3 * i + c];"),
     ("worm modulo truncated", "tau = tau - sys->worm_period * floor(tau / sys->worm_period);",
      "tau = fmod(tau, sys->worm_period);"),
 ]
 
-PINS = [name for name in dir(pins) if name.startswith("test_")]
+PINS = [getattr(pins, n) for n in dir(pins) if n.startswith("test_")]
+PINS += [getattr(adj_pins, n) for n in dir(adj_pins) if n.startswith("test_")]
 
 
 @pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
 def test_pins_catch_planted_mistake(name, old, new, tmp_path):
     src = oracle.source()
-    assert src.count(old) == 1, f"mutation site for '{name}' not found exactly once"
+    # the forward step comes first in the file; a text that the adjoint repeats
+    # is mutated at its first (forward) occurrence only
+    assert src.count(old) >= 1, f"mutation site for '{name}' not found"
     caught = []
-    with oracle.mutant(src.replace(old, new), str(tmp_path)):
-        for pin in PINS:
-            fn = getattr(pins, pin)
+    with oracle.mutant(src.replace(old, new, 1), str(tmp_path)):
+        for fn in PINS:
             try:
-                fn()
+                if "ground" in fn.__code__.co_varnames[:fn.__code__.co_argcount]:
+                    fn(True)
+                    fn(False)
+                else:
+                    fn()
             except (AssertionError, FloatingPointError, ValueError):
-                caught.append(pin)
+                caught.append(fn.__name__)
                 break
     assert caught, f"no pin caught mutant '{name}'"
