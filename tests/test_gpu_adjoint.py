@@ -119,7 +119,7 @@ def test_torch_autograd_function_over_several_robots():
     (J * w).sum().backward()
     for r, sy in enumerate(robots):
         xo, _ = oracle.run(sy, steps)
-        assert float(J[r]) == pytest.approx(xo[:, 0].mean() - sy.pos[:, 0].mean(), abs=1e-5)
+        assert float(J[r].detach()) == pytest.approx(xo[:, 0].mean() - sy.pos[:, 0].mean(), abs=1e-5)
         ra, rp, _, _ = oracle.adjoint(sy, steps, oracle.centroid_x_seed(sy.n_masses))
         s0, s1 = f.spring_off[r], f.spring_off[r + 1]
         _close(amp.grad[s0:s1].cpu().numpy() / float(w[r]), ra)
