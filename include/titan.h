@@ -298,6 +298,46 @@ const char *titan_batch_last_error(const titan_batch *b);
 /* Waits and frees the batch.  NULL is a no-op. */
 titan_status titan_batch_destroy(titan_batch *b);
 
+/* ------------------------------------------------------------------ surrogate
+ * A fitness-surrogate MLP (in -> hidden -> hidden -> hidden -> 1, GELU after
+ * each hidden layer) trained and evaluated on the tcgen05 tensor cores with
+ * BF16 operands and FP32 accumulation.  It pre-screens candidate robots in a
+ * morphology search whose survivors the simulator scores (the paper's
+ * Sec. III-F shape and topology optimisation, with a learned filter).
+ * Parameters are FP32 (layout: W1^T [hidden][in], b1, W2^T [hidden][hidden],
+ * b2, W3^T, b3, w4 [hidden], b4); activations BF16.  Batches are multiples
+ * of 128; in and hidden are multiples of 128.  Device pointers throughout. */
+typedef struct titan_mlp titan_mlp;
+
+/* C[M][N] = A[M][K] B[N][K]^T on the tensor cores: A and B row-major BF16
+ * (uint16 bit patterns, 16-byte aligned), C row-major FP32.  M and N multiples
+ * of 128, K of 64.  Waits for completion.  Errors: TITAN_E_INVALID,
+ * TITAN_E_CUDA, TITAN_E_TIMEOUT (a bounded wait in the kernel expired). */
+titan_status titan_gemm_bf16_tn(uint32_t M, uint32_t N, uint32_t K, const uint16_t *A_dev,
+                                const uint16_t *B_dev, float *C_dev, void *stream);
+
+titan_status titan_mlp_create(uint32_t in, uint32_t hidden, uint64_t seed, int32_t device, void *stream,
+                              titan_mlp **out);
+uint64_t titan_mlp_param_count(const titan_mlp *m);
+titan_status titan_mlp_get_params(titan_mlp *m, float *host_params);
+titan_status titan_mlp_set_params(titan_mlp *m, const float *host_params);
+
+/* y_dev[b] = network(x_dev[b][:]) for a batch of BF16 inputs. */
+titan_status titan_mlp_forward(titan_mlp *m, const uint16_t *x_dev, uint32_t batch, float *y_dev);
+
+/* Mean-squared-error loss against t_dev and its gradient with respect to
+ * every parameter (flat FP32, the parameter layout; grad_dev may be NULL). */
+titan_status titan_mlp_gradient(titan_mlp *m, const uint16_t *x_dev, const float *t_dev, uint32_t batch,
+                                float *loss_dev, float *grad_dev);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the batch's gradient;
+ * loss_dev (may be NULL) receives the batch loss.  Enqueued, not waited for. */
+titan_status titan_mlp_train_step(titan_mlp *m, const uint16_t *x_dev, const float *t_dev, uint32_t batch,
+                                  float lr, float *loss_dev);
+titan_status titan_mlp_sync(titan_mlp *m);
+const char *titan_mlp_last_error(const titan_mlp *m);
+titan_status titan_mlp_destroy(titan_mlp *m);
+
 #ifdef __cplusplus
 }
 #endif

@@ -87,6 +87,17 @@ def load(path: Optional[str] = None):
                                                   C.POINTER(titan_params), _P, _P, _P]),
                 "titan_set_step": (S, [_P, u64]),
                 "titan_adjoint": (S, [_P, u64, u32, _P, _P, _P, _P]),
+                "titan_gemm_bf16_tn": (S, [u32, u32, u32, _P, _P, _P, _P]),
+                "titan_mlp_create": (S, [u32, u32, u64, C.c_int32, _P, C.POINTER(_P)]),
+                "titan_mlp_param_count": (u64, [_P]),
+                "titan_mlp_get_params": (S, [_P, _P]),
+                "titan_mlp_set_params": (S, [_P, _P]),
+                "titan_mlp_forward": (S, [_P, _P, u32, _P]),
+                "titan_mlp_gradient": (S, [_P, _P, _P, u32, _P, _P]),
+                "titan_mlp_train_step": (S, [_P, _P, _P, u32, f32, _P]),
+                "titan_mlp_sync": (S, [_P]),
+                "titan_mlp_last_error": (C.c_char_p, [_P]),
+                "titan_mlp_destroy": (S, [_P]),
                 "titan_batch_create": (S, [u32, C.POINTER(titan_masses), C.POINTER(titan_springs),
                                            C.POINTER(titan_actuation), C.POINTER(titan_params),
                                            C.POINTER(_P)]),
@@ -496,3 +507,76 @@ class CentroidRollout:
 
             self._fn = _Fn
         return self._fn.apply(amp, phase)
+
+
+# --------------------------------------------------------------------------- tensor-core surrogate MLP
+
+def titan_gemm_bf16_tn(A, B, C, stream: Optional[int] = None) -> None:
+    """C = A B^T on the tcgen05 tensor cores (A, B: CUDA bfloat16 tensors [M, K], [N, K]; C: float32 [M, N])."""
+    M, K = A.shape
+    N = B.shape[0]
+    _check_mlp(load().titan_gemm_bf16_tn(M, N, K, _ptr(A), _ptr(B), _ptr(C), stream))
+
+
+def _check_mlp(status: int, m=None):
+    if status != TITAN_OK:
+        lib = load()
+        msg = lib.titan_mlp_last_error(m) if m else lib.titan_last_error(None)
+        raise TitanError(status, msg.decode(errors="replace"))
+
+
+class MLP:
+    """The surrogate network (titan_mlp_*): in -> hidden x 3 (GELU) -> 1."""
+
+    def __init__(self, n_in: int = 1024, hidden: int = 512, seed: int = 0, device: int = 0,
+                 stream: Optional[int] = None):
+        load()
+        out = _P()
+        _check_mlp(load().titan_mlp_create(n_in, hidden, seed, device, stream, C.byref(out)))
+        self.handle = out.value
+        self.n_in, self.hidden = n_in, hidden
+        self.n_params = int(load().titan_mlp_param_count(self.handle))
+
+    def get_params(self) -> np.ndarray:
+        p = np.empty(self.n_params, np.float32)
+        _check_mlp(load().titan_mlp_get_params(self.handle, _ptr(p)), self.handle)
+        return p
+
+    def set_params(self, p) -> None:
+        p = np.ascontiguousarray(p, np.float32)
+        _check_mlp(load().titan_mlp_set_params(self.handle, _ptr(p)), self.handle)
+
+    def forward(self, x, y) -> None:
+        _check_mlp(load().titan_mlp_forward(self.handle, _ptr(x), x.shape[0], _ptr(y)), self.handle)
+
+    def gradient(self, x, t, loss, grad) -> None:
+        _check_mlp(load().titan_mlp_gradient(self.handle, _ptr(x), _ptr(t), x.shape[0], _ptr(loss), _ptr(grad)),
+                   self.handle)
+
+    def train_step(self, x, t, lr: float, loss=None) -> None:
+        _check_mlp(load().titan_mlp_train_step(self.handle, _ptr(x), _ptr(t), x.shape[0], float(lr), _ptr(loss)),
+                   self.handle)
+
+    def sync(self) -> None:
+        _check_mlp(load().titan_mlp_sync(self.handle), self.handle)
+
+    def unpack(self, p):
+        """Splits a flat parameter vector into (W1t, b1, W2t, b2, W3t, b3, w4, b4)."""
+        h, i = self.hidden, self.n_in
+        out, o = [], 0
+        for shape in [(h, i), (h,), (h, h), (h,), (h, h), (h,), (h,), (1,)]:
+            n = int(np.prod(shape))
+            out.append(np.asarray(p[o:o + n]).reshape(shape))
+            o += n
+        return out
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            load().titan_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,87 @@
+"""The tcgen05 tensor-core GEMM and the surrogate MLP against references.
+
+GEMM: BF16 products are exact in FP32, so C = A B^T must match an FP32
+computation from the same BF16 inputs up to summation order (1e-4 of the
+largest entry).  MLP: the network keeps activations in BF16 (relative
+rounding 2^-9 per stored value, compounding over three layers and the
+backward pass), so its loss and gradient are compared with the FP64 reference
+evaluated on the same BF16-rounded weights and inputs at 3e-2, normwise."""
+import numpy as np
+import pytest
+
+from oracle import mlp as ref
+from paper_1911_10274_gb300 import titan as T
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (256, 384, 512), (512, 512, 4096), (4096, 512, 1024)])
+def test_tcgen05_gemm_matches_reference(M, N, K):
+    g = torch.Generator(device="cuda").manual_seed(M + N + K)
+    A = torch.randn(M, K, device="cuda", generator=g).bfloat16()
+    B = torch.randn(N, K, device="cuda", generator=g).bfloat16()
+    C = torch.full((M, N), float("nan"), device="cuda")
+    T.titan_gemm_bf16_tn(A, B, C)
+    ref_c = A.double() @ B.double().T
+    err = (C.double() - ref_c).abs().max().item()
+    assert err <= 1e-4 * ref_c.abs().max().item(), err
+
+
+def test_gemm_rejects_unaligned_shapes():
+    A = torch.zeros(100, 64, device="cuda").bfloat16()
+    B = torch.zeros(128, 64, device="cuda").bfloat16()
+    C = torch.zeros(100, 128, device="cuda")
+    with pytest.raises(T.TitanError) as ei:
+        T.titan_gemm_bf16_tn(A, B, C)
+    assert ei.value.status == T.TITAN_E_INVALID
+
+
+def _bf16_round(a):
+    return torch.as_tensor(a, dtype=torch.float32).bfloat16().float().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("n_in,hidden,B", [(128, 128, 128), (1024, 512, 512)])
+def test_mlp_forward_and_gradient_match_fp64_reference(n_in, hidden, B):
+    net = T.MLP(n_in, hidden, seed=3)
+    rng = np.random.default_rng(1)
+    x = torch.as_tensor(rng.normal(0, 1, (B, n_in)), dtype=torch.float32).bfloat16().cuda()
+    t = torch.as_tensor(rng.normal(0, 0.3, B), dtype=torch.float32).cuda()
+    p = net.get_params().astype(np.float64)
+    # the network multiplies BF16 copies of its weights: the reference uses the same values
+    pr = p.copy()
+    Wo = net.unpack(np.arange(net.n_params))
+    for idx in (Wo[0], Wo[2], Wo[4]):
+        pr[idx.ravel()] = _bf16_round(p[idx.ravel()])
+    xr = x.float().cpu().numpy().astype(np.float64)
+    y = torch.empty(B, device="cuda")
+    net.forward(x, y)
+    y_ref, _, _ = ref.forward(pr, xr, n_in, hidden)
+    yr = y.cpu().numpy()
+    assert np.abs(yr - y_ref).max() <= 3e-2 * np.abs(y_ref).max()
+    loss = torch.empty(1, device="cuda")
+    grad = torch.empty(net.n_params, device="cuda")
+    net.gradient(x, t, loss, grad)
+    l_ref, g_ref = ref.loss_and_grad(pr, xr, t.cpu().numpy().astype(np.float64), n_in, hidden)
+    assert float(loss) == pytest.approx(l_ref, rel=3e-2)
+    g = grad.cpu().numpy().astype(np.float64)
+    for sl in net.unpack(np.arange(net.n_params)):
+        gs, rs = g[sl.ravel()], g_ref[sl.ravel()]
+        assert np.linalg.norm(gs - rs) <= 3e-2 * np.linalg.norm(rs) + 1e-12
+
+
+def test_mlp_training_reduces_the_loss_on_a_learnable_target():
+    net = T.MLP(128, 128, seed=0)
+    rng = np.random.default_rng(5)
+    B = 512
+    X = rng.normal(0, 1, (B, 128))
+    t = np.tanh(X[:, :8].sum(axis=1) / 3.0)
+    x = torch.as_tensor(X, dtype=torch.float32).bfloat16().cuda()
+    tt = torch.as_tensor(t, dtype=torch.float32).cuda()
+    loss = torch.empty(1, device="cuda")
+    net.gradient(x, tt, loss, None)
+    first = float(loss)
+    for _ in range(300):
+        net.train_step(x, tt, 1e-3, loss)
+    net.sync()
+    assert float(loss) < 0.2 * first
