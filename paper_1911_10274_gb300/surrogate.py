@@ -1,0 +1,241 @@
+"""Surrogate-screened morphology search for actuated voxel robots.
+
+The paper's asynchronous design exists so that optimisation (topology and
+actuation, Sec. III-F; many agents in parallel, Sec. I) can run alongside the
+simulation.  This module closes that loop on the GPU:
+
+* morphologies: an 8 x 8 x 8 voxel grid, Bernoulli(0.6) occupancy, largest
+  26-connected component, one mass per voxel, 26-neighbourhood springs, every
+  spring actuated with amplitude 0.1 and the phase of its lower-index voxel;
+* fitness: the robot's centroid x-displacement after a rollout on the ground,
+  simulated by the batched persistent kernels (``titan.Batch``);
+* surrogate: an MLP on the tcgen05 tensor cores (``titan.MLP``) mapping the
+  1024 features (occupancy bits, then per-voxel phases scaled to [-1, 1), 0
+  where empty) to the standardised fitness, trained with Adam on simulated
+  rollouts;
+* search: a (mu + lambda) mutation search.  The plain form simulates every
+  mutant; the screened form lets the surrogate rank all mutants and simulates
+  only the top few, whose simulated fitness (the simulator remains the judge)
+  decides who survives.  A random pick of the same size is the ablation.
+
+Python here only orchestrates: every rollout and every network product runs
+in the library's kernels.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import List, Optional, Tuple
+
+import numpy as np
+
+from . import inputs
+from . import titan as T
+
+GRID = 8
+N_FEATURES = 2 * GRID ** 3
+
+
+@dataclasses.dataclass
+class Morph:
+    occ: np.ndarray      # (8, 8, 8) bool, (z, y, x)
+    phase: np.ndarray    # (8, 8, 8) float, radians (only occupied voxels matter)
+
+
+def random_morph(rng: np.random.Generator, p: float = 0.6) -> Morph:
+    occ = inputs.voxel_morphology(rng, GRID, p)
+    return Morph(occ=occ, phase=rng.uniform(0.0, 2.0 * np.pi, (GRID,) * 3))
+
+
+def robot(m: Morph, freq: float = 2.0) -> inputs.System:
+    return inputs.voxel_robot(m.occ, m.phase, amp=0.1, freq=freq)
+
+
+def encode(morphs: List[Morph]) -> np.ndarray:
+    """(n, 1024) float32: occupancy bits, then phases scaled to [-1, 1) (0 where empty)."""
+    X = np.zeros((len(morphs), N_FEATURES), np.float32)
+    for i, m in enumerate(morphs):
+        o = m.occ.ravel()
+        X[i, :GRID ** 3] = o
+        X[i, GRID ** 3:] = np.where(o, m.phase.ravel() / np.pi - 1.0, 0.0)
+    return X
+
+
+def fitness(morphs: List[Morph], steps: int, freq: float = 2.0, chunk: int = 4096,
+            device: int = 0) -> np.ndarray:
+    """Centroid x-displacement of each robot after `steps` steps (simulated)."""
+    out = np.empty(len(morphs))
+    for s in range(0, len(morphs), chunk):
+        robots = [robot(m, freq) for m in morphs[s:s + chunk]]
+        x0 = np.array([r.pos[:, 0].mean() for r in robots])
+        with T.Batch(robots, device=device) as b:
+            b.rollout(steps)
+            c = b.centroids()
+        out[s:s + chunk] = c[:, 0].astype(np.float64) - x0
+    return out
+
+
+def mutate(rng: np.random.Generator, m: Morph, flip_mean: float = 1.5, phase_prob: float = 0.15,
+           phase_sigma: float = 1.0) -> Morph:
+    """Toggles 1 + Poisson(flip_mean) voxels, perturbs some phases, keeps the
+    largest connected component (at least 8 voxels)."""
+    for _ in range(20):
+        occ = m.occ.copy()
+        phase = m.phase.copy()
+        for _ in range(1 + rng.poisson(flip_mean)):
+            z, y, x = rng.integers(0, GRID, 3)
+            if not occ[z, y, x]:
+                phase[z, y, x] = rng.uniform(0.0, 2.0 * np.pi)
+            occ[z, y, x] = not occ[z, y, x]
+        jig = rng.random((GRID,) * 3) < phase_prob
+        phase = np.where(jig, np.mod(phase + rng.normal(0.0, phase_sigma, phase.shape), 2.0 * np.pi), phase)
+        occ = inputs.largest_component(occ)
+        if occ.sum() >= 8:
+            return Morph(occ=occ, phase=phase)
+    return m
+
+
+class Surrogate:
+    """The tensor-core MLP plus target standardisation."""
+
+    def __init__(self, hidden: int = 512, seed: int = 0, device: int = 0):
+        import torch
+        self.torch = torch
+        self.net = T.MLP(N_FEATURES, hidden, seed=seed, device=device)
+        self.device = device
+        self.mu, self.sd = 0.0, 1.0
+
+    def _x(self, X):
+        return self.torch.as_tensor(X, dtype=self.torch.float32, device=f"cuda:{self.device}").bfloat16()
+
+    def fit(self, X: np.ndarray, y: np.ndarray, epochs: int = 20, batch: int = 4096, lr: float = 1e-3,
+            seed: int = 0) -> List[float]:
+        torch = self.torch
+        self.mu, self.sd = float(y.mean()), float(y.std() + 1e-12)
+        yt = (y - self.mu) / self.sd
+        n = (len(X) // 128) * 128
+        batch = min(batch, n)
+        batch -= batch % 128
+        rng = np.random.default_rng(seed)
+        Xd = self._x(X)
+        yd = torch.as_tensor(yt, dtype=torch.float32, device=f"cuda:{self.device}")
+        loss = torch.empty(1, device=f"cuda:{self.device}")
+        hist = []
+        for _ in range(epochs):
+            perm = torch.as_tensor(rng.permutation(len(X)), device=f"cuda:{self.device}")
+            for s in range(0, n - batch + 1, batch):
+                idx = perm[s:s + batch]
+                self.net.train_step(Xd[idx].contiguous(), yd[idx].contiguous(), lr, loss)
+            self.net.sync()
+            hist.append(float(loss))
+        return hist
+
+    def predict(self, X: np.ndarray) -> np.ndarray:
+        torch = self.torch
+        n = len(X)
+        pad = (-n) % 128
+        Xp = np.concatenate([X, np.zeros((pad, X.shape[1]), X.dtype)]) if pad else X
+        x = self._x(Xp)
+        y = torch.empty(len(Xp), device=f"cuda:{self.device}")
+        self.net.forward(x, y)
+        return y.cpu().numpy()[:n].astype(np.float64) * self.sd + self.mu
+
+
+def spearman(a, b) -> float:
+    ra = np.argsort(np.argsort(a))
+    rb = np.argsort(np.argsort(b))
+    return float(np.corrcoef(ra, rb)[0, 1])
+
+
+def search(mode: str, start: List[Morph], start_fit: np.ndarray, generations: int, mutants: int, screened: int,
+           steps: int, seed: int = 0, surrogate: Optional[Surrogate] = None, parents: int = 16,
+           freq: float = 2.0) -> dict:
+    """(mu + lambda) search from a simulated starting population.
+
+    mode 'plain': simulate all mutants; 'surrogate': simulate the `screened`
+    mutants the surrogate ranks highest; 'random': simulate `screened` random
+    mutants.  Returns the best simulated fitness after each generation and the
+    simulator rollouts spent so far (the starting population is not counted)."""
+    rng = np.random.default_rng(seed)
+    order = np.argsort(-start_fit)[:parents]
+    pop = [start[i] for i in order]
+    pop_fit = start_fit[order].copy()
+    best, used, hist = float(pop_fit[0]), 0, []
+    pred_corr = []
+    for g in range(generations):
+        kids = [mutate(rng, pop[k % len(pop)]) for k in range(mutants)]
+        if mode == "plain":
+            chosen = kids
+        elif mode == "surrogate":
+            pred = surrogate.predict(encode(kids))
+            top = np.argsort(-pred)[:screened]
+            chosen = [kids[i] for i in top]
+        else:
+            chosen = [kids[i] for i in rng.choice(len(kids), screened, replace=False)]
+        f = fitness(chosen, steps, freq)
+        used += len(chosen)
+        if mode == "surrogate":
+            pred_corr.append(spearman(pred[top], f))
+        allm = pop + chosen
+        allf = np.concatenate([pop_fit, f])
+        keep = np.argsort(-allf)[:parents]
+        pop = [allm[i] for i in keep]
+        pop_fit = allf[keep]
+        best = max(best, float(pop_fit[0]))
+        hist.append((used, best))
+    return {"history": hist, "best": best, "rollouts": used,
+            "screen_rank_corr": float(np.mean(pred_corr)) if pred_corr else None}
+
+
+def rollouts_to_reach(history, target: float) -> Optional[int]:
+    for used, best in history:
+        if best >= target:
+            return used
+    return None
+
+
+def main(argv=None):
+    """Full-scale run: python -m paper_1911_10274_gb300.surrogate [--train N] [--steps S] ..."""
+    import argparse
+    import json
+    import time
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--train", type=int, default=200_000)
+    ap.add_argument("--steps", type=int, default=10_000)
+    ap.add_argument("--generations", type=int, default=100)
+    ap.add_argument("--mutants", type=int, default=1024)
+    ap.add_argument("--screened", type=int, default=64)
+    ap.add_argument("--epochs", type=int, default=20)
+    ap.add_argument("--seed", type=int, default=0)
+    a = ap.parse_args(argv)
+    rng = np.random.default_rng(a.seed)
+    t0 = time.time()
+    morphs = [random_morph(rng) for _ in range(a.train)]
+    y = fitness(morphs, a.steps)
+    t_sim = time.time() - t0
+    X = encode(morphs)
+    n_val = max(128, a.train // 10)
+    sur = Surrogate(seed=a.seed)
+    t1 = time.time()
+    sur.fit(X[:-n_val], y[:-n_val], epochs=a.epochs)
+    t_fit = time.time() - t1
+    val_corr = spearman(sur.predict(X[-n_val:]), y[-n_val:])
+    start = morphs[-n_val:]
+    start_fit = y[-n_val:]
+    res = {}
+    for mode in ("plain", "surrogate", "random"):
+        res[mode] = search(mode, start, start_fit, a.generations, a.mutants, a.screened, a.steps, seed=a.seed + 1,
+                           surrogate=sur)
+    target = res["plain"]["best"]
+    out = {"train_rollouts": a.train, "steps": a.steps, "simulate_s": t_sim, "fit_s": t_fit,
+           "val_spearman": val_corr, "plain_best": target,
+           "plain_rollouts": res["plain"]["rollouts"],
+           "surrogate_best": res["surrogate"]["best"], "random_best": res["random"]["best"],
+           "surrogate_rollouts_to_plain_best": rollouts_to_reach(res["surrogate"]["history"], target),
+           "random_rollouts_to_plain_best": rollouts_to_reach(res["random"]["history"], target),
+           "surrogate_screen_rank_corr": res["surrogate"]["screen_rank_corr"]}
+    print(json.dumps(out))
+    return out
+
+
+if __name__ == "__main__":
+    main()
