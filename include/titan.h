@@ -155,6 +155,43 @@ titan_status titan_snapshot_wait(titan_sim *sim, uint64_t ticket, const float **
 titan_status titan_set_actuation(titan_sim *sim, uint32_t n, const uint32_t *spring_ids,
                                  const float *amp, const float *phase, float freq_hz);
 
+/* Worm actuation (Sec. V-B, Eqs. 3-5): rest(t) = L0 (1 + c[s] sin(omega tau)),
+ * tau = (t - t_offset[s]) mod period (floor modulo, in [0, period)).  c == 0
+ * turns a spring off.  Replaces any sinusoidal actuation.  Takes effect from
+ * the next enqueued step.  Errors: TITAN_E_INVALID. */
+titan_status titan_set_worm_actuation(titan_sim *sim, uint32_t n, const uint32_t *spring_ids,
+                                      const float *c, const float *t_offset, float omega, float period);
+
+/* ---- edits between steps (Sec. III-C: O(1) insertion and deletion; Sec.
+ * III-F: spring constants, rest lengths and topology changed while the
+ * simulation runs).  Ids are the caller's: springs and masses added later get
+ * the next free ids.  Parameter edits and removals patch the device arrays in
+ * place (O(1) per spring).  Additions are queued and the device layout is
+ * rebuilt, keeping the state, the step counter and the actuation, before the
+ * next call that uses the state (O(masses + springs) once per batch of
+ * additions); that rebuild invalidates earlier snapshot tickets. */
+
+/* New stiffness, rest length and/or dashpot (any array may be NULL = keep). */
+titan_status titan_set_spring_params(titan_sim *sim, uint32_t n, const uint32_t *spring_ids,
+                                     const double *k, const double *rest, const double *damping);
+
+/* Removes springs: their stiffness, dashpot and actuation become 0 (the paper's
+ * lazy deletion); the ids stay reserved. */
+titan_status titan_remove_springs(titan_sim *sim, uint32_t n, const uint32_t *spring_ids);
+
+/* Adds springs (ends [n][2] ids of existing or added masses); rest NULL: the
+ * distance between the two masses when the layout is rebuilt; damping NULL:
+ * params.damping.  *first_id (may be NULL) receives the first new id. */
+titan_status titan_add_springs(titan_sim *sim, uint32_t n, const uint32_t *ends, const double *k,
+                               const double *rest, const double *damping, uint32_t *first_id);
+
+/* Adds masses (pos [n][3], vel [n][3] or NULL, mass [n], fixed [n] or NULL). */
+titan_status titan_add_masses(titan_sim *sim, uint32_t n, const double *pos, const double *vel,
+                              const double *mass, const uint8_t *fixed, uint32_t *first_id);
+
+/* Fixes (nonzero) or frees masses (Sec. III-A constraints). */
+titan_status titan_set_fixed(titan_sim *sim, uint32_t n, const uint32_t *mass_ids, const uint8_t *fixed);
+
 /* Replaces the positions and velocities (host FP64 arrays [n][3], caller
  * order; vel NULL: zero) from the next enqueued step on; the step counter is
  * kept.  Used to resume from a checkpoint (Sec. III-D breakpoints).

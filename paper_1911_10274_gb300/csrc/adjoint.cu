@@ -177,7 +177,9 @@ extern "C" titan_status titan_adjoint(titan_sim *sim, uint64_t n_steps, uint32_t
     long long *seg_steps = nullptr;
     uint64_t n_seg = 0;
     int cur = 0;
+    if ((st_ = titan::ensure_layout(sim)) != TITAN_OK) goto out;
     if (sim->accumulate != TITAN_ACCUM_CSR) { st_ = afail(sim, TITAN_E_UNSUPPORTED, "the adjoint needs the CSR (deterministic) accumulation"); goto out; }
+    if (sim->act_mode == 2) { st_ = afail(sim, TITAN_E_UNSUPPORTED, "the adjoint differentiates the sinusoidal actuation (mode 1) only"); goto out; }
     if (!sim->has_act) { st_ = afail(sim, TITAN_E_INVALID, "the adjoint differentiates the actuation: call titan_set_actuation first"); goto out; }
     if (!seed_pos_dev || (S && (!grad_amp_dev || !grad_phase_dev))) { st_ = afail(sim, TITAN_E_INVALID, "null seed or gradient array"); goto out; }
     if (every == 0) every = 50;

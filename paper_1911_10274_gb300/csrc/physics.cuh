@@ -24,6 +24,27 @@ __device__ __forceinline__ float clock_phase(const StepConst &c, long long step)
     return (float)ph;
 }
 
+// Per-thread actuation clock for step `step`: mode 1 the phase 2 pi f t mod
+// 2 pi, mode 2 (the worm of Sec. V-B, Eq. 3) the time t mod t_p.
+__device__ __forceinline__ float actuation_clock(const StepConst &c, long long step) {
+    if (c.act_mode == 2) {
+        const double t = (double)step * c.dt_d;
+        return (float)(t - c.worm_period * floor(t / c.worm_period));
+    }
+    return clock_phase(c, step);
+}
+
+// Rest length of an actuated spring: a = (A, phi) in mode 1,
+// (c, t_o mod t_p) in mode 2 where tau = (t - t_o) mod t_p (Eqs. 3-4).
+__device__ __forceinline__ float actuated_length(const StepConst &c, float L0, float2 a, float clk) {
+    if (c.act_mode == 2) {
+        float tau = clk - a.y;
+        if (tau < 0.f) tau += (float)c.worm_period;
+        return L0 * (1.f + a.x * sinf(c.worm_omega * tau));
+    }
+    return L0 * (1.f + a.x * sinf(clk + a.y));
+}
+
 // Force on the mass at (p, v) from one spring to the mass at (q, w):
 // accumulates f u into (fx, fy, fz).  A zero-length spring contributes 0.
 __device__ __forceinline__ void spring_force(const float4 &p, const float4 &v, const float4 &q,

@@ -392,6 +392,31 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
     }
     sim->has_c = !uniform_c;
     if (uniform_c && s) sim->c.c_uniform = sim->damp[0];
+    sim->params = *p;
+    sim->h_mass.assign(m->mass, m->mass + n);
+    sim->h_fixed.assign(n, 0);
+    if (m->fixed)
+        for (uint32_t i = 0; i < n; ++i) sim->h_fixed[i] = m->fixed[i] ? 1 : 0;
+    sim->h_ends.assign(sp->ends, sp->ends + 2 * (size_t)s);
+    sim->h_k.assign(sp->k, sp->k + s);
+    sim->h_rest.resize(s);
+    sim->h_damp.resize(s);
+    for (uint32_t q = 0; q < s; ++q) {
+        sim->h_rest[q] = sp->rest ? sp->rest[q] : (double)sim->rest[q];
+        sim->h_damp[q] = sp->damping ? sp->damping[q] : p->damping;
+    }
+    if (!sp->rest) {          // keep the FP64 initial distances
+        for (uint32_t q = 0; q < s; ++q) {
+            const uint32_t i = sp->ends[2 * (size_t)q], j = sp->ends[2 * (size_t)q + 1];
+            double d2 = 0;
+            for (int a = 0; a < 3; ++a) {
+                const double d = m->pos[3 * (size_t)j + a] - m->pos[3 * (size_t)i + a];
+                d2 += d * d;
+            }
+            sim->h_rest[q] = std::sqrt(d2);
+        }
+    }
+    sim->c.act_mode = 1;
 
     // ---- device state
     const uint32_t nd = sim->n_dev;
@@ -495,6 +520,10 @@ titan_status titan_step(titan_sim *sim, uint64_t n_steps) {
     BusyGuard bg(sim);
     if (!bg.acquired) return fail(sim, TITAN_E_BUSY, "another call on this handle is in progress");
     DeviceGuard dg(sim->device);
+    {
+        titan_status es_ = titan::ensure_layout(sim);
+        if (es_ != TITAN_OK) return es_;
+    }
     TITAN_CK(sim, cudaGetLastError());
     while (n_steps > 0) {
         if (sim->graph_chunk > 0 && n_steps >= (uint64_t)sim->graph_chunk) {
@@ -517,6 +546,10 @@ titan_status titan_snapshot_async(titan_sim *sim, void *stream, uint64_t *ticket
     BusyGuard bg(sim);
     if (!bg.acquired) return fail(sim, TITAN_E_BUSY, "another call on this handle is in progress");
     DeviceGuard dg(sim->device);
+    {
+        titan_status es_ = titan::ensure_layout(sim);
+        if (es_ != TITAN_OK) return es_;
+    }
     cudaStream_t side = stream ? static_cast<cudaStream_t>(stream) : sim->side;
     const uint64_t tk = sim->last_ticket + 1;
     const int slot = (int)(tk & 1);
@@ -570,12 +603,16 @@ titan_status titan_set_actuation(titan_sim *sim, uint32_t n, const uint32_t *ids
     if (!bg.acquired) return fail(sim, TITAN_E_BUSY, "another call on this handle is in progress");
     if (n && (!ids || !amp || !phase)) return fail(sim, TITAN_E_INVALID, "spring_ids, amp and phase are required");
     if (!std::isfinite(freq_hz)) return fail(sim, TITAN_E_INVALID, "freq_hz must be finite");
+    {
+        titan_status es_ = titan::ensure_layout(sim);
+        if (es_ != TITAN_OK) return es_;
+    }
     for (uint32_t q = 0; q < n; ++q) {
         if (ids[q] >= sim->s) return fail(sim, TITAN_E_INVALID, "spring id out of range: " + std::to_string(ids[q]));
         if (!std::isfinite(amp[q]) || !std::isfinite(phase[q])) return fail(sim, TITAN_E_INVALID, "non-finite amp or phase");
     }
     DeviceGuard dg(sim->device);
-    if (sim->act_amp.empty()) {
+    if (sim->act_amp.empty() || sim->act_mode != 1) {
         sim->act_amp.assign(sim->s, 0.f);
         sim->act_phase.assign(sim->s, 0.f);
     }
@@ -584,6 +621,8 @@ titan_status titan_set_actuation(titan_sim *sim, uint32_t n, const uint32_t *ids
         sim->act_phase[ids[q]] = phase[q];
     }
     sim->c.act_omega = 2.0 * 3.14159265358979323846 * (double)freq_hz;
+    sim->c.act_mode = 1;
+    sim->act_mode = 1;
     TITAN_CK(sim, upload_actuation(sim));
     sim->has_act = true;
     if (sim->csr_kernel == 5 && !choose_halo_width(sim)) sim->csr_kernel = 4;   // larger entries
@@ -600,6 +639,10 @@ titan_status titan_set_state(titan_sim *sim, const double *pos, const double *ve
         if (!std::isfinite(pos[i]) || (vel && !std::isfinite(vel[i])))
             return fail(sim, TITAN_E_INVALID, "non-finite pos or vel");
     DeviceGuard dg(sim->device);
+    {
+        titan_status es_ = titan::ensure_layout(sim);
+        if (es_ != TITAN_OK) return es_;
+    }
     std::vector<MassState> st;
     fill_state(sim, pos, vel, st);
     TITAN_CK(sim, upload(sim->state[sim->cur], st, sim->stream));
@@ -612,6 +655,10 @@ titan_status titan_read_state_dev(titan_sim *sim, float *pos_dev, float *vel_dev
     BusyGuard bg(sim);
     if (!bg.acquired) return fail(sim, TITAN_E_BUSY, "another call on this handle is in progress");
     DeviceGuard dg(sim->device);
+    {
+        titan_status es_ = titan::ensure_layout(sim);
+        if (es_ != TITAN_OK) return es_;
+    }
     TITAN_CK(sim, titan::launch_unpermute(sim->state[sim->cur], sim->d_dev_of_caller, sim->n, pos_dev,
                                           vel_dev, sim->stream));
     if (stream && static_cast<cudaStream_t>(stream) != sim->stream) {
@@ -663,6 +710,341 @@ titan_status titan_destroy(titan_sim *sim) {
     }
     delete sim;
     return st;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ topology and parameter edits
+
+namespace {
+
+// Writes 32-bit words in device memory: base[idx[k]] = val[k] (stream-ordered).
+cudaError_t patch_words(titan_sim *sim, void *base, const std::vector<uint32_t> &idx,
+                        const std::vector<uint32_t> &val) {
+    if (idx.empty()) return cudaSuccess;
+    uint32_t *d = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&d, idx.size() * 8, sim->stream);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(d, idx.data(), idx.size() * 4, cudaMemcpyHostToDevice, sim->stream)) == cudaSuccess &&
+        (e = cudaMemcpyAsync(d + idx.size(), val.data(), idx.size() * 4, cudaMemcpyHostToDevice, sim->stream)) == cudaSuccess)
+        e = titan::launch_patch_words(static_cast<uint32_t *>(base), d, d + idx.size(), (uint32_t)idx.size(), sim->stream);
+    cudaFreeAsync(d, sim->stream);
+    return e;
+}
+
+uint32_t fbits(float f) {
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    return u;
+}
+
+// Turns the uniform dashpot into a per-entry array (needed once a spring's damping is edited).
+cudaError_t enable_per_spring_damping(titan_sim *sim) {
+    if (sim->has_c) return cudaSuccess;
+    cudaError_t e;
+    if (sim->accumulate == TITAN_ACCUM_CSR) {
+        std::vector<float> cc(sim->sell.entries, 0.f);
+        for (uint32_t e2 = 0; e2 < sim->sell.entries; ++e2)
+            if (sim->sell.spring[e2] != UINT32_MAX) cc[e2] = sim->damp[sim->sell.spring[e2]];
+        if (!sim->d_c && (e = dev_alloc(sim, &sim->d_c, sim->sell.entries)) != cudaSuccess) return e;
+        if ((e = upload(sim->d_c, cc, sim->stream)) != cudaSuccess) return e;
+    } else {
+        std::vector<float> cc(sim->s);
+        for (uint32_t r = 0; r < sim->s; ++r) cc[r] = sim->damp[sim->rec.order[r]];
+        if (!sim->d_rc && (e = dev_alloc(sim, &sim->d_rc, sim->s)) != cudaSuccess) return e;
+        if ((e = upload(sim->d_rc, cc, sim->stream)) != cudaSuccess) return e;
+    }
+    sim->has_c = true;
+    if (sim->csr_kernel == 5 && !choose_halo_width(sim)) sim->csr_kernel = 4;
+    free_graphs(sim);
+    return cudaSuccess;
+}
+
+// Pushes the current host parameters of device springs `ids` into the device layout.
+cudaError_t push_springs(titan_sim *sim, const std::vector<uint32_t> &ids, bool damping, bool actuation) {
+    std::vector<uint32_t> wi, wv, ci, cv, ai, av;
+    for (uint32_t q : ids) {
+        const float kf = sim->k[q], lf = sim->rest[q];
+        if (sim->accumulate == TITAN_ACCUM_CSR) {
+            for (int end = 0; end < 2; ++end) {
+                const uint32_t e = sim->sell.entry_of_end[2 * (size_t)q + end];
+                wi.push_back(2 * e); wv.push_back(fbits(kf));
+                wi.push_back(2 * e + 1); wv.push_back(fbits(lf));
+                if (damping) { ci.push_back(e); cv.push_back(fbits(sim->damp[q])); }
+                if (actuation) { ai.push_back(2 * e); av.push_back(fbits(sim->act_amp[q])); }
+            }
+        } else {
+            const uint32_t r = sim->rec.slot_of_spring[q];
+            wi.push_back(4 * r + 2); wv.push_back(fbits(kf));
+            wi.push_back(4 * r + 3); wv.push_back(fbits(lf));
+            if (damping) { ci.push_back(r); cv.push_back(fbits(sim->damp[q])); }
+            if (actuation) { ai.push_back(2 * r); av.push_back(fbits(sim->act_amp[q])); }
+        }
+    }
+    cudaError_t e;
+    void *words = sim->accumulate == TITAN_ACCUM_CSR ? (void *)sim->d_kl : (void *)sim->d_rec;
+    if ((e = patch_words(sim, words, wi, wv)) != cudaSuccess) return e;
+    if (damping && (e = patch_words(sim, sim->accumulate == TITAN_ACCUM_CSR ? (void *)sim->d_c : (void *)sim->d_rc, ci, cv)) != cudaSuccess)
+        return e;
+    if (actuation && (e = patch_words(sim, sim->accumulate == TITAN_ACCUM_CSR ? (void *)sim->d_act : (void *)sim->d_ract, ai, av)) != cudaSuccess)
+        return e;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+// Rebuilds the device layout after masses or springs were added, keeping the
+// state, the step counter and the actuation.  The handle stays valid;
+// snapshots taken before become invalid.
+titan_status titan::ensure_layout(titan_sim *sim) {
+    if (!sim->dirty) return TITAN_OK;
+    const uint32_t n_old = sim->n;
+    const uint32_t n_tot = (uint32_t)sim->h_mass.size();
+    const uint32_t s_tot = (uint32_t)sim->h_k.size();
+    std::vector<double> pos(3 * (size_t)n_tot), vel(3 * (size_t)n_tot);
+    if (n_old) {
+        float *d = nullptr;
+        std::vector<float> h(6 * (size_t)n_old);
+        TITAN_CK(sim, cudaMallocAsync((void **)&d, h.size() * 4, sim->stream));
+        cudaError_t e = titan::launch_unpermute(sim->state[sim->cur], sim->d_dev_of_caller, n_old, d,
+                                                d + 3 * (size_t)n_old, sim->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d, h.size() * 4, cudaMemcpyDeviceToHost, sim->stream);
+        cudaFreeAsync(d, sim->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(sim->stream);
+        TITAN_CK(sim, e);
+        for (size_t k = 0; k < 3 * (size_t)n_old; ++k) {
+            pos[k] = h[k];
+            vel[k] = h[3 * (size_t)n_old + k];
+        }
+    }
+    for (size_t k = 0; k < sim->pend_pos.size(); ++k) {
+        pos[3 * (size_t)n_old + k] = sim->pend_pos[k];
+        vel[3 * (size_t)n_old + k] = sim->pend_vel[k];
+    }
+    std::vector<double> rest = sim->h_rest;
+    for (uint32_t q = 0; q < s_tot; ++q)
+        if (std::isnan(rest[q])) {          // added without a rest length: the current distance
+            const uint32_t i = sim->h_ends[2 * (size_t)q], j = sim->h_ends[2 * (size_t)q + 1];
+            double d2 = 0;
+            for (int a = 0; a < 3; ++a) {
+                const double d = pos[3 * (size_t)j + a] - pos[3 * (size_t)i + a];
+                d2 += d * d;
+            }
+            rest[q] = std::sqrt(d2);
+        }
+    titan_masses ms{n_tot, pos.data(), vel.data(), sim->h_mass.data(), sim->h_fixed.data()};
+    titan_springs ss{s_tot, sim->h_ends.data(), sim->h_k.data(), rest.data(), sim->h_damp.data()};
+    titan_params p = sim->params;
+    p.stream = sim->stream;
+    titan_sim *fresh = nullptr;
+    titan_status st = titan_create(&ms, &ss, &p, &fresh);
+    if (st != TITAN_OK) return fail(sim, st, std::string("rebuild after a topology edit: ") + titan_last_error(nullptr));
+    // carry the clock and the actuation across
+    const uint64_t steps = sim->steps;
+    std::vector<float> amp = sim->act_amp, phase = sim->act_phase;
+    const int act_mode = sim->act_mode;
+    const titan::StepConst oldc = sim->c;
+    const bool own = sim->own_stream;
+    std::swap(static_cast<SimCore &>(*sim), static_cast<SimCore &>(*fresh));
+    sim->own_stream = own;
+    fresh->own_stream = false;
+    titan_destroy(fresh);
+    sim->steps = steps;
+    const long long v[2] = {(long long)steps, (long long)steps};
+    TITAN_CK(sim, cudaMemcpyAsync(sim->steps_dev, v, sizeof(v), cudaMemcpyHostToDevice, sim->stream));
+    if (act_mode) {
+        amp.resize(s_tot, 0.f);
+        phase.resize(s_tot, 0.f);
+        sim->act_amp = amp;
+        sim->act_phase = phase;
+        sim->act_mode = act_mode;
+        sim->c.act_mode = oldc.act_mode;
+        sim->c.act_omega = oldc.act_omega;
+        sim->c.worm_omega = oldc.worm_omega;
+        sim->c.worm_period = oldc.worm_period;
+        TITAN_CK(sim, upload_actuation(sim));
+        sim->has_act = true;
+        if (sim->csr_kernel == 5 && !choose_halo_width(sim)) sim->csr_kernel = 4;
+        free_graphs(sim);
+    }
+    TITAN_CK(sim, cudaStreamSynchronize(sim->stream));
+    return TITAN_OK;
+}
+
+extern "C" {
+
+titan_status titan_set_spring_params(titan_sim *sim, uint32_t n, const uint32_t *ids, const double *k,
+                                     const double *rest, const double *damping) {
+    if (!sim) return fail(nullptr, TITAN_E_INVALID, "sim is null");
+    BusyGuard bg(sim);
+    if (!bg.acquired) return fail(sim, TITAN_E_BUSY, "another call on this handle is in progress");
+    if (n && !ids) return fail(sim, TITAN_E_INVALID, "spring ids are required");
+    const uint32_t s_tot = (uint32_t)sim->h_k.size();
+    for (uint32_t q = 0; q < n; ++q) {
+        if (ids[q] >= s_tot) return fail(sim, TITAN_E_INVALID, "spring id out of range: " + std::to_string(ids[q]));
+        if (k && !(std::isfinite(k[q]) && k[q] >= 0)) return fail(sim, TITAN_E_INVALID, "k must be finite and >= 0");
+        if (rest && !(std::isfinite(rest[q]) && rest[q] >= 0)) return fail(sim, TITAN_E_INVALID, "rest must be finite and >= 0");
+        if (damping && !(std::isfinite(damping[q]) && damping[q] >= 0)) return fail(sim, TITAN_E_INVALID, "damping must be finite and >= 0");
+    }
+    DeviceGuard dg(sim->device);
+    std::vector<uint32_t> live;
+    for (uint32_t q = 0; q < n; ++q) {
+        const uint32_t id = ids[q];
+        if (k) sim->h_k[id] = k[q];
+        if (rest) sim->h_rest[id] = rest[q];
+        if (damping) sim->h_damp[id] = damping[q];
+        if (id < sim->s) {            // on the device already (else the next rebuild takes it)
+            if (k) sim->k[id] = (float)k[q];
+            if (rest) sim->rest[id] = (float)rest[q];
+            if (damping) sim->damp[id] = (float)damping[q];
+            live.push_back(id);
+        }
+    }
+    if (damping && !live.empty()) TITAN_CK(sim, enable_per_spring_damping(sim));
+    TITAN_CK(sim, push_springs(sim, live, damping != nullptr, false));
+    return TITAN_OK;
+}
+
+titan_status titan_remove_springs(titan_sim *sim, uint32_t n, const uint32_t *ids) {
+    if (!sim) return fail(nullptr, TITAN_E_INVALID, "sim is null");
+    BusyGuard bg(sim);
+    if (!bg.acquired) return fail(sim, TITAN_E_BUSY, "another call on this handle is in progress");
+    if (n && !ids) return fail(sim, TITAN_E_INVALID, "spring ids are required");
+    const uint32_t s_tot = (uint32_t)sim->h_k.size();
+    for (uint32_t q = 0; q < n; ++q)
+        if (ids[q] >= s_tot) return fail(sim, TITAN_E_INVALID, "spring id out of range: " + std::to_string(ids[q]));
+    DeviceGuard dg(sim->device);
+    std::vector<uint32_t> live;
+    for (uint32_t q = 0; q < n; ++q) {
+        const uint32_t id = ids[q];
+        sim->h_k[id] = 0.0;
+        sim->h_damp[id] = 0.0;
+        if (id < sim->act_amp.size()) sim->act_amp[id] = 0.f;
+        if (id < sim->s) {
+            sim->k[id] = 0.f;
+            sim->damp[id] = 0.f;
+            live.push_back(id);
+        }
+    }
+    if (!live.empty()) {
+        const bool damped = sim->has_c || sim->c.c_uniform != 0.f;
+        if (damped) TITAN_CK(sim, enable_per_spring_damping(sim));
+        TITAN_CK(sim, push_springs(sim, live, damped, sim->has_act));
+    }
+    return TITAN_OK;
+}
+
+titan_status titan_add_springs(titan_sim *sim, uint32_t n, const uint32_t *ends, const double *k, const double *rest,
+                               const double *damping, uint32_t *first_id) {
+    if (!sim) return fail(nullptr, TITAN_E_INVALID, "sim is null");
+    BusyGuard bg(sim);
+    if (!bg.acquired) return fail(sim, TITAN_E_BUSY, "another call on this handle is in progress");
+    if (n && (!ends || !k)) return fail(sim, TITAN_E_INVALID, "ends and k are required");
+    const uint32_t n_tot = (uint32_t)sim->h_mass.size();
+    if ((uint64_t)sim->h_k.size() + n >= (1u << 30)) return fail(sim, TITAN_E_INVALID, "too many springs");
+    for (uint32_t q = 0; q < n; ++q) {
+        const uint32_t i = ends[2 * (size_t)q], j = ends[2 * (size_t)q + 1];
+        if (i >= n_tot || j >= n_tot || i == j) return fail(sim, TITAN_E_INVALID, "bad spring ends in addition " + std::to_string(q));
+        if (!(std::isfinite(k[q]) && k[q] >= 0)) return fail(sim, TITAN_E_INVALID, "k must be finite and >= 0");
+        if (rest && !(std::isfinite(rest[q]) && rest[q] >= 0)) return fail(sim, TITAN_E_INVALID, "rest must be finite and >= 0");
+        if (damping && !(std::isfinite(damping[q]) && damping[q] >= 0)) return fail(sim, TITAN_E_INVALID, "damping must be finite and >= 0");
+    }
+    if (first_id) *first_id = (uint32_t)sim->h_k.size();
+    for (uint32_t q = 0; q < n; ++q) {
+        sim->h_ends.push_back(ends[2 * (size_t)q]);
+        sim->h_ends.push_back(ends[2 * (size_t)q + 1]);
+        sim->h_k.push_back(k[q]);
+        sim->h_rest.push_back(rest ? rest[q] : NAN);
+        sim->h_damp.push_back(damping ? damping[q] : sim->params.damping);
+    }
+    if (n) sim->dirty = true;
+    return TITAN_OK;
+}
+
+titan_status titan_add_masses(titan_sim *sim, uint32_t n, const double *pos, const double *vel, const double *mass,
+                              const uint8_t *fixed, uint32_t *first_id) {
+    if (!sim) return fail(nullptr, TITAN_E_INVALID, "sim is null");
+    BusyGuard bg(sim);
+    if (!bg.acquired) return fail(sim, TITAN_E_BUSY, "another call on this handle is in progress");
+    if (n && (!pos || !mass)) return fail(sim, TITAN_E_INVALID, "pos and mass are required");
+    if ((uint64_t)sim->h_mass.size() + n >= (1u << 31)) return fail(sim, TITAN_E_INVALID, "too many masses");
+    for (uint64_t i = 0; i < n; ++i) {
+        if (!(std::isfinite(mass[i]) && mass[i] > 0)) return fail(sim, TITAN_E_INVALID, "mass must be finite and > 0");
+        for (int a = 0; a < 3; ++a)
+            if (!std::isfinite(pos[3 * i + a]) || (vel && !std::isfinite(vel[3 * i + a])))
+                return fail(sim, TITAN_E_INVALID, "non-finite pos or vel");
+    }
+    if (first_id) *first_id = (uint32_t)sim->h_mass.size();
+    for (uint64_t i = 0; i < n; ++i) {
+        sim->h_mass.push_back(mass[i]);
+        sim->h_fixed.push_back(fixed && fixed[i] ? 1 : 0);
+        for (int a = 0; a < 3; ++a) {
+            sim->pend_pos.push_back(pos[3 * i + a]);
+            sim->pend_vel.push_back(vel ? vel[3 * i + a] : 0.0);
+        }
+    }
+    if (n) sim->dirty = true;
+    return TITAN_OK;
+}
+
+titan_status titan_set_fixed(titan_sim *sim, uint32_t n, const uint32_t *ids, const uint8_t *fixed) {
+    if (!sim) return fail(nullptr, TITAN_E_INVALID, "sim is null");
+    BusyGuard bg(sim);
+    if (!bg.acquired) return fail(sim, TITAN_E_BUSY, "another call on this handle is in progress");
+    if (n && (!ids || !fixed)) return fail(sim, TITAN_E_INVALID, "ids and fixed are required");
+    const uint32_t n_tot = (uint32_t)sim->h_mass.size();
+    for (uint32_t q = 0; q < n; ++q)
+        if (ids[q] >= n_tot) return fail(sim, TITAN_E_INVALID, "mass id out of range: " + std::to_string(ids[q]));
+    DeviceGuard dg(sim->device);
+    std::vector<uint32_t> wi, wv;
+    for (uint32_t q = 0; q < n; ++q) {
+        const uint32_t i = ids[q];
+        sim->h_fixed[i] = fixed[q] ? 1 : 0;
+        if (i < sim->n) {
+            sim->inv_mass[i] = fixed[q] ? 0.f : (float)(1.0 / sim->h_mass[i]);
+            wi.push_back(8 * sim->dev_of_caller[i] + 3);     // MassState word 3 = p.w = 1/m
+            wv.push_back(fbits(sim->inv_mass[i]));
+        }
+    }
+    TITAN_CK(sim, patch_words(sim, sim->state[sim->cur], wi, wv));
+    return TITAN_OK;
+}
+
+titan_status titan_set_worm_actuation(titan_sim *sim, uint32_t n, const uint32_t *ids, const float *c,
+                                      const float *t_offset, float omega, float period) {
+    if (!sim) return fail(nullptr, TITAN_E_INVALID, "sim is null");
+    {
+        BusyGuard bg(sim);
+        if (!bg.acquired) return fail(sim, TITAN_E_BUSY, "another call on this handle is in progress");
+        if (n && (!ids || !c || !t_offset)) return fail(sim, TITAN_E_INVALID, "ids, c and t_offset are required");
+        if (!std::isfinite(omega) || !(period > 0) || !std::isfinite(period))
+            return fail(sim, TITAN_E_INVALID, "omega must be finite and period > 0");
+        titan_status es = titan::ensure_layout(sim);
+        if (es != TITAN_OK) return es;
+        for (uint32_t q = 0; q < n; ++q) {
+            if (ids[q] >= sim->s) return fail(sim, TITAN_E_INVALID, "spring id out of range: " + std::to_string(ids[q]));
+            if (!std::isfinite(c[q]) || !std::isfinite(t_offset[q])) return fail(sim, TITAN_E_INVALID, "non-finite c or t_offset");
+        }
+        DeviceGuard dg(sim->device);
+        if (sim->act_amp.empty() || sim->act_mode != 2) {
+            sim->act_amp.assign(sim->s, 0.f);
+            sim->act_phase.assign(sim->s, 0.f);
+        }
+        for (uint32_t q = 0; q < n; ++q) {
+            sim->act_amp[ids[q]] = c[q];
+            const double to = (double)t_offset[q];
+            sim->act_phase[ids[q]] = (float)(to - (double)period * std::floor(to / (double)period));   // in [0, t_p)
+        }
+        sim->c.act_mode = 2;
+        sim->c.worm_omega = omega;
+        sim->c.worm_period = period;
+        sim->act_mode = 2;
+        TITAN_CK(sim, upload_actuation(sim));
+        sim->has_act = true;
+        if (sim->csr_kernel == 5 && !choose_halo_width(sim)) sim->csr_kernel = 4;
+        free_graphs(sim);
+    }
+    return TITAN_OK;
 }
 
 }  // extern "C"

@@ -15,7 +15,10 @@ using titan::MassState;
 constexpr int kDefaultGraphChunk = 64;
 constexpr uint32_t kDefaultSpinLimit = 1u << 22;
 
-struct titan_sim {
+// Everything a simulation owns; titan_sim adds the per-handle lock and error
+// text.  A topology rebuild builds a fresh core and swaps it in, so the
+// caller's handle stays valid.
+struct SimCore {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -74,6 +77,19 @@ struct titan_sim {
     uint32_t *d_adj_spring = nullptr;     // adjoint: spring id per SELL entry (+ owner bit)
 
     std::vector<void *> allocations;
+
+    // host copies kept for topology edits (FP64, caller order)
+    titan_params params{};
+    std::vector<double> h_mass;
+    std::vector<uint8_t> h_fixed;
+    std::vector<uint32_t> h_ends;
+    std::vector<double> h_k, h_rest, h_damp;
+    bool dirty = false;                   // masses or springs were added: rebuild before next use
+    std::vector<double> pend_pos, pend_vel;   // initial state of masses added since the last rebuild
+    int act_mode = 0;                     // 0 none, 1 sinusoid, 2 worm (Eqs. 3-4)
+};
+
+struct titan_sim : SimCore {
     std::string error;
     std::atomic<bool> busy{false};
 };
@@ -82,4 +98,6 @@ namespace titan {
 // Enqueues one fused step reading state buffer b of the simulation (runtime.cu).
 cudaError_t enqueue_sim_step(titan_sim *sim, cudaStream_t st, int b);
 void set_thread_error(const std::string &msg);
+// Rebuilds the device layout if masses or springs were added (runtime.cu).
+titan_status ensure_layout(titan_sim *sim);
 }  // namespace titan

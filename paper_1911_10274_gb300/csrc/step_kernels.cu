@@ -43,7 +43,7 @@ k_step_sell(const MassState *__restrict__ in, MassState *__restrict__ out, uint3
     const uint32_t width = (__ldg(slice_off + sl + 1) - e0) >> 5;   // even, warp-uniform
     const float4 p = __ldg(&in[i].p);
     const float4 v = __ldg(&in[i].v);
-    const float ph = HAS_ACT ? clock_phase(c, step) : 0.f;
+    const float ph = HAS_ACT ? actuation_clock(c, step) : 0.f;
 
     float fx = 0.f, fy = 0.f, fz = 0.f;
     uint32_t e = e0 + lane;
@@ -55,8 +55,8 @@ k_step_sell(const MassState *__restrict__ in, MassState *__restrict__ out, uint3
         float L0 = a0.y, L1 = a1.y;
         if (HAS_ACT) {
             const float2 s0 = __ldcs(act + e), s1 = __ldcs(act + e + 32);
-            L0 = a0.y * (1.f + s0.x * sinf(ph + s0.y));
-            L1 = a1.y * (1.f + s1.x * sinf(ph + s1.y));
+            L0 = actuated_length(c, a0.y, s0, ph);
+            L1 = actuated_length(c, a1.y, s1, ph);
         }
         float4 q0, w0, q1, w1;
         load_state(in + j0, q0, w0);
@@ -101,7 +101,7 @@ k_step_sell_pf(const MassState *__restrict__ in, MassState *__restrict__ out, ui
 
     const float4 p = __ldg(&in[i].p);
     const float4 v = __ldg(&in[i].v);
-    const float ph = HAS_ACT ? clock_phase(c, step) : 0.f;
+    const float ph = HAS_ACT ? actuation_clock(c, step) : 0.f;
     float fx = 0.f, fy = 0.f, fz = 0.f;
     if (width) {
         uint32_t e = e0 + lane;
@@ -128,8 +128,8 @@ k_step_sell_pf(const MassState *__restrict__ in, MassState *__restrict__ out, ui
             }
             float L0 = a0.y, L1 = a1.y;
             if (HAS_ACT) {
-                L0 = a0.y * (1.f + s0.x * sinf(ph + s0.y));
-                L1 = a1.y * (1.f + s1.x * sinf(ph + s1.y));
+                L0 = actuated_length(c, a0.y, s0, ph);
+                L1 = actuated_length(c, a1.y, s1, ph);
             }
             spring_force(p, v, q0, w0, a0.x, L0, c0, fx, fy, fz);
             spring_force(p, v, q1, w1, a1.x, L1, c1, fx, fy, fz);
@@ -213,7 +213,7 @@ k_step_halo(const MassState *__restrict__ in, MassState *__restrict__ out, uint3
     __syncthreads();
     if (!valid) return;
 
-    const float ph = HAS_ACT ? clock_phase(c, step) : 0.f;
+    const float ph = HAS_ACT ? actuation_clock(c, step) : 0.f;
     float fx = 0.f, fy = 0.f, fz = 0.f;
     if (width) {
         uint32_t e = e0 + lane;
@@ -239,8 +239,8 @@ k_step_halo(const MassState *__restrict__ in, MassState *__restrict__ out, uint3
             const float2 qb0 = tB[j0], qb1 = tB[j1];
             float L0 = a0.y, L1 = a1.y;
             if (HAS_ACT) {
-                L0 = a0.y * (1.f + s0.x * sinf(ph + s0.y));
-                L1 = a1.y * (1.f + s1.x * sinf(ph + s1.y));
+                L0 = actuated_length(c, a0.y, s0, ph);
+                L1 = actuated_length(c, a1.y, s1, ph);
             }
             spring_force(p, v, qa0, make_float4(qa0.w, qb0.x, qb0.y, 0.f), a0.x, L0, c0, fx, fy, fz);
             spring_force(p, v, qa1, make_float4(qa1.w, qb1.x, qb1.y, 0.f), a1.x, L1, c1, fx, fy, fz);
@@ -345,7 +345,7 @@ k_step_halo_tma(const MassState *__restrict__ in, MassState *__restrict__ out, u
     }
     if (!valid) return;
 
-    const float ph = HAS_ACT ? clock_phase(c, step) : 0.f;
+    const float ph = HAS_ACT ? actuation_clock(c, step) : 0.f;
     float fx = 0.f, fy = 0.f, fz = 0.f;
     for (uint32_t t = 0; t < width; t += 2) {
         const uint32_t a = t * 32 + lane, bb = a + 32;
@@ -367,8 +367,8 @@ k_step_halo_tma(const MassState *__restrict__ in, MassState *__restrict__ out, u
         const float2 qa1 = tA[j1], qb1 = tB[j1], qc1 = tC[j1];
         float L0 = a0.y, L1 = a1.y;
         if (HAS_ACT) {
-            L0 = a0.y * (1.f + s0.x * sinf(ph + s0.y));
-            L1 = a1.y * (1.f + s1.x * sinf(ph + s1.y));
+            L0 = actuated_length(c, a0.y, s0, ph);
+            L1 = actuated_length(c, a1.y, s1, ph);
         }
         spring_force(p, v, make_float4(qa0.x, qa0.y, qb0.x, 0.f), make_float4(qb0.y, qc0.x, qc0.y, 0.f),
                      a0.x, L0, c0, fx, fy, fz);
@@ -460,7 +460,7 @@ k_step_sell_staged(const MassState *__restrict__ in, MassState *__restrict__ out
         p = __ldg(&in[i].p);
         v = __ldg(&in[i].v);
     }
-    const float ph = HAS_ACT ? clock_phase(c, step) : 0.f;
+    const float ph = HAS_ACT ? actuation_clock(c, step) : 0.f;
     float fx = 0.f, fy = 0.f, fz = 0.f;
 
     for (uint32_t ch = 0; ch < n_chunks; ++ch) {
@@ -493,8 +493,8 @@ k_step_sell_staged(const MassState *__restrict__ in, MassState *__restrict__ out
                 float L0 = a0.y, L1 = a1.y;
                 if (HAS_ACT) {
                     const float2 s0 = st_act(s)[a], s1 = st_act(s)[b];
-                    L0 = a0.y * (1.f + s0.x * sinf(ph + s0.y));
-                    L1 = a1.y * (1.f + s1.x * sinf(ph + s1.y));
+                    L0 = actuated_length(c, a0.y, s0, ph);
+                    L1 = actuated_length(c, a1.y, s1, ph);
                 }
                 float4 q0, w0, q1, w1;
                 load_state(in + j0, q0, w0);
@@ -527,7 +527,7 @@ k_springs_atomic(const MassState *__restrict__ in, const uint4 *__restrict__ rec
     float L = __uint_as_float(r.w);
     if (HAS_ACT) {
         const float2 a = __ldcs(act + s);
-        L = L * (1.f + a.x * sinf(clock_phase(c, *step_in) + a.y));
+        L = actuated_length(c, L, a, actuation_clock(c, *step_in));
     }
     const float cs = HAS_C ? __ldcs(cc + s) : c.c_uniform;
     float4 p, v, q, w;
@@ -715,6 +715,19 @@ cudaError_t launch_step_atomic(const MassState *in, MassState *out, uint32_t n,
         k_masses_atomic<true><<<g, kThreads, 0, stream>>>(in, out, v.force, n, c, step_in, step_out);
     else
         k_masses_atomic<false><<<g, kThreads, 0, stream>>>(in, out, v.force, n, c, step_in, step_out);
+    return cudaGetLastError();
+}
+
+__global__ void k_patch_words(uint32_t *__restrict__ base, const uint32_t *__restrict__ idx,
+                              const uint32_t *__restrict__ val, uint32_t n) {
+    const uint32_t i = blockIdx.x * kThreads + threadIdx.x;
+    if (i < n) base[idx[i]] = val[i];
+}
+
+cudaError_t launch_patch_words(uint32_t *base, const uint32_t *idx, const uint32_t *val, uint32_t n,
+                               cudaStream_t stream) {
+    if (!n) return cudaSuccess;
+    k_patch_words<<<blocks_for(n), kThreads, 0, stream>>>(base, idx, val, n);
     return cudaGetLastError();
 }
 

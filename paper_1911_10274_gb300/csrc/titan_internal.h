@@ -38,6 +38,9 @@ struct StepConst {
     int32_t ground;
     double act_omega;     // 2 pi f (rad/s) of the sinusoidal actuation
     double dt_d;          // dt in FP64 for the phase of the actuation clock
+    int32_t act_mode;     // 1: L0 (1 + A sin(2 pi f t + phi)); 2: worm, L0 (1 + c sin(w tau))
+    float worm_omega;     // mode 2: w (rad/s)
+    double worm_period;   // mode 2: t_p (s); per-spring offsets are stored reduced to [0, t_p)
 };
 
 struct SellView {
@@ -90,6 +93,10 @@ size_t halo_tma_smem_bytes(uint32_t table_slots, uint32_t w_max, bool has_c, boo
 cudaError_t launch_step_atomic(const MassState *in, MassState *out, uint32_t n,
                                const AtomicView &v, const StepConst &c, const long long *step_in,
                                long long *step_out, cudaStream_t stream);
+
+// base[idx[k]] = val[k] for 32-bit words (in-place parameter edits).
+cudaError_t launch_patch_words(uint32_t *base, const uint32_t *idx, const uint32_t *val, uint32_t n,
+                               cudaStream_t stream);
 
 // Gathers device-order state into caller order: pos/vel [n][3] float.
 cudaError_t launch_unpermute(const MassState *state, const uint32_t *dev_of_caller, uint32_t n,

@@ -86,6 +86,12 @@ def load(path: Optional[str] = None):
                 "titan_step_atomic_noalloc": (S, [u32, _P, _P, _P, u32, _P, _P, _P, f32,
                                                   C.POINTER(titan_params), _P, _P, _P]),
                 "titan_set_step": (S, [_P, u64]),
+                "titan_set_worm_actuation": (S, [_P, u32, _P, _P, _P, f32, f32]),
+                "titan_set_spring_params": (S, [_P, u32, _P, _P, _P, _P]),
+                "titan_remove_springs": (S, [_P, u32, _P]),
+                "titan_add_springs": (S, [_P, u32, _P, _P, _P, _P, C.POINTER(u32)]),
+                "titan_add_masses": (S, [_P, u32, _P, _P, _P, _P, C.POINTER(u32)]),
+                "titan_set_fixed": (S, [_P, u32, _P, _P]),
                 "titan_adjoint": (S, [_P, u64, u32, _P, _P, _P, _P]),
                 "titan_gemm_bf16_tn": (S, [u32, u32, u32, _P, _P, _P, _P]),
                 "titan_mlp_create": (S, [u32, u32, u64, C.c_int32, _P, C.POINTER(_P)]),
@@ -185,6 +191,54 @@ def titan_set_state(sim: int, pos, vel=None) -> None:
 
 def titan_read_state_dev(sim: int, pos_dev=None, vel_dev=None, stream: Optional[int] = None) -> None:
     _check(load().titan_read_state_dev(sim, _ptr(pos_dev), _ptr(vel_dev), stream), sim)
+
+
+def _u32(a):
+    return np.ascontiguousarray(a, dtype=np.uint32)
+
+
+def _f64opt(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def titan_set_worm_actuation(sim: int, spring_ids, c, t_offset, omega: float, period: float) -> None:
+    ids, cc = _u32(spring_ids), np.ascontiguousarray(c, np.float32)
+    to = np.ascontiguousarray(t_offset, np.float32)
+    _check(load().titan_set_worm_actuation(sim, ids.size, _ptr(ids), _ptr(cc), _ptr(to), float(omega), float(period)), sim)
+
+
+def titan_set_spring_params(sim: int, spring_ids, k=None, rest=None, damping=None) -> None:
+    ids = _u32(spring_ids)
+    k, rest, damping = _f64opt(k), _f64opt(rest), _f64opt(damping)
+    _check(load().titan_set_spring_params(sim, ids.size, _ptr(ids), _ptr(k), _ptr(rest), _ptr(damping)), sim)
+
+
+def titan_remove_springs(sim: int, spring_ids) -> None:
+    ids = _u32(spring_ids)
+    _check(load().titan_remove_springs(sim, ids.size, _ptr(ids)), sim)
+
+
+def titan_add_springs(sim: int, ends, k, rest=None, damping=None) -> int:
+    e = _u32(ends).reshape(-1)
+    k, rest, damping = _f64opt(k), _f64opt(rest), _f64opt(damping)
+    first = C.c_uint32()
+    _check(load().titan_add_springs(sim, e.size // 2, _ptr(e), _ptr(k), _ptr(rest), _ptr(damping), C.byref(first)), sim)
+    return first.value
+
+
+def titan_add_masses(sim: int, pos, mass, vel=None, fixed=None) -> int:
+    p, m = _f64opt(pos).reshape(-1), _f64opt(mass)
+    v = None if vel is None else _f64opt(vel).reshape(-1)
+    f = None if fixed is None else np.ascontiguousarray(fixed, np.uint8)
+    first = C.c_uint32()
+    _check(load().titan_add_masses(sim, m.size, _ptr(p), _ptr(v), _ptr(m), _ptr(f), C.byref(first)), sim)
+    return first.value
+
+
+def titan_set_fixed(sim: int, mass_ids, fixed) -> None:
+    ids = _u32(mass_ids)
+    f = np.ascontiguousarray(fixed, np.uint8)
+    _check(load().titan_set_fixed(sim, ids.size, _ptr(ids), _ptr(f)), sim)
 
 
 def titan_set_step(sim: int, step: int) -> None:
@@ -379,7 +433,18 @@ class Sim:
 
     def snapshot(self):
         """(pos, vel, t) after every step enqueued so far (float32, caller order)."""
-        return titan_snapshot_wait(self.handle, titan_snapshot_async(self.handle), self.n)
+        t = titan_snapshot_async(self.handle)          # first: a pending rebuild changes n
+        return titan_snapshot_wait(self.handle, t, self.n)
+
+    def add_masses(self, pos, mass, vel=None, fixed=None) -> int:
+        first = titan_add_masses(self.handle, pos, mass, vel, fixed)
+        self.n += int(np.asarray(mass).size)
+        return first
+
+    def add_springs(self, ends, k, rest=None, damping=None) -> int:
+        first = titan_add_springs(self.handle, ends, k, rest, damping)
+        self.s += int(np.asarray(ends).size // 2)
+        return first
 
     def set_state(self, pos, vel=None) -> None:
         titan_set_state(self.handle, pos, vel)
