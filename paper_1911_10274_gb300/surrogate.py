@@ -60,6 +60,24 @@ def encode(morphs: List[Morph]) -> np.ndarray:
     return X
 
 
+def mirrored(morphs: List[Morph], y: np.ndarray):
+    """Exact symmetries of the task: reflecting a robot through x -> -x negates
+    its centroid x-displacement (ground, gravity and friction are symmetric);
+    reflecting y -> -y leaves it unchanged.  Returns the 4x augmented set."""
+    out_m, out_y = [], []
+    for m, f in zip(morphs, y):
+        for fx in (False, True):
+            for fy in (False, True):
+                occ, ph = m.occ, m.phase
+                if fx:
+                    occ, ph = occ[:, :, ::-1], ph[:, :, ::-1]
+                if fy:
+                    occ, ph = occ[:, ::-1, :], ph[:, ::-1, :]
+                out_m.append(Morph(occ=np.ascontiguousarray(occ), phase=np.ascontiguousarray(ph)))
+                out_y.append(-f if fx else f)
+    return out_m, np.array(out_y)
+
+
 def fitness(morphs: List[Morph], steps: int, freq: float = 2.0, chunk: int = 4096,
             device: int = 0) -> np.ndarray:
     """Centroid x-displacement of each robot after `steps` steps (simulated)."""
