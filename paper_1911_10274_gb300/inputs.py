@@ -240,8 +240,11 @@ def voxel_robot(occ: np.ndarray, phase_grid: np.ndarray, spacing: float = 0.1, m
                 k: float = 1e4, damping: float = 1.0, amp: float = 0.1, freq: float = 2.0) -> System:
     """Robot with one mass per occupied voxel and 26-neighbourhood springs.
 
-    Every spring is actuated with amplitude ``amp``; its phase is the phase of
-    its lower-linear-index voxel (phase_grid is (nz, ny, nx), radians).
+    Each voxel v carries an actuation signal amp sin(2 pi f t + phi_v)
+    (phase_grid is (nz, ny, nx), radians); a spring carries the mean of its two
+    voxels' signals, amp cos((phi_i - phi_j) / 2) sin(2 pi f t + (phi_i +
+    phi_j) / 2), so the rule does not depend on how voxels are numbered and a
+    mirrored robot gets mirrored springs.
     """
     nz, ny, nx = occ.shape
     full_pos = lattice_points(nx, ny, nz, spacing)
@@ -253,13 +256,13 @@ def voxel_robot(occ: np.ndarray, phase_grid: np.ndarray, spacing: float = 0.1, m
     pos = full_pos[keep]
     pos[:, 2] -= pos[:, 2].min()
     s = ends.shape[0]
-    lower = np.minimum(ends_full[:, 0], ends_full[:, 1]).astype(np.int64)
-    phase = phase_grid.ravel()[lower].astype(np.float64)
+    pi_ = phase_grid.ravel()[ends_full[:, 0].astype(np.int64)].astype(np.float64)
+    pj_ = phase_grid.ravel()[ends_full[:, 1].astype(np.int64)].astype(np.float64)
     return System(pos=pos, vel=np.zeros_like(pos), mass=np.full(keep.size, mass),
                   fixed=np.zeros(keep.size, np.uint8), ends=ends, k=np.full(s, k),
                   rest=_initial_lengths(pos, ends), damping=np.full(s, damping), dt=1e-4,
-                  ground=True, ground_k=1e5, mu=0.5, act_amp=np.full(s, amp), act_phase=phase,
-                  act_freq=freq, spacing=spacing, name="voxel_robot")
+                  ground=True, ground_k=1e5, mu=0.5, act_amp=amp * np.cos(0.5 * (pi_ - pj_)),
+                  act_phase=0.5 * (pi_ + pj_), act_freq=freq, spacing=spacing, name="voxel_robot")
 
 
 def two_masses(stretch: float = 1e-3, k: float = 1e4, m: float = 0.1, c: float = 0.0,
