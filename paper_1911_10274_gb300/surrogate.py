@@ -16,7 +16,10 @@ simulation.  This module closes that loop on the GPU:
 * search: a (mu + lambda) mutation search.  The plain form simulates every
   mutant; the screened form lets the surrogate rank all mutants and simulates
   only the top few, whose simulated fitness (the simulator remains the judge)
-  decides who survives.  A random pick of the same size is the ablation.
+  decides who survives; those simulated mutants also refine the network
+  (online fine-tuning on everything simulated so far, mirror-augmented),
+  because a network trained only on random robots ranks nearby mutants
+  poorly.  A random pick of the same size is the ablation.
 
 Python here only orchestrates: every rollout and every network product runs
 in the library's kernels.
@@ -147,6 +150,25 @@ class Surrogate:
             hist.append(float(loss))
         return hist
 
+    def refine(self, X: np.ndarray, y: np.ndarray, epochs: int = 3, batch: int = 1024, lr: float = 5e-4,
+               seed: int = 0) -> None:
+        """Continues training on (X, y) keeping the target standardisation."""
+        torch = self.torch
+        n = (len(X) // 128) * 128
+        if n == 0:
+            return
+        batch = max(128, min(batch, n) - min(batch, n) % 128)
+        rng = np.random.default_rng(seed)
+        Xd = self._x(X)
+        yd = torch.as_tensor((y - self.mu) / self.sd, dtype=torch.float32, device=f"cuda:{self.device}")
+        loss = torch.empty(1, device=f"cuda:{self.device}")
+        for _ in range(epochs):
+            perm = torch.as_tensor(rng.permutation(len(X)), device=f"cuda:{self.device}")
+            for s in range(0, n - batch + 1, batch):
+                idx = perm[s:s + batch]
+                self.net.train_step(Xd[idx].contiguous(), yd[idx].contiguous(), lr, loss)
+        self.net.sync()
+
     def predict(self, X: np.ndarray) -> np.ndarray:
         torch = self.torch
         n = len(X)
@@ -166,7 +188,7 @@ def spearman(a, b) -> float:
 
 def search(mode: str, start: List[Morph], start_fit: np.ndarray, generations: int, mutants: int, screened: int,
            steps: int, seed: int = 0, surrogate: Optional[Surrogate] = None, parents: int = 16,
-           freq: float = 2.0) -> dict:
+           freq: float = 2.0, refine_epochs: int = 2) -> dict:
     """(mu + lambda) search from a simulated starting population.
 
     mode 'plain': simulate all mutants; 'surrogate': simulate the `screened`
@@ -179,6 +201,7 @@ def search(mode: str, start: List[Morph], start_fit: np.ndarray, generations: in
     pop_fit = start_fit[order].copy()
     best, used, hist = float(pop_fit[0]), 0, []
     pred_corr = []
+    seen_m, seen_f = list(start), np.asarray(start_fit, np.float64)
     for g in range(generations):
         kids = [mutate(rng, pop[k % len(pop)]) for k in range(mutants)]
         if mode == "plain":
@@ -193,6 +216,10 @@ def search(mode: str, start: List[Morph], start_fit: np.ndarray, generations: in
         used += len(chosen)
         if mode == "surrogate":
             pred_corr.append(spearman(pred[top], f))
+            seen_m += chosen
+            seen_f = np.concatenate([seen_f, f])
+            am, af = mirrored(seen_m, seen_f)
+            surrogate.refine(encode(am), af, epochs=refine_epochs, seed=g)
         allm = pop + chosen
         allf = np.concatenate([pop_fit, f])
         keep = np.argsort(-allf)[:parents]
@@ -222,7 +249,7 @@ def main(argv=None):
     ap.add_argument("--generations", type=int, default=100)
     ap.add_argument("--mutants", type=int, default=1024)
     ap.add_argument("--screened", type=int, default=64)
-    ap.add_argument("--epochs", type=int, default=20)
+    ap.add_argument("--epochs", type=int, default=4)
     ap.add_argument("--seed", type=int, default=0)
     a = ap.parse_args(argv)
     rng = np.random.default_rng(a.seed)
@@ -234,7 +261,8 @@ def main(argv=None):
     n_val = max(128, a.train // 10)
     sur = Surrogate(seed=a.seed)
     t1 = time.time()
-    sur.fit(X[:-n_val], y[:-n_val], epochs=a.epochs)
+    am, ay = mirrored(morphs[:-n_val], y[:-n_val])
+    sur.fit(encode(am), ay, epochs=a.epochs)
     t_fit = time.time() - t1
     val_corr = spearman(sur.predict(X[-n_val:]), y[-n_val:])
     start = morphs[-n_val:]

@@ -103,7 +103,10 @@ def test_worm_actuation_matches_oracle():
                         fixed=np.zeros(len(pos), np.uint8), ends=ends, k=np.full(s, 1e4),
                         rest=np.linalg.norm(pos[ends[:, 1]] - pos[ends[:, 0]], axis=1),
                         damping=np.full(s, 1.0), dt=1e-4, ground=True, spacing=0.1)
-    t_o = np.minimum(pos[ends[:, 0], 0], pos[ends[:, 1], 0]) - pos[:, 0].min()
+    # Eq. 5 offsets are multiples of 0.1 s, i.e. of dt: the printed formula then
+    # wraps tau (a jump in rest length) exactly at step boundaries, where FP32
+    # and FP64 may land on opposite sides; half a step moves every wrap inside a step
+    t_o = np.minimum(pos[ends[:, 0], 0], pos[ends[:, 1], 0]) - pos[:, 0].min() + 0.5e-4
     sys.act_amp, sys.act_phase = np.full(s, 0.2), t_o
     xo, _ = oracle.run(sys, 2000, act_mode=2, worm=(20.0, 1.0))
     plain = sys.copy()
