@@ -305,9 +305,16 @@ titan_status titan_batch_create(uint32_t n_systems, const titan_masses *masses,
  * without waiting.  The actuation clock continues across rollouts. */
 titan_status titan_batch_rollout(titan_batch *b, uint64_t n_steps);
 
-/* Times each launch group with 128, 256 and 512 threads per CTA over a
- * probe_steps rollout (0: 50) and keeps the fastest.  The state is unchanged. */
+/* The autotuner: times each launch group with 128, 256 and 512 threads per
+ * CTA and 1, 2 or 4 threads per mass (a mass's springs split over that many
+ * threads) over a probe_steps rollout (0: 50) and keeps the fastest pair.
+ * The state is unchanged. */
 titan_status titan_batch_autotune(titan_batch *b, uint32_t probe_steps);
+
+/* Sets a launch group's shape by hand: threads per CTA (a multiple of 32,
+ * up to 512) and threads per mass (1, 2 or 4).  Errors: TITAN_E_INVALID. */
+titan_status titan_batch_configure(titan_batch *b, uint32_t group, uint32_t threads,
+                                   uint32_t threads_per_mass);
 
 /* Restores every system's initial state and the step counter to 0. */
 titan_status titan_batch_reset(titan_batch *b);
@@ -324,10 +331,10 @@ titan_status titan_batch_read(titan_batch *b, uint32_t system, float *pos, float
 titan_status titan_batch_centroids(titan_batch *b, float *out);
 
 /* Number of launch groups (one per cluster size) and, per group, its cluster
- * size, threads per CTA and CTA count. */
+ * size, threads per CTA, threads per mass and CTA count (outputs may be NULL). */
 uint32_t titan_batch_groups(const titan_batch *b);
 titan_status titan_batch_info(const titan_batch *b, uint32_t group, uint32_t *cluster,
-                              uint32_t *threads, uint32_t *ctas);
+                              uint32_t *threads, uint32_t *threads_per_mass, uint32_t *ctas);
 
 /* Text of the last error on this batch ("" if none). */
 const char *titan_batch_last_error(const titan_batch *b);

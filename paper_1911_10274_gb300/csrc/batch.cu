@@ -74,7 +74,13 @@ __host__ __device__ inline SmemLayout smem_layout(uint32_t slots, uint32_t n_sli
     return L;
 }
 
-template <bool ACT, bool GROUND>
+// TPM threads share one mass: thread `sub` of the group takes columns sub,
+// sub + TPM, ... of the mass's SELL row and the partial forces are combined
+// with a fixed shuffle tree (deterministic for a given TPM).  Actuation is
+// stored per half-edge as (A cos phi, A sin phi), so the rest length needs no
+// sine in the loop: sin(w t + phi) = sin(w t) cos(phi) + cos(w t) sin(phi),
+// with sin(w t), cos(w t) formed once per thread and step.
+template <bool ACT, bool GROUND, int TPM>
 __global__ void __launch_bounds__(512)
 k_batch_rollout(const CtaDesc *__restrict__ ctas, const MassState *__restrict__ state_in,
                 MassState *__restrict__ state_out, const uint32_t *__restrict__ slice_rel,
@@ -120,34 +126,52 @@ k_batch_rollout(const CtaDesc *__restrict__ ctas, const MassState *__restrict__ 
     const uint32_t my_rank = cluster_size > 1 ? cluster.block_rank() : 0;
     if (cluster_size > 1) cluster.sync();       // all CTAs' shared memory is loaded and alive
 
+    const uint32_t sub = tid % TPM;
+    const uint32_t per_pass = blockDim.x / TPM;
+    const uint32_t passes = (d.slot_count + per_pass - 1) / per_pass;   // CTA-uniform
     int cur = 0;
     for (uint32_t k = 0; k < n_steps; ++k) {
-        const float ph = ACT ? titan::clock_phase(c, step0 + (long long)k) : 0.f;
+        float sp = 0.f, cp = 1.f;
+        if (ACT) sincosf(titan::clock_phase(c, step0 + (long long)k), &sp, &cp);
         const MassState *src = st[cur];
         MassState *dst = st[cur ^ 1];
-        for (uint32_t m = tid; ok && m < d.slot_count; m += blockDim.x) {
-            const uint32_t slice = m >> 5, lane = m & 31;
-            const float4 p = src[m].p, v = src[m].v;
-            const uint32_t e0 = s_slice[slice];
-            const uint32_t width = (s_slice[slice + 1] - e0) >> 5;
+        for (uint32_t pass = 0; ok && pass < passes; ++pass) {
+            const uint32_t m = pass * per_pass + tid / TPM;
+            const bool live = m < d.slot_count;
             float fx = 0.f, fy = 0.f, fz = 0.f;
-            for (uint32_t t = 0; t < width; ++t) {
-                const uint32_t e = e0 + t * 32 + lane;
-                const uint32_t code = s_nbr[e];
-                const uint32_t rank = code >> kRankShift, local = code & (kMaxPerCta - 1);
-                const MassState *q = src + local;
-                if (rank != my_rank) q = cluster.map_shared_rank(q, rank);
-                const float4 qp = q->p, qv = q->v;
-                const float2 a = s_kl[e];
-                float L0 = a.y;
-                if (ACT) {
-                    const float2 s = s_act[e];
-                    L0 = a.y * (1.f + s.x * sinf(ph + s.y));
+            float4 p = make_float4(0.f, 0.f, 0.f, 0.f), v = p;
+            if (live) {
+                const uint32_t slice = m >> 5, lane = m & 31;
+                p = src[m].p;
+                v = src[m].v;
+                const uint32_t e0 = s_slice[slice];
+                const uint32_t width = (s_slice[slice + 1] - e0) >> 5;
+                for (uint32_t t = sub; t < width; t += TPM) {
+                    const uint32_t e = e0 + t * 32 + lane;
+                    const uint32_t code = s_nbr[e];
+                    const uint32_t rank = code >> kRankShift, local = code & (kMaxPerCta - 1);
+                    const MassState *q = src + local;
+                    if (rank != my_rank) q = cluster.map_shared_rank(q, rank);
+                    const float4 qp = q->p, qv = q->v;
+                    const float2 a = s_kl[e];
+                    float L0 = a.y;
+                    if (ACT) {
+                        const float2 s = s_act[e];               // (A cos phi, A sin phi)
+                        L0 = a.y + a.y * (s.x * sp + s.y * cp);
+                    }
+                    titan::spring_force(p, v, qp, qv, a.x, L0, c.c_uniform, fx, fy, fz);
                 }
-                titan::spring_force(p, v, qp, qv, a.x, L0, c.c_uniform, fx, fy, fz);
             }
-            if (m < d.mass_count) titan::integrate<GROUND>(p, v, fx, fy, fz, c, dst + m);
-            else dst[m] = src[m];
+#pragma unroll
+            for (int o = 1; o < TPM; o <<= 1) {
+                fx += __shfl_xor_sync(0xffffffffu, fx, o);
+                fy += __shfl_xor_sync(0xffffffffu, fy, o);
+                fz += __shfl_xor_sync(0xffffffffu, fz, o);
+            }
+            if (live && sub == 0) {
+                if (m < d.mass_count) titan::integrate<GROUND>(p, v, fx, fy, fz, c, dst + m);
+                else dst[m] = src[m];
+            }
         }
         if (cluster_size > 1) cluster.sync();
         else __syncthreads();
@@ -176,6 +200,7 @@ __global__ void k_batch_centroid(const uint32_t *__restrict__ mass_off, const ui
 struct Group {
     uint32_t cluster = 1;
     uint32_t threads = 256;
+    uint32_t tpm = 1;            // threads per mass
     uint32_t cta_first = 0, cta_count = 0;
     size_t smem = 0;
 };
@@ -281,8 +306,11 @@ cudaError_t launch_group(titan_batch *b, const Group &g, cudaStream_t st, long l
     MassState *out = b->d_state[b->cur ^ 1];
     void (*kern)(const CtaDesc *, const MassState *, MassState *, const uint32_t *, const float2 *,
                  const float2 *, const uint16_t *, titan::StepConst, long long, uint32_t, uint32_t, uint32_t, int *);
-    if (b->has_act) kern = b->c.ground ? k_batch_rollout<true, true> : k_batch_rollout<true, false>;
-    else kern = b->c.ground ? k_batch_rollout<false, true> : k_batch_rollout<false, false>;
+#define PICK(T)                                                                                   \
+    if (b->has_act) kern = b->c.ground ? k_batch_rollout<true, true, T> : k_batch_rollout<true, false, T>; \
+    else kern = b->c.ground ? k_batch_rollout<false, true, T> : k_batch_rollout<false, false, T>;
+    if (g.tpm == 4) { PICK(4) } else if (g.tpm == 2) { PICK(2) } else { PICK(1) }
+#undef PICK
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
     if (e != cudaSuccess) return e;
     return cudaLaunchKernelEx(&cfg, kern, ctas, in, out, (const uint32_t *)b->d_slice, (const float2 *)b->d_kl,
@@ -457,7 +485,9 @@ titan_status titan_batch_create(uint32_t n_systems, const titan_masses *masses, 
                                 L = std::sqrt(d2);
                             }
                             h.kl[e] = make_float2((float)s.k[q2], (float)L);
-                            if (any_act && act[r].amp) h.act[e] = make_float2((float)act[r].amp[q2], (float)act[r].phase[q2]);
+                            if (any_act && act[r].amp)
+                                h.act[e] = make_float2((float)(act[r].amp[q2] * std::cos(act[r].phase[q2])),
+                                                       (float)(act[r].amp[q2] * std::sin(act[r].phase[q2])));
                         } else {
                             const uint32_t self = std::min(i, m.n - 1);   // zero-parameter padding
                             h.nbr[e] = (uint16_t)(((self / per) << kRankShift) | (self % per));
@@ -660,23 +690,27 @@ titan_status titan_batch_autotune(titan_batch *b, uint32_t probe_steps) {
     cudaEvent_t e0, e1;
     BATCH_CK(b, cudaEventCreate(&e0));
     BATCH_CK(b, cudaEventCreate(&e1));
-    const int cand[3] = {128, 256, 512};
+    const int cand_t[3] = {128, 256, 512};
+    const int cand_m[3] = {1, 2, 4};
     for (auto &grp : b->groups) {
         float best = INFINITY;
-        uint32_t best_t = grp.threads;
-        for (int t : cand) {
-            grp.threads = (uint32_t)t;
-            float ms = 0;
-            for (int rep = 0; rep < 2; ++rep) {   // first repetition warms up
-                BATCH_CK(b, cudaEventRecord(e0, b->stream));
-                BATCH_CK(b, launch_group(b, grp, b->stream, 0, probe_steps));
-                BATCH_CK(b, cudaEventRecord(e1, b->stream));
-                BATCH_CK(b, cudaEventSynchronize(e1));
-                BATCH_CK(b, cudaEventElapsedTime(&ms, e0, e1));
+        uint32_t best_t = grp.threads, best_m = grp.tpm;
+        for (int t : cand_t)
+            for (int mm : cand_m) {
+                grp.threads = (uint32_t)t;
+                grp.tpm = (uint32_t)mm;
+                float ms = 0;
+                for (int rep = 0; rep < 2; ++rep) {   // first repetition warms up
+                    BATCH_CK(b, cudaEventRecord(e0, b->stream));
+                    BATCH_CK(b, launch_group(b, grp, b->stream, 0, probe_steps));
+                    BATCH_CK(b, cudaEventRecord(e1, b->stream));
+                    BATCH_CK(b, cudaEventSynchronize(e1));
+                    BATCH_CK(b, cudaEventElapsedTime(&ms, e0, e1));
+                }
+                if (ms < best) { best = ms; best_t = (uint32_t)t; best_m = (uint32_t)mm; }
             }
-            if (ms < best) { best = ms; best_t = (uint32_t)t; }
-        }
         grp.threads = best_t;
+        grp.tpm = best_m;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -686,11 +720,22 @@ titan_status titan_batch_autotune(titan_batch *b, uint32_t probe_steps) {
 }
 
 titan_status titan_batch_info(const titan_batch *b, uint32_t group, uint32_t *cluster, uint32_t *threads,
-                              uint32_t *ctas) {
+                              uint32_t *threads_per_mass, uint32_t *ctas) {
     if (!b || group >= b->groups.size()) return TITAN_E_INVALID;
     if (cluster) *cluster = b->groups[group].cluster;
     if (threads) *threads = b->groups[group].threads;
+    if (threads_per_mass) *threads_per_mass = b->groups[group].tpm;
     if (ctas) *ctas = b->groups[group].cta_count;
+    return TITAN_OK;
+}
+
+titan_status titan_batch_configure(titan_batch *b, uint32_t group, uint32_t threads, uint32_t threads_per_mass) {
+    if (!b || group >= b->groups.size()) return bfail(b, TITAN_E_INVALID, "batch is null or group out of range");
+    if (threads < 32 || threads > 512 || threads % 32 || !(threads_per_mass == 1 || threads_per_mass == 2 || threads_per_mass == 4))
+        return bfail(b, TITAN_E_INVALID, "threads must be a multiple of 32 in [32, 512] and threads_per_mass 1, 2 or 4");
+    b->groups[group].threads = threads;
+    b->groups[group].tpm = threads_per_mass;
+    if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
     return TITAN_OK;
 }
 

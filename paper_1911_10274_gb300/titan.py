@@ -114,7 +114,8 @@ def load(path: Optional[str] = None):
                 "titan_batch_read": (S, [_P, u32, _P, _P]),
                 "titan_batch_centroids": (S, [_P, _P]),
                 "titan_batch_groups": (u32, [_P]),
-                "titan_batch_info": (S, [_P, u32, C.POINTER(u32), C.POINTER(u32), C.POINTER(u32)]),
+                "titan_batch_configure": (S, [_P, u32, u32, u32]),
+                "titan_batch_info": (S, [_P, u32, C.POINTER(u32), C.POINTER(u32), C.POINTER(u32), C.POINTER(u32)]),
                 "titan_batch_last_error": (C.c_char_p, [_P]),
                 "titan_batch_destroy": (S, [_P]),
             }
@@ -360,13 +361,17 @@ class Batch:
         _bcheck(load().titan_batch_centroids(self.handle, _ptr(out)), self.handle)
         return out
 
+    def configure(self, group: int, threads: int, threads_per_mass: int) -> None:
+        _bcheck(load().titan_batch_configure(self.handle, group, threads, threads_per_mass), self.handle)
+
     def groups(self):
         lib = load()
         res = []
         for g in range(lib.titan_batch_groups(self.handle)):
-            cl, th, ct = C.c_uint32(), C.c_uint32(), C.c_uint32()
-            _bcheck(lib.titan_batch_info(self.handle, g, C.byref(cl), C.byref(th), C.byref(ct)), self.handle)
-            res.append(dict(cluster=cl.value, threads=th.value, ctas=ct.value))
+            cl, th, tm, ct = C.c_uint32(), C.c_uint32(), C.c_uint32(), C.c_uint32()
+            _bcheck(lib.titan_batch_info(self.handle, g, C.byref(cl), C.byref(th), C.byref(tm), C.byref(ct)),
+                    self.handle)
+            res.append(dict(cluster=cl.value, threads=th.value, threads_per_mass=tm.value, ctas=ct.value))
         return res
 
     def close(self) -> None:
