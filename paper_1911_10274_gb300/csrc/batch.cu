@@ -150,9 +150,15 @@ k_batch_rollout(const CtaDesc *__restrict__ ctas, const MassState *__restrict__ 
                     const uint32_t e = e0 + t * 32 + lane;
                     const uint32_t code = s_nbr[e];
                     const uint32_t rank = code >> kRankShift, local = code & (kMaxPerCta - 1);
-                    const MassState *q = src + local;
-                    if (rank != my_rank) q = cluster.map_shared_rank(q, rank);
-                    const float4 qp = q->p, qv = q->v;
+                    float4 qp, qv;
+                    if (rank == my_rank) {              // own shared memory: plain shared loads
+                        qp = src[local].p;
+                        qv = src[local].v;
+                    } else {                            // another CTA of the cluster (DSMEM)
+                        const MassState *q = cluster.map_shared_rank(src + local, rank);
+                        qp = q->p;
+                        qv = q->v;
+                    }
                     const float2 a = s_kl[e];
                     float L0 = a.y;
                     if (ACT) {
