@@ -55,18 +55,24 @@ struct CtaDesc {
     uint32_t robot;
 };
 
-// Shared-memory layout of one CTA (byte offsets; all 16-byte aligned).
+// Shared-memory layout of one CTA (byte offsets; all 16-byte aligned).  The
+// state is split per slot into (x, y, z, vx) float4 and (vy, vz) float2 arrays
+// (two buffers) plus 1/m: 16-byte loads at a 16-byte stride keep consecutive
+// slots in distinct banks (a 32-byte record read in two halves cannot).
 struct SmemLayout {
-    uint32_t state0, state1, slices, kl, act, nbr, total;
+    uint32_t a0, b0, a1, b1, inv, slices, kl, act, nbr, total;
 };
 
 __host__ __device__ inline uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
 
 __host__ __device__ inline SmemLayout smem_layout(uint32_t slots, uint32_t n_slices, uint32_t edges, bool act) {
     SmemLayout L;
-    L.state0 = 0;
-    L.state1 = slots * 32;
-    L.slices = 2 * slots * 32;
+    L.a0 = 0;
+    L.b0 = L.a0 + slots * 16;
+    L.a1 = L.b0 + slots * 8;
+    L.b1 = L.a1 + slots * 16;
+    L.inv = L.b1 + slots * 8;
+    L.slices = align16(L.inv + slots * 4);
     L.kl = align16(L.slices + 4 * ((n_slices + 1 + 3) & ~3u));
     L.act = L.kl + edges * 8;
     L.nbr = L.act + (act ? edges * 8 : 0);
@@ -74,12 +80,6 @@ __host__ __device__ inline SmemLayout smem_layout(uint32_t slots, uint32_t n_sli
     return L;
 }
 
-// TPM threads share one mass: thread `sub` of the group takes columns sub,
-// sub + TPM, ... of the mass's SELL row and the partial forces are combined
-// with a fixed shuffle tree (deterministic for a given TPM).  Actuation is
-// stored per half-edge as (A cos phi, A sin phi), so the rest length needs no
-// sine in the loop: sin(w t + phi) = sin(w t) cos(phi) + cos(w t) sin(phi),
-// with sin(w t), cos(w t) formed once per thread and step.
 template <bool ACT, bool GROUND, int TPM>
 __global__ void __launch_bounds__(512)
 k_batch_rollout(const CtaDesc *__restrict__ ctas, const MassState *__restrict__ state_in,
@@ -91,7 +91,9 @@ k_batch_rollout(const CtaDesc *__restrict__ ctas, const MassState *__restrict__ 
     __shared__ uint64_t bar;
     const CtaDesc d = ctas[blockIdx.x];
     const SmemLayout L = smem_layout(d.slot_count, d.n_slices, d.edge_count, ACT);
-    MassState *st[2] = {reinterpret_cast<MassState *>(sm + L.state0), reinterpret_cast<MassState *>(sm + L.state1)};
+    float4 *sa[2] = {reinterpret_cast<float4 *>(sm + L.a0), reinterpret_cast<float4 *>(sm + L.a1)};
+    float2 *sb[2] = {reinterpret_cast<float2 *>(sm + L.b0), reinterpret_cast<float2 *>(sm + L.b1)};
+    float *s_inv = reinterpret_cast<float *>(sm + L.inv);
     const uint32_t *s_slice = reinterpret_cast<const uint32_t *>(sm + L.slices);
     const float2 *s_kl = reinterpret_cast<const float2 *>(sm + L.kl);
     const float2 *s_act = reinterpret_cast<const float2 *>(sm + L.act);
@@ -100,18 +102,25 @@ k_batch_rollout(const CtaDesc *__restrict__ ctas, const MassState *__restrict__ 
 
     if (tid == 0) {
         const uint32_t slice_bytes = 4 * ((d.n_slices + 1 + 3) & ~3u);
-        const uint32_t bytes = d.slot_count * 32 + slice_bytes + d.edge_count * (ACT ? 18 : 10);
+        const uint32_t bytes = slice_bytes + d.edge_count * (ACT ? 18 : 10);
         titan::ptx::mbar_init(&bar, 1);
         titan::ptx::fence_mbar_init();
         titan::ptx::mbar_arrive_expect_tx(&bar, bytes);
         // every size is a multiple of 16 bytes; zero-size copies are not issued
-        titan::ptx::bulk_g2s(st[0], state_in + d.mass_begin, d.slot_count * 32, &bar);
         titan::ptx::bulk_g2s(sm + L.slices, slice_rel + d.slice_base, slice_bytes, &bar);
         if (d.edge_count) {
             titan::ptx::bulk_g2s(sm + L.kl, kl + d.edge_off, d.edge_count * 8, &bar);
             if (ACT) titan::ptx::bulk_g2s(sm + L.act, act + d.edge_off, d.edge_count * 8, &bar);
             titan::ptx::bulk_g2s(sm + L.nbr, nbr + d.edge_off, d.edge_count * 2, &bar);
         }
+    }
+    // the state goes through registers into the split layout while the bulk copies run
+    for (uint32_t m = tid; m < d.slot_count; m += blockDim.x) {
+        float4 p, v;
+        titan::load_state(state_in + d.mass_begin + m, p, v);
+        sa[0][m] = make_float4(p.x, p.y, p.z, v.x);
+        sb[0][m] = make_float2(v.y, v.z);
+        s_inv[m] = p.w;
     }
     __syncthreads();
     bool ok = titan::ptx::mbar_wait_bounded(&bar, 0, spin_limit);
@@ -133,8 +142,10 @@ k_batch_rollout(const CtaDesc *__restrict__ ctas, const MassState *__restrict__ 
     for (uint32_t k = 0; k < n_steps; ++k) {
         float sp = 0.f, cp = 1.f;
         if (ACT) sincosf(titan::clock_phase(c, step0 + (long long)k), &sp, &cp);
-        const MassState *src = st[cur];
-        MassState *dst = st[cur ^ 1];
+        const float4 *srcA = sa[cur];
+        const float2 *srcB = sb[cur];
+        float4 *dstA = sa[cur ^ 1];
+        float2 *dstB = sb[cur ^ 1];
         for (uint32_t pass = 0; ok && pass < passes; ++pass) {
             const uint32_t m = pass * per_pass + tid / TPM;
             const bool live = m < d.slot_count;
@@ -142,23 +153,27 @@ k_batch_rollout(const CtaDesc *__restrict__ ctas, const MassState *__restrict__ 
             float4 p = make_float4(0.f, 0.f, 0.f, 0.f), v = p;
             if (live) {
                 const uint32_t slice = m >> 5, lane = m & 31;
-                p = src[m].p;
-                v = src[m].v;
+                const float4 a0 = srcA[m];
+                const float2 b0 = srcB[m];
+                p = make_float4(a0.x, a0.y, a0.z, s_inv[m]);
+                v = make_float4(a0.w, b0.x, b0.y, 0.f);
                 const uint32_t e0 = s_slice[slice];
                 const uint32_t width = (s_slice[slice + 1] - e0) >> 5;
                 for (uint32_t t = sub; t < width; t += TPM) {
                     const uint32_t e = e0 + t * 32 + lane;
                     const uint32_t code = s_nbr[e];
                     const uint32_t rank = code >> kRankShift, local = code & (kMaxPerCta - 1);
-                    float4 qp, qv;
+                    float4 qa;
+                    float2 qb;
                     if (rank == my_rank) {              // own shared memory: plain shared loads
-                        qp = src[local].p;
-                        qv = src[local].v;
+                        qa = srcA[local];
+                        qb = srcB[local];
                     } else {                            // another CTA of the cluster (DSMEM)
-                        const MassState *q = cluster.map_shared_rank(src + local, rank);
-                        qp = q->p;
-                        qv = q->v;
+                        qa = *cluster.map_shared_rank(srcA + local, rank);
+                        qb = *cluster.map_shared_rank(srcB + local, rank);
                     }
+                    const float4 qp = make_float4(qa.x, qa.y, qa.z, 0.f);
+                    const float4 qv = make_float4(qa.w, qb.x, qb.y, 0.f);
                     const float2 a = s_kl[e];
                     float L0 = a.y;
                     if (ACT) {
@@ -175,8 +190,11 @@ k_batch_rollout(const CtaDesc *__restrict__ ctas, const MassState *__restrict__ 
                 fz += __shfl_xor_sync(0xffffffffu, fz, o);
             }
             if (live && sub == 0) {
-                if (m < d.mass_count) titan::integrate<GROUND>(p, v, fx, fy, fz, c, dst + m);
-                else dst[m] = src[m];
+                MassState o;
+                if (m < d.mass_count) titan::integrate<GROUND>(p, v, fx, fy, fz, c, &o);
+                else { o.p = p; o.v = v; }
+                dstA[m] = make_float4(o.p.x, o.p.y, o.p.z, o.v.x);
+                dstB[m] = make_float2(o.v.y, o.v.z);
             }
         }
         if (cluster_size > 1) cluster.sync();
@@ -184,7 +202,14 @@ k_batch_rollout(const CtaDesc *__restrict__ ctas, const MassState *__restrict__ 
         cur ^= 1;
     }
     if (ok)
-        for (uint32_t m = tid; m < d.mass_count; m += blockDim.x) state_out[d.mass_begin + m] = st[cur][m];
+        for (uint32_t m = tid; m < d.mass_count; m += blockDim.x) {
+            const float4 a = sa[cur][m];
+            const float2 b = sb[cur][m];
+            MassState o;
+            o.p = make_float4(a.x, a.y, a.z, s_inv[m]);
+            o.v = make_float4(a.w, b.x, b.y, 0.f);
+            state_out[d.mass_begin + m] = o;
+        }
 }
 
 // Per-robot centroid x, y, z (fixed summation order: mass by mass).
