@@ -247,6 +247,81 @@ def batched_leg(stream_handle, device, n_robots=4096, steps=2000, plain_robots=3
             "launch_groups": groups}
 
 
+def adjoint_leg(device, n_robots=4096, steps=200, every=50):
+    """Adjoint of a 200-step rollout of the batched robots (centroid
+    x-displacement w.r.t. every spring's actuation amplitude and phase),
+    checkpointing every 50 steps; the robots are one block-diagonal system."""
+    import torch
+    from paper_1911_10274_gb300 import inputs
+    from paper_1911_10274_gb300 import titan as T
+    robots = inputs.robot_batch(n_robots, seed=0)
+    f = T.CentroidRollout(robots, steps, every=every, device=device)
+    amp = torch.tensor(f.system.act_amp, dtype=torch.float32, device=f"cuda:{device}")
+    ph = torch.tensor(f.system.act_phase, dtype=torch.float32, device=f"cuda:{device}")
+    g = torch.ones(n_robots, device=f"cuda:{device}")
+    f.gradients(amp, ph, g)                      # warm-up (allocations, layouts)
+    times = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        f.gradients(amp, ph, g)
+        times.append(time.perf_counter() - t0)
+    t = min(times)
+    return {"workload": f"{n_robots} robots ({f.system.n_springs} springs), {steps}-step rollout, "
+                        f"checkpoint every {every}", "seconds": t,
+            "gradient_entries": 2 * f.system.n_springs, "adjoint_steps_per_s": steps / t,
+            "note": "forward with checkpoints + per-segment recompute + two reverse kernels per step"}
+
+
+def mlp_leg(device, batch=4096, n_in=1024, hidden=512, reps=20):
+    """The surrogate's tensor-core work: the largest forward GEMM
+    (batch x in) . (hidden x in)^T alone, and a whole training step."""
+    import torch
+    from paper_1911_10274_gb300 import titan as T
+    dev = f"cuda:{device}"
+    A = torch.randn(batch, n_in, device=dev).bfloat16()
+    B = torch.randn(hidden, n_in, device=dev).bfloat16()
+    C = torch.empty(batch, hidden, device=dev)
+    for _ in range(3):
+        T.titan_gemm_bf16_tn(A, B, C)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        T.titan_gemm_bf16_tn(A, B, C)            # each call waits for its kernel
+    gemm_s = (time.perf_counter() - t0) / reps
+    flops = 2.0 * batch * n_in * hidden
+    net = T.MLP(n_in, hidden, seed=0, device=device)
+    x = torch.randn(batch, n_in, device=dev).bfloat16()
+    t = torch.randn(batch, device=dev)
+    for _ in range(3):
+        net.train_step(x, t, 1e-3)
+    net.sync()
+    ts = torch.cuda.Event(enable_timing=True)
+    te = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        net.train_step(x, t, 1e-3)
+    net.sync()
+    step_s = (time.perf_counter() - t0) / reps
+    step_flops = 2.0 * batch * (n_in * hidden + 2 * hidden * hidden) * 3     # forward + two backward products
+    peak = bf16_peak()
+    return {"gemm": f"{batch}x{hidden}x{n_in} BF16, FP32 accumulate (tcgen05)",
+            "gemm_tflops": flops / gemm_s / 1e12, "gemm_s": gemm_s,
+            "train_step_s": step_s, "train_samples_per_s": batch / step_s,
+            "train_tflops": step_flops / step_s / 1e12,
+            "roofline": {"bound": "tensor", "achieved": flops / gemm_s / 1e12, "peak": peak[0], "unit": "TFLOP/s",
+                         "frac": flops / gemm_s / 1e12 / peak[0], "peak_source": peak[1],
+                         "note": "call time of a single 128-CTA GEMM including launch; the shapes are small"}}
+
+
+def bf16_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return float(json.load(open(p))["bf16_tflops"]), "measured cuBLAS BF16 burst"
+    return 1900.0, "fallback"
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_env()
@@ -324,6 +399,8 @@ def run_ours(args):
     sim.close()
     if not args.no_batched:
         line["batched"] = batched_leg(stream.cuda_stream, local)
+        line["adjoint"] = adjoint_leg(local)
+        line["surrogate_mlp"] = mlp_leg(local)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_leg(system)
     if rank == 0:
@@ -342,7 +419,8 @@ def main():
     ap.add_argument("--accumulate", choices=["csr", "atomic"], default="csr")
     ap.add_argument("--workload", default="lattice1m")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-batched", action="store_true", help="skip the batched-robots leg")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched-robots, adjoint and surrogate legs")
     ap.add_argument("--kernel-variant", type=int, default=0, help="CSR kernel: 0 auto, 1 direct loads, 2 TMA-staged, 3 bulk L2 prefetch, 4 halo, 5 halo+TMA")
     args = ap.parse_args()
     if args.warmup < 3:
