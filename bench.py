@@ -202,7 +202,7 @@ def config_for(args, system):
     return cfg
 
 
-def batched_leg(stream_handle, device, n_robots=4096, steps=2000, plain_robots=32, plain_steps=200):
+def batched_leg(stream_handle, device, n_robots=4096, steps=2000, plain_robots=32, plain_steps=200, tune=True):
     """Batched actuated robots (a, b, c ~ U{3..12}, 30% of springs actuated,
     ground contact): one rollout of `steps` steps for all robots in the
     persistent cluster launches, against plain per-robot launches (one kernel
@@ -213,7 +213,8 @@ def batched_leg(stream_handle, device, n_robots=4096, steps=2000, plain_robots=3
     robots = inputs.robot_batch(n_robots, seed=0)
     springs = sum(r.n_springs for r in robots)
     with T.Batch(robots, device=device, stream=stream_handle) as b:
-        b.autotune(50)
+        if tune:
+            b.autotune(50)
         times = []
         for _ in range(3):
             b.reset()
@@ -410,6 +411,25 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_leg(args):
+    """One leg alone, for profiling: prints its JSON object."""
+    import torch
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    if args.leg == "batched":
+        out = batched_leg(stream.cuda_stream, local, n_robots=args.robots, steps=args.rollout_steps,
+                          plain_robots=min(32, args.robots), plain_steps=20, tune=not args.untuned)
+    elif args.leg == "adjoint":
+        out = adjoint_leg(local, n_robots=args.robots, steps=args.rollout_steps)
+    elif args.leg == "mlp":
+        out = mlp_leg(local)
+    else:
+        raise SystemExit(f"unknown leg {args.leg}")
+    print(json.dumps({"leg": args.leg, **out}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -421,11 +441,18 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched-robots, adjoint and surrogate legs")
+    ap.add_argument("--leg", choices=["batched", "adjoint", "mlp"], default=None,
+                    help="run one secondary leg alone (for profiling) and print its JSON")
+    ap.add_argument("--robots", type=int, default=4096, help="robots of the --leg batched/adjoint run")
+    ap.add_argument("--rollout-steps", type=int, default=2000, help="rollout steps of the --leg run")
+    ap.add_argument("--untuned", action="store_true", help="--leg batched: keep the default launch shapes")
     ap.add_argument("--kernel-variant", type=int, default=0, help="CSR kernel: 0 auto, 1 direct loads, 2 TMA-staged, 3 bulk L2 prefetch, 4 halo, 5 halo+TMA")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
-    if args.impl == "reference":
+    if args.leg:
+        run_leg(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -165,7 +165,7 @@ __device__ __forceinline__ void prefetch_slice(const uint32_t *slice_off, uint32
 }
 
 template <bool HAS_C, bool HAS_ACT, bool GROUND>
-__global__ void __launch_bounds__(kHaloThreads, 6)
+__global__ void __launch_bounds__(kHaloThreads, 7)
 k_step_halo(const MassState *__restrict__ in, MassState *__restrict__ out, uint32_t n,
             const uint32_t *__restrict__ slice_off, const uint16_t *__restrict__ nslot,
             const float2 *__restrict__ kl, const float *__restrict__ cc,
