@@ -188,38 +188,46 @@ def spearman(a, b) -> float:
 
 def search(mode: str, start: List[Morph], start_fit: np.ndarray, generations: int, mutants: int, screened: int,
            steps: int, seed: int = 0, surrogate: Optional[Surrogate] = None, parents: int = 16,
-           freq: float = 2.0, refine_epochs: int = 2) -> dict:
+           freq: float = 2.0, refine_epochs: int = 2, target: Optional[float] = None,
+           max_rollouts: Optional[int] = None, refine_window: int = 8192) -> dict:
     """(mu + lambda) search from a simulated starting population.
 
     mode 'plain': simulate all mutants; 'surrogate': simulate the `screened`
-    mutants the surrogate ranks highest; 'random': simulate `screened` random
-    mutants.  Returns the best simulated fitness after each generation and the
-    simulator rollouts spent so far (the starting population is not counted)."""
+    mutants the surrogate ranks highest, then refine the surrogate on the last
+    `refine_window` mutants simulated (mirror-augmented); 'random': simulate
+    `screened` random mutants.  Stops after `generations`, or once the best simulated
+    fitness reaches `target`, or when `max_rollouts` would be exceeded.
+    Returns the best fitness after each generation with the simulator rollouts
+    spent so far (the starting population is not counted)."""
     rng = np.random.default_rng(seed)
     order = np.argsort(-start_fit)[:parents]
     pop = [start[i] for i in order]
     pop_fit = start_fit[order].copy()
     best, used, hist = float(pop_fit[0]), 0, []
-    pred_corr = []
-    seen_m, seen_f = list(start), np.asarray(start_fit, np.float64)
+    seen_m, seen_f = [], np.zeros(0)
+    gains = []
     for g in range(generations):
+        if target is not None and best >= target:
+            break
+        n_sim = mutants if mode == "plain" else screened
+        if max_rollouts is not None and used + n_sim > max_rollouts:
+            break
         kids = [mutate(rng, pop[k % len(pop)]) for k in range(mutants)]
         if mode == "plain":
             chosen = kids
         elif mode == "surrogate":
             pred = surrogate.predict(encode(kids))
-            top = np.argsort(-pred)[:screened]
-            chosen = [kids[i] for i in top]
+            chosen = [kids[i] for i in np.argsort(-pred)[:screened]]
         else:
             chosen = [kids[i] for i in rng.choice(len(kids), screened, replace=False)]
         f = fitness(chosen, steps, freq)
         used += len(chosen)
+        gains.append(float(f.mean() - pop_fit.mean()))
         if mode == "surrogate":
-            pred_corr.append(spearman(pred[top], f))
-            seen_m += chosen
-            seen_f = np.concatenate([seen_f, f])
+            seen_m = (seen_m + chosen)[-refine_window:]
+            seen_f = np.concatenate([seen_f, f])[-refine_window:]
             am, af = mirrored(seen_m, seen_f)
-            surrogate.refine(encode(am), af, epochs=refine_epochs, seed=g)
+            surrogate.refine(encode(am), af, epochs=refine_epochs, batch=512, seed=g)
         allm = pop + chosen
         allf = np.concatenate([pop_fit, f])
         keep = np.argsort(-allf)[:parents]
@@ -227,8 +235,8 @@ def search(mode: str, start: List[Morph], start_fit: np.ndarray, generations: in
         pop_fit = allf[keep]
         best = max(best, float(pop_fit[0]))
         hist.append((used, best))
-    return {"history": hist, "best": best, "rollouts": used,
-            "screen_rank_corr": float(np.mean(pred_corr)) if pred_corr else None}
+    return {"history": hist, "best": best, "rollouts": used, "generations": len(hist),
+            "mean_offspring_gain": float(np.mean(gains)) if gains else None}
 
 
 def rollouts_to_reach(history, target: float) -> Optional[int]:
@@ -239,9 +247,15 @@ def rollouts_to_reach(history, target: float) -> Optional[int]:
 
 
 def main(argv=None):
-    """Full-scale run: python -m paper_1911_10274_gb300.surrogate [--train N] [--steps S] ..."""
+    """Full-scale run: python -m paper_1911_10274_gb300.surrogate [--train N] [--steps S] ...
+
+    Trains on N random robots, runs the plain search for --generations, then
+    runs the screened search and its random-screening ablation until each
+    reaches the plain search's best fitness, within the plain search's rollout
+    budget; prints the rollouts each needed."""
     import argparse
     import json
+    import os
     import time
     ap = argparse.ArgumentParser()
     ap.add_argument("--train", type=int, default=200_000)
@@ -251,34 +265,56 @@ def main(argv=None):
     ap.add_argument("--screened", type=int, default=64)
     ap.add_argument("--epochs", type=int, default=4)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--screened-budget", type=int, default=25_600,
+                    help="rollout cap of the screened searches (and at most the plain search's)")
+    ap.add_argument("--fitness-cache", default=None,
+                    help="npz file holding the training robots' simulated fitness (written if absent)")
     a = ap.parse_args(argv)
     rng = np.random.default_rng(a.seed)
     t0 = time.time()
     morphs = [random_morph(rng) for _ in range(a.train)]
-    y = fitness(morphs, a.steps)
+    key = f"{a.seed}-{a.train}-{a.steps}"
+    y = None
+    if a.fitness_cache and os.path.exists(a.fitness_cache):
+        d = np.load(a.fitness_cache)
+        if str(d["key"]) == key:
+            y = d["y"]
+    cached = y is not None
+    if y is None:
+        y = fitness(morphs, a.steps)
+        if a.fitness_cache:
+            np.savez(a.fitness_cache, key=key, y=y)
     t_sim = time.time() - t0
-    X = encode(morphs)
     n_val = max(128, a.train // 10)
     sur = Surrogate(seed=a.seed)
     t1 = time.time()
     am, ay = mirrored(morphs[:-n_val], y[:-n_val])
     sur.fit(encode(am), ay, epochs=a.epochs)
     t_fit = time.time() - t1
-    val_corr = spearman(sur.predict(X[-n_val:]), y[-n_val:])
-    start = morphs[-n_val:]
-    start_fit = y[-n_val:]
-    res = {}
-    for mode in ("plain", "surrogate", "random"):
-        res[mode] = search(mode, start, start_fit, a.generations, a.mutants, a.screened, a.steps, seed=a.seed + 1,
-                           surrogate=sur)
-    target = res["plain"]["best"]
-    out = {"train_rollouts": a.train, "steps": a.steps, "simulate_s": t_sim, "fit_s": t_fit,
-           "val_spearman": val_corr, "plain_best": target,
-           "plain_rollouts": res["plain"]["rollouts"],
-           "surrogate_best": res["surrogate"]["best"], "random_best": res["random"]["best"],
-           "surrogate_rollouts_to_plain_best": rollouts_to_reach(res["surrogate"]["history"], target),
-           "random_rollouts_to_plain_best": rollouts_to_reach(res["random"]["history"], target),
-           "surrogate_screen_rank_corr": res["surrogate"]["screen_rank_corr"]}
+    val_corr = spearman(sur.predict(encode(morphs[-n_val:])), y[-n_val:])
+    start, start_fit = morphs[-n_val:], y[-n_val:]
+    t2 = time.time()
+    plain = search("plain", start, start_fit, a.generations, a.mutants, a.screened, a.steps, seed=a.seed + 1)
+    target, budget = plain["best"], min(plain["rollouts"], a.screened_budget)
+    t3 = time.time()
+    big = 10 ** 9
+    scr = search("surrogate", start, start_fit, big, a.mutants, a.screened, a.steps, seed=a.seed + 1,
+                 surrogate=sur, target=target, max_rollouts=budget)
+    t4 = time.time()
+    rnd = search("random", start, start_fit, big, a.mutants, a.screened, a.steps, seed=a.seed + 1,
+                 target=target, max_rollouts=budget)
+    t5 = time.time()
+    out = {"train_rollouts": a.train, "steps": a.steps, "fitness_cached": cached, "simulate_s": t_sim,
+           "fit_s": t_fit, "val_spearman": val_corr,
+           "plain": {"best": target, "rollouts": plain["rollouts"], "generations": plain["generations"],
+                     "s": t3 - t2},
+           "screened_budget": budget,
+           "surrogate": {"best": scr["best"], "rollouts_to_plain_best": rollouts_to_reach(scr["history"], target),
+                         "rollouts": scr["rollouts"], "generations": scr["generations"],
+                         "mean_offspring_gain": scr["mean_offspring_gain"], "s": t4 - t3},
+           "random": {"best": rnd["best"], "rollouts_to_plain_best": rollouts_to_reach(rnd["history"], target),
+                      "rollouts": rnd["rollouts"], "generations": rnd["generations"],
+                      "mean_offspring_gain": rnd["mean_offspring_gain"], "s": t5 - t4}}
     print(json.dumps(out))
     return out
 
