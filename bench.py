@@ -291,6 +291,20 @@ def mlp_leg(device, batch=4096, n_in=1024, hidden=512, reps=20):
         T.titan_gemm_bf16_tn(A, B, C)            # each call waits for its kernel
     gemm_s = (time.perf_counter() - t0) / reps
     flops = 2.0 * batch * n_in * hidden
+    # the same kernel on a square 8192^3 product: its throughput once launch cost is amortised
+    L = 8192
+    AL = torch.randn(L, L, device=dev).bfloat16()
+    BL = torch.randn(L, L, device=dev).bfloat16()
+    CL = torch.empty(L, L, device=dev)
+    for _ in range(3):
+        T.titan_gemm_bf16_tn(AL, BL, CL)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(5):
+        T.titan_gemm_bf16_tn(AL, BL, CL)
+    large_s = (time.perf_counter() - t0) / 5
+    large_tflops = 2.0 * L ** 3 / large_s / 1e12
+    del AL, BL, CL
     net = T.MLP(n_in, hidden, seed=0, device=device)
     x = torch.randn(batch, n_in, device=dev).bfloat16()
     t = torch.randn(batch, device=dev)
@@ -311,6 +325,7 @@ def mlp_leg(device, batch=4096, n_in=1024, hidden=512, reps=20):
             "gemm_tflops": flops / gemm_s / 1e12, "gemm_s": gemm_s,
             "train_step_s": step_s, "train_samples_per_s": batch / step_s,
             "train_tflops": step_flops / step_s / 1e12,
+            "gemm_8192_tflops": large_tflops, "gemm_8192_frac": large_tflops / peak[0],
             "roofline": {"bound": "tensor", "achieved": flops / gemm_s / 1e12, "peak": peak[0], "unit": "TFLOP/s",
                          "frac": flops / gemm_s / 1e12 / peak[0], "peak_source": peak[1],
                          "note": "call time of a single 128-CTA GEMM including launch; the shapes are small"}}

@@ -269,6 +269,16 @@ titan_status titan_step_atomic_noalloc(uint32_t n_masses, const float *pos_dev, 
                                        const titan_params *params, float *pos_out_dev,
                                        float *vel_out_dev, void *stream);
 
+/* Failure-path self-test of the bounded device waits (no counterpart in the
+ * paper; it backs the TITAN_E_TIMEOUT contract above).  Launches one CTA on
+ * `device` whose thread waits on an mbarrier that nothing arrives on, polling
+ * at most spin_limit times (1 <= spin_limit <= 2^20), and synchronises.
+ * Returns TITAN_E_TIMEOUT when the wait expired and the device flag reached
+ * the host - the expected outcome, after which the device stays usable;
+ * TITAN_E_INVALID for an out-of-range spin_limit; TITAN_E_CUDA otherwise.
+ * Allocates and frees one int of device memory; uses the legacy stream. */
+titan_status titan_selftest_wait_timeout(int32_t device, uint32_t spin_limit);
+
 /* Waits for outstanding work and frees every resource of the handle.
  * NULL is a no-op.  Returns the status of that final wait. */
 titan_status titan_destroy(titan_sim *sim);

@@ -86,6 +86,7 @@ def load(path: Optional[str] = None):
                 "titan_step_atomic_noalloc": (S, [u32, _P, _P, _P, u32, _P, _P, _P, f32,
                                                   C.POINTER(titan_params), _P, _P, _P]),
                 "titan_set_step": (S, [_P, u64]),
+                "titan_selftest_wait_timeout": (S, [C.c_int32, u32]),
                 "titan_set_worm_actuation": (S, [_P, u32, _P, _P, _P, f32, f32]),
                 "titan_set_spring_params": (S, [_P, u32, _P, _P, _P, _P]),
                 "titan_remove_springs": (S, [_P, u32, _P]),
@@ -277,6 +278,17 @@ def titan_step_atomic_noalloc(n_masses: int, pos_dev, vel_dev, inv_mass_dev, n_s
         n_masses, _ptr(pos_dev), _ptr(vel_dev), _ptr(inv_mass_dev), n_springs, _ptr(ends_dev),
         _ptr(k_dev), _ptr(rest_dev), float(damping), C.byref(params), _ptr(pos_out_dev),
         _ptr(vel_out_dev), stream))
+
+
+def titan_selftest_wait_timeout(device: int = 0, spin_limit: int = 4096) -> int:
+    """Runs the bounded-wait failure self-test on `device` and returns its
+    status: TITAN_E_TIMEOUT (4) is the expected outcome.  Other statuses
+    raise TitanError."""
+    st = load().titan_selftest_wait_timeout(device, spin_limit)
+    if st != TITAN_E_TIMEOUT:
+        _check(st)
+        raise TitanError(st, "titan_selftest_wait_timeout: the wait did not expire")
+    return st
 
 
 def _bcheck(status: int, batch=None):

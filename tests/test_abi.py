@@ -115,3 +115,9 @@ def test_batch_create_validates_before_touching_the_device():
     with pytest.raises(T.TitanError) as ei:
         T.Batch([sy, other])
     assert ei.value.status == T.TITAN_E_UNSUPPORTED
+
+
+def test_wait_timeout_selftest_rejects_unbounded_limits_before_touching_the_device():
+    for bad in (0, (1 << 20) + 1):
+        with pytest.raises(T.TitanError, match="spin_limit"):
+            T.titan_selftest_wait_timeout(0, bad)
