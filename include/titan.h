@@ -102,11 +102,15 @@ typedef struct {
     void *stream;             /* cudaStream_t for the step loop; NULL: own stream  */
     uint64_t spin_limit;      /* bound on device spin-wait iterations; 0: default  */
     int32_t graph_chunk;      /* steps per captured CUDA graph; 0: 64; < 0: none   */
-    int32_t kernel_variant;   /* CSR kernel: 0 auto (4 when it fits, else 3),
+    int32_t kernel_variant;   /* CSR kernel: 0 auto (6 for masses on a grid when
+                                 it fits, else 4 when it fits, else 3),
                                  1 direct loads, 2 TMA-staged stream, 3 bulk L2
                                  prefetch, 4 halo tables in shared memory, 5 halo +
-                                 TMA-staged stream (4 and 5 return TITAN_E_UNSUPPORTED
-                                 if their shared memory does not fit)                 */
+                                 TMA-staged stream, 6 grid-box tables (masses on a
+                                 cubic grid, at most one per cell; no neighbour
+                                 index in the stream).  4, 5 and 6 return
+                                 TITAN_E_UNSUPPORTED if their tables do not fit or
+                                 (6) the masses are not on a grid           */
     int32_t reserved[6];      /* zero                                              */
 } titan_params;
 
@@ -233,6 +237,12 @@ titan_status titan_sync(titan_sim *sim);
 
 /* Number of steps enqueued so far (the simulated time is steps * dt). */
 uint64_t titan_steps(const titan_sim *sim);
+
+/* The step kernel titan_create resolved params.kernel_variant to: 1..6 as
+ * listed for kernel_variant (never 0), 0 for atomic accumulation, -1 for a
+ * NULL handle.  The resolution is redone when added masses or springs force a
+ * layout rebuild. */
+int32_t titan_csr_kernel(const titan_sim *sim);
 
 /* Text of the last error on this handle, or of the last failed titan_create
  * on this thread when sim is NULL.  Owned by the library; never NULL. */

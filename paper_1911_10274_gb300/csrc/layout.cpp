@@ -18,6 +18,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
+#include <climits>
 #include <numeric>
 
 namespace titan {
@@ -60,13 +62,16 @@ void morton_order(const double *pos, uint32_t n, std::vector<uint32_t> &caller_o
     for (uint32_t d = 0; d < n; ++d) caller_of_dev[d] = key[d].second;
 }
 
-bool grid_tile_order(const double *pos, uint32_t n, double h, std::vector<uint32_t> &caller_of_dev) {
+bool grid_tile_order(const double *pos, uint32_t n, double h, std::vector<uint32_t> &caller_of_dev,
+                     std::vector<int32_t> *cell_of_dev) {
     caller_of_dev.clear();
+    if (cell_of_dev) cell_of_dev->clear();
     if (n == 0 || !(h > 0) || !std::isfinite(h)) return false;
     double lo[3] = {pos[0], pos[1], pos[2]};
     for (uint32_t i = 0; i < n; ++i)
         for (int a = 0; a < 3; ++a) lo[a] = std::min(lo[a], pos[3 * (size_t)i + a]);
-    struct Key { uint64_t tile; uint32_t lane, idx; };
+    // cube = 2 x 2 x 2 tiles = 8 x 8 x 4 cells = 256 device slots
+    struct Key { uint64_t cube; uint32_t slot, idx; };
     std::vector<Key> key(n);
     for (uint32_t i = 0; i < n; ++i) {
         uint64_t c[3];
@@ -76,23 +81,42 @@ bool grid_tile_order(const double *pos, uint32_t n, double h, std::vector<uint32
             if (std::fabs(q - r) > 1e-3 || r > (double)((1u << 22) - 1)) return false;
             c[a] = (uint64_t)r;
         }
-        const uint64_t tile = spread_bits3(c[0] >> 2) | (spread_bits3(c[1] >> 2) << 1) | (spread_bits3(c[2] >> 1) << 2);
-        key[i] = {tile, (uint32_t)((c[0] & 3) + 4 * (c[1] & 3) + 16 * (c[2] & 1)), i};
+        const uint64_t cube = spread_bits3(c[0] >> 3) | (spread_bits3(c[1] >> 3) << 1) | (spread_bits3(c[2] >> 2) << 2);
+        const uint32_t tile = (uint32_t)(((c[0] >> 2) & 1) | (((c[1] >> 2) & 1) << 1) | (((c[2] >> 1) & 1) << 2));
+        const uint32_t lane = (uint32_t)((c[0] & 3) + 4 * (c[1] & 3) + 16 * (c[2] & 1));
+        key[i] = {cube, 32 * tile + lane, i};
     }
     std::sort(key.begin(), key.end(), [](const Key &a, const Key &b) {
-        return a.tile != b.tile ? a.tile < b.tile : (a.lane != b.lane ? a.lane < b.lane : a.idx < b.idx);
+        return a.cube != b.cube ? a.cube < b.cube : (a.slot != b.slot ? a.slot < b.slot : a.idx < b.idx);
     });
-    uint64_t tiles = 0;
+    uint64_t cubes = 0;
     for (uint32_t k = 0; k < n; ++k) {
-        if (k && key[k].tile == key[k - 1].tile && key[k].lane == key[k - 1].lane) return false;  // shared cell
-        if (k == 0 || key[k].tile != key[k - 1].tile) ++tiles;
+        if (k && key[k].cube == key[k - 1].cube && key[k].slot == key[k - 1].slot) return false;  // shared cell
+        if (k == 0 || key[k].cube != key[k - 1].cube) ++cubes;
     }
-    if (tiles * 32 >= (1ull << 31)) return false;
-    caller_of_dev.assign(tiles * 32, UINT32_MAX);
+    if (cubes * 256 >= (1ull << 31)) return false;
+    caller_of_dev.assign(cubes * 256, UINT32_MAX);
+    if (cell_of_dev) cell_of_dev->assign(cubes * 256 * 3, 0);
     uint64_t t = 0;
     for (uint32_t k = 0; k < n; ++k) {
-        if (k && key[k].tile != key[k - 1].tile) ++t;
-        caller_of_dev[t * 32 + key[k].lane] = key[k].idx;
+        const bool first = k == 0 || key[k].cube != key[k - 1].cube;
+        if (k && first) ++t;
+        caller_of_dev[t * 256 + key[k].slot] = key[k].idx;
+        if (cell_of_dev && first) {
+            // every slot of the cube (holes included) gets its cell: cube origin + tile + lane offsets
+            int32_t o[3];
+            for (int a = 0; a < 3; ++a) {
+                const double q = std::nearbyint((pos[3 * (size_t)key[k].idx + a] - lo[a]) / h);
+                o[a] = (int32_t)q & ~(a == 2 ? 3 : 7);
+            }
+            for (uint32_t sl = 0; sl < 256; ++sl) {
+                const uint32_t tile = sl >> 5, l = sl & 31;
+                int32_t *c = cell_of_dev->data() + 3 * (t * 256 + sl);
+                c[0] = o[0] + 4 * (int32_t)(tile & 1) + (int32_t)(l & 3);
+                c[1] = o[1] + 4 * (int32_t)((tile >> 1) & 1) + (int32_t)((l >> 2) & 3);
+                c[2] = o[2] + 2 * (int32_t)((tile >> 2) & 1) + (int32_t)(l >> 4);
+            }
+        }
     }
     return true;
 }
@@ -114,7 +138,7 @@ uint32_t direction_class(const double *a, const double *b) {
 }  // namespace
 
 bool build_sell(uint32_t n, uint32_t s, const uint32_t *ends, const double *pos,
-                const std::vector<uint32_t> &dev_of, SellHost &out) {
+                const std::vector<uint32_t> &dev_of, SellHost &out, const int32_t *cell) {
     const uint32_t n_slices = (n + 31) / 32;
     std::vector<uint32_t> deg(n, 0);
     for (uint32_t q = 0; q < s; ++q) {
@@ -123,16 +147,34 @@ bool build_sell(uint32_t n, uint32_t s, const uint32_t *ends, const double *pos,
     }
     std::vector<uint64_t> rowptr(n + 1, 0);
     for (uint32_t i = 0; i < n; ++i) rowptr[i + 1] = rowptr[i] + deg[i];
-    // half-edge = (neighbour device index, spring index, end slot 0/1)
-    struct HalfEdge { uint32_t key, nbr, spring; };
+    // half-edge = (order key, neighbour device index, spring index).  The key
+    // is the direction class; on a grid it also holds the exact cell offset
+    // of the neighbour, so that equal keys mean equal offsets.
+    struct HalfEdge { uint64_t key; uint32_t nbr, spring; };
     std::vector<HalfEdge> he(rowptr[n]);
     std::vector<uint64_t> cur(rowptr.begin(), rowptr.end() - 1);
+    // 10 bits per component, clamped: equal codes are equal offsets for every
+    // offset within +-511 cells (the box builder checks the columns anyway)
+    auto offset_code = [&](uint32_t from, uint32_t to) -> uint64_t {
+        uint64_t code = 0;
+        for (int a = 0; a < 3; ++a) {
+            int64_t d = (int64_t)cell[3 * (size_t)to + a] - (int64_t)cell[3 * (size_t)from + a];
+            d = std::min<int64_t>(511, std::max<int64_t>(-512, d));
+            code = (code << 10) | (uint64_t)(d + 512);
+        }
+        return code;
+    };
     for (uint32_t q = 0; q < s; ++q) {
         const uint32_t ci = ends[2 * (size_t)q], cj = ends[2 * (size_t)q + 1];
         const uint32_t a = dev_of[ci], b = dev_of[cj];
         const uint32_t kab = direction_class(pos + 3 * (size_t)ci, pos + 3 * (size_t)cj);
-        he[cur[a]++] = {kab, b, q};
-        he[cur[b]++] = {26u - kab, a, q};      // the opposite direction
+        uint64_t ka = (uint64_t)kab << 32, kb = (uint64_t)(26u - kab) << 32;   // opposite direction
+        if (cell) {
+            ka |= offset_code(a, b);
+            kb |= offset_code(b, a);
+        }
+        he[cur[a]++] = {ka, b, q};
+        he[cur[b]++] = {kb, a, q};
     }
     for (uint32_t i = 0; i < n; ++i)
         std::sort(he.begin() + rowptr[i], he.begin() + rowptr[i + 1],
@@ -140,11 +182,52 @@ bool build_sell(uint32_t n, uint32_t s, const uint32_t *ends, const double *pos,
                       if (x.key != y.key) return x.key < y.key;
                       return x.nbr != y.nbr ? x.nbr < y.nbr : x.spring < y.spring;
                   });
+    // Column of every half-edge within its slice.  Default: its position in
+    // the row.  On a grid: one run of columns per distinct key of the slice
+    // (as many as the most any lane has), so that every entry of a column has
+    // the same cell offset and lanes lacking that offset hold padding.
+    std::vector<uint32_t> col(rowptr[n]);
     out.slice_off.assign(n_slices + 1, 0);
     uint64_t total = 0;
+    std::vector<std::pair<uint64_t, uint32_t>> runs;
     for (uint32_t sl = 0; sl < n_slices; ++sl) {
+        const uint32_t l_end = std::min<uint32_t>(32, n - sl * 32);
         uint32_t w = 0;
-        for (uint32_t l = 0; l < 32 && sl * 32 + l < n; ++l) w = std::max(w, deg[sl * 32 + l]);
+        if (!cell) {
+            for (uint32_t l = 0; l < l_end; ++l) {
+                const uint32_t i = sl * 32 + l;
+                w = std::max(w, deg[i]);
+                for (uint32_t t = 0; t < deg[i]; ++t) col[rowptr[i] + t] = t;
+            }
+        } else {
+            runs.clear();
+            for (uint32_t l = 0; l < l_end; ++l) {
+                const uint32_t i = sl * 32 + l;
+                for (uint64_t r = rowptr[i]; r < rowptr[i + 1];) {
+                    uint64_t r2 = r;
+                    while (r2 < rowptr[i + 1] && he[r2].key == he[r].key) ++r2;
+                    runs.push_back({he[r].key, (uint32_t)(r2 - r)});
+                    r = r2;
+                }
+            }
+            std::sort(runs.begin(), runs.end());
+            // keep, per key, the longest run; then the column where each key starts
+            std::vector<std::pair<uint64_t, uint32_t>> start;
+            for (size_t k = 0; k < runs.size(); ++k)
+                if (k + 1 == runs.size() || runs[k + 1].first != runs[k].first) {
+                    start.push_back({runs[k].first, w});
+                    w += runs[k].second;
+                }
+            for (uint32_t l = 0; l < l_end; ++l) {
+                const uint32_t i = sl * 32 + l;
+                for (uint64_t r = rowptr[i]; r < rowptr[i + 1];) {
+                    const uint64_t key = he[r].key;
+                    const auto it = std::lower_bound(start.begin(), start.end(), std::make_pair(key, 0u));
+                    uint32_t c = it->second;
+                    for (; r < rowptr[i + 1] && he[r].key == key; ++r) col[r] = c++;
+                }
+            }
+        }
         w = (w + 1) & ~1u;
         total += (uint64_t)w * 32;
         if (total > 0xffffffffULL) return false;
@@ -158,19 +241,18 @@ bool build_sell(uint32_t n, uint32_t s, const uint32_t *ends, const double *pos,
         const uint32_t w = (out.slice_off[sl + 1] - out.slice_off[sl]) / 32;
         for (uint32_t l = 0; l < 32; ++l) {
             const uint32_t i = sl * 32 + l;
-            for (uint32_t t = 0; t < w; ++t) {
-                const uint64_t e = out.slice_off[sl] + 32ull * t + l;
-                if (i < n && t < deg[i]) {
-                    const HalfEdge &h = he[rowptr[i] + t];
-                    out.nbr[e] = h.nbr;
-                    out.spring[e] = h.spring;
-                    // which end of spring h.spring this row is
-                    const uint32_t end0 = dev_of[ends[2 * (size_t)h.spring]];
-                    const bool is_i = (end0 == i) && !(end0 == h.nbr);
-                    out.entry_of_end[2 * (size_t)h.spring + (is_i ? 0 : 1)] = (uint32_t)e;
-                } else {
-                    out.nbr[e] = i < n ? i : 0;   // self: zero-length padding spring
-                }
+            for (uint32_t t = 0; t < w; ++t)        // padding: a zero-length spring to itself
+                out.nbr[out.slice_off[sl] + 32ull * t + l] = i < n ? i : 0;
+            if (i >= n) continue;
+            for (uint64_t r = rowptr[i]; r < rowptr[i + 1]; ++r) {
+                const HalfEdge &h = he[r];
+                const uint64_t e = out.slice_off[sl] + 32ull * col[r] + l;
+                out.nbr[e] = h.nbr;
+                out.spring[e] = h.spring;
+                // which end of spring h.spring this row is
+                const uint32_t end0 = dev_of[ends[2 * (size_t)h.spring]];
+                const bool is_i = (end0 == i) && !(end0 == h.nbr);
+                out.entry_of_end[2 * (size_t)h.spring + (is_i ? 0 : 1)] = (uint32_t)e;
             }
         }
     }
@@ -299,6 +381,91 @@ bool build_halo(uint32_t n, const SellHost &sell, uint32_t max_slots, bool grid_
         for (uint32_t e = 0; e < T; ++e) local[entries[e]] = UINT32_MAX;
     }
     out.conflict_ways = groups ? (double)wavefronts / (double)groups : 1.0;
+    return true;
+}
+
+bool build_box(uint32_t n, const SellHost &sell, const std::vector<int32_t> &cell, uint32_t max_slots,
+               BoxHost &out) {
+    const uint32_t n_blocks = (n + kHaloBlock - 1) / kHaloBlock;
+    const uint32_t slices_per_block = kHaloBlock / 32;
+    const uint32_t n_slices = (n + 31) / 32;
+    if (cell.size() != 3 * (size_t)n || sell.slice_off.size() != (size_t)n_slices + 1) return false;
+    out.col_off.assign(sell.entries / 32, 0);
+    out.own_slot.assign(n, 0);
+    out.ext_off.assign(n_blocks + 1, 0);
+    out.ext_idx.clear();
+    out.ext_slot.clear();
+    out.max_table = 0;
+    const int32_t *C = cell.data();
+    std::vector<uint32_t> seen;     // external masses of the current block
+    for (uint32_t b = 0; b < n_blocks; ++b) {
+        const uint32_t m0 = b * kHaloBlock, m1 = std::min(n, m0 + kHaloBlock);
+        const uint32_t sl0 = b * slices_per_block, sl1 = std::min(n_slices, sl0 + slices_per_block);
+        int64_t lo[3], hi[3], R[3] = {0, 0, 0};
+        for (int a = 0; a < 3; ++a) { lo[a] = INT64_MAX; hi[a] = INT64_MIN; }
+        for (uint32_t m = m0; m < m1; ++m)
+            for (int a = 0; a < 3; ++a) {
+                lo[a] = std::min<int64_t>(lo[a], C[3 * (size_t)m + a]);
+                hi[a] = std::max<int64_t>(hi[a], C[3 * (size_t)m + a]);
+            }
+        for (uint32_t sl = sl0; sl < sl1; ++sl)
+            for (uint32_t e = sell.slice_off[sl]; e < sell.slice_off[sl + 1]; ++e) {
+                if (sell.spring[e] == UINT32_MAX) continue;
+                const uint32_t i = sl * 32 + (e - sell.slice_off[sl]) % 32, j = sell.nbr[e];
+                for (int a = 0; a < 3; ++a)
+                    R[a] = std::max<int64_t>(R[a], std::llabs((int64_t)C[3 * (size_t)j + a] - C[3 * (size_t)i + a]));
+            }
+        int64_t dim[3];
+        for (int a = 0; a < 3; ++a) {
+            lo[a] -= R[a];
+            hi[a] += R[a];
+            dim[a] = hi[a] - lo[a] + 1;
+        }
+        dim[0] += ((4 - dim[0]) % 8 + 8) % 8;            // X = 4 (mod 8)
+        const int64_t slots = dim[0] * dim[1] * dim[2];
+        if (slots > (int64_t)max_slots || slots > 32767) return false;
+        out.max_table = std::max<uint32_t>(out.max_table, (uint32_t)slots);
+        auto slot = [&](uint32_t m) -> int64_t {
+            return (C[3 * (size_t)m] - lo[0]) + dim[0] * ((C[3 * (size_t)m + 1] - lo[1]) + dim[1] * (C[3 * (size_t)m + 2] - lo[2]));
+        };
+        for (uint32_t m = m0; m < m1; ++m) out.own_slot[m] = (uint16_t)slot(m);
+        seen.clear();
+        for (uint32_t sl = sl0; sl < sl1; ++sl) {
+            const uint32_t e0 = sell.slice_off[sl], w = (sell.slice_off[sl + 1] - e0) / 32;
+            for (uint32_t t = 0; t < w; ++t) {
+                bool have = false;
+                int64_t off = 0;
+                for (uint32_t l = 0; l < 32; ++l) {
+                    const uint32_t e = e0 + 32 * t + l, i = sl * 32 + l;
+                    if (i >= n || sell.spring[e] == UINT32_MAX) continue;
+                    const uint32_t j = sell.nbr[e];
+                    const int64_t o = slot(j) - slot(i);
+                    if (have && o != off) return false;           // column not offset-aligned
+                    // the neighbour's cell must be exactly the offset cell
+                    for (int a = 0; a < 3; ++a)
+                        if (C[3 * (size_t)j + a] < lo[a] || C[3 * (size_t)j + a] > hi[a]) return false;
+                    have = true;
+                    off = o;
+                    if (j < m0 || j >= m1) seen.push_back(j);
+                }
+                // every lane's read, padding included, must stay inside the box
+                for (uint32_t l = 0; l < 32; ++l) {
+                    const uint32_t i = sl * 32 + l;
+                    if (i >= n) continue;
+                    const int64_t r = slot(i) + off;
+                    if (r < 0 || r >= slots) return false;
+                }
+                out.col_off[e0 / 32 + t] = (int16_t)off;
+            }
+        }
+        std::sort(seen.begin(), seen.end());
+        seen.erase(std::unique(seen.begin(), seen.end()), seen.end());
+        for (uint32_t j : seen) {
+            out.ext_idx.push_back(j);
+            out.ext_slot.push_back((uint16_t)slot(j));
+        }
+        out.ext_off[b + 1] = (uint32_t)out.ext_idx.size();
+    }
     return true;
 }
 

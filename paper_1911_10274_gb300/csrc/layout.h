@@ -12,15 +12,20 @@ void morton_order(const double *pos, uint32_t n, std::vector<uint32_t> &caller_o
 
 // Grid-tile order for masses that sit on a cubic grid of pitch h (every
 // coordinate within 1e-3 h of lo + integer x h, at most one mass per cell):
-// cells are grouped in tiles of 4 x 4 x 2, tiles are ordered along a Morton
-// curve, and the mass in cell (x, y, z) of a tile goes to lane
-// (x & 3) + 4 (y & 3) + 16 (z & 1) of that tile's 32 device slots.  Slots of
-// empty cells are holes (caller_of_dev = UINT32_MAX).  Consequence used by the
-// halo kernel: the 16 lanes of a half-warp are a 4 x 4 x 1 layer of cells, and
-// any translate of such a layer covers each value of (device index mod 16)
-// once.  Returns false (leaving the output empty) if the masses are not on
-// such a grid.
-bool grid_tile_order(const double *pos, uint32_t n, double h, std::vector<uint32_t> &caller_of_dev);
+// cells are grouped in tiles of 4 x 4 x 2 and tiles in cubes of 2 x 2 x 2
+// (8 x 8 x 4 cells); cubes are ordered along a Morton curve and each
+// occupied cube gets 256 device slots, 32 per tile, so that a block of 256
+// device masses is one cube.  The mass in cell (x, y, z) of a tile goes to lane
+// (x & 3) + 4 (y & 3) + 16 (z & 1) of that tile's 32 slots.  Slots of empty
+// cells are holes (caller_of_dev = UINT32_MAX).  Consequences used by the
+// halo and box kernels: the 16 lanes of a half-warp are a 4 x 4 x 1 layer of
+// cells, any translate of such a layer covers each value of (device index
+// mod 16) once, and a block's box is 8 x 8 x 4 cells plus its halo.  Returns
+// false (leaving the output empty) if the masses are not on such a grid.
+// cell_of_dev (optional) receives the integer cell (x, y, z) of every device
+// index, holes included, relative to the lowest occupied cell.
+bool grid_tile_order(const double *pos, uint32_t n, double h, std::vector<uint32_t> &caller_of_dev,
+                     std::vector<int32_t> *cell_of_dev = nullptr);
 
 struct SellHost {
     std::vector<uint32_t> slice_off;      // [n_slices + 1]
@@ -32,8 +37,11 @@ struct SellHost {
 
 // Returns false if the padded incidence does not fit 32-bit entry offsets.
 // pos: caller-order positions [n][3], used only to order each row by direction.
+// cell (optional, [n][3] per device index): grid cells; columns are then
+// offset-aligned - every non-padding entry of a column of a slice points at
+// the same cell offset - which the box kernel relies on.
 bool build_sell(uint32_t n, uint32_t s, const uint32_t *ends, const double *pos,
-                const std::vector<uint32_t> &dev_of, SellHost &out);
+                const std::vector<uint32_t> &dev_of, SellHost &out, const int32_t *cell = nullptr);
 
 // Per-block neighbourhood tables for the halo kernel.  Block b is the CTA of
 // kHaloBlock consecutive device masses; its table holds the state of every mass
@@ -58,6 +66,30 @@ struct HaloHost {
 // grid_colours: the device order is a grid-tile order, so (device index mod
 // 16) is already a conflict-free colour; otherwise a greedy colouring is used.
 bool build_halo(uint32_t n, const SellHost &sell, uint32_t max_slots, bool grid_colours, HaloHost &out);
+
+// Box tables for the grid form of the halo kernel (masses in grid-tile order,
+// SELL built with offset-aligned columns).  Block b's table covers the box of
+// cells from its masses' lowest cell minus the largest spring offset to their
+// highest cell plus it; the cell (x, y, z) has slot
+// (x - x0) + X (y - y0) + X Y (z - z0), with the row length X padded to 4
+// modulo 8 so that a quarter-warp (a 4 x 2 patch of cells) reads 16-byte
+// entries in distinct banks and a half-warp (4 x 4) reads 8-byte entries in
+// distinct banks.  A neighbour's slot is then the mass's own slot plus the
+// column's offset, and the half-edge stream needs no neighbour index.
+struct BoxHost {
+    std::vector<int16_t> col_off;        // [E / 32] slot offset of every SELL column
+    std::vector<uint16_t> own_slot;      // [n]
+    std::vector<uint32_t> ext_off;       // [n_blocks + 1]
+    std::vector<uint32_t> ext_idx;       // device index of each external table entry
+    std::vector<uint16_t> ext_slot;      // its slot
+    uint32_t max_table = 0;              // largest box (slots) over all blocks
+};
+
+// Returns false if some box exceeds max_slots or a column is not
+// offset-aligned.  Checks that every entry's table read, padding included,
+// stays inside its block's box.
+bool build_box(uint32_t n, const SellHost &sell, const std::vector<int32_t> &cell, uint32_t max_slots,
+               BoxHost &out);
 
 struct RecordsHost {
     std::vector<uint32_t> order;            // [S] record r holds caller spring order[r]

@@ -138,7 +138,7 @@ titan_status validate(const titan_masses *m, const titan_springs *sp, const tita
     if (p->exec < TITAN_EXEC_AUTO || p->exec > TITAN_EXEC_PERSISTENT)
         return fail(nullptr, TITAN_E_INVALID, "params.exec out of range");
     if (p->device < 0) return fail(nullptr, TITAN_E_INVALID, "params.device must be >= 0");
-    if (p->kernel_variant < 0 || p->kernel_variant > 5) return fail(nullptr, TITAN_E_INVALID, "params.kernel_variant must be 0..5");
+    if (p->kernel_variant < 0 || p->kernel_variant > 6) return fail(nullptr, TITAN_E_INVALID, "params.kernel_variant must be 0..6");
     for (uint64_t i = 0; i < m->n; ++i) {
         for (int a = 0; a < 3; ++a) {
             if (!finite(m->pos[3 * i + a])) return fail(nullptr, TITAN_E_INVALID, "masses.pos has a non-finite value at mass " + std::to_string(i));
@@ -204,6 +204,11 @@ cudaError_t enqueue_step(titan_sim *sim, cudaStream_t st, int b) {
     if (sim->accumulate == TITAN_ACCUM_CSR) {
         titan::SellView v{sim->d_slice_off, sim->d_nbr, sim->d_kl, sim->has_c ? sim->d_c : nullptr,
                           sim->has_act ? sim->d_act : nullptr, 0, sim->spin_limit, sim->d_err};
+        if (sim->csr_kernel == 6) {
+            titan::BoxView h{sim->d_col_off, sim->d_own_slot, sim->d_ext_off, sim->d_ext_idx, sim->d_ext_slot,
+                             sim->box.max_table};
+            return titan::launch_step_box(in, out, sim->n_dev, v, h, sim->c, si, so, st);
+        }
         if (sim->csr_kernel == 4 || sim->csr_kernel == 5) {
             titan::HaloView h{sim->d_nslot, sim->d_own_slot, sim->d_ext_off, sim->d_ext_idx,
                               sim->d_ext_slot, sim->halo.max_table, sim->halo_ahead};
@@ -344,6 +349,7 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
 
     // ---- host-side layout
     const uint32_t n = m->n, s = sp->n;
+    std::vector<int32_t> cells;           // grid cell per device index (grid-tile order only)
     if (p->order == TITAN_ORDER_MORTON) {
         // masses on a grid (pitch = shortest spring) get the grid-tile order, others Morton
         double h = INFINITY;
@@ -356,9 +362,12 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
             }
             if (d2 > 0) h = std::min(h, std::sqrt(d2));
         }
-        sim->grid_order = s > 0 && titan::grid_tile_order(m->pos, n, h, sim->caller_of_dev) &&
+        sim->grid_order = s > 0 && titan::grid_tile_order(m->pos, n, h, sim->caller_of_dev, &cells) &&
                           sim->caller_of_dev.size() <= 2 * (size_t)n + 4096;
-        if (!sim->grid_order) titan::morton_order(m->pos, n, sim->caller_of_dev);
+        if (!sim->grid_order) {
+            cells.clear();
+            titan::morton_order(m->pos, n, sim->caller_of_dev);
+        }
     } else {
         sim->caller_of_dev.resize(n);
         for (uint32_t i = 0; i < n; ++i) sim->caller_of_dev[i] = i;
@@ -436,10 +445,18 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
     }
 
     if (sim->accumulate == TITAN_ACCUM_CSR) {
-        if (!titan::build_sell(nd, s, sp->ends, m->pos, sim->dev_of_caller, sim->sell))
+        if (!titan::build_sell(nd, s, sp->ends, m->pos, sim->dev_of_caller, sim->sell,
+                               sim->grid_order ? cells.data() : nullptr))
             return bail(fail(sim, TITAN_E_UNSUPPORTED, "padded incidence exceeds 2^32 entries"));
         const int want = p->kernel_variant;
-        sim->csr_kernel = want == 0 ? 4 : want;
+        sim->csr_kernel = want == 0 ? (sim->grid_order ? 6 : 4) : want;
+        if (sim->csr_kernel == 6 &&
+            !(sim->grid_order && titan::build_box(nd, sim->sell, cells, kHaloMaxSlots, sim->box))) {
+            if (want == 6)
+                return bail(fail(sim, TITAN_E_UNSUPPORTED, "the grid box kernel needs masses on a grid whose "
+                                                           "blocks' boxes fit " + std::to_string(kHaloMaxSlots) + " slots"));
+            sim->csr_kernel = 4;
+        }
         if ((sim->csr_kernel == 4 || sim->csr_kernel == 5) &&
             !titan::build_halo(nd, sim->sell, kHaloMaxSlots, sim->grid_order, sim->halo)) {
             if (want == 4 || want == 5)
@@ -466,7 +483,19 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
         CREATE_CK(dev_alloc(sim, &sim->d_kl, E));
         CREATE_CK(upload(sim->d_slice_off, sim->sell.slice_off, sim->stream));
         CREATE_CK(upload(sim->d_kl, kl, sim->stream));
-        if (sim->csr_kernel == 4 || sim->csr_kernel == 5) {
+        if (sim->csr_kernel == 6) {
+            const titan::BoxHost &h = sim->box;
+            CREATE_CK(dev_alloc(sim, &sim->d_col_off, h.col_off.size()));
+            CREATE_CK(dev_alloc(sim, &sim->d_own_slot, nd));
+            CREATE_CK(dev_alloc(sim, &sim->d_ext_off, h.ext_off.size()));
+            CREATE_CK(dev_alloc(sim, &sim->d_ext_idx, h.ext_idx.size()));
+            CREATE_CK(dev_alloc(sim, &sim->d_ext_slot, h.ext_slot.size()));
+            CREATE_CK(upload(sim->d_col_off, h.col_off, sim->stream));
+            CREATE_CK(upload(sim->d_own_slot, h.own_slot, sim->stream));
+            CREATE_CK(upload(sim->d_ext_off, h.ext_off, sim->stream));
+            CREATE_CK(upload(sim->d_ext_idx, h.ext_idx, sim->stream));
+            CREATE_CK(upload(sim->d_ext_slot, h.ext_slot, sim->stream));
+        } else if (sim->csr_kernel == 4 || sim->csr_kernel == 5) {
             sim->halo_ahead = 0;    // each warp prefetches its own slice
             const titan::HaloHost &h = sim->halo;
             CREATE_CK(dev_alloc(sim, &sim->d_nslot, E));
@@ -694,6 +723,11 @@ titan_status titan_sync(titan_sim *sim) {
 }
 
 uint64_t titan_steps(const titan_sim *sim) { return sim ? sim->steps : 0; }
+
+int32_t titan_csr_kernel(const titan_sim *sim) {
+    if (!sim) return -1;
+    return sim->accumulate == TITAN_ACCUM_CSR ? sim->csr_kernel : 0;
+}
 
 const char *titan_last_error(const titan_sim *sim) {
     return sim ? sim->error.c_str() : g_thread_error.c_str();

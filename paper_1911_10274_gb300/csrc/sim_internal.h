@@ -38,8 +38,9 @@ struct SimCore {
     std::vector<float> act_amp, act_phase;
     titan::SellHost sell;
     titan::HaloHost halo;
+    titan::BoxHost box;
     titan::RecordsHost rec;
-    int csr_kernel = 0;                   // resolved: 1 direct, 2 smem-staged, 3 bulk-prefetch, 4 halo, 5 halo+TMA
+    int csr_kernel = 0;                   // resolved: 1 direct, 2 smem-staged, 3 bulk-prefetch, 4 halo, 5 halo+TMA, 6 grid box
     uint32_t halo_w_max = 0;              // staged columns per slice (halo+TMA kernel)
     uint32_t halo_ahead = 0;              // L2 prefetch distance in blocks (halo kernel)
 
@@ -51,7 +52,8 @@ struct SimCore {
 
     uint32_t *d_slice_off = nullptr, *d_nbr = nullptr;
     uint16_t *d_nslot = nullptr, *d_own_slot = nullptr, *d_ext_slot = nullptr;
-    uint32_t *d_ext_off = nullptr, *d_ext_idx = nullptr;
+    uint32_t *d_ext_off = nullptr, *d_ext_idx = nullptr;   // halo or box tables (whichever kernel runs)
+    int16_t *d_col_off = nullptr;         // box kernel: slot offset per SELL column
     float2 *d_kl = nullptr, *d_act = nullptr;
     float *d_c = nullptr;
 

@@ -151,6 +151,7 @@ k_step_sell_pf(const MassState *__restrict__ in, MassState *__restrict__ out, ui
 // warp's own slice (ahead = 0, the default: prefetching further ahead was
 // measured to lose lines to L2 eviction), or `ahead` blocks in advance.
 constexpr int kHaloThreads = 256;
+constexpr int kBoxMinBlocks = 6;       // resident CTAs per SM the register budget is sized for
 
 template <bool HAS_C, bool HAS_ACT>
 __device__ __forceinline__ void prefetch_slice(const uint32_t *slice_off, uint32_t sl, const uint16_t *nslot,
@@ -165,7 +166,7 @@ __device__ __forceinline__ void prefetch_slice(const uint32_t *slice_off, uint32
 }
 
 template <bool HAS_C, bool HAS_ACT, bool GROUND>
-__global__ void __launch_bounds__(kHaloThreads, 7)
+__global__ void __launch_bounds__(kHaloThreads, 6)
 k_step_halo(const MassState *__restrict__ in, MassState *__restrict__ out, uint32_t n,
             const uint32_t *__restrict__ slice_off, const uint16_t *__restrict__ nslot,
             const float2 *__restrict__ kl, const float *__restrict__ cc,
@@ -244,6 +245,113 @@ k_step_halo(const MassState *__restrict__ in, MassState *__restrict__ out, uint3
             }
             spring_force(p, v, qa0, make_float4(qa0.w, qb0.x, qb0.y, 0.f), a0.x, L0, c0, fx, fy, fz);
             spring_force(p, v, qa1, make_float4(qa1.w, qb1.x, qb1.y, 0.f), a1.x, L1, c1, fx, fy, fz);
+        }
+    }
+    integrate<GROUND>(p, v, fx, fy, fz, c, out + i);
+}
+
+// K1, grid-box form: k_step_halo for masses on a grid.  The block's table is
+// the box of cells around its masses (see build_box), so a neighbour's slot
+// is the mass's own slot plus the column's offset (one int16 per SELL column,
+// the same for every lane) and the half-edge stream carries only {k, L0}
+// (8 bytes instead of 10).  Padding entries ({k, L0} = {0, 0}; a real spring
+// has L0 > 0) may point at an empty cell of the box, whose table slot holds
+// whatever was there: they are skipped, never evaluated.
+template <bool HAS_C, bool HAS_ACT>
+__device__ __forceinline__ void prefetch_slice_box(const uint32_t *slice_off, uint32_t sl, const float2 *kl,
+                                                   const float *cc, const float2 *act) {
+    const uint32_t e0 = __ldg(slice_off + sl);
+    const uint32_t ne = __ldg(slice_off + sl + 1) - e0;
+    if (!ne) return;
+    ptx::bulk_prefetch_l2(kl + e0, ne * 8);
+    if (HAS_C) ptx::bulk_prefetch_l2(cc + e0, ne * 4);
+    if (HAS_ACT) ptx::bulk_prefetch_l2(act + e0, ne * 8);
+}
+
+template <bool HAS_C, bool HAS_ACT, bool GROUND>
+__global__ void __launch_bounds__(kHaloThreads, kBoxMinBlocks)
+k_step_box(const MassState *__restrict__ in, MassState *__restrict__ out, uint32_t n,
+           const uint32_t *__restrict__ slice_off, const uint32_t *__restrict__ col_off2,
+           const float2 *__restrict__ kl, const float *__restrict__ cc, const float2 *__restrict__ act,
+           const uint16_t *__restrict__ own_slot, const uint32_t *__restrict__ ext_off,
+           const uint32_t *__restrict__ ext_idx, const uint16_t *__restrict__ ext_slot, uint32_t table_slots,
+           StepConst c, const long long *__restrict__ step_in, long long *__restrict__ step_out) {
+    extern __shared__ float4 tab4[];
+    float4 *tA = tab4;
+    float2 *tB = reinterpret_cast<float2 *>(tab4 + table_slots);
+    const uint32_t b = blockIdx.x, tid = threadIdx.x;
+    const uint32_t i = b * kHaloThreads + tid;
+    const uint32_t lane = tid & 31, sl = i >> 5;
+    const uint32_t n_slices = (n + 31) >> 5;
+    long long step = 0;
+    if (HAS_ACT) step = *step_in;
+    if (b == 0 && tid == 0) *step_out = *step_in + 1;
+    const bool valid = i < n;
+
+    if (lane == 0 && sl < n_slices) prefetch_slice_box<HAS_C, HAS_ACT>(slice_off, sl, kl, cc, act);
+    uint32_t e0 = 0, width = 0, s_own = 0;
+    float4 p = make_float4(0.f, 0.f, 0.f, 0.f), v = p;
+    if (valid) {
+        e0 = __ldg(slice_off + sl);
+        width = (__ldg(slice_off + sl + 1) - e0) >> 5;
+        load_state(in + i, p, v);
+        s_own = own_slot[i];
+        tA[s_own] = make_float4(p.x, p.y, p.z, v.x);
+        tB[s_own] = make_float2(v.y, v.z);
+    }
+    const uint32_t h0 = __ldg(ext_off + b), h1 = __ldg(ext_off + b + 1);
+    for (uint32_t h = h0 + tid; h < h1; h += kHaloThreads) {
+        float4 q, ww;
+        load_state(in + __ldg(ext_idx + h), q, ww);
+        const uint32_t s = __ldg(ext_slot + h);
+        tA[s] = make_float4(q.x, q.y, q.z, ww.x);
+        tB[s] = make_float2(ww.y, ww.z);
+    }
+    __syncthreads();
+    if (!valid) return;
+
+    const float ph = HAS_ACT ? actuation_clock(c, step) : 0.f;
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+    if (width) {
+        // widths are even and slices start at even column counts, so a pair of
+        // int16 column offsets is one aligned 32-bit word
+        const uint32_t *co = col_off2 + (e0 >> 6);
+        uint32_t e = e0 + lane;
+        uint32_t no = __ldg(co);
+        float2 na0 = __ldcs(kl + e), na1 = __ldcs(kl + e + 32);
+        float nc0 = c.c_uniform, nc1 = c.c_uniform;
+        float2 ns0 = make_float2(0.f, 0.f), ns1 = ns0;
+        if (HAS_C) { nc0 = __ldcs(cc + e); nc1 = __ldcs(cc + e + 32); }
+        if (HAS_ACT) { ns0 = __ldcs(act + e); ns1 = __ldcs(act + e + 32); }
+        for (uint32_t t = 0; t < width; t += 2) {
+            const uint32_t o = no;
+            const float2 a0 = na0, a1 = na1;
+            const float c0 = nc0, c1 = nc1;
+            const float2 s0 = ns0, s1 = ns1;
+            if (t + 2 < width) {
+                e += 64;
+                no = __ldg(co + (t >> 1) + 1);
+                na0 = __ldcs(kl + e); na1 = __ldcs(kl + e + 32);
+                if (HAS_C) { nc0 = __ldcs(cc + e); nc1 = __ldcs(cc + e + 32); }
+                if (HAS_ACT) { ns0 = __ldcs(act + e); ns1 = __ldcs(act + e + 32); }
+            }
+            const uint32_t j0 = s_own + (uint32_t)(int32_t)(int16_t)(o & 0xffffu);
+            const uint32_t j1 = s_own + (uint32_t)(int32_t)(int16_t)(o >> 16);
+            float L0 = a0.y, L1 = a1.y;
+            if (HAS_ACT) {
+                L0 = actuated_length(c, a0.y, s0, ph);
+                L1 = actuated_length(c, a1.y, s1, ph);
+            }
+            if (a0.y != 0.f) {
+                const float4 qa = tA[j0];
+                const float2 qb = tB[j0];
+                spring_force(p, v, qa, make_float4(qa.w, qb.x, qb.y, 0.f), a0.x, L0, c0, fx, fy, fz);
+            }
+            if (a1.y != 0.f) {
+                const float4 qa = tA[j1];
+                const float2 qb = tB[j1];
+                spring_force(p, v, qa, make_float4(qa.w, qb.x, qb.y, 0.f), a1.x, L1, c1, fx, fy, fz);
+            }
         }
     }
     integrate<GROUND>(p, v, fx, fy, fz, c, out + i);
@@ -656,6 +764,41 @@ cudaError_t launch_step_halo(const MassState *in, MassState *out, uint32_t n, co
         else    { if (gr) TITAN_HALO(false, false, true); else TITAN_HALO(false, false, false); }
     }
 #undef TITAN_HALO
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_box(const MassState *in, MassState *out, uint32_t n, const SellView &v, const BoxView &h,
+                            const StepConst &c, const long long *step_in, long long *step_out,
+                            cudaStream_t stream) {
+    const bool hc = v.c != nullptr, ha = v.act != nullptr, gr = c.ground != 0;
+    const unsigned g = n ? (n + kHaloThreads - 1) / kHaloThreads : 1;
+    const size_t bytes = (size_t)h.table_slots * (sizeof(float4) + sizeof(float2));
+    if (reinterpret_cast<uintptr_t>(h.col_off) & 3) return cudaErrorInvalidValue;
+#define TITAN_BOX(HC, HA, GR)                                                                    \
+    do {                                                                                         \
+        auto kern = k_step_box<HC, HA, GR>;                                                      \
+        if (bytes > 48 * 1024) {                                                                 \
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes); \
+            if (e != cudaSuccess) return e;                                                      \
+        }                                                                                        \
+        {                                                                                        \
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, \
+                                                 (int)cudaSharedmemCarveoutMaxShared);            \
+            if (e != cudaSuccess) return e;                                                      \
+        }                                                                                        \
+        kern<<<g, kHaloThreads, bytes, stream>>>(in, out, n, v.slice_off,                        \
+                                                 reinterpret_cast<const uint32_t *>(h.col_off), v.kl, v.c, \
+                                                 v.act, h.own_slot, h.ext_off, h.ext_idx, h.ext_slot, \
+                                                 h.table_slots, c, step_in, step_out);           \
+    } while (0)
+    if (hc) {
+        if (ha) { if (gr) TITAN_BOX(true, true, true); else TITAN_BOX(true, true, false); }
+        else    { if (gr) TITAN_BOX(true, false, true); else TITAN_BOX(true, false, false); }
+    } else {
+        if (ha) { if (gr) TITAN_BOX(false, true, true); else TITAN_BOX(false, true, false); }
+        else    { if (gr) TITAN_BOX(false, false, true); else TITAN_BOX(false, false, false); }
+    }
+#undef TITAN_BOX
     return cudaGetLastError();
 }
 

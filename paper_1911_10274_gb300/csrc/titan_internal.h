@@ -64,6 +64,15 @@ struct HaloView {
     uint32_t ahead;              // blocks between a CTA and the block whose stream it prefetches
 };
 
+struct BoxView {
+    const int16_t *col_off;      // [E / 32] slot offset per SELL column (4-byte aligned)
+    const uint16_t *own_slot;    // [n] slot of each mass in its block's box
+    const uint32_t *ext_off;     // [n_blocks + 1]
+    const uint32_t *ext_idx;     // external entries: device index
+    const uint16_t *ext_slot;    //                   and slot
+    uint32_t table_slots;        // slots per box (shared memory = 24 B each)
+};
+
 struct AtomicView {
     const uint4 *rec;            // [S] {i, j, bits(k), bits(L0)}
     const float *c;              // [S] or nullptr
@@ -82,6 +91,11 @@ cudaError_t launch_step_sell(const MassState *in, MassState *out, uint32_t n, co
 cudaError_t launch_step_halo(const MassState *in, MassState *out, uint32_t n, const SellView &v,
                              const HaloView &h, const StepConst &c, const long long *step_in,
                              long long *step_out, cudaStream_t stream);
+
+// Grid-box form of the halo kernel (see step_kernels.cu).
+cudaError_t launch_step_box(const MassState *in, MassState *out, uint32_t n, const SellView &v, const BoxView &h,
+                            const StepConst &c, const long long *step_in, long long *step_out,
+                            cudaStream_t stream);
 
 // Halo form with the half-edge stream staged into shared memory by TMA bulk
 // copies; slices wider than w_max columns read from global memory.

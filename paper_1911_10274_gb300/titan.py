@@ -81,6 +81,7 @@ def load(path: Optional[str] = None):
                 "titan_read_state_dev": (S, [_P, _P, _P, _P]),
                 "titan_sync": (S, [_P]),
                 "titan_steps": (u64, [_P]),
+                "titan_csr_kernel": (C.c_int32, [_P]),
                 "titan_last_error": (C.c_char_p, [_P]),
                 "titan_destroy": (S, [_P]),
                 "titan_step_atomic_noalloc": (S, [u32, _P, _P, _P, u32, _P, _P, _P, f32,
@@ -472,6 +473,11 @@ class Sim:
     @property
     def steps(self) -> int:
         return titan_steps(self.handle)
+
+    @property
+    def csr_kernel(self) -> int:
+        """The step kernel in use: 1..6 (see titan_params.kernel_variant), 0 atomic."""
+        return int(load().titan_csr_kernel(self.handle))
 
     def close(self) -> None:
         if getattr(self, "handle", None):

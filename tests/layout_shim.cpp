@@ -1,0 +1,92 @@
+// layout_shim.cpp -- exposes the library's host-side layout builders
+// (paper_1911_10274_gb300/csrc/layout.cpp) through a C interface so that the
+// CPU tests can check the device layouts without a GPU.  Test infrastructure:
+// compiled by tests/test_layout_host.py together with layout.cpp.
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "layout.h"
+
+namespace {
+struct Built {
+    std::vector<uint32_t> caller_of_dev, dev_of_caller;
+    std::vector<int32_t> cell;
+    titan::SellHost sell;
+    titan::HaloHost halo;
+    titan::BoxHost box;
+    int grid = 0, box_ok = 0, halo_ok = 0;
+} g;
+
+template <typename T>
+void copy_out(const std::vector<T> &v, void *dst) {
+    if (!v.empty()) std::memcpy(dst, v.data(), v.size() * sizeof(T));
+}
+}  // namespace
+
+extern "C" {
+
+// Orders the masses as titan_create does (grid-tile order on a grid of pitch
+// h, else Morton), builds the SELL incidence and both neighbourhood tables.
+// Returns 0 on success, 1 if the SELL could not be built.
+int shim_build(const double *pos, uint32_t n, const uint32_t *ends, uint32_t s, double h, uint32_t max_slots) {
+    g = Built();
+    g.grid = titan::grid_tile_order(pos, n, h, g.caller_of_dev, &g.cell) ? 1 : 0;
+    if (!g.grid) titan::morton_order(pos, n, g.caller_of_dev);
+    const uint32_t nd = (uint32_t)g.caller_of_dev.size();
+    g.dev_of_caller.assign(n, 0);
+    for (uint32_t d = 0; d < nd; ++d)
+        if (g.caller_of_dev[d] != UINT32_MAX) g.dev_of_caller[g.caller_of_dev[d]] = d;
+    if (!titan::build_sell(nd, s, ends, pos, g.dev_of_caller, g.sell, g.grid ? g.cell.data() : nullptr)) return 1;
+    g.halo_ok = titan::build_halo(nd, g.sell, max_slots, g.grid != 0, g.halo) ? 1 : 0;
+    g.box_ok = g.grid && titan::build_box(nd, g.sell, g.cell, max_slots, g.box) ? 1 : 0;
+    return 0;
+}
+
+// Scalars: 0 n_dev, 1 entries, 2 grid, 3 box_ok, 4 halo_ok, 5 box max_table, 6 halo max_table.
+uint64_t shim_scalar(int which) {
+    switch (which) {
+        case 0: return g.caller_of_dev.size();
+        case 1: return g.sell.entries;
+        case 2: return (uint64_t)g.grid;
+        case 3: return (uint64_t)g.box_ok;
+        case 4: return (uint64_t)g.halo_ok;
+        case 5: return g.box.max_table;
+        case 6: return g.halo.max_table;
+        default: return 0;
+    }
+}
+
+// Array lengths and copies, by name.
+uint64_t shim_len(const char *name) {
+    const std::string k(name);
+    if (k == "caller_of_dev") return g.caller_of_dev.size();
+    if (k == "cell") return g.cell.size();
+    if (k == "slice_off") return g.sell.slice_off.size();
+    if (k == "nbr") return g.sell.nbr.size();
+    if (k == "spring") return g.sell.spring.size();
+    if (k == "entry_of_end") return g.sell.entry_of_end.size();
+    if (k == "col_off") return g.box.col_off.size();
+    if (k == "box_own_slot") return g.box.own_slot.size();
+    if (k == "box_ext_off") return g.box.ext_off.size();
+    if (k == "box_ext_idx") return g.box.ext_idx.size();
+    if (k == "box_ext_slot") return g.box.ext_slot.size();
+    return 0;
+}
+
+void shim_get(const char *name, void *dst) {
+    const std::string k(name);
+    if (k == "caller_of_dev") copy_out(g.caller_of_dev, dst);
+    if (k == "cell") copy_out(g.cell, dst);
+    if (k == "slice_off") copy_out(g.sell.slice_off, dst);
+    if (k == "nbr") copy_out(g.sell.nbr, dst);
+    if (k == "spring") copy_out(g.sell.spring, dst);
+    if (k == "entry_of_end") copy_out(g.sell.entry_of_end, dst);
+    if (k == "col_off") copy_out(g.box.col_off, dst);
+    if (k == "box_own_slot") copy_out(g.box.own_slot, dst);
+    if (k == "box_ext_off") copy_out(g.box.ext_off, dst);
+    if (k == "box_ext_idx") copy_out(g.box.ext_idx, dst);
+    if (k == "box_ext_slot") copy_out(g.box.ext_slot, dst);
+}
+
+}  // extern "C"

@@ -43,10 +43,11 @@ MODES = [dict(accumulate=T.ACCUM_CSR), dict(accumulate=T.ACCUM_ATOMIC),
          dict(accumulate=T.ACCUM_CSR, kernel_variant=3),
          dict(accumulate=T.ACCUM_CSR, kernel_variant=4),
          dict(accumulate=T.ACCUM_CSR, kernel_variant=5),
+         dict(accumulate=T.ACCUM_CSR, kernel_variant=6),
          dict(accumulate=T.ACCUM_CSR, order=T.ORDER_INPUT),
          dict(accumulate=T.ACCUM_CSR, graph_chunk=-1)]
 MODE_IDS = ["csr", "atomic", "csr-direct-loads", "csr-tma-staged", "csr-bulk-prefetch", "csr-halo",
-            "csr-halo-tma", "csr-input-order", "csr-no-graph"]
+            "csr-halo-tma", "csr-grid-box", "csr-input-order", "csr-no-graph"]
 
 
 @pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
@@ -136,7 +137,7 @@ def test_lattice_with_holes_in_grid_tiles():
                         fixed=np.zeros(len(pos), np.uint8), ends=ends, k=np.full(len(ends), 1e4),
                         rest=d * rng.uniform(0.97, 1.03, len(d)), damping=np.full(len(ends), 1.0),
                         dt=1e-4, ground=True, spacing=0.1)
-    for var in (0, 5, 4, 3):
+    for var in (0, 6, 5, 4, 3):
         check(sys, 1000, kernel_variant=var)
 
 
@@ -201,7 +202,7 @@ def test_csr_kernel_variants_agree_bit_exact():
     sys = inputs.cube_drop(drop_height=0.02)
     sys.vel[:, 0] = 0.3
     a = gpu_run(sys, 500, kernel_variant=0)
-    for var in (1, 2, 3, 4, 5):
+    for var in (1, 2, 3, 4, 5, 6):
         b = gpu_run(sys, 500, kernel_variant=var)
         assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
 
@@ -302,9 +303,49 @@ def test_full_size_lattice_against_oracle_in_bench_configuration():
     xo, vo = oracle.run(sys, 64)
     for mode in (dict(accumulate=T.ACCUM_CSR), dict(accumulate=T.ACCUM_CSR, kernel_variant=1),
                  dict(accumulate=T.ACCUM_CSR, kernel_variant=2), dict(accumulate=T.ACCUM_CSR, kernel_variant=3),
-                 dict(accumulate=T.ACCUM_CSR, kernel_variant=4), dict(accumulate=T.ACCUM_ATOMIC)):
+                 dict(accumulate=T.ACCUM_CSR, kernel_variant=4), dict(accumulate=T.ACCUM_CSR, kernel_variant=6),
+                 dict(accumulate=T.ACCUM_ATOMIC)):
         xg, vg, _ = gpu_run(sys, 64, **mode)
         err = np.abs(xg - xo).max()
         assert err <= POS_TOL_FRAC * sys.spacing, err
         fx = sys.fixed.astype(bool)
         assert np.array_equal(xg[fx], sys.pos[fx].astype(np.float32).astype(np.float64))
+
+
+def test_auto_kernel_choice():
+    """Auto picks the grid-box kernel for masses on a grid, the coloured halo
+    kernel for an unstructured mesh; the box kernel refuses a mesh."""
+    with T.Sim(inputs.cube_drop(n=6)) as sim:
+        assert sim.csr_kernel == 6
+    mesh = inputs.random_mesh(n_points=3000, seed=2, lift=0.0)
+    with T.Sim(mesh) as sim:
+        assert sim.csr_kernel == 4
+    with T.Sim(mesh, accumulate=T.ACCUM_ATOMIC) as sim:
+        assert sim.csr_kernel == 0
+    with pytest.raises(T.TitanError, match="grid"):
+        T.Sim(mesh, kernel_variant=6)
+
+
+def test_grid_with_second_neighbour_springs_and_duplicates():
+    """Springs two cells apart (same direction class as the nearest
+    neighbour, a different cell offset) and a duplicated spring: the box
+    kernel's offset-aligned columns hold them apart; all kernels agree with
+    the oracle and with each other bit for bit."""
+    n = 6
+    pos = inputs.lattice_points(n, n, n, 0.1, (0.0, 0.0, 0.2))
+    ends = inputs.lattice_springs(n, n, n)
+    idx = np.arange(n ** 3).reshape(n, n, n)          # [z][y][x], as lattice_points numbers the sites
+    far = np.stack([idx[:-2].ravel(), idx[2:].ravel()], 1)
+    ends = np.concatenate([ends, far, ends[:7]]).astype(np.uint32)
+    d = np.linalg.norm(pos[ends[:, 1]] - pos[ends[:, 0]], axis=1)
+    rng = np.random.default_rng(4)
+    sys = inputs.System(pos=pos, vel=rng.normal(0, 0.05, pos.shape), mass=np.full(len(pos), 0.1),
+                        fixed=np.zeros(len(pos), np.uint8), ends=ends, k=rng.uniform(5e3, 2e4, len(ends)),
+                        rest=d * rng.uniform(0.97, 1.03, len(d)), damping=np.full(len(ends), 1.0),
+                        dt=1e-4, ground=True, spacing=0.1)
+    with T.Sim(sys) as sim:
+        assert sim.csr_kernel == 6
+    runs = [gpu_run(sys, 400, kernel_variant=v) for v in (6, 4, 3)]
+    for r in runs[1:]:
+        assert np.array_equal(runs[0][0], r[0]) and np.array_equal(runs[0][1], r[1])
+    check(sys, 400)

@@ -1,0 +1,183 @@
+"""Host-side layout builders (csrc/layout.cpp), checked on the CPU.
+
+The step kernels trust these tables for every shared-memory and global index
+they form, so the checks here are the bounds and consistency conditions the
+kernels rely on: every spring appears once from each end, in the row of its
+mass, pointing at its other end; on a grid every SELL column holds one cell
+offset; every box-table read, padding included, lands inside its block's box
+and on the slot of the intended neighbour; own and external slots are
+distinct; and on a full lattice the box reads are free of shared-memory bank
+conflicts.  layout.cpp is compiled here with the host compiler, through a
+small C shim (tests/layout_shim.cpp).
+"""
+import ctypes as C
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_1911_10274_gb300 import inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_1911_10274_gb300", "csrc")
+MAX_SLOTS = 1152
+BLOCK = 256
+
+
+@pytest.fixture(scope="module")
+def shim(tmp_path_factory):
+    if shutil.which("g++") is None:
+        pytest.skip("no host C++ compiler")
+    out = str(tmp_path_factory.mktemp("shim") / "liblayout_shim.so")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-I", CSRC,
+                    os.path.join(CSRC, "layout.cpp"), os.path.join(ROOT, "tests", "layout_shim.cpp"),
+                    "-o", out], check=True)
+    lib = C.CDLL(out)
+    lib.shim_build.restype = C.c_int
+    lib.shim_build.argtypes = [C.c_void_p, C.c_uint32, C.c_void_p, C.c_uint32, C.c_double, C.c_uint32]
+    lib.shim_scalar.restype = C.c_uint64
+    lib.shim_len.restype = C.c_uint64
+    lib.shim_len.argtypes = [C.c_char_p]
+    lib.shim_get.argtypes = [C.c_char_p, C.c_void_p]
+    return lib
+
+
+class Layout:
+    DT = {"caller_of_dev": np.uint32, "cell": np.int32, "slice_off": np.uint32, "nbr": np.uint32,
+          "spring": np.uint32, "entry_of_end": np.uint32, "col_off": np.int16, "box_own_slot": np.uint16,
+          "box_ext_off": np.uint32, "box_ext_idx": np.uint32, "box_ext_slot": np.uint16}
+
+    def __init__(self, lib, pos, ends):
+        pos = np.ascontiguousarray(pos, np.float64)
+        ends = np.ascontiguousarray(ends, np.uint32)
+        d = np.linalg.norm(pos[ends[:, 1]] - pos[ends[:, 0]], axis=1)
+        h = float(d[d > 0].min())
+        assert lib.shim_build(pos.ctypes.data, len(pos), ends.ctypes.data, len(ends), h, MAX_SLOTS) == 0
+        self.n, self.s = len(pos), len(ends)
+        self.ends = ends
+        self.n_dev, self.entries, self.grid, self.box_ok, self.halo_ok, self.box_slots, _ = \
+            [int(lib.shim_scalar(k)) for k in range(7)]
+        for name, dt in self.DT.items():
+            a = np.empty(int(lib.shim_len(name.encode())), dt)
+            if a.size:
+                lib.shim_get(name.encode(), a.ctypes.data)
+            setattr(self, name, a)
+        self.dev_of = np.zeros(self.n, np.int64)
+        real = self.caller_of_dev != np.uint32(0xFFFFFFFF)
+        self.dev_of[self.caller_of_dev[real]] = np.nonzero(real)[0]
+
+    def entry_coords(self):
+        """(row mass, column index in the slice, global column) of every entry."""
+        e = np.arange(self.entries, dtype=np.int64)
+        sl = np.searchsorted(self.slice_off.astype(np.int64), e, side="right") - 1
+        rel = e - self.slice_off[sl].astype(np.int64)
+        return sl * 32 + rel % 32, rel // 32, self.slice_off[sl].astype(np.int64) // 32 + rel // 32
+
+
+def lattice(nx, ny, nz, occupied=None):
+    return inputs.lattice_points(nx, ny, nz, 0.1), inputs.lattice_springs(nx, ny, nz, occupied)
+
+
+def check_sell(L):
+    assert L.slice_off[0] == 0 and L.slice_off[-1] == L.entries
+    assert np.all(np.diff(L.slice_off) % 64 == 0)                 # even widths of 32-entry columns
+    real = L.spring != np.uint32(0xFFFFFFFF)
+    assert real.sum() == 2 * L.s
+    row, _, _ = L.entry_coords()
+    # every spring once from each end, in its mass's row, pointing at the other end
+    for end in (0, 1):
+        e = L.entry_of_end[end::2].astype(np.int64)
+        assert np.array_equal(L.spring[e], np.arange(L.s, dtype=np.uint32))
+        assert np.array_equal(row[e], L.dev_of[L.ends[:, end]])
+        assert np.array_equal(L.nbr[e], L.dev_of[L.ends[:, 1 - end]])
+    pad = ~real
+    assert np.array_equal(L.nbr[pad], np.where(row[pad] < L.n_dev, row[pad], 0))
+
+
+def check_box(L):
+    assert L.box_ok
+    row, _, gcol = L.entry_coords()
+    real = L.spring != np.uint32(0xFFFFFFFF)
+    cell = L.cell.reshape(-1, 3).astype(np.int64)
+    # columns are offset-aligned: one cell offset per (slice, column)
+    off = cell[L.nbr[real]] - cell[row[real]]
+    key = gcol[real]
+    order = np.argsort(key, kind="stable")
+    k_sorted, o_sorted = key[order], off[order]
+    same = k_sorted[1:] == k_sorted[:-1]
+    assert np.all(o_sorted[1:][same] == o_sorted[:-1][same])
+    # slot arithmetic: own slot + column offset is the neighbour's slot in this block's box
+    own = L.box_own_slot.astype(np.int64)
+    blk = row // BLOCK
+    slot_of = {}
+    n_blocks = (L.n_dev + BLOCK - 1) // BLOCK
+    for b in range(n_blocks):
+        m0, m1 = b * BLOCK, min(L.n_dev, (b + 1) * BLOCK)
+        ext = L.box_ext_idx[L.box_ext_off[b]:L.box_ext_off[b + 1]].astype(np.int64)
+        eslot = L.box_ext_slot[L.box_ext_off[b]:L.box_ext_off[b + 1]].astype(np.int64)
+        slots = np.concatenate([own[m0:m1], eslot])
+        assert len(np.unique(slots)) == len(slots), f"block {b}: slots collide"
+        assert slots.max() < L.box_slots and slots.min() >= 0
+        assert not np.any((ext >= m0) & (ext < m1))
+        slot_of[b] = dict(zip(np.concatenate([np.arange(m0, m1), ext]).tolist(), slots.tolist()))
+    read = own[row] + L.col_off[gcol].astype(np.int64)
+    valid_row = row < L.n_dev
+    assert np.all(read[valid_row] >= 0) and np.all(read[valid_row] < L.box_slots)   # padding included
+    for e in np.nonzero(real)[0]:
+        assert read[e] == slot_of[blk[e]][int(L.nbr[e])]
+
+
+def test_full_lattice_grid_layout_and_box_tables(shim):
+    pos, ends = lattice(16, 16, 8)
+    L = Layout(shim, pos, ends)
+    assert L.grid and L.n_dev == L.n                            # 16 x 16 x 8 fills whole 8 x 8 x 4 cubes
+    assert L.box_slots == 12 * 10 * 6                           # (8 + 2 -> 12) x (8 + 2) x (4 + 2)
+    check_sell(L)
+    check_box(L)
+    # bank conflicts: per column, each quarter-warp's 16-byte reads hit 8 distinct
+    # 16-byte bank groups, each half-warp's 8-byte reads 16 distinct 8-byte groups
+    row, t, gcol = L.entry_coords()
+    real = L.spring != np.uint32(0xFFFFFFFF)
+    read = L.box_own_slot[row].astype(np.int64) + L.col_off[gcol].astype(np.int64)
+    lane = row % 32
+    bad = 0
+    groups = 0
+    for width, mod in ((8, 8), (16, 16)):
+        gid = gcol * (32 // width) + lane // width
+        for g in np.unique(gid):
+            sel = (gid == g) & real
+            if sel.sum() < width:
+                continue                                          # boundary columns with padding
+            groups += 1
+            bad += len(np.unique(read[sel] % mod)) != width
+    assert groups > 0 and bad == 0
+
+
+def test_lattice_with_holes_and_second_neighbours(shim):
+    pos, ends = lattice(10, 7, 5)
+    idx = np.arange(10 * 7 * 5).reshape(5, 7, 10)
+    far = np.stack([idx[:, :, :-2].ravel(), idx[:, :, 2:].ravel()], 1)
+    dup = ends[:5]
+    L = Layout(shim, pos, np.concatenate([ends, far, dup]))
+    assert L.grid and L.n_dev > L.n                             # holes in partly filled cubes
+    check_sell(L)
+    check_box(L)
+
+
+def test_voxel_robot_layout(shim):
+    rng = np.random.default_rng(3)
+    occ = inputs.voxel_morphology(rng)
+    sys = inputs.voxel_robot(occ, rng.uniform(0, 2 * np.pi, occ.shape))
+    L = Layout(shim, sys.pos, sys.ends)
+    assert L.grid
+    check_sell(L)
+    check_box(L)
+
+
+def test_unstructured_mesh_is_not_a_grid(shim):
+    sys = inputs.random_mesh(n_points=2000, seed=5, lift=0.0)
+    L = Layout(shim, sys.pos, sys.ends)
+    assert not L.grid and not L.box_ok and L.n_dev == L.n
+    check_sell(L)
