@@ -31,10 +31,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "spring updates/s"
-CSR_KERNELS = ["auto (halo table in shared memory)", "direct-loads", "tma-staged", "bulk-l2-prefetch",
-               "halo", "halo+tma"]
-CSR_KERNEL_NAMES = ["k_step_halo", "k_step_sell", "k_step_sell_staged", "k_step_sell_pf", "k_step_halo",
-                    "k_step_halo_tma"]
+# the step kernel a Sim resolved to (titan_csr_kernel), and its description
+CSR_KERNEL_NAMES = {0: "k_springs_atomic+k_masses_atomic", 1: "k_step_sell", 2: "k_step_sell_staged",
+                    3: "k_step_sell_pf", 4: "k_step_halo", 5: "k_step_halo_tma", 6: "k_step_box"}
+CSR_KERNELS = {0: "atomic scatter", 1: "direct-loads", 2: "tma-staged", 3: "bulk-l2-prefetch",
+               4: "halo (coloured neighbourhood table in shared memory)", 5: "halo+tma",
+               6: "grid box (box table in shared memory, no neighbour index in the stream)"}
 UNIT = "spring_updates/s"
 L2_BYTES = 126 * 1024 * 1024
 
@@ -180,7 +182,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_for(args, None),
+            "data": "synthetic", "config": config_for(args, None, auto_kernel(args)),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"each step: one FP64 oracle time step of a {system.name} "
                                        f"sub-lattice ({system.n_masses} masses, {system.n_springs} springs) "
@@ -189,12 +191,22 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def config_for(args, system):
+def auto_kernel(args):
+    """The step kernel our arm resolves to on this workload (for the reference arm's config)."""
+    if args.accumulate != "csr":
+        return 0
+    if args.kernel_variant:
+        return args.kernel_variant
+    return 4 if args.workload == "mesh2m" else 6
+
+
+def config_for(args, system, resolved=None):
     cfg = {"workload": {"lattice1m": "1M-mass lattice 100^3, 12,731,796 springs, fixed base, no ground, dt=5e-5",
                         "lattice50": "50^3 lattice, 1,558,396 springs", "mesh2m": "2M-point kNN mesh",
                         "cube1k": "10^3 cube drop"}[args.workload],
-           "accumulate": args.accumulate, "order": "morton", "graph_chunk": 64,
-           "csr_kernel": CSR_KERNELS[args.kernel_variant],
+           "accumulate": args.accumulate,
+           "order": "grid cubes of 8x8x4 cells, Morton" if resolved == 6 else "morton", "graph_chunk": 64,
+           "csr_kernel": CSR_KERNELS.get(resolved, f"variant {args.kernel_variant}"),
            "parallelism": f"replicas x{args.gpus}",
            "l2": "inputs larger than L2 (spring data > 126 MB), no flush"}
     if system is not None:
@@ -354,6 +366,7 @@ def run_ours(args):
     sim = T.Sim(system, accumulate=acc, stream=stream.cuda_stream, device=local,
                 kernel_variant=args.kernel_variant)
     launches_per_step = 1 if acc == T.ACCUM_CSR else 2
+    resolved = sim.csr_kernel
 
     def barrier():
         torch.cuda.synchronize()
@@ -398,11 +411,10 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * step_s, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": config_for(args, system),
+        "config": config_for(args, system, resolved),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": CSR_KERNEL_NAMES[args.kernel_variant]
-                     if acc == T.ACCUM_CSR else "k_springs_atomic+k_masses_atomic",
+                     "kernel": CSR_KERNEL_NAMES[resolved],
                      "algorithmic_bytes_per_launch": alg,
                      "peak_source": f"{peak_kind} HBM copy bandwidth"},
         "e2e": {"value": e2e_value, "unit": UNIT,
@@ -461,7 +473,7 @@ def main():
     ap.add_argument("--robots", type=int, default=4096, help="robots of the --leg batched/adjoint run")
     ap.add_argument("--rollout-steps", type=int, default=2000, help="rollout steps of the --leg run")
     ap.add_argument("--untuned", action="store_true", help="--leg batched: keep the default launch shapes")
-    ap.add_argument("--kernel-variant", type=int, default=0, help="CSR kernel: 0 auto, 1 direct loads, 2 TMA-staged, 3 bulk L2 prefetch, 4 halo, 5 halo+TMA")
+    ap.add_argument("--kernel-variant", type=int, default=0, help="CSR kernel: 0 auto, 1 direct loads, 2 TMA-staged, 3 bulk L2 prefetch, 4 halo, 5 halo+TMA, 6 grid box")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
