@@ -384,12 +384,15 @@ bool build_halo(uint32_t n, const SellHost &sell, uint32_t max_slots, bool grid_
     return true;
 }
 
-bool build_box(uint32_t n, const SellHost &sell, const std::vector<int32_t> &cell, uint32_t max_slots,
-               BoxHost &out) {
+bool build_box(uint32_t n, const SellHost &sell, const std::vector<int32_t> &cell,
+               const std::vector<uint32_t> &caller_of_dev, uint32_t max_slots, BoxHost &out) {
     const uint32_t n_blocks = (n + kHaloBlock - 1) / kHaloBlock;
     const uint32_t slices_per_block = kHaloBlock / 32;
     const uint32_t n_slices = (n + 31) / 32;
-    if (cell.size() != 3 * (size_t)n || sell.slice_off.size() != (size_t)n_slices + 1) return false;
+    if (cell.size() != 3 * (size_t)n || caller_of_dev.size() != n || sell.slice_off.size() != (size_t)n_slices + 1)
+        return false;
+    if (max_slots >= kBoxHole) return false;
+    auto hole = [&](uint32_t m) { return caller_of_dev[m] == UINT32_MAX; };
     out.col_off.assign(sell.entries / 32, 0);
     out.own_slot.assign(n, 0);
     out.ext_off.assign(n_blocks + 1, 0);
@@ -428,7 +431,7 @@ bool build_box(uint32_t n, const SellHost &sell, const std::vector<int32_t> &cel
         auto slot = [&](uint32_t m) -> int64_t {
             return (C[3 * (size_t)m] - lo[0]) + dim[0] * ((C[3 * (size_t)m + 1] - lo[1]) + dim[1] * (C[3 * (size_t)m + 2] - lo[2]));
         };
-        for (uint32_t m = m0; m < m1; ++m) out.own_slot[m] = (uint16_t)slot(m);
+        for (uint32_t m = m0; m < m1; ++m) out.own_slot[m] = hole(m) ? kBoxHole : (uint16_t)slot(m);
         seen.clear();
         for (uint32_t sl = sl0; sl < sl1; ++sl) {
             const uint32_t e0 = sell.slice_off[sl], w = (sell.slice_off[sl + 1] - e0) / 32;
@@ -439,6 +442,7 @@ bool build_box(uint32_t n, const SellHost &sell, const std::vector<int32_t> &cel
                     const uint32_t e = e0 + 32 * t + l, i = sl * 32 + l;
                     if (i >= n || sell.spring[e] == UINT32_MAX) continue;
                     const uint32_t j = sell.nbr[e];
+                    if (hole(i) || hole(j)) return false;             // holes have no springs
                     const int64_t o = slot(j) - slot(i);
                     if (have && o != off) return false;           // column not offset-aligned
                     // the neighbour's cell must be exactly the offset cell
@@ -451,7 +455,7 @@ bool build_box(uint32_t n, const SellHost &sell, const std::vector<int32_t> &cel
                 // every lane's read, padding included, must stay inside the box
                 for (uint32_t l = 0; l < 32; ++l) {
                     const uint32_t i = sl * 32 + l;
-                    if (i >= n) continue;
+                    if (i >= n || hole(i)) continue;
                     const int64_t r = slot(i) + off;
                     if (r < 0 || r >= slots) return false;
                 }

@@ -78,7 +78,7 @@ bool build_halo(uint32_t n, const SellHost &sell, uint32_t max_slots, bool grid_
 // column's offset, and the half-edge stream needs no neighbour index.
 struct BoxHost {
     std::vector<int16_t> col_off;        // [E / 32] slot offset of every SELL column
-    std::vector<uint16_t> own_slot;      // [n]
+    std::vector<uint16_t> own_slot;      // [n] (kBoxHole for holes)
     std::vector<uint32_t> ext_off;       // [n_blocks + 1]
     std::vector<uint32_t> ext_idx;       // device index of each external table entry
     std::vector<uint16_t> ext_slot;      // its slot
@@ -88,8 +88,11 @@ struct BoxHost {
 // Returns false if some box exceeds max_slots or a column is not
 // offset-aligned.  Checks that every entry's table read, padding included,
 // stays inside its block's box.
-bool build_box(uint32_t n, const SellHost &sell, const std::vector<int32_t> &cell, uint32_t max_slots,
-               BoxHost &out);
+// caller_of_dev marks holes (UINT32_MAX): they get own_slot = kBoxHole and
+// no table slot; the box kernel neither reads nor writes their state.
+constexpr uint16_t kBoxHole = 0xFFFF;
+bool build_box(uint32_t n, const SellHost &sell, const std::vector<int32_t> &cell,
+               const std::vector<uint32_t> &caller_of_dev, uint32_t max_slots, BoxHost &out);
 
 struct RecordsHost {
     std::vector<uint32_t> order;            // [S] record r holds caller spring order[r]

@@ -451,7 +451,7 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
         const int want = p->kernel_variant;
         sim->csr_kernel = want == 0 ? (sim->grid_order ? 6 : 4) : want;
         if (sim->csr_kernel == 6 &&
-            !(sim->grid_order && titan::build_box(nd, sim->sell, cells, kHaloMaxSlots, sim->box))) {
+            !(sim->grid_order && titan::build_box(nd, sim->sell, cells, sim->caller_of_dev, kHaloMaxSlots, sim->box))) {
             if (want == 6)
                 return bail(fail(sim, TITAN_E_UNSUPPORTED, "the grid box kernel needs masses on a grid whose "
                                                            "blocks' boxes fit " + std::to_string(kHaloMaxSlots) + " slots"));

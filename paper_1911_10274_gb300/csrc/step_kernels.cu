@@ -151,6 +151,7 @@ k_step_sell_pf(const MassState *__restrict__ in, MassState *__restrict__ out, ui
 // warp's own slice (ahead = 0, the default: prefetching further ahead was
 // measured to lose lines to L2 eviction), or `ahead` blocks in advance.
 constexpr int kHaloThreads = 256;
+constexpr uint32_t kBoxHoleSlot = 0xFFFF;   // own slot of a hole (layout.h: kBoxHole)
 constexpr int kBoxMinBlocks = 6;       // resident CTAs per SM the register budget is sized for
 
 template <bool HAS_C, bool HAS_ACT>
@@ -256,7 +257,8 @@ k_step_halo(const MassState *__restrict__ in, MassState *__restrict__ out, uint3
 // the same for every lane) and the half-edge stream carries only {k, L0}
 // (8 bytes instead of 10).  Padding entries ({k, L0} = {0, 0}; a real spring
 // has L0 > 0) may point at an empty cell of the box, whose table slot holds
-// whatever was there: they are skipped, never evaluated.
+// whatever was there: they are skipped, never evaluated.  Holes - device
+// slots of empty cells, marked by own slot 0xFFFF - do nothing at all.
 template <bool HAS_C, bool HAS_ACT>
 __device__ __forceinline__ void prefetch_slice_box(const uint32_t *slice_off, uint32_t sl, const float2 *kl,
                                                    const float *cc, const float2 *act) {
@@ -286,16 +288,18 @@ k_step_box(const MassState *__restrict__ in, MassState *__restrict__ out, uint32
     long long step = 0;
     if (HAS_ACT) step = *step_in;
     if (b == 0 && tid == 0) *step_out = *step_in + 1;
-    const bool valid = i < n;
+    // holes (empty cells of the block's cube) have no springs and never move:
+    // their state is neither read nor written
+    const uint32_t s_own = i < n ? own_slot[i] : kBoxHoleSlot;
+    const bool valid = s_own != kBoxHoleSlot;
 
     if (lane == 0 && sl < n_slices) prefetch_slice_box<HAS_C, HAS_ACT>(slice_off, sl, kl, cc, act);
-    uint32_t e0 = 0, width = 0, s_own = 0;
+    uint32_t e0 = 0, width = 0;
     float4 p = make_float4(0.f, 0.f, 0.f, 0.f), v = p;
     if (valid) {
         e0 = __ldg(slice_off + sl);
         width = (__ldg(slice_off + sl + 1) - e0) >> 5;
         load_state(in + i, p, v);
-        s_own = own_slot[i];
         tA[s_own] = make_float4(p.x, p.y, p.z, v.x);
         tB[s_own] = make_float2(v.y, v.z);
     }

@@ -39,7 +39,7 @@ int shim_build(const double *pos, uint32_t n, const uint32_t *ends, uint32_t s, 
         if (g.caller_of_dev[d] != UINT32_MAX) g.dev_of_caller[g.caller_of_dev[d]] = d;
     if (!titan::build_sell(nd, s, ends, pos, g.dev_of_caller, g.sell, g.grid ? g.cell.data() : nullptr)) return 1;
     g.halo_ok = titan::build_halo(nd, g.sell, max_slots, g.grid != 0, g.halo) ? 1 : 0;
-    g.box_ok = g.grid && titan::build_box(nd, g.sell, g.cell, max_slots, g.box) ? 1 : 0;
+    g.box_ok = g.grid && titan::build_box(nd, g.sell, g.cell, g.caller_of_dev, max_slots, g.box) ? 1 : 0;
     return 0;
 }
 

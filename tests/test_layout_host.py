@@ -110,6 +110,8 @@ def check_box(L):
     assert np.all(o_sorted[1:][same] == o_sorted[:-1][same])
     # slot arithmetic: own slot + column offset is the neighbour's slot in this block's box
     own = L.box_own_slot.astype(np.int64)
+    holes = L.caller_of_dev == np.uint32(0xFFFFFFFF)
+    assert np.all(own[holes] == 0xFFFF) and np.all(own[~holes] < L.box_slots)
     blk = row // BLOCK
     slot_of = {}
     n_blocks = (L.n_dev + BLOCK - 1) // BLOCK
@@ -117,13 +119,15 @@ def check_box(L):
         m0, m1 = b * BLOCK, min(L.n_dev, (b + 1) * BLOCK)
         ext = L.box_ext_idx[L.box_ext_off[b]:L.box_ext_off[b + 1]].astype(np.int64)
         eslot = L.box_ext_slot[L.box_ext_off[b]:L.box_ext_off[b + 1]].astype(np.int64)
-        slots = np.concatenate([own[m0:m1], eslot])
+        mine = np.arange(m0, m1)[~holes[m0:m1]]
+        slots = np.concatenate([own[mine], eslot])
         assert len(np.unique(slots)) == len(slots), f"block {b}: slots collide"
         assert slots.max() < L.box_slots and slots.min() >= 0
         assert not np.any((ext >= m0) & (ext < m1))
-        slot_of[b] = dict(zip(np.concatenate([np.arange(m0, m1), ext]).tolist(), slots.tolist()))
-    read = own[row] + L.col_off[gcol].astype(np.int64)
-    valid_row = row < L.n_dev
+        slot_of[b] = dict(zip(np.concatenate([mine, ext]).tolist(), slots.tolist()))
+    read = own[np.minimum(row, L.n_dev - 1)] + L.col_off[gcol].astype(np.int64)
+    valid_row = (row < L.n_dev) & ~holes[np.minimum(row, L.n_dev - 1)]
+    assert not np.any(real & ~valid_row)                       # holes carry no springs
     assert np.all(read[valid_row] >= 0) and np.all(read[valid_row] < L.box_slots)   # padding included
     for e in np.nonzero(real)[0]:
         assert read[e] == slot_of[blk[e]][int(L.nbr[e])]
