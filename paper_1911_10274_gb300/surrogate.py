@@ -239,6 +239,20 @@ def search(mode: str, start: List[Morph], start_fit: np.ndarray, generations: in
             "mean_offspring_gain": float(np.mean(gains)) if gains else None}
 
 
+def best_at(history, rollouts: int) -> Optional[float]:
+    """Best fitness a search had found once it had spent at most `rollouts`."""
+    got = [b for used, b in history if used <= rollouts]
+    return got[-1] if got else None
+
+
+def thin(history, points: int = 40):
+    """At most `points` evenly spaced (rollouts, best) pairs of a history."""
+    if len(history) <= points:
+        return [list(h) for h in history]
+    idx = np.unique(np.linspace(0, len(history) - 1, points).round().astype(int))
+    return [list(history[i]) for i in idx]
+
+
 def rollouts_to_reach(history, target: float) -> Optional[int]:
     for used, best in history:
         if best >= target:
@@ -265,8 +279,8 @@ def main(argv=None):
     ap.add_argument("--screened", type=int, default=64)
     ap.add_argument("--epochs", type=int, default=4)
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--screened-budget", type=int, default=25_600,
-                    help="rollout cap of the screened searches (and at most the plain search's)")
+    ap.add_argument("--screened-budget", type=int, default=0,
+                    help="rollout cap of the screened searches; 0: the plain search's own rollouts")
     ap.add_argument("--fitness-cache", default=None,
                     help="npz file holding the training robots' simulated fitness (written if absent)")
     a = ap.parse_args(argv)
@@ -295,7 +309,8 @@ def main(argv=None):
     start, start_fit = morphs[-n_val:], y[-n_val:]
     t2 = time.time()
     plain = search("plain", start, start_fit, a.generations, a.mutants, a.screened, a.steps, seed=a.seed + 1)
-    target, budget = plain["best"], min(plain["rollouts"], a.screened_budget)
+    target = plain["best"]
+    budget = plain["rollouts"] if a.screened_budget <= 0 else min(plain["rollouts"], a.screened_budget)
     t3 = time.time()
     big = 10 ** 9
     scr = search("surrogate", start, start_fit, big, a.mutants, a.screened, a.steps, seed=a.seed + 1,
@@ -311,10 +326,15 @@ def main(argv=None):
            "screened_budget": budget,
            "surrogate": {"best": scr["best"], "rollouts_to_plain_best": rollouts_to_reach(scr["history"], target),
                          "rollouts": scr["rollouts"], "generations": scr["generations"],
-                         "mean_offspring_gain": scr["mean_offspring_gain"], "s": t4 - t3},
+                         "mean_offspring_gain": scr["mean_offspring_gain"], "s": t4 - t3,
+                         "plain_best_at_same_rollouts": best_at(plain["history"], scr["rollouts"]),
+                         "plain_rollouts_to_this_best": rollouts_to_reach(plain["history"], scr["best"])},
            "random": {"best": rnd["best"], "rollouts_to_plain_best": rollouts_to_reach(rnd["history"], target),
                       "rollouts": rnd["rollouts"], "generations": rnd["generations"],
-                      "mean_offspring_gain": rnd["mean_offspring_gain"], "s": t5 - t4}}
+                      "mean_offspring_gain": rnd["mean_offspring_gain"], "s": t5 - t4,
+                      "plain_best_at_same_rollouts": best_at(plain["history"], rnd["rollouts"]),
+                      "plain_rollouts_to_this_best": rollouts_to_reach(plain["history"], rnd["best"])},
+           "curves": {k: thin(v["history"]) for k, v in (("plain", plain), ("surrogate", scr), ("random", rnd))}}
     print(json.dumps(out))
     return out
 
