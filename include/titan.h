@@ -82,9 +82,13 @@ typedef enum {
 } titan_order;
 
 typedef enum {
-    TITAN_EXEC_AUTO = 0,      /* persistent kernel when the system fits, else launches */
+    TITAN_EXEC_AUTO = 0,      /* persistent kernel when the system fits one cluster's
+                                 shared memory and each CTA's rows are short (small
+                                 systems), else launches; CSR accumulation only  */
     TITAN_EXEC_LAUNCH = 1,    /* one fused kernel launch per step (graph-captured)  */
-    TITAN_EXEC_PERSISTENT = 2 /* one launch runs many steps (cluster, shared memory) */
+    TITAN_EXEC_PERSISTENT = 2 /* one launch runs many steps (cluster, shared memory);
+                                 titan_create returns TITAN_E_UNSUPPORTED if the
+                                 system does not fit                               */
 } titan_exec;
 
 /* Integration parameters.  Fill with titan_default_params() first. */
@@ -237,6 +241,14 @@ titan_status titan_sync(titan_sim *sim);
 
 /* Number of steps enqueued so far (the simulated time is steps * dt). */
 uint64_t titan_steps(const titan_sim *sim);
+
+/* How titan_step runs, as resolved from params.exec: TITAN_EXEC_PERSISTENT
+ * (chunks of up to 65,536 steps per launch of one thread-block cluster that
+ * holds the whole system in shared memory) or TITAN_EXEC_LAUNCH (one fused
+ * kernel per step, graph-captured); -1 for a NULL handle.  Re-resolved when
+ * actuation or per-spring damping enlarges the entries and after a layout
+ * rebuild; an edit that no longer fits falls back to launches. */
+int32_t titan_exec_mode(const titan_sim *sim);
 
 /* The step kernel titan_create resolved params.kernel_variant to: 1..6 as
  * listed for kernel_variant (never 0), 0 for atomic accumulation, -1 for a

@@ -28,6 +28,11 @@ thread_local std::string g_thread_error = "";
 
 constexpr uint32_t kHaloMaxSlots = 4096;     // 96 KiB of shared memory per CTA
 constexpr size_t kHaloTmaMaxSmem = 112 * 1024;  // two CTAs per SM
+constexpr size_t kPersistSmemLimit = 220 * 1024;  // persistent kernel: shared memory per CTA
+// AUTO takes the persistent kernel only while one CTA's rows stay this short:
+// beyond it a per-step launch over the whole GPU is faster than a few SMs.
+constexpr uint32_t kPersistAutoMaxEntries = 32768;
+constexpr uint32_t kPersistChunk = 1u << 16;       // steps per persistent launch
 
 struct DeviceGuard {
     int prev = -1;
@@ -242,6 +247,35 @@ bool choose_halo_width(titan_sim *sim) {
     return true;
 }
 
+// Resolves params.exec for the current layout and entry size: the persistent
+// cluster kernel when the system fits one cluster's shared memory and (AUTO)
+// each CTA's rows are short enough that a few SMs beat a whole-GPU launch per
+// step; else one launch per step.  Rewrites the neighbour codes if the plan
+// changed.
+cudaError_t resolve_exec(titan_sim *sim) {
+    sim->persistent = false;
+    if (sim->accumulate != TITAN_ACCUM_CSR || sim->exec_req == TITAN_EXEC_LAUNCH) return cudaSuccess;
+    titan::PersistPlan plan;
+    std::vector<uint16_t> code;
+    if (!titan::plan_persistent(sim->n_dev, sim->sell.slice_off, sim->sell.nbr, sim->has_c, sim->has_act,
+                                kPersistSmemLimit, plan, code))
+        return cudaSuccess;
+    if (sim->exec_req == TITAN_EXEC_AUTO && plan.max_entries > kPersistAutoMaxEntries) return cudaSuccess;
+    cudaError_t e;
+    if (!sim->d_pcode && (e = dev_alloc(sim, &sim->d_pcode, code.size())) != cudaSuccess) return e;
+    if (plan.per_cta != sim->plan.per_cta || plan.cluster != sim->plan.cluster)
+        if ((e = upload(sim->d_pcode, code, sim->stream)) != cudaSuccess) return e;
+    sim->plan = plan;
+    sim->persistent = true;
+    return cudaSuccess;
+}
+
+// After per-spring damping or actuation arrays appear (larger SELL entries).
+cudaError_t entries_grew(titan_sim *sim) {
+    if (sim->csr_kernel == 5 && !choose_halo_width(sim)) sim->csr_kernel = 4;
+    return resolve_exec(sim);
+}
+
 // Reads (and clears) the device error flag set by bounded waits that expired.
 // The caller has synchronised the simulation stream.
 titan_status check_device_error(titan_sim *sim) {
@@ -323,6 +357,7 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
     sim->c.c_uniform = (float)p->damping;
     sim->c.act_omega = 0.0;
     sim->kernel_variant = p->kernel_variant;
+    sim->exec_req = p->exec;
     sim->spin_limit = p->spin_limit == 0 ? kDefaultSpinLimit
                                          : (uint32_t)(p->spin_limit > 0xffffffffull ? 0xffffffffull : p->spin_limit);
 
@@ -538,6 +573,10 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
             CREATE_CK(upload(sim->d_rc, cc, sim->stream));
         }
     }
+    CREATE_CK(resolve_exec(sim));
+    if (p->exec == TITAN_EXEC_PERSISTENT && !sim->persistent)
+        return bail(fail(sim, TITAN_E_UNSUPPORTED, "exec PERSISTENT: the system does not fit one cluster's shared "
+                                                   "memory (or accumulation is atomic)"));
     CREATE_CK(cudaStreamSynchronize(sim->stream));
 #undef CREATE_CK
     *out = sim;
@@ -554,6 +593,18 @@ titan_status titan_step(titan_sim *sim, uint64_t n_steps) {
         if (es_ != TITAN_OK) return es_;
     }
     TITAN_CK(sim, cudaGetLastError());
+    while (n_steps > 0 && sim->persistent) {
+        const uint32_t k = (uint32_t)std::min<uint64_t>(n_steps, kPersistChunk);
+        const int b = sim->cur;
+        TITAN_CK(sim, titan::launch_step_persistent(sim->state[b], sim->state[1 - b], sim->n_dev, sim->plan,
+                                                    sim->d_slice_off, sim->d_pcode, sim->d_kl,
+                                                    sim->has_c ? sim->d_c : nullptr, sim->has_act ? sim->d_act : nullptr,
+                                                    sim->c, sim->steps_dev + b, sim->steps_dev + (1 - b), k,
+                                                    sim->stream));
+        sim->cur ^= 1;
+        n_steps -= k;
+        sim->steps += k;
+    }
     while (n_steps > 0) {
         if (sim->graph_chunk > 0 && n_steps >= (uint64_t)sim->graph_chunk) {
             TITAN_CK(sim, ensure_graph(sim, sim->cur));
@@ -654,7 +705,7 @@ titan_status titan_set_actuation(titan_sim *sim, uint32_t n, const uint32_t *ids
     sim->act_mode = 1;
     TITAN_CK(sim, upload_actuation(sim));
     sim->has_act = true;
-    if (sim->csr_kernel == 5 && !choose_halo_width(sim)) sim->csr_kernel = 4;   // larger entries
+    TITAN_CK(sim, entries_grew(sim));   // larger entries
     free_graphs(sim);       // kernel variant and constants changed
     return TITAN_OK;
 }
@@ -724,6 +775,11 @@ titan_status titan_sync(titan_sim *sim) {
 
 uint64_t titan_steps(const titan_sim *sim) { return sim ? sim->steps : 0; }
 
+int32_t titan_exec_mode(const titan_sim *sim) {
+    if (!sim) return -1;
+    return sim->persistent ? TITAN_EXEC_PERSISTENT : TITAN_EXEC_LAUNCH;
+}
+
 int32_t titan_csr_kernel(const titan_sim *sim) {
     if (!sim) return -1;
     return sim->accumulate == TITAN_ACCUM_CSR ? sim->csr_kernel : 0;
@@ -789,7 +845,7 @@ cudaError_t enable_per_spring_damping(titan_sim *sim) {
         if ((e = upload(sim->d_rc, cc, sim->stream)) != cudaSuccess) return e;
     }
     sim->has_c = true;
-    if (sim->csr_kernel == 5 && !choose_halo_width(sim)) sim->csr_kernel = 4;
+    if ((e = entries_grew(sim)) != cudaSuccess) return e;
     free_graphs(sim);
     return cudaSuccess;
 }
@@ -898,7 +954,7 @@ titan_status titan::ensure_layout(titan_sim *sim) {
         sim->c.worm_period = oldc.worm_period;
         TITAN_CK(sim, upload_actuation(sim));
         sim->has_act = true;
-        if (sim->csr_kernel == 5 && !choose_halo_width(sim)) sim->csr_kernel = 4;
+        TITAN_CK(sim, entries_grew(sim));
         free_graphs(sim);
     }
     TITAN_CK(sim, cudaStreamSynchronize(sim->stream));
@@ -1075,7 +1131,7 @@ titan_status titan_set_worm_actuation(titan_sim *sim, uint32_t n, const uint32_t
         sim->act_mode = 2;
         TITAN_CK(sim, upload_actuation(sim));
         sim->has_act = true;
-        if (sim->csr_kernel == 5 && !choose_halo_width(sim)) sim->csr_kernel = 4;
+        TITAN_CK(sim, entries_grew(sim));
         free_graphs(sim);
     }
     return TITAN_OK;

@@ -43,6 +43,10 @@ struct SimCore {
     int csr_kernel = 0;                   // resolved: 1 direct, 2 smem-staged, 3 bulk-prefetch, 4 halo, 5 halo+TMA, 6 grid box
     uint32_t halo_w_max = 0;              // staged columns per slice (halo+TMA kernel)
     uint32_t halo_ahead = 0;              // L2 prefetch distance in blocks (halo kernel)
+    int exec_req = TITAN_EXEC_AUTO;       // params.exec
+    bool persistent = false;              // resolved: whole chunks of steps in one cluster launch
+    titan::PersistPlan plan;
+    uint16_t *d_pcode = nullptr;          // persistent kernel: neighbour code per SELL entry
 
     MassState *state[2] = {nullptr, nullptr};
     long long *steps_dev = nullptr;       // [2]

@@ -82,6 +82,7 @@ def load(path: Optional[str] = None):
                 "titan_sync": (S, [_P]),
                 "titan_steps": (u64, [_P]),
                 "titan_csr_kernel": (C.c_int32, [_P]),
+                "titan_exec_mode": (C.c_int32, [_P]),
                 "titan_last_error": (C.c_char_p, [_P]),
                 "titan_destroy": (S, [_P]),
                 "titan_step_atomic_noalloc": (S, [u32, _P, _P, _P, u32, _P, _P, _P, f32,
@@ -473,6 +474,11 @@ class Sim:
     @property
     def steps(self) -> int:
         return titan_steps(self.handle)
+
+    @property
+    def exec_mode(self) -> int:
+        """EXEC_PERSISTENT or EXEC_LAUNCH: how titan_step runs this system."""
+        return int(load().titan_exec_mode(self.handle))
 
     @property
     def csr_kernel(self) -> int:

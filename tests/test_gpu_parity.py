@@ -37,17 +37,19 @@ def check(sys, steps, step0=0, spacing=None, **kw):
     return err
 
 
+LAUNCH = dict(exec_mode=T.EXEC_LAUNCH)      # one kernel per step: the variant choice applies
 MODES = [dict(accumulate=T.ACCUM_CSR), dict(accumulate=T.ACCUM_ATOMIC),
-         dict(accumulate=T.ACCUM_CSR, kernel_variant=1),
-         dict(accumulate=T.ACCUM_CSR, kernel_variant=2),
-         dict(accumulate=T.ACCUM_CSR, kernel_variant=3),
-         dict(accumulate=T.ACCUM_CSR, kernel_variant=4),
-         dict(accumulate=T.ACCUM_CSR, kernel_variant=5),
-         dict(accumulate=T.ACCUM_CSR, kernel_variant=6),
+         dict(accumulate=T.ACCUM_CSR, kernel_variant=1, **LAUNCH),
+         dict(accumulate=T.ACCUM_CSR, kernel_variant=2, **LAUNCH),
+         dict(accumulate=T.ACCUM_CSR, kernel_variant=3, **LAUNCH),
+         dict(accumulate=T.ACCUM_CSR, kernel_variant=4, **LAUNCH),
+         dict(accumulate=T.ACCUM_CSR, kernel_variant=5, **LAUNCH),
+         dict(accumulate=T.ACCUM_CSR, kernel_variant=6, **LAUNCH),
+         dict(accumulate=T.ACCUM_CSR, exec_mode=T.EXEC_PERSISTENT),
          dict(accumulate=T.ACCUM_CSR, order=T.ORDER_INPUT),
-         dict(accumulate=T.ACCUM_CSR, graph_chunk=-1)]
+         dict(accumulate=T.ACCUM_CSR, graph_chunk=-1, **LAUNCH)]
 MODE_IDS = ["csr", "atomic", "csr-direct-loads", "csr-tma-staged", "csr-bulk-prefetch", "csr-halo",
-            "csr-halo-tma", "csr-grid-box", "csr-input-order", "csr-no-graph"]
+            "csr-halo-tma", "csr-grid-box", "csr-persistent", "csr-input-order", "csr-no-graph"]
 
 
 @pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
@@ -123,7 +125,7 @@ def test_random_mesh_scaled_down(order, variant):
     dt = 2e-5, 500 steps; tolerance relative to the mean point spacing.  Not
     on a grid: Morton order and greedily coloured halo tables."""
     sys = inputs.random_mesh(n_points=5000, seed=1, lift=0.0)
-    check(sys, 500, order=order, kernel_variant=variant)
+    check(sys, 500, order=order, kernel_variant=variant, **(LAUNCH if variant else {}))
 
 
 def test_lattice_with_holes_in_grid_tiles():
@@ -138,7 +140,7 @@ def test_lattice_with_holes_in_grid_tiles():
                         rest=d * rng.uniform(0.97, 1.03, len(d)), damping=np.full(len(ends), 1.0),
                         dt=1e-4, ground=True, spacing=0.1)
     for var in (0, 6, 5, 4, 3):
-        check(sys, 1000, kernel_variant=var)
+        check(sys, 1000, kernel_variant=var, **(LAUNCH if var else {}))
 
 
 def test_actuated_robot_1000_steps():
@@ -197,13 +199,14 @@ def test_resume_from_snapshot_is_bit_exact():
 
 
 def test_csr_kernel_variants_agree_bit_exact():
-    """The CSR kernels (halo, bulk-prefetched, direct, TMA-staged) sum the
-    same entries in the same order: identical trajectories."""
+    """The CSR kernels (persistent cluster, grid box, halo, bulk-prefetched,
+    direct, TMA-staged) sum the same entries in the same order: identical
+    trajectories."""
     sys = inputs.cube_drop(drop_height=0.02)
     sys.vel[:, 0] = 0.3
-    a = gpu_run(sys, 500, kernel_variant=0)
+    a = gpu_run(sys, 500, exec_mode=T.EXEC_PERSISTENT)
     for var in (1, 2, 3, 4, 5, 6):
-        b = gpu_run(sys, 500, kernel_variant=var)
+        b = gpu_run(sys, 500, kernel_variant=var, **LAUNCH)
         assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
 
 
@@ -301,10 +304,11 @@ def test_full_size_lattice_against_oracle_in_bench_configuration():
     every mass, and the fixed bottom layer exactly still."""
     sys = inputs.large_lattice(n=100, seed=0)
     xo, vo = oracle.run(sys, 64)
-    for mode in (dict(accumulate=T.ACCUM_CSR), dict(accumulate=T.ACCUM_CSR, kernel_variant=1),
-                 dict(accumulate=T.ACCUM_CSR, kernel_variant=2), dict(accumulate=T.ACCUM_CSR, kernel_variant=3),
-                 dict(accumulate=T.ACCUM_CSR, kernel_variant=4), dict(accumulate=T.ACCUM_CSR, kernel_variant=6),
-                 dict(accumulate=T.ACCUM_ATOMIC)):
+    for mode in (dict(accumulate=T.ACCUM_CSR), dict(accumulate=T.ACCUM_CSR, kernel_variant=1, **LAUNCH),
+                 dict(accumulate=T.ACCUM_CSR, kernel_variant=2, **LAUNCH),
+                 dict(accumulate=T.ACCUM_CSR, kernel_variant=3, **LAUNCH),
+                 dict(accumulate=T.ACCUM_CSR, kernel_variant=4, **LAUNCH),
+                 dict(accumulate=T.ACCUM_CSR, kernel_variant=6, **LAUNCH), dict(accumulate=T.ACCUM_ATOMIC)):
         xg, vg, _ = gpu_run(sys, 64, **mode)
         err = np.abs(xg - xo).max()
         assert err <= POS_TOL_FRAC * sys.spacing, err
@@ -313,12 +317,21 @@ def test_full_size_lattice_against_oracle_in_bench_configuration():
 
 
 def test_auto_kernel_choice():
-    """Auto picks the grid-box kernel for masses on a grid, the coloured halo
-    kernel for an unstructured mesh; the box kernel refuses a mesh."""
+    """Auto picks the persistent cluster kernel for systems that fit one
+    cluster, else launches; among launch kernels the grid-box kernel for
+    masses on a grid, the coloured halo kernel for an unstructured mesh; the
+    box kernel refuses a mesh, the persistent mode a system too large."""
     with T.Sim(inputs.cube_drop(n=6)) as sim:
-        assert sim.csr_kernel == 6
+        assert sim.csr_kernel == 6 and sim.exec_mode == T.EXEC_PERSISTENT
+    with T.Sim(inputs.cube_drop(n=6), exec_mode=T.EXEC_LAUNCH) as sim:
+        assert sim.exec_mode == T.EXEC_LAUNCH
+    big = inputs.large_lattice(n=20, seed=0)
+    with T.Sim(big) as sim:
+        assert sim.csr_kernel == 6 and sim.exec_mode == T.EXEC_LAUNCH
+    with pytest.raises(T.TitanError, match="PERSISTENT"):
+        T.Sim(big, exec_mode=T.EXEC_PERSISTENT)
     mesh = inputs.random_mesh(n_points=3000, seed=2, lift=0.0)
-    with T.Sim(mesh) as sim:
+    with T.Sim(mesh, exec_mode=T.EXEC_LAUNCH) as sim:
         assert sim.csr_kernel == 4
     with T.Sim(mesh, accumulate=T.ACCUM_ATOMIC) as sim:
         assert sim.csr_kernel == 0
@@ -345,7 +358,8 @@ def test_grid_with_second_neighbour_springs_and_duplicates():
                         dt=1e-4, ground=True, spacing=0.1)
     with T.Sim(sys) as sim:
         assert sim.csr_kernel == 6
-    runs = [gpu_run(sys, 400, kernel_variant=v) for v in (6, 4, 3)]
+    runs = [gpu_run(sys, 400, kernel_variant=v, **LAUNCH) for v in (6, 4, 3)]
+    runs.append(gpu_run(sys, 400, exec_mode=T.EXEC_PERSISTENT))
     for r in runs[1:]:
         assert np.array_equal(runs[0][0], r[0]) and np.array_equal(runs[0][1], r[1])
     check(sys, 400)
