@@ -207,8 +207,9 @@ def config_for(args, system, resolved=None):
            "accumulate": args.accumulate,
            "order": "grid cubes of 8x8x4 cells, Morton" if resolved == 6 else "morton", "graph_chunk": 64,
            "csr_kernel": CSR_KERNELS.get(resolved, f"variant {args.kernel_variant}"),
-           "parallelism": f"replicas x{args.gpus}",
-           "l2": "inputs larger than L2 (spring data > 126 MB), no flush"}
+           "parallelism": f"replicas x{args.gpus}", "exec": args.exec,
+           "l2": "inputs larger than L2 (spring data > 126 MB), no flush" if args.workload in ("lattice1m", "mesh2m")
+           else "working set fits in L2 / shared memory, no flush (small-system latency case, not the headline)"}
     if system is not None:
         cfg.update({"masses": system.n_masses, "springs": system.n_springs})
     return cfg
@@ -363,10 +364,12 @@ def run_ours(args):
     acc = T.ACCUM_CSR if args.accumulate == "csr" else T.ACCUM_ATOMIC
     stream = torch.cuda.Stream()            # a real stream: the legacy default stream is handle 0
     torch.cuda.set_stream(stream)
+    exec_mode = {"auto": T.EXEC_AUTO, "launch": T.EXEC_LAUNCH, "persistent": T.EXEC_PERSISTENT}[args.exec]
     sim = T.Sim(system, accumulate=acc, stream=stream.cuda_stream, device=local,
-                kernel_variant=args.kernel_variant)
+                kernel_variant=args.kernel_variant, exec_mode=exec_mode)
     launches_per_step = 1 if acc == T.ACCUM_CSR else 2
     resolved = sim.csr_kernel
+    persistent = sim.exec_mode == T.EXEC_PERSISTENT
 
     def barrier():
         torch.cuda.synchronize()
@@ -414,14 +417,14 @@ def run_ours(args):
         "config": config_for(args, system, resolved),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": CSR_KERNEL_NAMES[resolved],
+                     "kernel": "k_step_persist" if persistent else CSR_KERNEL_NAMES[resolved],
                      "algorithmic_bytes_per_launch": alg,
                      "peak_source": f"{peak_kind} HBM copy bandwidth"},
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": 32 * system.n_masses / args.steps,
                 "d2h_bytes_per_step": 24 * system.n_masses / args.steps,
                 "note": "titan_set_state from host FP64 arrays, K steps, titan_snapshot to pinned host"},
-        "gpu_launches": launches_per_step * args.steps,
+        "gpu_launches": -(-args.steps // 65536) if persistent else launches_per_step * args.steps,
         "clocks": clocks.summary(),
     }
     sim.close()
@@ -473,6 +476,8 @@ def main():
     ap.add_argument("--robots", type=int, default=4096, help="robots of the --leg batched/adjoint run")
     ap.add_argument("--rollout-steps", type=int, default=2000, help="rollout steps of the --leg run")
     ap.add_argument("--untuned", action="store_true", help="--leg batched: keep the default launch shapes")
+    ap.add_argument("--exec", choices=["auto", "launch", "persistent"], default="auto",
+                    help="step loop: persistent cluster kernel (small systems), per-step launches, or auto")
     ap.add_argument("--kernel-variant", type=int, default=0, help="CSR kernel: 0 auto, 1 direct loads, 2 TMA-staged, 3 bulk L2 prefetch, 4 halo, 5 halo+TMA, 6 grid box")
     args = ap.parse_args()
     if args.warmup < 3:
