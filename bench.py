@@ -205,7 +205,8 @@ def config_for(args, system, resolved=None):
                         "lattice50": "50^3 lattice, 1,558,396 springs", "mesh2m": "2M-point kNN mesh",
                         "cube1k": "10^3 cube drop"}[args.workload],
            "accumulate": args.accumulate,
-           "order": "grid cubes of 8x8x4 cells, Morton" if resolved == 6 else "morton", "graph_chunk": 64,
+           "order": "input order (no reordering)" if args.order == "input"
+           else ("grid cubes of 8x8x4 cells, Morton" if resolved == 6 else "morton"), "graph_chunk": 64,
            "csr_kernel": CSR_KERNELS.get(resolved, f"variant {args.kernel_variant}"),
            "parallelism": f"replicas x{args.gpus}", "exec": args.exec,
            "l2": "inputs larger than L2 (spring data > 126 MB), no flush" if args.workload in ("lattice1m", "mesh2m")
@@ -365,8 +366,9 @@ def run_ours(args):
     stream = torch.cuda.Stream()            # a real stream: the legacy default stream is handle 0
     torch.cuda.set_stream(stream)
     exec_mode = {"auto": T.EXEC_AUTO, "launch": T.EXEC_LAUNCH, "persistent": T.EXEC_PERSISTENT}[args.exec]
+    order = T.ORDER_MORTON if args.order == "morton" else T.ORDER_INPUT
     sim = T.Sim(system, accumulate=acc, stream=stream.cuda_stream, device=local,
-                kernel_variant=args.kernel_variant, exec_mode=exec_mode)
+                kernel_variant=args.kernel_variant, exec_mode=exec_mode, order=order)
     launches_per_step = 1 if acc == T.ACCUM_CSR else 2
     resolved = sim.csr_kernel
     persistent = sim.exec_mode == T.EXEC_PERSISTENT
@@ -476,6 +478,8 @@ def main():
     ap.add_argument("--robots", type=int, default=4096, help="robots of the --leg batched/adjoint run")
     ap.add_argument("--rollout-steps", type=int, default=2000, help="rollout steps of the --leg run")
     ap.add_argument("--untuned", action="store_true", help="--leg batched: keep the default launch shapes")
+    ap.add_argument("--order", choices=["morton", "input"], default="morton",
+                    help="device order of the masses: spatial (grid cubes or Morton) or the caller's order")
     ap.add_argument("--exec", choices=["auto", "launch", "persistent"], default="auto",
                     help="step loop: persistent cluster kernel (small systems), per-step launches, or auto")
     ap.add_argument("--kernel-variant", type=int, default=0, help="CSR kernel: 0 auto, 1 direct loads, 2 TMA-staged, 3 bulk L2 prefetch, 4 halo, 5 halo+TMA, 6 grid box")
