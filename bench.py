@@ -40,10 +40,13 @@ CSR_KERNELS = {0: "atomic scatter", 1: "direct-loads", 2: "tma-staged", 3: "bulk
 UNIT = "spring_updates/s"
 L2_BYTES = 126 * 1024 * 1024
 
-# ncu DRAM traffic of k_step_sell per launch on the 1M-mass lattice, with the
-# SHA-256 (first 16 hex digits) of the kernel source it was measured on.
-# Reported only while the source is unchanged.
-NCU_TRAFFIC = {}
+# ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one step
+# kernel launch, keyed by (workload, accumulation, kernel, SHA-256 prefix of
+# csrc/step_kernels.cu when it was captured).  Reported only while the source
+# is unchanged.  Capture: profiles/k_step_box_lattice1m.md.
+NCU_TRAFFIC = {
+    ("lattice1m", "csr", "k_step_box", "a8235582d9d8f0ca"): 251_633_664 + 14_066_176,
+}
 
 
 def kernel_source_hash() -> str:
@@ -411,7 +414,8 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     achieved = alg / step_s / 1e9
     h = kernel_source_hash()
-    traffic = NCU_TRAFFIC.get((args.workload, args.accumulate, h))
+    kernel_name = "k_step_persist" if persistent else CSR_KERNEL_NAMES[resolved]
+    traffic = NCU_TRAFFIC.get((args.workload, args.accumulate, kernel_name, h))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * step_s, "higher_is_better": True,
@@ -419,7 +423,7 @@ def run_ours(args):
         "config": config_for(args, system, resolved),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "k_step_persist" if persistent else CSR_KERNEL_NAMES[resolved],
+                     "kernel": kernel_name,
                      "algorithmic_bytes_per_launch": alg,
                      "peak_source": f"{peak_kind} HBM copy bandwidth"},
         "e2e": {"value": e2e_value, "unit": UNIT,
