@@ -113,23 +113,32 @@ k_step_persist(const MassState *__restrict__ in, MassState *__restrict__ out, ui
             float fx = 0.f, fy = 0.f, fz = 0.f;
             const uint32_t slice = m >> 5, lane = m & 31;
             const uint32_t e0 = s_rel[slice], width = (s_rel[slice + 1] - e0) >> 5;
-            for (uint32_t t = 0; t < width; ++t) {
+            // widths are even: two entries per iteration, both neighbours
+            // requested before either force is formed (same summation order
+            // as the launch kernels: entry t, then t + 1)
+            for (uint32_t t = 0; t < width; t += 2) {
                 const uint32_t e = e0 + t * 32 + lane;
-                const uint32_t cd = s_code[e];
-                const uint32_t r = cd >> kPersistLocalBits, local = cd & ((1u << kPersistLocalBits) - 1);
-                float4 qa;
-                float2 qb;
-                if (r == rank) {
-                    qa = srcA[local];
-                    qb = srcB[local];
-                } else {
-                    qa = *cluster.map_shared_rank(srcA + local, r);
-                    qb = *cluster.map_shared_rank(srcB + local, r);
+                float4 qa[2];
+                float2 qb[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint32_t cd = s_code[e + 32 * h];
+                    const uint32_t r = cd >> kPersistLocalBits, local = cd & ((1u << kPersistLocalBits) - 1);
+                    if (r == rank) {
+                        qa[h] = srcA[local];
+                        qb[h] = srcB[local];
+                    } else {
+                        qa[h] = *cluster.map_shared_rank(srcA + local, r);
+                        qb[h] = *cluster.map_shared_rank(srcB + local, r);
+                    }
                 }
-                const float2 a = s_kl[e];
-                const float L0 = HAS_ACT ? actuated_length(c, a.y, s_act[e], clk) : a.y;
-                spring_force(p, v, qa, make_float4(qa.w, qb.x, qb.y, 0.f), a.x, L0, HAS_C ? s_c[e] : c.c_uniform,
-                             fx, fy, fz);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float2 a = s_kl[e + 32 * h];
+                    const float L0 = HAS_ACT ? actuated_length(c, a.y, s_act[e + 32 * h], clk) : a.y;
+                    spring_force(p, v, qa[h], make_float4(qa[h].w, qb[h].x, qb[h].y, 0.f), a.x, L0,
+                                 HAS_C ? s_c[e + 32 * h] : c.c_uniform, fx, fy, fz);
+                }
             }
             MassState o;
             integrate<GROUND>(p, v, fx, fy, fz, c, &o);
@@ -161,32 +170,41 @@ bool plan_persistent(uint32_t n, const std::vector<uint32_t> &slice_off, const s
                      bool has_c, bool has_act, size_t smem_limit, PersistPlan &plan,
                      std::vector<uint16_t> &code) {
     if (n == 0 || slice_off.size() != (size_t)(n + 31) / 32 + 1) return false;
-    for (uint32_t cl = 1; cl <= 8; cl *= 2) {
-        uint32_t per = (n + cl - 1) / cl;
-        per = (per + 31) & ~31u;
-        if (per > (1u << kPersistLocalBits)) continue;
+    auto masses_per_cta = [&](uint32_t cl) { return ((n + cl - 1) / cl + 31) & ~31u; };
+    auto entries_per_cta = [&](uint32_t cl) {
+        const uint32_t per = masses_per_cta(cl);
         uint32_t max_e = 0;
-        for (uint32_t r = 0; r < cl; ++r) {
-            const uint32_t m0 = r * per;
-            if (m0 >= n) break;
-            const uint32_t sl0 = m0 / 32, sl1 = (std::min(n, m0 + per) + 31) / 32;
+        for (uint32_t r = 0; r < cl && r * per < n; ++r) {
+            const uint32_t sl0 = r * per / 32, sl1 = (std::min(n, (r + 1) * per) + 31) / 32;
             max_e = std::max(max_e, slice_off[sl1] - slice_off[sl0]);
         }
-        const size_t bytes = persistent_smem_bytes(per, max_e, has_c, has_act);
-        if (bytes > smem_limit) continue;
-        plan.cluster = cl;
-        plan.per_cta = per;
-        plan.max_entries = max_e;
-        plan.smem = bytes;
-        plan.threads = std::min<uint32_t>(512, per);
-        code.resize(nbr.size());
-        for (size_t e = 0; e < nbr.size(); ++e) {
-            const uint32_t j = nbr[e];
-            code[e] = (uint16_t)(((j / per) << kPersistLocalBits) | (j % per));
-        }
-        return true;
+        return max_e;
+    };
+    auto fits = [&](uint32_t cl) {
+        const uint32_t per = masses_per_cta(cl);
+        return per <= (1u << kPersistLocalBits) &&
+               persistent_smem_bytes(per, entries_per_cta(cl), has_c, has_act) <= smem_limit;
+    };
+    // the smallest cluster that fits and gives each thread one mass (512 per
+    // CTA); failing that, the smallest that fits at all
+    uint32_t cl = 0;
+    for (uint32_t c2 = 1; c2 <= 8 && !cl; c2 *= 2)
+        if (masses_per_cta(c2) <= 512 && fits(c2)) cl = c2;
+    for (uint32_t c2 = 1; c2 <= 8 && !cl; c2 *= 2)
+        if (fits(c2)) cl = c2;
+    if (!cl) return false;
+    const uint32_t per = masses_per_cta(cl);
+    plan.cluster = cl;
+    plan.per_cta = per;
+    plan.max_entries = entries_per_cta(cl);
+    plan.smem = persistent_smem_bytes(per, plan.max_entries, has_c, has_act);
+    plan.threads = std::min<uint32_t>(512, per);
+    code.resize(nbr.size());
+    for (size_t e = 0; e < nbr.size(); ++e) {
+        const uint32_t j = nbr[e];
+        code[e] = (uint16_t)(((j / per) << kPersistLocalBits) | (j % per));
     }
-    return false;
+    return true;
 }
 
 cudaError_t launch_step_persistent(const MassState *in, MassState *out, uint32_t n, const PersistPlan &plan,

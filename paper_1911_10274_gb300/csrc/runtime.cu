@@ -29,9 +29,10 @@ thread_local std::string g_thread_error = "";
 constexpr uint32_t kHaloMaxSlots = 4096;     // 96 KiB of shared memory per CTA
 constexpr size_t kHaloTmaMaxSmem = 112 * 1024;  // two CTAs per SM
 constexpr size_t kPersistSmemLimit = 220 * 1024;  // persistent kernel: shared memory per CTA
-// AUTO takes the persistent kernel only while one CTA's rows stay this short:
-// beyond it a per-step launch over the whole GPU is faster than a few SMs.
-constexpr uint32_t kPersistAutoMaxEntries = 32768;
+// AUTO takes the persistent kernel only while each CTA holds at most this many
+// masses (one per thread): beyond it a per-step launch over the whole GPU is
+// faster than the few SMs of one cluster.
+constexpr uint32_t kPersistAutoMaxPerCta = 512;
 constexpr uint32_t kPersistChunk = 1u << 16;       // steps per persistent launch
 
 struct DeviceGuard {
@@ -260,7 +261,7 @@ cudaError_t resolve_exec(titan_sim *sim) {
     if (!titan::plan_persistent(sim->n_dev, sim->sell.slice_off, sim->sell.nbr, sim->has_c, sim->has_act,
                                 kPersistSmemLimit, plan, code))
         return cudaSuccess;
-    if (sim->exec_req == TITAN_EXEC_AUTO && plan.max_entries > kPersistAutoMaxEntries) return cudaSuccess;
+    if (sim->exec_req == TITAN_EXEC_AUTO && plan.per_cta > kPersistAutoMaxPerCta) return cudaSuccess;
     cudaError_t e;
     if (!sim->d_pcode && (e = dev_alloc(sim, &sim->d_pcode, code.size())) != cudaSuccess) return e;
     if (plan.per_cta != sim->plan.per_cta || plan.cluster != sim->plan.cluster)
