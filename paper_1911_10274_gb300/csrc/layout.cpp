@@ -488,4 +488,82 @@ void build_records(uint32_t s, const uint32_t *ends, const std::vector<uint32_t>
     for (uint32_t r = 0; r < s; ++r) out.slot_of_spring[out.order[r]] = r;
 }
 
+size_t persistent_smem_bytes(uint32_t per_cta, uint32_t max_halo, uint32_t max_entries, bool has_c, bool has_act) {
+    return persist_layout(per_cta, max_halo, max_entries, has_c, has_act).total;
+}
+
+bool plan_persistent(uint32_t n, const std::vector<uint32_t> &slice_off, const std::vector<uint32_t> &nbr,
+                     bool has_c, bool has_act, size_t smem_limit, PersistPlan &plan,
+                     std::vector<uint16_t> &slot, std::vector<uint32_t> &halo) {
+    if (n == 0 || slice_off.size() != (size_t)(n + 31) / 32 + 1 || nbr.size() != slice_off.back()) return false;
+    // per cluster size: masses per CTA, each CTA's entries and halo (the
+    // distinct masses of other CTAs its rows touch, in first-use order)
+    struct Try {
+        uint32_t per = 0, max_e = 0, max_h = 0;
+        std::vector<uint32_t> halo_off;
+        std::vector<uint32_t> halo;
+        std::vector<uint16_t> slot;
+        size_t bytes = 0;
+    };
+    auto build = [&](uint32_t cl, Try &t) {
+        t.per = ((n + cl - 1) / cl + 31) & ~31u;
+        if (t.per > 4096) return false;
+        t.halo_off.assign(9, 0);
+        t.halo.clear();
+        t.slot.assign(nbr.size(), 0);
+        std::vector<uint32_t> local(n, UINT32_MAX);
+        for (uint32_t r = 0; r < cl; ++r) {
+            const uint32_t m0 = r * t.per, m1 = std::min(n, m0 + t.per);
+            const size_t h0 = t.halo.size();
+            if (m0 < n) {
+                const uint32_t sl0 = m0 / 32, sl1 = (m1 + 31) / 32;
+                t.max_e = std::max(t.max_e, slice_off[sl1] - slice_off[sl0]);
+                for (uint32_t e = slice_off[sl0]; e < slice_off[sl1]; ++e) {
+                    const uint32_t j = nbr[e];
+                    if (j >= m0 && j < m1) {
+                        t.slot[e] = (uint16_t)(j - m0);
+                        continue;
+                    }
+                    if (local[j] == UINT32_MAX) {
+                        local[j] = (uint32_t)(t.per + (t.halo.size() - h0));
+                        t.halo.push_back(((j / t.per) << 16) | (j % t.per));
+                    }
+                    t.slot[e] = (uint16_t)local[j];
+                }
+                for (size_t h = h0; h < t.halo.size(); ++h) {       // reset the first-use map
+                    const uint32_t code = t.halo[h];
+                    local[(code >> 16) * t.per + (code & 0xffffu)] = UINT32_MAX;
+                }
+            }
+            t.halo_off[r + 1] = (uint32_t)t.halo.size();
+            t.max_h = std::max<uint32_t>(t.max_h, (uint32_t)(t.halo.size() - h0));
+        }
+        for (uint32_t r = cl; r < 8; ++r) t.halo_off[r + 1] = t.halo_off[r];
+        if (t.per + t.max_h > 65535) return false;
+        t.bytes = persistent_smem_bytes(t.per, t.max_h, t.max_e, has_c, has_act);
+        return t.bytes <= smem_limit;
+    };
+    // the smallest cluster that fits and gives each thread one mass (512 per
+    // CTA); failing that, the smallest that fits at all
+    Try t;
+    uint32_t cl = 0;
+    for (int pass = 0; pass < 2 && !cl; ++pass)
+        for (uint32_t c2 = 1; c2 <= 8 && !cl; c2 *= 2) {
+            if (pass == 0 && (((n + c2 - 1) / c2 + 31) & ~31u) > 512) continue;
+            t = Try();
+            if (build(c2, t)) cl = c2;
+        }
+    if (!cl) return false;
+    plan.cluster = cl;
+    plan.per_cta = t.per;
+    plan.max_entries = t.max_e;
+    plan.max_halo = t.max_h;
+    plan.smem = t.bytes;
+    plan.threads = std::min<uint32_t>(512, t.per);
+    for (int r = 0; r < 9; ++r) plan.halo_off[r] = t.halo_off[r];
+    slot.swap(t.slot);
+    halo.swap(t.halo);
+    return true;
+}
+
 }  // namespace titan

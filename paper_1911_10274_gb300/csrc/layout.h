@@ -102,4 +102,64 @@ struct RecordsHost {
 void build_records(uint32_t s, const uint32_t *ends, const std::vector<uint32_t> &dev_of,
                    RecordsHost &out);
 
+// ---- persistent execution of one small system (see persistent.cu)
+
+#if defined(__CUDACC__)
+#define TITAN_HD __host__ __device__
+#else
+#define TITAN_HD
+#endif
+
+// Shared memory of one CTA: two state buffers of (own + halo) slots, split
+// (x, y, z, vx) / (vy, vz) for conflict-free 16- and 8-byte reads; 1/m of the
+// own slots; the relative slice offsets and the rows (slot per entry, {k, L0},
+// optional c and actuation).
+struct PersistLayout {
+    uint32_t a0, b0, a1, b1, inv, rel, kl, slot, cc, act, total;
+};
+
+TITAN_HD inline uint32_t al16(uint32_t x) { return (x + 15u) & ~15u; }
+
+TITAN_HD inline PersistLayout persist_layout(uint32_t own, uint32_t halo, uint32_t entries, bool has_c,
+                                                        bool has_act) {
+    const uint32_t slots = own + halo;
+    PersistLayout L;
+    L.a0 = 0;
+    L.b0 = L.a0 + slots * 16;
+    L.a1 = al16(L.b0 + slots * 8);
+    L.b1 = L.a1 + slots * 16;
+    L.inv = al16(L.b1 + slots * 8);
+    L.rel = al16(L.inv + own * 4);
+    L.kl = al16(L.rel + 4 * (own / 32 + 1));
+    L.act = L.kl + entries * 8;
+    L.cc = L.act + (has_act ? entries * 8 : 0);
+    L.slot = L.cc + (has_c ? entries * 4 : 0);
+    L.total = al16(L.slot + entries * 2);
+    return L;
+}
+
+// One cluster of `cluster` CTAs, CTA r owning device masses
+// [r per_cta, (r + 1) per_cta) and a halo of other CTAs' masses,
+// halo_off[r] .. halo_off[r + 1] in the halo list.
+struct PersistPlan {
+    uint32_t cluster = 0;       // CTAs (1, 2, 4 or 8)
+    uint32_t per_cta = 0;       // masses per CTA (multiple of 32, <= 4096)
+    uint32_t threads = 0;
+    uint32_t max_entries = 0;   // largest SELL entry count of one CTA
+    uint32_t max_halo = 0;      // largest halo of one CTA
+    uint32_t halo_off[9] = {};
+    size_t smem = 0;            // dynamic shared memory per CTA
+};
+
+size_t persistent_smem_bytes(uint32_t per_cta, uint32_t max_halo, uint32_t max_entries, bool has_c, bool has_act);
+
+// Picks the smallest cluster whose CTAs fit smem_limit (preferring one mass
+// per thread, 512 per CTA) and writes, per SELL entry, the neighbour's slot in
+// its CTA's local table (own masses first, then the halo), and the halo list
+// (rank << 16 | local slot in the owning CTA).  False if the system does not
+// fit one cluster of 8.
+bool plan_persistent(uint32_t n, const std::vector<uint32_t> &slice_off, const std::vector<uint32_t> &nbr,
+                     bool has_c, bool has_act, size_t smem_limit, PersistPlan &plan,
+                     std::vector<uint16_t> &slot, std::vector<uint32_t> &halo);
+
 }  // namespace titan

@@ -257,15 +257,22 @@ cudaError_t resolve_exec(titan_sim *sim) {
     sim->persistent = false;
     if (sim->accumulate != TITAN_ACCUM_CSR || sim->exec_req == TITAN_EXEC_LAUNCH) return cudaSuccess;
     titan::PersistPlan plan;
-    std::vector<uint16_t> code;
+    std::vector<uint16_t> slot;
+    std::vector<uint32_t> halo;
     if (!titan::plan_persistent(sim->n_dev, sim->sell.slice_off, sim->sell.nbr, sim->has_c, sim->has_act,
-                                kPersistSmemLimit, plan, code))
+                                kPersistSmemLimit, plan, slot, halo))
         return cudaSuccess;
     if (sim->exec_req == TITAN_EXEC_AUTO && plan.per_cta > kPersistAutoMaxPerCta) return cudaSuccess;
     cudaError_t e;
-    if (!sim->d_pcode && (e = dev_alloc(sim, &sim->d_pcode, code.size())) != cudaSuccess) return e;
-    if (plan.per_cta != sim->plan.per_cta || plan.cluster != sim->plan.cluster)
-        if ((e = upload(sim->d_pcode, code, sim->stream)) != cudaSuccess) return e;
+    if (!sim->d_pslot && (e = dev_alloc(sim, &sim->d_pslot, slot.size())) != cudaSuccess) return e;
+    if (halo.size() > sim->phalo_cap) {
+        if ((e = dev_alloc(sim, &sim->d_phalo, halo.size())) != cudaSuccess) return e;
+        sim->phalo_cap = halo.size();
+    }
+    if ((e = upload(sim->d_pslot, slot, sim->stream)) != cudaSuccess) return e;
+    if ((e = upload(sim->d_phalo, halo, sim->stream)) != cudaSuccess) return e;
+    // the host vectors must outlive the asynchronous copies
+    if ((e = cudaStreamSynchronize(sim->stream)) != cudaSuccess) return e;
     sim->plan = plan;
     sim->persistent = true;
     return cudaSuccess;
@@ -598,7 +605,7 @@ titan_status titan_step(titan_sim *sim, uint64_t n_steps) {
         const uint32_t k = (uint32_t)std::min<uint64_t>(n_steps, kPersistChunk);
         const int b = sim->cur;
         TITAN_CK(sim, titan::launch_step_persistent(sim->state[b], sim->state[1 - b], sim->n_dev, sim->plan,
-                                                    sim->d_slice_off, sim->d_pcode, sim->d_kl,
+                                                    sim->d_slice_off, sim->d_pslot, sim->d_phalo, sim->d_kl,
                                                     sim->has_c ? sim->d_c : nullptr, sim->has_act ? sim->d_act : nullptr,
                                                     sim->c, sim->steps_dev + b, sim->steps_dev + (1 - b), k,
                                                     sim->stream));

@@ -46,7 +46,9 @@ struct SimCore {
     int exec_req = TITAN_EXEC_AUTO;       // params.exec
     bool persistent = false;              // resolved: whole chunks of steps in one cluster launch
     titan::PersistPlan plan;
-    uint16_t *d_pcode = nullptr;          // persistent kernel: neighbour code per SELL entry
+    uint16_t *d_pslot = nullptr;          // persistent kernel: neighbour slot per SELL entry
+    uint32_t *d_phalo = nullptr;          // persistent kernel: halo list
+    size_t phalo_cap = 0;
 
     MassState *state[2] = {nullptr, nullptr};
     long long *steps_dev = nullptr;       // [2]

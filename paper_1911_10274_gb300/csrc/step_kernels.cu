@@ -255,21 +255,12 @@ k_step_halo(const MassState *__restrict__ in, MassState *__restrict__ out, uint3
 // the box of cells around its masses (see build_box), so a neighbour's slot
 // is the mass's own slot plus the column's offset (one int16 per SELL column,
 // the same for every lane) and the half-edge stream carries only {k, L0}
-// (8 bytes instead of 10).  Padding entries ({k, L0} = {0, 0}; a real spring
+// (8 bytes instead of 10).  It issues no bulk L2 prefetch: with the first
+// stream loads issued ahead of the table fill, the prefetch was measured to
+// cost more than it saved.  Padding entries ({k, L0} = {0, 0}; a real spring
 // has L0 > 0) may point at an empty cell of the box, whose table slot holds
 // whatever was there: they are skipped, never evaluated.  Holes - device
 // slots of empty cells, marked by own slot 0xFFFF - do nothing at all.
-template <bool HAS_C, bool HAS_ACT>
-__device__ __forceinline__ void prefetch_slice_box(const uint32_t *slice_off, uint32_t sl, const float2 *kl,
-                                                   const float *cc, const float2 *act) {
-    const uint32_t e0 = __ldg(slice_off + sl);
-    const uint32_t ne = __ldg(slice_off + sl + 1) - e0;
-    if (!ne) return;
-    ptx::bulk_prefetch_l2(kl + e0, ne * 8);
-    if (HAS_C) ptx::bulk_prefetch_l2(cc + e0, ne * 4);
-    if (HAS_ACT) ptx::bulk_prefetch_l2(act + e0, ne * 8);
-}
-
 template <bool HAS_C, bool HAS_ACT, bool GROUND>
 __global__ void __launch_bounds__(kHaloThreads, kBoxMinBlocks)
 k_step_box(const MassState *__restrict__ in, MassState *__restrict__ out, uint32_t n,
@@ -284,7 +275,6 @@ k_step_box(const MassState *__restrict__ in, MassState *__restrict__ out, uint32
     const uint32_t b = blockIdx.x, tid = threadIdx.x;
     const uint32_t i = b * kHaloThreads + tid;
     const uint32_t lane = tid & 31, sl = i >> 5;
-    const uint32_t n_slices = (n + 31) >> 5;
     long long step = 0;
     if (HAS_ACT) step = *step_in;
     if (b == 0 && tid == 0) *step_out = *step_in + 1;
@@ -293,12 +283,27 @@ k_step_box(const MassState *__restrict__ in, MassState *__restrict__ out, uint32
     const uint32_t s_own = i < n ? own_slot[i] : kBoxHoleSlot;
     const bool valid = s_own != kBoxHoleSlot;
 
-    if (lane == 0 && sl < n_slices) prefetch_slice_box<HAS_C, HAS_ACT>(slice_off, sl, kl, cc, act);
     uint32_t e0 = 0, width = 0;
     float4 p = make_float4(0.f, 0.f, 0.f, 0.f), v = p;
+    const uint32_t *co = col_off2;
+    uint32_t e = 0, no = 0;
+    float2 na0 = make_float2(0.f, 0.f), na1 = na0;
+    float nc0 = c.c_uniform, nc1 = c.c_uniform;
+    float2 ns0 = make_float2(0.f, 0.f), ns1 = ns0;
     if (valid) {
         e0 = __ldg(slice_off + sl);
         width = (__ldg(slice_off + sl + 1) - e0) >> 5;
+        // the first pair of columns is requested before the table fill so its
+        // latency overlaps the fill; widths are even and slices start at even
+        // column counts, so a pair of int16 column offsets is one aligned word
+        co = col_off2 + (e0 >> 6);
+        e = e0 + lane;
+        if (width) {
+            no = __ldg(co);
+            na0 = __ldcs(kl + e); na1 = __ldcs(kl + e + 32);
+            if (HAS_C) { nc0 = __ldcs(cc + e); nc1 = __ldcs(cc + e + 32); }
+            if (HAS_ACT) { ns0 = __ldcs(act + e); ns1 = __ldcs(act + e + 32); }
+        }
         load_state(in + i, p, v);
         tA[s_own] = make_float4(p.x, p.y, p.z, v.x);
         tB[s_own] = make_float2(v.y, v.z);
@@ -317,16 +322,6 @@ k_step_box(const MassState *__restrict__ in, MassState *__restrict__ out, uint32
     const float ph = HAS_ACT ? actuation_clock(c, step) : 0.f;
     float fx = 0.f, fy = 0.f, fz = 0.f;
     if (width) {
-        // widths are even and slices start at even column counts, so a pair of
-        // int16 column offsets is one aligned 32-bit word
-        const uint32_t *co = col_off2 + (e0 >> 6);
-        uint32_t e = e0 + lane;
-        uint32_t no = __ldg(co);
-        float2 na0 = __ldcs(kl + e), na1 = __ldcs(kl + e + 32);
-        float nc0 = c.c_uniform, nc1 = c.c_uniform;
-        float2 ns0 = make_float2(0.f, 0.f), ns1 = ns0;
-        if (HAS_C) { nc0 = __ldcs(cc + e); nc1 = __ldcs(cc + e + 32); }
-        if (HAS_ACT) { ns0 = __ldcs(act + e); ns1 = __ldcs(act + e + 32); }
         for (uint32_t t = 0; t < width; t += 2) {
             const uint32_t o = no;
             const float2 a0 = na0, a1 = na1;

@@ -110,30 +110,18 @@ cudaError_t launch_step_atomic(const MassState *in, MassState *out, uint32_t n,
                                const AtomicView &v, const StepConst &c, const long long *step_in,
                                long long *step_out, cudaStream_t stream);
 
-// Persistent execution of one small system (persistent.cu): one cluster of
-// `cluster` CTAs, CTA r owning device masses [r per_cta, (r + 1) per_cta).
-struct PersistPlan {
-    uint32_t cluster = 0;       // CTAs (1, 2, 4 or 8)
-    uint32_t per_cta = 0;       // masses per CTA (multiple of 32, <= 4096)
-    uint32_t threads = 0;
-    uint32_t max_entries = 0;   // largest SELL entry count of one CTA
-    size_t smem = 0;            // dynamic shared memory per CTA
+// The plan's scalars as the kernel receives them (by value).
+struct PersistArgs {
+    uint32_t cluster, per_cta, max_entries, max_halo;
+    uint32_t halo_off[9];
 };
-
-size_t persistent_smem_bytes(uint32_t per_cta, uint32_t max_entries, bool has_c, bool has_act);
-
-// Picks the smallest cluster whose CTAs fit smem_limit and writes the
-// neighbour codes (rank << 12 | local slot) of every SELL entry.  False if
-// the system does not fit one cluster of 8.
-bool plan_persistent(uint32_t n, const std::vector<uint32_t> &slice_off, const std::vector<uint32_t> &nbr,
-                     bool has_c, bool has_act, size_t smem_limit, PersistPlan &plan,
-                     std::vector<uint16_t> &code);
 
 // n_steps steps in one launch: reads `in`, writes `out` once at the end;
 // step_out = step_in + n_steps.
+struct PersistPlan;
 cudaError_t launch_step_persistent(const MassState *in, MassState *out, uint32_t n, const PersistPlan &plan,
-                                   const uint32_t *slice_off, const uint16_t *code, const float2 *kl,
-                                   const float *cc, const float2 *act, const StepConst &c,
+                                   const uint32_t *slice_off, const uint16_t *slot, const uint32_t *halo,
+                                   const float2 *kl, const float *cc, const float2 *act, const StepConst &c,
                                    const long long *step_in, long long *step_out, uint32_t n_steps,
                                    cudaStream_t stream);
 

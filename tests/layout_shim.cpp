@@ -15,7 +15,10 @@ struct Built {
     titan::SellHost sell;
     titan::HaloHost halo;
     titan::BoxHost box;
-    int grid = 0, box_ok = 0, halo_ok = 0;
+    titan::PersistPlan plan;
+    std::vector<uint16_t> pslot;
+    std::vector<uint32_t> phalo;
+    int grid = 0, box_ok = 0, halo_ok = 0, plan_ok = 0;
 } g;
 
 template <typename T>
@@ -41,6 +44,27 @@ int shim_build(const double *pos, uint32_t n, const uint32_t *ends, uint32_t s, 
     g.halo_ok = titan::build_halo(nd, g.sell, max_slots, g.grid != 0, g.halo) ? 1 : 0;
     g.box_ok = g.grid && titan::build_box(nd, g.sell, g.cell, g.caller_of_dev, max_slots, g.box) ? 1 : 0;
     return 0;
+}
+
+// Plans persistent execution of the last built layout within smem_limit
+// bytes per CTA.  Returns 1 if it fits one cluster.
+int shim_plan(uint64_t smem_limit, int has_c, int has_act) {
+    g.plan_ok = titan::plan_persistent((uint32_t)g.caller_of_dev.size(), g.sell.slice_off, g.sell.nbr, has_c != 0,
+                                       has_act != 0, (size_t)smem_limit, g.plan, g.pslot, g.phalo) ? 1 : 0;
+    return g.plan_ok;
+}
+
+// Plan scalars: 0 cluster, 1 per_cta, 2 threads, 3 max_entries, 4 max_halo, 5 smem, 10 + r: halo_off[r].
+uint64_t shim_plan_scalar(int which) {
+    switch (which) {
+        case 0: return g.plan.cluster;
+        case 1: return g.plan.per_cta;
+        case 2: return g.plan.threads;
+        case 3: return g.plan.max_entries;
+        case 4: return g.plan.max_halo;
+        case 5: return g.plan.smem;
+        default: return (which >= 10 && which < 19) ? g.plan.halo_off[which - 10] : 0;
+    }
 }
 
 // Scalars: 0 n_dev, 1 entries, 2 grid, 3 box_ok, 4 halo_ok, 5 box max_table, 6 halo max_table.
@@ -71,6 +95,8 @@ uint64_t shim_len(const char *name) {
     if (k == "box_ext_off") return g.box.ext_off.size();
     if (k == "box_ext_idx") return g.box.ext_idx.size();
     if (k == "box_ext_slot") return g.box.ext_slot.size();
+    if (k == "pslot") return g.pslot.size();
+    if (k == "phalo") return g.phalo.size();
     return 0;
 }
 
@@ -87,6 +113,8 @@ void shim_get(const char *name, void *dst) {
     if (k == "box_ext_off") copy_out(g.box.ext_off, dst);
     if (k == "box_ext_idx") copy_out(g.box.ext_idx, dst);
     if (k == "box_ext_slot") copy_out(g.box.ext_slot, dst);
+    if (k == "pslot") copy_out(g.pslot, dst);
+    if (k == "phalo") copy_out(g.phalo, dst);
 }
 
 }  // extern "C"

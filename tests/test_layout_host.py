@@ -41,13 +41,17 @@ def shim(tmp_path_factory):
     lib.shim_len.restype = C.c_uint64
     lib.shim_len.argtypes = [C.c_char_p]
     lib.shim_get.argtypes = [C.c_char_p, C.c_void_p]
+    lib.shim_plan.restype = C.c_int
+    lib.shim_plan.argtypes = [C.c_uint64, C.c_int, C.c_int]
+    lib.shim_plan_scalar.restype = C.c_uint64
     return lib
 
 
 class Layout:
     DT = {"caller_of_dev": np.uint32, "cell": np.int32, "slice_off": np.uint32, "nbr": np.uint32,
           "spring": np.uint32, "entry_of_end": np.uint32, "col_off": np.int16, "box_own_slot": np.uint16,
-          "box_ext_off": np.uint32, "box_ext_idx": np.uint32, "box_ext_slot": np.uint16}
+          "box_ext_off": np.uint32, "box_ext_idx": np.uint32, "box_ext_slot": np.uint16,
+          "pslot": np.uint16, "phalo": np.uint32}
 
     def __init__(self, lib, pos, ends):
         pos = np.ascontiguousarray(pos, np.float64)
@@ -64,6 +68,7 @@ class Layout:
             if a.size:
                 lib.shim_get(name.encode(), a.ctypes.data)
             setattr(self, name, a)
+        self.lib = lib
         self.dev_of = np.zeros(self.n, np.int64)
         real = self.caller_of_dev != np.uint32(0xFFFFFFFF)
         self.dev_of[self.caller_of_dev[real]] = np.nonzero(real)[0]
@@ -185,3 +190,59 @@ def test_unstructured_mesh_is_not_a_grid(shim):
     L = Layout(shim, sys.pos, sys.ends)
     assert not L.grid and not L.box_ok and L.n_dev == L.n
     check_sell(L)
+
+
+def check_persistent_plan(L, smem_limit=220 * 1024):
+    """Every row entry of a CTA reads either one of its own slots (the
+    neighbour's index minus the CTA's first mass) or a halo slot whose halo
+    entry names the neighbour's CTA and slot there; all reads stay inside the
+    CTA's own + halo slots; the shared memory fits."""
+    lib = L.lib
+    if not lib.shim_plan(smem_limit, 0, 0):
+        return False
+    cl, per, threads, max_e, max_h, smem = [int(lib.shim_plan_scalar(k)) for k in range(6)]
+    hoff = [int(lib.shim_plan_scalar(10 + r)) for r in range(9)]
+    for name in ("pslot", "phalo"):
+        a = np.empty(int(lib.shim_len(name.encode())), Layout.DT[name])
+        if a.size:
+            lib.shim_get(name.encode(), a.ctypes.data)
+        setattr(L, name, a)
+    assert cl in (1, 2, 4, 8) and per % 32 == 0 and cl * per >= L.n_dev and smem <= smem_limit
+    assert threads == min(512, per)
+    row, _, _ = L.entry_coords()
+    for r in range(cl):
+        m0, m1 = r * per, min(L.n_dev, (r + 1) * per)
+        if m0 >= L.n_dev:
+            break
+        sel = (row >= m0) & (row < m1)
+        nb = L.nbr[sel].astype(np.int64)
+        sl = L.pslot[sel].astype(np.int64)
+        halo = L.phalo[hoff[r]:hoff[r + 1]].astype(np.int64)
+        assert len(halo) <= max_h and sel.sum() <= max_e
+        own = (nb >= m0) & (nb < m1)
+        assert np.array_equal(sl[own], nb[own] - m0)
+        h = sl[~own] - per
+        assert np.all(h >= 0) and np.all(h < len(halo))
+        assert np.array_equal((halo[h] >> 16) * per + (halo[h] & 0xFFFF), nb[~own])
+        assert len(np.unique(halo)) == len(halo)                        # each halo mass copied once
+        assert not np.any(((halo >> 16) * per + (halo & 0xFFFF) >= m0) & ((halo >> 16) * per + (halo & 0xFFFF) < m1))
+    return True
+
+
+def test_persistent_plan_small_lattice_and_robot(shim):
+    pos, ends = lattice(10, 10, 10)
+    L = Layout(shim, pos, ends)
+    assert check_persistent_plan(L)
+    assert int(L.lib.shim_plan_scalar(1)) <= 512                          # one mass per thread
+    rng = np.random.default_rng(8)
+    occ = inputs.voxel_morphology(rng)
+    sys = inputs.voxel_robot(occ, rng.uniform(0, 2 * np.pi, occ.shape))
+    assert check_persistent_plan(Layout(shim, sys.pos, sys.ends))
+    mesh = inputs.random_mesh(n_points=1500, seed=6, lift=0.0)
+    assert check_persistent_plan(Layout(shim, mesh.pos, mesh.ends))
+
+
+def test_persistent_plan_refuses_what_does_not_fit(shim):
+    pos, ends = lattice(20, 20, 20)
+    L = Layout(shim, pos, ends)
+    assert not L.lib.shim_plan(220 * 1024, 0, 0)
