@@ -45,23 +45,38 @@ __device__ __forceinline__ float actuated_length(const StepConst &c, float L0, f
     return L0 * (1.f + a.x * sinf(clk + a.y));
 }
 
-// Force on the mass at (p, v) from one spring to the mass at (q, w):
-// accumulates f u into (fx, fy, fz).  A zero-length spring contributes 0.
-__device__ __forceinline__ void spring_force(const float4 &p, const float4 &v, const float4 &q,
-                                             const float4 &w, float k, float L, float c,
-                                             float &fx, float &fy, float &fz) {
+// The two factors of the force on the mass at (p, v) from one spring to the
+// mass at (q, w): the scalar f = k (l - L) + c (w - v) . u and the unit axis u
+// (the force is f u).  A zero-length spring has u = 0.  Seen from the other
+// end, d, u and the relative velocity change sign exactly and f is
+// bit-identical, so one end's (f, u) serves the other as (f, -u).
+__device__ __forceinline__ void spring_terms(const float4 &p, const float4 &v, const float4 &q, const float4 &w,
+                                             float k, float L, float c, float &f, float &ux, float &uy,
+                                             float &uz) {
     const float dx = q.x - p.x, dy = q.y - p.y, dz = q.z - p.z;
     const float l2 = dx * dx + dy * dy + dz * dz;
     // one reciprocal square root gives both 1/l and l = l2 / l; its error
     // (a few ulp) is below the rounding of the FP32 positions themselves
     const float inv = l2 > 0.f ? rsqrtf(l2) : 0.f;
     const float l = l2 * inv;
-    const float ux = dx * inv, uy = dy * inv, uz = dz * inv;
+    ux = dx * inv;
+    uy = dy * inv;
+    uz = dz * inv;
     const float rate = (w.x - v.x) * ux + (w.y - v.y) * uy + (w.z - v.z) * uz;
-    const float f = k * (l - L) + c * rate;
-    fx += f * ux;
-    fy += f * uy;
-    fz += f * uz;
+    f = k * (l - L) + c * rate;
+}
+
+// Force on the mass at (p, v) from one spring to the mass at (q, w):
+// accumulates f u into (fx, fy, fz), one fused multiply-add per component.
+// A zero-length spring contributes 0.
+__device__ __forceinline__ void spring_force(const float4 &p, const float4 &v, const float4 &q,
+                                             const float4 &w, float k, float L, float c,
+                                             float &fx, float &fy, float &fz) {
+    float f, ux, uy, uz;
+    spring_terms(p, v, q, w, k, L, c, f, ux, uy, uz);
+    fx = fmaf(f, ux, fx);
+    fy = fmaf(f, uy, fy);
+    fz = fmaf(f, uz, fz);
 }
 
 // The mass pass for one mass: gravity, ground contact with capped Coulomb
