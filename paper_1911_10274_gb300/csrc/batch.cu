@@ -549,11 +549,27 @@ titan_status titan_batch_create(uint32_t n_systems, const titan_masses *masses, 
         }
     }
     b->total_slots = slot_cursor;
-    // groups by cluster size, robots in decreasing size within a group (largest first)
+    // Groups: one launch per (cluster size, shared-memory class).  A launch's
+    // dynamic shared memory is the largest of its CTAs', so small robots get
+    // a class of their own and several of their CTAs share an SM (class k: at
+    // most 1/k of an SM's 228 KB); robots in decreasing size within a group.
+    static const uint32_t kPerSm[] = {1, 2, 3, 4, 6, 8};
+    auto smem_class = [&](uint32_t r) {
+        size_t worst = 0;
+        for (const auto &h : per_robot[r])
+            worst = std::max<size_t>(worst, smem_layout(h.d.slot_count, h.d.n_slices, h.d.edge_count, any_act).total);
+        uint32_t cls = 0;
+        for (uint32_t k = 0; k < sizeof(kPerSm) / sizeof(kPerSm[0]); ++k)
+            if (worst + 1024 <= 228u * 1024u / kPerSm[k]) cls = k;
+        return cls;
+    };
+    std::vector<uint32_t> class_of(n_systems);
+    for (uint32_t r = 0; r < n_systems; ++r) class_of[r] = smem_class(r);
     std::vector<uint32_t> order(n_systems);
     for (uint32_t r = 0; r < n_systems; ++r) order[r] = r;
     std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
         if (cluster_of[x] != cluster_of[y]) return cluster_of[x] > cluster_of[y];
+        if (class_of[x] != class_of[y]) return class_of[x] < class_of[y];
         return masses[x].n > masses[y].n;
     });
     std::vector<CtaDesc> descs;
@@ -562,7 +578,7 @@ titan_status titan_batch_create(uint32_t n_systems, const titan_masses *masses, 
     std::vector<uint16_t> nb;
     for (uint32_t k = 0; k < n_systems; ++k) {
         const uint32_t r = order[k];
-        if (b->groups.empty() || b->groups.back().cluster != cluster_of[r]) {
+        if (b->groups.empty() || b->groups.back().cluster != cluster_of[r] || class_of[order[k - 1]] != class_of[r]) {
             Group g;
             g.cluster = cluster_of[r];
             g.cta_first = (uint32_t)descs.size();
