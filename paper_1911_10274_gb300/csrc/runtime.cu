@@ -28,6 +28,7 @@ thread_local std::string g_thread_error = "";
 
 constexpr uint32_t kHaloMaxSlots = 4096;     // 96 KiB of shared memory per CTA
 constexpr size_t kHaloTmaMaxSmem = 112 * 1024;  // two CTAs per SM
+constexpr size_t kBoxTmaMaxSmem = 74 * 1024;    // three CTAs per SM
 constexpr size_t kPersistSmemLimit = 220 * 1024;  // persistent kernel: shared memory per CTA
 // AUTO takes the persistent kernel only while each CTA holds at most this many
 // masses (one per thread): beyond it a per-step launch over the whole GPU is
@@ -144,7 +145,7 @@ titan_status validate(const titan_masses *m, const titan_springs *sp, const tita
     if (p->exec < TITAN_EXEC_AUTO || p->exec > TITAN_EXEC_PERSISTENT)
         return fail(nullptr, TITAN_E_INVALID, "params.exec out of range");
     if (p->device < 0) return fail(nullptr, TITAN_E_INVALID, "params.device must be >= 0");
-    if (p->kernel_variant < 0 || p->kernel_variant > 6) return fail(nullptr, TITAN_E_INVALID, "params.kernel_variant must be 0..6");
+    if (p->kernel_variant < 0 || p->kernel_variant > 7) return fail(nullptr, TITAN_E_INVALID, "params.kernel_variant must be 0..7");
     for (uint64_t i = 0; i < m->n; ++i) {
         for (int a = 0; a < 3; ++a) {
             if (!finite(m->pos[3 * i + a])) return fail(nullptr, TITAN_E_INVALID, "masses.pos has a non-finite value at mass " + std::to_string(i));
@@ -210,9 +211,11 @@ cudaError_t enqueue_step(titan_sim *sim, cudaStream_t st, int b) {
     if (sim->accumulate == TITAN_ACCUM_CSR) {
         titan::SellView v{sim->d_slice_off, sim->d_nbr, sim->d_kl, sim->has_c ? sim->d_c : nullptr,
                           sim->has_act ? sim->d_act : nullptr, 0, sim->spin_limit, sim->d_err};
-        if (sim->csr_kernel == 6) {
+        if (sim->csr_kernel == 6 || sim->csr_kernel == 7) {
             titan::BoxView h{sim->d_col_off, sim->d_own_slot, sim->d_ext_off, sim->d_ext_idx, sim->d_ext_slot,
-                             sim->box.max_table};
+                             (sim->box.max_table + 1) & ~1u};
+            if (sim->csr_kernel == 7)
+                return titan::launch_step_box_tma(in, out, sim->n_dev, v, h, sim->halo_w_max, sim->c, si, so, st);
             return titan::launch_step_box(in, out, sim->n_dev, v, h, sim->c, si, so, st);
         }
         if (sim->csr_kernel == 4 || sim->csr_kernel == 5) {
@@ -244,6 +247,22 @@ bool choose_halo_width(titan_sim *sim) {
     };
     while (w_max > 2 && bytes(w_max) > kHaloTmaMaxSmem) w_max -= 2;
     if (bytes(w_max) > kHaloTmaMaxSmem) return false;
+    sim->halo_w_max = w_max;
+    return true;
+}
+
+// Staged columns per slice for the TMA-staged box kernel: every slice if three
+// CTAs per SM still fit, else the widest width that does.  False if not even
+// two columns fit.
+bool choose_box_width(titan_sim *sim) {
+    uint32_t w_max = 0;
+    for (size_t sl = 0; sl + 1 < sim->sell.slice_off.size(); ++sl)
+        w_max = std::max(w_max, (sim->sell.slice_off[sl + 1] - sim->sell.slice_off[sl]) / 32);
+    w_max = std::max(2u, (w_max + 1) & ~1u);
+    const uint32_t slots = (sim->box.max_table + 1) & ~1u;
+    auto bytes = [&](uint32_t w) { return titan::box_tma_smem_bytes(slots, w, sim->has_c, sim->has_act); };
+    while (w_max > 2 && bytes(w_max) > kBoxTmaMaxSmem) w_max -= 2;
+    if (bytes(w_max) > kBoxTmaMaxSmem) return false;
     sim->halo_w_max = w_max;
     return true;
 }
@@ -281,6 +300,7 @@ cudaError_t resolve_exec(titan_sim *sim) {
 // After per-spring damping or actuation arrays appear (larger SELL entries).
 cudaError_t entries_grew(titan_sim *sim) {
     if (sim->csr_kernel == 5 && !choose_halo_width(sim)) sim->csr_kernel = 4;
+    if (sim->csr_kernel == 7 && !choose_box_width(sim)) sim->csr_kernel = 6;
     return resolve_exec(sim);
 }
 
@@ -493,12 +513,17 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
             return bail(fail(sim, TITAN_E_UNSUPPORTED, "padded incidence exceeds 2^32 entries"));
         const int want = p->kernel_variant;
         sim->csr_kernel = want == 0 ? (sim->grid_order ? 6 : 4) : want;
-        if (sim->csr_kernel == 6 &&
+        if ((sim->csr_kernel == 6 || sim->csr_kernel == 7) &&
             !(sim->grid_order && titan::build_box(nd, sim->sell, cells, sim->caller_of_dev, kHaloMaxSlots, sim->box))) {
-            if (want == 6)
+            if (want == 6 || want == 7)
                 return bail(fail(sim, TITAN_E_UNSUPPORTED, "the grid box kernel needs masses on a grid whose "
                                                            "blocks' boxes fit " + std::to_string(kHaloMaxSlots) + " slots"));
             sim->csr_kernel = 4;
+        }
+        if (sim->csr_kernel == 7 && !choose_box_width(sim)) {
+            if (want == 7)
+                return bail(fail(sim, TITAN_E_UNSUPPORTED, "the TMA-staged box kernel's shared memory does not fit"));
+            sim->csr_kernel = 6;
         }
         if ((sim->csr_kernel == 4 || sim->csr_kernel == 5) &&
             !titan::build_halo(nd, sim->sell, kHaloMaxSlots, sim->grid_order, sim->halo)) {
@@ -526,7 +551,7 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
         CREATE_CK(dev_alloc(sim, &sim->d_kl, E));
         CREATE_CK(upload(sim->d_slice_off, sim->sell.slice_off, sim->stream));
         CREATE_CK(upload(sim->d_kl, kl, sim->stream));
-        if (sim->csr_kernel == 6) {
+        if (sim->csr_kernel == 6 || sim->csr_kernel == 7) {
             const titan::BoxHost &h = sim->box;
             CREATE_CK(dev_alloc(sim, &sim->d_col_off, h.col_off.size()));
             CREATE_CK(dev_alloc(sim, &sim->d_own_slot, nd));

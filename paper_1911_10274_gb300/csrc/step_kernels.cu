@@ -356,6 +356,134 @@ k_step_box(const MassState *__restrict__ in, MassState *__restrict__ out, uint32
     integrate<GROUND>(p, v, fx, fy, fz, c, out + i);
 }
 
+// K1, grid-box form with the stream staged by TMA: as k_step_box, but lane 0
+// of each warp first copies its slice's {k, L0} (and c, actuation) columns
+// into shared memory with 1-D bulk copies on one mbarrier per warp, so a
+// whole slice's stream is in flight at once while the table fills; the row
+// loop then reads only shared memory.  Slices wider than the staging buffer
+// (w_max columns) read their columns from global memory.  The mbarrier wait
+// is bounded by spin_limit polls; on expiry the warp records the error in
+// *err, waits (bounded) for its copies and leaves its masses unwritten.
+template <bool HAS_C, bool HAS_ACT>
+constexpr int box_entry_bytes() { return 8 + (HAS_C ? 4 : 0) + (HAS_ACT ? 8 : 0); }
+
+template <bool HAS_C, bool HAS_ACT, bool GROUND>
+__global__ void __launch_bounds__(kHaloThreads, 3)
+k_step_box_tma(const MassState *__restrict__ in, MassState *__restrict__ out, uint32_t n,
+               const uint32_t *__restrict__ slice_off, const uint32_t *__restrict__ col_off2,
+               const float2 *__restrict__ kl, const float *__restrict__ cc, const float2 *__restrict__ act,
+               const uint16_t *__restrict__ own_slot, const uint32_t *__restrict__ ext_off,
+               const uint32_t *__restrict__ ext_idx, const uint16_t *__restrict__ ext_slot, uint32_t table_slots,
+               uint32_t w_max, StepConst c, const long long *__restrict__ step_in, long long *__restrict__ step_out,
+               uint32_t spin_limit, int *__restrict__ err) {
+    constexpr uint32_t FULL = 0xffffffffu;
+    constexpr int EB = box_entry_bytes<HAS_C, HAS_ACT>();
+    extern __shared__ float4 btab[];
+    __shared__ uint64_t bars[kHaloThreads / 32];
+    float4 *tA = btab;
+    float2 *tB = reinterpret_cast<float2 *>(btab + table_slots);
+    const uint32_t b = blockIdx.x, tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    const uint32_t i = b * kHaloThreads + tid, sl = i >> 5;
+    const uint32_t n_slices = (n + 31) >> 5;
+    // per-warp staging buffer after the table: [kl float2 | act float2 | c float] x (w_max * 32)
+    unsigned char *wb = reinterpret_cast<unsigned char *>(tB + table_slots) + (size_t)w * w_max * 32 * EB;
+    float2 *s_kl = reinterpret_cast<float2 *>(wb);
+    float2 *s_act = reinterpret_cast<float2 *>(wb + (size_t)w_max * 32 * 8);
+    float *s_c = reinterpret_cast<float *>(wb + (size_t)w_max * 32 * (HAS_ACT ? 16 : 8));
+
+    long long step = 0;
+    if (HAS_ACT) step = *step_in;
+    if (b == 0 && tid == 0) *step_out = *step_in + 1;
+
+    const bool warp_live = sl < n_slices;                    // warp-uniform
+    uint32_t e0 = 0, width = 0;
+    if (warp_live) {
+        e0 = __ldg(slice_off + sl);
+        width = (__ldg(slice_off + sl + 1) - e0) >> 5;
+    }
+    const bool staged = warp_live && width > 0 && width <= w_max;
+    if (staged && lane == 0) {
+        const uint32_t ne = width * 32;
+        ptx::mbar_init(&bars[w], 1);
+        ptx::fence_mbar_init();
+        ptx::mbar_arrive_expect_tx(&bars[w], ne * EB);
+        ptx::bulk_g2s(s_kl, kl + e0, ne * 8, &bars[w]);
+        if (HAS_ACT) ptx::bulk_g2s(s_act, act + e0, ne * 8, &bars[w]);
+        if (HAS_C) ptx::bulk_g2s(s_c, cc + e0, ne * 4, &bars[w]);
+    }
+    const uint32_t s_own = i < n ? own_slot[i] : kBoxHoleSlot;
+    const bool valid = s_own != kBoxHoleSlot;
+    float4 p = make_float4(0.f, 0.f, 0.f, 0.f), v = p;
+    if (valid) {
+        load_state(in + i, p, v);
+        tA[s_own] = make_float4(p.x, p.y, p.z, v.x);
+        tB[s_own] = make_float2(v.y, v.z);
+    }
+    const uint32_t h0 = __ldg(ext_off + b), h1 = __ldg(ext_off + b + 1);
+    for (uint32_t h = h0 + tid; h < h1; h += kHaloThreads) {
+        float4 q, ww;
+        load_state(in + __ldg(ext_idx + h), q, ww);
+        const uint32_t s = __ldg(ext_slot + h);
+        tA[s] = make_float4(q.x, q.y, q.z, ww.x);
+        tB[s] = make_float2(ww.y, ww.z);
+    }
+    __syncthreads();                    // also publishes the mbarrier initialisation
+    if (!warp_live) return;
+    if (staged) {
+        bool done = false;
+        for (uint32_t it = 0; it < spin_limit; ++it) {
+            done = ptx::mbar_try_wait(&bars[w], 0);
+            if (__all_sync(FULL, done)) break;
+        }
+        if (!__all_sync(FULL, done)) {
+            if (lane == 0) {
+                atomicExch(err, 1);
+                ptx::mbar_wait_bounded(&bars[w], 0, spin_limit);
+            }
+            __syncwarp();
+            return;
+        }
+    }
+    if (!valid) return;
+
+    const float ph = HAS_ACT ? actuation_clock(c, step) : 0.f;
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+    const uint32_t *co = col_off2 + (e0 >> 6);      // even widths: a pair of int16 offsets per word
+    for (uint32_t t = 0; t < width; t += 2) {
+        const uint32_t a = t * 32 + lane, bb = a + 32;
+        float2 a0, a1, s0 = make_float2(0.f, 0.f), s1 = s0;
+        float c0 = c.c_uniform, c1 = c.c_uniform;
+        if (staged) {
+            a0 = s_kl[a]; a1 = s_kl[bb];
+            if (HAS_C) { c0 = s_c[a]; c1 = s_c[bb]; }
+            if (HAS_ACT) { s0 = s_act[a]; s1 = s_act[bb]; }
+        } else {
+            a0 = __ldcs(kl + e0 + a); a1 = __ldcs(kl + e0 + bb);
+            if (HAS_C) { c0 = __ldcs(cc + e0 + a); c1 = __ldcs(cc + e0 + bb); }
+            if (HAS_ACT) { s0 = __ldcs(act + e0 + a); s1 = __ldcs(act + e0 + bb); }
+        }
+        const uint32_t o = __ldg(co + (t >> 1));
+        const uint32_t j0 = s_own + (uint32_t)(int32_t)(int16_t)(o & 0xffffu);
+        const uint32_t j1 = s_own + (uint32_t)(int32_t)(int16_t)(o >> 16);
+        float L0 = a0.y, L1 = a1.y;
+        if (HAS_ACT) {
+            L0 = actuated_length(c, a0.y, s0, ph);
+            L1 = actuated_length(c, a1.y, s1, ph);
+        }
+        if (a0.y != 0.f) {
+            const float4 qa = tA[j0];
+            const float2 qb = tB[j0];
+            spring_force(p, v, qa, make_float4(qa.w, qb.x, qb.y, 0.f), a0.x, L0, c0, fx, fy, fz);
+        }
+        if (a1.y != 0.f) {
+            const float4 qa = tA[j1];
+            const float2 qb = tB[j1];
+            spring_force(p, v, qa, make_float4(qa.w, qb.x, qb.y, 0.f), a1.x, L1, c1, fx, fy, fz);
+        }
+    }
+    integrate<GROUND>(p, v, fx, fy, fz, c, out + i);
+}
+
 // K1, halo + TMA form.  As k_step_halo, but the half-edge stream of each
 // warp's slice (all columns of every array) is copied into shared memory by
 // the TMA engine (1-D bulk copies on one mbarrier per warp), issued before the
@@ -829,6 +957,45 @@ cudaError_t launch_step_halo_tma(const MassState *in, MassState *out, uint32_t n
         else    { if (gr) TITAN_HTMA(false, false, true); else TITAN_HTMA(false, false, false); }
     }
 #undef TITAN_HTMA
+    return cudaGetLastError();
+}
+
+size_t box_tma_smem_bytes(uint32_t table_slots, uint32_t w_max, bool has_c, bool has_act) {
+    return (size_t)table_slots * (sizeof(float4) + sizeof(float2)) +
+           (size_t)(kHaloThreads / 32) * w_max * 32 * (8 + (has_c ? 4 : 0) + (has_act ? 8 : 0));
+}
+
+cudaError_t launch_step_box_tma(const MassState *in, MassState *out, uint32_t n, const SellView &v,
+                                const BoxView &h, uint32_t w_max, const StepConst &c, const long long *step_in,
+                                long long *step_out, cudaStream_t stream) {
+    const bool hc = v.c != nullptr, ha = v.act != nullptr, gr = c.ground != 0;
+    const unsigned g = n ? (n + kHaloThreads - 1) / kHaloThreads : 1;
+    const size_t bytes = box_tma_smem_bytes(h.table_slots, w_max, hc, ha);
+    if (reinterpret_cast<uintptr_t>(h.col_off) & 3) return cudaErrorInvalidValue;
+    // the tables end on a 16-byte boundary only if the float2 part has an even slot count
+    if (h.table_slots & 1) return cudaErrorInvalidValue;
+#define TITAN_BTMA(HC, HA, GR)                                                                   \
+    do {                                                                                         \
+        auto kern = k_step_box_tma<HC, HA, GR>;                                                  \
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes); \
+        if (e != cudaSuccess) return e;                                                          \
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,           \
+                                 (int)cudaSharedmemCarveoutMaxShared);                            \
+        if (e != cudaSuccess) return e;                                                          \
+        kern<<<g, kHaloThreads, bytes, stream>>>(in, out, n, v.slice_off,                        \
+                                                 reinterpret_cast<const uint32_t *>(h.col_off), v.kl, v.c, \
+                                                 v.act, h.own_slot, h.ext_off, h.ext_idx, h.ext_slot, \
+                                                 h.table_slots, w_max, c, step_in, step_out,     \
+                                                 v.spin_limit, v.err);                           \
+    } while (0)
+    if (hc) {
+        if (ha) { if (gr) TITAN_BTMA(true, true, true); else TITAN_BTMA(true, true, false); }
+        else    { if (gr) TITAN_BTMA(true, false, true); else TITAN_BTMA(true, false, false); }
+    } else {
+        if (ha) { if (gr) TITAN_BTMA(false, true, true); else TITAN_BTMA(false, true, false); }
+        else    { if (gr) TITAN_BTMA(false, false, true); else TITAN_BTMA(false, false, false); }
+    }
+#undef TITAN_BTMA
     return cudaGetLastError();
 }
 

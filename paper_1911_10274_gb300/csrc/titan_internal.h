@@ -99,6 +99,13 @@ cudaError_t launch_step_box(const MassState *in, MassState *out, uint32_t n, con
                             const StepConst &c, const long long *step_in, long long *step_out,
                             cudaStream_t stream);
 
+// Grid-box form with the stream staged into shared memory by TMA bulk copies;
+// slices wider than w_max columns read from global memory.
+cudaError_t launch_step_box_tma(const MassState *in, MassState *out, uint32_t n, const SellView &v,
+                                const BoxView &h, uint32_t w_max, const StepConst &c, const long long *step_in,
+                                long long *step_out, cudaStream_t stream);
+size_t box_tma_smem_bytes(uint32_t table_slots, uint32_t w_max, bool has_c, bool has_act);
+
 // Halo form with the half-edge stream staged into shared memory by TMA bulk
 // copies; slices wider than w_max columns read from global memory.
 cudaError_t launch_step_halo_tma(const MassState *in, MassState *out, uint32_t n, const SellView &v,
