@@ -130,6 +130,24 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
+def max_over_ranks(values, world: int, device=None):
+    """Element-wise maximum of per-rank floats over all ranks (one all-reduce);
+    the values themselves at world size 1."""
+    if world <= 1:
+        return [float(x) for x in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x) for x in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def whole_job_rate(world: int, units_per_rank: float, seconds: float) -> float:
+    """Throughput of the whole job: every rank processed units_per_rank (weak
+    scaling, independent replicas); the job took the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -403,14 +421,9 @@ def run_ours(args):
         p, v, _ = sim.snapshot()
         e2e_s = time.perf_counter() - t0
         barrier()
-    t_max = ms / 1e3
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_max, e2e_s], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max, e2e_s = float(tt[0]), float(tt[1])
-    value = world * system.n_springs * args.steps / t_max
-    e2e_value = world * system.n_springs * args.steps / e2e_s
+    t_max, e2e_s = max_over_ranks([ms / 1e3, e2e_s], world, device="cuda")
+    value = whole_job_rate(world, system.n_springs * args.steps, t_max)
+    e2e_value = whole_job_rate(world, system.n_springs * args.steps, e2e_s)
     step_s = t_max / args.steps
     alg = algorithmic_bytes(system.n_masses, system.n_springs)
     peak, peak_kind = measured_peaks()
