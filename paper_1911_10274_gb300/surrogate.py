@@ -194,7 +194,7 @@ def search(mode: str, start: List[Morph], start_fit: np.ndarray, generations: in
 
     mode 'plain': simulate all mutants; 'surrogate': simulate the `screened`
     mutants the surrogate ranks highest, then refine the surrogate on the last
-    `refine_window` mutants simulated (mirror-augmented); 'random': simulate
+    `refine_window` mutants simulated (0: all of them; mirror-augmented); 'random': simulate
     `screened` random mutants.  Stops after `generations`, or once the best simulated
     fitness reaches `target`, or when `max_rollouts` would be exceeded.
     Returns the best fitness after each generation with the simulator rollouts
@@ -224,8 +224,10 @@ def search(mode: str, start: List[Morph], start_fit: np.ndarray, generations: in
         used += len(chosen)
         gains.append(float(f.mean() - pop_fit.mean()))
         if mode == "surrogate":
-            seen_m = (seen_m + chosen)[-refine_window:]
-            seen_f = np.concatenate([seen_f, f])[-refine_window:]
+            seen_m = seen_m + chosen
+            seen_f = np.concatenate([seen_f, f])
+            if refine_window > 0:
+                seen_m, seen_f = seen_m[-refine_window:], seen_f[-refine_window:]
             am, af = mirrored(seen_m, seen_f)
             surrogate.refine(encode(am), af, epochs=refine_epochs, batch=512, seed=g)
         allm = pop + chosen
@@ -279,6 +281,10 @@ def main(argv=None):
     ap.add_argument("--screened", type=int, default=64)
     ap.add_argument("--epochs", type=int, default=4)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--search-seed", type=int, default=None, help="seed of the searches (default: seed + 1)")
+    ap.add_argument("--refine-epochs", type=int, default=2)
+    ap.add_argument("--refine-window", type=int, default=8192, help="simulated mutants refined on; 0: all")
+    ap.add_argument("--no-random", action="store_true", help="skip the random-screening ablation")
     ap.add_argument("--screened-budget", type=int, default=0,
                     help="rollout cap of the screened searches; 0: the plain search's own rollouts")
     ap.add_argument("--fitness-cache", default=None,
@@ -308,18 +314,23 @@ def main(argv=None):
     val_corr = spearman(sur.predict(encode(morphs[-n_val:])), y[-n_val:])
     start, start_fit = morphs[-n_val:], y[-n_val:]
     t2 = time.time()
-    plain = search("plain", start, start_fit, a.generations, a.mutants, a.screened, a.steps, seed=a.seed + 1)
+    sseed = a.seed + 1 if a.search_seed is None else a.search_seed
+    plain = search("plain", start, start_fit, a.generations, a.mutants, a.screened, a.steps, seed=sseed)
     target = plain["best"]
     budget = plain["rollouts"] if a.screened_budget <= 0 else min(plain["rollouts"], a.screened_budget)
     t3 = time.time()
     big = 10 ** 9
-    scr = search("surrogate", start, start_fit, big, a.mutants, a.screened, a.steps, seed=a.seed + 1,
-                 surrogate=sur, target=target, max_rollouts=budget)
+    scr = search("surrogate", start, start_fit, big, a.mutants, a.screened, a.steps, seed=sseed,
+                 surrogate=sur, target=target, max_rollouts=budget, refine_epochs=a.refine_epochs,
+                 refine_window=a.refine_window)
     t4 = time.time()
-    rnd = search("random", start, start_fit, big, a.mutants, a.screened, a.steps, seed=a.seed + 1,
-                 target=target, max_rollouts=budget)
+    rnd = {"history": [], "best": None, "rollouts": 0, "generations": 0, "mean_offspring_gain": None}
+    if not a.no_random:
+        rnd = search("random", start, start_fit, big, a.mutants, a.screened, a.steps, seed=sseed,
+                     target=target, max_rollouts=budget)
     t5 = time.time()
     out = {"train_rollouts": a.train, "steps": a.steps, "fitness_cached": cached, "simulate_s": t_sim,
+           "search_seed": sseed, "refine_epochs": a.refine_epochs, "refine_window": a.refine_window,
            "fit_s": t_fit, "val_spearman": val_corr,
            "plain": {"best": target, "rollouts": plain["rollouts"], "generations": plain["generations"],
                      "s": t3 - t2},
@@ -333,7 +344,8 @@ def main(argv=None):
                       "rollouts": rnd["rollouts"], "generations": rnd["generations"],
                       "mean_offspring_gain": rnd["mean_offspring_gain"], "s": t5 - t4,
                       "plain_best_at_same_rollouts": best_at(plain["history"], rnd["rollouts"]),
-                      "plain_rollouts_to_this_best": rollouts_to_reach(plain["history"], rnd["best"])},
+                      "plain_rollouts_to_this_best": rollouts_to_reach(plain["history"], rnd["best"])
+                      if rnd["best"] is not None else None},
            "curves": {k: thin(v["history"]) for k, v in (("plain", plain), ("surrogate", scr), ("random", rnd))}}
     print(json.dumps(out))
     return out
