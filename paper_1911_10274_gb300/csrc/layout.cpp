@@ -62,17 +62,6 @@ void morton_order(const double *pos, uint32_t n, std::vector<uint32_t> &caller_o
     for (uint32_t d = 0; d < n; ++d) caller_of_dev[d] = key[d].second;
 }
 
-void sort_blocks_by_degree(std::vector<uint32_t> &caller_of_dev, const std::vector<uint32_t> &degree_of_caller,
-                           uint32_t block) {
-    const size_t n = caller_of_dev.size();
-    auto deg = [&](uint32_t c) { return c == UINT32_MAX ? 0u : degree_of_caller[c]; };
-    for (size_t b0 = 0; b0 < n; b0 += block) {
-        const size_t b1 = std::min(n, b0 + block);
-        std::stable_sort(caller_of_dev.begin() + b0, caller_of_dev.begin() + b1,
-                         [&](uint32_t x, uint32_t y) { return deg(x) > deg(y); });
-    }
-}
-
 bool grid_tile_order(const double *pos, uint32_t n, double h, std::vector<uint32_t> &caller_of_dev,
                      std::vector<int32_t> *cell_of_dev) {
     caller_of_dev.clear();

@@ -22,14 +22,6 @@ void morton_order(const double *pos, uint32_t n, std::vector<uint32_t> &caller_o
 // cells, any translate of such a layer covers each value of (device index
 // mod 16) once, and a block's box is 8 x 8 x 4 cells plus its halo.  Returns
 // false (leaving the output empty) if the masses are not on such a grid.
-// Within each block of `block` consecutive device slots, orders the masses by
-// decreasing degree (stable): slices of 32 then hold masses of similar degree
-// and the SELL rows need little padding, while every mass stays in its block
-// (the unit of the neighbourhood tables).  For Morton-ordered meshes, whose
-// degrees vary.
-void sort_blocks_by_degree(std::vector<uint32_t> &caller_of_dev, const std::vector<uint32_t> &degree_of_caller,
-                           uint32_t block);
-
 // cell_of_dev (optional) receives the integer cell (x, y, z) of every device
 // index, holes included, relative to the lowest occupied cell.
 bool grid_tile_order(const double *pos, uint32_t n, double h, std::vector<uint32_t> &caller_of_dev,

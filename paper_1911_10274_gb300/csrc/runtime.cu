@@ -430,12 +430,6 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
         if (!sim->grid_order) {
             cells.clear();
             titan::morton_order(m->pos, n, sim->caller_of_dev);
-            std::vector<uint32_t> degree(n, 0);
-            for (uint32_t q = 0; q < s; ++q) {
-                ++degree[sp->ends[2 * (size_t)q]];
-                ++degree[sp->ends[2 * (size_t)q + 1]];
-            }
-            titan::sort_blocks_by_degree(sim->caller_of_dev, degree, titan::kHaloBlock);
         }
     } else {
         sim->caller_of_dev.resize(n);

@@ -30,20 +30,12 @@ void copy_out(const std::vector<T> &v, void *dst) {
 extern "C" {
 
 // Orders the masses as titan_create does (grid-tile order on a grid of pitch
-// h, else Morton with each block sorted by degree), builds the SELL incidence and both neighbourhood tables.
+// h, else Morton), builds the SELL incidence and both neighbourhood tables.
 // Returns 0 on success, 1 if the SELL could not be built.
 int shim_build(const double *pos, uint32_t n, const uint32_t *ends, uint32_t s, double h, uint32_t max_slots) {
     g = Built();
     g.grid = titan::grid_tile_order(pos, n, h, g.caller_of_dev, &g.cell) ? 1 : 0;
-    if (!g.grid) {
-        titan::morton_order(pos, n, g.caller_of_dev);
-        std::vector<uint32_t> degree(n, 0);
-        for (uint32_t q = 0; q < s; ++q) {
-            ++degree[ends[2 * (size_t)q]];
-            ++degree[ends[2 * (size_t)q + 1]];
-        }
-        titan::sort_blocks_by_degree(g.caller_of_dev, degree, titan::kHaloBlock);
-    }
+    if (!g.grid) titan::morton_order(pos, n, g.caller_of_dev);
     const uint32_t nd = (uint32_t)g.caller_of_dev.size();
     g.dev_of_caller.assign(n, 0);
     for (uint32_t d = 0; d < nd; ++d)
