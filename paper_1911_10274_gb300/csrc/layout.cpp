@@ -11,7 +11,9 @@
 // classes), then by neighbour index: in a lattice, column t of a slice is then
 // the same lattice direction for every interior mass, so the 32 neighbour
 // gathers of one column hit a compact, shifted block of consecutive states
-// (few cache lines) instead of 32 unrelated ones.
+// (few cache lines) instead of 32 unrelated ones.  On a grid the order is by
+// exact cell offset and the columns are offset-aligned (see build_sell).
+// Grid order, box tables and the persistent plan: see layout.h.
 // Spring records: one {i, j, k, L0} record per spring, sorted by (lower,
 // higher) device index, for the atomic scatter.
 #include "layout.h"

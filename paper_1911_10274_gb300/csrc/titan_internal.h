@@ -7,7 +7,8 @@
 //   SELL-32 incidence (deterministic gather, K1): masses are taken in slices of
 //                 32 consecutive device indices; slice s holds W_s columns of 32
 //                 half-edge entries (column-major, entry = off[s] + 32 t + lane),
-//                 W_s = the slice's largest degree rounded up to even.  Per
+//                 W_s = the slice's largest degree rounded up to even (on a grid:
+//                 its number of offset-aligned columns, see layout.h).  Per
 //                 entry: nbr (u32 device index) and {k, L0} (float2), optionally
 //                 c (float) and actuation {A, phi} (float2).  Padding entries
 //                 point at the mass itself with k = L0 = c = A = 0, which gives an
