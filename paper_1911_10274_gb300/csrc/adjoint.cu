@@ -76,6 +76,44 @@ k_adj_mass(const MassState *__restrict__ X, const float4 *__restrict__ xbo, cons
     vb[i] = v_b;
 }
 
+// The adjoint of one spring seen from the mass at (p, v): adds to x_b, v_b and,
+// for the spring's owner half-edge, to the spring's dJ/dA and dJ/dphi.
+template <bool HAS_C>
+__device__ __forceinline__ void adj_half_edge(const float4 &p, const float4 &v, const float4 &Fi, const float4 &q,
+                                              const float4 &w, const float4 &Fj, float2 a, float2 s, float cd,
+                                              float ph, uint32_t spr, float4 &x_b, float4 &v_b,
+                                              float *__restrict__ grad_amp, float *__restrict__ grad_phase) {
+    const float dx = q.x - p.x, dy = q.y - p.y, dz = q.z - p.z;
+    const float l2 = dx * dx + dy * dy + dz * dz;
+    if (!(l2 > 0.f)) return;                              // zero length: no force
+    const float inv = rsqrtf(l2);
+    const float l = l2 * inv;
+    const float ux = dx * inv, uy = dy * inv, uz = dz * inv;
+    const float k = a.x;
+    float sn, cs;
+    sincosf(ph + s.y, &sn, &cs);
+    const float L = a.y * (1.f + s.x * sn);
+    const float dvx = w.x - v.x, dvy = w.y - v.y, dvz = w.z - v.z;
+    const float rate = dvx * ux + dvy * uy + dvz * uz;
+    const float f = k * (l - L) + cd * rate;
+    const float gx = Fi.x - Fj.x, gy = Fi.y - Fj.y, gz = Fi.z - Fj.z;
+    const float fb = gx * ux + gy * uy + gz * uz;
+    const float lb = k * fb, Lb = -k * fb, rb = cd * fb;
+    const float ubx = f * gx + rb * dvx, uby = f * gy + rb * dvy, ubz = f * gz + rb * dvz;
+    v_b.x -= rb * ux; v_b.y -= rb * uy; v_b.z -= rb * uz;
+    const float udot = ubx * ux + uby * uy + ubz * uz;
+    x_b.x -= (ubx - udot * ux) * inv + lb * ux;
+    x_b.y -= (uby - udot * uy) * inv + lb * uy;
+    x_b.z -= (ubz - udot * uz) * inv + lb * uz;
+    if (spr & kOwner) {
+        const uint32_t sid = spr & ~kOwner;
+        grad_amp[sid] += Lb * a.y * sn;
+        grad_phase[sid] += Lb * a.y * s.x * cs;
+    }
+}
+
+// Widths are even: two entries per iteration, every load of both issued
+// before either is reversed (summation order unchanged: entry t, then t + 1).
 template <bool HAS_C>
 __global__ void __launch_bounds__(kT)
 k_adj_spring(const MassState *__restrict__ X, const float4 *__restrict__ Fb, float4 *__restrict__ xb,
@@ -88,46 +126,26 @@ k_adj_spring(const MassState *__restrict__ X, const float4 *__restrict__ Fb, flo
     const uint32_t sl = i >> 5, lane = i & 31;
     const uint32_t e0 = slice_off[sl];
     const uint32_t width = (slice_off[sl + 1] - e0) >> 5;
-    const float4 p = X[i].p, v = X[i].v;
+    float4 p, v;
+    titan::load_state(X + i, p, v);
     const float4 Fi = Fb[i];
     float4 x_b = xb[i], v_b = vb[i];
     const float ph = titan::clock_phase(c, step);
-    for (uint32_t t = 0; t < width; ++t) {
-        const uint32_t e = e0 + 32 * t + lane;
-        const uint32_t spr = spring[e];
-        if (spr == kNoSpring) continue;                   // padding entry
-        const uint32_t j = nbr[e];
-        const float4 q = X[j].p, w = X[j].v;
-        const float dx = q.x - p.x, dy = q.y - p.y, dz = q.z - p.z;
-        const float l2 = dx * dx + dy * dy + dz * dz;
-        if (!(l2 > 0.f)) continue;                          // zero length: no force
-        const float inv = rsqrtf(l2);
-        const float l = l2 * inv;
-        const float ux = dx * inv, uy = dy * inv, uz = dz * inv;
-        const float2 a = kl[e], s = act[e];
-        const float k = a.x;
-        float sn, cs;
-        sincosf(ph + s.y, &sn, &cs);
-        const float L = a.y * (1.f + s.x * sn);
-        const float cd = HAS_C ? cc[e] : c.c_uniform;
-        const float dvx = w.x - v.x, dvy = w.y - v.y, dvz = w.z - v.z;
-        const float rate = dvx * ux + dvy * uy + dvz * uz;
-        const float f = k * (l - L) + cd * rate;
-        const float4 Fj = Fb[j];
-        const float gx = Fi.x - Fj.x, gy = Fi.y - Fj.y, gz = Fi.z - Fj.z;
-        const float fb = gx * ux + gy * uy + gz * uz;
-        const float lb = k * fb, Lb = -k * fb, rb = cd * fb;
-        float ubx = f * gx + rb * dvx, uby = f * gy + rb * dvy, ubz = f * gz + rb * dvz;
-        v_b.x -= rb * ux; v_b.y -= rb * uy; v_b.z -= rb * uz;
-        const float udot = ubx * ux + uby * uy + ubz * uz;
-        x_b.x -= (ubx - udot * ux) * inv + lb * ux;
-        x_b.y -= (uby - udot * uy) * inv + lb * uy;
-        x_b.z -= (ubz - udot * uz) * inv + lb * uz;
-        if (spr & kOwner) {
-            const uint32_t sid = spr & ~kOwner;
-            grad_amp[sid] += Lb * a.y * sn;
-            grad_phase[sid] += Lb * a.y * s.x * cs;
-        }
+    for (uint32_t t = 0; t < width; t += 2) {
+        const uint32_t e = e0 + 32 * t + lane, f = e + 32;
+        const uint32_t spr0 = __ldg(spring + e), spr1 = __ldg(spring + f);
+        // padding entries point at the mass itself: their loads are harmless
+        const uint32_t j0 = __ldg(nbr + e), j1 = __ldg(nbr + f);
+        const float2 a0 = __ldg(kl + e), a1 = __ldg(kl + f), s0 = __ldg(act + e), s1 = __ldg(act + f);
+        const float c0 = HAS_C ? __ldg(cc + e) : c.c_uniform, c1 = HAS_C ? __ldg(cc + f) : c.c_uniform;
+        float4 q0, w0, q1, w1;
+        titan::load_state(X + j0, q0, w0);
+        titan::load_state(X + j1, q1, w1);
+        const float4 F0 = __ldg(Fb + j0), F1 = __ldg(Fb + j1);
+        if (spr0 != kNoSpring)
+            adj_half_edge<HAS_C>(p, v, Fi, q0, w0, F0, a0, s0, c0, ph, spr0, x_b, v_b, grad_amp, grad_phase);
+        if (spr1 != kNoSpring)
+            adj_half_edge<HAS_C>(p, v, Fi, q1, w1, F1, a1, s1, c1, ph, spr1, x_b, v_b, grad_amp, grad_phase);
     }
     xb[i] = x_b;
     vb[i] = v_b;
