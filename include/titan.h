@@ -113,11 +113,9 @@ typedef struct {
                                  TMA-staged stream, 6 grid-box tables (masses on a
                                  cubic grid, at most one per cell; no neighbour
                                  index in the stream), 7 grid box + TMA-staged
-                                 stream, 8 grid box + per-thread copy ring (uniform
-                                 damping and no actuation; otherwise runs as 6).
-                                 4 to 8 return TITAN_E_UNSUPPORTED if their tables
-                                 do not fit or (6 to 8) the masses are not on a
-                                 grid                                       */
+                                 stream.  4 to 7 return TITAN_E_UNSUPPORTED if
+                                 their tables do not fit or (6, 7) the masses are
+                                 not on a grid                              */
     int32_t reserved[6];      /* zero                                              */
 } titan_params;
 
@@ -253,7 +251,7 @@ uint64_t titan_steps(const titan_sim *sim);
  * rebuild; an edit that no longer fits falls back to launches. */
 int32_t titan_exec_mode(const titan_sim *sim);
 
-/* The step kernel titan_create resolved params.kernel_variant to: 1..8 as
+/* The step kernel titan_create resolved params.kernel_variant to: 1..7 as
  * listed for kernel_variant (never 0), 0 for atomic accumulation, -1 for a
  * NULL handle.  The resolution is redone when added masses or springs force a
  * layout rebuild. */

@@ -61,19 +61,6 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
-// Per-thread asynchronous 8-byte copy global -> shared (LDGSTS), completed
-// by this thread's cp.async.wait_group; both addresses 8-byte aligned.
-__device__ __forceinline__ void cp_async_8(void *dst, const void *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-
-// Closes the group of this thread's cp.async copies issued since the last commit.
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-
-// Waits until at most N of this thread's committed groups are still in flight.
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
 // 1-D bulk prefetch of global memory into L2 (TMA engine); no completion
 // tracking.  addr 16-byte aligned, bytes a multiple of 16.
 __device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes) {

@@ -145,7 +145,7 @@ titan_status validate(const titan_masses *m, const titan_springs *sp, const tita
     if (p->exec < TITAN_EXEC_AUTO || p->exec > TITAN_EXEC_PERSISTENT)
         return fail(nullptr, TITAN_E_INVALID, "params.exec out of range");
     if (p->device < 0) return fail(nullptr, TITAN_E_INVALID, "params.device must be >= 0");
-    if (p->kernel_variant < 0 || p->kernel_variant > 8) return fail(nullptr, TITAN_E_INVALID, "params.kernel_variant must be 0..8");
+    if (p->kernel_variant < 0 || p->kernel_variant > 7) return fail(nullptr, TITAN_E_INVALID, "params.kernel_variant must be 0..7");
     for (uint64_t i = 0; i < m->n; ++i) {
         for (int a = 0; a < 3; ++a) {
             if (!finite(m->pos[3 * i + a])) return fail(nullptr, TITAN_E_INVALID, "masses.pos has a non-finite value at mass " + std::to_string(i));
@@ -211,11 +211,9 @@ cudaError_t enqueue_step(titan_sim *sim, cudaStream_t st, int b) {
     if (sim->accumulate == TITAN_ACCUM_CSR) {
         titan::SellView v{sim->d_slice_off, sim->d_nbr, sim->d_kl, sim->has_c ? sim->d_c : nullptr,
                           sim->has_act ? sim->d_act : nullptr, 0, sim->spin_limit, sim->d_err};
-        if (sim->csr_kernel >= 6 && sim->csr_kernel <= 8) {
+        if (sim->csr_kernel == 6 || sim->csr_kernel == 7) {
             titan::BoxView h{sim->d_col_off, sim->d_own_slot, sim->d_ext_off, sim->d_ext_idx, sim->d_ext_slot,
                              (sim->box.max_table + 1) & ~1u};
-            if (sim->csr_kernel == 8 && !sim->has_c && !sim->has_act)
-                return titan::launch_step_box_ring(in, out, sim->n_dev, v, h, sim->c, si, so, st);
             if (sim->csr_kernel == 7)
                 return titan::launch_step_box_tma(in, out, sim->n_dev, v, h, sim->halo_w_max, sim->c, si, so, st);
             return titan::launch_step_box(in, out, sim->n_dev, v, h, sim->c, si, so, st);
@@ -515,9 +513,9 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
             return bail(fail(sim, TITAN_E_UNSUPPORTED, "padded incidence exceeds 2^32 entries"));
         const int want = p->kernel_variant;
         sim->csr_kernel = want == 0 ? (sim->grid_order ? 6 : 4) : want;
-        if (sim->csr_kernel >= 6 && sim->csr_kernel <= 8 &&
+        if ((sim->csr_kernel == 6 || sim->csr_kernel == 7) &&
             !(sim->grid_order && titan::build_box(nd, sim->sell, cells, sim->caller_of_dev, kHaloMaxSlots, sim->box))) {
-            if (want >= 6)
+            if (want == 6 || want == 7)
                 return bail(fail(sim, TITAN_E_UNSUPPORTED, "the grid box kernel needs masses on a grid whose "
                                                            "blocks' boxes fit " + std::to_string(kHaloMaxSlots) + " slots"));
             sim->csr_kernel = 4;
@@ -553,7 +551,7 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
         CREATE_CK(dev_alloc(sim, &sim->d_kl, E));
         CREATE_CK(upload(sim->d_slice_off, sim->sell.slice_off, sim->stream));
         CREATE_CK(upload(sim->d_kl, kl, sim->stream));
-        if (sim->csr_kernel >= 6 && sim->csr_kernel <= 8) {
+        if (sim->csr_kernel == 6 || sim->csr_kernel == 7) {
             const titan::BoxHost &h = sim->box;
             CREATE_CK(dev_alloc(sim, &sim->d_col_off, h.col_off.size()));
             CREATE_CK(dev_alloc(sim, &sim->d_own_slot, nd));

@@ -356,102 +356,6 @@ k_step_box(const MassState *__restrict__ in, MassState *__restrict__ out, uint32
     integrate<GROUND>(p, v, fx, fy, fz, c, out + i);
 }
 
-// K1, grid-box form with a per-thread copy ring: as k_step_box, but each
-// thread keeps its next kBoxRing {k, L0} entries in flight with per-thread
-// asynchronous copies into a ring in shared memory (one slot per lane per
-// column, read back only by the lane that copied it, so no barrier is
-// needed), deepening the stream pipeline without holding the data in
-// registers.  Uniform damping and no actuation only (the common case of
-// large lattices); the runtime uses k_step_box otherwise.
-constexpr int kBoxRing = 6;            // columns in flight per thread (even)
-
-template <bool GROUND>
-__global__ void __launch_bounds__(kHaloThreads, kBoxMinBlocks)
-k_step_box_ring(const MassState *__restrict__ in, MassState *__restrict__ out, uint32_t n,
-                const uint32_t *__restrict__ slice_off, const uint32_t *__restrict__ col_off2,
-                const float2 *__restrict__ kl, const uint16_t *__restrict__ own_slot,
-                const uint32_t *__restrict__ ext_off, const uint32_t *__restrict__ ext_idx,
-                const uint16_t *__restrict__ ext_slot, uint32_t table_slots, StepConst c,
-                const long long *__restrict__ step_in, long long *__restrict__ step_out) {
-    extern __shared__ float4 rtab[];
-    float4 *tA = rtab;
-    float2 *tB = reinterpret_cast<float2 *>(rtab + table_slots);
-    const uint32_t b = blockIdx.x, tid = threadIdx.x;
-    const uint32_t i = b * kHaloThreads + tid;
-    const uint32_t lane = tid & 31, w = tid >> 5, sl = i >> 5;
-    // ring[w][column slot][lane], after the table (16-byte aligned: even slot count)
-    float2 *ring = reinterpret_cast<float2 *>(tB + table_slots) + (size_t)w * kBoxRing * 32 + lane;
-    if (b == 0 && tid == 0) *step_out = *step_in + 1;
-    const uint32_t s_own = i < n ? own_slot[i] : kBoxHoleSlot;
-    const bool valid = s_own != kBoxHoleSlot;
-
-    uint32_t e0 = 0, width = 0;
-    float4 p = make_float4(0.f, 0.f, 0.f, 0.f), v = p;
-    const uint32_t *co = col_off2;
-    if (valid) {
-        e0 = __ldg(slice_off + sl);
-        width = (__ldg(slice_off + sl + 1) - e0) >> 5;
-        co = col_off2 + (e0 >> 6);       // even widths: a pair of int16 offsets per word
-    }
-    // fill the ring (columns 0 .. kBoxRing - 1), one group per column pair
-#pragma unroll
-    for (int r = 0; r < kBoxRing; r += 2) {
-        if ((uint32_t)r < width) {
-            ptx::cp_async_8(ring + 32 * r, kl + e0 + 32 * r + lane);
-            ptx::cp_async_8(ring + 32 * (r + 1), kl + e0 + 32 * (r + 1) + lane);
-        }
-        ptx::cp_async_commit();
-    }
-    if (valid) {
-        load_state(in + i, p, v);
-        tA[s_own] = make_float4(p.x, p.y, p.z, v.x);
-        tB[s_own] = make_float2(v.y, v.z);
-    }
-    const uint32_t h0 = __ldg(ext_off + b), h1 = __ldg(ext_off + b + 1);
-    for (uint32_t h = h0 + tid; h < h1; h += kHaloThreads) {
-        float4 q, ww;
-        load_state(in + __ldg(ext_idx + h), q, ww);
-        const uint32_t s = __ldg(ext_slot + h);
-        tA[s] = make_float4(q.x, q.y, q.z, ww.x);
-        tB[s] = make_float2(ww.y, ww.z);
-    }
-    __syncthreads();
-    if (!valid) {
-        ptx::cp_async_wait<0>();          // no copy of this thread outlives it
-        return;
-    }
-
-    float fx = 0.f, fy = 0.f, fz = 0.f;
-    uint32_t slot = 0;                    // ring slot of column t
-    for (uint32_t t = 0; t < width; t += 2) {
-        ptx::cp_async_wait<kBoxRing / 2 - 1>();      // the group of columns t, t + 1 has landed
-        const float2 a0 = ring[32 * slot], a1 = ring[32 * (slot + 1)];
-        const uint32_t o = __ldg(co + (t >> 1));
-        const uint32_t j0 = s_own + (uint32_t)(int32_t)(int16_t)(o & 0xffffu);
-        const uint32_t j1 = s_own + (uint32_t)(int32_t)(int16_t)(o >> 16);
-        if (a0.y != 0.f) {
-            const float4 qa = tA[j0];
-            const float2 qb = tB[j0];
-            spring_force(p, v, qa, make_float4(qa.w, qb.x, qb.y, 0.f), a0.x, a0.y, c.c_uniform, fx, fy, fz);
-        }
-        if (a1.y != 0.f) {
-            const float4 qa = tA[j1];
-            const float2 qb = tB[j1];
-            spring_force(p, v, qa, make_float4(qa.w, qb.x, qb.y, 0.f), a1.x, a1.y, c.c_uniform, fx, fy, fz);
-        }
-        // refill the two slots just read (their values are consumed above)
-        const uint32_t tn = t + kBoxRing;
-        if (tn < width) {
-            ptx::cp_async_8(ring + 32 * slot, kl + e0 + 32 * tn + lane);
-            ptx::cp_async_8(ring + 32 * (slot + 1), kl + e0 + 32 * (tn + 1) + lane);
-        }
-        ptx::cp_async_commit();
-        slot = slot + 2 == kBoxRing ? 0 : slot + 2;
-    }
-    ptx::cp_async_wait<0>();
-    integrate<GROUND>(p, v, fx, fy, fz, c, out + i);
-}
-
 // K1, grid-box form with the stream staged by TMA: as k_step_box, but lane 0
 // of each warp first copies its slice's {k, L0} (and c, actuation) columns
 // into shared memory with 1-D bulk copies on one mbarrier per warp, so a
@@ -1053,25 +957,6 @@ cudaError_t launch_step_halo_tma(const MassState *in, MassState *out, uint32_t n
         else    { if (gr) TITAN_HTMA(false, false, true); else TITAN_HTMA(false, false, false); }
     }
 #undef TITAN_HTMA
-    return cudaGetLastError();
-}
-
-cudaError_t launch_step_box_ring(const MassState *in, MassState *out, uint32_t n, const SellView &v,
-                                 const BoxView &h, const StepConst &c, const long long *step_in, long long *step_out,
-                                 cudaStream_t stream) {
-    if (v.c || v.act) return cudaErrorInvalidValue;          // uniform damping, no actuation only
-    if ((reinterpret_cast<uintptr_t>(h.col_off) & 3) || (h.table_slots & 1)) return cudaErrorInvalidValue;
-    const unsigned g = n ? (n + kHaloThreads - 1) / kHaloThreads : 1;
-    const size_t bytes = (size_t)h.table_slots * (sizeof(float4) + sizeof(float2)) +
-                         (size_t)(kHaloThreads / 32) * kBoxRing * 32 * sizeof(float2);
-    auto kern = c.ground ? k_step_box_ring<true> : k_step_box_ring<false>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
-    if (e != cudaSuccess) return e;
-    kern<<<g, kHaloThreads, bytes, stream>>>(in, out, n, v.slice_off, reinterpret_cast<const uint32_t *>(h.col_off),
-                                             v.kl, h.own_slot, h.ext_off, h.ext_idx, h.ext_slot, h.table_slots, c,
-                                             step_in, step_out);
     return cudaGetLastError();
 }
 

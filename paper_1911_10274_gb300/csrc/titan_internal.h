@@ -100,12 +100,6 @@ cudaError_t launch_step_box(const MassState *in, MassState *out, uint32_t n, con
                             const StepConst &c, const long long *step_in, long long *step_out,
                             cudaStream_t stream);
 
-// Grid-box form with a per-thread asynchronous-copy ring for the stream
-// (uniform damping, no actuation; cudaErrorInvalidValue otherwise).
-cudaError_t launch_step_box_ring(const MassState *in, MassState *out, uint32_t n, const SellView &v,
-                                 const BoxView &h, const StepConst &c, const long long *step_in, long long *step_out,
-                                 cudaStream_t stream);
-
 // Grid-box form with the stream staged into shared memory by TMA bulk copies;
 // slices wider than w_max columns read from global memory.
 cudaError_t launch_step_box_tma(const MassState *in, MassState *out, uint32_t n, const SellView &v,

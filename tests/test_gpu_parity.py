@@ -46,12 +46,11 @@ MODES = [dict(accumulate=T.ACCUM_CSR), dict(accumulate=T.ACCUM_ATOMIC),
          dict(accumulate=T.ACCUM_CSR, kernel_variant=5, **LAUNCH),
          dict(accumulate=T.ACCUM_CSR, kernel_variant=6, **LAUNCH),
          dict(accumulate=T.ACCUM_CSR, kernel_variant=7, **LAUNCH),
-         dict(accumulate=T.ACCUM_CSR, kernel_variant=8, **LAUNCH),
          dict(accumulate=T.ACCUM_CSR, exec_mode=T.EXEC_PERSISTENT),
          dict(accumulate=T.ACCUM_CSR, order=T.ORDER_INPUT),
          dict(accumulate=T.ACCUM_CSR, graph_chunk=-1, **LAUNCH)]
 MODE_IDS = ["csr", "atomic", "csr-direct-loads", "csr-tma-staged", "csr-bulk-prefetch", "csr-halo",
-            "csr-halo-tma", "csr-grid-box", "csr-grid-box-tma", "csr-grid-box-ring", "csr-persistent", "csr-input-order", "csr-no-graph"]
+            "csr-halo-tma", "csr-grid-box", "csr-grid-box-tma", "csr-persistent", "csr-input-order", "csr-no-graph"]
 
 
 @pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
@@ -141,7 +140,7 @@ def test_lattice_with_holes_in_grid_tiles():
                         fixed=np.zeros(len(pos), np.uint8), ends=ends, k=np.full(len(ends), 1e4),
                         rest=d * rng.uniform(0.97, 1.03, len(d)), damping=np.full(len(ends), 1.0),
                         dt=1e-4, ground=True, spacing=0.1)
-    for var in (0, 8, 7, 6, 5, 4, 3):
+    for var in (0, 7, 6, 5, 4, 3):
         check(sys, 1000, kernel_variant=var, **(LAUNCH if var else {}))
 
 
@@ -207,7 +206,7 @@ def test_csr_kernel_variants_agree_bit_exact():
     sys = inputs.cube_drop(drop_height=0.02)
     sys.vel[:, 0] = 0.3
     a = gpu_run(sys, 500, exec_mode=T.EXEC_PERSISTENT)
-    for var in (1, 2, 3, 4, 5, 6, 7, 8):
+    for var in (1, 2, 3, 4, 5, 6, 7):
         b = gpu_run(sys, 500, kernel_variant=var, **LAUNCH)
         assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
 
@@ -311,8 +310,7 @@ def test_full_size_lattice_against_oracle_in_bench_configuration():
                  dict(accumulate=T.ACCUM_CSR, kernel_variant=3, **LAUNCH),
                  dict(accumulate=T.ACCUM_CSR, kernel_variant=4, **LAUNCH),
                  dict(accumulate=T.ACCUM_CSR, kernel_variant=6, **LAUNCH),
-                 dict(accumulate=T.ACCUM_CSR, kernel_variant=7, **LAUNCH),
-                 dict(accumulate=T.ACCUM_CSR, kernel_variant=8, **LAUNCH), dict(accumulate=T.ACCUM_ATOMIC)):
+                 dict(accumulate=T.ACCUM_CSR, kernel_variant=7, **LAUNCH), dict(accumulate=T.ACCUM_ATOMIC)):
         xg, vg, _ = gpu_run(sys, 64, **mode)
         err = np.abs(xg - xo).max()
         assert err <= POS_TOL_FRAC * sys.spacing, err
@@ -362,7 +360,7 @@ def test_grid_with_second_neighbour_springs_and_duplicates():
                         dt=1e-4, ground=True, spacing=0.1)
     with T.Sim(sys) as sim:
         assert sim.csr_kernel == 6
-    runs = [gpu_run(sys, 400, kernel_variant=v, **LAUNCH) for v in (6, 7, 8, 4, 3)]
+    runs = [gpu_run(sys, 400, kernel_variant=v, **LAUNCH) for v in (6, 7, 4, 3)]
     runs.append(gpu_run(sys, 400, exec_mode=T.EXEC_PERSISTENT))
     for r in runs[1:]:
         assert np.array_equal(runs[0][0], r[0]) and np.array_equal(runs[0][1], r[1])
