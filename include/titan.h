@@ -387,9 +387,10 @@ titan_status titan_batch_destroy(titan_batch *b);
 typedef struct titan_mlp titan_mlp;
 
 /* C[M][N] = A[M][K] B[N][K]^T on the tensor cores: A and B row-major BF16
- * (uint16 bit patterns, 16-byte aligned), C row-major FP32.  M and N multiples
- * of 128, K of 64.  Waits for completion.  Errors: TITAN_E_INVALID,
- * TITAN_E_CUDA, TITAN_E_TIMEOUT (a bounded wait in the kernel expired). */
+ * (uint16 bit patterns, 16-byte aligned), C row-major FP32, all on the
+ * current device.  M and N multiples of 128, K of 64.  Runs on `stream` and
+ * waits for completion.  Errors: TITAN_E_INVALID, TITAN_E_CUDA,
+ * TITAN_E_TIMEOUT (a bounded wait in the kernel expired). */
 titan_status titan_gemm_bf16_tn(uint32_t M, uint32_t N, uint32_t K, const uint16_t *A_dev,
                                 const uint16_t *B_dev, float *C_dev, void *stream);
 

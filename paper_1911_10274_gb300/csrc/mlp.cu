@@ -466,14 +466,22 @@ titan_status titan_gemm_bf16_tn(uint32_t M, uint32_t N, uint32_t K, const uint16
     if (!A_dev || !B_dev || !C_dev) return mfail(nullptr, TITAN_E_INVALID, "titan_gemm_bf16_tn: null pointer");
     if (M % BM || N % BN || K % BK || !M || !N || !K)
         return mfail(nullptr, TITAN_E_INVALID, "titan_gemm_bf16_tn: M and N must be multiples of 128, K of 64");
-    static int *err = nullptr;
+    // one device error flag per device ordinal, allocated on first use with that device current
+    static int *err_of[64] = {};
     static std::mutex mu;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+        return mfail(nullptr, TITAN_E_CUDA, "titan_gemm_bf16_tn: no current device");
+    int *err = nullptr;
     {
         std::lock_guard<std::mutex> lk(mu);
-        if (!err) {
-            if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) return mfail(nullptr, TITAN_E_OOM, "error flag");
-            cudaMemset(err, 0, sizeof(int));
+        if (!err_of[dev]) {
+            if (cudaMalloc(&err_of[dev], sizeof(int)) != cudaSuccess)
+                return mfail(nullptr, TITAN_E_OOM, "titan_gemm_bf16_tn: error flag");
+            if (cudaMemset(err_of[dev], 0, sizeof(int)) != cudaSuccess)
+                return mfail(nullptr, TITAN_E_CUDA, "titan_gemm_bf16_tn: error flag");
         }
+        err = err_of[dev];
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     EpiArgs ep{EPI_F32, (int)N, nullptr, C_dev, nullptr, nullptr};
