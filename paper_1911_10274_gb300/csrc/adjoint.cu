@@ -77,12 +77,14 @@ k_adj_mass(const MassState *__restrict__ X, const float4 *__restrict__ xbo, cons
 }
 
 // The adjoint of one spring seen from the mass at (p, v): adds to x_b, v_b and,
-// for the spring's owner half-edge, to the spring's dJ/dA and dJ/dphi.
+// for the spring's owner half-edge, to the spring's (dJ/dA, dJ/dphi) kept at
+// that half-edge's entry (coalesced with the rows; gathered per spring at the
+// end).
 template <bool HAS_C>
 __device__ __forceinline__ void adj_half_edge(const float4 &p, const float4 &v, const float4 &Fi, const float4 &q,
                                               const float4 &w, const float4 &Fj, float2 a, float2 s, float cd,
                                               float ph, uint32_t spr, float4 &x_b, float4 &v_b,
-                                              float *__restrict__ grad_amp, float *__restrict__ grad_phase) {
+                                              float2 *__restrict__ gacc) {
     const float dx = q.x - p.x, dy = q.y - p.y, dz = q.z - p.z;
     const float l2 = dx * dx + dy * dy + dz * dz;
     if (!(l2 > 0.f)) return;                              // zero length: no force
@@ -105,10 +107,11 @@ __device__ __forceinline__ void adj_half_edge(const float4 &p, const float4 &v, 
     x_b.x -= (ubx - udot * ux) * inv + lb * ux;
     x_b.y -= (uby - udot * uy) * inv + lb * uy;
     x_b.z -= (ubz - udot * uz) * inv + lb * uz;
-    if (spr & kOwner) {
-        const uint32_t sid = spr & ~kOwner;
-        grad_amp[sid] += Lb * a.y * sn;
-        grad_phase[sid] += Lb * a.y * s.x * cs;
+    if (spr & kOwner) {                   // gacc points at this entry's accumulator
+        float2 g = *gacc;
+        g.x += Lb * a.y * sn;
+        g.y += Lb * a.y * s.x * cs;
+        *gacc = g;
     }
 }
 
@@ -120,7 +123,7 @@ k_adj_spring(const MassState *__restrict__ X, const float4 *__restrict__ Fb, flo
              float4 *__restrict__ vb, uint32_t n, const uint32_t *__restrict__ slice_off,
              const uint32_t *__restrict__ nbr, const uint32_t *__restrict__ spring,
              const float2 *__restrict__ kl, const float2 *__restrict__ act, const float *__restrict__ cc,
-             titan::StepConst c, long long step, float *__restrict__ grad_amp, float *__restrict__ grad_phase) {
+             titan::StepConst c, long long step, float2 *__restrict__ gacc) {
     const uint32_t i = blockIdx.x * kT + threadIdx.x;
     if (i >= n) return;
     const uint32_t sl = i >> 5, lane = i & 31;
@@ -143,12 +146,22 @@ k_adj_spring(const MassState *__restrict__ X, const float4 *__restrict__ Fb, flo
         titan::load_state(X + j1, q1, w1);
         const float4 F0 = __ldg(Fb + j0), F1 = __ldg(Fb + j1);
         if (spr0 != kNoSpring)
-            adj_half_edge<HAS_C>(p, v, Fi, q0, w0, F0, a0, s0, c0, ph, spr0, x_b, v_b, grad_amp, grad_phase);
+            adj_half_edge<HAS_C>(p, v, Fi, q0, w0, F0, a0, s0, c0, ph, spr0, x_b, v_b, gacc + e);
         if (spr1 != kNoSpring)
-            adj_half_edge<HAS_C>(p, v, Fi, q1, w1, F1, a1, s1, c1, ph, spr1, x_b, v_b, grad_amp, grad_phase);
+            adj_half_edge<HAS_C>(p, v, Fi, q1, w1, F1, a1, s1, c1, ph, spr1, x_b, v_b, gacc + f);
     }
     xb[i] = x_b;
     vb[i] = v_b;
+}
+
+// grad[q] = the accumulator of spring q's owner entry.
+__global__ void k_adj_gather(const float2 *__restrict__ gacc, const uint32_t *__restrict__ owner, uint32_t S,
+                             float *__restrict__ grad_amp, float *__restrict__ grad_phase) {
+    const uint32_t q = blockIdx.x * kT + threadIdx.x;
+    if (q >= S) return;
+    const float2 g = gacc[owner[q]];
+    grad_amp[q] = g.x;
+    grad_phase[q] = g.y;
 }
 
 __global__ void k_adj_seed(const float *__restrict__ seed_pos, const float *__restrict__ seed_vel,
@@ -193,6 +206,7 @@ extern "C" titan_status titan_adjoint(titan_sim *sim, uint64_t n_steps, uint32_t
     MassState *ckpt = nullptr, *seg = nullptr;
     float4 *xb[2] = {nullptr, nullptr}, *vb[2] = {nullptr, nullptr}, *Fb = nullptr;
     long long *seg_steps = nullptr;
+    float2 *gacc = nullptr;
     uint64_t n_seg = 0;
     int cur = 0;
     if ((st_ = titan::ensure_layout(sim)) != TITAN_OK) goto out;
@@ -215,6 +229,13 @@ extern "C" titan_status titan_adjoint(titan_sim *sim, uint64_t n_steps, uint32_t
             sim->allocations.push_back(p1);
             sim->d_adj_spring = static_cast<uint32_t *>(p1);
             ADJ_CK(cudaMemcpy(sim->d_adj_spring, spr.data(), spr.size() * 4, cudaMemcpyHostToDevice));
+            std::vector<uint32_t> owner(S);
+            for (uint32_t q = 0; q < S; ++q) owner[q] = sim->sell.entry_of_end[2 * (size_t)q];
+            void *p3 = nullptr;
+            ADJ_CK(cudaMalloc(&p3, std::max<size_t>(owner.size(), 1) * 4));
+            sim->allocations.push_back(p3);
+            sim->d_adj_owner = static_cast<uint32_t *>(p3);
+            ADJ_CK(cudaMemcpy(sim->d_adj_owner, owner.data(), owner.size() * 4, cudaMemcpyHostToDevice));
             if (!sim->d_nbr) {
                 void *p2 = nullptr;
                 ADJ_CK(cudaMalloc(&p2, std::max<size_t>(sim->sell.nbr.size(), 1) * 4));
@@ -233,6 +254,8 @@ extern "C" titan_status titan_adjoint(titan_sim *sim, uint64_t n_steps, uint32_t
         }
         ADJ_CK(cudaMallocAsync((void **)&Fb, vec_bytes, s));
         ADJ_CK(cudaMallocAsync((void **)&seg_steps, sizeof(long long) * (every + 1), s));
+        ADJ_CK(cudaMallocAsync((void **)&gacc, std::max<size_t>(sim->sell.entries, 1) * sizeof(float2), s));
+        ADJ_CK(cudaMemsetAsync(gacc, 0, std::max<size_t>(sim->sell.entries, 1) * sizeof(float2), s));
         const uint64_t step0 = sim->steps;
         // forward rollout through the ordinary step, keeping checkpoints
         ADJ_CK(cudaMemcpyAsync(ckpt, sim->state[sim->cur], state_bytes, cudaMemcpyDeviceToDevice, s));
@@ -253,10 +276,7 @@ extern "C" titan_status titan_adjoint(titan_sim *sim, uint64_t n_steps, uint32_t
                                                              sim->n, xb[0], vb[0]);
             ADJ_CK(cudaGetLastError());
         }
-        if (S) {
-            ADJ_CK(cudaMemsetAsync(grad_amp_dev, 0, (size_t)S * 4, s));
-            ADJ_CK(cudaMemsetAsync(grad_phase_dev, 0, (size_t)S * 4, s));
-        }
+
         titan::SellView v{sim->d_slice_off, sim->d_nbr, sim->d_kl, sim->has_c ? sim->d_c : nullptr, sim->d_act, 1,
                           sim->spin_limit, sim->d_err};
         for (uint64_t g = n_seg; g-- > 0;) {
@@ -278,14 +298,18 @@ extern "C" titan_status titan_adjoint(titan_sim *sim, uint64_t n_steps, uint32_t
                 if (sim->has_c)
                     k_adj_spring<true><<<gm, kT, 0, s>>>(X, Fb, xb[cur ^ 1], vb[cur ^ 1], nd, sim->d_slice_off, sim->d_nbr,
                                                          sim->d_adj_spring, sim->d_kl, sim->d_act, sim->d_c, sim->c,
-                                                         stepk, grad_amp_dev, grad_phase_dev);
+                                                         stepk, gacc);
                 else
                     k_adj_spring<false><<<gm, kT, 0, s>>>(X, Fb, xb[cur ^ 1], vb[cur ^ 1], nd, sim->d_slice_off, sim->d_nbr,
                                                           sim->d_adj_spring, sim->d_kl, sim->d_act, sim->d_c, sim->c,
-                                                          stepk, grad_amp_dev, grad_phase_dev);
+                                                          stepk, gacc);
                 ADJ_CK(cudaGetLastError());
                 cur ^= 1;
             }
+        }
+        if (S) {
+            k_adj_gather<<<(S + kT - 1) / kT, kT, 0, s>>>(gacc, sim->d_adj_owner, S, grad_amp_dev, grad_phase_dev);
+            ADJ_CK(cudaGetLastError());
         }
     }
 done:
@@ -297,6 +321,7 @@ done:
     }
     if (Fb) cudaFreeAsync(Fb, s);
     if (seg_steps) cudaFreeAsync(seg_steps, s);
+    if (gacc) cudaFreeAsync(gacc, s);
     if (prev >= 0) cudaSetDevice(prev);
 out:
     sim->busy.store(false);

@@ -83,6 +83,7 @@ struct SimCore {
     uint64_t last_ticket = 0;
 
     uint32_t *d_adj_spring = nullptr;     // adjoint: spring id per SELL entry (+ owner bit)
+    uint32_t *d_adj_owner = nullptr;      // adjoint: owner SELL entry of each spring
 
     std::vector<void *> allocations;
 
