@@ -277,16 +277,15 @@ extern "C" titan_status titan_adjoint(titan_sim *sim, uint64_t n_steps, uint32_t
             ADJ_CK(cudaGetLastError());
         }
 
-        titan::SellView v{sim->d_slice_off, sim->d_nbr, sim->d_kl, sim->has_c ? sim->d_c : nullptr, sim->d_act, 1,
-                          sim->spin_limit, sim->d_err};
         for (uint64_t g = n_seg; g-- > 0;) {
             const uint64_t len = std::min<uint64_t>(every, n_steps - g * every);
             const long long first = (long long)(step0 + g * every);
             ADJ_CK(cudaMemcpyAsync(seg, ckpt + g * nd, state_bytes, cudaMemcpyDeviceToDevice, s));
             ADJ_CK(cudaMemcpyAsync(seg_steps, &first, sizeof(long long), cudaMemcpyHostToDevice, s));
+            // the simulation's own step kernel (every CSR kernel gives bit-identical states)
             for (uint64_t k = 0; k < len; ++k)
-                ADJ_CK(titan::launch_step_sell(seg + k * nd, seg + (k + 1) * nd, nd, v, sim->c, seg_steps + k,
-                                               seg_steps + k + 1, s));
+                ADJ_CK(titan::enqueue_sim_step_io(sim, s, seg + k * nd, seg + (k + 1) * nd, seg_steps + k,
+                                                  seg_steps + k + 1));
             for (uint64_t k = len; k-- > 0;) {
                 const MassState *X = seg + k * nd;
                 if (sim->c.ground)

@@ -203,11 +203,8 @@ cudaError_t upload_actuation(titan_sim *sim) {
     return upload(sim->d_ract, a, sim->stream);
 }
 
-cudaError_t enqueue_step(titan_sim *sim, cudaStream_t st, int b) {
-    const MassState *in = sim->state[b];
-    MassState *out = sim->state[1 - b];
-    const long long *si = sim->steps_dev + b;
-    long long *so = sim->steps_dev + (1 - b);
+cudaError_t enqueue_step_io(titan_sim *sim, cudaStream_t st, const MassState *in, MassState *out,
+                            const long long *si, long long *so) {
     if (sim->accumulate == TITAN_ACCUM_CSR) {
         titan::SellView v{sim->d_slice_off, sim->d_nbr, sim->d_kl, sim->has_c ? sim->d_c : nullptr,
                           sim->has_act ? sim->d_act : nullptr, 0, sim->spin_limit, sim->d_err};
@@ -232,6 +229,10 @@ cudaError_t enqueue_step(titan_sim *sim, cudaStream_t st, int b) {
     titan::AtomicView v{sim->d_rec, sim->has_c ? sim->d_rc : nullptr,
                         sim->has_act ? sim->d_ract : nullptr, sim->d_force, sim->s};
     return titan::launch_step_atomic(in, out, sim->n_dev, v, sim->c, si, so, st);
+}
+
+cudaError_t enqueue_step(titan_sim *sim, cudaStream_t st, int b) {
+    return enqueue_step_io(sim, st, sim->state[b], sim->state[1 - b], sim->steps_dev + b, sim->steps_dev + (1 - b));
 }
 
 // Staged columns per slice for the halo+TMA kernel: every slice if two CTAs
@@ -319,6 +320,11 @@ titan_status check_device_error(titan_sim *sim) {
 }  // namespace
 
 cudaError_t titan::enqueue_sim_step(titan_sim *sim, cudaStream_t st, int b) { return enqueue_step(sim, st, b); }
+
+cudaError_t titan::enqueue_sim_step_io(titan_sim *sim, cudaStream_t st, const MassState *in, MassState *out,
+                                       const long long *step_in, long long *step_out) {
+    return enqueue_step_io(sim, st, in, out, step_in, step_out);
+}
 
 namespace {
 

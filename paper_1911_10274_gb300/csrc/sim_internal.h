@@ -106,6 +106,9 @@ struct titan_sim : SimCore {
 namespace titan {
 // Enqueues one fused step reading state buffer b of the simulation (runtime.cu).
 cudaError_t enqueue_sim_step(titan_sim *sim, cudaStream_t st, int b);
+// The same step kernel between caller-chosen buffers (adjoint recomputation).
+cudaError_t enqueue_sim_step_io(titan_sim *sim, cudaStream_t st, const MassState *in, MassState *out,
+                                const long long *step_in, long long *step_out);
 void set_thread_error(const std::string &msg);
 // Rebuilds the device layout if masses or springs were added (runtime.cu).
 titan_status ensure_layout(titan_sim *sim);
