@@ -41,11 +41,14 @@ void set_thread_error(const std::string &msg);   // runtime.cu
 
 namespace {
 
+// BM x BN output tile per CTA; BN = 128 or 256 (wide tiles for large
+// products: each A tile then feeds twice the columns, halving the A traffic
+// from L2 per FLOP).
 constexpr int BM = 128, BN = 128, BK = 64, STAGES = 4;
 constexpr int kGemmThreads = 128;
-constexpr uint32_t kStageA = BM * BK * 2, kStageB = BN * BK * 2;
-constexpr size_t kGemmSmem = (size_t)STAGES * (kStageA + kStageB) + 1024;   // + alignment slack
-constexpr uint32_t kTmemCols = 128;
+constexpr uint32_t kStageA = BM * BK * 2;
+template <int BN_> constexpr uint32_t stage_b() { return (uint32_t)BN_ * BK * 2; }
+template <int BN_> constexpr size_t gemm_smem() { return (size_t)STAGES * (kStageA + stage_b<BN_>()) + 1024; }
 
 enum Epi { EPI_F32 = 0, EPI_BIAS_GELU = 1, EPI_GELU_GRAD = 2 };
 
@@ -64,9 +67,13 @@ __device__ __forceinline__ float gelu_grad(float z) {
 }
 
 // Instruction descriptor of tcgen05.mma.kind::f16: FP32 accumulator, BF16 A
-// and B, both K-major, N = BN, M = BM.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+// and B, both K-major, N = BN_, M = BM.
+template <int BN_>
+constexpr uint32_t idesc() {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN_ >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
 
+template <int BN_>
 __global__ void __launch_bounds__(kGemmThreads, 1)
 k_gemm_tn(const __grid_constant__ CUtensorMap tma_a, const __grid_constant__ CUtensorMap tma_b, int K, EpiArgs ep,
           uint32_t spin_limit, int *__restrict__ err) {
@@ -78,9 +85,11 @@ k_gemm_tn(const __grid_constant__ CUtensorMap tma_a, const __grid_constant__ CUt
     // 1024-byte aligned tiles (the 128-byte swizzle pattern repeats every 1024 bytes)
     const uint32_t raw = titan::ptx::smem_u32(gsm_raw);
     uint8_t *gsm = gsm_raw + (((raw + 1023u) & ~1023u) - raw);
+    constexpr uint32_t kStageB = stage_b<BN_>();
+    constexpr uint32_t kTmemCols = (uint32_t)BN_;      // one FP32 column per output column
     auto tileA = [&](int s) { return gsm + (size_t)s * (kStageA + kStageB); };
     auto tileB = [&](int s) { return gsm + (size_t)s * (kStageA + kStageB) + kStageA; };
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN_;
     const int num_kb = K / BK;
 
     if (warp == 0) titan::ptx::tmem_alloc(&tmem_base, kTmemCols);
@@ -124,7 +133,7 @@ k_gemm_tn(const __grid_constant__ CUtensorMap tma_a, const __grid_constant__ CUt
 #pragma unroll
             for (int k = 0; k < BK / 16; ++k)
                 titan::ptx::tc_mma_bf16(taddr, titan::ptx::smem_desc_sw128(a0 + 32 * k),
-                                        titan::ptx::smem_desc_sw128(b0 + 32 * k), kIdesc, (kb | k) != 0);
+                                        titan::ptx::smem_desc_sw128(b0 + 32 * k), idesc<BN_>(), (kb | k) != 0);
             titan::ptx::tc_commit(&empty[s]);
         }
         titan::ptx::tc_commit(&accf);                  // fires when every issued MMA is done
@@ -138,7 +147,7 @@ k_gemm_tn(const __grid_constant__ CUtensorMap tma_a, const __grid_constant__ CUt
         if (tid == 0) atomicExch(err, 1);
     } else {
         const int row = m0 + warp * 32 + lane;
-        for (int c0 = 0; c0 < BN; c0 += 32) {
+        for (int c0 = 0; c0 < BN_; c0 += 32) {
             float v[32];
             titan::ptx::tmem_ld32(taddr + ((warp * 32u) << 16) + (uint32_t)c0, v);
             const int col = n0 + c0;
@@ -285,12 +294,12 @@ EncodeTiledFn encode_fn() {
 }
 
 // Tensor map of a row-major [rows, cols] BF16 matrix read in 64 x 128 boxes.
-bool make_map(CUtensorMap *map, const void *base, uint64_t rows, uint64_t cols) {
+bool make_map(CUtensorMap *map, const void *base, uint64_t rows, uint64_t cols, uint32_t box_rows = 128) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
     const cuuint64_t dims[2] = {cols, rows};
     const cuuint64_t strides[1] = {cols * 2};
-    const cuuint32_t box[2] = {BK, 128};
+    const cuuint32_t box[2] = {BK, box_rows};
     const cuuint32_t estr[2] = {1, 1};
     return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -299,23 +308,33 @@ bool make_map(CUtensorMap *map, const void *base, uint64_t rows, uint64_t cols) 
 
 // C[M, N] = A[M, K] B[N, K]^T with the given epilogue.  M, N multiples of 128,
 // K a multiple of 64; A, B 16-byte aligned with row strides of K elements.
-cudaError_t gemm_tn(const void *A, const void *B, int M, int N, int K, const EpiArgs &ep, cudaStream_t st,
-                    uint32_t spin_limit, int *err) {
-    if (M % BM || N % BN || K % BK || M <= 0 || N <= 0 || K <= 0) return cudaErrorInvalidValue;
-    if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15) return cudaErrorInvalidValue;
-    CUtensorMap ma, mb;
-    if (!make_map(&ma, A, M, K) || !make_map(&mb, B, N, K)) return cudaErrorInvalidValue;
+template <int BN_>
+cudaError_t gemm_tn_launch(const CUtensorMap &ma, const CUtensorMap &mb, int M, int N, int K, const EpiArgs &ep,
+                           cudaStream_t st, uint32_t spin_limit, int *err) {
     static std::atomic<uint64_t> attr_set{0};
     int dev = 0;
     cudaGetDevice(&dev);
     if (!(attr_set.load() & (1ull << (dev & 63)))) {
-        cudaError_t e = cudaFuncSetAttribute(k_gemm_tn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem);
+        cudaError_t e = cudaFuncSetAttribute(k_gemm_tn<BN_>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)gemm_smem<BN_>());
         if (e != cudaSuccess) return e;
         attr_set.fetch_or(1ull << (dev & 63));
     }
-    dim3 grid(N / BN, M / BM);
-    k_gemm_tn<<<grid, kGemmThreads, kGemmSmem, st>>>(ma, mb, K, ep, spin_limit, err);
+    dim3 grid(N / BN_, M / BM);
+    k_gemm_tn<BN_><<<grid, kGemmThreads, gemm_smem<BN_>(), st>>>(ma, mb, K, ep, spin_limit, err);
     return cudaGetLastError();
+}
+
+cudaError_t gemm_tn(const void *A, const void *B, int M, int N, int K, const EpiArgs &ep, cudaStream_t st,
+                    uint32_t spin_limit, int *err) {
+    if (M % BM || N % BN || K % BK || M <= 0 || N <= 0 || K <= 0) return cudaErrorInvalidValue;
+    if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15) return cudaErrorInvalidValue;
+    // 256-wide tiles once there are at least two waves of them on 152 SMs
+    const bool wide = N % 256 == 0 && (int64_t)(N / 256) * (M / BM) >= 2 * 152;
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, A, M, K) || !make_map(&mb, B, N, K, wide ? 256 : 128)) return cudaErrorInvalidValue;
+    return wide ? gemm_tn_launch<256>(ma, mb, M, N, K, ep, st, spin_limit, err)
+                : gemm_tn_launch<128>(ma, mb, M, N, K, ep, st, spin_limit, err);
 }
 
 inline unsigned nblk(size_t n, int t) { return (unsigned)((n + t - 1) / t); }

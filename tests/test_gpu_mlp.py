@@ -16,7 +16,9 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (256, 384, 512), (512, 512, 4096), (4096, 512, 1024)])
+# the last two shapes have at least two waves of 256-wide tiles: the wide-tile kernel
+@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (256, 384, 512), (512, 512, 4096), (4096, 512, 1024),
+                                   (4096, 2560, 256), (2048, 5120, 192)])
 def test_tcgen05_gemm_matches_reference(M, N, K):
     g = torch.Generator(device="cuda").manual_seed(M + N + K)
     A = torch.randn(M, K, device="cuda", generator=g).bfloat16()
