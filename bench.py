@@ -232,6 +232,7 @@ def config_for(args, system, resolved=None):
            else ("grid cubes of 8x8x4 cells, Morton" if resolved == 6 else "morton"), "graph_chunk": 64,
            "csr_kernel": CSR_KERNELS.get(resolved, f"variant {args.kernel_variant}"),
            "parallelism": f"replicas x{args.gpus}", "exec": args.exec,
+           "l2_persist": not getattr(args, "no_l2_persist", False),
            "l2": "inputs larger than L2 (spring data > 126 MB), no flush" if args.workload in ("lattice1m", "mesh2m")
            else "working set fits in L2 / shared memory, no flush (small-system latency case, not the headline)"}
     if system is not None:
@@ -394,7 +395,8 @@ def run_ours(args):
     exec_mode = {"auto": T.EXEC_AUTO, "launch": T.EXEC_LAUNCH, "persistent": T.EXEC_PERSISTENT}[args.exec]
     order = T.ORDER_MORTON if args.order == "morton" else T.ORDER_INPUT
     sim = T.Sim(system, accumulate=acc, stream=stream.cuda_stream, device=local,
-                kernel_variant=args.kernel_variant, exec_mode=exec_mode, order=order)
+                kernel_variant=args.kernel_variant, exec_mode=exec_mode, order=order,
+                l2_persist=not args.no_l2_persist)
     launches_per_step = 1 if acc == T.ACCUM_CSR else 2
     resolved = sim.csr_kernel
     persistent = sim.exec_mode == T.EXEC_PERSISTENT
@@ -500,6 +502,8 @@ def main():
     ap.add_argument("--robots", type=int, default=4096, help="robots of the --leg batched/adjoint run")
     ap.add_argument("--rollout-steps", type=int, default=2000, help="rollout steps of the --leg run")
     ap.add_argument("--untuned", action="store_true", help="--leg batched: keep the default launch shapes")
+    ap.add_argument("--no-l2-persist", action="store_true",
+                    help="do not keep the state buffers resident in L2 (access-policy window)")
     ap.add_argument("--order", choices=["morton", "input"], default="morton",
                     help="device order of the masses: spatial (grid cubes or Morton) or the caller's order")
     ap.add_argument("--exec", choices=["auto", "launch", "persistent"], default="auto",

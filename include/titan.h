@@ -116,7 +116,12 @@ typedef struct {
                                  stream.  4 to 7 return TITAN_E_UNSUPPORTED if
                                  their tables do not fit or (6, 7) the masses are
                                  not on a grid                              */
-    int32_t reserved[6];      /* zero                                              */
+    int32_t l2_persist;       /* nonzero (default): keep the two state buffers of a
+                                 CSR simulation resident in L2 (an access-policy
+                                 window on the step kernels; the context's
+                                 persisting-L2 limit is raised while any such
+                                 handle lives and restored by titan_destroy)    */
+    int32_t reserved[5];      /* zero                                              */
 } titan_params;
 
 /* Writes the defaults listed above into *p (p != NULL). */

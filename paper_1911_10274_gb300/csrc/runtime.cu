@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -112,7 +113,47 @@ void free_graphs(titan_sim *sim) {
     }
 }
 
+// The context-wide persisting-L2 limit is shared by every simulation that
+// asks for it: raised while at least one lives, restored after the last.
+std::mutex g_l2_mu;
+int g_l2_users = 0;
+size_t g_l2_prev = 0;
+
+void l2_persist_on(titan_sim *sim) {
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, sim->device) != cudaSuccess) return;
+    const size_t bytes = 2 * (size_t)sim->n_dev * sizeof(MassState);
+    if (prop.persistingL2CacheMaxSize <= 0 || bytes == 0 || bytes > (size_t)prop.accessPolicyMaxWindowSize) return;
+    std::lock_guard<std::mutex> lk(g_l2_mu);
+    size_t cur = 0;
+    if (cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize) != cudaSuccess) return;
+    const size_t want = std::min<size_t>((size_t)prop.persistingL2CacheMaxSize, std::max(cur, bytes));
+    if (want != cur && cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    if (g_l2_users++ == 0) g_l2_prev = cur;
+    sim->l2win.base_ptr = sim->state[0];
+    sim->l2win.num_bytes = bytes;
+    sim->l2win.hitRatio = std::min(1.f, (float)((double)want / (double)bytes));
+    sim->l2win.hitProp = cudaAccessPropertyPersisting;
+    sim->l2win.missProp = cudaAccessPropertyStreaming;
+    sim->l2_on = true;
+}
+
+void l2_persist_off(titan_sim *sim) {
+    if (!sim->l2_on) return;
+    sim->l2_on = false;
+    std::lock_guard<std::mutex> lk(g_l2_mu);
+    if (--g_l2_users == 0) {
+        cudaCtxResetPersistingL2Cache();
+        cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, g_l2_prev);
+        cudaGetLastError();
+    }
+}
+
 void release(titan_sim *sim) {
+    l2_persist_off(sim);
     free_graphs(sim);
     for (int b = 0; b < 2; ++b) {
         if (sim->snap_host[b]) cudaFreeHost(sim->snap_host[b]);
@@ -213,7 +254,8 @@ cudaError_t enqueue_step_io(titan_sim *sim, cudaStream_t st, const MassState *in
                              (sim->box.max_table + 1) & ~1u};
             if (sim->csr_kernel == 7)
                 return titan::launch_step_box_tma(in, out, sim->n_dev, v, h, sim->halo_w_max, sim->c, si, so, st);
-            return titan::launch_step_box(in, out, sim->n_dev, v, h, sim->c, si, so, st);
+            return titan::launch_step_box(in, out, sim->n_dev, v, h, sim->c, si, so, st,
+                                          sim->l2_on ? &sim->l2win : nullptr);
         }
         if (sim->csr_kernel == 4 || sim->csr_kernel == 5) {
             titan::HaloView h{sim->d_nslot, sim->d_own_slot, sim->d_ext_off, sim->d_ext_idx,
@@ -363,6 +405,7 @@ void titan_default_params(titan_params *p) {
     p->stream = nullptr;
     p->spin_limit = 0;
     p->graph_chunk = 0;
+    p->l2_persist = 1;
 }
 
 titan_status titan_create(const titan_masses *m, const titan_springs *sp, const titan_params *p,
@@ -498,8 +541,8 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
 
     // ---- device state
     const uint32_t nd = sim->n_dev;
-    CREATE_CK(dev_alloc(sim, &sim->state[0], nd));
-    CREATE_CK(dev_alloc(sim, &sim->state[1], nd));
+    CREATE_CK(dev_alloc(sim, &sim->state[0], 2 * (size_t)nd));   // both buffers in one range (L2 window)
+    sim->state[1] = sim->state[0] + nd;
     CREATE_CK(dev_alloc(sim, &sim->steps_dev, 2));
     CREATE_CK(dev_alloc(sim, &sim->d_err, 1));
     CREATE_CK(cudaMemsetAsync(sim->d_err, 0, sizeof(int), sim->stream));
@@ -612,6 +655,7 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
             CREATE_CK(upload(sim->d_rc, cc, sim->stream));
         }
     }
+    if (p->l2_persist && sim->accumulate == TITAN_ACCUM_CSR) l2_persist_on(sim);
     CREATE_CK(resolve_exec(sim));
     if (p->exec == TITAN_EXEC_PERSISTENT && !sim->persistent)
         return bail(fail(sim, TITAN_E_UNSUPPORTED, "exec PERSISTENT: the system does not fit one cluster's shared "

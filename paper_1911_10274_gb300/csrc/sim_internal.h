@@ -44,6 +44,8 @@ struct SimCore {
     uint32_t halo_w_max = 0;              // staged columns per slice (halo+TMA kernel)
     uint32_t halo_ahead = 0;              // L2 prefetch distance in blocks (halo kernel)
     int exec_req = TITAN_EXEC_AUTO;       // params.exec
+    bool l2_on = false;                   // the step kernels carry an L2 persistence window
+    cudaAccessPolicyWindow l2win{};       // over both state buffers (one allocation)
     bool persistent = false;              // resolved: whole chunks of steps in one cluster launch
     titan::PersistPlan plan;
     uint16_t *d_pslot = nullptr;          // persistent kernel: neighbour slot per SELL entry

@@ -896,7 +896,7 @@ cudaError_t launch_step_halo(const MassState *in, MassState *out, uint32_t n, co
 
 cudaError_t launch_step_box(const MassState *in, MassState *out, uint32_t n, const SellView &v, const BoxView &h,
                             const StepConst &c, const long long *step_in, long long *step_out,
-                            cudaStream_t stream) {
+                            cudaStream_t stream, const cudaAccessPolicyWindow *l2win) {
     const bool hc = v.c != nullptr, ha = v.act != nullptr, gr = c.ground != 0;
     const unsigned g = n ? (n + kHaloThreads - 1) / kHaloThreads : 1;
     const size_t bytes = (size_t)h.table_slots * (sizeof(float4) + sizeof(float2));
@@ -913,10 +913,23 @@ cudaError_t launch_step_box(const MassState *in, MassState *out, uint32_t n, con
                                                  (int)cudaSharedmemCarveoutMaxShared);            \
             if (e != cudaSuccess) return e;                                                      \
         }                                                                                        \
-        kern<<<g, kHaloThreads, bytes, stream>>>(in, out, n, v.slice_off,                        \
-                                                 reinterpret_cast<const uint32_t *>(h.col_off), v.kl, v.c, \
-                                                 v.act, h.own_slot, h.ext_off, h.ext_idx, h.ext_slot, \
-                                                 h.table_slots, c, step_in, step_out);           \
+        cudaLaunchConfig_t cfg = {};                                                             \
+        cfg.gridDim = dim3(g);                                                                   \
+        cfg.blockDim = dim3(kHaloThreads);                                                       \
+        cfg.dynamicSmemBytes = bytes;                                                            \
+        cfg.stream = stream;                                                                     \
+        cudaLaunchAttribute attr[1];                                                             \
+        if (l2win) {                                                                             \
+            attr[0].id = cudaLaunchAttributeAccessPolicyWindow;                                  \
+            attr[0].val.accessPolicyWindow = *l2win;                                             \
+            cfg.attrs = attr;                                                                    \
+            cfg.numAttrs = 1;                                                                    \
+        }                                                                                        \
+        cudaError_t e = cudaLaunchKernelEx(&cfg, kern, in, out, n, v.slice_off,                  \
+                                           reinterpret_cast<const uint32_t *>(h.col_off), v.kl, v.c, v.act, \
+                                           h.own_slot, h.ext_off, h.ext_idx, h.ext_slot, h.table_slots, c, \
+                                           step_in, step_out);                                   \
+        if (e != cudaSuccess) return e;                                                          \
     } while (0)
     if (hc) {
         if (ha) { if (gr) TITAN_BOX(true, true, true); else TITAN_BOX(true, true, false); }

@@ -95,10 +95,11 @@ cudaError_t launch_step_halo(const MassState *in, MassState *out, uint32_t n, co
                              const HaloView &h, const StepConst &c, const long long *step_in,
                              long long *step_out, cudaStream_t stream);
 
-// Grid-box form of the halo kernel (see step_kernels.cu).
+// Grid-box form of the halo kernel (see step_kernels.cu).  l2win (optional):
+// an L2 access-policy window attached to the launch.
 cudaError_t launch_step_box(const MassState *in, MassState *out, uint32_t n, const SellView &v, const BoxView &h,
                             const StepConst &c, const long long *step_in, long long *step_out,
-                            cudaStream_t stream);
+                            cudaStream_t stream, const cudaAccessPolicyWindow *l2win = nullptr);
 
 // Grid-box form with the stream staged into shared memory by TMA bulk copies;
 // slices wider than w_max columns read from global memory.

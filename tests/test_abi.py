@@ -48,6 +48,27 @@ def test_default_params():
     p = T.titan_default_params()
     assert p.dt == 1e-4 and list(p.gravity) == [0.0, 0.0, -9.81]
     assert p.accumulate == T.ACCUM_CSR and p.order == T.ORDER_MORTON and p.exec == T.EXEC_AUTO
+    assert p.l2_persist == 1 and list(p.reserved) == [0] * 5
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """The ctypes mirrors of the ABI structs have the header's sizes and offsets."""
+    import ctypes
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "sz.c"
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "titan.h"\n'
+                   'int main(void) { printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(titan_params), '
+                   'offsetof(titan_params, stream), offsetof(titan_params, kernel_variant), '
+                   'offsetof(titan_params, l2_persist), sizeof(titan_masses), sizeof(titan_springs)); return 0; }\n')
+    exe = tmp_path / "sz"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = [ctypes.sizeof(T.titan_params), T.titan_params.stream.offset, T.titan_params.kernel_variant.offset,
+            T.titan_params.l2_persist.offset, ctypes.sizeof(T.titan_masses), ctypes.sizeof(T.titan_springs)]
+    assert got == want
 
 
 def _arrays(sys):
