@@ -231,35 +231,54 @@ __global__ void k_loss(const float *__restrict__ y, const float *__restrict__ t,
     if (threadIdx.x == 0 && loss) *loss = part[0] / (float)B;
 }
 
-// Output layer backward: dw[c] = sum_b dy[b] H[b, c], db = sum_b dy[b];
-// dZ[b, c] = dy[b] w[c] GELU'(Z[b, c]) in BF16.
+// Column reductions over the batch run in two fixed-order stages so that the
+// whole GPU takes part: stage one sums chunks of kRowChunk rows per column
+// (grid: column blocks x row chunks), stage two adds the chunk sums in order.
+constexpr int kRowChunk = 64;
+
+// Output layer backward, stage one: per (chunk, column) the partial of
+// dw[c] = sum_b dy[b] H[b, c]; and, elementwise, dZ[b, c] = dy[b] w[c] GELU'(Z[b, c]) in BF16.
 __global__ void k_out_backward(const __nv_bfloat16 *__restrict__ H, const float *__restrict__ Z, const float *__restrict__ dy,
-                               const float *__restrict__ w, float *__restrict__ dw, float *__restrict__ db,
-                               __nv_bfloat16 *__restrict__ dZ, int B, int cols) {
+                               const float *__restrict__ w, float *__restrict__ part, __nv_bfloat16 *__restrict__ dZ,
+                               int B, int cols) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;
+    if (c >= cols) return;
+    const int b0 = k * kRowChunk, b1 = min(B, b0 + kRowChunk);
+    const float wc = w[c];
+    float s = 0.f;
+    for (int b = b0; b < b1; ++b) {
+        const size_t o = (size_t)b * cols + c;
+        const float d = dy[b];
+        s += d * __bfloat162float(H[o]);
+        dZ[o] = __float2bfloat16_rn(d * wc * gelu_grad(Z[o]));
+    }
+    part[(size_t)k * cols + c] = s;
+}
+
+// Stage one of the bias gradients: per (chunk, column) the partial column sum of a BF16 [B, cols] matrix.
+__global__ void k_col_sum_part(const __nv_bfloat16 *__restrict__ M, float *__restrict__ part, int B, int cols) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;
+    if (c >= cols) return;
+    const int b0 = k * kRowChunk, b1 = min(B, b0 + kRowChunk);
+    float s = 0.f;
+    for (int b = b0; b < b1; ++b) s += __bfloat162float(M[(size_t)b * cols + c]);
+    part[(size_t)k * cols + c] = s;
+}
+
+// Stage two: out[c] = sum over chunks, in chunk order; thread `cols` also
+// forms db = sum_b dy[b] when dy is given (the output bias).
+__global__ void k_col_sum_final(const float *__restrict__ part, int chunks, int cols, float *__restrict__ out,
+                                const float *__restrict__ dy, int B, float *__restrict__ db) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c < cols) {
         float s = 0.f;
-        for (int b = 0; b < B; ++b) {
-            const size_t o = (size_t)b * cols + c;
-            s += dy[b] * __bfloat162float(H[o]);
-            dZ[o] = __float2bfloat16_rn(dy[b] * w[c] * gelu_grad(Z[o]));
-        }
-        dw[c] = s;
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        for (int k = 0; k < chunks; ++k) s += part[(size_t)k * cols + c];
+        out[c] = s;
+    } else if (c == cols && dy) {
         float s = 0.f;
         for (int b = 0; b < B; ++b) s += dy[b];
         db[0] = s;
     }
-}
-
-// Column sums of a BF16 [B, cols] matrix (bias gradients), fixed order.
-__global__ void k_col_sum(const __nv_bfloat16 *__restrict__ M, float *__restrict__ out, int B, int cols) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= cols) return;
-    float s = 0.f;
-    for (int b = 0; b < B; ++b) s += __bfloat162float(M[(size_t)b * cols + c]);
-    out[c] = s;
 }
 
 __global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m, float *__restrict__ v,
@@ -361,6 +380,7 @@ struct titan_mlp {
     __nv_bfloat16 *dZ[3] = {nullptr, nullptr, nullptr};
     __nv_bfloat16 *xT = nullptr, *aT = nullptr, *bT = nullptr;   // transposes for weight gradients
     float *y = nullptr, *dy = nullptr;
+    float *part = nullptr;                                 // column-reduction chunk sums [B / kRowChunk][hidden]
     int *err = nullptr;
     uint64_t adam_t = 0;
     std::vector<void *> allocs;
@@ -420,6 +440,7 @@ cudaError_t ensure_batch(titan_mlp *m, uint32_t B) {
     if ((e = malloc_t(m, &m->bT, (size_t)B * m->hid)) != cudaSuccess) return e;
     if ((e = malloc_t(m, &m->y, B)) != cudaSuccess) return e;
     if ((e = malloc_t(m, &m->dy, B)) != cudaSuccess) return e;
+    if ((e = malloc_t(m, &m->part, (size_t)((B + kRowChunk - 1) / kRowChunk) * m->hid)) != cudaSuccess) return e;
     m->cap = B;
     return cudaSuccess;
 }
@@ -441,9 +462,11 @@ cudaError_t backward_pass(titan_mlp *m, const __nv_bfloat16 *x, const float *t, 
     cudaError_t e = forward_pass(m, x, B, m->y);
     if (e != cudaSuccess) return e;
     k_loss<<<1, 256, 0, m->stream>>>(m->y, t, m->dy, loss, (int)B);
-    k_out_backward<<<nblk(m->hid, 128), 128, 0, m->stream>>>(m->H[2], m->Z[2], m->dy, m->p + m->off_w4,
-                                                             m->g + m->off_w4, m->g + m->off_b4, m->dZ[2], (int)B,
-                                                             (int)m->hid);
+    const int chunks = ((int)B + kRowChunk - 1) / kRowChunk;
+    k_out_backward<<<dim3(nblk(m->hid, 128), chunks), 128, 0, m->stream>>>(m->H[2], m->Z[2], m->dy, m->p + m->off_w4,
+                                                                          m->part, m->dZ[2], (int)B, (int)m->hid);
+    k_col_sum_final<<<nblk(m->hid + 1, 128), 128, 0, m->stream>>>(m->part, chunks, (int)m->hid, m->g + m->off_w4,
+                                                                   m->dy, (int)B, m->g + m->off_b4);
     for (int l = 2; l >= 0; --l) {
         // dW_l^T (hid x in_l) = dZ_l^T (hid x B) . A_{l-1}^T (in_l x B)^T
         const uint32_t in = layer_in(m, l);
@@ -454,7 +477,9 @@ cudaError_t backward_pass(titan_mlp *m, const __nv_bfloat16 *x, const float *t, 
         EpiArgs ep{EPI_F32, (int)in, nullptr, m->g + m->off_w[l], nullptr, nullptr};
         if ((e = gemm_tn(m->bT, actT, (int)m->hid, (int)in, (int)B, ep, m->stream, m->spin_limit, m->err)) != cudaSuccess)
             return e;
-        k_col_sum<<<nblk(m->hid, 128), 128, 0, m->stream>>>(m->dZ[l], m->g + m->off_b[l], (int)B, (int)m->hid);
+        k_col_sum_part<<<dim3(nblk(m->hid, 128), chunks), 128, 0, m->stream>>>(m->dZ[l], m->part, (int)B, (int)m->hid);
+        k_col_sum_final<<<nblk(m->hid, 128), 128, 0, m->stream>>>(m->part, chunks, (int)m->hid, m->g + m->off_b[l],
+                                                                  nullptr, (int)B, nullptr);
         if (l > 0) {
             // dZ_{l-1} = (dZ_l . W_l^T) * GELU'(Z_{l-1}):  A = dZ_l (B x hid), B operand = W_l (in x hid)
             EpiArgs ep2{EPI_GELU_GRAD, (int)m->hid, nullptr, nullptr, m->dZ[l - 1], m->Z[l - 1]};
