@@ -151,20 +151,30 @@ bool build_sell(uint32_t n, uint32_t s, const uint32_t *ends, const double *pos,
     for (uint32_t i = 0; i < n; ++i) rowptr[i + 1] = rowptr[i] + deg[i];
     // half-edge = (order key, neighbour device index, spring index).  The key
     // is the direction class; on a grid it also holds the exact cell offset
-    // of the neighbour, so that equal keys mean equal offsets.
+    // of the neighbour (10 bits per component, clamped to +-511: equal keys
+    // mean equal offsets for every offset within that range; the box builder
+    // checks the columns anyway).
     struct HalfEdge { uint64_t key; uint32_t nbr, spring; };
     std::vector<HalfEdge> he(rowptr[n]);
     std::vector<uint64_t> cur(rowptr.begin(), rowptr.end() - 1);
-    // 10 bits per component, clamped: equal codes are equal offsets for every
-    // offset within +-511 cells (the box builder checks the columns anyway)
-    auto offset_code = [&](uint32_t from, uint32_t to) -> uint64_t {
-        uint64_t code = 0;
+    // On a grid the order pairs each offset with its opposite: the canonical
+    // ("positive") member p of {o, -o} ranks the pair (by its direction class,
+    // then its code), and within the pair +p precedes -p.  A row then reads
+    // +p1, -p1, +p2, -p2, ...: the order in which the cube kernel receives the
+    // -p force of an in-cube spring from the mass that computed it as +p.
+    auto paired_key = [&](uint32_t from, uint32_t to) -> uint64_t {
+        int64_t d[3];
+        for (int a = 0; a < 3; ++a) d[a] = (int64_t)cell[3 * (size_t)to + a] - (int64_t)cell[3 * (size_t)from + a];
+        const bool positive = d[2] > 0 || (d[2] == 0 && (d[1] > 0 || (d[1] == 0 && d[0] > 0)));
+        if (!positive)
+            for (int a = 0; a < 3; ++a) d[a] = -d[a];
+        uint64_t cls = 0, code = 0;
+        for (int a = 2; a >= 0; --a) cls = 3 * cls + (uint64_t)(d[a] > 0 ? 2 : (d[a] < 0 ? 0 : 1));
         for (int a = 0; a < 3; ++a) {
-            int64_t d = (int64_t)cell[3 * (size_t)to + a] - (int64_t)cell[3 * (size_t)from + a];
-            d = std::min<int64_t>(511, std::max<int64_t>(-512, d));
-            code = (code << 10) | (uint64_t)(d + 512);
+            const int64_t c = std::min<int64_t>(511, std::max<int64_t>(-512, d[a]));
+            code = (code << 10) | (uint64_t)(c + 512);
         }
-        return code;
+        return (((cls << 30) | code) << 1) | (positive ? 0u : 1u);
     };
     for (uint32_t q = 0; q < s; ++q) {
         const uint32_t ci = ends[2 * (size_t)q], cj = ends[2 * (size_t)q + 1];
@@ -172,8 +182,8 @@ bool build_sell(uint32_t n, uint32_t s, const uint32_t *ends, const double *pos,
         const uint32_t kab = direction_class(pos + 3 * (size_t)ci, pos + 3 * (size_t)cj);
         uint64_t ka = (uint64_t)kab << 32, kb = (uint64_t)(26u - kab) << 32;   // opposite direction
         if (cell) {
-            ka |= offset_code(a, b);
-            kb |= offset_code(b, a);
+            ka = paired_key(a, b);
+            kb = paired_key(b, a);
         }
         he[cur[a]++] = {ka, b, q};
         he[cur[b]++] = {kb, a, q};
