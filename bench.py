@@ -34,11 +34,12 @@ METRIC = "spring updates/s"
 # the step kernel a Sim resolved to (titan_csr_kernel), and its description
 CSR_KERNEL_NAMES = {0: "k_springs_atomic+k_masses_atomic", 1: "k_step_sell", 2: "k_step_sell_staged",
                     3: "k_step_sell_pf", 4: "k_step_halo", 5: "k_step_halo_tma", 6: "k_step_box",
-                    7: "k_step_box_tma"}
+                    7: "k_step_box_tma", 8: "k_step_cube"}
 CSR_KERNELS = {0: "atomic scatter", 1: "direct-loads", 2: "tma-staged", 3: "bulk-l2-prefetch",
                4: "halo (coloured neighbourhood table in shared memory)", 5: "halo+tma",
                6: "grid box (box table in shared memory, no neighbour index in the stream)",
-               7: "grid box, stream staged in shared memory by TMA bulk copies"}
+               7: "grid box, stream staged in shared memory by TMA bulk copies",
+               8: "cube (springs inside a 256-mass cube read and evaluated once)"}
 UNIT = "spring_updates/s"
 L2_BYTES = 126 * 1024 * 1024
 
@@ -220,7 +221,7 @@ def auto_kernel(args):
         return 0
     if args.kernel_variant:
         return args.kernel_variant
-    return 4 if args.workload == "mesh2m" else 6
+    return 4 if args.workload == "mesh2m" else 8
 
 
 def config_for(args, system, resolved=None):
@@ -508,7 +509,7 @@ def main():
                     help="device order of the masses: spatial (grid cubes or Morton) or the caller's order")
     ap.add_argument("--exec", choices=["auto", "launch", "persistent"], default="auto",
                     help="step loop: persistent cluster kernel (small systems), per-step launches, or auto")
-    ap.add_argument("--kernel-variant", type=int, default=0, help="CSR kernel: 0 auto, 1 direct loads, 2 TMA-staged, 3 bulk L2 prefetch, 4 halo, 5 halo+TMA, 6 grid box, 7 grid box+TMA")
+    ap.add_argument("--kernel-variant", type=int, default=0, help="CSR kernel: 0 auto, 1 direct loads, 2 TMA-staged, 3 bulk L2 prefetch, 4 halo, 5 halo+TMA, 6 grid box, 7 grid box+TMA, 8 cube")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -106,16 +106,19 @@ typedef struct {
     void *stream;             /* cudaStream_t for the step loop; NULL: own stream  */
     uint64_t spin_limit;      /* bound on device spin-wait iterations; 0: default  */
     int32_t graph_chunk;      /* steps per captured CUDA graph; 0: 64; < 0: none   */
-    int32_t kernel_variant;   /* CSR kernel: 0 auto (6 for masses on a grid when
-                                 it fits, else 4 when it fits, else 3),
+    int32_t kernel_variant;   /* CSR kernel: 0 auto (8 for 26-neighbour lattices,
+                                 else 6 for masses on a grid when it fits, else 4
+                                 when it fits, else 3),
                                  1 direct loads, 2 TMA-staged stream, 3 bulk L2
                                  prefetch, 4 halo tables in shared memory, 5 halo +
                                  TMA-staged stream, 6 grid-box tables (masses on a
                                  cubic grid, at most one per cell; no neighbour
                                  index in the stream), 7 grid box + TMA-staged
-                                 stream.  4 to 7 return TITAN_E_UNSUPPORTED if
-                                 their tables do not fit or (6, 7) the masses are
-                                 not on a grid                              */
+                                 stream, 8 cube (springs inside a 256-mass cube
+                                 read and evaluated once; 26-neighbour springs on
+                                 a grid, at most one per mass and offset).  4 to 8
+                                 return TITAN_E_UNSUPPORTED if their tables do not
+                                 fit or their layout conditions fail        */
     int32_t l2_persist;       /* nonzero (default): keep the two state buffers of a
                                  CSR simulation resident in L2 (an access-policy
                                  window on the step kernels; the context's
@@ -256,7 +259,7 @@ uint64_t titan_steps(const titan_sim *sim);
  * rebuild; an edit that no longer fits falls back to launches. */
 int32_t titan_exec_mode(const titan_sim *sim);
 
-/* The step kernel titan_create resolved params.kernel_variant to: 1..7 as
+/* The step kernel titan_create resolved params.kernel_variant to: 1..8 as
  * listed for kernel_variant (never 0), 0 for atomic accumulation, -1 for a
  * NULL handle.  The resolution is redone when added masses or springs force a
  * layout rebuild. */

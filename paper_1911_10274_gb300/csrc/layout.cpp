@@ -410,6 +410,7 @@ bool build_box(uint32_t n, const SellHost &sell, const std::vector<int32_t> &cel
     out.ext_off.assign(n_blocks + 1, 0);
     out.ext_idx.clear();
     out.ext_slot.clear();
+    out.dims.assign(2 * (size_t)n_blocks, 0);
     out.max_table = 0;
     const int32_t *C = cell.data();
     std::vector<uint32_t> seen;     // external masses of the current block
@@ -440,6 +441,8 @@ bool build_box(uint32_t n, const SellHost &sell, const std::vector<int32_t> &cel
         const int64_t slots = dim[0] * dim[1] * dim[2];
         if (slots > (int64_t)max_slots || slots > 32767) return false;
         out.max_table = std::max<uint32_t>(out.max_table, (uint32_t)slots);
+        out.dims[2 * (size_t)b] = (uint32_t)dim[0];
+        out.dims[2 * (size_t)b + 1] = (uint32_t)dim[1];
         auto slot = [&](uint32_t m) -> int64_t {
             return (C[3 * (size_t)m] - lo[0]) + dim[0] * ((C[3 * (size_t)m + 1] - lo[1]) + dim[1] * (C[3 * (size_t)m + 2] - lo[2]));
         };
@@ -482,6 +485,100 @@ bool build_box(uint32_t n, const SellHost &sell, const std::vector<int32_t> &cel
         }
         out.ext_off[b + 1] = (uint32_t)out.ext_idx.size();
     }
+    return true;
+}
+
+bool build_cube(uint32_t n, uint32_t s, const uint32_t *ends, const std::vector<uint32_t> &dev_of,
+                const SellHost &sell, const std::vector<int32_t> &cell, const std::vector<uint32_t> &caller_of_dev,
+                const BoxHost &box, CubeHost &out) {
+    constexpr uint32_t P = kCubePasses, W = kHaloBlock / 32;
+    if (n % kHaloBlock || cell.size() != 3 * (size_t)n || caller_of_dev.size() != n || box.own_slot.size() != n)
+        return false;
+    const uint32_t n_cubes = n / kHaloBlock;
+    auto pass_of = [&](int dx, int dy, int dz, int &sign) -> int {
+        for (uint32_t j = 0; j < P; ++j) {
+            if (kCubeDirs[j][0] == dx && kCubeDirs[j][1] == dy && kCubeDirs[j][2] == dz) { sign = +1; return (int)j; }
+            if (kCubeDirs[j][0] == -dx && kCubeDirs[j][1] == -dy && kCubeDirs[j][2] == -dz) { sign = -1; return (int)j; }
+        }
+        return -1;
+    };
+    const int32_t *C = cell.data();
+    out.base.assign(n_cubes + 1, 0);
+    out.meta.assign((size_t)n_cubes * P * W * 4, 0);
+    out.spring.clear();
+    out.pos_of_end.assign(2 * (size_t)s, UINT32_MAX);
+    // per spring end: the end index (0 = ends[2q]) of device mass m
+    auto end_of = [&](uint32_t q, uint32_t m) -> int { return dev_of[ends[2 * (size_t)q]] == m ? 0 : 1; };
+    std::vector<uint32_t> plus(P * kHaloBlock), minus(P * kHaloBlock);
+    for (uint32_t b = 0; b < n_cubes; ++b) {
+        const uint32_t m0 = b * kHaloBlock;
+        std::fill(plus.begin(), plus.end(), UINT32_MAX);
+        std::fill(minus.begin(), minus.end(), UINT32_MAX);
+        // every spring of the cube's masses, by pass and sign
+        for (uint32_t sl = m0 / 32; sl < (m0 + kHaloBlock) / 32; ++sl)
+            for (uint32_t e = sell.slice_off[sl]; e < sell.slice_off[sl + 1]; ++e) {
+                const uint32_t q = sell.spring[e];
+                if (q == UINT32_MAX) continue;
+                const uint32_t m = sl * 32 + (e - sell.slice_off[sl]) % 32, j = sell.nbr[e];
+                const int dx = C[3 * (size_t)j] - C[3 * (size_t)m], dy = C[3 * (size_t)j + 1] - C[3 * (size_t)m + 1],
+                          dz = C[3 * (size_t)j + 2] - C[3 * (size_t)m + 2];
+                int sign = 0;
+                const int pj = pass_of(dx, dy, dz, sign);
+                if (pj < 0) return false;                                   // not a 26-neighbour offset
+                uint32_t &slot = (sign > 0 ? plus : minus)[(size_t)pj * kHaloBlock + (m - m0)];
+                if (slot != UINT32_MAX) return false;                       // two springs, one offset
+                slot = q;
+            }
+        const uint32_t start = (uint32_t)out.spring.size();
+        out.base[b] = start;
+        for (uint32_t pj = 0; pj < P; ++pj)
+            for (uint32_t t = 0; t < kHaloBlock; ++t) {
+                const uint32_t q = plus[(size_t)pj * kHaloBlock + t];
+                if (q != UINT32_MAX) out.pos_of_end[2 * (size_t)q + end_of(q, m0 + t)] = (uint32_t)out.spring.size();
+                out.spring.push_back(q);
+            }
+        const uint32_t ext_start = (uint32_t)out.spring.size();
+        for (uint32_t pj = 0; pj < P; ++pj) {
+            const int dx = kCubeDirs[pj][0], dy = kCubeDirs[pj][1], dz = kCubeDirs[pj][2];
+            // box slot offset of +p in this cube's table
+            const int32_t X = (int32_t)box.dims[2 * (size_t)b], Y = (int32_t)box.dims[2 * (size_t)b + 1];
+            const int32_t off = dx + X * dy + X * Y * dz;
+            for (uint32_t w = 0; w < W; ++w) {
+                uint32_t recv = 0, ext = 0;
+                const uint32_t ext_base = (uint32_t)out.spring.size() - ext_start;
+                for (uint32_t l = 0; l < 32; ++l) {
+                    const uint32_t t = w * 32 + l, m = m0 + t;
+                    const uint32_t qp = plus[(size_t)pj * kHaloBlock + t], qm = minus[(size_t)pj * kHaloBlock + t];
+                    if (qp != UINT32_MAX) {
+                        const uint32_t j = dev_of[ends[2 * (size_t)qp + 1 - end_of(qp, m)]];
+                        if (j >= m0 && j < m0 + kHaloBlock &&
+                            (int32_t)box.own_slot[j] - (int32_t)box.own_slot[m] != off)
+                            return false;
+                    }
+                    if (qm == UINT32_MAX) continue;
+                    const uint32_t j = dev_of[ends[2 * (size_t)qm + 1 - end_of(qm, m)]];   // the -p partner
+                    if (j >= m0 && j < m0 + kHaloBlock) {
+                        // in the cube: its +p spring must be this one
+                        if (plus[(size_t)pj * kHaloBlock + (j - m0)] != qm) return false;
+                        recv |= 1u << l;
+                    } else {
+                        ext |= 1u << l;
+                        out.pos_of_end[2 * (size_t)qm + end_of(qm, m)] = (uint32_t)out.spring.size();
+                        out.spring.push_back(qm);
+                    }
+                }
+                uint32_t *mt = &out.meta[(((size_t)b * P + pj) * W + w) * 4];
+                mt[0] = recv;
+                mt[1] = ext;
+                mt[2] = ext_base;
+                mt[3] = (uint32_t)(uint16_t)(int16_t)off;
+            }
+        }
+        // every cube's region starts on a 128-byte boundary (its plus rows are 2 KB each)
+        while (out.spring.size() % 16) out.spring.push_back(UINT32_MAX);
+    }
+    out.base[n_cubes] = (uint32_t)out.spring.size();
+    out.entries = (uint32_t)out.spring.size();
     return true;
 }
 

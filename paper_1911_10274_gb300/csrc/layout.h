@@ -82,6 +82,7 @@ struct BoxHost {
     std::vector<uint32_t> ext_off;       // [n_blocks + 1]
     std::vector<uint32_t> ext_idx;       // device index of each external table entry
     std::vector<uint16_t> ext_slot;      // its slot
+    std::vector<uint32_t> dims;          // [n_blocks][2] row length X and rows per layer Y of each box
     uint32_t max_table = 0;              // largest box (slots) over all blocks
 };
 
@@ -93,6 +94,38 @@ struct BoxHost {
 constexpr uint16_t kBoxHole = 0xFFFF;
 bool build_box(uint32_t n, const SellHost &sell, const std::vector<int32_t> &cell,
                const std::vector<uint32_t> &caller_of_dev, uint32_t max_slots, BoxHost &out);
+
+// Cube-pair layout (the cube kernel; masses in grid order, 26-neighbourhood
+// springs, at most one spring per mass and offset).  A block of 256 device
+// masses is one cube of 8 x 8 x 4 cells; its step runs 13 passes, one per
+// canonical direction p (kCubeDirs, the paired row order).  In pass j every
+// mass evaluates its +p spring from the dense "plus" stream and publishes the
+// force in shared memory; a mass whose -p partner is in the cube takes that
+// force (negated) instead of evaluating the spring again, and one whose -p
+// partner is outside reads the spring from the cube's compact "ext" stream.
+// Springs inside a cube are thus read and evaluated once, and each mass still
+// adds its forces in its row order (+p1, -p1, +p2, ...), so the result is
+// bit-identical to the other CSR kernels.
+constexpr int kCubeDirs[13][3] = {{1, 0, 0},  {-1, 1, 0}, {0, 1, 0},  {1, 1, 0},  {-1, -1, 1}, {0, -1, 1}, {1, -1, 1},
+                                  {-1, 0, 1}, {0, 0, 1},  {1, 0, 1},  {-1, 1, 1}, {0, 1, 1},  {1, 1, 1}};
+constexpr uint32_t kCubePasses = 13;
+
+struct CubeHost {
+    std::vector<uint32_t> base;       // [n_cubes + 1] first stream entry of each cube (plus, then ext)
+    std::vector<uint32_t> meta;       // [n_cubes][13][8 warps][4]: recv mask, ext mask, ext base (from
+                                      // the cube's ext start), box slot offset of +p (int16 in 32 bits)
+    std::vector<uint32_t> spring;     // [entries] caller spring of each stream entry (UINT32_MAX: padding)
+    std::vector<uint32_t> pos_of_end; // [2 S] stream entry of each spring end (UINT32_MAX: received)
+    uint32_t entries = 0;
+};
+
+// Returns false unless every spring joins two masses of the grid at one of
+// the 26 neighbour offsets, no mass has two springs with the same offset, and
+// the blocks are cubes (grid order).  Needs the SELL (paired grid order) and
+// the box tables of the same layout.
+bool build_cube(uint32_t n, uint32_t s, const uint32_t *ends, const std::vector<uint32_t> &dev_of,
+                const SellHost &sell, const std::vector<int32_t> &cell, const std::vector<uint32_t> &caller_of_dev,
+                const BoxHost &box, CubeHost &out);
 
 struct RecordsHost {
     std::vector<uint32_t> order;            // [S] record r holds caller spring order[r]

@@ -186,7 +186,7 @@ titan_status validate(const titan_masses *m, const titan_springs *sp, const tita
     if (p->exec < TITAN_EXEC_AUTO || p->exec > TITAN_EXEC_PERSISTENT)
         return fail(nullptr, TITAN_E_INVALID, "params.exec out of range");
     if (p->device < 0) return fail(nullptr, TITAN_E_INVALID, "params.device must be >= 0");
-    if (p->kernel_variant < 0 || p->kernel_variant > 7) return fail(nullptr, TITAN_E_INVALID, "params.kernel_variant must be 0..7");
+    if (p->kernel_variant < 0 || p->kernel_variant > 8) return fail(nullptr, TITAN_E_INVALID, "params.kernel_variant must be 0..8");
     for (uint64_t i = 0; i < m->n; ++i) {
         for (int a = 0; a < 3; ++a) {
             if (!finite(m->pos[3 * i + a])) return fail(nullptr, TITAN_E_INVALID, "masses.pos has a non-finite value at mass " + std::to_string(i));
@@ -233,7 +233,17 @@ cudaError_t upload_actuation(titan_sim *sim) {
             const uint32_t q = sim->sell.spring[e2];
             if (q != UINT32_MAX) a[e2] = make_float2(sim->act_amp[q], sim->act_phase[q]);
         }
-        return upload(sim->d_act, a, sim->stream);
+        if ((e = upload(sim->d_act, a, sim->stream)) != cudaSuccess) return e;
+        if (sim->csr_kernel == 8) {
+            if (!sim->d_cact && (e = dev_alloc(sim, &sim->d_cact, sim->cube.entries)) != cudaSuccess) return e;
+            std::vector<float2> ca(sim->cube.entries, make_float2(0.f, 0.f));
+            for (uint32_t e2 = 0; e2 < sim->cube.entries; ++e2) {
+                const uint32_t q = sim->cube.spring[e2];
+                if (q != UINT32_MAX) ca[e2] = make_float2(sim->act_amp[q], sim->act_phase[q]);
+            }
+            if ((e = upload(sim->d_cact, ca, sim->stream)) != cudaSuccess) return e;
+        }
+        return cudaSuccess;
     }
     if (!sim->d_ract && (e = dev_alloc(sim, &sim->d_ract, sim->s)) != cudaSuccess) return e;
     std::vector<float2> a(sim->s);
@@ -249,9 +259,15 @@ cudaError_t enqueue_step_io(titan_sim *sim, cudaStream_t st, const MassState *in
     if (sim->accumulate == TITAN_ACCUM_CSR) {
         titan::SellView v{sim->d_slice_off, sim->d_nbr, sim->d_kl, sim->has_c ? sim->d_c : nullptr,
                           sim->has_act ? sim->d_act : nullptr, 0, sim->spin_limit, sim->d_err};
-        if (sim->csr_kernel == 6 || sim->csr_kernel == 7) {
+        if (sim->csr_kernel >= 6 && sim->csr_kernel <= 8) {
             titan::BoxView h{sim->d_col_off, sim->d_own_slot, sim->d_ext_off, sim->d_ext_idx, sim->d_ext_slot,
                              (sim->box.max_table + 1) & ~1u};
+            if (sim->csr_kernel == 8) {
+                titan::CubeView cv{sim->d_cube_base, sim->d_cube_meta, sim->d_ckl, sim->has_c ? sim->d_cc : nullptr,
+                                   sim->has_act ? sim->d_cact : nullptr};
+                return titan::launch_step_cube(in, out, sim->n_dev, cv, h, sim->c, si, so, st,
+                                               sim->l2_on ? &sim->l2win : nullptr);
+            }
             if (sim->csr_kernel == 7)
                 return titan::launch_step_box_tma(in, out, sim->n_dev, v, h, sim->halo_w_max, sim->c, si, so, st);
             return titan::launch_step_box(in, out, sim->n_dev, v, h, sim->c, si, so, st,
@@ -561,13 +577,21 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
                                sim->grid_order ? cells.data() : nullptr))
             return bail(fail(sim, TITAN_E_UNSUPPORTED, "padded incidence exceeds 2^32 entries"));
         const int want = p->kernel_variant;
-        sim->csr_kernel = want == 0 ? (sim->grid_order ? 6 : 4) : want;
-        if ((sim->csr_kernel == 6 || sim->csr_kernel == 7) &&
+        sim->csr_kernel = want == 0 ? (sim->grid_order ? 8 : 4) : want;
+        if (sim->csr_kernel >= 6 && sim->csr_kernel <= 8 &&
             !(sim->grid_order && titan::build_box(nd, sim->sell, cells, sim->caller_of_dev, kHaloMaxSlots, sim->box))) {
-            if (want == 6 || want == 7)
+            if (want >= 6)
                 return bail(fail(sim, TITAN_E_UNSUPPORTED, "the grid box kernel needs masses on a grid whose "
                                                            "blocks' boxes fit " + std::to_string(kHaloMaxSlots) + " slots"));
             sim->csr_kernel = 4;
+        }
+        if (sim->csr_kernel == 8 &&
+            !titan::build_cube(nd, s, sp->ends, sim->dev_of_caller, sim->sell, cells, sim->caller_of_dev, sim->box,
+                               sim->cube)) {
+            if (want == 8)
+                return bail(fail(sim, TITAN_E_UNSUPPORTED, "the cube kernel needs 26-neighbour springs on a grid, "
+                                                           "at most one per mass and offset"));
+            sim->csr_kernel = 6;
         }
         if (sim->csr_kernel == 7 && !choose_box_width(sim)) {
             if (want == 7)
@@ -600,7 +624,7 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
         CREATE_CK(dev_alloc(sim, &sim->d_kl, E));
         CREATE_CK(upload(sim->d_slice_off, sim->sell.slice_off, sim->stream));
         CREATE_CK(upload(sim->d_kl, kl, sim->stream));
-        if (sim->csr_kernel == 6 || sim->csr_kernel == 7) {
+        if (sim->csr_kernel >= 6 && sim->csr_kernel <= 8) {
             const titan::BoxHost &h = sim->box;
             CREATE_CK(dev_alloc(sim, &sim->d_col_off, h.col_off.size()));
             CREATE_CK(dev_alloc(sim, &sim->d_own_slot, nd));
@@ -612,6 +636,31 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
             CREATE_CK(upload(sim->d_ext_off, h.ext_off, sim->stream));
             CREATE_CK(upload(sim->d_ext_idx, h.ext_idx, sim->stream));
             CREATE_CK(upload(sim->d_ext_slot, h.ext_slot, sim->stream));
+            if (sim->csr_kernel == 8) {
+                const titan::CubeHost &cu = sim->cube;
+                std::vector<float2> ckl(cu.entries, make_float2(0.f, 0.f));
+                std::vector<float> c2;
+                if (sim->has_c) c2.assign(cu.entries, 0.f);
+                for (uint32_t e = 0; e < cu.entries; ++e) {
+                    const uint32_t q = cu.spring[e];
+                    if (q == UINT32_MAX) continue;
+                    ckl[e] = make_float2(sim->k[q], sim->rest[q]);
+                    if (sim->has_c) c2[e] = sim->damp[q];
+                }
+                std::vector<uint4> meta(cu.meta.size() / 4);
+                memcpy(meta.data(), cu.meta.data(), cu.meta.size() * sizeof(uint32_t));
+                CREATE_CK(dev_alloc(sim, &sim->d_cube_base, cu.base.size()));
+                CREATE_CK(dev_alloc(sim, &sim->d_cube_meta, meta.size()));
+                CREATE_CK(dev_alloc(sim, &sim->d_ckl, ckl.size()));
+                CREATE_CK(upload(sim->d_cube_base, cu.base, sim->stream));
+                CREATE_CK(upload(sim->d_cube_meta, meta, sim->stream));
+                CREATE_CK(upload(sim->d_ckl, ckl, sim->stream));
+                if (sim->has_c) {
+                    CREATE_CK(dev_alloc(sim, &sim->d_cc, c2.size()));
+                    CREATE_CK(upload(sim->d_cc, c2, sim->stream));
+                }
+                CREATE_CK(cudaStreamSynchronize(sim->stream));     // the host vectors go out of scope
+            }
         } else if (sim->csr_kernel == 4 || sim->csr_kernel == 5) {
             sim->halo_ahead = 0;    // each warp prefetches its own slice
             const titan::HaloHost &h = sim->halo;
@@ -921,6 +970,13 @@ cudaError_t enable_per_spring_damping(titan_sim *sim) {
             if (sim->sell.spring[e2] != UINT32_MAX) cc[e2] = sim->damp[sim->sell.spring[e2]];
         if (!sim->d_c && (e = dev_alloc(sim, &sim->d_c, sim->sell.entries)) != cudaSuccess) return e;
         if ((e = upload(sim->d_c, cc, sim->stream)) != cudaSuccess) return e;
+        if (sim->csr_kernel == 8) {
+            std::vector<float> c2(sim->cube.entries, 0.f);
+            for (uint32_t e2 = 0; e2 < sim->cube.entries; ++e2)
+                if (sim->cube.spring[e2] != UINT32_MAX) c2[e2] = sim->damp[sim->cube.spring[e2]];
+            if (!sim->d_cc && (e = dev_alloc(sim, &sim->d_cc, sim->cube.entries)) != cudaSuccess) return e;
+            if ((e = upload(sim->d_cc, c2, sim->stream)) != cudaSuccess) return e;
+        }
     } else {
         std::vector<float> cc(sim->s);
         for (uint32_t r = 0; r < sim->s; ++r) cc[r] = sim->damp[sim->rec.order[r]];
@@ -936,6 +992,7 @@ cudaError_t enable_per_spring_damping(titan_sim *sim) {
 // Pushes the current host parameters of device springs `ids` into the device layout.
 cudaError_t push_springs(titan_sim *sim, const std::vector<uint32_t> &ids, bool damping, bool actuation) {
     std::vector<uint32_t> wi, wv, ci, cv, ai, av;
+    std::vector<uint32_t> xwi, xwv, xci, xcv, xai, xav;      // the cube stream (cube kernel)
     for (uint32_t q : ids) {
         const float kf = sim->k[q], lf = sim->rest[q];
         if (sim->accumulate == TITAN_ACCUM_CSR) {
@@ -945,6 +1002,14 @@ cudaError_t push_springs(titan_sim *sim, const std::vector<uint32_t> &ids, bool 
                 wi.push_back(2 * e + 1); wv.push_back(fbits(lf));
                 if (damping) { ci.push_back(e); cv.push_back(fbits(sim->damp[q])); }
                 if (actuation) { ai.push_back(2 * e); av.push_back(fbits(sim->act_amp[q])); }
+                if (sim->csr_kernel == 8) {
+                    const uint32_t x = sim->cube.pos_of_end[2 * (size_t)q + end];
+                    if (x == UINT32_MAX) continue;                  // this end receives the force
+                    xwi.push_back(2 * x); xwv.push_back(fbits(kf));
+                    xwi.push_back(2 * x + 1); xwv.push_back(fbits(lf));
+                    if (damping) { xci.push_back(x); xcv.push_back(fbits(sim->damp[q])); }
+                    if (actuation) { xai.push_back(2 * x); xav.push_back(fbits(sim->act_amp[q])); }
+                }
             }
         } else {
             const uint32_t r = sim->rec.slot_of_spring[q];
@@ -961,6 +1026,11 @@ cudaError_t push_springs(titan_sim *sim, const std::vector<uint32_t> &ids, bool 
         return e;
     if (actuation && (e = patch_words(sim, sim->accumulate == TITAN_ACCUM_CSR ? (void *)sim->d_act : (void *)sim->d_ract, ai, av)) != cudaSuccess)
         return e;
+    if (!xwi.empty()) {
+        if ((e = patch_words(sim, sim->d_ckl, xwi, xwv)) != cudaSuccess) return e;
+        if (damping && (e = patch_words(sim, sim->d_cc, xci, xcv)) != cudaSuccess) return e;
+        if (actuation && (e = patch_words(sim, sim->d_cact, xai, xav)) != cudaSuccess) return e;
+    }
     return cudaSuccess;
 }
 

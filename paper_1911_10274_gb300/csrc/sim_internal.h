@@ -39,8 +39,10 @@ struct SimCore {
     titan::SellHost sell;
     titan::HaloHost halo;
     titan::BoxHost box;
+    titan::CubeHost cube;
     titan::RecordsHost rec;
-    int csr_kernel = 0;                   // resolved: 1 direct, 2 smem-staged, 3 bulk-prefetch, 4 halo, 5 halo+TMA, 6 grid box
+    int csr_kernel = 0;                   // resolved: 1 direct, 2 smem-staged, 3 bulk-prefetch, 4 halo, 5 halo+TMA,
+                                          // 6 grid box, 7 grid box+TMA, 8 cube
     uint32_t halo_w_max = 0;              // staged columns per slice (halo+TMA kernel)
     uint32_t halo_ahead = 0;              // L2 prefetch distance in blocks (halo kernel)
     int exec_req = TITAN_EXEC_AUTO;       // params.exec
@@ -62,6 +64,10 @@ struct SimCore {
     uint16_t *d_nslot = nullptr, *d_own_slot = nullptr, *d_ext_slot = nullptr;
     uint32_t *d_ext_off = nullptr, *d_ext_idx = nullptr;   // halo or box tables (whichever kernel runs)
     int16_t *d_col_off = nullptr;         // box kernel: slot offset per SELL column
+    uint32_t *d_cube_base = nullptr;      // cube kernel: stream start of each cube
+    uint4 *d_cube_meta = nullptr;         //              per (cube, pass, warp) masks, ext base, offset
+    float2 *d_ckl = nullptr, *d_cact = nullptr;   //      cube stream {k, L0}, actuation
+    float *d_cc = nullptr;                //              cube stream damping
     float2 *d_kl = nullptr, *d_act = nullptr;
     float *d_c = nullptr;
 

@@ -76,6 +76,14 @@ struct BoxView {
     uint32_t table_slots;        // slots per box (shared memory = 24 B each)
 };
 
+struct CubeView {
+    const uint32_t *base;        // [n_cubes + 1] first stream entry of each cube
+    const uint4 *meta;           // [n_cubes][13][8]: recv mask, ext mask, ext base, +p slot offset
+    const float2 *kl;            // cube stream {k, L0}
+    const float *c;              // or nullptr (uniform c)
+    const float2 *act;           // or nullptr (no actuation)
+};
+
 struct AtomicView {
     const uint4 *rec;            // [S] {i, j, bits(k), bits(L0)}
     const float *c;              // [S] or nullptr
@@ -100,6 +108,12 @@ cudaError_t launch_step_halo(const MassState *in, MassState *out, uint32_t n, co
 cudaError_t launch_step_box(const MassState *in, MassState *out, uint32_t n, const SellView &v, const BoxView &h,
                             const StepConst &c, const long long *step_in, long long *step_out,
                             cudaStream_t stream, const cudaAccessPolicyWindow *l2win = nullptr);
+
+// Cube form (26-neighbourhood lattices): springs inside a block's cube read
+// and evaluated once (see step_kernels.cu).  n a multiple of 256.
+cudaError_t launch_step_cube(const MassState *in, MassState *out, uint32_t n, const CubeView &v, const BoxView &h,
+                             const StepConst &c, const long long *step_in, long long *step_out, cudaStream_t stream,
+                             const cudaAccessPolicyWindow *l2win = nullptr);
 
 // Grid-box form with the stream staged into shared memory by TMA bulk copies;
 // slices wider than w_max columns read from global memory.

@@ -483,7 +483,7 @@ class Sim:
 
     @property
     def csr_kernel(self) -> int:
-        """The step kernel in use: 1..7 (see titan_params.kernel_variant), 0 atomic."""
+        """The step kernel in use: 1..8 (see titan_params.kernel_variant), 0 atomic."""
         return int(load().titan_csr_kernel(self.handle))
 
     def close(self) -> None:

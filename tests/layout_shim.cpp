@@ -15,6 +15,8 @@ struct Built {
     titan::SellHost sell;
     titan::HaloHost halo;
     titan::BoxHost box;
+    titan::CubeHost cube;
+    int cube_ok = 0;
     titan::PersistPlan plan;
     std::vector<uint16_t> pslot;
     std::vector<uint32_t> phalo;
@@ -43,6 +45,8 @@ int shim_build(const double *pos, uint32_t n, const uint32_t *ends, uint32_t s, 
     if (!titan::build_sell(nd, s, ends, pos, g.dev_of_caller, g.sell, g.grid ? g.cell.data() : nullptr)) return 1;
     g.halo_ok = titan::build_halo(nd, g.sell, max_slots, g.grid != 0, g.halo) ? 1 : 0;
     g.box_ok = g.grid && titan::build_box(nd, g.sell, g.cell, g.caller_of_dev, max_slots, g.box) ? 1 : 0;
+    g.cube_ok = g.box_ok && titan::build_cube(nd, s, ends, g.dev_of_caller, g.sell, g.cell, g.caller_of_dev, g.box,
+                                              g.cube) ? 1 : 0;
     return 0;
 }
 
@@ -67,7 +71,8 @@ uint64_t shim_plan_scalar(int which) {
     }
 }
 
-// Scalars: 0 n_dev, 1 entries, 2 grid, 3 box_ok, 4 halo_ok, 5 box max_table, 6 halo max_table.
+// Scalars: 0 n_dev, 1 entries, 2 grid, 3 box_ok, 4 halo_ok, 5 box max_table, 6 halo max_table,
+// 7 cube_ok, 8 cube stream entries.
 uint64_t shim_scalar(int which) {
     switch (which) {
         case 0: return g.caller_of_dev.size();
@@ -77,6 +82,8 @@ uint64_t shim_scalar(int which) {
         case 4: return (uint64_t)g.halo_ok;
         case 5: return g.box.max_table;
         case 6: return g.halo.max_table;
+        case 7: return (uint64_t)g.cube_ok;
+        case 8: return g.cube.entries;
         default: return 0;
     }
 }
@@ -95,6 +102,11 @@ uint64_t shim_len(const char *name) {
     if (k == "box_ext_off") return g.box.ext_off.size();
     if (k == "box_ext_idx") return g.box.ext_idx.size();
     if (k == "box_ext_slot") return g.box.ext_slot.size();
+    if (k == "cube_base") return g.cube.base.size();
+    if (k == "cube_meta") return g.cube.meta.size();
+    if (k == "cube_spring") return g.cube.spring.size();
+    if (k == "cube_pos_of_end") return g.cube.pos_of_end.size();
+    if (k == "box_dims") return g.box.dims.size();
     if (k == "pslot") return g.pslot.size();
     if (k == "phalo") return g.phalo.size();
     return 0;
@@ -113,6 +125,11 @@ void shim_get(const char *name, void *dst) {
     if (k == "box_ext_off") copy_out(g.box.ext_off, dst);
     if (k == "box_ext_idx") copy_out(g.box.ext_idx, dst);
     if (k == "box_ext_slot") copy_out(g.box.ext_slot, dst);
+    if (k == "cube_base") copy_out(g.cube.base, dst);
+    if (k == "cube_meta") copy_out(g.cube.meta, dst);
+    if (k == "cube_spring") copy_out(g.cube.spring, dst);
+    if (k == "cube_pos_of_end") copy_out(g.cube.pos_of_end, dst);
+    if (k == "box_dims") copy_out(g.box.dims, dst);
     if (k == "pslot") copy_out(g.pslot, dst);
     if (k == "phalo") copy_out(g.phalo, dst);
 }

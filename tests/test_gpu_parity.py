@@ -46,11 +46,12 @@ MODES = [dict(accumulate=T.ACCUM_CSR), dict(accumulate=T.ACCUM_ATOMIC),
          dict(accumulate=T.ACCUM_CSR, kernel_variant=5, **LAUNCH),
          dict(accumulate=T.ACCUM_CSR, kernel_variant=6, **LAUNCH),
          dict(accumulate=T.ACCUM_CSR, kernel_variant=7, **LAUNCH),
+         dict(accumulate=T.ACCUM_CSR, kernel_variant=8, **LAUNCH),
          dict(accumulate=T.ACCUM_CSR, exec_mode=T.EXEC_PERSISTENT),
          dict(accumulate=T.ACCUM_CSR, order=T.ORDER_INPUT),
          dict(accumulate=T.ACCUM_CSR, graph_chunk=-1, **LAUNCH)]
 MODE_IDS = ["csr", "atomic", "csr-direct-loads", "csr-tma-staged", "csr-bulk-prefetch", "csr-halo",
-            "csr-halo-tma", "csr-grid-box", "csr-grid-box-tma", "csr-persistent", "csr-input-order", "csr-no-graph"]
+            "csr-halo-tma", "csr-grid-box", "csr-grid-box-tma", "csr-cube", "csr-persistent", "csr-input-order", "csr-no-graph"]
 
 
 @pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
@@ -140,7 +141,7 @@ def test_lattice_with_holes_in_grid_tiles():
                         fixed=np.zeros(len(pos), np.uint8), ends=ends, k=np.full(len(ends), 1e4),
                         rest=d * rng.uniform(0.97, 1.03, len(d)), damping=np.full(len(ends), 1.0),
                         dt=1e-4, ground=True, spacing=0.1)
-    for var in (0, 7, 6, 5, 4, 3):
+    for var in (0, 8, 7, 6, 5, 4, 3):
         check(sys, 1000, kernel_variant=var, **(LAUNCH if var else {}))
 
 
@@ -206,7 +207,7 @@ def test_csr_kernel_variants_agree_bit_exact():
     sys = inputs.cube_drop(drop_height=0.02)
     sys.vel[:, 0] = 0.3
     a = gpu_run(sys, 500, exec_mode=T.EXEC_PERSISTENT)
-    for var in (1, 2, 3, 4, 5, 6, 7):
+    for var in (1, 2, 3, 4, 5, 6, 7, 8):
         b = gpu_run(sys, 500, kernel_variant=var, **LAUNCH)
         assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
 
@@ -310,7 +311,8 @@ def test_full_size_lattice_against_oracle_in_bench_configuration():
                  dict(accumulate=T.ACCUM_CSR, kernel_variant=3, **LAUNCH),
                  dict(accumulate=T.ACCUM_CSR, kernel_variant=4, **LAUNCH),
                  dict(accumulate=T.ACCUM_CSR, kernel_variant=6, **LAUNCH),
-                 dict(accumulate=T.ACCUM_CSR, kernel_variant=7, **LAUNCH), dict(accumulate=T.ACCUM_ATOMIC)):
+                 dict(accumulate=T.ACCUM_CSR, kernel_variant=7, **LAUNCH),
+                 dict(accumulate=T.ACCUM_CSR, kernel_variant=8, **LAUNCH), dict(accumulate=T.ACCUM_ATOMIC)):
         xg, vg, _ = gpu_run(sys, 64, **mode)
         err = np.abs(xg - xo).max()
         assert err <= POS_TOL_FRAC * sys.spacing, err
@@ -320,16 +322,17 @@ def test_full_size_lattice_against_oracle_in_bench_configuration():
 
 def test_auto_kernel_choice():
     """Auto picks the persistent cluster kernel for systems that fit one
-    cluster, else launches; among launch kernels the grid-box kernel for
-    masses on a grid, the coloured halo kernel for an unstructured mesh; the
-    box kernel refuses a mesh, the persistent mode a system too large."""
+    cluster, else launches; among launch kernels the cube kernel for
+    26-neighbour lattices (the grid-box kernel for other grids, see the
+    second-neighbour test), the coloured halo kernel for an unstructured mesh;
+    the box kernel refuses a mesh, the persistent mode a system too large."""
     with T.Sim(inputs.cube_drop(n=6)) as sim:
-        assert sim.csr_kernel == 6 and sim.exec_mode == T.EXEC_PERSISTENT
+        assert sim.csr_kernel == 8 and sim.exec_mode == T.EXEC_PERSISTENT
     with T.Sim(inputs.cube_drop(n=6), exec_mode=T.EXEC_LAUNCH) as sim:
         assert sim.exec_mode == T.EXEC_LAUNCH
     big = inputs.large_lattice(n=20, seed=0)
     with T.Sim(big) as sim:
-        assert sim.csr_kernel == 6 and sim.exec_mode == T.EXEC_LAUNCH
+        assert sim.csr_kernel == 8 and sim.exec_mode == T.EXEC_LAUNCH
     with pytest.raises(T.TitanError, match="PERSISTENT"):
         T.Sim(big, exec_mode=T.EXEC_PERSISTENT)
     mesh = inputs.random_mesh(n_points=3000, seed=2, lift=0.0)
@@ -359,7 +362,9 @@ def test_grid_with_second_neighbour_springs_and_duplicates():
                         rest=d * rng.uniform(0.97, 1.03, len(d)), damping=np.full(len(ends), 1.0),
                         dt=1e-4, ground=True, spacing=0.1)
     with T.Sim(sys) as sim:
-        assert sim.csr_kernel == 6
+        assert sim.csr_kernel == 6                # second neighbours: no cube layout
+    with pytest.raises(T.TitanError, match="cube"):
+        T.Sim(sys, kernel_variant=8)
     runs = [gpu_run(sys, 400, kernel_variant=v, **LAUNCH) for v in (6, 7, 4, 3)]
     runs.append(gpu_run(sys, 400, exec_mode=T.EXEC_PERSISTENT))
     for r in runs[1:]:

@@ -51,7 +51,8 @@ class Layout:
     DT = {"caller_of_dev": np.uint32, "cell": np.int32, "slice_off": np.uint32, "nbr": np.uint32,
           "spring": np.uint32, "entry_of_end": np.uint32, "col_off": np.int16, "box_own_slot": np.uint16,
           "box_ext_off": np.uint32, "box_ext_idx": np.uint32, "box_ext_slot": np.uint16,
-          "pslot": np.uint16, "phalo": np.uint32}
+          "pslot": np.uint16, "phalo": np.uint32, "cube_base": np.uint32, "cube_meta": np.uint32,
+          "cube_spring": np.uint32, "cube_pos_of_end": np.uint32, "box_dims": np.uint32}
 
     def __init__(self, lib, pos, ends):
         pos = np.ascontiguousarray(pos, np.float64)
@@ -61,8 +62,8 @@ class Layout:
         assert lib.shim_build(pos.ctypes.data, len(pos), ends.ctypes.data, len(ends), h, MAX_SLOTS) == 0
         self.n, self.s = len(pos), len(ends)
         self.ends = ends
-        self.n_dev, self.entries, self.grid, self.box_ok, self.halo_ok, self.box_slots, _ = \
-            [int(lib.shim_scalar(k)) for k in range(7)]
+        self.n_dev, self.entries, self.grid, self.box_ok, self.halo_ok, self.box_slots, _, self.cube_ok, \
+            self.cube_entries = [int(lib.shim_scalar(k)) for k in range(9)]
         for name, dt in self.DT.items():
             a = np.empty(int(lib.shim_len(name.encode())), dt)
             if a.size:
@@ -246,3 +247,87 @@ def test_persistent_plan_refuses_what_does_not_fit(shim):
     pos, ends = lattice(20, 20, 20)
     L = Layout(shim, pos, ends)
     assert not L.lib.shim_plan(220 * 1024, 0, 0)
+
+
+CUBE_DIRS = [(1, 0, 0), (-1, 1, 0), (0, 1, 0), (1, 1, 0), (-1, -1, 1), (0, -1, 1), (1, -1, 1),
+             (-1, 0, 1), (0, 0, 1), (1, 0, 1), (-1, 1, 1), (0, 1, 1), (1, 1, 1)]
+
+
+def check_cube(L):
+    """Replays the cube kernel's data flow on the host: for every mass, the
+    springs it adds in pass order (+p from its plus entry, then -p received
+    from the in-cube partner's plus entry or read from the ext stream) are
+    exactly its SELL row, in order; every spring end is stored once or
+    received; the pass offsets match the box geometry."""
+    assert L.cube_ok
+    NONE = 0xFFFFFFFF
+    P, W = 13, 8
+    cell = L.cell.reshape(-1, 3).astype(np.int64)
+    dev_of_cell = {tuple(c): d for d, c in enumerate(cell.tolist())}
+    meta = L.cube_meta.reshape(-1, P, W, 4)
+    dims = L.box_dims.reshape(-1, 2).astype(np.int64)
+    row, _, _ = L.entry_coords()
+    real = L.spring != NONE
+    order = np.argsort(row[real], kind="stable")
+    rows = {}
+    for m, q in zip(row[real][order].tolist(), L.spring[real][order].tolist()):
+        rows.setdefault(m, []).append(q)
+    n_cubes = L.n_dev // BLOCK
+    assert len(L.cube_base) == n_cubes + 1 and np.all(L.cube_base[:-1] % 16 == 0)
+    for b in range(n_cubes):
+        base = int(L.cube_base[b])
+        ext0 = base + P * BLOCK
+        for j, (dx, dy, dz) in enumerate(CUBE_DIRS):
+            off = np.int16(meta[b, j, 0, 3] & 0xFFFF)
+            assert off == dx + dims[b, 0] * dy + dims[b, 0] * dims[b, 1] * dz
+        for t in range(BLOCK):
+            m = b * BLOCK + t
+            w, l = divmod(t, 32)
+            seq = []
+            for j, (dx, dy, dz) in enumerate(CUBE_DIRS):
+                q = int(L.cube_spring[base + j * BLOCK + t])
+                if q != NONE:
+                    seq.append(q)
+                recv, ext, ebase = int(meta[b, j, w, 0]), int(meta[b, j, w, 1]), int(meta[b, j, w, 2])
+                assert not (recv >> l & 1 and ext >> l & 1)
+                if recv >> l & 1:
+                    pm = dev_of_cell[(cell[m, 0] - dx, cell[m, 1] - dy, cell[m, 2] - dz)]
+                    assert b * BLOCK <= pm < (b + 1) * BLOCK
+                    seq.append(int(L.cube_spring[base + j * BLOCK + (pm - b * BLOCK)]))
+                elif ext >> l & 1:
+                    seq.append(int(L.cube_spring[ext0 + ebase + bin(ext & ((1 << l) - 1)).count("1")]))
+            assert seq == rows.get(m, []), (m, seq, rows.get(m))
+    # every spring: one end at a plus entry, the other at an ext entry or received
+    pe = L.cube_pos_of_end.reshape(-1, 2)
+    stored = (pe != NONE).sum(1)
+    assert np.all(stored >= 1) and np.all(stored <= 2)
+    for q, (a, c) in enumerate(pe.tolist()):
+        for pos in (a, c):
+            if pos != NONE:
+                assert L.cube_spring[pos] == q
+
+
+def test_cube_layout_replays_every_row_in_order(shim):
+    pos, ends = lattice(16, 16, 8)
+    L = Layout(shim, pos, ends)
+    check_cube(L)
+    # springs inside a cube are stored once: fewer entries than half-edges
+    assert L.cube_entries < 0.75 * 2 * L.s
+
+
+def test_cube_layout_with_holes(shim):
+    pos, ends = lattice(10, 7, 5)
+    L = Layout(shim, pos, ends)
+    check_cube(L)
+    rng = np.random.default_rng(3)
+    occ = inputs.voxel_morphology(rng)
+    sys = inputs.voxel_robot(occ, rng.uniform(0, 2 * np.pi, occ.shape))
+    check_cube(Layout(shim, sys.pos, sys.ends))
+
+
+def test_cube_layout_refuses_second_neighbours_and_duplicates(shim):
+    pos, ends = lattice(10, 7, 5)
+    idx = np.arange(10 * 7 * 5).reshape(5, 7, 10)
+    far = np.stack([idx[:, :, :-2].ravel(), idx[:, :, 2:].ravel()], 1)
+    assert not Layout(shim, pos, np.concatenate([ends, far])).cube_ok
+    assert not Layout(shim, pos, np.concatenate([ends, ends[:3]])).cube_ok
