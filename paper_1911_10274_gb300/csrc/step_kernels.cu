@@ -367,19 +367,18 @@ k_step_box(const MassState *__restrict__ in, MassState *__restrict__ out, uint32
 // evaluates the spring from the cube's compact ext stream.  Each mass adds
 // +p1, -p1, +p2, ... in its row order, so the trajectory is bit-identical to
 // the other CSR kernels.  Stream: 143 MB instead of 208 MB on the 1M lattice.
+// The pass directions of layout.h's kCubeDirs, as (dx + 1) | (dy + 1) << 2 | (dz + 1) << 4.
+__constant__ uint8_t c_cube_dir[13] = {0x16, 0x18, 0x19, 0x1a, 0x20, 0x21, 0x22, 0x24, 0x25, 0x26, 0x28, 0x29, 0x2a};
 __device__ __forceinline__ int3 cube_dir(int j) {
-    switch (j) {
-        case 0: return make_int3(1, 0, 0);    case 1: return make_int3(-1, 1, 0);  case 2: return make_int3(0, 1, 0);
-        case 3: return make_int3(1, 1, 0);    case 4: return make_int3(-1, -1, 1); case 5: return make_int3(0, -1, 1);
-        case 6: return make_int3(1, -1, 1);   case 7: return make_int3(-1, 0, 1);  case 8: return make_int3(0, 0, 1);
-        case 9: return make_int3(1, 0, 1);    case 10: return make_int3(-1, 1, 1); case 11: return make_int3(0, 1, 1);
-        default: return make_int3(1, 1, 1);
-    }
+    const uint32_t d = c_cube_dir[j];
+    return make_int3((int)(d & 3) - 1, (int)((d >> 2) & 3) - 1, (int)((d >> 4) & 3) - 1);
 }
 constexpr int kCubeP = 13;
 
+constexpr int kCubeMinBlocks = 5;      // resident CTAs per SM the register budget is sized for
+
 template <bool HAS_C, bool HAS_ACT, bool GROUND>
-__global__ void __launch_bounds__(kHaloThreads, kBoxMinBlocks)
+__global__ void __launch_bounds__(kHaloThreads, kCubeMinBlocks)
 k_step_cube(const MassState *__restrict__ in, MassState *__restrict__ out, uint32_t n,
             const uint32_t *__restrict__ cube_base, const uint4 *__restrict__ cube_meta,
             const float2 *__restrict__ kl, const float *__restrict__ cc, const float2 *__restrict__ act,
@@ -410,7 +409,8 @@ k_step_cube(const MassState *__restrict__ in, MassState *__restrict__ out, uint3
         if (HAS_C) c_n = __ldcs(cc + base + tid);
         if (HAS_ACT) s_n = __ldcs(act + base + tid);
     }
-    uint4 m_n = __ldg(mt);
+    // pass metadata runs two passes ahead of its use, the plus entries one
+    uint4 m_n = __ldg(mt), m_nn = __ldg(mt + (kHaloThreads / 32));
     float4 p = make_float4(0.f, 0.f, 0.f, 0.f), v = p;
     if (valid) {
         load_state(in + i, p, v);
@@ -433,18 +433,29 @@ k_step_cube(const MassState *__restrict__ in, MassState *__restrict__ out, uint3
     const float clk = HAS_ACT ? actuation_clock(c, step) : 0.f;
     const uint32_t below = (1u << lane) - 1u;
     float fx = 0.f, fy = 0.f, fz = 0.f;
-#pragma unroll
+#pragma unroll 1
     for (int j = 0; j < kCubeP; ++j) {
         const float2 a = a_n, sa = s_n;
         const float ca = c_n;
         const uint4 m = m_n;
+        // this pass's ext entry is requested before the +p work and the barrier
+        const bool take_ext = valid && !((m.x >> lane) & 1u) && ((m.y >> lane) & 1u);
+        const uint32_t ex = ext0 + m.z + __popc(m.y & below);
+        float2 a2 = make_float2(0.f, 0.f), s2 = a2;
+        float c2 = c.c_uniform;
+        if (take_ext) {
+            a2 = __ldcs(kl + ex);
+            if (HAS_C) c2 = __ldcs(cc + ex);
+            if (HAS_ACT) s2 = __ldcs(act + ex);
+        }
         if (j + 1 < kCubeP) {
             if (valid) {
                 a_n = __ldcs(kl + base + (j + 1) * kHaloThreads + tid);
                 if (HAS_C) c_n = __ldcs(cc + base + (j + 1) * kHaloThreads + tid);
                 if (HAS_ACT) s_n = __ldcs(act + base + (j + 1) * kHaloThreads + tid);
             }
-            m_n = __ldg(mt + (j + 1) * (kHaloThreads / 32));
+            m_n = m_nn;
+            if (j + 2 < kCubeP) m_nn = __ldg(mt + (j + 2) * (kHaloThreads / 32));
         }
         const int32_t off = (int32_t)(int16_t)(m.w & 0xffffu);
         float f = 0.f, ux = 0.f, uy = 0.f, uz = 0.f;
@@ -471,14 +482,11 @@ k_step_cube(const MassState *__restrict__ in, MassState *__restrict__ out, uint3
                 fx = fmaf(g.x, -g.y, fx);
                 fy = fmaf(g.x, -g.z, fy);
                 fz = fmaf(g.x, -g.w, fz);
-            } else if ((m.y >> lane) & 1u) {                // -p from outside the cube
-                const uint32_t e = ext0 + m.z + __popc(m.y & below);
-                const float2 a2 = __ldcs(kl + e);
-                const float c2 = HAS_C ? __ldcs(cc + e) : c.c_uniform;
+            } else if (take_ext) {                          // -p from outside the cube
                 const uint32_t js = s_own - (uint32_t)off;
                 const float4 qa = tA[js];
                 const float2 qb = tB[js];
-                const float L = HAS_ACT ? actuated_length(c, a2.y, __ldcs(act + e), clk) : a2.y;
+                const float L = HAS_ACT ? actuated_length(c, a2.y, s2, clk) : a2.y;
                 spring_force(p, v, qa, make_float4(qa.w, qb.x, qb.y, 0.f), a2.x, L, c2, fx, fy, fz);
             }
         }
