@@ -221,7 +221,7 @@ def auto_kernel(args):
         return 0
     if args.kernel_variant:
         return args.kernel_variant
-    return 4 if args.workload == "mesh2m" else 8
+    return 4 if args.workload == "mesh2m" else 6
 
 
 def config_for(args, system, resolved=None):

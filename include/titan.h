@@ -106,9 +106,8 @@ typedef struct {
     void *stream;             /* cudaStream_t for the step loop; NULL: own stream  */
     uint64_t spin_limit;      /* bound on device spin-wait iterations; 0: default  */
     int32_t graph_chunk;      /* steps per captured CUDA graph; 0: 64; < 0: none   */
-    int32_t kernel_variant;   /* CSR kernel: 0 auto (8 for 26-neighbour lattices,
-                                 else 6 for masses on a grid when it fits, else 4
-                                 when it fits, else 3),
+    int32_t kernel_variant;   /* CSR kernel: 0 auto (6 for masses on a grid when
+                                 it fits, else 4 when it fits, else 3),
                                  1 direct loads, 2 TMA-staged stream, 3 bulk L2
                                  prefetch, 4 halo tables in shared memory, 5 halo +
                                  TMA-staged stream, 6 grid-box tables (masses on a

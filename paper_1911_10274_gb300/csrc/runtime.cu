@@ -577,7 +577,7 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
                                sim->grid_order ? cells.data() : nullptr))
             return bail(fail(sim, TITAN_E_UNSUPPORTED, "padded incidence exceeds 2^32 entries"));
         const int want = p->kernel_variant;
-        sim->csr_kernel = want == 0 ? (sim->grid_order ? 8 : 4) : want;
+        sim->csr_kernel = want == 0 ? (sim->grid_order ? 6 : 4) : want;
         if (sim->csr_kernel >= 6 && sim->csr_kernel <= 8 &&
             !(sim->grid_order && titan::build_box(nd, sim->sell, cells, sim->caller_of_dev, kHaloMaxSlots, sim->box))) {
             if (want >= 6)

@@ -366,7 +366,10 @@ k_step_box(const MassState *__restrict__ in, MassState *__restrict__ out, uint32
 // and its axis changes sign exactly) - and one whose -p partner is outside
 // evaluates the spring from the cube's compact ext stream.  Each mass adds
 // +p1, -p1, +p2, ... in its row order, so the trajectory is bit-identical to
-// the other CSR kernels.  Stream: 143 MB instead of 208 MB on the 1M lattice.
+// the other CSR kernels.  Stream: 143 MB instead of 208 MB on the 1M lattice,
+// but the 13 barriers per block and the divergent outside-partner path cost
+// more than the bytes saved (measured 84.4 us/step against 59.8 for
+// k_step_box): kernel variant 8, taken only when asked for.
 // The pass directions of layout.h's kCubeDirs, as (dx + 1) | (dy + 1) << 2 | (dz + 1) << 4.
 __constant__ uint8_t c_cube_dir[13] = {0x16, 0x18, 0x19, 0x1a, 0x20, 0x21, 0x22, 0x24, 0x25, 0x26, 0x28, 0x29, 0x2a};
 __device__ __forceinline__ int3 cube_dir(int j) {

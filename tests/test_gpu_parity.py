@@ -322,17 +322,19 @@ def test_full_size_lattice_against_oracle_in_bench_configuration():
 
 def test_auto_kernel_choice():
     """Auto picks the persistent cluster kernel for systems that fit one
-    cluster, else launches; among launch kernels the cube kernel for
-    26-neighbour lattices (the grid-box kernel for other grids, see the
-    second-neighbour test), the coloured halo kernel for an unstructured mesh;
-    the box kernel refuses a mesh, the persistent mode a system too large."""
+    cluster, else launches; among launch kernels the grid-box kernel for
+    masses on a grid, the coloured halo kernel for an unstructured mesh; the
+    cube kernel is taken when asked for on a 26-neighbour lattice; the box
+    kernel refuses a mesh, the persistent mode a system too large."""
     with T.Sim(inputs.cube_drop(n=6)) as sim:
-        assert sim.csr_kernel == 8 and sim.exec_mode == T.EXEC_PERSISTENT
+        assert sim.csr_kernel == 6 and sim.exec_mode == T.EXEC_PERSISTENT
     with T.Sim(inputs.cube_drop(n=6), exec_mode=T.EXEC_LAUNCH) as sim:
         assert sim.exec_mode == T.EXEC_LAUNCH
     big = inputs.large_lattice(n=20, seed=0)
     with T.Sim(big) as sim:
-        assert sim.csr_kernel == 8 and sim.exec_mode == T.EXEC_LAUNCH
+        assert sim.csr_kernel == 6 and sim.exec_mode == T.EXEC_LAUNCH
+    with T.Sim(big, kernel_variant=8, exec_mode=T.EXEC_LAUNCH) as sim:
+        assert sim.csr_kernel == 8
     with pytest.raises(T.TitanError, match="PERSISTENT"):
         T.Sim(big, exec_mode=T.EXEC_PERSISTENT)
     mesh = inputs.random_mesh(n_points=3000, seed=2, lift=0.0)
