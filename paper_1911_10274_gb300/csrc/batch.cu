@@ -7,10 +7,11 @@
 // contiguous range of the robot's masses: at launch it copies its masses'
 // state and their SELL-32 half-edge rows into shared memory with 1-D TMA bulk
 // copies (one mbarrier, bounded wait), then runs every time step of the
-// rollout without touching global memory: forces from neighbour states read
-// in its own shared memory or, for masses owned by another CTA of the cluster,
-// through distributed shared memory; integration into the other state buffer;
-// one hardware cluster barrier per step.  The final state goes back to global
+// rollout without touching global memory: each step first copies the current
+// state of its halo - the masses of other CTAs of the cluster its rows touch -
+// out of their shared memory (distributed shared memory, one coalesced pass),
+// then reads every neighbour from its own shared memory; integration into the
+// other state buffer; one hardware cluster barrier per step.  The final state goes back to global
 // memory.  The step is the same as the single-system kernels' (Sec. III-B,
 // Eq. 1 with the Sec. III-A constraints), including sinusoidal actuation.
 #include <cooperative_groups.h>
@@ -39,8 +40,10 @@ void set_thread_error(const std::string &msg);   // runtime.cu
 namespace {
 
 constexpr int kMaxCluster = 8;
-constexpr uint32_t kRankShift = 12;               // neighbour = rank << 12 | local index
-constexpr uint32_t kMaxPerCta = 1u << kRankShift;  // masses per CTA
+constexpr uint32_t kMaxPerCta = 4096;             // masses per CTA
+// A CTA's rows address its own masses at slots [0, slot_count) and its halo
+// at [slot_count, slot_count + halo_count); a halo entry names the owner as
+// rank << 16 | slot there.
 constexpr size_t kBatchSmemLimit = 220 * 1024;
 
 // Per-CTA descriptor.  All offsets are in elements of the arrays they index.
@@ -53,6 +56,10 @@ struct CtaDesc {
     uint32_t slice_base;    // first relative slice offset (multiple of 4)
     uint32_t n_slices;
     uint32_t robot;
+    uint32_t halo_off;      // first entry of this CTA's halo list
+    uint32_t halo_count;    // masses of other CTAs of the cluster its rows touch
+    uint32_t halo_slots;    // halo slots in the layout: the largest halo_count of the robot's CTAs, so
+                            // that every CTA of a cluster has its state buffers at the same offsets
 };
 
 // Shared-memory layout of one CTA (byte offsets; all 16-byte aligned).  The
@@ -65,13 +72,15 @@ struct SmemLayout {
 
 __host__ __device__ inline uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
 
-__host__ __device__ inline SmemLayout smem_layout(uint32_t slots, uint32_t n_slices, uint32_t edges, bool act) {
+__host__ __device__ inline SmemLayout smem_layout(uint32_t slots, uint32_t halo, uint32_t n_slices, uint32_t edges,
+                                                  bool act) {
+    const uint32_t tab = slots + halo;          // own masses, then the halo
     SmemLayout L;
     L.a0 = 0;
-    L.b0 = L.a0 + slots * 16;
-    L.a1 = L.b0 + slots * 8;
-    L.b1 = L.a1 + slots * 16;
-    L.inv = L.b1 + slots * 8;
+    L.b0 = L.a0 + tab * 16;
+    L.a1 = align16(L.b0 + tab * 8);
+    L.b1 = L.a1 + tab * 16;
+    L.inv = align16(L.b1 + tab * 8);
     L.slices = align16(L.inv + slots * 4);
     L.kl = align16(L.slices + 4 * ((n_slices + 1 + 3) & ~3u));
     L.act = L.kl + edges * 8;
@@ -85,14 +94,15 @@ __global__ void __launch_bounds__(512)
 k_batch_rollout(const CtaDesc *__restrict__ ctas, const MassState *__restrict__ state_in,
                 MassState *__restrict__ state_out, const uint32_t *__restrict__ slice_rel,
                 const float2 *__restrict__ kl, const float2 *__restrict__ act,
-                const uint16_t *__restrict__ nbr, titan::StepConst c, long long step0, uint32_t n_steps,
-                uint32_t cluster_size, uint32_t spin_limit, int *__restrict__ err) {
+                const uint16_t *__restrict__ nbr, const uint32_t *__restrict__ halo, titan::StepConst c,
+                long long step0, uint32_t n_steps, uint32_t cluster_size, uint32_t spin_limit,
+                int *__restrict__ err) {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ uint64_t bar;
     const CtaDesc d = ctas[blockIdx.x];
-    const SmemLayout L = smem_layout(d.slot_count, d.n_slices, d.edge_count, ACT);
-    float4 *sa[2] = {reinterpret_cast<float4 *>(sm + L.a0), reinterpret_cast<float4 *>(sm + L.a1)};
-    float2 *sb[2] = {reinterpret_cast<float2 *>(sm + L.b0), reinterpret_cast<float2 *>(sm + L.b1)};
+    const SmemLayout L = smem_layout(d.slot_count, d.halo_slots, d.n_slices, d.edge_count, ACT);
+    float4 *const a0s = reinterpret_cast<float4 *>(sm + L.a0), *const a1s = reinterpret_cast<float4 *>(sm + L.a1);
+    float2 *const b0s = reinterpret_cast<float2 *>(sm + L.b0), *const b1s = reinterpret_cast<float2 *>(sm + L.b1);
     float *s_inv = reinterpret_cast<float *>(sm + L.inv);
     const uint32_t *s_slice = reinterpret_cast<const uint32_t *>(sm + L.slices);
     const float2 *s_kl = reinterpret_cast<const float2 *>(sm + L.kl);
@@ -118,8 +128,8 @@ k_batch_rollout(const CtaDesc *__restrict__ ctas, const MassState *__restrict__ 
     for (uint32_t m = tid; m < d.slot_count; m += blockDim.x) {
         float4 p, v;
         titan::load_state(state_in + d.mass_begin + m, p, v);
-        sa[0][m] = make_float4(p.x, p.y, p.z, v.x);
-        sb[0][m] = make_float2(v.y, v.z);
+        a0s[m] = make_float4(p.x, p.y, p.z, v.x);
+        b0s[m] = make_float2(v.y, v.z);
         s_inv[m] = p.w;
     }
     __syncthreads();
@@ -132,7 +142,6 @@ k_batch_rollout(const CtaDesc *__restrict__ ctas, const MassState *__restrict__ 
         titan::ptx::mbar_wait_bounded(&bar, 0, spin_limit);
     }
     cg::cluster_group cluster = cg::this_cluster();
-    const uint32_t my_rank = cluster_size > 1 ? cluster.block_rank() : 0;
     if (cluster_size > 1) cluster.sync();       // all CTAs' shared memory is loaded and alive
 
     const uint32_t sub = tid % TPM;
@@ -142,10 +151,20 @@ k_batch_rollout(const CtaDesc *__restrict__ ctas, const MassState *__restrict__ 
     for (uint32_t k = 0; k < n_steps; ++k) {
         float sp = 0.f, cp = 1.f;
         if (ACT) sincosf(titan::clock_phase(c, step0 + (long long)k), &sp, &cp);
-        const float4 *srcA = sa[cur];
-        const float2 *srcB = sb[cur];
-        float4 *dstA = sa[cur ^ 1];
-        float2 *dstB = sb[cur ^ 1];
+        float4 *srcA = cur ? a1s : a0s;
+        float2 *srcB = cur ? b1s : b0s;
+        float4 *dstA = cur ? a0s : a1s;
+        float2 *dstB = cur ? b0s : b1s;
+        if (d.halo_count) {
+            // the halo's current state, copied out of the other CTAs' shared memory
+            for (uint32_t h = tid; h < d.halo_count; h += blockDim.x) {
+                const uint32_t code = halo[d.halo_off + h];
+                const uint32_t rank = code >> 16, local = code & 0xffffu;
+                srcA[d.slot_count + h] = *cluster.map_shared_rank(srcA + local, rank);
+                srcB[d.slot_count + h] = *cluster.map_shared_rank(srcB + local, rank);
+            }
+            __syncthreads();
+        }
         for (uint32_t pass = 0; ok && pass < passes; ++pass) {
             const uint32_t m = pass * per_pass + tid / TPM;
             const bool live = m < d.slot_count;
@@ -161,17 +180,9 @@ k_batch_rollout(const CtaDesc *__restrict__ ctas, const MassState *__restrict__ 
                 const uint32_t width = (s_slice[slice + 1] - e0) >> 5;
                 for (uint32_t t = sub; t < width; t += TPM) {
                     const uint32_t e = e0 + t * 32 + lane;
-                    const uint32_t code = s_nbr[e];
-                    const uint32_t rank = code >> kRankShift, local = code & (kMaxPerCta - 1);
-                    float4 qa;
-                    float2 qb;
-                    if (rank == my_rank) {              // own shared memory: plain shared loads
-                        qa = srcA[local];
-                        qb = srcB[local];
-                    } else {                            // another CTA of the cluster (DSMEM)
-                        qa = *cluster.map_shared_rank(srcA + local, rank);
-                        qb = *cluster.map_shared_rank(srcB + local, rank);
-                    }
+                    const uint32_t slot = s_nbr[e];         // own slot or halo slot
+                    const float4 qa = srcA[slot];
+                    const float2 qb = srcB[slot];
                     const float4 qp = make_float4(qa.x, qa.y, qa.z, 0.f);
                     const float4 qv = make_float4(qa.w, qb.x, qb.y, 0.f);
                     const float2 a = s_kl[e];
@@ -203,8 +214,8 @@ k_batch_rollout(const CtaDesc *__restrict__ ctas, const MassState *__restrict__ 
     }
     if (ok)
         for (uint32_t m = tid; m < d.mass_count; m += blockDim.x) {
-            const float4 a = sa[cur][m];
-            const float2 b = sb[cur][m];
+            const float4 a = (cur ? a1s : a0s)[m];
+            const float2 b = (cur ? b1s : b0s)[m];
             MassState o;
             o.p = make_float4(a.x, a.y, a.z, s_inv[m]);
             o.v = make_float4(a.w, b.x, b.y, 0.f);
@@ -261,6 +272,7 @@ struct titan_batch {
     uint32_t *d_slice = nullptr;
     float2 *d_kl = nullptr, *d_act = nullptr;
     uint16_t *d_nbr = nullptr;
+    uint32_t *d_halo = nullptr;
     uint32_t *d_moff = nullptr, *d_mcnt = nullptr;
     float *d_centroid = nullptr;
     int *d_err = nullptr;
@@ -336,7 +348,8 @@ cudaError_t launch_group(titan_batch *b, const Group &g, cudaStream_t st, long l
     const MassState *in = b->d_state[b->cur];
     MassState *out = b->d_state[b->cur ^ 1];
     void (*kern)(const CtaDesc *, const MassState *, MassState *, const uint32_t *, const float2 *,
-                 const float2 *, const uint16_t *, titan::StepConst, long long, uint32_t, uint32_t, uint32_t, int *);
+                 const float2 *, const uint16_t *, const uint32_t *, titan::StepConst, long long, uint32_t, uint32_t,
+                 uint32_t, int *);
 #define PICK(T)                                                                                   \
     if (b->has_act) kern = b->c.ground ? k_batch_rollout<true, true, T> : k_batch_rollout<true, false, T>; \
     else kern = b->c.ground ? k_batch_rollout<false, true, T> : k_batch_rollout<false, false, T>;
@@ -345,7 +358,8 @@ cudaError_t launch_group(titan_batch *b, const Group &g, cudaStream_t st, long l
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
     if (e != cudaSuccess) return e;
     return cudaLaunchKernelEx(&cfg, kern, ctas, in, out, (const uint32_t *)b->d_slice, (const float2 *)b->d_kl,
-                              (const float2 *)b->d_act, (const uint16_t *)b->d_nbr, b->c, step0, n_steps,
+                              (const float2 *)b->d_act, (const uint16_t *)b->d_nbr, (const uint32_t *)b->d_halo,
+                              b->c, step0, n_steps,
                               g.cluster, b->spin_limit, b->d_err);
 }
 
@@ -437,7 +451,13 @@ titan_status titan_batch_create(uint32_t n_systems, const titan_masses *masses, 
     CK(cudaSetDevice(p->device));
 
     // ---- host layout: per robot, the cluster size and per-CTA SELL blocks
-    struct CtaHost { CtaDesc d; std::vector<uint32_t> slices; std::vector<float2> kl, act; std::vector<uint16_t> nbr; };
+    struct CtaHost {
+        CtaDesc d;
+        std::vector<uint32_t> slices;
+        std::vector<float2> kl, act;
+        std::vector<uint16_t> nbr;   // own slot or halo slot per entry
+        std::vector<uint32_t> halo;  // rank << 16 | slot of each halo mass in its owner CTA
+    };
     std::vector<std::vector<CtaHost>> per_robot(n_systems);
     std::vector<uint32_t> cluster_of(n_systems);
     uint32_t slot_cursor = 0;
@@ -457,6 +477,19 @@ titan_status titan_batch_create(uint32_t n_systems, const titan_masses *masses, 
             he[cur[j]++] = {i, q};
         }
         for (uint32_t i = 0; i < m.n; ++i) std::sort(he.begin() + rowptr[i], he.begin() + rowptr[i + 1]);
+        // distinct masses outside [q0, q1) that the rows of [q0, q1) touch
+        std::vector<uint32_t> mark(m.n, UINT32_MAX);
+        uint32_t gen = 0;
+        auto halo_count = [&](uint32_t q0, uint32_t q1) {
+            ++gen;                                    // a fresh mark for every call
+            uint32_t cnt = 0;
+            for (uint32_t i = q0; i < q1; ++i)
+                for (uint32_t r2 = rowptr[i]; r2 < rowptr[i + 1]; ++r2) {
+                    const uint32_t j = he[r2].first;
+                    if ((j < q0 || j >= q1) && mark[j] != gen) { mark[j] = gen; ++cnt; }
+                }
+            return cnt;
+        };
         // smallest cluster whose per-CTA shared memory fits
         uint32_t C = 1;
         for (;; C *= 2) {
@@ -466,6 +499,10 @@ titan_status titan_batch_create(uint32_t n_systems, const titan_masses *masses, 
             }
             const uint32_t per = ((m.n + C - 1) / C + 31) & ~31u;
             if (per > kMaxPerCta) continue;
+            // the layout of every CTA of the cluster reserves the largest halo
+            uint32_t hc = 0;
+            if (C > 1)
+                for (uint32_t q0 = 0; q0 < m.n; q0 += per) hc = std::max(hc, halo_count(q0, std::min(m.n, q0 + per)));
             size_t worst = 0;
             for (uint32_t q0 = 0; q0 < m.n; q0 += per) {
                 uint32_t edges = 0, ns = 0;
@@ -475,9 +512,9 @@ titan_status titan_batch_create(uint32_t n_systems, const titan_masses *masses, 
                     edges += 32 * ((w + 1) & ~1u);
                 }
                 edges = (edges + 63) & ~63u;
-                worst = std::max<size_t>(worst, smem_layout(per, ns, edges, any_act).total);
+                worst = std::max<size_t>(worst, smem_layout(per, hc, ns, edges, any_act).total);
             }
-            if (worst <= kBatchSmemLimit) break;
+            if (worst <= kBatchSmemLimit && per + hc <= 65535) break;
         }
         cluster_of[r] = C;
         const uint32_t per = ((m.n + C - 1) / C + 31) & ~31u;
@@ -486,8 +523,17 @@ titan_status titan_batch_create(uint32_t n_systems, const titan_masses *masses, 
         for (uint32_t q = 0; q < C; ++q) {
             CtaHost h;
             const uint32_t m0 = std::min(m.n, q * per), m1 = std::min(m.n, m0 + per);
-            h.d = CtaDesc{slot_cursor + m0, m1 - m0, per, 0, 0, 0, 0, r};
-            // SELL of the CTA's masses, neighbours encoded as rank << 12 | local index
+            h.d = CtaDesc{slot_cursor + m0, m1 - m0, per, 0, 0, 0, 0, r, 0, 0, 0};
+            // SELL of the CTA's masses, neighbours as own slots (j - m0) or halo slots (per + h)
+            std::fill(mark.begin(), mark.end(), UINT32_MAX);      // here: halo slot of a mass
+            auto slot_of = [&](uint32_t j) -> uint16_t {
+                if (j >= m0 && j < m1) return (uint16_t)(j - m0);
+                if (mark[j] == UINT32_MAX) {
+                    mark[j] = per + (uint32_t)h.halo.size();
+                    h.halo.push_back(((j / per) << 16) | (j % per));
+                }
+                return (uint16_t)mark[j];
+            };
             h.slices.push_back(0);
             for (uint32_t sl = m0; sl < m0 + per; sl += 32) {
                 uint32_t w = 0;
@@ -504,7 +550,7 @@ titan_status titan_batch_create(uint32_t n_systems, const titan_masses *masses, 
                         if (i < m1 && t < deg[i]) {
                             const auto &x = he[rowptr[i] + t];
                             const uint32_t j = x.first, q2 = x.second;
-                            h.nbr[e] = (uint16_t)(((j / per) << kRankShift) | (j % per));
+                            h.nbr[e] = slot_of(j);
                             double L;
                             if (s.rest) L = s.rest[q2];
                             else {
@@ -521,7 +567,7 @@ titan_status titan_batch_create(uint32_t n_systems, const titan_masses *masses, 
                                                        (float)(act[r].amp[q2] * std::sin(act[r].phase[q2])));
                         } else {
                             const uint32_t self = std::min(i, m.n - 1);   // zero-parameter padding
-                            h.nbr[e] = (uint16_t)(((self / per) << kRankShift) | (self % per));
+                            h.nbr[e] = slot_of(self);
                         }
                     }
                 }
@@ -533,8 +579,12 @@ titan_status titan_batch_create(uint32_t n_systems, const titan_masses *masses, 
             h.nbr.resize(E, 0);
             h.d.edge_count = E;
             h.d.n_slices = (uint32_t)h.slices.size() - 1;
+            h.d.halo_count = (uint32_t)h.halo.size();
             per_robot[r].push_back(std::move(h));
         }
+        uint32_t halo_slots = 0;
+        for (const auto &hh : per_robot[r]) halo_slots = std::max(halo_slots, hh.d.halo_count);
+        for (auto &hh : per_robot[r]) hh.d.halo_slots = halo_slots;
         slot_cursor += C * per;
         // initial state of every slot of this robot (padding slots: fixed, at rest)
         b->init_state.resize(slot_cursor);
@@ -557,7 +607,7 @@ titan_status titan_batch_create(uint32_t n_systems, const titan_masses *masses, 
     auto smem_class = [&](uint32_t r) {
         size_t worst = 0;
         for (const auto &h : per_robot[r])
-            worst = std::max<size_t>(worst, smem_layout(h.d.slot_count, h.d.n_slices, h.d.edge_count, any_act).total);
+            worst = std::max<size_t>(worst, smem_layout(h.d.slot_count, h.d.halo_slots, h.d.n_slices, h.d.edge_count, any_act).total);
         uint32_t cls = 0;
         for (uint32_t k = 0; k < sizeof(kPerSm) / sizeof(kPerSm[0]); ++k)
             if (worst + 1024 <= 228u * 1024u / kPerSm[k]) cls = k;
@@ -576,6 +626,7 @@ titan_status titan_batch_create(uint32_t n_systems, const titan_masses *masses, 
     std::vector<uint32_t> slices;
     std::vector<float2> kl, ac;
     std::vector<uint16_t> nb;
+    std::vector<uint32_t> hl;
     for (uint32_t k = 0; k < n_systems; ++k) {
         const uint32_t r = order[k];
         if (b->groups.empty() || b->groups.back().cluster != cluster_of[r] || class_of[order[k - 1]] != class_of[r]) {
@@ -594,9 +645,11 @@ titan_status titan_batch_create(uint32_t n_systems, const titan_masses *masses, 
             kl.insert(kl.end(), h.kl.begin(), h.kl.end());
             ac.insert(ac.end(), h.act.begin(), h.act.end());
             nb.insert(nb.end(), h.nbr.begin(), h.nbr.end());
+            h.d.halo_off = (uint32_t)hl.size();
+            hl.insert(hl.end(), h.halo.begin(), h.halo.end());
             descs.push_back(h.d);
             ++g.cta_count;
-            g.smem = std::max<size_t>(g.smem, smem_layout(h.d.slot_count, h.d.n_slices, h.d.edge_count, any_act).total);
+            g.smem = std::max<size_t>(g.smem, smem_layout(h.d.slot_count, h.d.halo_slots, h.d.n_slices, h.d.edge_count, any_act).total);
         }
         per_robot[r].clear();
     }
@@ -621,6 +674,7 @@ titan_status titan_batch_create(uint32_t n_systems, const titan_masses *masses, 
     CK(balloc(b, &b->d_kl, kl.size()));
     if (any_act) CK(balloc(b, &b->d_act, ac.size()));
     CK(balloc(b, &b->d_nbr, nb.size()));
+    CK(balloc(b, &b->d_halo, std::max<size_t>(hl.size(), 1)));
     CK(balloc(b, &b->d_moff, n_systems));
     CK(balloc(b, &b->d_mcnt, n_systems));
     CK(balloc(b, &b->d_centroid, 3 * (size_t)n_systems));
@@ -631,6 +685,7 @@ titan_status titan_batch_create(uint32_t n_systems, const titan_masses *masses, 
     CK(cudaMemcpy(b->d_kl, kl.data(), kl.size() * sizeof(float2), cudaMemcpyHostToDevice));
     if (any_act) CK(cudaMemcpy(b->d_act, ac.data(), ac.size() * sizeof(float2), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(b->d_nbr, nb.data(), nb.size() * 2, cudaMemcpyHostToDevice));
+    if (!hl.empty()) CK(cudaMemcpy(b->d_halo, hl.data(), hl.size() * 4, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(b->d_moff, b->mass_off.data(), n_systems * 4, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(b->d_mcnt, b->mass_cnt.data(), n_systems * 4, cudaMemcpyHostToDevice));
     CK(cudaMemset(b->d_err, 0, sizeof(int)));
