@@ -94,8 +94,9 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.proc = None
         self.gpu = gpu_index
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv") \
-            if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/titan_clocks_{os.getpid()}.csv"
+        import tempfile
+        self.path = os.path.join(os.environ.get("TITAN_CLOCKS_DIR", tempfile.gettempdir()),
+                                 f"titan_clocks_gpu{gpu_index}_{os.getpid()}.csv")
 
     def __enter__(self):
         try:

@@ -12,7 +12,7 @@
  * the forces it received (Sec. III-A: masses are also subject to gravity, to
  * solid planes with friction, and to constraints).
  *
- * Readings of points the paper leaves open (each one is listed in the design doc):
+ * Readings of points the paper leaves open:
  *  - Spring law.  Eq. 1 prints F = k(x1 - x2); read as Hooke's law on the
  *    extension along the spring axis, f = k(l - L), with L the rest length,
  *    plus an axial dashpot c * ((v_j - v_i) . u).  u is the unit vector from

@@ -15,7 +15,7 @@ simulation.  This module closes that loop on the GPU:
   rollouts;
 * search: a (mu + lambda) mutation search.  The plain form simulates every
   mutant; the screened form lets the surrogate rank all mutants and simulates
-  only the top few, whose simulated fitness (the simulator remains the judge)
+  only the top few, whose simulated fitness (the simulator has the final say)
   decides who survives; those simulated mutants also refine the network
   (online fine-tuning on everything simulated so far, mirror-augmented),
   because a network trained only on random robots ranks nearby mutants
