@@ -5,8 +5,9 @@ actuation, Sec. III-F; many agents in parallel, Sec. I) can run alongside the
 simulation.  This module closes that loop on the GPU:
 
 * morphologies: an 8 x 8 x 8 voxel grid, Bernoulli(0.6) occupancy, largest
-  26-connected component, one mass per voxel, 26-neighbourhood springs, every
-  spring actuated with amplitude 0.1 and the phase of its lower-index voxel;
+  26-connected component, one mass per voxel, 26-neighbourhood springs; each
+  voxel carries a phase and every spring the mean of its two voxels'
+  sinusoidal signals (amplitude 0.1, 2 Hz);
 * fitness: the robot's centroid x-displacement after a rollout on the ground,
   simulated by the batched persistent kernels (``titan.Batch``);
 * surrogate: an MLP on the tcgen05 tensor cores (``titan.MLP``) mapping the
@@ -17,9 +18,10 @@ simulation.  This module closes that loop on the GPU:
   mutant; the screened form lets the surrogate rank all mutants and simulates
   only the top few, whose simulated fitness (the simulator has the final say)
   decides who survives; those simulated mutants also refine the network
-  (online fine-tuning on everything simulated so far, mirror-augmented),
-  because a network trained only on random robots ranks nearby mutants
-  poorly.  A random pick of the same size is the ablation.
+  (online fine-tuning on a window of the latest simulated mutants, or all of
+  them, mirror-augmented), because a network trained only on random robots
+  ranks nearby mutants poorly.  A random pick of the same size is the
+  ablation.
 
 Python here only orchestrates: every rollout and every network product runs
 in the library's kernels.
