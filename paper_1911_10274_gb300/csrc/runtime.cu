@@ -279,7 +279,8 @@ cudaError_t enqueue_step_io(titan_sim *sim, cudaStream_t st, const MassState *in
             if (sim->csr_kernel == 5)
                 return titan::launch_step_halo_tma(in, out, sim->n_dev, v, h, sim->halo_w_max, sim->c, si,
                                                    so, st);
-            return titan::launch_step_halo(in, out, sim->n_dev, v, h, sim->c, si, so, st);
+            return titan::launch_step_halo(in, out, sim->n_dev, v, h, sim->c, si, so, st,
+                                           sim->l2_on ? &sim->l2win : nullptr);
         }
         v.variant = sim->csr_kernel == 3 ? 0 : sim->csr_kernel;   // launcher: 0 prefetch, 1 direct, 2 staged
         return titan::launch_step_sell(in, out, sim->n_dev, v, sim->c, si, so, st);

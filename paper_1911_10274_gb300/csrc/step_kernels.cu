@@ -1005,7 +1005,7 @@ cudaError_t launch_step_sell(const MassState *in, MassState *out, uint32_t n, co
 
 cudaError_t launch_step_halo(const MassState *in, MassState *out, uint32_t n, const SellView &v,
                              const HaloView &h, const StepConst &c, const long long *step_in,
-                             long long *step_out, cudaStream_t stream) {
+                             long long *step_out, cudaStream_t stream, const cudaAccessPolicyWindow *l2win) {
     const bool hc = v.c != nullptr, ha = v.act != nullptr, gr = c.ground != 0;
     const unsigned g = n ? (n + kHaloThreads - 1) / kHaloThreads : 1;
     const size_t bytes = (size_t)h.table_slots * (sizeof(float4) + sizeof(float2));
@@ -1021,9 +1021,22 @@ cudaError_t launch_step_halo(const MassState *in, MassState *out, uint32_t n, co
                                                  (int)cudaSharedmemCarveoutMaxShared);            \
             if (e != cudaSuccess) return e;                                                      \
         }                                                                                        \
-        kern<<<g, kHaloThreads, bytes, stream>>>(in, out, n, v.slice_off, h.nslot, v.kl, v.c, v.act, \
-                                                 h.own_slot, h.ext_off, h.ext_idx, h.ext_slot,   \
-                                                 h.table_slots, h.ahead, c, step_in, step_out);  \
+        cudaLaunchConfig_t cfg = {};                                                             \
+        cfg.gridDim = dim3(g);                                                                   \
+        cfg.blockDim = dim3(kHaloThreads);                                                       \
+        cfg.dynamicSmemBytes = bytes;                                                            \
+        cfg.stream = stream;                                                                     \
+        cudaLaunchAttribute attr[1];                                                             \
+        if (l2win) {                                                                             \
+            attr[0].id = cudaLaunchAttributeAccessPolicyWindow;                                  \
+            attr[0].val.accessPolicyWindow = *l2win;                                             \
+            cfg.attrs = attr;                                                                    \
+            cfg.numAttrs = 1;                                                                    \
+        }                                                                                        \
+        cudaError_t e = cudaLaunchKernelEx(&cfg, kern, in, out, n, v.slice_off, h.nslot, v.kl, v.c, v.act, \
+                                           h.own_slot, h.ext_off, h.ext_idx, h.ext_slot, h.table_slots, \
+                                           h.ahead, c, step_in, step_out);                       \
+        if (e != cudaSuccess) return e;                                                          \
     } while (0)
     if (hc) {
         if (ha) { if (gr) TITAN_HALO(true, true, true); else TITAN_HALO(true, true, false); }

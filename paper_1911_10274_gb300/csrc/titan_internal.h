@@ -101,7 +101,8 @@ cudaError_t launch_step_sell(const MassState *in, MassState *out, uint32_t n, co
 // Halo form of the fused CSR step (see step_kernels.cu).
 cudaError_t launch_step_halo(const MassState *in, MassState *out, uint32_t n, const SellView &v,
                              const HaloView &h, const StepConst &c, const long long *step_in,
-                             long long *step_out, cudaStream_t stream);
+                             long long *step_out, cudaStream_t stream,
+                             const cudaAccessPolicyWindow *l2win = nullptr);
 
 // Grid-box form of the halo kernel (see step_kernels.cu).  l2win (optional):
 // an L2 access-policy window attached to the launch.

@@ -372,3 +372,14 @@ def test_grid_with_second_neighbour_springs_and_duplicates():
     for r in runs[1:]:
         assert np.array_equal(runs[0][0], r[0]) and np.array_equal(runs[0][1], r[1])
     check(sys, 400)
+
+
+def test_l2_persistence_changes_no_bit():
+    """The L2 access-policy window on the state buffers is a cache hint: with
+    and without it the trajectories are identical (grid-box and halo kernels)."""
+    lattice = inputs.large_lattice(n=20, seed=0)
+    mesh = inputs.random_mesh(n_points=4000, seed=3, lift=0.0)
+    for sys in (lattice, mesh):
+        a = gpu_run(sys, 200, l2_persist=True, **LAUNCH)
+        b = gpu_run(sys, 200, l2_persist=False, **LAUNCH)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
