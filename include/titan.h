@@ -121,8 +121,8 @@ typedef struct {
     int32_t l2_persist;       /* nonzero (default): keep the two state buffers of a
                                  CSR simulation resident in L2 (an access-policy
                                  window on the grid-box, cube and halo step
-                                 kernels, hit ratio scaled down when the state is
-                                 larger than the persisting part of L2; the context's
+                                 kernels, taken only when both buffers fit the
+                                 persisting part of L2; the context's
                                  persisting-L2 limit is raised while any such
                                  handle lives and restored by titan_destroy)    */
     int32_t reserved[5];      /* zero                                              */
