@@ -435,10 +435,15 @@ titan_status titan_batch_create(uint32_t n_systems, const titan_masses *masses, 
     c.ground = p->ground ? 1 : 0; c.ground_k = (float)p->ground_k; c.mu = (float)p->mu;
     c.c_uniform = (float)p->damping;
     c.act_omega = 2.0 * 3.14159265358979323846 * freq;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    // every failure after this point releases what was built and gives the
+    // caller back its current device
     auto bail = [&](titan_status st) {
         titan::set_thread_error(b->error);
         release(b);
         delete b;
+        if (prev >= 0) cudaSetDevice(prev);
         return st;
     };
 #define CK(call)                                                             \
@@ -446,8 +451,6 @@ titan_status titan_batch_create(uint32_t n_systems, const titan_masses *masses, 
         cudaError_t e_ = (call);                                             \
         if (e_ != cudaSuccess) return bail(bfail_cuda(b, e_, #call));        \
     } while (0)
-    int prev = -1;
-    cudaGetDevice(&prev);
     CK(cudaSetDevice(p->device));
 
     // ---- host layout: per robot, the cluster size and per-CTA SELL blocks
@@ -493,10 +496,8 @@ titan_status titan_batch_create(uint32_t n_systems, const titan_masses *masses, 
         // smallest cluster whose per-CTA shared memory fits
         uint32_t C = 1;
         for (;; C *= 2) {
-            if (C > (uint32_t)kMaxCluster) {
-                delete b;
-                return bfail(nullptr, TITAN_E_UNSUPPORTED, "system " + std::to_string(r) + " does not fit a cluster of 8 CTAs");
-            }
+            if (C > (uint32_t)kMaxCluster)
+                return bail(bfail(b, TITAN_E_UNSUPPORTED, "system " + std::to_string(r) + " does not fit a cluster of 8 CTAs"));
             const uint32_t per = ((m.n + C - 1) / C + 31) & ~31u;
             if (per > kMaxPerCta) continue;
             // the layout of every CTA of the cluster reserves the largest halo
