@@ -142,3 +142,14 @@ def test_wait_timeout_selftest_rejects_unbounded_limits_before_touching_the_devi
     for bad in (0, (1 << 20) + 1):
         with pytest.raises(T.TitanError, match="spin_limit"):
             T.titan_selftest_wait_timeout(0, bad)
+
+
+def test_every_source_and_header_is_a_rebuild_input():
+    """Editing any file of the kernel sources or the public header must make
+    the library stale, headers of device code (.cuh) included."""
+    from paper_1911_10274_gb300 import build as B
+    watched = {os.path.abspath(f) for f in B._inputs()}
+    for d in (B.CSRC, B.INCLUDE):
+        for f in os.listdir(d):
+            if f.endswith((".cu", ".cpp", ".h", ".cuh")):
+                assert os.path.abspath(os.path.join(d, f)) in watched, f
