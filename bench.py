@@ -45,16 +45,21 @@ L2_BYTES = 126 * 1024 * 1024
 
 # ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one step
 # kernel launch, keyed by (workload, accumulation, kernel, SHA-256 prefix of
-# csrc/step_kernels.cu when it was captured).  Reported only while the source
-# is unchanged.  Capture: profiles/k_step_box_lattice1m.md.
+# the files the step kernels are compiled from: their source, the physics
+# header and the build script with its flags).  Reported only while those are
+# unchanged.  Capture: profiles/k_step_box_lattice1m.md.
 NCU_TRAFFIC = {
-    ("lattice1m", "csr", "k_step_box", "f7d62d1cec8d9746"): 251_621_120 + 10_171_904,
+    ("lattice1m", "csr", "k_step_box", "25173d1fe6a0f164"): 251_619_584 + 10_234_624,
 }
+KERNEL_INPUTS = ("paper_1911_10274_gb300/csrc/step_kernels.cu", "paper_1911_10274_gb300/csrc/physics.cuh",
+                 "paper_1911_10274_gb300/build.py")
 
 
 def kernel_source_hash() -> str:
-    p = os.path.join(ROOT, "paper_1911_10274_gb300", "csrc", "step_kernels.cu")
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for rel in KERNEL_INPUTS:
+        h.update(open(os.path.join(ROOT, rel), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def measured_peaks():

@@ -50,7 +50,10 @@ def build(force: bool = False, verbose: bool = False, jobs: int = 0) -> str:
     nvcc = _nvcc()
     cuda_lib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "lib64")
     os.makedirs(BUILD_DIR, exist_ok=True)
-    common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
+    # -ftz=true: single-precision denormal results flush to zero in every
+    # kernel alike (so GPU paths stay bit-identical to one another); the
+    # reciprocal square root of the spring step then needs no denormal path
+    common = ARCH + ["-O3", "-ftz=true", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
                      "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
     if verbose:
         common += ["-Xptxas", "-v"]

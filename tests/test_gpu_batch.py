@@ -104,3 +104,31 @@ def test_unactuated_batch_with_fixed_masses():
             xg, _ = b.read(r)
             fx = sy.fixed.astype(bool)
             assert np.array_equal(xg[fx], sy.pos[fx].astype(np.float32))
+
+
+def test_system_too_dense_for_a_cluster_is_refused_and_the_device_kept():
+    """4096 masses on a line, each joined to its next 32: 64 half-edges per
+    mass, so even 8 CTAs of 512 masses need 320 KB of rows each.  Creation
+    must refuse it (unsupported, nothing built) and leave the caller's current
+    device as it was; a small batch still works afterwards."""
+    import torch
+    n, reach = 4096, 32
+    pos = np.zeros((n, 3))
+    pos[:, 0] = 0.1 * np.arange(n)
+    pos[:, 2] = 1.0
+    ends = np.array([(i, i + d) for i in range(n) for d in range(1, reach + 1) if i + d < n], np.uint32)
+    s = ends.shape[0]
+    dense = inputs.System(pos=pos, vel=np.zeros_like(pos), mass=np.full(n, 0.1), fixed=np.zeros(n, np.uint8),
+                          ends=ends, k=np.full(s, 1e3), rest=0.1 * (ends[:, 1] - ends[:, 0]).astype(np.float64),
+                          damping=np.full(s, 1.0), dt=1e-4, ground=True)
+    torch.cuda.set_device(0)
+    before = torch.cuda.current_device()
+    with pytest.raises(T.TitanError) as ei:
+        T.Batch([dense])
+    assert ei.value.status == T.TITAN_E_UNSUPPORTED
+    assert "cluster of 8" in str(ei.value)
+    assert torch.cuda.current_device() == before
+    robots = _robots()[:2]
+    with T.Batch(robots) as b:
+        b.rollout(100)
+        _check(b, robots, 100)
