@@ -25,6 +25,7 @@
 #include <string>
 #include <vector>
 
+#include "layout.h"
 #include "physics.cuh"
 #include "ptx.cuh"
 #include "titan.h"
@@ -39,59 +40,13 @@ void set_thread_error(const std::string &msg);   // runtime.cu
 
 namespace {
 
-constexpr int kMaxCluster = 8;
-constexpr uint32_t kMaxPerCta = 4096;             // masses per CTA
-// A CTA's rows address its own masses at slots [0, slot_count) and its halo
-// at [slot_count, slot_count + halo_count); a halo entry names the owner as
-// rank << 16 | slot there.
-constexpr size_t kBatchSmemLimit = 220 * 1024;
-
-// Per-CTA descriptor.  All offsets are in elements of the arrays they index.
-struct CtaDesc {
-    uint32_t mass_begin;    // first global mass slot of this CTA
-    uint32_t mass_count;    // masses owned (<= kMaxPerCta)
-    uint32_t slot_count;    // mass_count rounded up to 32
-    uint32_t edge_off;      // first SELL entry (multiple of 64)
-    uint32_t edge_count;    // SELL entries (multiple of 64)
-    uint32_t slice_base;    // first relative slice offset (multiple of 4)
-    uint32_t n_slices;
-    uint32_t robot;
-    uint32_t halo_off;      // first entry of this CTA's halo list
-    uint32_t halo_count;    // masses of other CTAs of the cluster its rows touch
-    uint32_t halo_slots;    // halo slots in the layout: the largest halo_count of the robot's CTAs, so
-                            // that every CTA of a cluster has its state buffers at the same offsets
-};
-
-// Shared-memory layout of one CTA (byte offsets; all 16-byte aligned).  The
-// state is split per slot into (x, y, z, vx) float4 and (vy, vz) float2 arrays
-// (two buffers) plus 1/m: 16-byte loads at a 16-byte stride keep consecutive
-// slots in distinct banks (a 32-byte record read in two halves cannot).
-struct SmemLayout {
-    uint32_t a0, b0, a1, b1, inv, slices, kl, act, nbr, total;
-};
-
-__host__ __device__ inline uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
-
-__host__ __device__ inline SmemLayout smem_layout(uint32_t slots, uint32_t halo, uint32_t n_slices, uint32_t edges,
-                                                  bool act) {
-    const uint32_t tab = slots + halo;          // own masses, then the halo
-    SmemLayout L;
-    L.a0 = 0;
-    L.b0 = L.a0 + tab * 16;
-    L.a1 = align16(L.b0 + tab * 8);
-    L.b1 = L.a1 + tab * 16;
-    L.inv = align16(L.b1 + tab * 8);
-    L.slices = align16(L.inv + slots * 4);
-    L.kl = align16(L.slices + 4 * ((n_slices + 1 + 3) & ~3u));
-    L.act = L.kl + edges * 8;
-    L.nbr = L.act + (act ? edges * 8 : 0);
-    L.total = align16(L.nbr + edges * 2);
-    return L;
-}
+using titan::BatchCta;
+using titan::BatchSmem;
+using titan::batch_smem_layout;
 
 template <bool ACT, bool GROUND, int TPM>
 __global__ void __launch_bounds__(512)
-k_batch_rollout(const CtaDesc *__restrict__ ctas, const MassState *__restrict__ state_in,
+k_batch_rollout(const BatchCta *__restrict__ ctas, const MassState *__restrict__ state_in,
                 MassState *__restrict__ state_out, const uint32_t *__restrict__ slice_rel,
                 const float2 *__restrict__ kl, const float2 *__restrict__ act,
                 const uint16_t *__restrict__ nbr, const uint32_t *__restrict__ halo, titan::StepConst c,
@@ -99,8 +54,8 @@ k_batch_rollout(const CtaDesc *__restrict__ ctas, const MassState *__restrict__ 
                 int *__restrict__ err) {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ uint64_t bar;
-    const CtaDesc d = ctas[blockIdx.x];
-    const SmemLayout L = smem_layout(d.slot_count, d.halo_slots, d.n_slices, d.edge_count, ACT);
+    const BatchCta d = ctas[blockIdx.x];
+    const BatchSmem L = batch_smem_layout(d.slot_count, d.halo_slots, d.n_slices, d.edge_count, ACT);
     float4 *const a0s = reinterpret_cast<float4 *>(sm + L.a0), *const a1s = reinterpret_cast<float4 *>(sm + L.a1);
     float2 *const b0s = reinterpret_cast<float2 *>(sm + L.b0), *const b1s = reinterpret_cast<float2 *>(sm + L.b1);
     float *s_inv = reinterpret_cast<float *>(sm + L.inv);
@@ -263,10 +218,10 @@ struct titan_batch {
     uint64_t steps = 0;
     uint32_t spin_limit = 1u << 22;
     std::vector<uint32_t> mass_off, mass_cnt;   // per robot, into the global mass slots
-    std::vector<MassState> init_state;           // caller-provided initial state (global slots)
+    std::vector<float> init_state;               // caller-provided initial state, [slots][8] (x y z 1/m vx vy vz 0)
     std::vector<Group> groups;
     // device
-    CtaDesc *d_ctas = nullptr;
+    BatchCta *d_ctas = nullptr;
     MassState *d_state[2] = {nullptr, nullptr};
     int cur = 0;
     uint32_t *d_slice = nullptr;
@@ -344,10 +299,10 @@ cudaError_t launch_group(titan_batch *b, const Group &g, cudaStream_t st, long l
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    const CtaDesc *ctas = b->d_ctas + g.cta_first;
+    const BatchCta *ctas = b->d_ctas + g.cta_first;
     const MassState *in = b->d_state[b->cur];
     MassState *out = b->d_state[b->cur ^ 1];
-    void (*kern)(const CtaDesc *, const MassState *, MassState *, const uint32_t *, const float2 *,
+    void (*kern)(const BatchCta *, const MassState *, MassState *, const uint32_t *, const float2 *,
                  const float2 *, const uint16_t *, const uint32_t *, titan::StepConst, long long, uint32_t, uint32_t,
                  uint32_t, int *);
 #define PICK(T)                                                                                   \
@@ -396,7 +351,8 @@ titan_status titan_batch_create(uint32_t n_systems, const titan_masses *masses, 
         const titan_springs &s = springs[r];
         const std::string at = " (system " + std::to_string(r) + ")";
         if (m.n == 0 || !m.pos || !m.mass) return bfail(nullptr, TITAN_E_INVALID, "empty system or null pos/mass" + at);
-        if (m.n > kMaxCluster * kMaxPerCta) return bfail(nullptr, TITAN_E_INVALID, "system too large for one cluster" + at);
+        if (m.n > titan::kBatchMaxCluster * titan::kBatchMaxPerCta)
+            return bfail(nullptr, TITAN_E_INVALID, "system too large for one cluster" + at);
         if (s.n && (!s.ends || !s.k)) return bfail(nullptr, TITAN_E_INVALID, "null springs.ends or springs.k" + at);
         for (uint32_t i = 0; i < m.n; ++i) {
             if (!(m.mass[i] > 0) || !std::isfinite(m.mass[i])) return bfail(nullptr, TITAN_E_INVALID, "mass must be finite and > 0" + at);
@@ -453,208 +409,23 @@ titan_status titan_batch_create(uint32_t n_systems, const titan_masses *masses, 
     } while (0)
     CK(cudaSetDevice(p->device));
 
-    // ---- host layout: per robot, the cluster size and per-CTA SELL blocks
-    struct CtaHost {
-        CtaDesc d;
-        std::vector<uint32_t> slices;
-        std::vector<float2> kl, act;
-        std::vector<uint16_t> nbr;   // own slot or halo slot per entry
-        std::vector<uint32_t> halo;  // rank << 16 | slot of each halo mass in its owner CTA
-    };
-    std::vector<std::vector<CtaHost>> per_robot(n_systems);
-    std::vector<uint32_t> cluster_of(n_systems);
-    uint32_t slot_cursor = 0;
-    for (uint32_t r = 0; r < n_systems; ++r) {
-        const titan_masses &m = masses[r];
-        const titan_springs &s = springs[r];
-        // incidence in input order: row of mass i = its half-edges (neighbour, spring)
-        std::vector<uint32_t> deg(m.n, 0);
-        for (uint32_t q = 0; q < s.n; ++q) { ++deg[s.ends[2 * (size_t)q]]; ++deg[s.ends[2 * (size_t)q + 1]]; }
-        std::vector<uint32_t> rowptr(m.n + 1, 0);
-        for (uint32_t i = 0; i < m.n; ++i) rowptr[i + 1] = rowptr[i] + deg[i];
-        std::vector<std::pair<uint32_t, uint32_t>> he(rowptr[m.n]);
-        std::vector<uint32_t> cur(rowptr.begin(), rowptr.end() - 1);
-        for (uint32_t q = 0; q < s.n; ++q) {
-            const uint32_t i = s.ends[2 * (size_t)q], j = s.ends[2 * (size_t)q + 1];
-            he[cur[i]++] = {j, q};
-            he[cur[j]++] = {i, q};
-        }
-        for (uint32_t i = 0; i < m.n; ++i) std::sort(he.begin() + rowptr[i], he.begin() + rowptr[i + 1]);
-        // distinct masses outside [q0, q1) that the rows of [q0, q1) touch
-        std::vector<uint32_t> mark(m.n, UINT32_MAX);
-        uint32_t gen = 0;
-        auto halo_count = [&](uint32_t q0, uint32_t q1) {
-            ++gen;                                    // a fresh mark for every call
-            uint32_t cnt = 0;
-            for (uint32_t i = q0; i < q1; ++i)
-                for (uint32_t r2 = rowptr[i]; r2 < rowptr[i + 1]; ++r2) {
-                    const uint32_t j = he[r2].first;
-                    if ((j < q0 || j >= q1) && mark[j] != gen) { mark[j] = gen; ++cnt; }
-                }
-            return cnt;
-        };
-        // smallest cluster whose per-CTA shared memory fits
-        uint32_t C = 1;
-        for (;; C *= 2) {
-            if (C > (uint32_t)kMaxCluster)
-                return bail(bfail(b, TITAN_E_UNSUPPORTED, "system " + std::to_string(r) + " does not fit a cluster of 8 CTAs"));
-            const uint32_t per = ((m.n + C - 1) / C + 31) & ~31u;
-            if (per > kMaxPerCta) continue;
-            // the layout of every CTA of the cluster reserves the largest halo
-            uint32_t hc = 0;
-            if (C > 1)
-                for (uint32_t q0 = 0; q0 < m.n; q0 += per) hc = std::max(hc, halo_count(q0, std::min(m.n, q0 + per)));
-            size_t worst = 0;
-            for (uint32_t q0 = 0; q0 < m.n; q0 += per) {
-                uint32_t edges = 0, ns = 0;
-                for (uint32_t sl = q0; sl < std::min(m.n, q0 + per); sl += 32, ++ns) {
-                    uint32_t w = 0;
-                    for (uint32_t i = sl; i < std::min(m.n, sl + 32); ++i) w = std::max(w, deg[i]);
-                    edges += 32 * ((w + 1) & ~1u);
-                }
-                edges = (edges + 63) & ~63u;
-                worst = std::max<size_t>(worst, smem_layout(per, hc, ns, edges, any_act).total);
-            }
-            if (worst <= kBatchSmemLimit && per + hc <= 65535) break;
-        }
-        cluster_of[r] = C;
-        const uint32_t per = ((m.n + C - 1) / C + 31) & ~31u;
-        b->mass_off.push_back(slot_cursor);
-        b->mass_cnt.push_back(m.n);
-        for (uint32_t q = 0; q < C; ++q) {
-            CtaHost h;
-            const uint32_t m0 = std::min(m.n, q * per), m1 = std::min(m.n, m0 + per);
-            h.d = CtaDesc{slot_cursor + m0, m1 - m0, per, 0, 0, 0, 0, r, 0, 0, 0};
-            // SELL of the CTA's masses, neighbours as own slots (j - m0) or halo slots (per + h)
-            std::fill(mark.begin(), mark.end(), UINT32_MAX);      // here: halo slot of a mass
-            auto slot_of = [&](uint32_t j) -> uint16_t {
-                if (j >= m0 && j < m1) return (uint16_t)(j - m0);
-                if (mark[j] == UINT32_MAX) {
-                    mark[j] = per + (uint32_t)h.halo.size();
-                    h.halo.push_back(((j / per) << 16) | (j % per));
-                }
-                return (uint16_t)mark[j];
-            };
-            h.slices.push_back(0);
-            for (uint32_t sl = m0; sl < m0 + per; sl += 32) {
-                uint32_t w = 0;
-                for (uint32_t i = sl; i < std::min(m1, sl + 32); ++i) w = std::max(w, deg[i]);
-                w = (w + 1) & ~1u;
-                const uint32_t base = (uint32_t)h.kl.size();
-                h.kl.resize(base + 32 * w, make_float2(0.f, 0.f));
-                h.act.resize(base + 32 * w, make_float2(0.f, 0.f));
-                h.nbr.resize(base + 32 * w, 0);
-                for (uint32_t l = 0; l < 32; ++l) {
-                    const uint32_t i = sl + l;
-                    for (uint32_t t = 0; t < w; ++t) {
-                        const uint32_t e = base + 32 * t + l;
-                        if (i < m1 && t < deg[i]) {
-                            const auto &x = he[rowptr[i] + t];
-                            const uint32_t j = x.first, q2 = x.second;
-                            h.nbr[e] = slot_of(j);
-                            double L;
-                            if (s.rest) L = s.rest[q2];
-                            else {
-                                double d2 = 0;
-                                for (int a = 0; a < 3; ++a) {
-                                    const double dd = m.pos[3 * (size_t)j + a] - m.pos[3 * (size_t)i + a];
-                                    d2 += dd * dd;
-                                }
-                                L = std::sqrt(d2);
-                            }
-                            h.kl[e] = make_float2((float)s.k[q2], (float)L);
-                            if (any_act && act[r].amp)
-                                h.act[e] = make_float2((float)(act[r].amp[q2] * std::cos(act[r].phase[q2])),
-                                                       (float)(act[r].amp[q2] * std::sin(act[r].phase[q2])));
-                        } else {
-                            const uint32_t self = std::min(i, m.n - 1);   // zero-parameter padding
-                            h.nbr[e] = slot_of(self);
-                        }
-                    }
-                }
-                h.slices.push_back((uint32_t)h.kl.size());
-            }
-            const uint32_t E = ((uint32_t)h.kl.size() + 63) & ~63u;
-            h.kl.resize(E, make_float2(0.f, 0.f));
-            h.act.resize(E, make_float2(0.f, 0.f));
-            h.nbr.resize(E, 0);
-            h.d.edge_count = E;
-            h.d.n_slices = (uint32_t)h.slices.size() - 1;
-            h.d.halo_count = (uint32_t)h.halo.size();
-            per_robot[r].push_back(std::move(h));
-        }
-        uint32_t halo_slots = 0;
-        for (const auto &hh : per_robot[r]) halo_slots = std::max(halo_slots, hh.d.halo_count);
-        for (auto &hh : per_robot[r]) hh.d.halo_slots = halo_slots;
-        slot_cursor += C * per;
-        // initial state of every slot of this robot (padding slots: fixed, at rest)
-        b->init_state.resize(slot_cursor);
-        for (uint32_t k = 0; k < C * per; ++k) {
-            MassState st{};
-            if (k < m.n) {
-                const double im = (m.fixed && m.fixed[k]) ? 0.0 : 1.0 / m.mass[k];
-                st.p = make_float4((float)m.pos[3 * (size_t)k], (float)m.pos[3 * (size_t)k + 1], (float)m.pos[3 * (size_t)k + 2], (float)im);
-                if (m.vel) st.v = make_float4((float)m.vel[3 * (size_t)k], (float)m.vel[3 * (size_t)k + 1], (float)m.vel[3 * (size_t)k + 2], 0.f);
-            }
-            b->init_state[b->mass_off[r] + k] = st;
-        }
+    // ---- host layout (layout.cpp): clusters, per-CTA rows and halos, launch groups
+    titan::BatchHost L;
+    std::string why;
+    if (!titan::build_batch(n_systems, masses, springs, act, L, &why))
+        return bail(bfail(b, TITAN_E_UNSUPPORTED, why));
+    b->mass_off = L.mass_off;
+    b->mass_cnt = L.mass_cnt;
+    b->init_state = std::move(L.init_state);
+    b->total_slots = L.total_slots;
+    for (const titan::BatchGroup &lg : L.groups) {
+        Group g;
+        g.cluster = lg.cluster;
+        g.cta_first = lg.cta_first;
+        g.cta_count = lg.cta_count;
+        g.smem = lg.smem;
+        b->groups.push_back(g);
     }
-    b->total_slots = slot_cursor;
-    // Groups: one launch per (cluster size, shared-memory class).  A launch's
-    // dynamic shared memory is the largest of its CTAs', so small robots get
-    // a class of their own and several of their CTAs share an SM (class k: at
-    // most 1/k of an SM's 228 KB); robots in decreasing size within a group.
-    static const uint32_t kPerSm[] = {1, 2, 3, 4, 6, 8};
-    auto smem_class = [&](uint32_t r) {
-        size_t worst = 0;
-        for (const auto &h : per_robot[r])
-            worst = std::max<size_t>(worst, smem_layout(h.d.slot_count, h.d.halo_slots, h.d.n_slices, h.d.edge_count, any_act).total);
-        uint32_t cls = 0;
-        for (uint32_t k = 0; k < sizeof(kPerSm) / sizeof(kPerSm[0]); ++k)
-            if (worst + 1024 <= 228u * 1024u / kPerSm[k]) cls = k;
-        return cls;
-    };
-    std::vector<uint32_t> class_of(n_systems);
-    for (uint32_t r = 0; r < n_systems; ++r) class_of[r] = smem_class(r);
-    std::vector<uint32_t> order(n_systems);
-    for (uint32_t r = 0; r < n_systems; ++r) order[r] = r;
-    std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
-        if (cluster_of[x] != cluster_of[y]) return cluster_of[x] > cluster_of[y];
-        if (class_of[x] != class_of[y]) return class_of[x] < class_of[y];
-        return masses[x].n > masses[y].n;
-    });
-    std::vector<CtaDesc> descs;
-    std::vector<uint32_t> slices;
-    std::vector<float2> kl, ac;
-    std::vector<uint16_t> nb;
-    std::vector<uint32_t> hl;
-    for (uint32_t k = 0; k < n_systems; ++k) {
-        const uint32_t r = order[k];
-        if (b->groups.empty() || b->groups.back().cluster != cluster_of[r] || class_of[order[k - 1]] != class_of[r]) {
-            Group g;
-            g.cluster = cluster_of[r];
-            g.cta_first = (uint32_t)descs.size();
-            b->groups.push_back(g);
-        }
-        Group &g = b->groups.back();
-        for (auto &h : per_robot[r]) {
-            h.d.edge_off = (uint32_t)kl.size();
-            while (slices.size() % 4) slices.push_back(0);
-            h.d.slice_base = (uint32_t)slices.size();
-            slices.insert(slices.end(), h.slices.begin(), h.slices.end());
-            while (slices.size() % 4) slices.push_back(0);
-            kl.insert(kl.end(), h.kl.begin(), h.kl.end());
-            ac.insert(ac.end(), h.act.begin(), h.act.end());
-            nb.insert(nb.end(), h.nbr.begin(), h.nbr.end());
-            h.d.halo_off = (uint32_t)hl.size();
-            hl.insert(hl.end(), h.halo.begin(), h.halo.end());
-            descs.push_back(h.d);
-            ++g.cta_count;
-            g.smem = std::max<size_t>(g.smem, smem_layout(h.d.slot_count, h.d.halo_slots, h.d.n_slices, h.d.edge_count, any_act).total);
-        }
-        per_robot[r].clear();
-    }
-    for (auto &g : b->groups) g.threads = g.cluster > 1 ? 256 : 256;
 
     // ---- device
     if (p->stream) b->stream = static_cast<cudaStream_t>(p->stream);
@@ -668,25 +439,27 @@ titan_status titan_batch_create(uint32_t n_systems, const titan_masses *masses, 
         CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         b->group_events.push_back(e);
     }
-    CK(balloc(b, &b->d_ctas, descs.size()));
+    static_assert(sizeof(MassState) == 8 * sizeof(float), "state slot = 8 floats");
+    const size_t E = L.nbr.size();
+    CK(balloc(b, &b->d_ctas, L.ctas.size()));
     CK(balloc(b, &b->d_state[0], b->total_slots));
     CK(balloc(b, &b->d_state[1], b->total_slots));
-    CK(balloc(b, &b->d_slice, slices.size()));
-    CK(balloc(b, &b->d_kl, kl.size()));
-    if (any_act) CK(balloc(b, &b->d_act, ac.size()));
-    CK(balloc(b, &b->d_nbr, nb.size()));
-    CK(balloc(b, &b->d_halo, std::max<size_t>(hl.size(), 1)));
+    CK(balloc(b, &b->d_slice, L.slices.size()));
+    CK(balloc(b, &b->d_kl, E));
+    if (L.any_act) CK(balloc(b, &b->d_act, E));
+    CK(balloc(b, &b->d_nbr, E));
+    CK(balloc(b, &b->d_halo, std::max<size_t>(L.halo.size(), 1)));
     CK(balloc(b, &b->d_moff, n_systems));
     CK(balloc(b, &b->d_mcnt, n_systems));
     CK(balloc(b, &b->d_centroid, 3 * (size_t)n_systems));
     CK(balloc(b, &b->d_err, 1));
-    CK(cudaMemcpy(b->d_ctas, descs.data(), descs.size() * sizeof(CtaDesc), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(b->d_state[0], b->init_state.data(), b->init_state.size() * sizeof(MassState), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(b->d_slice, slices.data(), slices.size() * 4, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(b->d_kl, kl.data(), kl.size() * sizeof(float2), cudaMemcpyHostToDevice));
-    if (any_act) CK(cudaMemcpy(b->d_act, ac.data(), ac.size() * sizeof(float2), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(b->d_nbr, nb.data(), nb.size() * 2, cudaMemcpyHostToDevice));
-    if (!hl.empty()) CK(cudaMemcpy(b->d_halo, hl.data(), hl.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(b->d_ctas, L.ctas.data(), L.ctas.size() * sizeof(BatchCta), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(b->d_state[0], b->init_state.data(), b->init_state.size() * sizeof(float), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(b->d_slice, L.slices.data(), L.slices.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(b->d_kl, L.kl.data(), L.kl.size() * sizeof(float), cudaMemcpyHostToDevice));
+    if (L.any_act) CK(cudaMemcpy(b->d_act, L.act.data(), L.act.size() * sizeof(float), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(b->d_nbr, L.nbr.data(), E * 2, cudaMemcpyHostToDevice));
+    if (!L.halo.empty()) CK(cudaMemcpy(b->d_halo, L.halo.data(), L.halo.size() * 4, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(b->d_moff, b->mass_off.data(), n_systems * 4, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(b->d_mcnt, b->mass_cnt.data(), n_systems * 4, cudaMemcpyHostToDevice));
     CK(cudaMemset(b->d_err, 0, sizeof(int)));
@@ -739,7 +512,7 @@ titan_status titan_batch_reset(titan_batch *b) {
     if (!b) return bfail(nullptr, TITAN_E_INVALID, "batch is null");
     BusyB g(b);
     if (!g.acquired) return bfail(b, TITAN_E_BUSY, "another call on this batch is in progress");
-    BATCH_CK(b, cudaMemcpyAsync(b->d_state[b->cur], b->init_state.data(), b->init_state.size() * sizeof(MassState),
+    BATCH_CK(b, cudaMemcpyAsync(b->d_state[b->cur], b->init_state.data(), b->init_state.size() * sizeof(float),
                                 cudaMemcpyHostToDevice, b->stream));
     BATCH_CK(b, cudaStreamSynchronize(b->stream));
     b->steps = 0;

@@ -1,4 +1,5 @@
-// layout.cpp -- host-side construction of the device layouts (run once per titan_create).
+// layout.cpp -- host-side construction of the device layouts (run once per titan_create,
+// and once per titan_batch_create for the batch layout at the end).
 //
 // Morton order: masses are sorted by the 63-bit Morton code of their position
 // quantised to 2^21 cells per axis over the bounding cube, so that masses that
@@ -23,6 +24,8 @@
 #include <cstdlib>
 #include <climits>
 #include <numeric>
+#include <string>
+#include <utility>
 
 namespace titan {
 
@@ -672,6 +675,219 @@ bool plan_persistent(uint32_t n, const std::vector<uint32_t> &slice_off, const s
     for (int r = 0; r < 9; ++r) plan.halo_off[r] = t.halo_off[r];
     slot.swap(t.slot);
     halo.swap(t.halo);
+    return true;
+}
+
+
+bool build_batch(uint32_t n_systems, const titan_masses *masses, const titan_springs *springs,
+                 const titan_actuation *act, BatchHost &out, std::string *why) {
+    out = BatchHost();
+    bool any_act = false;
+    for (uint32_t r = 0; r < n_systems; ++r)
+        if (act && act[r].amp) any_act = true;
+    out.any_act = any_act;
+    // per system: the CTAs' rows, halo lists and descriptors (offsets into
+    // the global arrays are set when the CTAs are placed in launch order)
+    struct CtaHost {
+        BatchCta d;
+        std::vector<uint32_t> slices;
+        std::vector<float> kl, act;
+        std::vector<uint16_t> nbr;   // own slot or halo slot per entry
+        std::vector<uint32_t> halo;  // rank << 16 | slot of each halo mass in its owner CTA
+    };
+    std::vector<std::vector<CtaHost>> per_sys(n_systems);
+    std::vector<uint32_t> cluster_of(n_systems);
+    uint32_t slot_cursor = 0;
+    for (uint32_t r = 0; r < n_systems; ++r) {
+        const titan_masses &m = masses[r];
+        const titan_springs &s = springs[r];
+        const bool sys_act = act && act[r].amp;
+        // incidence in caller order: row of mass i = its half-edges (neighbour, spring), sorted
+        std::vector<uint32_t> deg(m.n, 0);
+        for (uint32_t q = 0; q < s.n; ++q) { ++deg[s.ends[2 * (size_t)q]]; ++deg[s.ends[2 * (size_t)q + 1]]; }
+        std::vector<uint32_t> rowptr(m.n + 1, 0);
+        for (uint32_t i = 0; i < m.n; ++i) rowptr[i + 1] = rowptr[i] + deg[i];
+        std::vector<std::pair<uint32_t, uint32_t>> he(rowptr[m.n]);
+        std::vector<uint32_t> cur(rowptr.begin(), rowptr.end() - 1);
+        for (uint32_t q = 0; q < s.n; ++q) {
+            const uint32_t i = s.ends[2 * (size_t)q], j = s.ends[2 * (size_t)q + 1];
+            he[cur[i]++] = {j, q};
+            he[cur[j]++] = {i, q};
+        }
+        for (uint32_t i = 0; i < m.n; ++i) std::sort(he.begin() + rowptr[i], he.begin() + rowptr[i + 1]);
+        // distinct masses outside [q0, q1) that the rows of [q0, q1) touch
+        std::vector<uint32_t> mark(m.n, UINT32_MAX);
+        uint32_t gen = 0;
+        auto halo_count = [&](uint32_t q0, uint32_t q1) {
+            ++gen;                                    // a fresh mark for every call
+            uint32_t cnt = 0;
+            for (uint32_t i = q0; i < q1; ++i)
+                for (uint32_t r2 = rowptr[i]; r2 < rowptr[i + 1]; ++r2) {
+                    const uint32_t j = he[r2].first;
+                    if ((j < q0 || j >= q1) && mark[j] != gen) { mark[j] = gen; ++cnt; }
+                }
+            return cnt;
+        };
+        // smallest cluster whose per-CTA shared memory fits
+        uint32_t C = 1;
+        for (;; C *= 2) {
+            if (C > kBatchMaxCluster) {
+                if (why) *why = "system " + std::to_string(r) + " does not fit a cluster of 8 CTAs";
+                out = BatchHost();
+                return false;
+            }
+            const uint32_t per = ((m.n + C - 1) / C + 31) & ~31u;
+            if (per > kBatchMaxPerCta) continue;
+            // the layout of every CTA of the cluster reserves the largest halo
+            uint32_t hc = 0;
+            if (C > 1)
+                for (uint32_t q0 = 0; q0 < m.n; q0 += per) hc = std::max(hc, halo_count(q0, std::min(m.n, q0 + per)));
+            size_t worst = 0;
+            for (uint32_t q0 = 0; q0 < m.n; q0 += per) {
+                uint32_t edges = 0, ns = 0;
+                for (uint32_t sl = q0; sl < std::min(m.n, q0 + per); sl += 32, ++ns) {
+                    uint32_t w = 0;
+                    for (uint32_t i = sl; i < std::min(m.n, sl + 32); ++i) w = std::max(w, deg[i]);
+                    edges += 32 * ((w + 1) & ~1u);
+                }
+                edges = (edges + 63) & ~63u;
+                worst = std::max<size_t>(worst, batch_smem_layout(per, hc, ns, edges, any_act).total);
+            }
+            if (worst <= kBatchSmemLimit && per + hc <= 65535) break;
+        }
+        cluster_of[r] = C;
+        const uint32_t per = ((m.n + C - 1) / C + 31) & ~31u;
+        out.mass_off.push_back(slot_cursor);
+        out.mass_cnt.push_back(m.n);
+        for (uint32_t q = 0; q < C; ++q) {
+            CtaHost h;
+            const uint32_t m0 = std::min(m.n, q * per), m1 = std::min(m.n, m0 + per);
+            h.d = BatchCta{slot_cursor + m0, m1 - m0, per, 0, 0, 0, 0, r, 0, 0, 0};
+            // neighbours as own slots (j - m0) or halo slots (per + h)
+            std::fill(mark.begin(), mark.end(), UINT32_MAX);      // here: halo slot of a mass
+            auto slot_of = [&](uint32_t j) -> uint16_t {
+                if (j >= m0 && j < m1) return (uint16_t)(j - m0);
+                if (mark[j] == UINT32_MAX) {
+                    mark[j] = per + (uint32_t)h.halo.size();
+                    h.halo.push_back(((j / per) << 16) | (j % per));
+                }
+                return (uint16_t)mark[j];
+            };
+            h.slices.push_back(0);
+            for (uint32_t sl = m0; sl < m0 + per; sl += 32) {
+                uint32_t w = 0;
+                for (uint32_t i = sl; i < std::min(m1, sl + 32); ++i) w = std::max(w, deg[i]);
+                w = (w + 1) & ~1u;
+                const uint32_t base = (uint32_t)h.nbr.size();
+                h.kl.resize(2 * (size_t)(base + 32 * w), 0.f);
+                h.act.resize(2 * (size_t)(base + 32 * w), 0.f);
+                h.nbr.resize(base + 32 * w, 0);
+                for (uint32_t l = 0; l < 32; ++l) {
+                    const uint32_t i = sl + l;
+                    for (uint32_t t = 0; t < w; ++t) {
+                        const uint32_t e = base + 32 * t + l;
+                        if (i < m1 && t < deg[i]) {
+                            const auto &x = he[rowptr[i] + t];
+                            const uint32_t j = x.first, q2 = x.second;
+                            h.nbr[e] = slot_of(j);
+                            double L;
+                            if (s.rest) L = s.rest[q2];
+                            else {
+                                double d2 = 0;
+                                for (int a = 0; a < 3; ++a) {
+                                    const double dd = m.pos[3 * (size_t)j + a] - m.pos[3 * (size_t)i + a];
+                                    d2 += dd * dd;
+                                }
+                                L = std::sqrt(d2);
+                            }
+                            h.kl[2 * (size_t)e] = (float)s.k[q2];
+                            h.kl[2 * (size_t)e + 1] = (float)L;
+                            if (sys_act) {
+                                h.act[2 * (size_t)e] = (float)(act[r].amp[q2] * std::cos(act[r].phase[q2]));
+                                h.act[2 * (size_t)e + 1] = (float)(act[r].amp[q2] * std::sin(act[r].phase[q2]));
+                            }
+                        } else {
+                            const uint32_t self = std::min(i, m.n - 1);   // zero-parameter padding
+                            h.nbr[e] = slot_of(self);
+                        }
+                    }
+                }
+                h.slices.push_back((uint32_t)h.nbr.size());
+            }
+            const uint32_t E = ((uint32_t)h.nbr.size() + 63) & ~63u;
+            h.kl.resize(2 * (size_t)E, 0.f);
+            h.act.resize(2 * (size_t)E, 0.f);
+            h.nbr.resize(E, 0);
+            h.d.edge_count = E;
+            h.d.n_slices = (uint32_t)h.slices.size() - 1;
+            h.d.halo_count = (uint32_t)h.halo.size();
+            per_sys[r].push_back(std::move(h));
+        }
+        uint32_t halo_slots = 0;
+        for (const auto &hh : per_sys[r]) halo_slots = std::max(halo_slots, hh.d.halo_count);
+        for (auto &hh : per_sys[r]) hh.d.halo_slots = halo_slots;
+        slot_cursor += C * per;
+        // initial state of every slot of this system (padding slots: fixed, at rest)
+        out.init_state.resize(8 * (size_t)slot_cursor, 0.f);
+        for (uint32_t k = 0; k < m.n; ++k) {
+            float *st = &out.init_state[8 * (size_t)(out.mass_off[r] + k)];
+            for (int a = 0; a < 3; ++a) {
+                st[a] = (float)m.pos[3 * (size_t)k + a];
+                st[4 + a] = m.vel ? (float)m.vel[3 * (size_t)k + a] : 0.f;
+            }
+            st[3] = (m.fixed && m.fixed[k]) ? 0.f : (float)(1.0 / m.mass[k]);
+        }
+    }
+    out.total_slots = slot_cursor;
+    // launch groups by (cluster size, shared-memory class); a launch's
+    // dynamic shared memory is the largest of its CTAs'
+    static const uint32_t kPerSm[] = {1, 2, 3, 4, 6, 8};
+    auto smem_class = [&](uint32_t r) {
+        size_t worst = 0;
+        for (const auto &h : per_sys[r])
+            worst = std::max<size_t>(worst, batch_smem_layout(h.d.slot_count, h.d.halo_slots, h.d.n_slices,
+                                                              h.d.edge_count, any_act).total);
+        uint32_t cls = 0;
+        for (uint32_t k = 0; k < sizeof(kPerSm) / sizeof(kPerSm[0]); ++k)
+            if (worst + 1024 <= 228u * 1024u / kPerSm[k]) cls = k;
+        return cls;
+    };
+    std::vector<uint32_t> class_of(n_systems);
+    for (uint32_t r = 0; r < n_systems; ++r) class_of[r] = smem_class(r);
+    std::vector<uint32_t> order(n_systems);
+    for (uint32_t r = 0; r < n_systems; ++r) order[r] = r;
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
+        if (cluster_of[x] != cluster_of[y]) return cluster_of[x] > cluster_of[y];
+        if (class_of[x] != class_of[y]) return class_of[x] < class_of[y];
+        return masses[x].n > masses[y].n;
+    });
+    for (uint32_t k = 0; k < n_systems; ++k) {
+        const uint32_t r = order[k];
+        if (out.groups.empty() || out.groups.back().cluster != cluster_of[r] || class_of[order[k - 1]] != class_of[r]) {
+            BatchGroup g;
+            g.cluster = cluster_of[r];
+            g.cta_first = (uint32_t)out.ctas.size();
+            out.groups.push_back(g);
+        }
+        BatchGroup &g = out.groups.back();
+        for (auto &h : per_sys[r]) {
+            h.d.edge_off = (uint32_t)out.nbr.size();
+            while (out.slices.size() % 4) out.slices.push_back(0);
+            h.d.slice_base = (uint32_t)out.slices.size();
+            out.slices.insert(out.slices.end(), h.slices.begin(), h.slices.end());
+            while (out.slices.size() % 4) out.slices.push_back(0);
+            out.kl.insert(out.kl.end(), h.kl.begin(), h.kl.end());
+            if (any_act) out.act.insert(out.act.end(), h.act.begin(), h.act.end());
+            out.nbr.insert(out.nbr.end(), h.nbr.begin(), h.nbr.end());
+            h.d.halo_off = (uint32_t)out.halo.size();
+            out.halo.insert(out.halo.end(), h.halo.begin(), h.halo.end());
+            out.ctas.push_back(h.d);
+            ++g.cta_count;
+            g.smem = std::max<size_t>(g.smem, batch_smem_layout(h.d.slot_count, h.d.halo_slots, h.d.n_slices,
+                                                                h.d.edge_count, any_act).total);
+        }
+        per_sys[r].clear();
+    }
     return true;
 }
 

@@ -1,9 +1,13 @@
 // layout.h -- host-side builders of the device layouts (see layout.cpp).
 #pragma once
 
+#include <stddef.h>
 #include <stdint.h>
 
+#include <string>
 #include <vector>
+
+#include "titan.h"
 
 namespace titan {
 
@@ -194,5 +198,95 @@ size_t persistent_smem_bytes(uint32_t per_cta, uint32_t max_halo, uint32_t max_e
 bool plan_persistent(uint32_t n, const std::vector<uint32_t> &slice_off, const std::vector<uint32_t> &nbr,
                      bool has_c, bool has_act, size_t smem_limit, PersistPlan &plan,
                      std::vector<uint16_t> &slot, std::vector<uint32_t> &halo);
+
+// ---- batches of independent systems (see batch.cu)
+//
+// Every system is owned by one thread-block cluster of C CTAs (C = 1, 2, 4 or
+// 8, the smallest whose CTAs fit kBatchSmemLimit).  CTA q of a system owns its
+// masses [q P, (q + 1) P) in caller order, P = ceil(n / C) rounded up to 32,
+// at global state slots mass_begin .. mass_begin + P (slots past the system's
+// last mass are padding: fixed, at rest).  The CTA's rows are SELL-32 over its
+// P slots (slices of 32 masses, widths even, padding entries {k, L0} = {0, 0}
+// pointing at the mass itself, or at the system's last mass for slots past
+// it); each entry names its neighbour by a slot of the CTA's table: own
+// masses at [0, P), other CTAs' masses - the halo - at [P, P + halo_count),
+// halo entry h being (owner rank << 16 | owner slot).  A row keeps its
+// springs in the order of (neighbour, spring) in caller numbering.
+
+constexpr uint32_t kBatchMaxCluster = 8;
+constexpr uint32_t kBatchMaxPerCta = 4096;          // masses per CTA
+constexpr size_t kBatchSmemLimit = 220 * 1024;      // shared memory per CTA
+
+// Per-CTA descriptor.  All offsets are in elements of the arrays they index.
+struct BatchCta {
+    uint32_t mass_begin;    // first global state slot of this CTA
+    uint32_t mass_count;    // masses owned (<= kBatchMaxPerCta)
+    uint32_t slot_count;    // P, a multiple of 32 (the same for every CTA of a system)
+    uint32_t edge_off;      // first SELL entry (multiple of 64)
+    uint32_t edge_count;    // SELL entries (multiple of 64)
+    uint32_t slice_base;    // first relative slice offset (multiple of 4)
+    uint32_t n_slices;      // P / 32
+    uint32_t robot;         // system index
+    uint32_t halo_off;      // first entry of this CTA's halo list
+    uint32_t halo_count;    // masses of other CTAs of the cluster its rows touch
+    uint32_t halo_slots;    // halo slots in the layout: the largest halo_count of the system's CTAs, so
+                            // that every CTA of a cluster has its state buffers at the same offsets
+};
+
+// Shared-memory image of one CTA (byte offsets, all 16-byte aligned): two
+// state buffers of (own + halo) slots split into (x, y, z, vx) float4 and
+// (vy, vz) float2 arrays, 1/m of the own slots, the relative slice offsets,
+// {k, L0} per entry, the actuation pair per entry (if any), the slot per entry.
+struct BatchSmem {
+    uint32_t a0, b0, a1, b1, inv, slices, kl, act, nbr, total;
+};
+
+TITAN_HD inline BatchSmem batch_smem_layout(uint32_t slots, uint32_t halo, uint32_t n_slices, uint32_t edges,
+                                            bool act) {
+    const uint32_t tab = slots + halo;
+    BatchSmem L;
+    L.a0 = 0;
+    L.b0 = L.a0 + tab * 16;
+    L.a1 = al16(L.b0 + tab * 8);
+    L.b1 = L.a1 + tab * 16;
+    L.inv = al16(L.b1 + tab * 8);
+    L.slices = al16(L.inv + slots * 4);
+    L.kl = al16(L.slices + 4 * ((n_slices + 1 + 3) & ~3u));
+    L.act = L.kl + edges * 8;
+    L.nbr = L.act + (act ? edges * 8 : 0);
+    L.total = al16(L.nbr + edges * 2);
+    return L;
+}
+
+// One launch: the CTAs [cta_first, cta_first + cta_count) of clusters of
+// `cluster` CTAs, dynamic shared memory `smem` (the largest of its CTAs).
+// Launches are split by cluster size and by shared-memory class (at most 1/k
+// of an SM's 228 KB, k = 1, 2, 3, 4, 6, 8) so small systems share an SM.
+struct BatchGroup {
+    uint32_t cluster = 1;
+    uint32_t cta_first = 0, cta_count = 0;
+    size_t smem = 0;
+};
+
+struct BatchHost {
+    std::vector<BatchCta> ctas;          // launch order: by group, systems in decreasing size within a group
+    std::vector<BatchGroup> groups;
+    std::vector<uint32_t> slices;        // relative slice offsets of every CTA (each run padded to 4)
+    std::vector<float> kl;               // [E][2] {k, L0}
+    std::vector<float> act;              // [E][2] {A cos phi, A sin phi} (empty if no system is actuated)
+    std::vector<uint16_t> nbr;           // [E] table slot of the neighbour
+    std::vector<uint32_t> halo;          // halo lists of every CTA
+    std::vector<uint32_t> mass_off;      // [systems] first global state slot
+    std::vector<uint32_t> mass_cnt;      // [systems] masses
+    std::vector<float> init_state;       // [slots][8] x, y, z, 1/m, vx, vy, vz, 0 (FP32 of the caller's values)
+    uint32_t total_slots = 0;
+    bool any_act = false;
+};
+
+// Builds the layout of n_systems validated systems (act may be null; act[r].amp
+// null: system r is not actuated).  False, with the reason in *why, if a
+// system fits no cluster of kBatchMaxCluster CTAs.
+bool build_batch(uint32_t n_systems, const titan_masses *masses, const titan_springs *springs,
+                 const titan_actuation *act, BatchHost &out, std::string *why);
 
 }  // namespace titan

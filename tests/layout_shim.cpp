@@ -1,5 +1,6 @@
 // layout_shim.cpp -- exposes the library's host-side layout builders
-// (paper_1911_10274_gb300/csrc/layout.cpp) through a C interface so that the
+// (paper_1911_10274_gb300/csrc/layout.cpp: single-system tables, the
+// persistent plan and the batch layout) through a C interface so that the
 // CPU tests can check the device layouts without a GPU.  Test infrastructure:
 // compiled by tests/test_layout_host.py together with layout.cpp.
 #include <cstring>
@@ -132,6 +133,79 @@ void shim_get(const char *name, void *dst) {
     if (k == "box_dims") copy_out(g.box.dims, dst);
     if (k == "pslot") copy_out(g.pslot, dst);
     if (k == "phalo") copy_out(g.phalo, dst);
+}
+
+// ---- batch layout (titan_batch_create's host part)
+
+namespace {
+titan::BatchHost bh;
+std::string bwhy;
+}  // namespace
+
+// Builds the batch layout of n systems.  Returns 1 on success, 0 if refused
+// (reason: shim_batch_why).
+int shim_build_batch(uint32_t n, const titan_masses *m, const titan_springs *s, const titan_actuation *a) {
+    bwhy.clear();
+    return titan::build_batch(n, m, s, a, bh, &bwhy) ? 1 : 0;
+}
+
+const char *shim_batch_why() { return bwhy.c_str(); }
+
+// 0 total_slots, 1 any_act, 2 CTAs, 3 groups.
+uint64_t shim_batch_scalar(int which) {
+    switch (which) {
+        case 0: return bh.total_slots;
+        case 1: return bh.any_act ? 1 : 0;
+        case 2: return bh.ctas.size();
+        case 3: return bh.groups.size();
+        default: return 0;
+    }
+}
+
+// Shared memory of one CTA image (the kernel's own formula).
+uint64_t shim_batch_smem(uint32_t slots, uint32_t halo, uint32_t n_slices, uint32_t edges, int act) {
+    return titan::batch_smem_layout(slots, halo, n_slices, edges, act != 0).total;
+}
+
+// Arrays: "ctas" as 11 uint32 per CTA (BatchCta field order), "groups" as 4
+// uint64 per group (cluster, cta_first, cta_count, smem), then slices, kl,
+// act, nbr, halo, mass_off, mass_cnt, init_state as stored.
+uint64_t shim_batch_len(const char *name) {
+    const std::string k(name);
+    if (k == "ctas") return bh.ctas.size() * 11;
+    if (k == "groups") return bh.groups.size() * 4;
+    if (k == "slices") return bh.slices.size();
+    if (k == "kl") return bh.kl.size();
+    if (k == "act") return bh.act.size();
+    if (k == "nbr") return bh.nbr.size();
+    if (k == "halo") return bh.halo.size();
+    if (k == "mass_off") return bh.mass_off.size();
+    if (k == "mass_cnt") return bh.mass_cnt.size();
+    if (k == "init_state") return bh.init_state.size();
+    return 0;
+}
+
+void shim_batch_get(const char *name, void *dst) {
+    const std::string k(name);
+    static_assert(sizeof(titan::BatchCta) == 11 * sizeof(uint32_t), "BatchCta is 11 words");
+    if (k == "ctas") copy_out(bh.ctas, dst);
+    if (k == "groups") {
+        uint64_t *o = static_cast<uint64_t *>(dst);
+        for (size_t g = 0; g < bh.groups.size(); ++g) {
+            o[4 * g] = bh.groups[g].cluster;
+            o[4 * g + 1] = bh.groups[g].cta_first;
+            o[4 * g + 2] = bh.groups[g].cta_count;
+            o[4 * g + 3] = bh.groups[g].smem;
+        }
+    }
+    if (k == "slices") copy_out(bh.slices, dst);
+    if (k == "kl") copy_out(bh.kl, dst);
+    if (k == "act") copy_out(bh.act, dst);
+    if (k == "nbr") copy_out(bh.nbr, dst);
+    if (k == "halo") copy_out(bh.halo, dst);
+    if (k == "mass_off") copy_out(bh.mass_off, dst);
+    if (k == "mass_cnt") copy_out(bh.mass_cnt, dst);
+    if (k == "init_state") copy_out(bh.init_state, dst);
 }
 
 }  // extern "C"

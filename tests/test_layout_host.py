@@ -31,7 +31,7 @@ def shim(tmp_path_factory):
     if shutil.which("g++") is None:
         pytest.skip("no host C++ compiler")
     out = str(tmp_path_factory.mktemp("shim") / "liblayout_shim.so")
-    subprocess.run(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-I", CSRC,
+    subprocess.run(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-I", CSRC, "-I", os.path.join(ROOT, "include"),
                     os.path.join(CSRC, "layout.cpp"), os.path.join(ROOT, "tests", "layout_shim.cpp"),
                     "-o", out], check=True)
     lib = C.CDLL(out)
@@ -44,6 +44,15 @@ def shim(tmp_path_factory):
     lib.shim_plan.restype = C.c_int
     lib.shim_plan.argtypes = [C.c_uint64, C.c_int, C.c_int]
     lib.shim_plan_scalar.restype = C.c_uint64
+    lib.shim_build_batch.restype = C.c_int
+    lib.shim_build_batch.argtypes = [C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.shim_batch_why.restype = C.c_char_p
+    lib.shim_batch_scalar.restype = C.c_uint64
+    lib.shim_batch_smem.restype = C.c_uint64
+    lib.shim_batch_smem.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int]
+    lib.shim_batch_len.restype = C.c_uint64
+    lib.shim_batch_len.argtypes = [C.c_char_p]
+    lib.shim_batch_get.argtypes = [C.c_char_p, C.c_void_p]
     return lib
 
 
@@ -331,3 +340,204 @@ def test_cube_layout_refuses_second_neighbours_and_duplicates(shim):
     far = np.stack([idx[:, :, :-2].ravel(), idx[:, :, 2:].ravel()], 1)
     assert not Layout(shim, pos, np.concatenate([ends, far])).cube_ok
     assert not Layout(shim, pos, np.concatenate([ends, ends[:3]])).cube_ok
+
+
+# ---------------------------------------------------------------- batch layout
+
+class BatchLayout:
+    """titan_batch_create's host layout of a list of inputs.System, read back
+    through the shim."""
+    CTA_FIELDS = ("mass_begin", "mass_count", "slot_count", "edge_off", "edge_count", "slice_base", "n_slices",
+                  "robot", "halo_off", "halo_count", "halo_slots")
+    DT = {"ctas": np.uint32, "groups": np.uint64, "slices": np.uint32, "kl": np.float32, "act": np.float32,
+          "nbr": np.uint16, "halo": np.uint32, "mass_off": np.uint32, "mass_cnt": np.uint32,
+          "init_state": np.float32}
+
+    def __init__(self, lib, systems):
+        from paper_1911_10274_gb300 import titan as T
+        keep, ms, ss, acts = [], [], [], []
+        for sy in systems:
+            d = dict(pos=np.ascontiguousarray(sy.pos, np.float64), vel=np.ascontiguousarray(sy.vel, np.float64),
+                     mass=np.ascontiguousarray(sy.mass, np.float64), fixed=np.ascontiguousarray(sy.fixed, np.uint8),
+                     ends=np.ascontiguousarray(sy.ends, np.uint32), k=np.ascontiguousarray(sy.k, np.float64),
+                     rest=np.ascontiguousarray(sy.rest, np.float64))
+            ptr = lambda a: a.ctypes.data if a.size else None
+            ms.append(T.titan_masses(sy.n_masses, ptr(d["pos"]), ptr(d["vel"]), ptr(d["mass"]), ptr(d["fixed"])))
+            ss.append(T.titan_springs(sy.n_springs, ptr(d["ends"]), ptr(d["k"]), ptr(d["rest"]), None))
+            if sy.act_amp is not None:
+                d["amp"] = np.ascontiguousarray(sy.act_amp, np.float64)
+                d["phase"] = np.ascontiguousarray(sy.act_phase, np.float64)
+                acts.append(T.titan_actuation(ptr(d["amp"]), ptr(d["phase"]), float(sy.act_freq)))
+            else:
+                acts.append(T.titan_actuation(None, None, 0.0))
+            keep.append(d)
+        n = len(systems)
+        M = (T.titan_masses * max(1, n))(*ms)
+        S = (T.titan_springs * max(1, n))(*ss)
+        A = (T.titan_actuation * max(1, n))(*acts)
+        self.ok = lib.shim_build_batch(n, C.addressof(M), C.addressof(S), C.addressof(A)) == 1
+        self.why = lib.shim_batch_why().decode()
+        if not self.ok:
+            return
+        self.total_slots, self.any_act = int(lib.shim_batch_scalar(0)), bool(lib.shim_batch_scalar(1))
+        for name, dt in self.DT.items():
+            a = np.empty(int(lib.shim_batch_len(name.encode())), dt)
+            if a.size:
+                lib.shim_batch_get(name.encode(), a.ctypes.data)
+            setattr(self, name, a)
+        self.ctas = self.ctas.reshape(-1, 11).astype(np.int64)
+        self.groups = self.groups.reshape(-1, 4).astype(np.int64)
+        self.kl = self.kl.reshape(-1, 2)
+        self.act = self.act.reshape(-1, 2)
+        self.init_state = self.init_state.reshape(-1, 8)
+        self.cta = [dict(zip(self.CTA_FIELDS, row)) for row in self.ctas]
+
+
+def _batch_systems():
+    """Robots of every cluster size and shared-memory class, plus the
+    degenerate systems: one spring, no springs, fixed masses with velocities,
+    an unactuated system among actuated ones."""
+    rng = np.random.default_rng(5)
+    out = [inputs.actuated_box(a, b, c, rng) for a, b, c in
+           [(3, 3, 3), (12, 12, 12), (5, 4, 3), (14, 14, 14), (7, 3, 9), (10, 10, 10), (8, 8, 8), (4, 11, 6),
+            (3, 12, 3)]]
+    two = inputs.two_masses()
+    two.act_amp, two.act_phase = None, None
+    out.append(two)
+    lone = inputs.actuated_box(2, 1, 1, rng)
+    lone.ends = np.zeros((0, 2), np.uint32)
+    for f in ("k", "rest", "damping"):
+        setattr(lone, f, np.zeros(0))
+    lone.act_amp, lone.act_phase = None, None
+    out.append(lone)
+    fx = inputs.actuated_box(6, 5, 4, rng)
+    fx.fixed[:30] = 1
+    fx.vel[:] = rng.normal(0.0, 0.1, fx.vel.shape)
+    out.append(fx)
+    plain = inputs.actuated_box(9, 8, 7, rng)
+    plain.act_amp, plain.act_phase = None, None
+    out.append(plain)
+    return out
+
+
+def _decode_slot(L, c, rank, P, slot):
+    """Caller index (within its system) of the mass a table slot names."""
+    own = slot < P
+    j = np.where(own, rank * P + slot.astype(np.int64), 0)
+    if (~own).any():
+        code = L.halo[c["halo_off"] + slot[~own].astype(np.int64) - P].astype(np.int64)
+        j[~own] = (code >> 16) * P + (code & 0xFFFF)
+    return j
+
+
+def test_batch_layout_encodes_every_spring_and_every_index_stays_in_range(shim):
+    systems = _batch_systems()
+    L = BatchLayout(shim, systems)
+    assert L.ok, L.why
+    E = L.nbr.size
+    assert L.kl.shape[0] == E and (not L.any_act or L.act.shape[0] == E)
+    # groups: consecutive, cover every CTA, whole clusters, cluster sizes non-increasing
+    assert L.groups[0, 1] == 0 and L.groups[-1, 1] + L.groups[-1, 2] == len(L.cta)
+    assert np.all(L.groups[1:, 1] == L.groups[:-1, 1] + L.groups[:-1, 2])
+    assert np.all(L.groups[:, 2] % L.groups[:, 0] == 0) and np.all(np.diff(L.groups[:, 0]) <= 0)
+    assert set(L.groups[:, 0]) == {1, 2, 4, 8}
+    # incidence of every system: springs of mass i = inc[r][inc_ptr[r][i]:inc_ptr[r][i + 1]]
+    inc, inc_ptr = [], []
+    for sy in systems:
+        half = np.concatenate([sy.ends[:, 0], sy.ends[:, 1]]).astype(np.int64)
+        spr = np.concatenate([np.arange(sy.n_springs)] * 2)
+        o = np.argsort(half, kind="stable")
+        inc.append(spr[o])
+        inc_ptr.append(np.searchsorted(half[o], np.arange(sy.n_masses + 1)))
+    seen_robots = []
+    for cluster, first, count, smem in L.groups:
+        assert smem <= 220 * 1024
+        for c0 in range(first, first + count, cluster):
+            cl = L.cta[c0:c0 + cluster]
+            r = cl[0]["robot"]
+            sy = systems[r]
+            n = sy.n_masses
+            seen_robots.append(r)
+            P = cl[0]["slot_count"]
+            assert P % 32 == 0 and P <= 4096 and cluster * P >= n
+            for rank, c in enumerate(cl):
+                # one system and one state layout per cluster, CTA q at rank q
+                assert c["robot"] == r and c["slot_count"] == P
+                assert c["halo_slots"] == max(x["halo_count"] for x in cl)
+                m0, m1 = min(n, rank * P), min(n, rank * P + P)
+                assert c["mass_begin"] == L.mass_off[r] + m0 and c["mass_count"] == m1 - m0
+                assert c["mass_begin"] + P <= L.total_slots
+                # every array range the bulk copies and the kernel read
+                assert c["n_slices"] * 32 == P and c["slice_base"] % 4 == 0
+                assert c["slice_base"] + (c["n_slices"] + 4) // 4 * 4 <= L.slices.size
+                assert c["edge_off"] % 64 == 0 and c["edge_count"] % 64 == 0
+                assert c["edge_off"] + c["edge_count"] <= E
+                assert c["halo_off"] + c["halo_count"] <= L.halo.size
+                assert shim.shim_batch_smem(P, c["halo_slots"], c["n_slices"], c["edge_count"],
+                                            int(L.any_act)) <= smem
+                # halo: other ranks of this cluster, masses that exist, no repeats
+                hl = L.halo[c["halo_off"]:c["halo_off"] + c["halo_count"]].astype(np.int64)
+                hr, hs = hl >> 16, hl & 0xFFFF
+                assert np.all(hr < cluster) and np.all(hr != rank) and np.all(hs < P)
+                assert np.all(hr * P + hs < n) and len(set(hl.tolist())) == hl.size
+                rel = L.slices[c["slice_base"]:c["slice_base"] + c["n_slices"] + 1].astype(np.int64)
+                assert rel[0] == 0 and np.all(np.diff(rel) % 64 == 0) and rel[-1] <= c["edge_count"]
+                nb = L.nbr[c["edge_off"]:c["edge_off"] + c["edge_count"]]
+                kl = L.kl[c["edge_off"]:c["edge_off"] + c["edge_count"]]
+                ac = L.act[c["edge_off"]:c["edge_off"] + c["edge_count"]] if L.any_act else None
+                assert np.all(nb[:rel[-1]] < P + c["halo_count"])
+                # rows: decode each lane's entries back to (neighbour, k, L0) and compare with the springs
+                got = {}
+                for s_ in range(c["n_slices"]):
+                    w = (rel[s_ + 1] - rel[s_]) // 32
+                    for lane in range(32):
+                        i = rank * P + s_ * 32 + lane                   # caller index of the row's mass
+                        e = rel[s_] + 32 * np.arange(w) + lane
+                        j = _decode_slot(L, c, rank, P, nb[e])
+                        pad = (kl[e, 0] == 0) & (kl[e, 1] == 0)
+                        assert np.all(j[pad] == min(i, n - 1)), (r, i)
+                        if i >= n:
+                            assert pad.all()
+                            continue
+                        assert not pad[:np.count_nonzero(~pad)].any()  # springs first, padding after
+                        got[i] = (j[~pad], kl[e][~pad], None if ac is None else ac[e][~pad])
+                for i, (j, k, a) in got.items():
+                    q = inc[r][inc_ptr[r][i]:inc_ptr[r][i + 1]]
+                    other = np.where(sy.ends[q, 0] == i, sy.ends[q, 1], sy.ends[q, 0]).astype(np.int64)
+                    order = np.lexsort((q, other))                       # by (neighbour, spring)
+                    q, other = q[order], other[order]
+                    assert np.array_equal(j, other), (r, i)
+                    assert np.array_equal(k[:, 0], sy.k[q].astype(np.float32))
+                    assert np.array_equal(k[:, 1], sy.rest[q].astype(np.float32))
+                    if a is not None:
+                        if sy.act_amp is None:
+                            assert not a.any()
+                        else:
+                            A, ph = sy.act_amp[q], sy.act_phase[q]
+                            np.testing.assert_array_equal(a[:, 0], (A * np.cos(ph)).astype(np.float32))
+                            np.testing.assert_array_equal(a[:, 1], (A * np.sin(ph)).astype(np.float32))
+            # initial state: real masses in caller order, padding slots fixed and at rest
+            st = L.init_state[L.mass_off[r]:L.mass_off[r] + cluster * P]
+            assert np.array_equal(st[:n, :3], sy.pos.astype(np.float32))
+            assert np.array_equal(st[:n, 4:7], sy.vel.astype(np.float32))
+            inv = np.where(sy.fixed.astype(bool), 0.0, 1.0 / sy.mass).astype(np.float32)
+            assert np.array_equal(st[:n, 3], inv) and not st[n:].any() and not st[:, 7].any()
+    assert sorted(seen_robots) == list(range(len(systems)))
+    assert L.total_slots == L.init_state.shape[0]
+
+
+def test_batch_layout_refuses_a_system_too_dense_for_a_cluster(shim):
+    """4096 masses each joined to its 32 successors: 64 half-edges per mass do
+    not fit 8 CTAs of 220 KB; the builder says which system."""
+    small = inputs.actuated_box(3, 3, 3, np.random.default_rng(0))
+    n, reach = 4096, 32
+    pos = np.zeros((n, 3))
+    pos[:, 0] = 0.1 * np.arange(n)
+    ends = np.array([(i, i + d) for i in range(n) for d in range(1, reach + 1) if i + d < n], np.uint32)
+    s = ends.shape[0]
+    dense = inputs.System(pos=pos, vel=np.zeros_like(pos), mass=np.full(n, 0.1), fixed=np.zeros(n, np.uint8),
+                          ends=ends, k=np.full(s, 1e3), rest=0.1 * (ends[:, 1] - ends[:, 0]).astype(np.float64),
+                          damping=np.full(s, 1.0), dt=1e-4)
+    L = BatchLayout(shim, [small, dense])
+    assert not L.ok and L.why == "system 1 does not fit a cluster of 8 CTAs"
+    assert BatchLayout(shim, [small]).ok
