@@ -153,6 +153,7 @@ k_step_sell_pf(const MassState *__restrict__ in, MassState *__restrict__ out, ui
 // measured to lose lines to L2 eviction), or `ahead` blocks in advance.
 constexpr int kHaloThreads = 256;
 constexpr uint32_t kBoxHoleSlot = 0xFFFF;   // own slot of a hole (layout.h: kBoxHole)
+constexpr int kHaloMinBlocks = 6;      // resident CTAs per SM of the coloured-table halo kernel
 constexpr int kBoxMinBlocks = 6;       // resident CTAs per SM the register budget is sized for
 
 template <bool HAS_C, bool HAS_ACT>
@@ -168,7 +169,7 @@ __device__ __forceinline__ void prefetch_slice(const uint32_t *slice_off, uint32
 }
 
 template <bool HAS_C, bool HAS_ACT, bool GROUND>
-__global__ void __launch_bounds__(kHaloThreads, 6)
+__global__ void __launch_bounds__(kHaloThreads, kHaloMinBlocks)
 k_step_halo(const MassState *__restrict__ in, MassState *__restrict__ out, uint32_t n,
             const uint32_t *__restrict__ slice_off, const uint16_t *__restrict__ nslot,
             const float2 *__restrict__ kl, const float *__restrict__ cc,
@@ -1004,12 +1005,29 @@ cudaError_t launch_step_sell(const MassState *in, MassState *out, uint32_t n, co
     return cudaGetLastError();
 }
 
+// Shared-memory carveout for a kernel whose CTAs each hold `bytes` of dynamic
+// shared memory and of which `resident` fit an SM by registers: shared memory
+// for those CTAs (each also holds 1 KB reserved by the system), the rest of the
+// SM's unified L1 / shared memory left to L1, where the halo and state gathers
+// then hit more often.  At least 50 %: with six 17 KB tables per SM that was
+// measured 5 % faster than the largest shared carveout on the 1M-mass lattice.
+// The carveout is a hint: the driver always gives a single CTA what it needs.
+static int carveout_for(size_t bytes, int resident) {
+    int dev = 0, max_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&max_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess || max_sm <= 0)
+        return (int)cudaSharedmemCarveoutMaxShared;
+    const size_t need = (size_t)resident * (bytes + 1024);
+    return (int)std::min<size_t>(100, std::max<size_t>(50, (100 * need + (size_t)max_sm - 1) / (size_t)max_sm));
+}
+
 cudaError_t launch_step_halo(const MassState *in, MassState *out, uint32_t n, const SellView &v,
                              const HaloView &h, const StepConst &c, const long long *step_in,
                              long long *step_out, cudaStream_t stream, const cudaAccessPolicyWindow *l2win) {
     const bool hc = v.c != nullptr, ha = v.act != nullptr, gr = c.ground != 0;
     const unsigned g = n ? (n + kHaloThreads - 1) / kHaloThreads : 1;
     const size_t bytes = (size_t)h.table_slots * (sizeof(float4) + sizeof(float2));
+    const int carveout = carveout_for(bytes, kHaloMinBlocks);
 #define TITAN_HALO(HC, HA, GR)                                                                   \
     do {                                                                                         \
         auto kern = k_step_halo<HC, HA, GR>;                                                     \
@@ -1019,7 +1037,7 @@ cudaError_t launch_step_halo(const MassState *in, MassState *out, uint32_t n, co
         }                                                                                        \
         {                                                                                        \
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, \
-                                                 (int)cudaSharedmemCarveoutMaxShared);            \
+                                                 carveout);            \
             if (e != cudaSuccess) return e;                                                      \
         }                                                                                        \
         cudaLaunchConfig_t cfg = {};                                                             \
@@ -1057,23 +1075,7 @@ cudaError_t launch_step_box(const MassState *in, MassState *out, uint32_t n, con
     const unsigned g = n ? (n + kHaloThreads - 1) / kHaloThreads : 1;
     const size_t bytes = (size_t)h.table_slots * (sizeof(float4) + sizeof(float2));
     if (reinterpret_cast<uintptr_t>(h.col_off) & 3) return cudaErrorInvalidValue;
-    // Shared memory for the resident CTAs the register budget allows, the rest
-    // of the SM's unified L1 / shared memory left to L1: the halo and state
-    // gathers hit L1 more often.  A 50 % carveout (six 17 KB tables per SM)
-    // measured 5 % faster than the largest shared carveout on the 1M-mass
-    // lattice; larger tables ask for what their resident CTAs need (each CTA
-    // also holds 1 KB reserved by the system).  The carveout is a hint: the
-    // driver always gives a single CTA what it needs.
-    int carveout = (int)cudaSharedmemCarveoutMaxShared;
-    {
-        int dev = 0, max_sm = 0;
-        if (cudaGetDevice(&dev) == cudaSuccess &&
-            cudaDeviceGetAttribute(&max_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&
-            max_sm > 0) {
-            const size_t need = (size_t)kBoxMinBlocks * (bytes + 1024);
-            carveout = (int)std::min<size_t>(100, std::max<size_t>(50, (100 * need + (size_t)max_sm - 1) / (size_t)max_sm));
-        }
-    }
+    const int carveout = carveout_for(bytes, kBoxMinBlocks);
 #define TITAN_BOX(HC, HA, GR)                                                                    \
     do {                                                                                         \
         auto kern = k_step_box<HC, HA, GR>;                                                      \
