@@ -66,3 +66,31 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
     with redirect_stdout(buf):
         assert bench.run_reference(args) is None
     assert buf.getvalue() == ""
+
+
+def test_reference_arm_prints_one_complete_json_line(monkeypatch):
+    """Rank 0 of the reference arm times the FP64 oracle on the host and prints
+    the contract's line: the same metric and unit as our arm, the CPU baseline
+    it measured, and an end-to-end figure with no host-device copies.  A small
+    cube stands in for the sub-lattice so the test takes a fraction of a second."""
+    import json
+    import bench
+    from paper_1911_10274_gb300 import inputs
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
+        monkeypatch.delenv(k, raising=False)
+    monkeypatch.setattr(bench, "sub_lattice_for_budget", lambda seconds: inputs.cube_drop(n=4))
+    args = type("A", (), dict(steps=2, warmup=3, gpus=1, workload="lattice1m", accumulate="csr",
+                              kernel_variant=0, order="morton", exec="auto", no_l2_persist=False))()
+    buf = io.StringIO()
+    with redirect_stdout(buf):
+        bench.run_reference(args)
+    lines = buf.getvalue().strip().splitlines()
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["value"] > 0 and d["steps"] == 2 and d["warmup"] == 3 and d["n_gpus"] == 1
+    assert d["higher_is_better"] is True and d["vs_baseline"] is None and d["dtype"] == "f64"
+    assert d["config"]["workload"].startswith("1M-mass lattice")
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
