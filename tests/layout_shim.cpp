@@ -135,6 +135,15 @@ void shim_get(const char *name, void *dst) {
     if (k == "phalo") copy_out(g.phalo, dst);
 }
 
+// Spring records of the atomic path for the last built ordering: order[r] is
+// the caller spring held by record r, slot[q] the record of caller spring q.
+void shim_records(uint32_t s, const uint32_t *ends, uint32_t *order, uint32_t *slot) {
+    titan::RecordsHost rec;
+    titan::build_records(s, ends, g.dev_of_caller, rec);
+    copy_out(rec.order, order);
+    copy_out(rec.slot_of_spring, slot);
+}
+
 // ---- batch layout (titan_batch_create's host part)
 
 namespace {

@@ -44,6 +44,7 @@ def shim(tmp_path_factory):
     lib.shim_plan.restype = C.c_int
     lib.shim_plan.argtypes = [C.c_uint64, C.c_int, C.c_int]
     lib.shim_plan_scalar.restype = C.c_uint64
+    lib.shim_records.argtypes = [C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.shim_build_batch.restype = C.c_int
     lib.shim_build_batch.argtypes = [C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.shim_batch_why.restype = C.c_char_p
@@ -541,3 +542,25 @@ def test_batch_layout_refuses_a_system_too_dense_for_a_cluster(shim):
     L = BatchLayout(shim, [small, dense])
     assert not L.ok and L.why == "system 1 does not fit a cluster of 8 CTAs"
     assert BatchLayout(shim, [small]).ok
+
+
+def test_spring_records_are_sorted_by_device_ends_and_stable(shim):
+    """The atomic path's records: a permutation of the springs sorted by
+    (lower, higher) device index of their ends, duplicate springs kept in
+    caller order, with slot_of_spring its inverse."""
+    sy = inputs.random_mesh(n_points=3000, knn=6, seed=4)
+    ends = np.concatenate([sy.ends, sy.ends[:50][:, ::-1], sy.ends[10:20]]).astype(np.uint32)   # duplicates, both orientations
+    ends = np.ascontiguousarray(ends)
+    L = Layout(shim, sy.pos, ends)
+    s = len(ends)
+    order = np.empty(s, np.uint32)
+    slot = np.empty(s, np.uint32)
+    shim.shim_records(s, ends.ctypes.data, order.ctypes.data, slot.ctypes.data)
+    assert np.array_equal(np.sort(order), np.arange(s))
+    assert np.array_equal(slot[order], np.arange(s))
+    d = L.dev_of[ends.astype(np.int64)]
+    lo, hi = d.min(axis=1), d.max(axis=1)
+    key = lo[order] * (1 << 32) + hi[order]
+    assert np.all(np.diff(key) >= 0)
+    tie = np.diff(key) == 0
+    assert np.all(np.diff(order.astype(np.int64))[tie] > 0)     # equal keys stay in caller order
