@@ -1,5 +1,7 @@
 // batch.cu -- many independent spring-mass systems ("robots") advanced for a
-// whole rollout in one persistent launch per cluster size.
+// whole rollout in one persistent launch per cluster size and shared-memory
+// class (the host layout - clusters, rows, halos, launch groups - is built by
+// build_batch in layout.cpp; this file validates, uploads and launches).
 //
 // The paper simulates hundreds of worms at once (Sec. V-B) and many agents in
 // parallel (Sec. I).  Here every robot is owned by one thread-block cluster of
