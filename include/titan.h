@@ -319,8 +319,9 @@ titan_status titan_destroy(titan_sim *sim);
  * Many independent systems (robots) advanced together: the paper's parallel
  * robots and agents (Sec. I; Sec. V-B, 100 worms simulated at once).  Each
  * system is owned by one thread-block cluster whose shared memory holds its
- * state and springs for a whole rollout; all clusters of one size run in one
- * persistent launch, and the launches of a rollout form one CUDA graph.
+ * state and springs for a whole rollout; the clusters of one size and
+ * shared-memory class run in one persistent launch (small systems share an
+ * SM), and the launches of a rollout form one CUDA graph.
  * Systems keep their own mass order; masses of different systems never
  * interact. */
 typedef struct titan_batch titan_batch;
