@@ -94,3 +94,31 @@ def test_reference_arm_prints_one_complete_json_line(monkeypatch):
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_algorithmic_bytes_and_traffic_key():
+    """Per step: 16 B per spring (its {i, j, k, L0} record) and 52 B per mass
+    (position and velocity read and written, 1/m read): 255.7 MB on the
+    1M-mass lattice.  The ncu traffic key follows every file the step kernels
+    are compiled from, so a changed kernel reports no stale traffic."""
+    import shutil
+    import tempfile
+    import bench
+    assert bench.algorithmic_bytes(1_000_000, 12_731_796) == 16 * 12_731_796 + 52 * 1_000_000 == 255_708_736
+    h0 = bench.kernel_source_hash()
+    with tempfile.TemporaryDirectory() as d:
+        for rel in bench.KERNEL_INPUTS:
+            os.makedirs(os.path.dirname(os.path.join(d, rel)), exist_ok=True)
+            shutil.copy(os.path.join(bench.ROOT, rel), os.path.join(d, rel))
+        old = bench.ROOT
+        try:
+            bench.ROOT = d
+            assert bench.kernel_source_hash() == h0
+            for rel in bench.KERNEL_INPUTS:
+                with open(os.path.join(d, rel), "a") as f:
+                    f.write("\n")
+                h1 = bench.kernel_source_hash()
+                assert h1 != h0
+                h0 = h1
+        finally:
+            bench.ROOT = old
