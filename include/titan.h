@@ -61,7 +61,9 @@ typedef struct {
 /* Springs (Sec. III-B, Eq. 1).  ends [n][2] mass indices i != j (< masses.n);
  * k [n] stiffness >= 0; rest [n] rest length >= 0 (NULL: the initial
  * distance between the two masses); damping [n] axial dashpot >= 0 (NULL:
- * titan_params.damping for every spring). */
+ * titan_params.damping for every spring).  A rest length of 0 is legal on
+ * every kernel: the spring pulls its ends together with force k l, and while
+ * they coincide (l = 0) it has no axis and exerts no force. */
 typedef struct {
     uint32_t n;
     const uint32_t *ends;
@@ -287,13 +289,19 @@ const char *titan_last_error(const titan_sim *sim);
  * Enqueued on `stream` (a cudaStream_t; NULL: the legacy default stream) on
  * the current device; the call does not wait for it.
  * Limits: n_masses <= 262144; larger counts return TITAN_E_INVALID.
- * The first call on each device looks up the array's device address
+ * The first call on each device (and the first after the device's context is
+ * recreated, e.g. by cudaDeviceReset) looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call before
  * any stream capture.  All calls share the one array per device and each call
  * clears the part it uses first: calls whose work overlaps on the GPU (other
  * streams, other threads) race on it and must be serialised by the caller.
- * Errors: TITAN_E_INVALID (sizes, null pointers, dt/damping), TITAN_E_CUDA;
- * the text is in titan_last_error(NULL). */
+ * Spring ends must be < n_masses and distinct.  They are device data, so the
+ * kernel checks them: a spring that breaks this is skipped (nothing is read or
+ * written through it) and counted; the next call first waits for the work
+ * queued on its stream, reads and clears that count and, if it is nonzero,
+ * returns TITAN_E_INVALID without stepping.
+ * Errors: TITAN_E_INVALID (sizes, null pointers, dt/damping, bad spring ends
+ * in the previous call), TITAN_E_CUDA; the text is in titan_last_error(NULL). */
 titan_status titan_step_atomic_noalloc(uint32_t n_masses, const float *pos_dev, const float *vel_dev,
                                        const float *inv_mass_dev, uint32_t n_springs,
                                        const uint32_t *ends_dev, const float *k_dev,

@@ -617,7 +617,7 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
             sim->csr_kernel = 4;
         }
         const uint32_t E = sim->sell.entries;
-        std::vector<float2> kl(E, make_float2(0.f, 0.f));
+        std::vector<float2> kl(E, make_float2(0.f, titan::kPadRest));
         std::vector<float> cc;
         if (sim->has_c) cc.assign(E, 0.f);
         for (uint32_t e = 0; e < E; ++e) {
@@ -644,7 +644,7 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
             CREATE_CK(upload(sim->d_ext_slot, h.ext_slot, sim->stream));
             if (sim->csr_kernel == 8) {
                 const titan::CubeHost &cu = sim->cube;
-                std::vector<float2> ckl(cu.entries, make_float2(0.f, 0.f));
+                std::vector<float2> ckl(cu.entries, make_float2(0.f, titan::kPadRest));
                 std::vector<float> c2;
                 if (sim->has_c) c2.assign(cu.entries, 0.f);
                 for (uint32_t e = 0; e < cu.entries; ++e) {

@@ -259,10 +259,11 @@ k_step_halo(const MassState *__restrict__ in, MassState *__restrict__ out, uint3
 // the same for every lane) and the half-edge stream carries only {k, L0}
 // (8 bytes instead of 10).  It issues no bulk L2 prefetch: with the first
 // stream loads issued ahead of the table fill, the prefetch was measured to
-// cost more than it saved.  Padding entries ({k, L0} = {0, 0}; a real spring
-// has L0 > 0) may point at an empty cell of the box, whose table slot holds
-// whatever was there: they are skipped, never evaluated.  Holes - device
-// slots of empty cells, marked by own slot 0xFFFF - do nothing at all.
+// cost more than it saved.  Padding entries ({k, L0} = {0, kPadRest}: a
+// negative rest length, where every real spring, zero-rest-length ones
+// included, has L0 >= 0) may point at an empty cell of the box, whose table
+// slot holds whatever was there: they are skipped, never evaluated.  Holes -
+// device slots of empty cells, marked by own slot 0xFFFF - do nothing at all.
 template <bool HAS_C, bool HAS_ACT, bool GROUND>
 __global__ void __launch_bounds__(kHaloThreads, kBoxMinBlocks)
 k_step_box(const MassState *__restrict__ in, MassState *__restrict__ out, uint32_t n,
@@ -343,12 +344,12 @@ k_step_box(const MassState *__restrict__ in, MassState *__restrict__ out, uint32
                 L0 = actuated_length(c, a0.y, s0, ph);
                 L1 = actuated_length(c, a1.y, s1, ph);
             }
-            if (a0.y != 0.f) {
+            if (a0.y >= 0.f) {          // not padding
                 const float4 qa = tA[j0];
                 const float2 qb = tB[j0];
                 spring_force(p, v, qa, make_float4(qa.w, qb.x, qb.y, 0.f), a0.x, L0, c0, fx, fy, fz);
             }
-            if (a1.y != 0.f) {
+            if (a1.y >= 0.f) {
                 const float4 qa = tA[j1];
                 const float2 qb = tB[j1];
                 spring_force(p, v, qa, make_float4(qa.w, qb.x, qb.y, 0.f), a1.x, L1, c1, fx, fy, fz);
@@ -464,7 +465,7 @@ k_step_cube(const MassState *__restrict__ in, MassState *__restrict__ out, uint3
         }
         const int32_t off = (int32_t)(int16_t)(m.w & 0xffffu);
         float f = 0.f, ux = 0.f, uy = 0.f, uz = 0.f;
-        if (valid && a.y != 0.f) {                          // +p: evaluate and publish
+        if (valid && a.y >= 0.f) {                          // +p (not padding): evaluate and publish
             const uint32_t js = s_own + (uint32_t)off;
             const float4 qa = tA[js];
             const float2 qb = tB[js];
@@ -614,12 +615,12 @@ k_step_box_tma(const MassState *__restrict__ in, MassState *__restrict__ out, ui
             L0 = actuated_length(c, a0.y, s0, ph);
             L1 = actuated_length(c, a1.y, s1, ph);
         }
-        if (a0.y != 0.f) {
+        if (a0.y >= 0.f) {          // not padding
             const float4 qa = tA[j0];
             const float2 qb = tB[j0];
             spring_force(p, v, qa, make_float4(qa.w, qb.x, qb.y, 0.f), a0.x, L0, c0, fx, fy, fz);
         }
-        if (a1.y != 0.f) {
+        if (a1.y >= 0.f) {
             const float4 qa = tA[j1];
             const float2 qb = tB[j1];
             spring_force(p, v, qa, make_float4(qa.w, qb.x, qb.y, 0.f), a1.x, L1, c1, fx, fy, fz);

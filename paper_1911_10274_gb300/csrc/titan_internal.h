@@ -11,8 +11,12 @@
 //                 its number of offset-aligned columns, see layout.h).  Per
 //                 entry: nbr (u32 device index) and {k, L0} (float2), optionally
 //                 c (float) and actuation {A, phi} (float2).  Padding entries
-//                 point at the mass itself with k = L0 = c = A = 0, which gives an
-//                 exactly zero force (a zero-length spring has no axis).
+//                 point at the mass itself with k = c = A = 0 and the rest
+//                 length kPadRest (negative, so never a real spring's: rest
+//                 lengths are >= 0).  Evaluated, a padding entry gives an exactly
+//                 zero force (a zero-length spring has no axis); the grid
+//                 kernels, whose padding may address an empty table slot, skip
+//                 it by the sign of its rest length.
 //   Spring records (atomic scatter, K2): {i, j, k, L0} as one uint4 (128-bit
 //                 load), sorted by the lower device index, plus a float4 force
 //                 accumulator per mass.
@@ -24,6 +28,11 @@
 #include <vector>
 
 namespace titan {
+
+// Rest length stored in the {k, L0} of a padding entry.  Real springs have
+// L0 >= 0 (zero is legal: a zero-rest-length spring pulls with k l), so a
+// negative value marks padding unambiguously.
+constexpr float kPadRest = -1.0f;
 
 struct __align__(16) MassState {
     float4 p;   // x, y, z, 1/m (0: fixed)

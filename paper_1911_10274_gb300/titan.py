@@ -271,11 +271,59 @@ def titan_destroy(sim: int) -> None:
     _check(load().titan_destroy(sim))
 
 
+def check_noalloc_args(n_masses: int, n_springs: int, pos, vel, inv_mass, ends, k, rest, pos_out, vel_out,
+                       device=None) -> None:
+    """Checks the tensors of titan_step_atomic_noalloc before anything is
+    launched: the C call takes raw device pointers, so a host array, a tensor
+    of the wrong type, size or device, or an output that shares memory with an
+    input would otherwise be read or written blindly.  `device` is the device
+    the tensors must be on (default: the current CUDA device).  Raises
+    TypeError or ValueError."""
+    import torch
+    if device is None:
+        device = torch.device("cuda", torch.cuda.current_device())
+    named = dict(pos=pos, vel=vel, inv_mass=inv_mass, ends=ends, k=k, rest=rest, pos_out=pos_out,
+                 vel_out=vel_out)
+    sizes = dict(pos=3 * n_masses, vel=3 * n_masses, inv_mass=n_masses, ends=2 * n_springs, k=n_springs,
+                 rest=n_springs, pos_out=3 * n_masses, vel_out=3 * n_masses)
+    for name, t in named.items():
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"titan_step_atomic_noalloc: {name} must be a torch tensor on {device}, "
+                            f"not {type(t).__name__}")
+        if t.device != device:
+            raise ValueError(f"titan_step_atomic_noalloc: {name} is on {t.device}, expected {device}")
+        want = (torch.int32,) if name == "ends" else (torch.float32,)
+        if t.dtype not in want:
+            raise TypeError(f"titan_step_atomic_noalloc: {name} has dtype {t.dtype}, expected {want[0]}")
+        if not t.is_contiguous():
+            raise ValueError(f"titan_step_atomic_noalloc: {name} must be contiguous")
+        if t.numel() != sizes[name]:
+            raise ValueError(f"titan_step_atomic_noalloc: {name} has {t.numel()} elements, expected {sizes[name]}")
+
+    def span(t):
+        a = t.data_ptr()
+        return a, a + t.numel() * t.element_size()
+
+    for out in ("pos_out", "vel_out"):
+        o0, o1 = span(named[out])
+        for name, t in named.items():
+            if name == out or t.numel() == 0 or named[out].numel() == 0:
+                continue
+            a0, a1 = span(t)
+            if o0 < a1 and a0 < o1:
+                raise ValueError(f"titan_step_atomic_noalloc: {out} overlaps {name}")
+
+
 def titan_step_atomic_noalloc(n_masses: int, pos_dev, vel_dev, inv_mass_dev, n_springs: int, ends_dev,
                               k_dev, rest_dev, damping: float, params: titan_params, pos_out_dev,
                               vel_out_dev, stream: Optional[int] = None) -> None:
     """One atomic-scatter step on caller-owned device tensors, allocating
-    nothing (the accumulator is a fixed array inside the library)."""
+    nothing (the accumulator is a fixed array inside the library).  The
+    tensors are checked first (check_noalloc_args): float32 (ends int32),
+    contiguous, on the current CUDA device, of the sizes the counts imply,
+    outputs apart from every input."""
+    check_noalloc_args(n_masses, n_springs, pos_dev, vel_dev, inv_mass_dev, ends_dev, k_dev, rest_dev,
+                       pos_out_dev, vel_out_dev)
     _check(load().titan_step_atomic_noalloc(
         n_masses, _ptr(pos_dev), _ptr(vel_dev), _ptr(inv_mass_dev), n_springs, _ptr(ends_dev),
         _ptr(k_dev), _ptr(rest_dev), float(damping), C.byref(params), _ptr(pos_out_dev),
@@ -425,7 +473,8 @@ class Sim:
             fixed=np.ascontiguousarray(system.fixed, dtype=np.uint8),
             ends=np.ascontiguousarray(system.ends, dtype=np.uint32),
             k=np.ascontiguousarray(system.k, dtype=np.float64),
-            rest=np.ascontiguousarray(system.rest, dtype=np.float64),
+            # rest None: NULL, the library takes each spring's initial length
+            rest=None if system.rest is None else np.ascontiguousarray(system.rest, dtype=np.float64),
             damping=np.ascontiguousarray(system.damping, dtype=np.float64))
         kp = self._keep
         m = titan_masses(self.n, _ptr(kp["pos"]), _ptr(kp["vel"]), _ptr(kp["mass"]), _ptr(kp["fixed"]))

@@ -68,7 +68,7 @@ def _contact_start():
     return s2
 
 
-@pytest.mark.parametrize("mode", MODES[:7], ids=MODE_IDS[:7])
+@pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
 def test_cube_contact_100_steps(mode):
     """From the oracle's state at step 3150 (just before the cube lands), 100
     steps through the first ground contact."""
@@ -78,7 +78,7 @@ def test_cube_contact_100_steps(mode):
     check(sys, 100, **mode)
 
 
-@pytest.mark.parametrize("mode", MODES[:7], ids=MODE_IDS[:7])
+@pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
 def test_cube_penetrating_and_sliding_100_steps(mode):
     """Cube placed 1 mm into the ground, sliding at 0.1 m/s: penalty contact
     and capped Coulomb friction on every bottom mass from the first step."""
@@ -97,6 +97,85 @@ def test_cube_with_perturbed_rest_lengths_1000_steps(mode):
     sys.rest = sys.rest * rng.uniform(0.95, 1.05, sys.n_springs)
     sys.k = 1e4 * np.exp(0.5 * rng.standard_normal(sys.n_springs))
     check(sys, 1000, **mode)
+
+
+def _zero_rest_grid():
+    """The 10^3 cube (a grid: every kernel variant applies) with twelve springs
+    of rest length 0 - legal input: such a spring pulls its ends together with
+    force k l - softened to k = 300 so the lattice stays well conditioned."""
+    sys = inputs.cube_drop(drop_height=0.3)
+    rng = np.random.default_rng(21)
+    idx = rng.choice(sys.n_springs, 12, replace=False)
+    sys.rest[idx] = 0.0
+    sys.k[idx] = 300.0
+    sys.vel[:, 0] = 0.1
+    return sys, idx
+
+
+@pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
+def test_grid_lattice_with_zero_rest_length_springs(mode):
+    """Every kernel applies zero-rest-length springs (the grid kernels mark
+    their padding by a negative rest length, never by a physical value);
+    1000 steps of free fall, no contact."""
+    sys, idx = _zero_rest_grid()
+    without = sys.copy()
+    without.k[idx] = 0.0
+    xo, _ = oracle.run(sys, 1000)
+    xw, _ = oracle.run(without, 1000)
+    # the test is sensitive: dropping those springs moves masses far beyond the tolerance
+    assert np.abs(xo - xw).max() > 100 * POS_TOL_FRAC * sys.spacing
+    check(sys, 1000, **mode)
+
+
+def test_zero_rest_length_springs_bit_identical_across_csr_kernels():
+    sys, _ = _zero_rest_grid()
+    a = gpu_run(sys, 500, exec_mode=T.EXEC_PERSISTENT)
+    for var in range(1, 9):
+        b = gpu_run(sys, 500, kernel_variant=var, **LAUNCH)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]), var
+
+
+def _coincident_pair():
+    """A 4^3 lattice plus one extra mass placed exactly on mass 0, joined to it
+    by a spring whose rest length is NULL (the initial distance: 0) and to
+    mass 1 by an ordinary one.  The pair starts with different velocities, so
+    the zero-rest-length spring first has no axis (no force) and then pulls
+    with k l as the masses separate."""
+    base = inputs.cube_drop(n=4, drop_height=0.3)
+    pos = np.concatenate([base.pos, base.pos[:1]])
+    vel = np.zeros_like(pos)
+    vel[-1] = (0.3, -0.2, 0.1)
+    n = len(pos)
+    ends = np.concatenate([base.ends, np.array([[0, n - 1], [n - 1, 1]], np.uint32)]).astype(np.uint32)
+    k = np.concatenate([base.k, [2000.0, 1000.0]])
+    rest = np.linalg.norm(pos[ends[:, 1]] - pos[ends[:, 0]], axis=1)
+    assert rest[-2] == 0.0
+    sys = inputs.System(pos=pos, vel=vel, mass=np.full(n, 0.1), fixed=np.zeros(n, np.uint8), ends=ends,
+                        k=k, rest=rest, damping=np.full(len(ends), 1.0), dt=1e-4, ground=True, spacing=0.1)
+    return sys
+
+
+@pytest.mark.parametrize("mode", [m for m in MODES if m.get("kernel_variant") not in (6, 7, 8)],
+                         ids=[i for m, i in zip(MODES, MODE_IDS) if m.get("kernel_variant") not in (6, 7, 8)])
+def test_coincident_masses_joined_with_null_rest_length(mode):
+    """Coincident masses are off-grid (one mass per cell), so the grid
+    kernels do not apply; every other kernel is compared with the oracle,
+    which is given the rest lengths the library derives from NULL."""
+    sys = _coincident_pair()
+    null_rest = sys.copy()
+    null_rest.rest = None
+    xo, vo = oracle.run(sys, 1000)
+    assert np.linalg.norm(xo[-1] - xo[0]) > 1e-3          # they separated: the spring is stretched
+    xg, vg, _ = gpu_run(null_rest, 1000, **mode)
+    assert np.all(np.isfinite(xg))
+    assert np.abs(xg - xo).max() <= POS_TOL_FRAC * sys.spacing
+    assert np.abs(vg - vo).max() <= 1e3 * POS_TOL_FRAC * sys.spacing
+
+
+def test_coincident_masses_are_refused_by_the_grid_kernels():
+    sys = _coincident_pair()
+    with pytest.raises(T.TitanError, match="grid"):
+        T.Sim(sys, kernel_variant=6, **LAUNCH)
 
 
 def test_per_spring_damping():
