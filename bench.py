@@ -34,12 +34,13 @@ METRIC = "spring updates/s"
 # the step kernel a Sim resolved to (titan_csr_kernel), and its description
 CSR_KERNEL_NAMES = {0: "k_springs_atomic+k_masses_atomic", 1: "k_step_sell", 2: "k_step_sell_staged",
                     3: "k_step_sell_pf", 4: "k_step_halo", 5: "k_step_halo_tma", 6: "k_step_box",
-                    7: "k_step_box_tma", 8: "k_step_cube"}
+                    7: "k_step_box_tma", 8: "k_step_cube", 9: "k_step_box_ring"}
 CSR_KERNELS = {0: "atomic scatter", 1: "direct-loads", 2: "tma-staged", 3: "bulk-l2-prefetch",
                4: "halo (coloured neighbourhood table in shared memory)", 5: "halo+tma",
                6: "grid box (box table in shared memory, no neighbour index in the stream)",
                7: "grid box, stream staged in shared memory by TMA bulk copies",
-               8: "cube (springs inside a 256-mass cube read and evaluated once)"}
+               8: "cube (springs inside a 256-mass cube read and evaluated once)",
+               9: "grid box, each warp's stream fed through a ring of bulk copies in shared memory"}
 UNIT = "spring_updates/s"
 L2_BYTES = 126 * 1024 * 1024
 
@@ -74,6 +75,11 @@ def algorithmic_bytes(n_masses: int, n_springs: int) -> int:
     """Bytes one step must move: 16 per spring (i, j, k, L0) and 52 per mass
     (position and velocity read and written, 1/m read)."""
     return 16 * n_springs + 52 * n_masses
+
+
+WORKLOADS = {"lattice1m": "1M-mass lattice 100^3, 12,731,796 springs, fixed base, no ground, dt=5e-5",
+             "lattice50": "50^3 lattice, 1,558,396 springs", "mesh2m": "2M-point kNN mesh",
+             "cube1k": "10^3 cube drop"}
 
 
 def make_workload(name: str):
@@ -183,15 +189,75 @@ def sub_lattice_for_budget(seconds_per_step: float):
     return inputs.large_lattice(n=n, seed=0)
 
 
+def host_cpu():
+    """nproc and the host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            info = open("/proc/cpuinfo").read().splitlines()
+            for key in ("model name", "Model", "CPU part"):
+                hit = [ln.split(":", 1)[1].strip() for ln in info if ln.lower().startswith(key.lower())]
+                if hit:
+                    model = hit[0] if key != "CPU part" else f"CPU part {hit[0]}"
+                    break
+        except Exception:
+            pass
+    return os.cpu_count(), model or "unknown"
+
+
 def cpu_baseline_leg(system, target_seconds: float = 15.0):
-    """The oracle as it stands, single thread, on a bounded number of steps of
-    the same workload (from its initial state)."""
+    """The oracle as it stands on the host cores, from the workload's initial
+    state, on a bounded number of steps: the serial FP64 program on one
+    thread (the paper's own CPU comparison is single-threaded) and its
+    per-mass-gather variant on all cores (bit-identical trajectory); plus the
+    10^3 cube drop timed in full (10,000 steps) by both."""
+    import oracle
+    from paper_1911_10274_gb300 import inputs
+    nproc, model = host_cpu()
     probe = time_oracle(system, 1)
     steps = max(1, min(200, int(target_seconds / max(probe, 1e-6))))
     t = time_oracle(system, steps)
-    return {"value": system.n_springs * steps / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{system.name}: {steps} time steps of the full system from its initial "
-                      f"state, FP64, one thread ({t:.1f} s)"}
+    out = {"value": system.n_springs * steps / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{system.name}: {steps} time steps of the full system from its initial "
+                     f"state, FP64, one thread ({t:.1f} s)",
+           "nproc": nproc, "cpu_model": model}
+    cube = inputs.cube_drop()
+    t0 = time.perf_counter()
+    oracle.run(cube, 10_000)
+    t_c0 = time.perf_counter() - t0
+    out["cube1k_full"] = {"value": cube.n_springs * 10_000 / t_c0, "unit": UNIT, "cores": 1,
+                          "seconds": t_c0, "sample": "10^3 cube drop, all 10,000 steps, FP64, one thread"}
+    try:
+        par = oracle.Parallel(system)
+        t0 = time.perf_counter()
+        par.run(1)
+        p_probe = time.perf_counter() - t0
+        p_steps = max(1, min(400, int(target_seconds / 2 / max(p_probe, 1e-6))))
+        t0 = time.perf_counter()
+        par.run(p_steps)
+        t_p = time.perf_counter() - t0
+        out["all_cores"] = {"value": system.n_springs * p_steps / t_p, "unit": UNIT, "cores": par.threads_used,
+                            "sample": f"{system.name}: {p_steps} time steps, FP64, per-mass gather on "
+                                      f"{par.threads_used} threads ({t_p:.1f} s), trajectory bit-identical "
+                                      f"to the serial oracle"}
+        pc = oracle.Parallel(cube)
+        t0 = time.perf_counter()
+        pc.run(10_000)
+        t_pc = time.perf_counter() - t0
+        out["cube1k_full_all_cores"] = {"value": cube.n_springs * 10_000 / t_pc, "unit": UNIT,
+                                        "cores": pc.threads_used, "seconds": t_pc,
+                                        "sample": "10^3 cube drop, all 10,000 steps, FP64, per-mass gather"}
+    except Exception as exc:            # no OpenMP runtime on this host
+        out["all_cores"] = {"unavailable": f"{type(exc).__name__}: {exc}"[:200]}
+    return out
 
 
 def run_reference(args):
@@ -212,8 +278,15 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_for(args, None, auto_kernel(args)),
+            "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload],
+                       "impl": "FP64 CPU oracle: spring pass then mass pass, input order, one thread",
+                       "accumulate": "serial spring loop in input order", "order": "input order (no reordering)",
+                       "parallelism": "serial, rank 0 only", "l2": "not applicable (host)",
+                       "sample": f"each timed step is one oracle step of the {system.n_masses}-mass "
+                                 f"({system.n_springs}-spring) sub-lattice of the same recipe"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "nproc": host_cpu()[0], "cpu_model": host_cpu()[1],
                              "sample": f"each step: one FP64 oracle time step of a {system.name} "
                                        f"sub-lattice ({system.n_masses} masses, {system.n_springs} springs) "
                                        f"of the benchmark recipe, one thread"},
@@ -221,19 +294,8 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def auto_kernel(args):
-    """The step kernel our arm resolves to on this workload (for the reference arm's config)."""
-    if args.accumulate != "csr":
-        return 0
-    if args.kernel_variant:
-        return args.kernel_variant
-    return 4 if args.workload == "mesh2m" else 6
-
-
 def config_for(args, system, resolved=None):
-    cfg = {"workload": {"lattice1m": "1M-mass lattice 100^3, 12,731,796 springs, fixed base, no ground, dt=5e-5",
-                        "lattice50": "50^3 lattice, 1,558,396 springs", "mesh2m": "2M-point kNN mesh",
-                        "cube1k": "10^3 cube drop"}[args.workload],
+    cfg = {"workload": WORKLOADS[args.workload],
            "accumulate": args.accumulate,
            "order": "input order (no reordering)" if args.order == "input"
            else ("grid cubes of 8x8x4 cells, Morton" if resolved == 6 else "morton"), "graph_chunk": 64,
@@ -403,7 +465,7 @@ def run_ours(args):
     order = T.ORDER_MORTON if args.order == "morton" else T.ORDER_INPUT
     sim = T.Sim(system, accumulate=acc, stream=stream.cuda_stream, device=local,
                 kernel_variant=args.kernel_variant, exec_mode=exec_mode, order=order,
-                l2_persist=not args.no_l2_persist)
+                l2_persist=not args.no_l2_persist, box_ring=args.box_ring)
     launches_per_step = 1 if acc == T.ACCUM_CSR else 2
     resolved = sim.csr_kernel
     persistent = sim.exec_mode == T.EXEC_PERSISTENT
@@ -515,7 +577,8 @@ def main():
                     help="device order of the masses: spatial (grid cubes or Morton) or the caller's order")
     ap.add_argument("--exec", choices=["auto", "launch", "persistent"], default="auto",
                     help="step loop: persistent cluster kernel (small systems), per-step launches, or auto")
-    ap.add_argument("--kernel-variant", type=int, default=0, help="CSR kernel: 0 auto, 1 direct loads, 2 TMA-staged, 3 bulk L2 prefetch, 4 halo, 5 halo+TMA, 6 grid box, 7 grid box+TMA, 8 cube")
+    ap.add_argument("--kernel-variant", type=int, default=0, help="CSR kernel: 0 auto, 1 direct loads, 2 TMA-staged, 3 bulk L2 prefetch, 4 halo, 5 halo+TMA, 6 grid box, 7 grid box+TMA, 8 cube, 9 grid box + stream ring")
+    ap.add_argument("--box-ring", type=int, default=0, help="kernel 9's ring per warp: 0/1 4x2 columns, 2 6x2, 3 3x4")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -117,9 +117,11 @@ typedef struct {
                                  index in the stream), 7 grid box + TMA-staged
                                  stream, 8 cube (springs inside a 256-mass cube
                                  read and evaluated once; 26-neighbour springs on
-                                 a grid, at most one per mass and offset).  4 to 8
-                                 return TITAN_E_UNSUPPORTED if their tables do not
-                                 fit or their layout conditions fail        */
+                                 a grid, at most one per mass and offset), 9 grid
+                                 box with each warp's stream fed through a ring
+                                 of bulk copies in shared memory (box_ring).  4
+                                 to 9 return TITAN_E_UNSUPPORTED if their tables
+                                 do not fit or their layout conditions fail */
     int32_t l2_persist;       /* nonzero (default): keep the two state buffers of a
                                  CSR simulation resident in L2 (an access-policy
                                  window on the grid-box, cube and halo step
@@ -127,7 +129,9 @@ typedef struct {
                                  persisting part of L2; the context's
                                  persisting-L2 limit is raised while any such
                                  handle lives and restored by titan_destroy)    */
-    int32_t reserved[5];      /* zero                                              */
+    int32_t box_ring;         /* kernel variant 9's ring per warp: 0 or 1 (default)
+                                 4 stages of 2 columns, 2: 6 x 2, 3: 3 x 4      */
+    int32_t reserved[4];      /* zero                                              */
 } titan_params;
 
 /* Writes the defaults listed above into *p (p != NULL). */

@@ -22,7 +22,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "titan_oracle.c")
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
+_SRC_OMP = os.path.join(_HERE, "titan_oracle_omp.c")
+_LIB_OMP_PATH = os.path.join(_OUT_DIR, "liboracle_omp.so")
 _lib = None
+_lib_omp = None
 _lock = threading.Lock()
 
 
@@ -37,6 +40,20 @@ def build(force: bool = False) -> str:
                            "-fno-fast-math", _SRC, "-o", tmp, "-lm"])
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
+
+
+def build_parallel(force: bool = False) -> str:
+    """Compile the all-cores variant (titan_oracle_omp.c, OpenMP) into
+    oracle/_build/liboracle_omp.so, with the serial oracle's flags."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_OMP))
+    if not force and os.path.exists(_LIB_OMP_PATH) and os.path.getmtime(_LIB_OMP_PATH) >= newest:
+        return _LIB_OMP_PATH
+    tmp = _LIB_OMP_PATH + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+                           "-fno-fast-math", "-fopenmp", "-I", _HERE, _SRC_OMP, "-o", tmp, "-lm"])
+    os.replace(tmp, _LIB_OMP_PATH)
+    return _LIB_OMP_PATH
 
 
 class OracleSystem(C.Structure):
@@ -74,6 +91,23 @@ def _load():
         if _lib is None:
             _lib = _bind(C.CDLL(build()))
     return _lib
+
+
+def _load_parallel():
+    global _lib_omp
+    with _lock:
+        if _lib_omp is None:
+            lib = C.CDLL(build_parallel())
+            P = C.POINTER(OracleSystem)
+            lib.titan_oracle_incidence.argtypes = [P, C.c_void_p, C.c_void_p]
+            lib.titan_oracle_incidence.restype = None
+            lib.titan_oracle_run_parallel.argtypes = [P, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64,
+                                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
+            lib.titan_oracle_run_parallel.restype = C.c_int
+            lib.titan_oracle_max_threads.argtypes = []
+            lib.titan_oracle_max_threads.restype = C.c_int
+            _lib_omp = lib
+    return _lib_omp
 
 
 @contextlib.contextmanager
@@ -148,6 +182,41 @@ def run(sys, n_steps: int, step0: int = 0, pos=None, vel=None, act_mode=None, wo
     lib.titan_oracle_run(C.byref(b.struct), x.ctypes.data, v.ctypes.data, int(step0), int(n_steps),
                          F.ctypes.data)
     return x, v
+
+
+class Parallel:
+    """The all-cores variant bound to one system: its per-mass incidence is
+    built once; run() then advances a state like the serial run() (the same
+    trajectory, bit for bit) on `threads` threads (0: all cores)."""
+
+    def __init__(self, sys, act_mode=None, worm=None, threads: int = 0):
+        self.lib = _load_parallel()
+        self.sys = sys
+        self.bound = _Bound(sys, act_mode, worm)
+        self.rowptr = np.zeros(sys.n_masses + 1, np.int64)
+        self.ent = np.zeros(max(1, 2 * sys.n_springs), np.uint64)
+        self.lib.titan_oracle_incidence(C.byref(self.bound.struct), self.rowptr.ctypes.data, self.ent.ctypes.data)
+        self.threads = int(threads)
+        self.threads_used = 0
+
+    def run(self, n_steps: int, step0: int = 0, pos=None, vel=None):
+        x = _f64(self.sys.pos if pos is None else pos).copy()
+        v = _f64(self.sys.vel if vel is None else vel).copy()
+        F = np.empty_like(x)
+        self.threads_used = self.lib.titan_oracle_run_parallel(
+            C.byref(self.bound.struct), x.ctypes.data, v.ctypes.data, int(step0), int(n_steps), F.ctypes.data,
+            self.rowptr.ctypes.data, self.ent.ctypes.data, self.threads)
+        return x, v
+
+
+def run_parallel(sys, n_steps: int, step0: int = 0, pos=None, vel=None, act_mode=None, worm=None,
+                 threads: int = 0):
+    """run() on all cores (or `threads`): the same trajectory, bit for bit."""
+    return Parallel(sys, act_mode, worm, threads).run(n_steps, step0, pos, vel)
+
+
+def max_threads() -> int:
+    return int(_load_parallel().titan_oracle_max_threads())
 
 
 def spring_forces(sys, pos=None, vel=None, step: int = 0, act_mode=None, worm=None):

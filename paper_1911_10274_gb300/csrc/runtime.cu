@@ -191,7 +191,8 @@ titan_status validate(const titan_masses *m, const titan_springs *sp, const tita
     if (p->exec < TITAN_EXEC_AUTO || p->exec > TITAN_EXEC_PERSISTENT)
         return fail(nullptr, TITAN_E_INVALID, "params.exec out of range");
     if (p->device < 0) return fail(nullptr, TITAN_E_INVALID, "params.device must be >= 0");
-    if (p->kernel_variant < 0 || p->kernel_variant > 8) return fail(nullptr, TITAN_E_INVALID, "params.kernel_variant must be 0..8");
+    if (p->kernel_variant < 0 || p->kernel_variant > 9) return fail(nullptr, TITAN_E_INVALID, "params.kernel_variant must be 0..9");
+    if (p->box_ring < 0 || p->box_ring > 3) return fail(nullptr, TITAN_E_INVALID, "params.box_ring must be 0..3");
     for (uint64_t i = 0; i < m->n; ++i) {
         for (int a = 0; a < 3; ++a) {
             if (!finite(m->pos[3 * i + a])) return fail(nullptr, TITAN_E_INVALID, "masses.pos has a non-finite value at mass " + std::to_string(i));
@@ -264,9 +265,12 @@ cudaError_t enqueue_step_io(titan_sim *sim, cudaStream_t st, const MassState *in
     if (sim->accumulate == TITAN_ACCUM_CSR) {
         titan::SellView v{sim->d_slice_off, sim->d_nbr, sim->d_kl, sim->has_c ? sim->d_c : nullptr,
                           sim->has_act ? sim->d_act : nullptr, 0, sim->spin_limit, sim->d_err};
-        if (sim->csr_kernel >= 6 && sim->csr_kernel <= 8) {
+        if (sim->csr_kernel >= 6 && sim->csr_kernel <= 9) {
             titan::BoxView h{sim->d_col_off, sim->d_own_slot, sim->d_ext_off, sim->d_ext_idx, sim->d_ext_slot,
                              (sim->box.max_table + 1) & ~1u};
+            if (sim->csr_kernel == 9)
+                return titan::launch_step_box_ring(in, out, sim->n_dev, v, h, sim->box_ring, sim->c, si, so, st,
+                                                   sim->l2_on ? &sim->l2win : nullptr);
             if (sim->csr_kernel == 8) {
                 titan::CubeView cv{sim->d_cube_base, sim->d_cube_meta, sim->d_ckl, sim->has_c ? sim->d_cc : nullptr,
                                    sim->has_act ? sim->d_cact : nullptr};
@@ -456,6 +460,7 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
     sim->c.c_uniform = (float)p->damping;
     sim->c.act_omega = 0.0;
     sim->kernel_variant = p->kernel_variant;
+    sim->box_ring = p->box_ring;
     sim->exec_req = p->exec;
     sim->spin_limit = p->spin_limit == 0 ? kDefaultSpinLimit
                                          : (uint32_t)(p->spin_limit > 0xffffffffull ? 0xffffffffull : p->spin_limit);
@@ -584,7 +589,7 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
             return bail(fail(sim, TITAN_E_UNSUPPORTED, "padded incidence exceeds 2^32 entries"));
         const int want = p->kernel_variant;
         sim->csr_kernel = want == 0 ? (sim->grid_order ? 6 : 4) : want;
-        if (sim->csr_kernel >= 6 && sim->csr_kernel <= 8 &&
+        if (sim->csr_kernel >= 6 && sim->csr_kernel <= 9 &&
             !(sim->grid_order && titan::build_box(nd, sim->sell, cells, sim->caller_of_dev, kHaloMaxSlots, sim->box))) {
             if (want >= 6)
                 return bail(fail(sim, TITAN_E_UNSUPPORTED, "the grid box kernel needs masses on a grid whose "
@@ -630,7 +635,7 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
         CREATE_CK(dev_alloc(sim, &sim->d_kl, E));
         CREATE_CK(upload(sim->d_slice_off, sim->sell.slice_off, sim->stream));
         CREATE_CK(upload(sim->d_kl, kl, sim->stream));
-        if (sim->csr_kernel >= 6 && sim->csr_kernel <= 8) {
+        if (sim->csr_kernel >= 6 && sim->csr_kernel <= 9) {
             const titan::BoxHost &h = sim->box;
             CREATE_CK(dev_alloc(sim, &sim->d_col_off, h.col_off.size()));
             CREATE_CK(dev_alloc(sim, &sim->d_own_slot, nd));

@@ -78,6 +78,7 @@ struct SimCore {
 
     int graph_chunk = kDefaultGraphChunk;
     int kernel_variant = 0;
+    int box_ring = 0;                     // kernel variant 9's ring configuration
     uint32_t spin_limit = kDefaultSpinLimit;
     int *d_err = nullptr;                 // device error flag (bounded waits)
     cudaGraphExec_t graph[2] = {nullptr, nullptr};

@@ -132,6 +132,16 @@ cudaError_t launch_step_box_tma(const MassState *in, MassState *out, uint32_t n,
                                 long long *step_out, cudaStream_t stream);
 size_t box_tma_smem_bytes(uint32_t table_slots, uint32_t w_max, bool has_c, bool has_act);
 
+// Grid-box form with the stream fed through a per-warp ring of bulk copies
+// (step_ring.cu).  config 0/1: 4 stages of 2 columns, 2: 6 x 2, 3: 3 x 4.
+// table_slots must be even.
+cudaError_t launch_step_box_ring(const MassState *in, MassState *out, uint32_t n, const SellView &v, const BoxView &h,
+                                 int config, const StepConst &c, const long long *step_in, long long *step_out,
+                                 cudaStream_t stream, const cudaAccessPolicyWindow *l2win = nullptr);
+size_t box_ring_smem_bytes(uint32_t table_slots, uint32_t ring_cols, bool has_c, bool has_act);
+int box_ring_stages(int config);
+int box_ring_cols(int config);
+
 // Halo form with the half-edge stream staged into shared memory by TMA bulk
 // copies; slices wider than w_max columns read from global memory.
 cudaError_t launch_step_halo_tma(const MassState *in, MassState *out, uint32_t n, const SellView &v,
