@@ -391,6 +391,11 @@ uint32_t titan_batch_groups(const titan_batch *b);
 titan_status titan_batch_info(const titan_batch *b, uint32_t group, uint32_t *cluster,
                               uint32_t *threads, uint32_t *threads_per_mass, uint32_t *ctas);
 
+/* The launch group (0 .. titan_batch_groups - 1) whose launches advance
+ * system `system`.  TITAN_E_INVALID for a null batch or output, or a system
+ * index out of range. */
+titan_status titan_batch_system_group(const titan_batch *b, uint32_t system, uint32_t *group);
+
 /* Text of the last error on this batch ("" if none). */
 const char *titan_batch_last_error(const titan_batch *b);
 

@@ -222,6 +222,7 @@ struct titan_batch {
     std::vector<uint32_t> mass_off, mass_cnt;   // per robot, into the global mass slots
     std::vector<float> init_state;               // caller-provided initial state, [slots][8] (x y z 1/m vx vy vz 0)
     std::vector<Group> groups;
+    std::vector<uint32_t> group_of;              // per system: the launch group holding its cluster
     // device
     BatchCta *d_ctas = nullptr;
     MassState *d_state[2] = {nullptr, nullptr};
@@ -420,12 +421,15 @@ titan_status titan_batch_create(uint32_t n_systems, const titan_masses *masses, 
     b->mass_cnt = L.mass_cnt;
     b->init_state = std::move(L.init_state);
     b->total_slots = L.total_slots;
+    b->group_of.assign(n_systems, UINT32_MAX);
     for (const titan::BatchGroup &lg : L.groups) {
         Group g;
         g.cluster = lg.cluster;
         g.cta_first = lg.cta_first;
         g.cta_count = lg.cta_count;
         g.smem = lg.smem;
+        for (uint32_t q = lg.cta_first; q < lg.cta_first + lg.cta_count; ++q)
+            b->group_of[L.ctas[q].robot] = (uint32_t)b->groups.size();
         b->groups.push_back(g);
     }
 
@@ -618,6 +622,12 @@ titan_status titan_batch_configure(titan_batch *b, uint32_t group, uint32_t thre
 }
 
 uint32_t titan_batch_groups(const titan_batch *b) { return b ? (uint32_t)b->groups.size() : 0; }
+
+titan_status titan_batch_system_group(const titan_batch *b, uint32_t system, uint32_t *group) {
+    if (!b || !group || system >= b->group_of.size()) return TITAN_E_INVALID;
+    *group = b->group_of[system];
+    return TITAN_OK;
+}
 
 const char *titan_batch_last_error(const titan_batch *b) { return b ? b->error.c_str() : ""; }
 

@@ -117,6 +117,7 @@ def load(path: Optional[str] = None):
                 "titan_batch_read": (S, [_P, u32, _P, _P]),
                 "titan_batch_centroids": (S, [_P, _P]),
                 "titan_batch_groups": (u32, [_P]),
+                "titan_batch_system_group": (S, [_P, u32, C.POINTER(u32)]),
                 "titan_batch_configure": (S, [_P, u32, u32, u32]),
                 "titan_batch_info": (S, [_P, u32, C.POINTER(u32), C.POINTER(u32), C.POINTER(u32), C.POINTER(u32)]),
                 "titan_batch_last_error": (C.c_char_p, [_P]),
@@ -410,6 +411,12 @@ class Batch:
 
     def sync(self) -> None:
         _bcheck(load().titan_batch_sync(self.handle), self.handle)
+
+    def group_of(self, r: int) -> int:
+        """Index (into groups()) of the launch group that advances system r."""
+        g = C.c_uint32()
+        _bcheck(load().titan_batch_system_group(self.handle, r, C.byref(g)), self.handle)
+        return int(g.value)
 
     def read(self, r: int):
         n = self.sizes[r]

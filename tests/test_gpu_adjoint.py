@@ -1,9 +1,12 @@
 """The GPU adjoint (titan_adjoint, FP32) against the FP64 oracle's adjoint and
 FP64 central finite differences (h = 1e-6) of the oracle's rollout.
 
-Tolerance: 1e-3 relative, normwise over the gradient vector (max absolute
-error <= 1e-3 x the largest gradient entry), the bar the benchmark target sets
-for the adjoint."""
+Tolerance: 1e-3 relative, the bar the benchmark target sets for the adjoint,
+read two ways.  Normwise: max absolute error <= 1e-3 x the largest gradient
+entry.  Entry by entry: |g - ref| <= 1e-3 |ref| for every entry at least 1 %
+of the largest (smaller entries are held to the normwise bound, 1e-3 of the
+largest: their relative error is not meaningful at FP32 once they are
+several orders of magnitude below it)."""
 import numpy as np
 import pytest
 
@@ -44,6 +47,11 @@ def _close(g, ref):
     assert scale > 0
     err = np.abs(g - ref).max()
     assert err <= REL * scale, f"max error {err:.3e} vs {REL} x {scale:.3e}"
+    big = np.abs(ref) >= 1e-2 * scale
+    rel = np.abs(g[big] - ref[big]) / np.abs(ref[big])
+    worst = int(np.flatnonzero(big)[np.argmax(rel)])
+    assert rel.max() <= REL, (f"entry {worst}: {g[worst]:.6e} vs {ref[worst]:.6e} "
+                              f"(relative {rel.max():.2e}; {big.sum()} entries checked)")
 
 
 @pytest.mark.parametrize("ground", [False, True], ids=["floating", "on-ground"])
@@ -68,9 +76,11 @@ def test_adjoint_matches_central_differences_on_the_benchmark_objective():
     seed = oracle.centroid_x_seed(sy.n_masses)
     ga, gp, _, _ = _gpu_adjoint(sy, steps, seed, every=50)
     ra, rp, _, _ = oracle.adjoint(sy, steps, seed)
+    _close(ga, ra)
+    _close(gp, rp)
     scale_a, scale_p = np.abs(ra).max(), np.abs(rp).max()
     rng = np.random.default_rng(2)
-    for s in rng.choice(np.flatnonzero(sy.act_amp > 0), 6, replace=False):
+    for s in rng.choice(np.flatnonzero(sy.act_amp > 0), 24, replace=False):
         for which, g, scale in (("amp", ga, scale_a), ("phase", gp, scale_p)):
             def J(delta):
                 alt = sy.copy()
@@ -83,7 +93,8 @@ def test_adjoint_matches_central_differences_on_the_benchmark_objective():
                 x, _ = oracle.run(alt, steps)
                 return float((seed * x).sum())
             fd = (J(1e-6) - J(-1e-6)) / 2e-6
-            assert abs(g[s] - fd) <= REL * scale, (which, s, g[s], fd)
+            # relative to the entry itself, floored at 1 % of the largest entry
+            assert abs(g[s] - fd) <= REL * max(abs(fd), 1e-2 * scale), (which, s, g[s], fd)
 
 
 def test_checkpoint_interval_does_not_change_the_result():

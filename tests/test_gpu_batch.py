@@ -132,3 +132,35 @@ def test_system_too_dense_for_a_cluster_is_refused_and_the_device_kept():
     with T.Batch(robots) as b:
         b.rollout(100)
         _check(b, robots, 100)
+
+
+def test_benchmark_batch_sample_matches_oracle_in_every_launch_group():
+    """The benchmark's own batch (4096 robots, a, b, c ~ U{3..12}), autotuned
+    as the benchmark runs it, 300 steps: at least 64 robots, with at least four
+    (or all) from every launch group, compared with the oracle one by one."""
+    robots = inputs.robot_batch(4096, seed=0)
+    with T.Batch(robots) as b:
+        b.autotune(50)
+        n_groups = len(b.groups())
+        group_of = np.array([b.group_of(r) for r in range(len(robots))])
+        assert set(group_of.tolist()) == set(range(n_groups)), "every group holds robots"
+        b.rollout(300)
+        rng = np.random.default_rng(0)
+        picks = set()
+        for g in range(n_groups):
+            members = np.flatnonzero(group_of == g)
+            picks.update(rng.choice(members, min(4, len(members)), replace=False).tolist())
+        while len(picks) < 64:
+            picks.add(int(rng.integers(len(robots))))
+        sample = sorted(picks)
+        assert {group_of[r] for r in sample} == set(range(n_groups))
+        _check_sample(b, robots, sample, 300)
+
+
+def _check_sample(batch, robots, sample, steps):
+    for r in sample:
+        sy = robots[r]
+        xo, _ = oracle.run(sy, steps)
+        xg, _ = batch.read(r)
+        err = np.abs(xg.astype(np.float64) - xo).max()
+        assert err <= POS_TOL_FRAC * sy.spacing, (r, sy.name, err)
