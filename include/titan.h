@@ -119,9 +119,12 @@ typedef struct {
                                  read and evaluated once; 26-neighbour springs on
                                  a grid, at most one per mass and offset), 9 grid
                                  box with each warp's stream fed through a ring
-                                 of bulk copies in shared memory (box_ring).  4
-                                 to 9 return TITAN_E_UNSUPPORTED if their tables
-                                 do not fit or their layout conditions fail */
+                                 of bulk copies in shared memory, 10 two-phase
+                                 cube (as 8: every spring in a cube evaluated
+                                 once, forces exchanged through shared memory
+                                 in direction groups).  4 to 10 return
+                                 TITAN_E_UNSUPPORTED if their tables do not fit
+                                 or their layout conditions fail            */
     int32_t l2_persist;       /* nonzero (default): keep the two state buffers of a
                                  CSR simulation resident in L2 (an access-policy
                                  window on the grid-box, cube and halo step
@@ -129,8 +132,11 @@ typedef struct {
                                  persisting part of L2; the context's
                                  persisting-L2 limit is raised while any such
                                  handle lives and restored by titan_destroy)    */
-    int32_t box_ring;         /* kernel variant 9's ring per warp: 0 or 1 (default)
-                                 4 stages of 2 columns, 2: 6 x 2, 3: 3 x 4      */
+    int32_t kernel_config;    /* 0..3, the chosen variant's shape (0: default).
+                                 9: ring per warp, 0/1 4 stages x 2 columns,
+                                 2: 6 x 2, 3: 3 x 4.  10: directions per group,
+                                 0/1: 4, 2: 7, 3: 13.  Results do not depend
+                                 on it (bit for bit)                            */
     int32_t reserved[4];      /* zero                                              */
 } titan_params;
 

@@ -11,6 +11,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <thread>
 #include <atomic>
 #include <cmath>
 #include <mutex>
@@ -160,6 +161,8 @@ void l2_persist_off(titan_sim *sim) {
 void release(titan_sim *sim) {
     l2_persist_off(sim);
     free_graphs(sim);
+    if (sim->state_stage) cudaFreeHost(sim->state_stage);
+    if (sim->state_staged) cudaEventDestroy(sim->state_staged);
     for (int b = 0; b < 2; ++b) {
         if (sim->snap_host[b]) cudaFreeHost(sim->snap_host[b]);
         if (sim->snap_ready[b]) cudaEventDestroy(sim->snap_ready[b]);
@@ -191,8 +194,8 @@ titan_status validate(const titan_masses *m, const titan_springs *sp, const tita
     if (p->exec < TITAN_EXEC_AUTO || p->exec > TITAN_EXEC_PERSISTENT)
         return fail(nullptr, TITAN_E_INVALID, "params.exec out of range");
     if (p->device < 0) return fail(nullptr, TITAN_E_INVALID, "params.device must be >= 0");
-    if (p->kernel_variant < 0 || p->kernel_variant > 9) return fail(nullptr, TITAN_E_INVALID, "params.kernel_variant must be 0..9");
-    if (p->box_ring < 0 || p->box_ring > 3) return fail(nullptr, TITAN_E_INVALID, "params.box_ring must be 0..3");
+    if (p->kernel_variant < 0 || p->kernel_variant > 10) return fail(nullptr, TITAN_E_INVALID, "params.kernel_variant must be 0..10");
+    if (p->kernel_config < 0 || p->kernel_config > 3) return fail(nullptr, TITAN_E_INVALID, "params.kernel_config must be 0..3");
     for (uint64_t i = 0; i < m->n; ++i) {
         for (int a = 0; a < 3; ++a) {
             if (!finite(m->pos[3 * i + a])) return fail(nullptr, TITAN_E_INVALID, "masses.pos has a non-finite value at mass " + std::to_string(i));
@@ -229,6 +232,50 @@ void fill_state(const titan_sim *sim, const double *pos, const double *vel, std:
     }
 }
 
+// fill_state into `out` ([n_dev]) on up to 16 host threads, each checking its
+// masses' values; false (and `out` partly written) if one is not finite.
+bool fill_state_parallel(const titan_sim *sim, const double *pos, const double *vel, MassState *out) {
+    const uint32_t nd = sim->n_dev;
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const unsigned nt = (unsigned)std::min<uint64_t>(std::min(16u, hw), std::max<uint64_t>(1, nd / 65536));
+    std::atomic<bool> ok{true};
+    auto work = [&](unsigned t) {
+        const uint32_t d0 = (uint32_t)((uint64_t)nd * t / nt), d1 = (uint32_t)((uint64_t)nd * (t + 1) / nt);
+        for (uint32_t d = d0; d < d1; ++d) {
+            const uint32_t i = sim->caller_of_dev[d];
+            MassState m;
+            if (i == UINT32_MAX) {            // hole: a fixed, unconnected slot
+                m.p = make_float4(0.f, 0.f, 0.f, 0.f);
+                m.v = make_float4(0.f, 0.f, 0.f, 0.f);
+                out[d] = m;
+                continue;
+            }
+            const double *x = pos + 3 * (size_t)i, *v = vel ? vel + 3 * (size_t)i : nullptr;
+            if (!std::isfinite(x[0]) || !std::isfinite(x[1]) || !std::isfinite(x[2]) ||
+                (v && (!std::isfinite(v[0]) || !std::isfinite(v[1]) || !std::isfinite(v[2])))) {
+                ok.store(false, std::memory_order_relaxed);
+                return;
+            }
+            m.p = make_float4((float)x[0], (float)x[1], (float)x[2], sim->inv_mass[i]);
+            m.v = v ? make_float4((float)v[0], (float)v[1], (float)v[2], 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+            out[d] = m;
+        }
+    };
+    if (nt == 1) {
+        work(0);
+    } else {
+        std::vector<std::thread> pool;
+        for (unsigned t = 1; t < nt; ++t) pool.emplace_back(work, t);
+        work(0);
+        for (auto &th : pool) th.join();
+    }
+    return ok.load();
+}
+
+// The cube kernels (8 and 10) run from the cube stream.
+bool uses_cube(const titan_sim *sim) { return sim->csr_kernel == 8 || sim->csr_kernel == 10; }
+
+
 // Uploads the per-entry actuation arrays of the current layout.
 cudaError_t upload_actuation(titan_sim *sim) {
     cudaError_t e;
@@ -240,7 +287,7 @@ cudaError_t upload_actuation(titan_sim *sim) {
             if (q != UINT32_MAX) a[e2] = make_float2(sim->act_amp[q], sim->act_phase[q]);
         }
         if ((e = upload(sim->d_act, a, sim->stream)) != cudaSuccess) return e;
-        if (sim->csr_kernel == 8) {
+        if (uses_cube(sim)) {
             if (!sim->d_cact && (e = dev_alloc(sim, &sim->d_cact, sim->cube.entries)) != cudaSuccess) return e;
             std::vector<float2> ca(sim->cube.entries, make_float2(0.f, 0.f));
             for (uint32_t e2 = 0; e2 < sim->cube.entries; ++e2) {
@@ -265,15 +312,20 @@ cudaError_t enqueue_step_io(titan_sim *sim, cudaStream_t st, const MassState *in
     if (sim->accumulate == TITAN_ACCUM_CSR) {
         titan::SellView v{sim->d_slice_off, sim->d_nbr, sim->d_kl, sim->has_c ? sim->d_c : nullptr,
                           sim->has_act ? sim->d_act : nullptr, 0, sim->spin_limit, sim->d_err};
-        if (sim->csr_kernel >= 6 && sim->csr_kernel <= 9) {
+        if (sim->csr_kernel >= 6 && sim->csr_kernel <= 10) {
             titan::BoxView h{sim->d_col_off, sim->d_own_slot, sim->d_ext_off, sim->d_ext_idx, sim->d_ext_slot,
                              (sim->box.max_table + 1) & ~1u};
             if (sim->csr_kernel == 9)
-                return titan::launch_step_box_ring(in, out, sim->n_dev, v, h, sim->box_ring, sim->c, si, so, st,
+                return titan::launch_step_box_ring(in, out, sim->n_dev, v, h, sim->kernel_config, sim->c, si, so, st,
                                                    sim->l2_on ? &sim->l2win : nullptr);
-            if (sim->csr_kernel == 8) {
+            if (uses_cube(sim)) {
                 titan::CubeView cv{sim->d_cube_base, sim->d_cube_meta, sim->d_ckl, sim->has_c ? sim->d_cc : nullptr,
                                    sim->has_act ? sim->d_cact : nullptr};
+                if (sim->csr_kernel == 10) {
+                    titan::Cube2View c2{cv, sim->d_cext_slot, sim->d_cube_partner, sim->cube2_ext_cap};
+                    return titan::launch_step_cube2(in, out, sim->n_dev, c2, h, sim->kernel_config, sim->c, si, so,
+                                                    st, sim->l2_on ? &sim->l2win : nullptr);
+                }
                 return titan::launch_step_cube(in, out, sim->n_dev, cv, h, sim->c, si, so, st,
                                                sim->l2_on ? &sim->l2win : nullptr);
             }
@@ -460,7 +512,7 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
     sim->c.c_uniform = (float)p->damping;
     sim->c.act_omega = 0.0;
     sim->kernel_variant = p->kernel_variant;
-    sim->box_ring = p->box_ring;
+    sim->kernel_config = p->kernel_config;
     sim->exec_req = p->exec;
     sim->spin_limit = p->spin_limit == 0 ? kDefaultSpinLimit
                                          : (uint32_t)(p->spin_limit > 0xffffffffull ? 0xffffffffull : p->spin_limit);
@@ -589,17 +641,17 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
             return bail(fail(sim, TITAN_E_UNSUPPORTED, "padded incidence exceeds 2^32 entries"));
         const int want = p->kernel_variant;
         sim->csr_kernel = want == 0 ? (sim->grid_order ? 6 : 4) : want;
-        if (sim->csr_kernel >= 6 && sim->csr_kernel <= 9 &&
+        if (sim->csr_kernel >= 6 && sim->csr_kernel <= 10 &&
             !(sim->grid_order && titan::build_box(nd, sim->sell, cells, sim->caller_of_dev, kHaloMaxSlots, sim->box))) {
             if (want >= 6)
                 return bail(fail(sim, TITAN_E_UNSUPPORTED, "the grid box kernel needs masses on a grid whose "
                                                            "blocks' boxes fit " + std::to_string(kHaloMaxSlots) + " slots"));
             sim->csr_kernel = 4;
         }
-        if (sim->csr_kernel == 8 &&
+        if (uses_cube(sim) &&
             !titan::build_cube(nd, s, sp->ends, sim->dev_of_caller, sim->sell, cells, sim->caller_of_dev, sim->box,
                                sim->cube)) {
-            if (want == 8)
+            if (want == 8 || want == 10)
                 return bail(fail(sim, TITAN_E_UNSUPPORTED, "the cube kernel needs 26-neighbour springs on a grid, "
                                                            "at most one per mass and offset"));
             sim->csr_kernel = 6;
@@ -635,7 +687,7 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
         CREATE_CK(dev_alloc(sim, &sim->d_kl, E));
         CREATE_CK(upload(sim->d_slice_off, sim->sell.slice_off, sim->stream));
         CREATE_CK(upload(sim->d_kl, kl, sim->stream));
-        if (sim->csr_kernel >= 6 && sim->csr_kernel <= 9) {
+        if (sim->csr_kernel >= 6 && sim->csr_kernel <= 10) {
             const titan::BoxHost &h = sim->box;
             CREATE_CK(dev_alloc(sim, &sim->d_col_off, h.col_off.size()));
             CREATE_CK(dev_alloc(sim, &sim->d_own_slot, nd));
@@ -647,7 +699,7 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
             CREATE_CK(upload(sim->d_ext_off, h.ext_off, sim->stream));
             CREATE_CK(upload(sim->d_ext_idx, h.ext_idx, sim->stream));
             CREATE_CK(upload(sim->d_ext_slot, h.ext_slot, sim->stream));
-            if (sim->csr_kernel == 8) {
+            if (uses_cube(sim)) {
                 const titan::CubeHost &cu = sim->cube;
                 std::vector<float2> ckl(cu.entries, make_float2(0.f, titan::kPadRest));
                 std::vector<float> c2;
@@ -669,6 +721,16 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
                 if (sim->has_c) {
                     CREATE_CK(dev_alloc(sim, &sim->d_cc, c2.size()));
                     CREATE_CK(upload(sim->d_cc, c2, sim->stream));
+                }
+                std::vector<uint32_t> xslot;
+                std::vector<uint8_t> ptab;
+                if (sim->csr_kernel == 10) {
+                    sim->cube2_ext_cap = titan::build_cube_ext_slots(sim->cube, sim->box, (uint32_t)titan::cube2_group(sim->kernel_config), xslot);
+                    titan::cube_partner_table(ptab);
+                    CREATE_CK(dev_alloc(sim, &sim->d_cext_slot, xslot.size()));
+                    CREATE_CK(dev_alloc(sim, &sim->d_cube_partner, ptab.size()));
+                    CREATE_CK(upload(sim->d_cext_slot, xslot, sim->stream));
+                    CREATE_CK(upload(sim->d_cube_partner, ptab, sim->stream));
                 }
                 CREATE_CK(cudaStreamSynchronize(sim->stream));     // the host vectors go out of scope
             }
@@ -858,18 +920,34 @@ titan_status titan_set_state(titan_sim *sim, const double *pos, const double *ve
     BusyGuard bg(sim);
     if (!bg.acquired) return fail(sim, TITAN_E_BUSY, "another call on this handle is in progress");
     if (sim->n && !pos) return fail(sim, TITAN_E_INVALID, "pos is required");
-    for (uint64_t i = 0; i < 3 * (uint64_t)sim->n; ++i)
-        if (!std::isfinite(pos[i]) || (vel && !std::isfinite(vel[i])))
-            return fail(sim, TITAN_E_INVALID, "non-finite pos or vel");
     DeviceGuard dg(sim->device);
     {
         titan_status es_ = titan::ensure_layout(sim);
         if (es_ != TITAN_OK) return es_;
     }
-    std::vector<MassState> st;
-    fill_state(sim, pos, vel, st);
-    TITAN_CK(sim, upload(sim->state[sim->cur], st, sim->stream));
-    // pageable source: the copy is staged before cudaMemcpyAsync returns
+    const size_t nd = sim->n_dev;
+    if (nd == 0) return TITAN_OK;
+    // a library-owned pinned staging buffer: the device-order states are
+    // written there (validated and converted on several host threads) and
+    // leave in one asynchronous copy; its previous copy must be done first
+    if (sim->state_stage_cap < nd) {
+        if (sim->state_stage) {
+            TITAN_CK(sim, cudaEventSynchronize(sim->state_staged));
+            cudaFreeHost(sim->state_stage);
+            sim->state_stage = nullptr;
+            sim->state_stage_cap = 0;
+        }
+        TITAN_CK(sim, cudaHostAlloc((void **)&sim->state_stage, nd * sizeof(MassState), cudaHostAllocDefault));
+        sim->state_stage_cap = nd;
+        if (!sim->state_staged) TITAN_CK(sim, cudaEventCreateWithFlags(&sim->state_staged, cudaEventDisableTiming));
+    } else {
+        TITAN_CK(sim, cudaEventSynchronize(sim->state_staged));
+    }
+    if (!fill_state_parallel(sim, pos, vel, sim->state_stage))
+        return fail(sim, TITAN_E_INVALID, "non-finite pos or vel");
+    TITAN_CK(sim, cudaMemcpyAsync(sim->state[sim->cur], sim->state_stage, nd * sizeof(MassState),
+                                  cudaMemcpyHostToDevice, sim->stream));
+    TITAN_CK(sim, cudaEventRecord(sim->state_staged, sim->stream));
     return TITAN_OK;
 }
 
@@ -981,7 +1059,7 @@ cudaError_t enable_per_spring_damping(titan_sim *sim) {
             if (sim->sell.spring[e2] != UINT32_MAX) cc[e2] = sim->damp[sim->sell.spring[e2]];
         if (!sim->d_c && (e = dev_alloc(sim, &sim->d_c, sim->sell.entries)) != cudaSuccess) return e;
         if ((e = upload(sim->d_c, cc, sim->stream)) != cudaSuccess) return e;
-        if (sim->csr_kernel == 8) {
+        if (uses_cube(sim)) {
             std::vector<float> c2(sim->cube.entries, 0.f);
             for (uint32_t e2 = 0; e2 < sim->cube.entries; ++e2)
                 if (sim->cube.spring[e2] != UINT32_MAX) c2[e2] = sim->damp[sim->cube.spring[e2]];
@@ -1013,7 +1091,7 @@ cudaError_t push_springs(titan_sim *sim, const std::vector<uint32_t> &ids, bool 
                 wi.push_back(2 * e + 1); wv.push_back(fbits(lf));
                 if (damping) { ci.push_back(e); cv.push_back(fbits(sim->damp[q])); }
                 if (actuation) { ai.push_back(2 * e); av.push_back(fbits(sim->act_amp[q])); }
-                if (sim->csr_kernel == 8) {
+                if (uses_cube(sim)) {
                     const uint32_t x = sim->cube.pos_of_end[2 * (size_t)q + end];
                     if (x == UINT32_MAX) continue;                  // this end receives the force
                     xwi.push_back(2 * x); xwv.push_back(fbits(kf));

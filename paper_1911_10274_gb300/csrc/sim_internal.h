@@ -68,6 +68,9 @@ struct SimCore {
     uint4 *d_cube_meta = nullptr;         //              per (cube, pass, warp) masks, ext base, offset
     float2 *d_ckl = nullptr, *d_cact = nullptr;   //      cube stream {k, L0}, actuation
     float *d_cc = nullptr;                //              cube stream damping
+    uint32_t *d_cext_slot = nullptr;      // two-phase cube kernel: own | partner slot of each ext entry
+    uint8_t *d_cube_partner = nullptr;    //                        [13][256] in-cube partner lanes
+    uint32_t cube2_ext_cap = 0;           //                        largest ext count of a direction group
     float2 *d_kl = nullptr, *d_act = nullptr;
     float *d_c = nullptr;
 
@@ -78,7 +81,7 @@ struct SimCore {
 
     int graph_chunk = kDefaultGraphChunk;
     int kernel_variant = 0;
-    int box_ring = 0;                     // kernel variant 9's ring configuration
+    int kernel_config = 0;                // variant-specific configuration (titan_params.kernel_config)
     uint32_t spin_limit = kDefaultSpinLimit;
     int *d_err = nullptr;                 // device error flag (bounded waits)
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -86,6 +89,9 @@ struct SimCore {
     // snapshots: slot = ticket & 1
     float *snap_dev[2] = {nullptr, nullptr};     // [2][n][3] pos then vel, caller order
     float *snap_host[2] = {nullptr, nullptr};    // pinned, same layout
+    titan::MassState *state_stage = nullptr;     // pinned staging of titan_set_state ([n_dev])
+    size_t state_stage_cap = 0;
+    cudaEvent_t state_staged = nullptr;          // the staging buffer's last upload is done
     cudaEvent_t snap_ready[2] = {nullptr, nullptr};
     cudaEvent_t snap_done[2] = {nullptr, nullptr};
     double snap_t[2] = {0, 0};

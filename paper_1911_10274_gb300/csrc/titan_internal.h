@@ -93,6 +93,14 @@ struct CubeView {
     const float2 *act;           // or nullptr (no actuation)
 };
 
+// The two-phase cube kernel's extra arrays (step_cube2.cu).
+struct Cube2View {
+    CubeView cube;
+    const uint32_t *ext_slot;    // per cube-stream entry: own slot | outside partner's slot << 16 (ext entries)
+    const uint8_t *partner;      // [13][256] in-cube partner lane of each cell, 0xFF outside
+    uint32_t ext_cap;            // largest ext entry count of one direction group of one cube
+};
+
 struct AtomicView {
     const uint4 *rec;            // [S] {i, j, bits(k), bits(L0)}
     const float *c;              // [S] or nullptr
@@ -141,6 +149,15 @@ cudaError_t launch_step_box_ring(const MassState *in, MassState *out, uint32_t n
 size_t box_ring_smem_bytes(uint32_t table_slots, uint32_t ring_cols, bool has_c, bool has_act);
 int box_ring_stages(int config);
 int box_ring_cols(int config);
+
+// Two-phase cube form (step_cube2.cu): each spring in a cube evaluated once,
+// forces exchanged through shared memory in groups of cube2_group(config)
+// directions.  n a multiple of 256, table_slots even.
+cudaError_t launch_step_cube2(const MassState *in, MassState *out, uint32_t n, const Cube2View &v, const BoxView &h,
+                              int config, const StepConst &c, const long long *step_in, long long *step_out,
+                              cudaStream_t stream, const cudaAccessPolicyWindow *l2win = nullptr);
+size_t cube2_smem_bytes(uint32_t table_slots, int group, uint32_t ext_cap);
+int cube2_group(int config);
 
 // Halo form with the half-edge stream staged into shared memory by TMA bulk
 // copies; slices wider than w_max columns read from global memory.

@@ -182,6 +182,53 @@ class Surrogate:
         return y.cpu().numpy()[:n].astype(np.float64) * self.sd + self.mu
 
 
+class Ensemble:
+    """Several surrogates that differ in their initial weights and each see
+    their own bootstrap resample of the training set.  Their spread measures
+    how far a candidate lies from anything they were trained on, which a
+    single network's point prediction cannot show; predict() returns the
+    screening score mean + kappa * std (an upper confidence bound), so a
+    mutant the members disagree on is simulated rather than discarded."""
+
+    def __init__(self, members: int = 5, hidden: int = 512, seed: int = 0, device: int = 0, kappa: float = 1.0):
+        self.members = [Surrogate(hidden=hidden, seed=seed * 1000 + k, device=device) for k in range(members)]
+        self.kappa = float(kappa)
+        self.seed = seed
+
+    def _boot(self, n: int, k: int, salt: int) -> np.ndarray:
+        return np.random.default_rng([self.seed, k, salt]).integers(0, n, n)
+
+    def fit(self, X: np.ndarray, y: np.ndarray, epochs: int = 20, batch: int = 4096, lr: float = 1e-3,
+            seed: int = 0) -> List[float]:
+        out = []
+        for k, m in enumerate(self.members):
+            idx = self._boot(len(X), k, seed)
+            out.append(m.fit(X[idx], y[idx], epochs=epochs, batch=batch, lr=lr, seed=seed + k)[-1])
+        return out
+
+    def refine(self, X: np.ndarray, y: np.ndarray, epochs: int = 3, batch: int = 1024, lr: float = 5e-4,
+               seed: int = 0) -> None:
+        for k, m in enumerate(self.members):
+            idx = self._boot(len(X), k, 7919 + seed)
+            m.refine(X[idx], y[idx], epochs=epochs, batch=batch, lr=lr, seed=seed + k)
+
+    def predict_stats(self, X: np.ndarray):
+        P = np.stack([m.predict(X) for m in self.members])
+        return P.mean(axis=0), P.std(axis=0)
+
+    def predict(self, X: np.ndarray) -> np.ndarray:
+        mu, sd = self.predict_stats(X)
+        return mu + self.kappa * sd
+
+    def get_state(self):
+        return [(m.net.get_params(), m.mu, m.sd) for m in self.members]
+
+    def set_state(self, state) -> None:
+        for m, (p, mu, sd) in zip(self.members, state):
+            m.net.set_params(p)
+            m.mu, m.sd = mu, sd
+
+
 def spearman(a, b) -> float:
     ra = np.argsort(np.argsort(a))
     rb = np.argsort(np.argsort(b))
@@ -291,7 +338,15 @@ def main(argv=None):
                     help="rollout cap of the screened searches; 0: the plain search's own rollouts")
     ap.add_argument("--fitness-cache", default=None,
                     help="npz file holding the training robots' simulated fitness (written if absent)")
+    ap.add_argument("--search-seeds", default=None,
+                    help="comma-separated search seeds: run every arm once per seed from the same trained "
+                         "networks and report rollouts-to-plain-best per seed (one JSON line per seed, then a summary)")
+    ap.add_argument("--ensemble", type=int, default=0, help="also run the ensemble-screened arm with this many members")
+    ap.add_argument("--kappa", type=float, default=1.0, help="ensemble screening score: mean + kappa * std")
+    ap.add_argument("--no-single", action="store_true", help="skip the single-network screened arm")
     a = ap.parse_args(argv)
+    if a.search_seeds:
+        return multi_seed(a)
     rng = np.random.default_rng(a.seed)
     t0 = time.time()
     morphs = [random_morph(rng) for _ in range(a.train)]
@@ -351,6 +406,106 @@ def main(argv=None):
            "curves": {k: thin(v["history"]) for k, v in (("plain", plain), ("surrogate", scr), ("random", rnd))}}
     print(json.dumps(out))
     return out
+
+
+def _train_set(a):
+    """The random training robots, their simulated fitness (cached in
+    a.fitness_cache when given) and the wall time spent simulating."""
+    import os
+    import time
+    rng = np.random.default_rng(a.seed)
+    t0 = time.time()
+    morphs = [random_morph(rng) for _ in range(a.train)]
+    key = f"{a.seed}-{a.train}-{a.steps}"
+    y = None
+    if a.fitness_cache and os.path.exists(a.fitness_cache):
+        d = np.load(a.fitness_cache)
+        if str(d["key"]) == key:
+            y = d["y"]
+    if y is None:
+        y = fitness(morphs, a.steps)
+        if a.fitness_cache:
+            np.savez(a.fitness_cache, key=key, y=y)
+    return morphs, y, time.time() - t0
+
+
+def multi_seed(a):
+    """Every arm (plain, single-network screened, ensemble screened, random
+    pick) once per search seed, all from the same trained networks (their
+    parameters restored before each search), each screened arm capped at the
+    plain search's rollouts.  Prints one JSON line per seed and a summary with
+    the median rollouts-to-plain-best of each arm (None counts as not reached)."""
+    import json
+    import time
+    morphs, y, t_sim = _train_set(a)
+    n_val = max(128, a.train // 10)
+    am, ay = mirrored(morphs[:-n_val], y[:-n_val])
+    Xtr = encode(am)
+    start, start_fit = morphs[-n_val:], y[-n_val:]
+    t1 = time.time()
+    single = None
+    if not a.no_single:
+        single = Surrogate(seed=a.seed)
+        single.fit(Xtr, ay, epochs=a.epochs)
+        single_state = (single.net.get_params(), single.mu, single.sd)
+    ens = None
+    if a.ensemble > 0:
+        ens = Ensemble(members=a.ensemble, seed=a.seed, kappa=a.kappa)
+        ens.fit(Xtr, ay, epochs=a.epochs)
+        ens_state = ens.get_state()
+    t_fit = time.time() - t1
+    val = {}
+    Xval = encode(start)
+    if single is not None:
+        val["single_spearman"] = spearman(single.predict(Xval), start_fit)
+    if ens is not None:
+        mu, sd = ens.predict_stats(Xval)
+        val["ensemble_mean_spearman"] = spearman(mu, start_fit)
+        val["ensemble_ucb_spearman"] = spearman(mu + a.kappa * sd, start_fit)
+    big = 10 ** 9
+    rows = []
+    for sseed in [int(x) for x in a.search_seeds.split(",")]:
+        t2 = time.time()
+        plain = search("plain", start, start_fit, a.generations, a.mutants, a.screened, a.steps, seed=sseed)
+        target, budget = plain["best"], plain["rollouts"]
+        arms = {"plain": {"best": target, "rollouts": budget, "rollouts_to_plain_best":
+                          rollouts_to_reach(plain["history"], target), "s": time.time() - t2}}
+        todo = []
+        if single is not None:
+            todo.append(("single", single, single_state))
+        if ens is not None:
+            todo.append(("ensemble", ens, ens_state))
+        todo.append(("random", None, None))
+        for name, model, state in todo:
+            t3 = time.time()
+            if name == "single":
+                model.net.set_params(state[0])
+                model.mu, model.sd = state[1], state[2]
+            elif name == "ensemble":
+                model.set_state(state)
+            r = search("random" if model is None else "surrogate", start, start_fit, big, a.mutants, a.screened,
+                       a.steps, seed=sseed, surrogate=model, target=target, max_rollouts=budget,
+                       refine_epochs=a.refine_epochs, refine_window=a.refine_window)
+            arms[name] = {"best": r["best"], "rollouts": r["rollouts"],
+                          "rollouts_to_plain_best": rollouts_to_reach(r["history"], target),
+                          "plain_best_at_same_rollouts": best_at(plain["history"], r["rollouts"]),
+                          "s": time.time() - t3}
+        row = {"search_seed": sseed, "arms": arms}
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+
+    def med(name):
+        v = [r["arms"][name]["rollouts_to_plain_best"] for r in rows if name in r["arms"]]
+        v = [x if x is not None else float("inf") for x in v]
+        return float(np.median(v)) if v else None
+
+    summary = {"summary": True, "train_rollouts": a.train, "steps": a.steps, "simulate_s": t_sim, "fit_s": t_fit,
+               "mutants": a.mutants, "screened": a.screened, "generations": a.generations,
+               "ensemble": a.ensemble, "kappa": a.kappa, "refine_window": a.refine_window,
+               "validation": val, "seeds": [r["search_seed"] for r in rows],
+               "median_rollouts_to_plain_best": {k: med(k) for k in rows[0]["arms"]} if rows else {}}
+    print(json.dumps(summary), flush=True)
+    return {"rows": rows, "summary": summary}
 
 
 if __name__ == "__main__":
