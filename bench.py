@@ -300,7 +300,8 @@ def config_for(args, system, resolved=None):
     cfg = {"workload": WORKLOADS[args.workload],
            "accumulate": args.accumulate,
            "order": "input order (no reordering)" if args.order == "input"
-           else ("grid cubes of 8x8x4 cells, Morton" if resolved == 6 else "morton"), "graph_chunk": 64,
+           else ("grid cubes of 8x8x4 cells, Morton" if resolved in (6, 8, 9, 10) else "morton"),
+           "graph_chunk": 64 if args.graph_chunk == 0 else args.graph_chunk,
            "csr_kernel": CSR_KERNELS.get(resolved, f"variant {args.kernel_variant}"),
            "parallelism": f"replicas x{args.gpus}", "exec": args.exec,
            "l2_persist": not getattr(args, "no_l2_persist", False),
@@ -467,7 +468,7 @@ def run_ours(args):
     order = T.ORDER_MORTON if args.order == "morton" else T.ORDER_INPUT
     sim = T.Sim(system, accumulate=acc, stream=stream.cuda_stream, device=local,
                 kernel_variant=args.kernel_variant, exec_mode=exec_mode, order=order,
-                l2_persist=not args.no_l2_persist, kernel_config=args.kernel_config)
+                l2_persist=not args.no_l2_persist, kernel_config=args.kernel_config, graph_chunk=args.graph_chunk)
     launches_per_step = 1 if acc == T.ACCUM_CSR else 2
     resolved = sim.csr_kernel
     persistent = sim.exec_mode == T.EXEC_PERSISTENT
@@ -580,6 +581,8 @@ def main():
     ap.add_argument("--exec", choices=["auto", "launch", "persistent"], default="auto",
                     help="step loop: persistent cluster kernel (small systems), per-step launches, or auto")
     ap.add_argument("--kernel-variant", type=int, default=0, help="CSR kernel: 0 auto, 1 direct loads, 2 TMA-staged, 3 bulk L2 prefetch, 4 halo, 5 halo+TMA, 6 grid box, 7 grid box+TMA, 8 cube, 9 grid box + stream ring")
+    ap.add_argument("--graph-chunk", type=int, default=0,
+                    help="steps per captured CUDA graph (0: the library default; < 0: direct launches)")
     ap.add_argument("--kernel-config", type=int, default=0, help="variant 9: ring per warp (0/1 4x2 columns, 2 6x2, 3 3x4); variant 10: directions per group (0/1 4, 2 7, 3 13)")
     args = ap.parse_args()
     if args.warmup < 3:

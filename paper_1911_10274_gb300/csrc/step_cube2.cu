@@ -47,11 +47,15 @@ k_step_cube2(const MassState *__restrict__ in, MassState *__restrict__ out, uint
              const uint32_t *__restrict__ ext_idx, const uint16_t *__restrict__ ext_tslot, uint32_t table_slots,
              uint32_t ext_cap, StepConst c, const long long *__restrict__ step_in, long long *__restrict__ step_out) {
     extern __shared__ float4 c2sm[];
+    // the cube's pass metadata and the partner table, read many times per step, live in shared memory
+    __shared__ uint4 smeta[kC2Dirs * (kC2Threads / 32)];
+    __shared__ uint32_t sptab[kC2Dirs * kC2Threads / 4];
     float4 *tA = c2sm;
     float2 *tB = reinterpret_cast<float2 *>(c2sm + table_slots);
     float4 *store = reinterpret_cast<float4 *>(tB + table_slots);      // [G][256] plus terms, then ext terms
     float4 *ext_store = store + G * kC2Threads;
-    float4 *zero_slot = ext_store + ext_cap;
+    const uint32_t zero_idx = G * kC2Threads + ext_cap;                 // a slot holding (0, 0, 0, 0)
+    const uint8_t *ptab = reinterpret_cast<const uint8_t *>(sptab);
     const uint32_t b = blockIdx.x, tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     const uint32_t i = b * kC2Threads + tid;
     long long step = 0;
@@ -62,10 +66,10 @@ k_step_cube2(const MassState *__restrict__ in, MassState *__restrict__ out, uint
     const uint32_t base = __ldg(cube_base + b);
     const uint32_t ext0 = base + kC2Dirs * kC2Threads;
     const uint4 *mt = cube_meta + (size_t)b * kC2Dirs * (kC2Threads / 32);   // [dir][warp]
-    // the cube's ext entries: in direction order; the count from the last direction's last warp
-    const uint4 m_last = __ldg(mt + (kC2Dirs - 1) * (kC2Threads / 32) + (kC2Threads / 32 - 1));
-    const uint32_t ext_total = m_last.z + __popc(m_last.y);
-    if (tid == 0) *zero_slot = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (tid < kC2Dirs * (kC2Threads / 32)) smeta[tid] = __ldg(mt + tid);
+    for (uint32_t k = tid; k < kC2Dirs * kC2Threads / 4; k += kC2Threads)
+        sptab[k] = __ldg(reinterpret_cast<const uint32_t *>(partner) + k);
+    if (tid == 0) store[zero_idx] = make_float4(0.f, 0.f, 0.f, 0.f);
 
     // the first group's plus entries are requested before the table fill
     float2 pk[G], ps[G];
@@ -92,6 +96,9 @@ k_step_cube2(const MassState *__restrict__ in, MassState *__restrict__ out, uint
     }
     __syncthreads();
 
+    // the cube's ext entries, in direction order: the count from the last direction's last warp
+    const uint4 m_last = smeta[kC2Dirs * (kC2Threads / 32) - 1];
+    const uint32_t ext_total = m_last.z + __popc(m_last.y);
     const float clk = HAS_ACT ? actuation_clock(c, step) : 0.f;
     const uint32_t below = (1u << lane) - 1u;
     float fx = 0.f, fy = 0.f, fz = 0.f;
@@ -103,7 +110,7 @@ k_step_cube2(const MassState *__restrict__ in, MassState *__restrict__ out, uint
         for (int q = 0; q < G; ++q) {
             if (q >= nd) break;
             const int j = j0 + q;
-            const int32_t off = (int32_t)(int16_t)(__ldg(mt + j * (kC2Threads / 32)).w & 0xffffu);
+            const int32_t off = (int32_t)(int16_t)(smeta[j * (kC2Threads / 32)].w & 0xffffu);
             const float2 a = pk[q];
             float f = 0.f, ux = 0.f, uy = 0.f, uz = 0.f;
             if (valid && a.y >= 0.f) {                       // not padding (no +p spring)
@@ -117,8 +124,8 @@ k_step_cube2(const MassState *__restrict__ in, MassState *__restrict__ out, uint
             store[q * kC2Threads + tid] = make_float4(f, ux, uy, uz);
         }
         // the group's ext springs, evaluated from the outside partner's side
-        const uint32_t e_lo = __ldg(mt + j0 * (kC2Threads / 32)).z;
-        const uint32_t e_hi = j0 + G < kC2Dirs ? __ldg(mt + (j0 + G) * (kC2Threads / 32)).z : ext_total;
+        const uint32_t e_lo = smeta[j0 * (kC2Threads / 32)].z;
+        const uint32_t e_hi = j0 + G < kC2Dirs ? smeta[(j0 + G) * (kC2Threads / 32)].z : ext_total;
         for (uint32_t e = e_lo + tid; e < e_hi; e += kC2Threads) {
             const uint32_t sl = __ldg(ext_slot + ext0 + e);
             const uint32_t so = sl & 0xffffu, sp = sl >> 16;          // receiving mass, outside partner
@@ -153,13 +160,12 @@ k_step_cube2(const MassState *__restrict__ in, MassState *__restrict__ out, uint
                 fx = fmaf(s.x, s.y, fx);
                 fy = fmaf(s.x, s.z, fy);
                 fz = fmaf(s.x, s.w, fz);
-                const uint4 m = __ldg(mt + j * (kC2Threads / 32) + w);
-                const float4 *src = zero_slot;
-                if ((m.x >> lane) & 1u)                     // -p partner in the cube: its +p slot
-                    src = store + q * kC2Threads + __ldg(partner + j * kC2Threads + tid);
-                else if ((m.y >> lane) & 1u)                // -p partner outside: the ext slot
-                    src = ext_store + (m.z + __popc(m.y & below) - e_lo);
-                const float4 g = *src;
+                const uint4 m = smeta[j * (kC2Threads / 32) + w];
+                // -p partner in the cube: its +p slot; outside: the ext slot; none: the zero slot
+                const uint32_t idx = ((m.x >> lane) & 1u) ? q * kC2Threads + ptab[j * kC2Threads + tid]
+                                   : ((m.y >> lane) & 1u) ? G * kC2Threads + (m.z + __popc(m.y & below) - e_lo)
+                                                          : zero_idx;
+                const float4 g = store[idx];
                 fx = fmaf(g.x, -g.y, fx);
                 fy = fmaf(g.x, -g.z, fy);
                 fz = fmaf(g.x, -g.w, fz);
@@ -230,7 +236,7 @@ cudaError_t launch_step_cube2(const MassState *in, MassState *out, uint32_t n, c
     switch (config) {
         case 2: return launch_c2<7, 4>(in, out, n, v, h, c, step_in, step_out, stream, l2win);
         case 3: return launch_c2<13, 2>(in, out, n, v, h, c, step_in, step_out, stream, l2win);
-        default: return launch_c2<4, 5>(in, out, n, v, h, c, step_in, step_out, stream, l2win);
+        default: return launch_c2<4, 4>(in, out, n, v, h, c, step_in, step_out, stream, l2win);
     }
 }
 
