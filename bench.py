@@ -34,15 +34,12 @@ METRIC = "spring updates/s"
 # the step kernel a Sim resolved to (titan_csr_kernel), and its description
 CSR_KERNEL_NAMES = {0: "k_springs_atomic+k_masses_atomic", 1: "k_step_sell", 2: "k_step_sell_staged",
                     3: "k_step_sell_pf", 4: "k_step_halo", 5: "k_step_halo_tma", 6: "k_step_box",
-                    7: "k_step_box_tma", 8: "k_step_cube", 9: "k_step_box_ring",
-                    10: "k_step_cube2"}
+                    7: "k_step_box_tma", 8: "k_step_cube"}
 CSR_KERNELS = {0: "atomic scatter", 1: "direct-loads", 2: "tma-staged", 3: "bulk-l2-prefetch",
                4: "halo (coloured neighbourhood table in shared memory)", 5: "halo+tma",
                6: "grid box (box table in shared memory, no neighbour index in the stream)",
                7: "grid box, stream staged in shared memory by TMA bulk copies",
-               8: "cube (springs inside a 256-mass cube read and evaluated once)",
-               9: "grid box, each warp's stream fed through a ring of bulk copies in shared memory",
-               10: "two-phase cube (each spring in a 256-mass cube evaluated once, forces exchanged in shared memory)"}
+               8: "cube (springs inside a 256-mass cube read and evaluated once)"}
 UNIT = "spring_updates/s"
 L2_BYTES = 126 * 1024 * 1024
 
@@ -305,6 +302,7 @@ def config_for(args, system, resolved=None):
            "csr_kernel": CSR_KERNELS.get(resolved, f"variant {args.kernel_variant}"),
            "parallelism": f"replicas x{args.gpus}", "exec": args.exec,
            "l2_persist": not getattr(args, "no_l2_persist", False),
+           "launch_overlap": not getattr(args, "no_launch_overlap", False),
            "l2": "inputs larger than L2 (spring data > 126 MB), no flush" if args.workload in ("lattice1m", "mesh2m")
            else "working set fits in L2 / shared memory, no flush (small-system latency case, not the headline)"}
     if system is not None:
@@ -468,7 +466,8 @@ def run_ours(args):
     order = T.ORDER_MORTON if args.order == "morton" else T.ORDER_INPUT
     sim = T.Sim(system, accumulate=acc, stream=stream.cuda_stream, device=local,
                 kernel_variant=args.kernel_variant, exec_mode=exec_mode, order=order,
-                l2_persist=not args.no_l2_persist, kernel_config=args.kernel_config, graph_chunk=args.graph_chunk)
+                l2_persist=not args.no_l2_persist, launch_overlap=not args.no_launch_overlap,
+                graph_chunk=args.graph_chunk)
     launches_per_step = 1 if acc == T.ACCUM_CSR else 2
     resolved = sim.csr_kernel
     persistent = sim.exec_mode == T.EXEC_PERSISTENT
@@ -580,10 +579,11 @@ def main():
                     help="device order of the masses: spatial (grid cubes or Morton) or the caller's order")
     ap.add_argument("--exec", choices=["auto", "launch", "persistent"], default="auto",
                     help="step loop: persistent cluster kernel (small systems), per-step launches, or auto")
-    ap.add_argument("--kernel-variant", type=int, default=0, help="CSR kernel: 0 auto, 1 direct loads, 2 TMA-staged, 3 bulk L2 prefetch, 4 halo, 5 halo+TMA, 6 grid box, 7 grid box+TMA, 8 cube, 9 grid box + stream ring")
+    ap.add_argument("--kernel-variant", type=int, default=0, help="CSR kernel: 0 auto, 1 direct loads, 2 TMA-staged, 3 bulk L2 prefetch, 4 halo, 5 halo+TMA, 6 grid box, 7 grid box+TMA, 8 cube")
     ap.add_argument("--graph-chunk", type=int, default=0,
                     help="steps per captured CUDA graph (0: the library default; < 0: direct launches)")
-    ap.add_argument("--kernel-config", type=int, default=0, help="variant 9: ring per warp (0/1 4x2 columns, 2 6x2, 3 3x4); variant 10: directions per group (0/1 4, 2 7, 3 13)")
+    ap.add_argument("--no-launch-overlap", action="store_true",
+                    help="launch the step kernels in plain stream order (no programmatic dependent launch)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -132,11 +132,13 @@ typedef struct {
                                  persisting part of L2; the context's
                                  persisting-L2 limit is raised while any such
                                  handle lives and restored by titan_destroy)    */
-    int32_t kernel_config;    /* 0..3, the chosen variant's shape (0: default).
-                                 9: ring per warp, 0/1 4 stages x 2 columns,
-                                 2: 6 x 2, 3: 3 x 4.  10: directions per group,
-                                 0/1: 4, 2: 7, 3: 13.  Results do not depend
-                                 on it (bit for bit)                            */
+    int32_t launch_overlap;   /* nonzero (default): the grid-box and halo step
+                                 kernels are launched as programmatic dependents
+                                 of the previous step, so a step's CTAs start
+                                 (and fetch their stream) while the previous
+                                 step's last CTAs finish; they read the state
+                                 only once it is complete.  0: plain stream
+                                 order.  No result depends on it (bit for bit) */
     int32_t reserved[4];      /* zero                                              */
 } titan_params;
 

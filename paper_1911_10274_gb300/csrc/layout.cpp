@@ -585,48 +585,6 @@ bool build_cube(uint32_t n, uint32_t s, const uint32_t *ends, const std::vector<
     return true;
 }
 
-uint32_t build_cube_ext_slots(const CubeHost &cube, const BoxHost &box, uint32_t group, std::vector<uint32_t> &out) {
-    constexpr uint32_t P = kCubePasses, W = kHaloBlock / 32;
-    const uint32_t n_cubes = cube.base.empty() ? 0 : (uint32_t)cube.base.size() - 1;
-    out.assign(cube.entries, 0u);
-    uint32_t cap = 0;
-    if (group == 0) return 0;
-    for (uint32_t b = 0; b < n_cubes; ++b) {
-        const uint32_t ext0 = cube.base[b] + P * kHaloBlock;
-        uint32_t group_start = 0;
-        for (uint32_t j = 0; j < P; ++j) {
-            if (j % group == 0) group_start = cube.meta[(((size_t)b * P + j) * W) * 4 + 2];
-            for (uint32_t w = 0; w < W; ++w) {
-                const uint32_t *mt = &cube.meta[(((size_t)b * P + j) * W + w) * 4];
-                const int32_t off = (int32_t)(int16_t)(uint16_t)(mt[3] & 0xffffu);
-                uint32_t e = mt[2];
-                for (uint32_t l = 0; l < 32; ++l) {
-                    if (!((mt[1] >> l) & 1u)) continue;
-                    const uint32_t own = box.own_slot[(size_t)b * kHaloBlock + w * 32 + l];
-                    const uint32_t part = (uint32_t)((int32_t)own - off);
-                    out[ext0 + e] = own | (part << 16);
-                    ++e;
-                    cap = std::max(cap, e - group_start);
-                }
-            }
-        }
-    }
-    return cap;
-}
-
-void cube_partner_table(std::vector<uint8_t> &out) {
-    out.assign(kCubePasses * kHaloBlock, 0xFF);
-    for (uint32_t j = 0; j < kCubePasses; ++j)
-        for (uint32_t t = 0; t < kHaloBlock; ++t) {
-            const int w = (int)(t >> 5), l = (int)(t & 31);
-            const int x = 4 * (w & 1) + (l & 3), y = 4 * ((w >> 1) & 1) + ((l >> 2) & 3), z = 2 * (w >> 2) + (l >> 4);
-            const int px = x - kCubeDirs[j][0], py = y - kCubeDirs[j][1], pz = z - kCubeDirs[j][2];
-            if (px < 0 || px >= 8 || py < 0 || py >= 8 || pz < 0 || pz >= 4) continue;
-            const int pw = (px >> 2) | ((py >> 2) << 1) | ((pz >> 1) << 2);
-            out[(size_t)j * kHaloBlock + t] = (uint8_t)(32 * pw + (px & 3) + 4 * (py & 3) + 16 * (pz & 1));
-        }
-}
-
 void build_records(uint32_t s, const uint32_t *ends, const std::vector<uint32_t> &dev_of,
                    RecordsHost &out) {
     out.order.resize(s);

@@ -131,20 +131,6 @@ bool build_cube(uint32_t n, uint32_t s, const uint32_t *ends, const std::vector<
                 const SellHost &sell, const std::vector<int32_t> &cell, const std::vector<uint32_t> &caller_of_dev,
                 const BoxHost &box, CubeHost &out);
 
-// For the two-phase cube kernel (step_cube2.cu): per cube-stream entry, the
-// box slots of an ext entry's receiving mass and of its outside -p partner
-// (own | partner << 16; 0 for plus entries and padding).  Returns the largest
-// number of ext entries that one group of `group` consecutive directions
-// (0..group-1, group..2 group-1, ...) of one cube holds.
-uint32_t build_cube_ext_slots(const CubeHost &cube, const BoxHost &box, uint32_t group, std::vector<uint32_t> &out);
-
-// The in-cube -p partner of every cell for every direction of kCubeDirs: out
-// [13][256], the index (0..255) in the cube of the cell c - d(j), or 0xFF when
-// that cell lies outside the cube.  Cells are indexed as in the grid order:
-// 32 (tile) + lane, tile = (x >> 2) + 2 (y >> 2) + 4 (z >> 1), lane = (x & 3) +
-// 4 (y & 3) + 16 (z & 1) for a cell (x, y, z) of the 8 x 8 x 4 cube.
-void cube_partner_table(std::vector<uint8_t> &out);
-
 struct RecordsHost {
     std::vector<uint32_t> order;            // [S] record r holds caller spring order[r]
     std::vector<uint32_t> slot_of_spring;   // [S] inverse of order

@@ -67,6 +67,16 @@ __device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 
+// Programmatic dependent launch.  A kernel launched with the
+// programmatic-stream-serialization attribute may start before the kernel
+// ahead of it in the stream has finished: grid_dep_wait() blocks until that
+// kernel has completed and its memory operations are visible (it returns at
+// once for a kernel launched normally).  grid_dep_launch() lets the next
+// kernel of the stream, if launched that way, start its CTAs once every CTA of
+// this grid has issued it or exited.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Hardware cluster barrier (all threads of all CTAs of the cluster).
 __device__ __forceinline__ void cluster_sync() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");

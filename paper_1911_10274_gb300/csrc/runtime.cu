@@ -108,10 +108,19 @@ cudaError_t upload(T *dst, const std::vector<T> &src, cudaStream_t st) {
 }
 
 void free_graphs(titan_sim *sim) {
-    for (auto &g : sim->graph) {
-        if (g) cudaGraphExecDestroy(g);
-        g = nullptr;
-    }
+    for (auto &lvl : sim->graph)
+        for (auto &g : lvl) {
+            if (g) cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    sim->graphs_built = false;
+}
+
+// Steps run by the captured graph of level L (0 when the level is unused).
+int graph_steps(const titan_sim *sim, int L) {
+    const int k = sim->graph_chunk >> L;
+    if (sim->graph_chunk <= 0 || L >= kGraphLevels || k < 2 || (k << L) != sim->graph_chunk || (k & 1)) return 0;
+    return k;
 }
 
 // The context-wide persisting-L2 limit is shared by every simulation that
@@ -194,8 +203,7 @@ titan_status validate(const titan_masses *m, const titan_springs *sp, const tita
     if (p->exec < TITAN_EXEC_AUTO || p->exec > TITAN_EXEC_PERSISTENT)
         return fail(nullptr, TITAN_E_INVALID, "params.exec out of range");
     if (p->device < 0) return fail(nullptr, TITAN_E_INVALID, "params.device must be >= 0");
-    if (p->kernel_variant < 0 || p->kernel_variant > 10) return fail(nullptr, TITAN_E_INVALID, "params.kernel_variant must be 0..10");
-    if (p->kernel_config < 0 || p->kernel_config > 3) return fail(nullptr, TITAN_E_INVALID, "params.kernel_config must be 0..3");
+    if (p->kernel_variant < 0 || p->kernel_variant > 8) return fail(nullptr, TITAN_E_INVALID, "params.kernel_variant must be 0..8");
     for (uint64_t i = 0; i < m->n; ++i) {
         for (int a = 0; a < 3; ++a) {
             if (!finite(m->pos[3 * i + a])) return fail(nullptr, TITAN_E_INVALID, "masses.pos has a non-finite value at mass " + std::to_string(i));
@@ -272,8 +280,8 @@ bool fill_state_parallel(const titan_sim *sim, const double *pos, const double *
     return ok.load();
 }
 
-// The cube kernels (8 and 10) run from the cube stream.
-bool uses_cube(const titan_sim *sim) { return sim->csr_kernel == 8 || sim->csr_kernel == 10; }
+// The cube kernel (8) runs from the cube stream.
+bool uses_cube(const titan_sim *sim) { return sim->csr_kernel == 8; }
 
 
 // Uploads the per-entry actuation arrays of the current layout.
@@ -312,27 +320,19 @@ cudaError_t enqueue_step_io(titan_sim *sim, cudaStream_t st, const MassState *in
     if (sim->accumulate == TITAN_ACCUM_CSR) {
         titan::SellView v{sim->d_slice_off, sim->d_nbr, sim->d_kl, sim->has_c ? sim->d_c : nullptr,
                           sim->has_act ? sim->d_act : nullptr, 0, sim->spin_limit, sim->d_err};
-        if (sim->csr_kernel >= 6 && sim->csr_kernel <= 10) {
+        if (sim->csr_kernel >= 6 && sim->csr_kernel <= 8) {
             titan::BoxView h{sim->d_col_off, sim->d_own_slot, sim->d_ext_off, sim->d_ext_idx, sim->d_ext_slot,
                              (sim->box.max_table + 1) & ~1u};
-            if (sim->csr_kernel == 9)
-                return titan::launch_step_box_ring(in, out, sim->n_dev, v, h, sim->kernel_config, sim->c, si, so, st,
-                                                   sim->l2_on ? &sim->l2win : nullptr);
             if (uses_cube(sim)) {
                 titan::CubeView cv{sim->d_cube_base, sim->d_cube_meta, sim->d_ckl, sim->has_c ? sim->d_cc : nullptr,
                                    sim->has_act ? sim->d_cact : nullptr};
-                if (sim->csr_kernel == 10) {
-                    titan::Cube2View c2{cv, sim->d_cext_slot, sim->d_cube_partner, sim->cube2_ext_cap};
-                    return titan::launch_step_cube2(in, out, sim->n_dev, c2, h, sim->kernel_config, sim->c, si, so,
-                                                    st, sim->l2_on ? &sim->l2win : nullptr);
-                }
                 return titan::launch_step_cube(in, out, sim->n_dev, cv, h, sim->c, si, so, st,
                                                sim->l2_on ? &sim->l2win : nullptr);
             }
             if (sim->csr_kernel == 7)
                 return titan::launch_step_box_tma(in, out, sim->n_dev, v, h, sim->halo_w_max, sim->c, si, so, st);
             return titan::launch_step_box(in, out, sim->n_dev, v, h, sim->c, si, so, st,
-                                          sim->l2_on ? &sim->l2win : nullptr);
+                                          sim->l2_on ? &sim->l2win : nullptr, sim->launch_overlap);
         }
         if (sim->csr_kernel == 4 || sim->csr_kernel == 5) {
             titan::HaloView h{sim->d_nslot, sim->d_own_slot, sim->d_ext_off, sim->d_ext_idx,
@@ -341,7 +341,7 @@ cudaError_t enqueue_step_io(titan_sim *sim, cudaStream_t st, const MassState *in
                 return titan::launch_step_halo_tma(in, out, sim->n_dev, v, h, sim->halo_w_max, sim->c, si,
                                                    so, st);
             return titan::launch_step_halo(in, out, sim->n_dev, v, h, sim->c, si, so, st,
-                                           sim->l2_on ? &sim->l2win : nullptr);
+                                           sim->l2_on ? &sim->l2win : nullptr, sim->launch_overlap);
         }
         v.variant = sim->csr_kernel == 3 ? 0 : sim->csr_kernel;   // launcher: 0 prefetch, 1 direct, 2 staged
         return titan::launch_step_sell(in, out, sim->n_dev, v, sim->c, si, so, st);
@@ -448,19 +448,42 @@ cudaError_t titan::enqueue_sim_step_io(titan_sim *sim, cudaStream_t st, const Ma
 
 namespace {
 
-cudaError_t ensure_graph(titan_sim *sim, int b) {
-    if (sim->graph[b]) return cudaSuccess;
+cudaError_t capture_graph(titan_sim *sim, int L, int b) {
     cudaError_t e = cudaStreamBeginCapture(sim->capture, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
     cudaError_t le = cudaSuccess;
-    for (int k = 0; k < sim->graph_chunk && le == cudaSuccess; ++k) le = enqueue_step(sim, sim->capture, b ^ (k & 1));
+    const int k_steps = graph_steps(sim, L);
+    for (int k = 0; k < k_steps && le == cudaSuccess; ++k) le = enqueue_step(sim, sim->capture, b ^ (k & 1));
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(sim->capture, &g);
     if (le != cudaSuccess) { if (g) cudaGraphDestroy(g); return le; }
     if (e != cudaSuccess) return e;
-    e = cudaGraphInstantiate(&sim->graph[b], g, 0);
+    e = cudaGraphInstantiate(&sim->graph[L][b], g, 0);
     cudaGraphDestroy(g);
     return e;
+}
+
+// Captures every level's graph for both starting buffers at once (so that no
+// later titan_step captures), on the first stepping call after a layout or
+// constants change.  If capturing the programmatic launches fails, the step
+// kernels fall back to plain stream order and the graphs are captured again.
+cudaError_t ensure_graphs(titan_sim *sim) {
+    if (sim->graphs_built || sim->graph_chunk <= 0) return cudaSuccess;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        cudaError_t e = cudaSuccess;
+        for (int L = 0; L < kGraphLevels && e == cudaSuccess; ++L)
+            for (int b = 0; b < 2 && e == cudaSuccess; ++b)
+                if (graph_steps(sim, L)) e = capture_graph(sim, L, b);
+        if (e == cudaSuccess) {
+            sim->graphs_built = true;
+            return cudaSuccess;
+        }
+        free_graphs(sim);
+        cudaGetLastError();
+        if (!sim->launch_overlap || attempt) return e;
+        sim->launch_overlap = false;
+    }
+    return cudaErrorUnknown;
 }
 
 }  // namespace
@@ -484,6 +507,7 @@ void titan_default_params(titan_params *p) {
     p->spin_limit = 0;
     p->graph_chunk = 0;
     p->l2_persist = 1;
+    p->launch_overlap = 1;
 }
 
 titan_status titan_create(const titan_masses *m, const titan_springs *sp, const titan_params *p,
@@ -512,7 +536,7 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
     sim->c.c_uniform = (float)p->damping;
     sim->c.act_omega = 0.0;
     sim->kernel_variant = p->kernel_variant;
-    sim->kernel_config = p->kernel_config;
+    sim->launch_overlap = p->launch_overlap != 0;
     sim->exec_req = p->exec;
     sim->spin_limit = p->spin_limit == 0 ? kDefaultSpinLimit
                                          : (uint32_t)(p->spin_limit > 0xffffffffull ? 0xffffffffull : p->spin_limit);
@@ -641,7 +665,7 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
             return bail(fail(sim, TITAN_E_UNSUPPORTED, "padded incidence exceeds 2^32 entries"));
         const int want = p->kernel_variant;
         sim->csr_kernel = want == 0 ? (sim->grid_order ? 6 : 4) : want;
-        if (sim->csr_kernel >= 6 && sim->csr_kernel <= 10 &&
+        if (sim->csr_kernel >= 6 && sim->csr_kernel <= 8 &&
             !(sim->grid_order && titan::build_box(nd, sim->sell, cells, sim->caller_of_dev, kHaloMaxSlots, sim->box))) {
             if (want >= 6)
                 return bail(fail(sim, TITAN_E_UNSUPPORTED, "the grid box kernel needs masses on a grid whose "
@@ -651,7 +675,7 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
         if (uses_cube(sim) &&
             !titan::build_cube(nd, s, sp->ends, sim->dev_of_caller, sim->sell, cells, sim->caller_of_dev, sim->box,
                                sim->cube)) {
-            if (want == 8 || want == 10)
+            if (want == 8)
                 return bail(fail(sim, TITAN_E_UNSUPPORTED, "the cube kernel needs 26-neighbour springs on a grid, "
                                                            "at most one per mass and offset"));
             sim->csr_kernel = 6;
@@ -687,7 +711,7 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
         CREATE_CK(dev_alloc(sim, &sim->d_kl, E));
         CREATE_CK(upload(sim->d_slice_off, sim->sell.slice_off, sim->stream));
         CREATE_CK(upload(sim->d_kl, kl, sim->stream));
-        if (sim->csr_kernel >= 6 && sim->csr_kernel <= 10) {
+        if (sim->csr_kernel >= 6 && sim->csr_kernel <= 8) {
             const titan::BoxHost &h = sim->box;
             CREATE_CK(dev_alloc(sim, &sim->d_col_off, h.col_off.size()));
             CREATE_CK(dev_alloc(sim, &sim->d_own_slot, nd));
@@ -721,16 +745,6 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
                 if (sim->has_c) {
                     CREATE_CK(dev_alloc(sim, &sim->d_cc, c2.size()));
                     CREATE_CK(upload(sim->d_cc, c2, sim->stream));
-                }
-                std::vector<uint32_t> xslot;
-                std::vector<uint8_t> ptab;
-                if (sim->csr_kernel == 10) {
-                    sim->cube2_ext_cap = titan::build_cube_ext_slots(sim->cube, sim->box, (uint32_t)titan::cube2_group(sim->kernel_config), xslot);
-                    titan::cube_partner_table(ptab);
-                    CREATE_CK(dev_alloc(sim, &sim->d_cext_slot, xslot.size()));
-                    CREATE_CK(dev_alloc(sim, &sim->d_cube_partner, ptab.size()));
-                    CREATE_CK(upload(sim->d_cext_slot, xslot, sim->stream));
-                    CREATE_CK(upload(sim->d_cube_partner, ptab, sim->stream));
                 }
                 CREATE_CK(cudaStreamSynchronize(sim->stream));     // the host vectors go out of scope
             }
@@ -810,18 +824,23 @@ titan_status titan_step(titan_sim *sim, uint64_t n_steps) {
         n_steps -= k;
         sim->steps += k;
     }
-    while (n_steps > 0) {
-        if (sim->graph_chunk > 0 && n_steps >= (uint64_t)sim->graph_chunk) {
-            TITAN_CK(sim, ensure_graph(sim, sim->cur));
-            TITAN_CK(sim, cudaGraphLaunch(sim->graph[sim->cur], sim->stream));
-            n_steps -= sim->graph_chunk;
-            sim->steps += sim->graph_chunk;      // even chunk: the parity is unchanged
-        } else {
-            TITAN_CK(sim, enqueue_step(sim, sim->stream, sim->cur));
-            sim->cur ^= 1;
-            --n_steps;
-            ++sim->steps;
+    // whole graphs, largest level first (each an even step count: the buffer
+    // parity is unchanged), then at most one single launch
+    if (n_steps >= 2 && sim->graph_chunk > 0) TITAN_CK(sim, ensure_graphs(sim));
+    for (int L = 0; L < kGraphLevels && n_steps >= 2; ++L) {
+        const uint64_t k = (uint64_t)graph_steps(sim, L);
+        if (!k) continue;
+        while (n_steps >= k) {
+            TITAN_CK(sim, cudaGraphLaunch(sim->graph[L][sim->cur], sim->stream));
+            n_steps -= k;
+            sim->steps += k;
         }
+    }
+    while (n_steps > 0) {
+        TITAN_CK(sim, enqueue_step(sim, sim->stream, sim->cur));
+        sim->cur ^= 1;
+        --n_steps;
+        ++sim->steps;
     }
     return TITAN_OK;
 }

@@ -13,6 +13,7 @@
 using titan::MassState;
 
 constexpr int kDefaultGraphChunk = 64;
+constexpr int kGraphLevels = 8;
 constexpr uint32_t kDefaultSpinLimit = 1u << 22;
 
 // Everything a simulation owns; titan_sim adds the per-handle lock and error
@@ -68,9 +69,6 @@ struct SimCore {
     uint4 *d_cube_meta = nullptr;         //              per (cube, pass, warp) masks, ext base, offset
     float2 *d_ckl = nullptr, *d_cact = nullptr;   //      cube stream {k, L0}, actuation
     float *d_cc = nullptr;                //              cube stream damping
-    uint32_t *d_cext_slot = nullptr;      // two-phase cube kernel: own | partner slot of each ext entry
-    uint8_t *d_cube_partner = nullptr;    //                        [13][256] in-cube partner lanes
-    uint32_t cube2_ext_cap = 0;           //                        largest ext count of a direction group
     float2 *d_kl = nullptr, *d_act = nullptr;
     float *d_c = nullptr;
 
@@ -81,10 +79,13 @@ struct SimCore {
 
     int graph_chunk = kDefaultGraphChunk;
     int kernel_variant = 0;
-    int kernel_config = 0;                // variant-specific configuration (titan_params.kernel_config)
+    bool launch_overlap = true;           // programmatic dependent launches of the step kernels
     uint32_t spin_limit = kDefaultSpinLimit;
     int *d_err = nullptr;                 // device error flag (bounded waits)
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    // captured step loops: level L runs graph_chunk >> L steps (levels while
+    // that count is even and >= 2), one graph per starting buffer
+    cudaGraphExec_t graph[kGraphLevels][2] = {};
+    bool graphs_built = false;
 
     // snapshots: slot = ticket & 1
     float *snap_dev[2] = {nullptr, nullptr};     // [2][n][3] pos then vel, caller order

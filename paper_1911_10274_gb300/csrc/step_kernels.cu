@@ -184,9 +184,7 @@ k_step_halo(const MassState *__restrict__ in, MassState *__restrict__ out, uint3
     const uint32_t i = b * kHaloThreads + tid;
     const uint32_t lane = tid & 31, sl = i >> 5, w = tid >> 5;
     const uint32_t n_slices = (n + 31) >> 5;
-    long long step = 0;
-    if (HAS_ACT) step = *step_in;
-    if (b == 0 && tid == 0) *step_out = *step_in + 1;
+    ptx::grid_dep_launch();         // the next step's CTAs may take SM slots this step's tail frees
     const bool valid = i < n;
 
     if (lane == 0) {
@@ -201,6 +199,13 @@ k_step_halo(const MassState *__restrict__ in, MassState *__restrict__ out, uint3
     if (valid) {
         e0 = __ldg(slice_off + sl);
         width = (__ldg(slice_off + sl + 1) - e0) >> 5;
+    }
+    // the state and the step counter are written by the previous step
+    ptx::grid_dep_wait();
+    long long step = 0;
+    if (HAS_ACT) step = *step_in;
+    if (b == 0 && tid == 0) *step_out = *step_in + 1;
+    if (valid) {
         load_state(in + i, p, v);
         const uint32_t s = own_slot[i];
         tA[s] = make_float4(p.x, p.y, p.z, v.x);
@@ -278,9 +283,7 @@ k_step_box(const MassState *__restrict__ in, MassState *__restrict__ out, uint32
     const uint32_t b = blockIdx.x, tid = threadIdx.x;
     const uint32_t i = b * kHaloThreads + tid;
     const uint32_t lane = tid & 31, sl = i >> 5;
-    long long step = 0;
-    if (HAS_ACT) step = *step_in;
-    if (b == 0 && tid == 0) *step_out = *step_in + 1;
+    ptx::grid_dep_launch();         // the next step's CTAs may take SM slots this step's tail frees
     // holes (empty cells of the block's cube) have no springs and never move:
     // their state is neither read nor written
     const uint32_t s_own = i < n ? own_slot[i] : kBoxHoleSlot;
@@ -307,11 +310,19 @@ k_step_box(const MassState *__restrict__ in, MassState *__restrict__ out, uint32
             if (HAS_C) { nc0 = __ldcs(cc + e); nc1 = __ldcs(cc + e + 32); }
             if (HAS_ACT) { ns0 = __ldcs(act + e); ns1 = __ldcs(act + e + 32); }
         }
+    }
+    const uint32_t h0 = __ldg(ext_off + b), h1 = __ldg(ext_off + b + 1);
+    // everything above reads layout data only; the state and the step counter
+    // are written by the previous step, which must have completed
+    ptx::grid_dep_wait();
+    long long step = 0;
+    if (HAS_ACT) step = *step_in;
+    if (b == 0 && tid == 0) *step_out = *step_in + 1;
+    if (valid) {
         load_state(in + i, p, v);
         tA[s_own] = make_float4(p.x, p.y, p.z, v.x);
         tB[s_own] = make_float2(v.y, v.z);
     }
-    const uint32_t h0 = __ldg(ext_off + b), h1 = __ldg(ext_off + b + 1);
     for (uint32_t h = h0 + tid; h < h1; h += kHaloThreads) {
         float4 q, ww;
         load_state(in + __ldg(ext_idx + h), q, ww);
@@ -1022,9 +1033,27 @@ static int carveout_for(size_t bytes, int resident) {
     return (int)std::min<size_t>(100, std::max<size_t>(50, (100 * need + (size_t)max_sm - 1) / (size_t)max_sm));
 }
 
+// The launch attributes of a step kernel: the L2 window (optional) and
+// programmatic stream serialization (overlap).
+static unsigned step_attrs(cudaLaunchAttribute *attr, const cudaAccessPolicyWindow *l2win, bool overlap) {
+    unsigned k = 0;
+    if (l2win) {
+        attr[k].id = cudaLaunchAttributeAccessPolicyWindow;
+        attr[k].val.accessPolicyWindow = *l2win;
+        ++k;
+    }
+    if (overlap) {
+        attr[k].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[k].val.programmaticStreamSerializationAllowed = 1;
+        ++k;
+    }
+    return k;
+}
+
 cudaError_t launch_step_halo(const MassState *in, MassState *out, uint32_t n, const SellView &v,
                              const HaloView &h, const StepConst &c, const long long *step_in,
-                             long long *step_out, cudaStream_t stream, const cudaAccessPolicyWindow *l2win) {
+                             long long *step_out, cudaStream_t stream, const cudaAccessPolicyWindow *l2win,
+                             bool overlap) {
     const bool hc = v.c != nullptr, ha = v.act != nullptr, gr = c.ground != 0;
     const unsigned g = n ? (n + kHaloThreads - 1) / kHaloThreads : 1;
     const size_t bytes = (size_t)h.table_slots * (sizeof(float4) + sizeof(float2));
@@ -1046,13 +1075,9 @@ cudaError_t launch_step_halo(const MassState *in, MassState *out, uint32_t n, co
         cfg.blockDim = dim3(kHaloThreads);                                                       \
         cfg.dynamicSmemBytes = bytes;                                                            \
         cfg.stream = stream;                                                                     \
-        cudaLaunchAttribute attr[1];                                                             \
-        if (l2win) {                                                                             \
-            attr[0].id = cudaLaunchAttributeAccessPolicyWindow;                                  \
-            attr[0].val.accessPolicyWindow = *l2win;                                             \
-            cfg.attrs = attr;                                                                    \
-            cfg.numAttrs = 1;                                                                    \
-        }                                                                                        \
+        cudaLaunchAttribute attr[2];                                                             \
+        cfg.attrs = attr;                                                                        \
+        cfg.numAttrs = step_attrs(attr, l2win, overlap);                                         \
         cudaError_t e = cudaLaunchKernelEx(&cfg, kern, in, out, n, v.slice_off, h.nslot, v.kl, v.c, v.act, \
                                            h.own_slot, h.ext_off, h.ext_idx, h.ext_slot, h.table_slots, \
                                            h.ahead, c, step_in, step_out);                       \
@@ -1071,7 +1096,7 @@ cudaError_t launch_step_halo(const MassState *in, MassState *out, uint32_t n, co
 
 cudaError_t launch_step_box(const MassState *in, MassState *out, uint32_t n, const SellView &v, const BoxView &h,
                             const StepConst &c, const long long *step_in, long long *step_out,
-                            cudaStream_t stream, const cudaAccessPolicyWindow *l2win) {
+                            cudaStream_t stream, const cudaAccessPolicyWindow *l2win, bool overlap) {
     const bool hc = v.c != nullptr, ha = v.act != nullptr, gr = c.ground != 0;
     const unsigned g = n ? (n + kHaloThreads - 1) / kHaloThreads : 1;
     const size_t bytes = (size_t)h.table_slots * (sizeof(float4) + sizeof(float2));
@@ -1094,13 +1119,9 @@ cudaError_t launch_step_box(const MassState *in, MassState *out, uint32_t n, con
         cfg.blockDim = dim3(kHaloThreads);                                                       \
         cfg.dynamicSmemBytes = bytes;                                                            \
         cfg.stream = stream;                                                                     \
-        cudaLaunchAttribute attr[1];                                                             \
-        if (l2win) {                                                                             \
-            attr[0].id = cudaLaunchAttributeAccessPolicyWindow;                                  \
-            attr[0].val.accessPolicyWindow = *l2win;                                             \
-            cfg.attrs = attr;                                                                    \
-            cfg.numAttrs = 1;                                                                    \
-        }                                                                                        \
+        cudaLaunchAttribute attr[2];                                                             \
+        cfg.attrs = attr;                                                                        \
+        cfg.numAttrs = step_attrs(attr, l2win, overlap);                                         \
         cudaError_t e = cudaLaunchKernelEx(&cfg, kern, in, out, n, v.slice_off,                  \
                                            reinterpret_cast<const uint32_t *>(h.col_off), v.kl, v.c, v.act, \
                                            h.own_slot, h.ext_off, h.ext_idx, h.ext_slot, h.table_slots, c, \

@@ -93,14 +93,6 @@ struct CubeView {
     const float2 *act;           // or nullptr (no actuation)
 };
 
-// The two-phase cube kernel's extra arrays (step_cube2.cu).
-struct Cube2View {
-    CubeView cube;
-    const uint32_t *ext_slot;    // per cube-stream entry: own slot | outside partner's slot << 16 (ext entries)
-    const uint8_t *partner;      // [13][256] in-cube partner lane of each cell, 0xFF outside
-    uint32_t ext_cap;            // largest ext entry count of one direction group of one cube
-};
-
 struct AtomicView {
     const uint4 *rec;            // [S] {i, j, bits(k), bits(L0)}
     const float *c;              // [S] or nullptr
@@ -119,13 +111,16 @@ cudaError_t launch_step_sell(const MassState *in, MassState *out, uint32_t n, co
 cudaError_t launch_step_halo(const MassState *in, MassState *out, uint32_t n, const SellView &v,
                              const HaloView &h, const StepConst &c, const long long *step_in,
                              long long *step_out, cudaStream_t stream,
-                             const cudaAccessPolicyWindow *l2win = nullptr);
+                             const cudaAccessPolicyWindow *l2win = nullptr, bool overlap = false);
 
 // Grid-box form of the halo kernel (see step_kernels.cu).  l2win (optional):
-// an L2 access-policy window attached to the launch.
+// an L2 access-policy window attached to the launch.  overlap: launched as a
+// programmatic dependent of the previous kernel in the stream (its CTAs start
+// early and wait for that kernel before reading the state).
 cudaError_t launch_step_box(const MassState *in, MassState *out, uint32_t n, const SellView &v, const BoxView &h,
                             const StepConst &c, const long long *step_in, long long *step_out,
-                            cudaStream_t stream, const cudaAccessPolicyWindow *l2win = nullptr);
+                            cudaStream_t stream, const cudaAccessPolicyWindow *l2win = nullptr,
+                            bool overlap = false);
 
 // Cube form (26-neighbourhood lattices): springs inside a block's cube read
 // and evaluated once (see step_kernels.cu).  n a multiple of 256.
@@ -139,25 +134,6 @@ cudaError_t launch_step_box_tma(const MassState *in, MassState *out, uint32_t n,
                                 const BoxView &h, uint32_t w_max, const StepConst &c, const long long *step_in,
                                 long long *step_out, cudaStream_t stream);
 size_t box_tma_smem_bytes(uint32_t table_slots, uint32_t w_max, bool has_c, bool has_act);
-
-// Grid-box form with the stream fed through a per-warp ring of bulk copies
-// (step_ring.cu).  config 0/1: 4 stages of 2 columns, 2: 6 x 2, 3: 3 x 4.
-// table_slots must be even.
-cudaError_t launch_step_box_ring(const MassState *in, MassState *out, uint32_t n, const SellView &v, const BoxView &h,
-                                 int config, const StepConst &c, const long long *step_in, long long *step_out,
-                                 cudaStream_t stream, const cudaAccessPolicyWindow *l2win = nullptr);
-size_t box_ring_smem_bytes(uint32_t table_slots, uint32_t ring_cols, bool has_c, bool has_act);
-int box_ring_stages(int config);
-int box_ring_cols(int config);
-
-// Two-phase cube form (step_cube2.cu): each spring in a cube evaluated once,
-// forces exchanged through shared memory in groups of cube2_group(config)
-// directions.  n a multiple of 256, table_slots even.
-cudaError_t launch_step_cube2(const MassState *in, MassState *out, uint32_t n, const Cube2View &v, const BoxView &h,
-                              int config, const StepConst &c, const long long *step_in, long long *step_out,
-                              cudaStream_t stream, const cudaAccessPolicyWindow *l2win = nullptr);
-size_t cube2_smem_bytes(uint32_t table_slots, int group, uint32_t ext_cap);
-int cube2_group(int config);
 
 // Halo form with the half-edge stream staged into shared memory by TMA bulk
 // copies; slices wider than w_max columns read from global memory.

@@ -48,7 +48,7 @@ class titan_params(C.Structure):
                 ("accumulate", C.c_int32), ("order", C.c_int32), ("exec", C.c_int32),
                 ("device", C.c_int32), ("stream", C.c_void_p), ("spin_limit", C.c_uint64),
                 ("graph_chunk", C.c_int32), ("kernel_variant", C.c_int32),
-                ("l2_persist", C.c_int32), ("kernel_config", C.c_int32), ("reserved", C.c_int32 * 4)]
+                ("l2_persist", C.c_int32), ("launch_overlap", C.c_int32), ("reserved", C.c_int32 * 4)]
 
 
 class titan_actuation(C.Structure):
@@ -468,7 +468,7 @@ class Sim:
 
     def __init__(self, system, accumulate: int = ACCUM_CSR, order: int = ORDER_MORTON,
                  exec_mode: int = EXEC_AUTO, graph_chunk: int = 0, stream: Optional[int] = None,
-                 device: int = 0, kernel_variant: int = 0, l2_persist: bool = True, kernel_config: int = 0):
+                 device: int = 0, kernel_variant: int = 0, l2_persist: bool = True, launch_overlap: bool = True):
         load()
         self.n = int(system.pos.shape[0])
         self.s = int(system.ends.shape[0])
@@ -496,7 +496,7 @@ class Sim:
         p.graph_chunk = graph_chunk
         p.kernel_variant = kernel_variant
         p.l2_persist = 1 if l2_persist else 0
-        p.kernel_config = kernel_config
+        p.launch_overlap = 1 if launch_overlap else 0
         p.stream = stream
         self.handle = titan_create(m, sp, p)
         self._keep = None

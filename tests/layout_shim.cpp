@@ -18,8 +18,6 @@ struct Built {
     titan::BoxHost box;
     titan::CubeHost cube;
     int cube_ok = 0;
-    std::vector<uint32_t> cube_ext_slot;
-    std::vector<uint8_t> cube_partner;
     titan::PersistPlan plan;
     std::vector<uint16_t> pslot;
     std::vector<uint32_t> phalo;
@@ -51,13 +49,6 @@ int shim_build(const double *pos, uint32_t n, const uint32_t *ends, uint32_t s, 
     g.cube_ok = g.box_ok && titan::build_cube(nd, s, ends, g.dev_of_caller, g.sell, g.cell, g.caller_of_dev, g.box,
                                               g.cube) ? 1 : 0;
     return 0;
-}
-
-// The two-phase cube kernel's arrays for the last built cube layout with
-// direction groups of `group`: returns the largest ext count of one group.
-uint32_t shim_cube2(uint32_t group) {
-    titan::cube_partner_table(g.cube_partner);
-    return titan::build_cube_ext_slots(g.cube, g.box, group, g.cube_ext_slot);
 }
 
 // Plans persistent execution of the last built layout within smem_limit
@@ -117,8 +108,6 @@ uint64_t shim_len(const char *name) {
     if (k == "cube_spring") return g.cube.spring.size();
     if (k == "cube_pos_of_end") return g.cube.pos_of_end.size();
     if (k == "box_dims") return g.box.dims.size();
-    if (k == "cube_ext_slot") return g.cube_ext_slot.size();
-    if (k == "cube_partner") return g.cube_partner.size();
     if (k == "pslot") return g.pslot.size();
     if (k == "phalo") return g.phalo.size();
     return 0;
@@ -142,8 +131,6 @@ void shim_get(const char *name, void *dst) {
     if (k == "cube_spring") copy_out(g.cube.spring, dst);
     if (k == "cube_pos_of_end") copy_out(g.cube.pos_of_end, dst);
     if (k == "box_dims") copy_out(g.box.dims, dst);
-    if (k == "cube_ext_slot") copy_out(g.cube_ext_slot, dst);
-    if (k == "cube_partner") copy_out(g.cube_partner, dst);
     if (k == "pslot") copy_out(g.pslot, dst);
     if (k == "phalo") copy_out(g.phalo, dst);
 }

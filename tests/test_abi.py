@@ -48,7 +48,7 @@ def test_default_params():
     p = T.titan_default_params()
     assert p.dt == 1e-4 and list(p.gravity) == [0.0, 0.0, -9.81]
     assert p.accumulate == T.ACCUM_CSR and p.order == T.ORDER_MORTON and p.exec == T.EXEC_AUTO
-    assert p.l2_persist == 1 and p.kernel_config == 0 and list(p.reserved) == [0] * 4
+    assert p.l2_persist == 1 and p.launch_overlap == 1 and list(p.reserved) == [0] * 4
 
 
 def test_binding_structs_match_the_header(tmp_path):

@@ -47,18 +47,11 @@ MODES = [dict(accumulate=T.ACCUM_CSR), dict(accumulate=T.ACCUM_ATOMIC),
          dict(accumulate=T.ACCUM_CSR, kernel_variant=6, **LAUNCH),
          dict(accumulate=T.ACCUM_CSR, kernel_variant=7, **LAUNCH),
          dict(accumulate=T.ACCUM_CSR, kernel_variant=8, **LAUNCH),
-         dict(accumulate=T.ACCUM_CSR, kernel_variant=9, **LAUNCH),
-         dict(accumulate=T.ACCUM_CSR, kernel_variant=9, kernel_config=2, **LAUNCH),
-         dict(accumulate=T.ACCUM_CSR, kernel_variant=9, kernel_config=3, **LAUNCH),
-         dict(accumulate=T.ACCUM_CSR, kernel_variant=10, **LAUNCH),
-         dict(accumulate=T.ACCUM_CSR, kernel_variant=10, kernel_config=2, **LAUNCH),
-         dict(accumulate=T.ACCUM_CSR, kernel_variant=10, kernel_config=3, **LAUNCH),
          dict(accumulate=T.ACCUM_CSR, exec_mode=T.EXEC_PERSISTENT),
          dict(accumulate=T.ACCUM_CSR, order=T.ORDER_INPUT),
          dict(accumulate=T.ACCUM_CSR, graph_chunk=-1, **LAUNCH)]
 MODE_IDS = ["csr", "atomic", "csr-direct-loads", "csr-tma-staged", "csr-bulk-prefetch", "csr-halo",
-            "csr-halo-tma", "csr-grid-box", "csr-grid-box-tma", "csr-cube", "csr-grid-box-ring", "csr-grid-box-ring6x2",
-            "csr-grid-box-ring3x4", "csr-cube2", "csr-cube2-g7", "csr-cube2-g13", "csr-persistent", "csr-input-order",
+            "csr-halo-tma", "csr-grid-box", "csr-grid-box-tma", "csr-cube", "csr-persistent", "csr-input-order",
             "csr-no-graph"]
 
 
@@ -138,9 +131,9 @@ def test_grid_lattice_with_zero_rest_length_springs(mode):
 def test_zero_rest_length_springs_bit_identical_across_csr_kernels():
     sys, _ = _zero_rest_grid()
     a = gpu_run(sys, 500, exec_mode=T.EXEC_PERSISTENT)
-    for var, ring in [(v, 0) for v in range(1, 11)] + [(9, 2), (9, 3), (10, 2), (10, 3)]:
-        b = gpu_run(sys, 500, kernel_variant=var, kernel_config=ring, **LAUNCH)
-        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]), (var, ring)
+    for var in range(1, 9):
+        b = gpu_run(sys, 500, kernel_variant=var, **LAUNCH)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]), var
 
 
 def _coincident_pair():
@@ -163,8 +156,8 @@ def _coincident_pair():
     return sys
 
 
-@pytest.mark.parametrize("mode", [m for m in MODES if m.get("kernel_variant") not in (6, 7, 8, 9, 10)],
-                         ids=[i for m, i in zip(MODES, MODE_IDS) if m.get("kernel_variant") not in (6, 7, 8, 9, 10)])
+@pytest.mark.parametrize("mode", [m for m in MODES if m.get("kernel_variant") not in (6, 7, 8)],
+                         ids=[i for m, i in zip(MODES, MODE_IDS) if m.get("kernel_variant") not in (6, 7, 8)])
 def test_coincident_masses_joined_with_null_rest_length(mode):
     """Coincident masses are off-grid (one mass per cell), so the grid
     kernels do not apply; every other kernel is compared with the oracle,
@@ -182,9 +175,8 @@ def test_coincident_masses_joined_with_null_rest_length(mode):
 
 def test_coincident_masses_are_refused_by_the_grid_kernels():
     sys = _coincident_pair()
-    for var in (6, 9):
-        with pytest.raises(T.TitanError, match="grid"):
-            T.Sim(sys, kernel_variant=var, **LAUNCH)
+    with pytest.raises(T.TitanError, match="grid"):
+        T.Sim(sys, kernel_variant=6, **LAUNCH)
 
 
 def test_per_spring_damping():
@@ -229,7 +221,7 @@ def test_lattice_with_holes_in_grid_tiles():
                         fixed=np.zeros(len(pos), np.uint8), ends=ends, k=np.full(len(ends), 1e4),
                         rest=d * rng.uniform(0.97, 1.03, len(d)), damping=np.full(len(ends), 1.0),
                         dt=1e-4, ground=True, spacing=0.1)
-    for var in (0, 10, 9, 8, 7, 6, 5, 4, 3):
+    for var in (0, 8, 7, 6, 5, 4, 3):
         check(sys, 1000, kernel_variant=var, **(LAUNCH if var else {}))
 
 
@@ -295,9 +287,29 @@ def test_csr_kernel_variants_agree_bit_exact():
     sys = inputs.cube_drop(drop_height=0.02)
     sys.vel[:, 0] = 0.3
     a = gpu_run(sys, 500, exec_mode=T.EXEC_PERSISTENT)
-    for var, ring in [(v, 0) for v in range(1, 11)] + [(9, 2), (9, 3), (10, 2), (10, 3)]:
-        b = gpu_run(sys, 500, kernel_variant=var, kernel_config=ring, **LAUNCH)
-        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]), (var, ring)
+    for var in range(1, 9):
+        b = gpu_run(sys, 500, kernel_variant=var, **LAUNCH)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]), var
+
+
+def test_graph_ladder_and_launch_overlap_change_no_bit():
+    """titan_step splits any step count into captured graphs of 64, 32, ...,
+    2 steps plus at most one direct launch; step kernels launched as
+    programmatic dependents (their CTAs start during the previous step's tail)
+    or in plain stream order: every combination gives the same bits."""
+    for sys in (inputs.large_lattice(n=20, seed=2), inputs.random_mesh(n_points=4000, seed=5, lift=0.0)):
+        counts = [1, 2, 3, 5, 20, 63, 64, 65, 130]
+        ref = None
+        for kw in (dict(graph_chunk=-1, launch_overlap=False), dict(graph_chunk=-1), dict(launch_overlap=False), {}):
+            with T.Sim(sys, **LAUNCH, **kw) as sim:
+                for k in counts:
+                    sim.step(k)
+                x, v, t = sim.snapshot()
+            assert t == pytest.approx(sum(counts) * sys.dt, rel=1e-12)
+            if ref is None:
+                ref = (x, v)
+            else:
+                assert np.array_equal(ref[0], x) and np.array_equal(ref[1], v), kw
 
 
 def test_graph_replay_matches_direct_launches_bit_exact():
@@ -401,10 +413,6 @@ def test_full_size_lattice_against_oracle_in_bench_configuration():
                  dict(accumulate=T.ACCUM_CSR, kernel_variant=6, **LAUNCH),
                  dict(accumulate=T.ACCUM_CSR, kernel_variant=7, **LAUNCH),
                  dict(accumulate=T.ACCUM_CSR, kernel_variant=8, **LAUNCH),
-                 dict(accumulate=T.ACCUM_CSR, kernel_variant=9, **LAUNCH),
-                 dict(accumulate=T.ACCUM_CSR, kernel_variant=10, **LAUNCH),
-                 dict(accumulate=T.ACCUM_CSR, kernel_variant=10, kernel_config=2, **LAUNCH),
-                 dict(accumulate=T.ACCUM_CSR, kernel_variant=10, kernel_config=3, **LAUNCH),
                  dict(accumulate=T.ACCUM_ATOMIC)):
         xg, vg, _ = gpu_run(sys, 64, **mode)
         err = np.abs(xg - xo).max()
@@ -426,9 +434,8 @@ def test_auto_kernel_choice():
     big = inputs.large_lattice(n=20, seed=0)
     with T.Sim(big) as sim:
         assert sim.csr_kernel == 6 and sim.exec_mode == T.EXEC_LAUNCH
-    for var in (8, 10):
-        with T.Sim(big, kernel_variant=var, exec_mode=T.EXEC_LAUNCH) as sim:
-            assert sim.csr_kernel == var
+    with T.Sim(big, kernel_variant=8, exec_mode=T.EXEC_LAUNCH) as sim:
+        assert sim.csr_kernel == 8
     with pytest.raises(T.TitanError, match="PERSISTENT"):
         T.Sim(big, exec_mode=T.EXEC_PERSISTENT)
     mesh = inputs.random_mesh(n_points=3000, seed=2, lift=0.0)
@@ -459,10 +466,9 @@ def test_grid_with_second_neighbour_springs_and_duplicates():
                         dt=1e-4, ground=True, spacing=0.1)
     with T.Sim(sys) as sim:
         assert sim.csr_kernel == 6                # second neighbours: no cube layout
-    for var in (8, 10):
-        with pytest.raises(T.TitanError, match="cube"):
-            T.Sim(sys, kernel_variant=var)
-    runs = [gpu_run(sys, 400, kernel_variant=v, **LAUNCH) for v in (6, 9, 7, 4, 3)]
+    with pytest.raises(T.TitanError, match="cube"):
+        T.Sim(sys, kernel_variant=8)
+    runs = [gpu_run(sys, 400, kernel_variant=v, **LAUNCH) for v in (6, 7, 4, 3)]
     runs.append(gpu_run(sys, 400, exec_mode=T.EXEC_PERSISTENT))
     for r in runs[1:]:
         assert np.array_equal(runs[0][0], r[0]) and np.array_equal(runs[0][1], r[1])

@@ -44,8 +44,6 @@ def shim(tmp_path_factory):
     lib.shim_plan.restype = C.c_int
     lib.shim_plan.argtypes = [C.c_uint64, C.c_int, C.c_int]
     lib.shim_plan_scalar.restype = C.c_uint64
-    lib.shim_cube2.restype = C.c_uint32
-    lib.shim_cube2.argtypes = [C.c_uint32]
     lib.shim_records.argtypes = [C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.shim_build_batch.restype = C.c_int
     lib.shim_build_batch.argtypes = [C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p]
@@ -317,72 +315,6 @@ def check_cube(L):
         for pos in (a, c):
             if pos != NONE:
                 assert L.cube_spring[pos] == q
-
-
-def check_cube2(L, group):
-    """The two-phase cube kernel's extra arrays: every ext entry carries the
-    box slots of its receiving mass and of the receiving mass's -p partner
-    (the spring's other end, outside the cube); the partner table names, for
-    every in-cube -p partner the meta marks, exactly that partner; the group
-    capacity bounds every group's ext entries."""
-    cap = int(L.lib.shim_cube2(group))
-    xs = np.empty(int(L.lib.shim_len(b"cube_ext_slot")), np.uint32)
-    L.lib.shim_get(b"cube_ext_slot", xs.ctypes.data)
-    pt = np.empty(int(L.lib.shim_len(b"cube_partner")), np.uint8)
-    L.lib.shim_get(b"cube_partner", pt.ctypes.data)
-    assert xs.size == L.cube_entries and pt.size == 13 * BLOCK
-    pt = pt.reshape(13, BLOCK)
-    P, W = 13, 8
-    meta = L.cube_meta.reshape(-1, P, W, 4)
-    cell = L.cell.reshape(-1, 3).astype(np.int64)
-    dev_of_cell = {tuple(c): d for d, c in enumerate(cell.tolist())}
-    n_cubes = L.n_dev // BLOCK
-    for b in range(n_cubes):
-        ext0 = int(L.cube_base[b]) + P * BLOCK
-        slot_of = {int(m): int(L.box_own_slot[m]) for m in range(b * BLOCK, (b + 1) * BLOCK)}
-        h0, h1 = int(L.box_ext_off[b]), int(L.box_ext_off[b + 1])
-        slot_of.update({int(m): int(sl) for m, sl in zip(L.box_ext_idx[h0:h1], L.box_ext_slot[h0:h1])})
-        starts = [int(meta[b, j, 0, 2]) for j in range(P)]
-        total = int(meta[b, P - 1, W - 1, 2]) + bin(int(meta[b, P - 1, W - 1, 1])).count("1")
-        for j0 in range(0, P, group):
-            hi = starts[j0 + group] if j0 + group < P else total
-            assert hi - starts[j0] <= cap
-        for j, (dx, dy, dz) in enumerate(CUBE_DIRS):
-            for t in range(BLOCK):
-                w, l = divmod(t, 32)
-                m = b * BLOCK + t
-                recv, ext, ebase = (int(meta[b, j, w, k]) for k in range(3))
-                partner_cell = (cell[m, 0] - dx, cell[m, 1] - dy, cell[m, 2] - dz)
-                if recv >> l & 1:
-                    assert pt[j, t] != 0xFF
-                    assert b * BLOCK + int(pt[j, t]) == dev_of_cell[partner_cell]
-                if ext >> l & 1:
-                    e = ext0 + ebase + bin(ext & ((1 << l) - 1)).count("1")
-                    own, part = int(xs[e]) & 0xFFFF, int(xs[e]) >> 16
-                    pm = dev_of_cell[partner_cell]
-                    assert not (b * BLOCK <= pm < (b + 1) * BLOCK)
-                    assert own == slot_of[m] and part == slot_of[pm]
-                    q = int(L.cube_spring[e])
-                    assert {int(L.dev_of[L.ends[q, 0]]), int(L.dev_of[L.ends[q, 1]])} == {m, pm}
-    # the partner table is pure geometry: inside the 8 x 8 x 4 cube or 0xFF
-    for j, (dx, dy, dz) in enumerate(CUBE_DIRS):
-        for t in range(BLOCK):
-            w, l = divmod(t, 32)
-            x, y, z = 4 * (w & 1) + (l & 3), 4 * ((w >> 1) & 1) + ((l >> 2) & 3), 2 * (w >> 2) + (l >> 4)
-            px, py, pz = x - dx, y - dy, z - dz
-            inside = 0 <= px < 8 and 0 <= py < 8 and 0 <= pz < 4
-            assert (pt[j, t] != 0xFF) == inside
-
-
-@pytest.mark.parametrize("group", [4, 7, 13])
-def test_two_phase_cube_arrays(shim, group):
-    pos, ends = lattice(16, 16, 8)
-    check_cube2(Layout(shim, pos, ends), group)
-
-
-def test_two_phase_cube_arrays_with_holes(shim):
-    pos, ends = lattice(10, 7, 5)
-    check_cube2(Layout(shim, pos, ends), 4)
 
 
 def test_cube_layout_replays_every_row_in_order(shim):
