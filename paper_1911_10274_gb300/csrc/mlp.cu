@@ -81,6 +81,7 @@ k_gemm_tn(const __grid_constant__ CUtensorMap tma_a, const __grid_constant__ CUt
     __shared__ uint64_t full[STAGES], empty[STAGES], accf;
     __shared__ uint32_t tmem_base;
     __shared__ int failed;
+    __shared__ int n_issued;                          // k blocks whose TMA loads were issued
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     // 1024-byte aligned tiles (the 128-byte swizzle pattern repeats every 1024 bytes)
     const uint32_t raw = titan::ptx::smem_u32(gsm_raw);
@@ -101,6 +102,7 @@ k_gemm_tn(const __grid_constant__ CUtensorMap tma_a, const __grid_constant__ CUt
         titan::ptx::mbar_init(&accf, 1);
         titan::ptx::fence_mbar_init();
         failed = 0;
+        n_issued = 0;
     }
     titan::ptx::tc_fence_before();
     __syncthreads();
@@ -118,6 +120,7 @@ k_gemm_tn(const __grid_constant__ CUtensorMap tma_a, const __grid_constant__ CUt
             titan::ptx::mbar_arrive_expect_tx(&full[s], kStageA + kStageB);
             titan::ptx::tma_load_2d(tileA(s), &tma_a, kb * BK, m0, &full[s]);
             titan::ptx::tma_load_2d(tileB(s), &tma_b, kb * BK, n0, &full[s]);
+            n_issued = kb + 1;
         }
     } else if (warp == 1 && lane == 0) {               // MMA issuer
         bool ok = true;
@@ -144,7 +147,20 @@ k_gemm_tn(const __grid_constant__ CUtensorMap tma_a, const __grid_constant__ CUt
     titan::ptx::tc_fence_after();
     __syncthreads();
     if (!acc_ok || failed) {
-        if (tid == 0) atomicExch(err, 1);
+        // a bounded wait expired: record it, then wait (bounded again) for
+        // this CTA's own copies and products still in flight - the last TMA
+        // load issued on each stage and every committed MMA - before the
+        // tensor memory is freed and the CTA exits
+        if (tid == 0) {
+            atomicExch(err, 1);
+            for (int st = 0; st < STAGES; ++st) {
+                int last = -1;
+                for (int kb = st; kb < n_issued; kb += STAGES) last = kb;
+                if (last >= 0) titan::ptx::mbar_wait_bounded(&full[st], (uint32_t)(last / STAGES) & 1u, spin_limit);
+            }
+            if (!acc_ok) titan::ptx::mbar_wait_bounded(&accf, 0, spin_limit);
+        }
+        __syncthreads();
     } else {
         const int row = m0 + warp * 32 + lane;
         for (int c0 = 0; c0 < BN_; c0 += 32) {
@@ -305,7 +321,7 @@ EncodeTiledFn encode_fn() {
     std::call_once(once, [] {
         void *p = nullptr;
         cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
             fn = reinterpret_cast<EncodeTiledFn>(p);
     });

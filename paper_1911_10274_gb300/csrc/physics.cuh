@@ -16,6 +16,18 @@ __device__ __forceinline__ void load_state(const MassState *m, float4 &p, float4
         : "l"(m));
 }
 
+// The same load through L2 only (.cg, never served from L1), ordered after
+// every earlier memory operation of the thread (volatile, with a memory
+// clobber): for a kernel whose CTAs start before the previous step has
+// finished writing the state (a programmatic dependent launch), issued only
+// after waiting for that step.
+__device__ __forceinline__ void load_state_after_wait(const MassState *m, float4 &p, float4 &v) {
+    asm volatile("ld.global.cg.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=f"(p.x), "=f"(p.y), "=f"(p.z), "=f"(p.w), "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(m)
+                 : "memory");
+}
+
 // Phase of the actuation clock at step `step`: 2 pi f t mod 2 pi with
 // t = step dt, formed in FP64 so that long runs keep full FP32 phase accuracy.
 __device__ __forceinline__ float clock_phase(const StepConst &c, long long step) {

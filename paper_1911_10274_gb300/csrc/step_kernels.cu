@@ -152,6 +152,17 @@ k_step_sell_pf(const MassState *__restrict__ in, MassState *__restrict__ out, ui
 // warp's own slice (ahead = 0, the default: prefetching further ahead was
 // measured to lose lines to L2 eviction), or `ahead` blocks in advance.
 constexpr int kHaloThreads = 256;
+
+// A neighbour or own state read by a step kernel.  Launched as a programmatic
+// dependent (OVERLAP), the kernel's CTAs may start while the previous step is
+// still writing the state: after waiting for it they read through L2 only,
+// since a line of that buffer left in L1 by an earlier step can be stale
+// (measured: with cached loads the trajectory drifted by centimetres).
+template <bool OVERLAP>
+__device__ __forceinline__ void read_state(const MassState *m, float4 &p, float4 &v) {
+    if (OVERLAP) load_state_after_wait(m, p, v);
+    else load_state(m, p, v);
+}
 constexpr uint32_t kBoxHoleSlot = 0xFFFF;   // own slot of a hole (layout.h: kBoxHole)
 constexpr int kHaloMinBlocks = 6;      // resident CTAs per SM of the coloured-table halo kernel
 constexpr int kBoxMinBlocks = 6;       // resident CTAs per SM the register budget is sized for
@@ -168,7 +179,7 @@ __device__ __forceinline__ void prefetch_slice(const uint32_t *slice_off, uint32
     if (HAS_ACT) ptx::bulk_prefetch_l2(act + e0, ne * 8);
 }
 
-template <bool HAS_C, bool HAS_ACT, bool GROUND>
+template <bool HAS_C, bool HAS_ACT, bool GROUND, bool OVERLAP>
 __global__ void __launch_bounds__(kHaloThreads, kHaloMinBlocks)
 k_step_halo(const MassState *__restrict__ in, MassState *__restrict__ out, uint32_t n,
             const uint32_t *__restrict__ slice_off, const uint16_t *__restrict__ nslot,
@@ -184,7 +195,7 @@ k_step_halo(const MassState *__restrict__ in, MassState *__restrict__ out, uint3
     const uint32_t i = b * kHaloThreads + tid;
     const uint32_t lane = tid & 31, sl = i >> 5, w = tid >> 5;
     const uint32_t n_slices = (n + 31) >> 5;
-    ptx::grid_dep_launch();         // the next step's CTAs may take SM slots this step's tail frees
+    if (OVERLAP) ptx::grid_dep_launch();    // the next step's CTAs may take SM slots this tail frees
     const bool valid = i < n;
 
     if (lane == 0) {
@@ -201,12 +212,12 @@ k_step_halo(const MassState *__restrict__ in, MassState *__restrict__ out, uint3
         width = (__ldg(slice_off + sl + 1) - e0) >> 5;
     }
     // the state and the step counter are written by the previous step
-    ptx::grid_dep_wait();
+    if (OVERLAP) ptx::grid_dep_wait();
     long long step = 0;
     if (HAS_ACT) step = *step_in;
     if (b == 0 && tid == 0) *step_out = *step_in + 1;
     if (valid) {
-        load_state(in + i, p, v);
+        read_state<OVERLAP>(in + i, p, v);
         const uint32_t s = own_slot[i];
         tA[s] = make_float4(p.x, p.y, p.z, v.x);
         tB[s] = make_float2(v.y, v.z);
@@ -214,7 +225,7 @@ k_step_halo(const MassState *__restrict__ in, MassState *__restrict__ out, uint3
     const uint32_t h0 = __ldg(ext_off + b), h1 = __ldg(ext_off + b + 1);
     for (uint32_t h = h0 + tid; h < h1; h += kHaloThreads) {
         float4 q, ww;
-        load_state(in + __ldg(ext_idx + h), q, ww);
+        read_state<OVERLAP>(in + __ldg(ext_idx + h), q, ww);
         const uint32_t s = __ldg(ext_slot + h);
         tA[s] = make_float4(q.x, q.y, q.z, ww.x);
         tB[s] = make_float2(ww.y, ww.z);
@@ -269,7 +280,7 @@ k_step_halo(const MassState *__restrict__ in, MassState *__restrict__ out, uint3
 // included, has L0 >= 0) may point at an empty cell of the box, whose table
 // slot holds whatever was there: they are skipped, never evaluated.  Holes -
 // device slots of empty cells, marked by own slot 0xFFFF - do nothing at all.
-template <bool HAS_C, bool HAS_ACT, bool GROUND>
+template <bool HAS_C, bool HAS_ACT, bool GROUND, bool OVERLAP>
 __global__ void __launch_bounds__(kHaloThreads, kBoxMinBlocks)
 k_step_box(const MassState *__restrict__ in, MassState *__restrict__ out, uint32_t n,
            const uint32_t *__restrict__ slice_off, const uint32_t *__restrict__ col_off2,
@@ -283,7 +294,7 @@ k_step_box(const MassState *__restrict__ in, MassState *__restrict__ out, uint32
     const uint32_t b = blockIdx.x, tid = threadIdx.x;
     const uint32_t i = b * kHaloThreads + tid;
     const uint32_t lane = tid & 31, sl = i >> 5;
-    ptx::grid_dep_launch();         // the next step's CTAs may take SM slots this step's tail frees
+    if (OVERLAP) ptx::grid_dep_launch();    // the next step's CTAs may take SM slots this tail frees
     // holes (empty cells of the block's cube) have no springs and never move:
     // their state is neither read nor written
     const uint32_t s_own = i < n ? own_slot[i] : kBoxHoleSlot;
@@ -314,18 +325,18 @@ k_step_box(const MassState *__restrict__ in, MassState *__restrict__ out, uint32
     const uint32_t h0 = __ldg(ext_off + b), h1 = __ldg(ext_off + b + 1);
     // everything above reads layout data only; the state and the step counter
     // are written by the previous step, which must have completed
-    ptx::grid_dep_wait();
+    if (OVERLAP) ptx::grid_dep_wait();
     long long step = 0;
     if (HAS_ACT) step = *step_in;
     if (b == 0 && tid == 0) *step_out = *step_in + 1;
     if (valid) {
-        load_state(in + i, p, v);
+        read_state<OVERLAP>(in + i, p, v);
         tA[s_own] = make_float4(p.x, p.y, p.z, v.x);
         tB[s_own] = make_float2(v.y, v.z);
     }
     for (uint32_t h = h0 + tid; h < h1; h += kHaloThreads) {
         float4 q, ww;
-        load_state(in + __ldg(ext_idx + h), q, ww);
+        read_state<OVERLAP>(in + __ldg(ext_idx + h), q, ww);
         const uint32_t s = __ldg(ext_slot + h);
         tA[s] = make_float4(q.x, q.y, q.z, ww.x);
         tB[s] = make_float2(ww.y, ww.z);
@@ -1060,7 +1071,7 @@ cudaError_t launch_step_halo(const MassState *in, MassState *out, uint32_t n, co
     const int carveout = carveout_for(bytes, kHaloMinBlocks);
 #define TITAN_HALO(HC, HA, GR)                                                                   \
     do {                                                                                         \
-        auto kern = k_step_halo<HC, HA, GR>;                                                     \
+        auto kern = overlap ? k_step_halo<HC, HA, GR, true> : k_step_halo<HC, HA, GR, false>;   \
         if (bytes > 48 * 1024) {                                                                 \
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes); \
             if (e != cudaSuccess) return e;                                                      \
@@ -1104,7 +1115,7 @@ cudaError_t launch_step_box(const MassState *in, MassState *out, uint32_t n, con
     const int carveout = carveout_for(bytes, kBoxMinBlocks);
 #define TITAN_BOX(HC, HA, GR)                                                                    \
     do {                                                                                         \
-        auto kern = k_step_box<HC, HA, GR>;                                                      \
+        auto kern = overlap ? k_step_box<HC, HA, GR, true> : k_step_box<HC, HA, GR, false>;     \
         if (bytes > 48 * 1024) {                                                                 \
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes); \
             if (e != cudaSuccess) return e;                                                      \
