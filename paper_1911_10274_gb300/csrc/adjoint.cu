@@ -262,7 +262,7 @@ extern "C" titan_status titan_adjoint(titan_sim *sim, uint64_t n_steps, uint32_t
         for (uint64_t g = 0; g < n_seg; ++g) {
             const uint64_t len = std::min<uint64_t>(every, n_steps - g * every);
             for (uint64_t k = 0; k < len; ++k) {
-                ADJ_CK(titan::enqueue_sim_step(sim, s, sim->cur));
+                ADJ_CK(titan::enqueue_sim_step(sim, s, sim->cur, k > 0));
                 sim->cur ^= 1;
                 ++sim->steps;
             }
@@ -285,7 +285,7 @@ extern "C" titan_status titan_adjoint(titan_sim *sim, uint64_t n_steps, uint32_t
             // the simulation's own step kernel (every CSR kernel gives bit-identical states)
             for (uint64_t k = 0; k < len; ++k)
                 ADJ_CK(titan::enqueue_sim_step_io(sim, s, seg + k * nd, seg + (k + 1) * nd, seg_steps + k,
-                                                  seg_steps + k + 1));
+                                                  seg_steps + k + 1, k > 0));
             for (uint64_t k = len; k-- > 0;) {
                 const MassState *X = seg + k * nd;
                 if (sim->c.ground)

@@ -315,8 +315,14 @@ cudaError_t upload_actuation(titan_sim *sim) {
     return upload(sim->d_ract, a, sim->stream);
 }
 
+// after_step: the operation just before this one on `st` is this
+// simulation's previous step kernel.  Only then may the step start early as a
+// programmatic dependent (it waits for that kernel before reading the state);
+// after a copy, a set_state or any other operation it is launched in plain
+// stream order.
 cudaError_t enqueue_step_io(titan_sim *sim, cudaStream_t st, const MassState *in, MassState *out,
-                            const long long *si, long long *so) {
+                            const long long *si, long long *so, bool after_step) {
+    const bool overlap = sim->launch_overlap && after_step;
     if (sim->accumulate == TITAN_ACCUM_CSR) {
         titan::SellView v{sim->d_slice_off, sim->d_nbr, sim->d_kl, sim->has_c ? sim->d_c : nullptr,
                           sim->has_act ? sim->d_act : nullptr, 0, sim->spin_limit, sim->d_err};
@@ -332,7 +338,7 @@ cudaError_t enqueue_step_io(titan_sim *sim, cudaStream_t st, const MassState *in
             if (sim->csr_kernel == 7)
                 return titan::launch_step_box_tma(in, out, sim->n_dev, v, h, sim->halo_w_max, sim->c, si, so, st);
             return titan::launch_step_box(in, out, sim->n_dev, v, h, sim->c, si, so, st,
-                                          sim->l2_on ? &sim->l2win : nullptr, sim->launch_overlap);
+                                          sim->l2_on ? &sim->l2win : nullptr, overlap);
         }
         if (sim->csr_kernel == 4 || sim->csr_kernel == 5) {
             titan::HaloView h{sim->d_nslot, sim->d_own_slot, sim->d_ext_off, sim->d_ext_idx,
@@ -341,7 +347,7 @@ cudaError_t enqueue_step_io(titan_sim *sim, cudaStream_t st, const MassState *in
                 return titan::launch_step_halo_tma(in, out, sim->n_dev, v, h, sim->halo_w_max, sim->c, si,
                                                    so, st);
             return titan::launch_step_halo(in, out, sim->n_dev, v, h, sim->c, si, so, st,
-                                           sim->l2_on ? &sim->l2win : nullptr, sim->launch_overlap);
+                                           sim->l2_on ? &sim->l2win : nullptr, overlap);
         }
         v.variant = sim->csr_kernel == 3 ? 0 : sim->csr_kernel;   // launcher: 0 prefetch, 1 direct, 2 staged
         return titan::launch_step_sell(in, out, sim->n_dev, v, sim->c, si, so, st);
@@ -351,8 +357,9 @@ cudaError_t enqueue_step_io(titan_sim *sim, cudaStream_t st, const MassState *in
     return titan::launch_step_atomic(in, out, sim->n_dev, v, sim->c, si, so, st);
 }
 
-cudaError_t enqueue_step(titan_sim *sim, cudaStream_t st, int b) {
-    return enqueue_step_io(sim, st, sim->state[b], sim->state[1 - b], sim->steps_dev + b, sim->steps_dev + (1 - b));
+cudaError_t enqueue_step(titan_sim *sim, cudaStream_t st, int b, bool after_step) {
+    return enqueue_step_io(sim, st, sim->state[b], sim->state[1 - b], sim->steps_dev + b, sim->steps_dev + (1 - b),
+                           after_step);
 }
 
 // Staged columns per slice for the halo+TMA kernel: every slice if two CTAs
@@ -439,11 +446,13 @@ titan_status check_device_error(titan_sim *sim) {
 
 }  // namespace
 
-cudaError_t titan::enqueue_sim_step(titan_sim *sim, cudaStream_t st, int b) { return enqueue_step(sim, st, b); }
+cudaError_t titan::enqueue_sim_step(titan_sim *sim, cudaStream_t st, int b, bool after_step) {
+    return enqueue_step(sim, st, b, after_step);
+}
 
 cudaError_t titan::enqueue_sim_step_io(titan_sim *sim, cudaStream_t st, const MassState *in, MassState *out,
-                                       const long long *step_in, long long *step_out) {
-    return enqueue_step_io(sim, st, in, out, step_in, step_out);
+                                       const long long *step_in, long long *step_out, bool after_step) {
+    return enqueue_step_io(sim, st, in, out, step_in, step_out, after_step);
 }
 
 namespace {
@@ -453,7 +462,8 @@ cudaError_t capture_graph(titan_sim *sim, int L, int b) {
     if (e != cudaSuccess) return e;
     cudaError_t le = cudaSuccess;
     const int k_steps = graph_steps(sim, L);
-    for (int k = 0; k < k_steps && le == cudaSuccess; ++k) le = enqueue_step(sim, sim->capture, b ^ (k & 1));
+    // the graph's first step follows whatever precedes the graph launch: plain order
+    for (int k = 0; k < k_steps && le == cudaSuccess; ++k) le = enqueue_step(sim, sim->capture, b ^ (k & 1), k > 0);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(sim->capture, &g);
     if (le != cudaSuccess) { if (g) cudaGraphDestroy(g); return le; }
@@ -836,8 +846,8 @@ titan_status titan_step(titan_sim *sim, uint64_t n_steps) {
             sim->steps += k;
         }
     }
-    while (n_steps > 0) {
-        TITAN_CK(sim, enqueue_step(sim, sim->stream, sim->cur));
+    for (bool first = true; n_steps > 0; first = false) {
+        TITAN_CK(sim, enqueue_step(sim, sim->stream, sim->cur, !first));
         sim->cur ^= 1;
         --n_steps;
         ++sim->steps;

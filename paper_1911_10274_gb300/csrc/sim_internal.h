@@ -121,10 +121,12 @@ struct titan_sim : SimCore {
 
 namespace titan {
 // Enqueues one fused step reading state buffer b of the simulation (runtime.cu).
-cudaError_t enqueue_sim_step(titan_sim *sim, cudaStream_t st, int b);
+// after_step: the operation just before it on st is this simulation's previous
+// step kernel (only then may it start early, as a programmatic dependent).
+cudaError_t enqueue_sim_step(titan_sim *sim, cudaStream_t st, int b, bool after_step);
 // The same step kernel between caller-chosen buffers (adjoint recomputation).
 cudaError_t enqueue_sim_step_io(titan_sim *sim, cudaStream_t st, const MassState *in, MassState *out,
-                                const long long *step_in, long long *step_out);
+                                const long long *step_in, long long *step_out, bool after_step);
 void set_thread_error(const std::string &msg);
 // Rebuilds the device layout if masses or springs were added (runtime.cu).
 titan_status ensure_layout(titan_sim *sim);

@@ -163,6 +163,14 @@ __device__ __forceinline__ void read_state(const MassState *m, float4 &p, float4
     if (OVERLAP) load_state_after_wait(m, p, v);
     else load_state(m, p, v);
 }
+
+// The step counter the previous step wrote, read the same way (through L2
+// only after the wait: neighbouring counters share a cache line, so an L1 copy
+// of it can be a step or more out of date).
+template <bool OVERLAP>
+__device__ __forceinline__ long long read_step(const long long *p) {
+    return OVERLAP ? __ldcg(p) : *p;
+}
 constexpr uint32_t kBoxHoleSlot = 0xFFFF;   // own slot of a hole (layout.h: kBoxHole)
 constexpr int kHaloMinBlocks = 6;      // resident CTAs per SM of the coloured-table halo kernel
 constexpr int kBoxMinBlocks = 6;       // resident CTAs per SM the register budget is sized for
@@ -214,8 +222,8 @@ k_step_halo(const MassState *__restrict__ in, MassState *__restrict__ out, uint3
     // the state and the step counter are written by the previous step
     if (OVERLAP) ptx::grid_dep_wait();
     long long step = 0;
-    if (HAS_ACT) step = *step_in;
-    if (b == 0 && tid == 0) *step_out = *step_in + 1;
+    if (HAS_ACT || (b == 0 && tid == 0)) step = read_step<OVERLAP>(step_in);
+    if (b == 0 && tid == 0) *step_out = step + 1;
     if (valid) {
         read_state<OVERLAP>(in + i, p, v);
         const uint32_t s = own_slot[i];
@@ -327,8 +335,8 @@ k_step_box(const MassState *__restrict__ in, MassState *__restrict__ out, uint32
     // are written by the previous step, which must have completed
     if (OVERLAP) ptx::grid_dep_wait();
     long long step = 0;
-    if (HAS_ACT) step = *step_in;
-    if (b == 0 && tid == 0) *step_out = *step_in + 1;
+    if (HAS_ACT || (b == 0 && tid == 0)) step = read_step<OVERLAP>(step_in);
+    if (b == 0 && tid == 0) *step_out = step + 1;
     if (valid) {
         read_state<OVERLAP>(in + i, p, v);
         tA[s_own] = make_float4(p.x, p.y, p.z, v.x);

@@ -297,7 +297,8 @@ def test_graph_ladder_and_launch_overlap_change_no_bit():
     2 steps plus at most one direct launch; step kernels launched as
     programmatic dependents (their CTAs start during the previous step's tail)
     or in plain stream order: every combination gives the same bits."""
-    for sys in (inputs.large_lattice(n=20, seed=2), inputs.random_mesh(n_points=4000, seed=5, lift=0.0)):
+    robot = inputs.actuated_box(9, 7, 5, np.random.default_rng(17))        # actuated: the step counter matters
+    for sys in (inputs.large_lattice(n=20, seed=2), inputs.random_mesh(n_points=4000, seed=5, lift=0.0), robot):
         counts = [1, 2, 3, 5, 20, 63, 64, 65, 130]
         ref = None
         for kw in (dict(graph_chunk=-1, launch_overlap=False), dict(graph_chunk=-1), dict(launch_overlap=False), {}):
@@ -308,6 +309,9 @@ def test_graph_ladder_and_launch_overlap_change_no_bit():
             assert t == pytest.approx(sum(counts) * sys.dt, rel=1e-12)
             if ref is None:
                 ref = (x, v)
+                if sys is robot:
+                    xo, _ = oracle.run(robot, sum(counts))
+                    assert np.abs(x - xo).max() <= POS_TOL_FRAC * robot.spacing
             else:
                 assert np.array_equal(ref[0], x) and np.array_equal(ref[1], v), kw
 
