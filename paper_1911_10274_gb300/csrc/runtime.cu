@@ -288,8 +288,9 @@ bool uses_cube(const titan_sim *sim) { return sim->csr_kernel == 8; }
 cudaError_t upload_actuation(titan_sim *sim) {
     cudaError_t e;
     if (sim->accumulate == TITAN_ACCUM_CSR) {
-        if (!sim->d_act && (e = dev_alloc(sim, &sim->d_act, sim->sell.entries)) != cudaSuccess) return e;
-        std::vector<float2> a(sim->sell.entries, make_float2(0.f, 0.f));
+        if (!sim->d_act && (e = dev_alloc(sim, &sim->d_act, sim->sell.entries + titan::kStreamTail)) != cudaSuccess)
+            return e;
+        std::vector<float2> a(sim->sell.entries + titan::kStreamTail, make_float2(0.f, 0.f));
         for (uint32_t e2 = 0; e2 < sim->sell.entries; ++e2) {
             const uint32_t q = sim->sell.spring[e2];
             if (q != UINT32_MAX) a[e2] = make_float2(sim->act_amp[q], sim->act_phase[q]);
@@ -708,9 +709,9 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
             sim->csr_kernel = 4;
         }
         const uint32_t E = sim->sell.entries;
-        std::vector<float2> kl(E, make_float2(0.f, titan::kPadRest));
+        std::vector<float2> kl(E + titan::kStreamTail, make_float2(0.f, titan::kPadRest));
         std::vector<float> cc;
-        if (sim->has_c) cc.assign(E, 0.f);
+        if (sim->has_c) cc.assign(E + titan::kStreamTail, 0.f);
         for (uint32_t e = 0; e < E; ++e) {
             const uint32_t q = sim->sell.spring[e];
             if (q == UINT32_MAX) continue;
@@ -718,12 +719,13 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
             if (sim->has_c) cc[e] = sim->damp[q];
         }
         CREATE_CK(dev_alloc(sim, &sim->d_slice_off, sim->sell.slice_off.size()));
-        CREATE_CK(dev_alloc(sim, &sim->d_kl, E));
+        CREATE_CK(dev_alloc(sim, &sim->d_kl, E + titan::kStreamTail));
         CREATE_CK(upload(sim->d_slice_off, sim->sell.slice_off, sim->stream));
         CREATE_CK(upload(sim->d_kl, kl, sim->stream));
         if (sim->csr_kernel >= 6 && sim->csr_kernel <= 8) {
             const titan::BoxHost &h = sim->box;
-            CREATE_CK(dev_alloc(sim, &sim->d_col_off, h.col_off.size()));
+            CREATE_CK(dev_alloc(sim, &sim->d_col_off, h.col_off.size() + 2));      // + one word read ahead
+            CREATE_CK(cudaMemsetAsync(sim->d_col_off, 0, (h.col_off.size() + 2) * sizeof(int16_t), sim->stream));
             CREATE_CK(dev_alloc(sim, &sim->d_own_slot, nd));
             CREATE_CK(dev_alloc(sim, &sim->d_ext_off, h.ext_off.size()));
             CREATE_CK(dev_alloc(sim, &sim->d_ext_idx, h.ext_idx.size()));
@@ -776,7 +778,7 @@ titan_status titan_create(const titan_masses *m, const titan_springs *sp, const 
             CREATE_CK(upload(sim->d_nbr, sim->sell.nbr, sim->stream));
         }
         if (sim->has_c) {
-            CREATE_CK(dev_alloc(sim, &sim->d_c, E));
+            CREATE_CK(dev_alloc(sim, &sim->d_c, E + titan::kStreamTail));
             CREATE_CK(upload(sim->d_c, cc, sim->stream));
         }
     } else {
@@ -1083,10 +1085,11 @@ cudaError_t enable_per_spring_damping(titan_sim *sim) {
     if (sim->has_c) return cudaSuccess;
     cudaError_t e;
     if (sim->accumulate == TITAN_ACCUM_CSR) {
-        std::vector<float> cc(sim->sell.entries, 0.f);
+        std::vector<float> cc(sim->sell.entries + titan::kStreamTail, 0.f);
         for (uint32_t e2 = 0; e2 < sim->sell.entries; ++e2)
             if (sim->sell.spring[e2] != UINT32_MAX) cc[e2] = sim->damp[sim->sell.spring[e2]];
-        if (!sim->d_c && (e = dev_alloc(sim, &sim->d_c, sim->sell.entries)) != cudaSuccess) return e;
+        if (!sim->d_c && (e = dev_alloc(sim, &sim->d_c, sim->sell.entries + titan::kStreamTail)) != cudaSuccess)
+            return e;
         if ((e = upload(sim->d_c, cc, sim->stream)) != cudaSuccess) return e;
         if (uses_cube(sim)) {
             std::vector<float> c2(sim->cube.entries, 0.f);

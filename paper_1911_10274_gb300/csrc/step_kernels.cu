@@ -360,13 +360,14 @@ k_step_box(const MassState *__restrict__ in, MassState *__restrict__ out, uint32
             const float2 a0 = na0, a1 = na1;
             const float c0 = nc0, c1 = nc1;
             const float2 s0 = ns0, s1 = ns1;
-            if (t + 2 < width) {
-                e += 64;
-                no = __ldg(co + (t >> 1) + 1);
-                na0 = __ldcs(kl + e); na1 = __ldcs(kl + e + 32);
-                if (HAS_C) { nc0 = __ldcs(cc + e); nc1 = __ldcs(cc + e + 32); }
-                if (HAS_ACT) { ns0 = __ldcs(act + e); ns1 = __ldcs(act + e + 32); }
-            }
+            // the next pair, unconditionally: past the slice's last pair this
+            // reads the next slice's entries or the arrays' tail (kStreamTail),
+            // values never used
+            e += 64;
+            no = __ldg(co + (t >> 1) + 1);
+            na0 = __ldcs(kl + e); na1 = __ldcs(kl + e + 32);
+            if (HAS_C) { nc0 = __ldcs(cc + e); nc1 = __ldcs(cc + e + 32); }
+            if (HAS_ACT) { ns0 = __ldcs(act + e); ns1 = __ldcs(act + e + 32); }
             const uint32_t j0 = s_own + (uint32_t)(int32_t)(int16_t)(o & 0xffffu);
             const uint32_t j1 = s_own + (uint32_t)(int32_t)(int16_t)(o >> 16);
             float L0 = a0.y, L1 = a1.y;

@@ -34,6 +34,12 @@ namespace titan {
 // negative value marks padding unambiguously.
 constexpr float kPadRest = -1.0f;
 
+// Entries past the end of the SELL stream arrays ({k, L0}, c, actuation):
+// padding a kernel may read ahead into, so that its loop needs no bounds test
+// for the next column pair of the last slice.  The column-offset array of the
+// grid-box kernels likewise carries one word past its end.
+constexpr uint32_t kStreamTail = 64;
+
 struct __align__(16) MassState {
     float4 p;   // x, y, z, 1/m (0: fixed)
     float4 v;   // vx, vy, vz, unused (0)
