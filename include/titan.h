@@ -187,6 +187,21 @@ titan_status titan_snapshot_wait(titan_sim *sim, uint64_t ticket, const float **
 titan_status titan_set_actuation(titan_sim *sim, uint32_t n, const uint32_t *spring_ids,
                                  const float *amp, const float *phase, float freq_hz);
 
+/* titan_set_actuation for every spring at once from DEVICE arrays (the
+ * simulation's device): amp_dev[s] and phase_dev[s] for spring s in caller
+ * order, n floats each; n must equal the simulation's spring count (n_springs
+ * at creation plus springs added since).  The call checks every value on
+ * the device, then copies the arrays into the library (it waits for both on
+ * the simulation's stream, so the caller may reuse or free the arrays once
+ * it returns; work the caller enqueued on other streams that writes them
+ * must be complete).  Nothing changes on error.  Takes effect from the next
+ * enqueued step.  The paper has no counterpart:
+ * it keeps an optimisation loop's actuation on the GPU between rollouts.
+ * Errors: TITAN_E_INVALID (n not the spring count, null array with n > 0,
+ * non-finite value or freq_hz), TITAN_E_CUDA. */
+titan_status titan_set_actuation_dev(titan_sim *sim, uint32_t n, const float *amp_dev, const float *phase_dev,
+                                     float freq_hz);
+
 /* Worm actuation (Sec. V-B, Eqs. 3-5): rest(t) = L0 (1 + c[s] sin(omega tau)),
  * tau = (t - t_offset[s]) mod period (floor modulo, in [0, period)).  c == 0
  * turns a spring off.  Replaces any sinusoidal actuation.  Takes effect from
@@ -252,8 +267,9 @@ titan_status titan_set_step(titan_sim *sim, uint64_t step);
  * state after the rollout).  All arrays are DEVICE float arrays in caller
  * order: seed_pos_dev and seed_vel_dev [n][3] (seed_vel_dev may be NULL),
  * gradients [n_springs] (overwritten).  Requires CSR accumulation and
- * actuation set with titan_set_actuation.  At the kinks of contact and
- * friction the derivative of the branch the forward step took is used.
+ * actuation set with titan_set_actuation or titan_set_actuation_dev.  At the
+ * kinks of contact and friction the derivative of the branch the forward step
+ * took is used.
  * Enqueued on the simulation stream.  Errors: TITAN_E_INVALID,
  * TITAN_E_UNSUPPORTED (atomic accumulation), TITAN_E_OOM, TITAN_E_CUDA. */
 titan_status titan_adjoint(titan_sim *sim, uint64_t n_steps, uint32_t every, const float *seed_pos_dev,
@@ -368,14 +384,16 @@ titan_status titan_batch_create(uint32_t n_systems, const titan_masses *masses,
  * without waiting.  The actuation clock continues across rollouts. */
 titan_status titan_batch_rollout(titan_batch *b, uint64_t n_steps);
 
-/* The autotuner: times each launch group with 128, 256 and 512 threads per
- * CTA and 1, 2 or 4 threads per mass (a mass's springs split over that many
- * threads) over a probe_steps rollout (0: 50) and keeps the fastest pair.
- * The state is unchanged. */
+/* The autotuner: times each launch group with 128, 256, 512 and 1024 threads
+ * per CTA and at most 1, 2, 4 or 8 threads per mass over a probe_steps
+ * rollout (0: 50) and keeps the fastest pair.  The state is unchanged. */
 titan_status titan_batch_autotune(titan_batch *b, uint32_t probe_steps);
 
 /* Sets a launch group's shape by hand: threads per CTA (a multiple of 32,
- * up to 512) and threads per mass (1, 2 or 4).  Errors: TITAN_E_INVALID. */
+ * up to 1024) and the most threads per mass (1, 2, 4 or 8): a mass's springs
+ * are split over that many threads, and each CTA takes the largest power of
+ * two up to it that still gives every mass of the CTA its own threads in one
+ * pass (at least 1).  Errors: TITAN_E_INVALID. */
 titan_status titan_batch_configure(titan_batch *b, uint32_t group, uint32_t threads,
                                    uint32_t threads_per_mass);
 
@@ -394,7 +412,8 @@ titan_status titan_batch_read(titan_batch *b, uint32_t system, float *pos, float
 titan_status titan_batch_centroids(titan_batch *b, float *out);
 
 /* Number of launch groups (one per cluster size) and, per group, its cluster
- * size, threads per CTA, threads per mass and CTA count (outputs may be NULL). */
+ * size, threads per CTA, most threads per mass and CTA count (outputs may be
+ * NULL). */
 uint32_t titan_batch_groups(const titan_batch *b);
 titan_status titan_batch_info(const titan_batch *b, uint32_t group, uint32_t *cluster,
                               uint32_t *threads, uint32_t *threads_per_mass, uint32_t *ctas);
@@ -423,11 +442,19 @@ typedef struct titan_mlp titan_mlp;
 
 /* C[M][N] = A[M][K] B[N][K]^T on the tensor cores: A and B row-major BF16
  * (uint16 bit patterns, 16-byte aligned), C row-major FP32, all on the
- * current device.  M and N multiples of 128, K of 64.  Runs on `stream` and
- * waits for completion.  Errors: TITAN_E_INVALID, TITAN_E_CUDA,
- * TITAN_E_TIMEOUT (a bounded wait in the kernel expired). */
+ * current device.  M and N multiples of 128, K of 64.  Enqueued on `stream`
+ * (NULL: the legacy default stream); returns without waiting.  A kernel
+ * whose bounded wait expires sets a per-device flag in pinned host memory;
+ * the next titan_gemm_bf16_tn or titan_gemm_check on that device reads it
+ * without waiting, clears it and returns TITAN_E_TIMEOUT (that call enqueues
+ * nothing).  Errors: TITAN_E_INVALID, TITAN_E_CUDA, TITAN_E_TIMEOUT. */
 titan_status titan_gemm_bf16_tn(uint32_t M, uint32_t N, uint32_t K, const uint16_t *A_dev,
                                 const uint16_t *B_dev, float *C_dev, void *stream);
+
+/* Reads (and clears) the current device's GEMM flag: TITAN_E_TIMEOUT if a
+ * titan_gemm_bf16_tn kernel gave up on a bounded wait.  Call it after
+ * synchronising the streams the GEMMs ran on to see every such failure. */
+titan_status titan_gemm_check(void);
 
 titan_status titan_mlp_create(uint32_t in, uint32_t hidden, uint64_t seed, int32_t device, void *stream,
                               titan_mlp **out);

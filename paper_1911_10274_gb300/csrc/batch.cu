@@ -46,13 +46,13 @@ using titan::BatchCta;
 using titan::BatchSmem;
 using titan::batch_smem_layout;
 
-template <bool ACT, bool GROUND, int TPM>
-__global__ void __launch_bounds__(512)
+template <bool ACT, bool GROUND>
+__global__ void __launch_bounds__(1024)
 k_batch_rollout(const BatchCta *__restrict__ ctas, const MassState *__restrict__ state_in,
                 MassState *__restrict__ state_out, const uint32_t *__restrict__ slice_rel,
                 const float2 *__restrict__ kl, const float2 *__restrict__ act,
                 const uint16_t *__restrict__ nbr, const uint32_t *__restrict__ halo, titan::StepConst c,
-                long long step0, uint32_t n_steps, uint32_t cluster_size, uint32_t spin_limit,
+                long long step0, uint32_t n_steps, uint32_t cluster_size, uint32_t tpm_max, uint32_t spin_limit,
                 int *__restrict__ err) {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ uint64_t bar;
@@ -101,8 +101,13 @@ k_batch_rollout(const BatchCta *__restrict__ ctas, const MassState *__restrict__
     cg::cluster_group cluster = cg::this_cluster();
     if (cluster_size > 1) cluster.sync();       // all CTAs' shared memory is loaded and alive
 
-    const uint32_t sub = tid % TPM;
-    const uint32_t per_pass = blockDim.x / TPM;
+    // threads per mass: the most (a power of two up to tpm_max) that still
+    // give every mass of this CTA its own thread group in one pass
+    uint32_t tpm = 1;
+    while (tpm < tpm_max && 2 * tpm * d.slot_count <= blockDim.x) tpm *= 2;
+    const uint32_t tpm_log = (uint32_t)__ffs((int)tpm) - 1;
+    const uint32_t sub = tid & (tpm - 1);
+    const uint32_t per_pass = blockDim.x >> tpm_log;
     const uint32_t passes = (d.slot_count + per_pass - 1) / per_pass;   // CTA-uniform
     int cur = 0;
     for (uint32_t k = 0; k < n_steps; ++k) {
@@ -123,7 +128,7 @@ k_batch_rollout(const BatchCta *__restrict__ ctas, const MassState *__restrict__
             __syncthreads();
         }
         for (uint32_t pass = 0; ok && pass < passes; ++pass) {
-            const uint32_t m = pass * per_pass + tid / TPM;
+            const uint32_t m = pass * per_pass + (tid >> tpm_log);
             const bool live = m < d.slot_count;
             float fx = 0.f, fy = 0.f, fz = 0.f;
             float4 p = make_float4(0.f, 0.f, 0.f, 0.f), v = p;
@@ -133,26 +138,50 @@ k_batch_rollout(const BatchCta *__restrict__ ctas, const MassState *__restrict__
                 const float2 b0 = srcB[m];
                 p = make_float4(a0.x, a0.y, a0.z, s_inv[m]);
                 v = make_float4(a0.w, b0.x, b0.y, 0.f);
-                const uint32_t e0 = s_slice[slice];
-                const uint32_t width = (s_slice[slice + 1] - e0) >> 5;
-                for (uint32_t t = sub; t < width; t += TPM) {
-                    const uint32_t e = e0 + t * 32 + lane;
+                const uint32_t e0 = s_slice[slice] + lane;
+                const uint32_t width = (s_slice[slice + 1] - s_slice[slice]) >> 5;
+                // the neighbour's state and the spring's constants of row entry t
+                auto load = [&](uint32_t t, float4 &qp, float4 &qv, float &k, float &L0) {
+                    const uint32_t e = e0 + t * 32;
                     const uint32_t slot = s_nbr[e];         // own slot or halo slot
                     const float4 qa = srcA[slot];
                     const float2 qb = srcB[slot];
-                    const float4 qp = make_float4(qa.x, qa.y, qa.z, 0.f);
-                    const float4 qv = make_float4(qa.w, qb.x, qb.y, 0.f);
+                    qp = make_float4(qa.x, qa.y, qa.z, 0.f);
+                    qv = make_float4(qa.w, qb.x, qb.y, 0.f);
                     const float2 a = s_kl[e];
-                    float L0 = a.y;
+                    k = a.x;
+                    L0 = a.y;
                     if (ACT) {
                         const float2 s = s_act[e];               // (A cos phi, A sin phi)
                         L0 = a.y + a.y * (s.x * sp + s.y * cp);
                     }
-                    titan::spring_force(p, v, qp, qv, a.x, L0, c.c_uniform, fx, fy, fz);
+                };
+                // four entries in flight per thread (their shared-memory loads
+                // overlap), added in row order like the one-at-a-time tail
+                uint32_t t = sub;
+                for (; t + 3 * tpm < width; t += 4 * tpm) {
+                    float4 qp[4], qv[4];
+                    float k[4], L0[4], f[4], ux[4], uy[4], uz[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) load(t + u * tpm, qp[u], qv[u], k[u], L0[u]);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        titan::spring_terms(p, v, qp[u], qv[u], k[u], L0[u], c.c_uniform, f[u], ux[u], uy[u], uz[u]);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        fx = __fmaf_rn(f[u], ux[u], fx);
+                        fy = __fmaf_rn(f[u], uy[u], fy);
+                        fz = __fmaf_rn(f[u], uz[u], fz);
+                    }
+                }
+                for (; t < width; t += tpm) {
+                    float4 qp, qv;
+                    float k, L0;
+                    load(t, qp, qv, k, L0);
+                    titan::spring_force(p, v, qp, qv, k, L0, c.c_uniform, fx, fy, fz);
                 }
             }
-#pragma unroll
-            for (int o = 1; o < TPM; o <<= 1) {
+            for (uint32_t o = 1; o < tpm; o <<= 1) {   // CTA-uniform: every lane takes part
                 fx += __shfl_xor_sync(0xffffffffu, fx, o);
                 fy += __shfl_xor_sync(0xffffffffu, fy, o);
                 fz += __shfl_xor_sync(0xffffffffu, fz, o);
@@ -199,7 +228,7 @@ __global__ void k_batch_centroid(const uint32_t *__restrict__ mass_off, const ui
 struct Group {
     uint32_t cluster = 1;
     uint32_t threads = 256;
-    uint32_t tpm = 1;            // threads per mass
+    uint32_t tpm = 1;            // most threads per mass (each CTA takes the most that fit its masses)
     uint32_t cta_first = 0, cta_count = 0;
     size_t smem = 0;
 };
@@ -307,18 +336,15 @@ cudaError_t launch_group(titan_batch *b, const Group &g, cudaStream_t st, long l
     MassState *out = b->d_state[b->cur ^ 1];
     void (*kern)(const BatchCta *, const MassState *, MassState *, const uint32_t *, const float2 *,
                  const float2 *, const uint16_t *, const uint32_t *, titan::StepConst, long long, uint32_t, uint32_t,
-                 uint32_t, int *);
-#define PICK(T)                                                                                   \
-    if (b->has_act) kern = b->c.ground ? k_batch_rollout<true, true, T> : k_batch_rollout<true, false, T>; \
-    else kern = b->c.ground ? k_batch_rollout<false, true, T> : k_batch_rollout<false, false, T>;
-    if (g.tpm == 4) { PICK(4) } else if (g.tpm == 2) { PICK(2) } else { PICK(1) }
-#undef PICK
+                 uint32_t, uint32_t, int *);
+    if (b->has_act) kern = b->c.ground ? k_batch_rollout<true, true> : k_batch_rollout<true, false>;
+    else kern = b->c.ground ? k_batch_rollout<false, true> : k_batch_rollout<false, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
     if (e != cudaSuccess) return e;
     return cudaLaunchKernelEx(&cfg, kern, ctas, in, out, (const uint32_t *)b->d_slice, (const float2 *)b->d_kl,
                               (const float2 *)b->d_act, (const uint16_t *)b->d_nbr, (const uint32_t *)b->d_halo,
                               b->c, step0, n_steps,
-                              g.cluster, b->spin_limit, b->d_err);
+                              g.cluster, g.tpm, b->spin_limit, b->d_err);
 }
 
 // All groups run concurrently (one stream each), forked from and joined into b->stream.
@@ -393,7 +419,7 @@ titan_status titan_batch_create(uint32_t n_systems, const titan_masses *masses, 
     c.gx = (float)p->gravity[0]; c.gy = (float)p->gravity[1]; c.gz = (float)p->gravity[2];
     c.ground = p->ground ? 1 : 0; c.ground_k = (float)p->ground_k; c.mu = (float)p->mu;
     c.c_uniform = (float)p->damping;
-    c.act_omega = 2.0 * 3.14159265358979323846 * freq;
+    titan::set_act_clock(c, freq);
     int prev = -1;
     cudaGetDevice(&prev);
     // every failure after this point releases what was built and gives the
@@ -572,8 +598,8 @@ titan_status titan_batch_autotune(titan_batch *b, uint32_t probe_steps) {
     cudaEvent_t e0, e1;
     BATCH_CK(b, cudaEventCreate(&e0));
     BATCH_CK(b, cudaEventCreate(&e1));
-    const int cand_t[3] = {128, 256, 512};
-    const int cand_m[3] = {1, 2, 4};
+    const int cand_t[4] = {128, 256, 512, 1024};
+    const int cand_m[4] = {1, 2, 4, 8};
     for (auto &grp : b->groups) {
         float best = INFINITY;
         uint32_t best_t = grp.threads, best_m = grp.tpm;
@@ -613,8 +639,9 @@ titan_status titan_batch_info(const titan_batch *b, uint32_t group, uint32_t *cl
 
 titan_status titan_batch_configure(titan_batch *b, uint32_t group, uint32_t threads, uint32_t threads_per_mass) {
     if (!b || group >= b->groups.size()) return bfail(b, TITAN_E_INVALID, "batch is null or group out of range");
-    if (threads < 32 || threads > 512 || threads % 32 || !(threads_per_mass == 1 || threads_per_mass == 2 || threads_per_mass == 4))
-        return bfail(b, TITAN_E_INVALID, "threads must be a multiple of 32 in [32, 512] and threads_per_mass 1, 2 or 4");
+    if (threads < 32 || threads > 1024 || threads % 32 ||
+        !(threads_per_mass == 1 || threads_per_mass == 2 || threads_per_mass == 4 || threads_per_mass == 8))
+        return bfail(b, TITAN_E_INVALID, "threads must be a multiple of 32 in [32, 1024] and threads_per_mass 1, 2, 4 or 8");
     b->groups[group].threads = threads;
     b->groups[group].tpm = threads_per_mass;
     if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }

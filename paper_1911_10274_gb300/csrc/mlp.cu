@@ -27,6 +27,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <map>
 #include <mutex>
 #include <random>
 #include <string>
@@ -59,6 +60,8 @@ struct EpiArgs {
     float *out_f32;               // [M, ldc]       (F32: C; BIAS_GELU: pre-activation Z)
     __nv_bfloat16 *out_bf16;      // [M, ldc]       (BIAS_GELU: GELU(Z); GELU_GRAD: dZ)
     const float *z;               // [M, ldc]       (GELU_GRAD: the forward pre-activation)
+    __nv_bfloat16 *out_t = nullptr;   // [N, ldt] the transpose of out_bf16, if given (BIAS_GELU, GELU_GRAD)
+    int ldt = 0;
 };
 
 __device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
@@ -91,7 +94,10 @@ k_gemm_tn(const __grid_constant__ CUtensorMap tma_a, const __grid_constant__ CUt
     auto tileA = [&](int s) { return gsm + (size_t)s * (kStageA + kStageB); };
     auto tileB = [&](int s) { return gsm + (size_t)s * (kStageA + kStageB) + kStageA; };
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN_;
+    // split K (gridDim.z slices): slice z multiplies columns [z K, (z + 1) K) of A
+    // and B and writes its partial product to its own M x ldc block of out_f32
     const int num_kb = K / BK;
+    const int k0 = (int)blockIdx.z * K;
 
     if (warp == 0) titan::ptx::tmem_alloc(&tmem_base, kTmemCols);
     if (tid == 32) {
@@ -118,8 +124,8 @@ k_gemm_tn(const __grid_constant__ CUtensorMap tma_a, const __grid_constant__ CUt
                 break;
             }
             titan::ptx::mbar_arrive_expect_tx(&full[s], kStageA + kStageB);
-            titan::ptx::tma_load_2d(tileA(s), &tma_a, kb * BK, m0, &full[s]);
-            titan::ptx::tma_load_2d(tileB(s), &tma_b, kb * BK, n0, &full[s]);
+            titan::ptx::tma_load_2d(tileA(s), &tma_a, k0 + kb * BK, m0, &full[s]);
+            titan::ptx::tma_load_2d(tileB(s), &tma_b, k0 + kb * BK, n0, &full[s]);
             n_issued = kb + 1;
         }
     } else if (warp == 1 && lane == 0) {               // MMA issuer
@@ -152,7 +158,9 @@ k_gemm_tn(const __grid_constant__ CUtensorMap tma_a, const __grid_constant__ CUt
         // load issued on each stage and every committed MMA - before the
         // tensor memory is freed and the CTA exits
         if (tid == 0) {
-            atomicExch(err, 1);
+            // a plain store: the flag may live in pinned host memory
+            *reinterpret_cast<volatile int *>(err) = 1;
+            __threadfence_system();
             for (int st = 0; st < STAGES; ++st) {
                 int last = -1;
                 for (int kb = st; kb < n_issued; kb += STAGES) last = kb;
@@ -167,7 +175,7 @@ k_gemm_tn(const __grid_constant__ CUtensorMap tma_a, const __grid_constant__ CUt
             float v[32];
             titan::ptx::tmem_ld32(taddr + ((warp * 32u) << 16) + (uint32_t)c0, v);
             const int col = n0 + c0;
-            const size_t off = (size_t)row * ep.ldc + col;
+            const size_t off = (size_t)row * ep.ldc + col + (size_t)blockIdx.z * gridDim.y * BM * ep.ldc;
             if (ep.mode == EPI_F32) {
 #pragma unroll
                 for (int k = 0; k < 32; k += 4)
@@ -177,14 +185,23 @@ k_gemm_tn(const __grid_constant__ CUtensorMap tma_a, const __grid_constant__ CUt
                 for (int k = 0; k < 32; k += 2) {
                     const float z0 = v[k] + ep.bias[col + k], z1 = v[k + 1] + ep.bias[col + k + 1];
                     *reinterpret_cast<float2 *>(ep.out_f32 + off + k) = make_float2(z0, z1);
-                    *reinterpret_cast<__nv_bfloat162 *>(ep.out_bf16 + off + k) = __floats2bfloat162_rn(gelu(z0), gelu(z1));
+                    const __nv_bfloat162 h = __floats2bfloat162_rn(gelu(z0), gelu(z1));
+                    *reinterpret_cast<__nv_bfloat162 *>(ep.out_bf16 + off + k) = h;
+                    if (ep.out_t) {       // the 32 lanes write 32 consecutive rows of one column
+                        ep.out_t[(size_t)(col + k) * ep.ldt + row] = h.x;
+                        ep.out_t[(size_t)(col + k + 1) * ep.ldt + row] = h.y;
+                    }
                 }
             } else {
 #pragma unroll
                 for (int k = 0; k < 32; k += 2) {
                     const float2 z = *reinterpret_cast<const float2 *>(ep.z + off + k);
-                    *reinterpret_cast<__nv_bfloat162 *>(ep.out_bf16 + off + k) =
-                        __floats2bfloat162_rn(v[k] * gelu_grad(z.x), v[k + 1] * gelu_grad(z.y));
+                    const __nv_bfloat162 d = __floats2bfloat162_rn(v[k] * gelu_grad(z.x), v[k + 1] * gelu_grad(z.y));
+                    *reinterpret_cast<__nv_bfloat162 *>(ep.out_bf16 + off + k) = d;
+                    if (ep.out_t) {
+                        ep.out_t[(size_t)(col + k) * ep.ldt + row] = d.x;
+                        ep.out_t[(size_t)(col + k + 1) * ep.ldt + row] = d.y;
+                    }
                 }
             }
         }
@@ -229,28 +246,39 @@ __global__ void k_out_layer(const __nv_bfloat16 *__restrict__ H, const float *__
 }
 
 // dy = 2 (y - t) / B and the mean-squared error (one block, fixed order).
+// The output bias's gradient db = sum_b dy[b] is reduced alongside, in the
+// same fixed order.
 __global__ void k_loss(const float *__restrict__ y, const float *__restrict__ t, float *__restrict__ dy,
-                       float *__restrict__ loss, int B) {
-    __shared__ float part[256];
-    float s = 0.f;
+                       float *__restrict__ loss, int B, float *__restrict__ db) {
+    __shared__ float part[256], pdb[256];
+    float s = 0.f, sd = 0.f;
     for (int i = threadIdx.x; i < B; i += 256) {
         const float d = y[i] - t[i];
-        dy[i] = 2.f * d / (float)B;
+        const float g = 2.f * d / (float)B;
+        dy[i] = g;
         s += d * d;
+        sd += g;
     }
     part[threadIdx.x] = s;
+    pdb[threadIdx.x] = sd;
     __syncthreads();
     for (int o = 128; o; o >>= 1) {
-        if (threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
+        if (threadIdx.x < o) {
+            part[threadIdx.x] += part[threadIdx.x + o];
+            pdb[threadIdx.x] += pdb[threadIdx.x + o];
+        }
         __syncthreads();
     }
-    if (threadIdx.x == 0 && loss) *loss = part[0] / (float)B;
+    if (threadIdx.x == 0) {
+        if (loss) *loss = part[0] / (float)B;
+        if (db) *db = pdb[0];
+    }
 }
 
 // Column reductions over the batch run in two fixed-order stages so that the
 // whole GPU takes part: stage one sums chunks of kRowChunk rows per column
 // (grid: column blocks x row chunks), stage two adds the chunk sums in order.
-constexpr int kRowChunk = 64;
+constexpr int kRowChunk = 32;
 
 // Output layer backward, stage one: per (chunk, column) the partial of
 // dw[c] = sum_b dy[b] H[b, c]; and, elementwise, dZ[b, c] = dy[b] w[c] GELU'(Z[b, c]) in BF16.
@@ -281,32 +309,96 @@ __global__ void k_col_sum_part(const __nv_bfloat16 *__restrict__ M, float *__res
     part[(size_t)k * cols + c] = s;
 }
 
-// Stage two: out[c] = sum over chunks, in chunk order; thread `cols` also
-// forms db = sum_b dy[b] when dy is given (the output bias).
-__global__ void k_col_sum_final(const float *__restrict__ part, int chunks, int cols, float *__restrict__ out,
-                                const float *__restrict__ dy, int B, float *__restrict__ db) {
+// Stage two: out[c] = sum over chunks, in chunk order.
+__global__ void k_col_sum_final(const float *__restrict__ part, int chunks, int cols, float *__restrict__ out) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < cols) {
-        float s = 0.f;
-        for (int k = 0; k < chunks; ++k) s += part[(size_t)k * cols + c];
-        out[c] = s;
-    } else if (c == cols && dy) {
-        float s = 0.f;
-        for (int b = 0; b < B; ++b) s += dy[b];
-        db[0] = s;
-    }
+    if (c >= cols) return;
+    float s = 0.f;
+    for (int k = 0; k < chunks; ++k) s += part[(size_t)k * cols + c];
+    out[c] = s;
 }
 
-__global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m, float *__restrict__ v,
-                       size_t n, float lr, float b1, float b2, float eps, float c1, float c2) {
+// out[i] = sum over z of part[z][i], z in order (a split-K product's slices).
+__global__ void k_sum_splits(float *__restrict__ out, const float *__restrict__ part, int splits, size_t n) {
     const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const float gi = g[i];
-    const float mi = b1 * m[i] + (1.f - b1) * gi;
-    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-    m[i] = mi;
-    v[i] = vi;
-    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    float s = part[i];
+    for (int z = 1; z < splits; ++z) s += part[(size_t)z * n + i];
+    out[i] = s;
+}
+
+// Adam (beta1, beta2, eps; bias corrections c1 = 1 - b1^t, c2 = 1 - b2^t)
+// on parameter i: updates m, v and p, returns the new p.
+struct AdamArgs {
+    float *p;
+    const float *g;
+    float *m, *v;
+    const float *lr;                      // device: a captured step reads the current rate
+    unsigned long long *t;                // device step counter (advanced by k_adam_vec)
+    float b1, b2, eps;
+};
+
+__device__ __forceinline__ float adam_one(const AdamArgs &a, size_t i, float c1, float c2, float lr) {
+    const float gi = a.g[i];
+    const float mi = a.b1 * a.m[i] + (1.f - a.b1) * gi;
+    const float vi = a.b2 * a.v[i] + (1.f - a.b2) * gi * gi;
+    a.m[i] = mi;
+    a.v[i] = vi;
+    const float pi = a.p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + a.eps);
+    a.p[i] = pi;
+    return pi;
+}
+
+// The vectors of the network (b1, b2, b3, w4, b4: three ranges of `lens`
+// parameters from `offs`), one block; the block first takes step t + 1 and,
+// when every thread has read t, stores it (the weight kernel that follows in
+// stream order reads the new value).
+__global__ void k_adam_vec(AdamArgs a, uint32_t off0, uint32_t len0, uint32_t off1, uint32_t len1, uint32_t off2,
+                           uint32_t len2) {
+    const unsigned long long t = *a.t + 1;
+    const float tf = (float)t;
+    const float c1 = 1.f - powf(a.b1, tf), c2 = 1.f - powf(a.b2, tf), lr = *a.lr;
+    for (uint32_t k = threadIdx.x; k < len0; k += blockDim.x) adam_one(a, off0 + k, c1, c2, lr);
+    for (uint32_t k = threadIdx.x; k < len1; k += blockDim.x) adam_one(a, off1 + k, c1, c2, lr);
+    for (uint32_t k = threadIdx.x; k < len2; k += blockDim.x) adam_one(a, off2 + k, c1, c2, lr);
+    __syncthreads();
+    if (threadIdx.x == 0) *a.t = t;
+}
+
+// The three weight matrices W_l^T ([hid][in_l] at off_w[l], blockIdx.z = l),
+// 32 x 32 tiles: Adam on every entry, then the BF16 copies the next step's
+// products read - W^T itself (wt, same layout) and W (w, [in_l][hid], the
+// tile transposed through shared memory) - written coalesced.
+struct AdamW {
+    uint32_t off[3], cols[3];
+    __nv_bfloat16 *wt[3], *w[3];
+    uint32_t rows;
+};
+
+__global__ void k_adam_w(AdamArgs a, AdamW W) {
+    __shared__ __nv_bfloat16 tile[32][34];
+    // the layer's fields picked without indexing the parameter block at run time
+    const uint32_t l = blockIdx.z, rows = W.rows;
+    const uint32_t cols = l == 0 ? W.cols[0] : (l == 1 ? W.cols[1] : W.cols[2]);
+    const uint32_t off = l == 0 ? W.off[0] : (l == 1 ? W.off[1] : W.off[2]);
+    __nv_bfloat16 *const wt = l == 0 ? W.wt[0] : (l == 1 ? W.wt[1] : W.wt[2]);
+    __nv_bfloat16 *const wn = l == 0 ? W.w[0] : (l == 1 ? W.w[1] : W.w[2]);
+    const uint32_t bx = blockIdx.x * 32, by = blockIdx.y * 32;
+    if (bx >= cols || by >= rows) return;       // layers narrower than the grid
+    const float tf = (float)*a.t;
+    const float c1 = 1.f - powf(a.b1, tf), c2 = 1.f - powf(a.b2, tf), lr = *a.lr;
+    for (uint32_t k = threadIdx.y; k < 32; k += 8) {
+        const uint32_t r = by + k, c = bx + threadIdx.x;
+        const size_t o = (size_t)r * cols + c;
+        const __nv_bfloat16 h = __float2bfloat16_rn(adam_one(a, off + o, c1, c2, lr));
+        wt[o] = h;
+        tile[k][threadIdx.x] = h;
+    }
+    __syncthreads();
+    for (uint32_t k = threadIdx.y; k < 32; k += 8) {
+        const uint32_t c = bx + k, r = by + threadIdx.x;
+        wn[(size_t)c * rows + r] = tile[threadIdx.x][k];
+    }
 }
 
 // ------------------------------------------------------------------ host helpers
@@ -345,7 +437,7 @@ bool make_map(CUtensorMap *map, const void *base, uint64_t rows, uint64_t cols, 
 // K a multiple of 64; A, B 16-byte aligned with row strides of K elements.
 template <int BN_>
 cudaError_t gemm_tn_launch(const CUtensorMap &ma, const CUtensorMap &mb, int M, int N, int K, const EpiArgs &ep,
-                           cudaStream_t st, uint32_t spin_limit, int *err) {
+                           cudaStream_t st, uint32_t spin_limit, int *err, int splits = 1) {
     static std::atomic<uint64_t> attr_set{0};
     int dev = 0;
     cudaGetDevice(&dev);
@@ -355,21 +447,26 @@ cudaError_t gemm_tn_launch(const CUtensorMap &ma, const CUtensorMap &mb, int M, 
         if (e != cudaSuccess) return e;
         attr_set.fetch_or(1ull << (dev & 63));
     }
-    dim3 grid(N / BN_, M / BM);
-    k_gemm_tn<BN_><<<grid, kGemmThreads, gemm_smem<BN_>(), st>>>(ma, mb, K, ep, spin_limit, err);
+    dim3 grid(N / BN_, M / BM, splits);
+    k_gemm_tn<BN_><<<grid, kGemmThreads, gemm_smem<BN_>(), st>>>(ma, mb, K / splits, ep, spin_limit, err);
     return cudaGetLastError();
 }
 
+// splits > 1 (EPI_F32 only): K is cut into `splits` equal slices, each a
+// multiple of BK, whose partial products land in consecutive M x ldc blocks of
+// ep.out_f32 (the caller sums them, k_sum_splits).
 cudaError_t gemm_tn(const void *A, const void *B, int M, int N, int K, const EpiArgs &ep, cudaStream_t st,
-                    uint32_t spin_limit, int *err) {
+                    uint32_t spin_limit, int *err, int splits = 1) {
     if (M % BM || N % BN || K % BK || M <= 0 || N <= 0 || K <= 0) return cudaErrorInvalidValue;
+    if (splits < 1 || (splits > 1 && (ep.mode != EPI_F32 || (K / splits) % BK || K % splits)))
+        return cudaErrorInvalidValue;
     if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15) return cudaErrorInvalidValue;
     // 256-wide tiles once there are at least two waves of them on 152 SMs
-    const bool wide = N % 256 == 0 && (int64_t)(N / 256) * (M / BM) >= 2 * 152;
+    const bool wide = splits == 1 && N % 256 == 0 && (int64_t)(N / 256) * (M / BM) >= 2 * 152;
     CUtensorMap ma, mb;
     if (!make_map(&ma, A, M, K) || !make_map(&mb, B, N, K, wide ? 256 : 128)) return cudaErrorInvalidValue;
     return wide ? gemm_tn_launch<256>(ma, mb, M, N, K, ep, st, spin_limit, err)
-                : gemm_tn_launch<128>(ma, mb, M, N, K, ep, st, spin_limit, err);
+                : gemm_tn_launch<128>(ma, mb, M, N, K, ep, st, spin_limit, err, splits);
 }
 
 inline unsigned nblk(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -394,11 +491,25 @@ struct titan_mlp {
     float *Z[3] = {nullptr, nullptr, nullptr};
     __nv_bfloat16 *H[3] = {nullptr, nullptr, nullptr};
     __nv_bfloat16 *dZ[3] = {nullptr, nullptr, nullptr};
-    __nv_bfloat16 *xT = nullptr, *aT = nullptr, *bT = nullptr;   // transposes for weight gradients
+    // transposes for the weight gradients: x^T, H_0^T and H_1^T (written by
+    // the forward products' epilogues), dZ_l^T (one buffer, layer by layer)
+    __nv_bfloat16 *xT = nullptr, *HT[2] = {nullptr, nullptr}, *bT = nullptr;
     float *y = nullptr, *dy = nullptr;
     float *part = nullptr;                                 // column-reduction chunk sums [B / kRowChunk][hidden]
+    float *wsk = nullptr;                                  // split-K partial weight gradients [splits][hid][in]
+    size_t wsk_cap = 0;                                    // floats
     int *err = nullptr;
-    uint64_t adam_t = 0;
+    // the training step replayed as one CUDA graph per batch size: it reads its
+    // batch from gx / gt (the caller's arrays are copied there first) and the
+    // learning rate and step count from device memory
+    cudaStream_t capture = nullptr;
+    std::map<uint32_t, cudaGraphExec_t> train_graph;
+    bool graphs_ok = true;
+    __nv_bfloat16 *gx = nullptr;
+    float *gt = nullptr, *gloss = nullptr, *d_lr = nullptr;
+    unsigned long long *d_step = nullptr;
+    uint32_t g_cap = 0;
+    float lr_set = -1.f;
     std::vector<void *> allocs;
     std::string error;
 };
@@ -432,6 +543,18 @@ cudaError_t malloc_t(titan_mlp *m, T **p, size_t count) {
 
 uint32_t layer_in(const titan_mlp *m, int l) { return l == 0 ? m->in : m->hid; }
 
+// K slices of a weight-gradient product (hid x in, summed over the batch B):
+// its hid/128 x in/128 tiles alone fill a small part of the 152 SMs, so the
+// batch is cut into up to 8 slices of at least 4 k-blocks while the tiles
+// times the slices stay within one wave.
+int wgrad_splits(uint32_t hid, uint32_t in, uint32_t B) {
+    const uint32_t tiles = (hid / BM) * (in / 128);
+    int s = 1;
+    while (s < 8 && tiles * (uint32_t)(2 * s) <= 152 && B % (uint32_t)(2 * s * BK) == 0 && B / (2 * s) >= 4 * BK)
+        s *= 2;
+    return s;
+}
+
 // Refreshes both BF16 layouts of the hidden-layer weights from the FP32 master.
 cudaError_t refresh_bf16(titan_mlp *m) {
     for (int l = 0; l < 3; ++l) {
@@ -440,6 +563,25 @@ cudaError_t refresh_bf16(titan_mlp *m) {
         dim3 grid(nblk(layer_in(m, l), 32), nblk(m->hid, 32));
         k_transpose_bf16<<<grid, dim3(32, 8), 0, m->stream>>>(m->wt[l], m->w[l], (int)m->hid, (int)layer_in(m, l));
     }
+    return cudaGetLastError();
+}
+
+// One Adam step on every parameter (the step counter advanced on the
+// device) and the BF16 copies of the new weights, in two launches.
+cudaError_t adam_step(titan_mlp *m) {
+    AdamArgs a{m->p, m->g, m->m, m->v, m->d_lr, m->d_step, 0.9f, 0.999f, 1e-8f};
+    // b1, b2 and (b3, w4, b4): the parameter layout keeps the last three contiguous
+    k_adam_vec<<<1, 1024, 0, m->stream>>>(a, (uint32_t)m->off_b[0], m->hid, (uint32_t)m->off_b[1], m->hid,
+                                          (uint32_t)m->off_b[2], 2 * m->hid + 1);
+    AdamW W;
+    for (int l = 0; l < 3; ++l) {
+        W.off[l] = (uint32_t)m->off_w[l];
+        W.cols[l] = layer_in(m, l);
+        W.wt[l] = m->wt[l];
+        W.w[l] = m->w[l];
+    }
+    W.rows = m->hid;
+    k_adam_w<<<dim3(std::max(m->in, m->hid) / 32, m->hid / 32, 3), dim3(32, 8), 0, m->stream>>>(a, W);
     return cudaGetLastError();
 }
 
@@ -452,20 +594,33 @@ cudaError_t ensure_batch(titan_mlp *m, uint32_t B) {
         if ((e = malloc_t(m, &m->dZ[l], (size_t)B * m->hid)) != cudaSuccess) return e;
     }
     if ((e = malloc_t(m, &m->xT, (size_t)B * m->in)) != cudaSuccess) return e;
-    if ((e = malloc_t(m, &m->aT, (size_t)B * m->hid)) != cudaSuccess) return e;
+    if ((e = malloc_t(m, &m->HT[0], (size_t)B * m->hid)) != cudaSuccess) return e;
+    if ((e = malloc_t(m, &m->HT[1], (size_t)B * m->hid)) != cudaSuccess) return e;
     if ((e = malloc_t(m, &m->bT, (size_t)B * m->hid)) != cudaSuccess) return e;
     if ((e = malloc_t(m, &m->y, B)) != cudaSuccess) return e;
     if ((e = malloc_t(m, &m->dy, B)) != cudaSuccess) return e;
     if ((e = malloc_t(m, &m->part, (size_t)((B + kRowChunk - 1) / kRowChunk) * m->hid)) != cudaSuccess) return e;
+    size_t ws = 0;
+    for (int l = 0; l < 3; ++l)
+        ws = std::max(ws, (size_t)wgrad_splits(m->hid, layer_in(m, l), B) * m->hid * layer_in(m, l));
+    if (ws > m->wsk_cap) {
+        if ((e = malloc_t(m, &m->wsk, ws)) != cudaSuccess) return e;
+        m->wsk_cap = ws;
+    }
     m->cap = B;
     return cudaSuccess;
 }
 
-cudaError_t forward_pass(titan_mlp *m, const __nv_bfloat16 *x, uint32_t B, float *y) {
+// keep_t: also write H_0^T and H_1^T (the backward pass's weight gradients read them).
+cudaError_t forward_pass(titan_mlp *m, const __nv_bfloat16 *x, uint32_t B, float *y, bool keep_t = false) {
     cudaError_t e;
     const __nv_bfloat16 *a = x;
     for (int l = 0; l < 3; ++l) {
         EpiArgs ep{EPI_BIAS_GELU, (int)m->hid, m->p + m->off_b[l], m->Z[l], m->H[l], nullptr};
+        if (keep_t && l < 2) {
+            ep.out_t = m->HT[l];
+            ep.ldt = (int)B;
+        }
         if ((e = gemm_tn(a, m->wt[l], (int)B, (int)m->hid, (int)layer_in(m, l), ep, m->stream, m->spin_limit, m->err)) != cudaSuccess)
             return e;
         a = m->H[l];
@@ -475,35 +630,71 @@ cudaError_t forward_pass(titan_mlp *m, const __nv_bfloat16 *x, uint32_t B, float
 }
 
 cudaError_t backward_pass(titan_mlp *m, const __nv_bfloat16 *x, const float *t, uint32_t B, float *loss) {
-    cudaError_t e = forward_pass(m, x, B, m->y);
+    cudaError_t e = forward_pass(m, x, B, m->y, true);
     if (e != cudaSuccess) return e;
-    k_loss<<<1, 256, 0, m->stream>>>(m->y, t, m->dy, loss, (int)B);
+    k_loss<<<1, 256, 0, m->stream>>>(m->y, t, m->dy, loss, (int)B, m->g + m->off_b4);
     const int chunks = ((int)B + kRowChunk - 1) / kRowChunk;
     k_out_backward<<<dim3(nblk(m->hid, 128), chunks), 128, 0, m->stream>>>(m->H[2], m->Z[2], m->dy, m->p + m->off_w4,
                                                                           m->part, m->dZ[2], (int)B, (int)m->hid);
-    k_col_sum_final<<<nblk(m->hid + 1, 128), 128, 0, m->stream>>>(m->part, chunks, (int)m->hid, m->g + m->off_w4,
-                                                                   m->dy, (int)B, m->g + m->off_b4);
+    k_col_sum_final<<<nblk(m->hid, 128), 128, 0, m->stream>>>(m->part, chunks, (int)m->hid, m->g + m->off_w4);
     for (int l = 2; l >= 0; --l) {
         // dW_l^T (hid x in_l) = dZ_l^T (hid x B) . A_{l-1}^T (in_l x B)^T
         const uint32_t in = layer_in(m, l);
-        const __nv_bfloat16 *act = l == 0 ? x : m->H[l - 1];
-        __nv_bfloat16 *actT = l == 0 ? m->xT : m->aT;
-        k_transpose_bf16<<<dim3(nblk(m->hid, 32), nblk(B, 32)), dim3(32, 8), 0, m->stream>>>(m->dZ[l], m->bT, (int)B, (int)m->hid);
-        k_transpose_bf16<<<dim3(nblk(in, 32), nblk(B, 32)), dim3(32, 8), 0, m->stream>>>(act, actT, (int)B, (int)in);
-        EpiArgs ep{EPI_F32, (int)in, nullptr, m->g + m->off_w[l], nullptr, nullptr};
-        if ((e = gemm_tn(m->bT, actT, (int)m->hid, (int)in, (int)B, ep, m->stream, m->spin_limit, m->err)) != cudaSuccess)
+        const __nv_bfloat16 *actT = l == 0 ? m->xT : m->HT[l - 1];
+        // dZ_2^T here; dZ_1^T and dZ_0^T come from the epilogue of the product that forms them
+        if (l == 2)
+            k_transpose_bf16<<<dim3(nblk(m->hid, 32), nblk(B, 32)), dim3(32, 8), 0, m->stream>>>(m->dZ[2], m->bT, (int)B,
+                                                                                                 (int)m->hid);
+        if (l == 0)
+            k_transpose_bf16<<<dim3(nblk(in, 32), nblk(B, 32)), dim3(32, 8), 0, m->stream>>>(x, m->xT, (int)B, (int)in);
+        const int splits = wgrad_splits(m->hid, in, B);
+        EpiArgs ep{EPI_F32, (int)in, nullptr, splits > 1 ? m->wsk : m->g + m->off_w[l], nullptr, nullptr};
+        if ((e = gemm_tn(m->bT, actT, (int)m->hid, (int)in, (int)B, ep, m->stream, m->spin_limit, m->err, splits)) !=
+            cudaSuccess)
             return e;
+        if (splits > 1) {
+            const size_t n = (size_t)m->hid * in;
+            k_sum_splits<<<nblk(n, 256), 256, 0, m->stream>>>(m->g + m->off_w[l], m->wsk, splits, n);
+        }
         k_col_sum_part<<<dim3(nblk(m->hid, 128), chunks), 128, 0, m->stream>>>(m->dZ[l], m->part, (int)B, (int)m->hid);
-        k_col_sum_final<<<nblk(m->hid, 128), 128, 0, m->stream>>>(m->part, chunks, (int)m->hid, m->g + m->off_b[l],
-                                                                  nullptr, (int)B, nullptr);
+        k_col_sum_final<<<nblk(m->hid, 128), 128, 0, m->stream>>>(m->part, chunks, (int)m->hid, m->g + m->off_b[l]);
         if (l > 0) {
             // dZ_{l-1} = (dZ_l . W_l^T) * GELU'(Z_{l-1}):  A = dZ_l (B x hid), B operand = W_l (in x hid)
             EpiArgs ep2{EPI_GELU_GRAD, (int)m->hid, nullptr, nullptr, m->dZ[l - 1], m->Z[l - 1]};
+            ep2.out_t = m->bT;            // this layer's weight-gradient product (above) has read bT
+            ep2.ldt = (int)B;
             if ((e = gemm_tn(m->dZ[l], m->w[l], (int)B, (int)in, (int)m->hid, ep2, m->stream, m->spin_limit, m->err)) != cudaSuccess)
                 return e;
         }
     }
     return cudaGetLastError();
+}
+
+// One training step for a batch of B read from gx / gt, captured into a graph:
+// the forward and backward products, the step counter, Adam, and the BF16
+// copies of the new weights.
+cudaError_t capture_train(titan_mlp *m, uint32_t B, cudaGraphExec_t *out) {
+    cudaError_t e = cudaStreamBeginCapture(m->capture, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    cudaStream_t saved = m->stream;
+    m->stream = m->capture;
+    cudaError_t le = backward_pass(m, m->gx, m->gt, B, m->gloss);
+    if (le == cudaSuccess) le = adam_step(m);
+    m->stream = saved;
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(m->capture, &g);
+    if (le != cudaSuccess || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return le != cudaSuccess ? le : e;
+    }
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    return e;
+}
+
+void drop_train_graphs(titan_mlp *m) {
+    for (auto &kv : m->train_graph) cudaGraphExecDestroy(kv.second);
+    m->train_graph.clear();
 }
 
 titan_status check_err(titan_mlp *m) {
@@ -521,38 +712,67 @@ titan_status check_err(titan_mlp *m) {
 
 extern "C" {
 
+// One bounded-wait flag per device ordinal for the standalone GEMM, in
+// pinned host memory mapped into the device: a call reads it without
+// waiting for its stream.
+namespace {
+std::mutex g_gemm_mu;
+volatile int *g_gemm_flag[64] = {};
+int *g_gemm_flag_dev[64] = {};
+
+titan_status gemm_flag(int *dev_out, volatile int **host, int **dev_ptr, const char *who) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+        return mfail(nullptr, TITAN_E_CUDA, std::string(who) + ": no current device");
+    std::lock_guard<std::mutex> lk(g_gemm_mu);
+    if (!g_gemm_flag[dev]) {
+        void *h = nullptr, *d = nullptr;
+        if (cudaHostAlloc(&h, sizeof(int), cudaHostAllocMapped) != cudaSuccess)
+            return mfail(nullptr, TITAN_E_OOM, std::string(who) + ": error flag");
+        *static_cast<volatile int *>(h) = 0;
+        if (cudaHostGetDevicePointer(&d, h, 0) != cudaSuccess) {
+            cudaFreeHost(h);
+            return mfail(nullptr, TITAN_E_CUDA, std::string(who) + ": error flag");
+        }
+        g_gemm_flag[dev] = static_cast<volatile int *>(h);
+        g_gemm_flag_dev[dev] = static_cast<int *>(d);
+    }
+    *dev_out = dev;
+    *host = g_gemm_flag[dev];
+    *dev_ptr = g_gemm_flag_dev[dev];
+    return TITAN_OK;
+}
+}  // namespace
+
 titan_status titan_gemm_bf16_tn(uint32_t M, uint32_t N, uint32_t K, const uint16_t *A_dev, const uint16_t *B_dev,
                                 float *C_dev, void *stream) {
     if (!A_dev || !B_dev || !C_dev) return mfail(nullptr, TITAN_E_INVALID, "titan_gemm_bf16_tn: null pointer");
     if (M % BM || N % BN || K % BK || !M || !N || !K)
         return mfail(nullptr, TITAN_E_INVALID, "titan_gemm_bf16_tn: M and N must be multiples of 128, K of 64");
-    // one device error flag per device ordinal, allocated on first use with that device current
-    static int *err_of[64] = {};
-    static std::mutex mu;
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
-        return mfail(nullptr, TITAN_E_CUDA, "titan_gemm_bf16_tn: no current device");
+    volatile int *flag = nullptr;
     int *err = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(mu);
-        if (!err_of[dev]) {
-            if (cudaMalloc(&err_of[dev], sizeof(int)) != cudaSuccess)
-                return mfail(nullptr, TITAN_E_OOM, "titan_gemm_bf16_tn: error flag");
-            if (cudaMemset(err_of[dev], 0, sizeof(int)) != cudaSuccess)
-                return mfail(nullptr, TITAN_E_CUDA, "titan_gemm_bf16_tn: error flag");
-        }
-        err = err_of[dev];
+    titan_status fs = gemm_flag(&dev, &flag, &err, "titan_gemm_bf16_tn");
+    if (fs != TITAN_OK) return fs;
+    if (*flag) {                     // an earlier call's kernel gave up on a wait
+        *flag = 0;
+        return mfail(nullptr, TITAN_E_TIMEOUT, "titan_gemm_bf16_tn: a bounded wait expired in an earlier call");
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     EpiArgs ep{EPI_F32, (int)N, nullptr, C_dev, nullptr, nullptr};
     cudaError_t e = gemm_tn(A_dev, B_dev, (int)M, (int)N, (int)K, ep, st, 1u << 22, err);
     if (e != cudaSuccess) return mfail(nullptr, TITAN_E_CUDA, std::string("titan_gemm_bf16_tn: ") + cudaGetErrorString(e));
-    e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return mfail(nullptr, TITAN_E_CUDA, std::string("titan_gemm_bf16_tn: ") + cudaGetErrorString(e));
-    int flag = 0;
-    cudaMemcpy(&flag, err, sizeof(int), cudaMemcpyDeviceToHost);
-    if (flag) {
-        cudaMemset(err, 0, sizeof(int));
+    return TITAN_OK;
+}
+
+titan_status titan_gemm_check(void) {
+    int dev = 0;
+    volatile int *flag = nullptr;
+    int *err = nullptr;
+    titan_status fs = gemm_flag(&dev, &flag, &err, "titan_gemm_check");
+    if (fs != TITAN_OK) return fs;
+    if (*flag) {
+        *flag = 0;
         return mfail(nullptr, TITAN_E_TIMEOUT, "titan_gemm_bf16_tn: a bounded wait expired");
     }
     return TITAN_OK;
@@ -581,6 +801,7 @@ titan_status titan_mlp_create(uint32_t in, uint32_t hidden, uint64_t seed, int32
     auto bail = [&](titan_status st) {
         titan::set_thread_error(m->error);
         for (void *p : m->allocs) cudaFree(p);
+        if (m->capture) cudaStreamDestroy(m->capture);
         if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
         delete m;
         return st;
@@ -599,6 +820,11 @@ titan_status titan_mlp_create(uint32_t in, uint32_t hidden, uint64_t seed, int32
     C_CK(malloc_t(m, &m->m, o));
     C_CK(malloc_t(m, &m->v, o));
     C_CK(malloc_t(m, &m->err, 1));
+    C_CK(malloc_t(m, &m->d_lr, 1));
+    C_CK(malloc_t(m, &m->gloss, 1));
+    C_CK(malloc_t(m, &m->d_step, 1));
+    C_CK(cudaMemset(m->d_step, 0, sizeof(unsigned long long)));
+    C_CK(cudaStreamCreateWithFlags(&m->capture, cudaStreamNonBlocking));
     for (int l = 0; l < 3; ++l) {
         C_CK(malloc_t(m, &m->wt[l], (size_t)hidden * layer_in(m, l)));
         C_CK(malloc_t(m, &m->w[l], (size_t)hidden * layer_in(m, l)));
@@ -670,14 +896,40 @@ titan_status titan_mlp_train_step(titan_mlp *m, const uint16_t *x_dev, const flo
     if (!m || !x_dev || !t_dev || batch % 128 || !batch)
         return mfail(m, TITAN_E_INVALID, "titan_mlp_train_step: batch must be a positive multiple of 128");
     MLP_CK(m, cudaSetDevice(m->device));
+    const uint32_t cap0 = m->cap;
     MLP_CK(m, ensure_batch(m, batch));
+    if (m->cap != cap0) drop_train_graphs(m);           // the activations moved
+    if (lr != m->lr_set) {                              // pageable source: staged before the call returns
+        MLP_CK(m, cudaMemcpyAsync(m->d_lr, &lr, sizeof(float), cudaMemcpyHostToDevice, m->stream));
+        m->lr_set = lr;
+    }
+    if (m->graphs_ok) {
+        if (batch > m->g_cap) {
+            drop_train_graphs(m);
+            MLP_CK(m, malloc_t(m, &m->gx, (size_t)batch * m->in));
+            MLP_CK(m, malloc_t(m, &m->gt, batch));
+            m->g_cap = batch;
+        }
+        auto it = m->train_graph.find(batch);
+        if (it == m->train_graph.end()) {
+            cudaGraphExec_t ge = nullptr;
+            if (capture_train(m, batch, &ge) == cudaSuccess) {
+                it = m->train_graph.emplace(batch, ge).first;
+            } else {                                    // capture refused: launch the kernels directly
+                cudaGetLastError();
+                m->graphs_ok = false;
+            }
+        }
+        if (m->graphs_ok) {
+            MLP_CK(m, cudaMemcpyAsync(m->gx, x_dev, (size_t)batch * m->in * 2, cudaMemcpyDeviceToDevice, m->stream));
+            MLP_CK(m, cudaMemcpyAsync(m->gt, t_dev, (size_t)batch * 4, cudaMemcpyDeviceToDevice, m->stream));
+            MLP_CK(m, cudaGraphLaunch(it->second, m->stream));
+            if (loss_dev) MLP_CK(m, cudaMemcpyAsync(loss_dev, m->gloss, 4, cudaMemcpyDeviceToDevice, m->stream));
+            return TITAN_OK;
+        }
+    }
     MLP_CK(m, backward_pass(m, reinterpret_cast<const __nv_bfloat16 *>(x_dev), t_dev, batch, loss_dev));
-    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
-    ++m->adam_t;
-    const float c1 = 1.f - std::pow(b1, (float)m->adam_t), c2 = 1.f - std::pow(b2, (float)m->adam_t);
-    k_adam<<<nblk(m->n_params, 256), 256, 0, m->stream>>>(m->p, m->g, m->m, m->v, m->n_params, lr, b1, b2, eps, c1, c2);
-    MLP_CK(m, cudaGetLastError());
-    MLP_CK(m, refresh_bf16(m));
+    MLP_CK(m, adam_step(m));
     return TITAN_OK;
 }
 
@@ -688,6 +940,8 @@ const char *titan_mlp_last_error(const titan_mlp *m) { return m ? m->error.c_str
 titan_status titan_mlp_destroy(titan_mlp *m) {
     if (!m) return TITAN_OK;
     cudaStreamSynchronize(m->stream);
+    drop_train_graphs(m);
+    if (m->capture) cudaStreamDestroy(m->capture);
     for (void *p : m->allocs) cudaFree(p);
     if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
     delete m;

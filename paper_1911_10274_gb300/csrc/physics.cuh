@@ -6,8 +6,6 @@
 
 namespace titan {
 
-constexpr double kTwoPi = 6.283185307179586476925286766559;
-
 // One 256-bit read-only load of a mass's whole 32-byte state (sm_100+ vector
 // width): one L1 request per neighbour gather instead of two.
 __device__ __forceinline__ void load_state(const MassState *m, float4 &p, float4 &v) {
@@ -29,19 +27,21 @@ __device__ __forceinline__ void load_state_after_wait(const MassState *m, float4
 }
 
 // Phase of the actuation clock at step `step`: 2 pi f t mod 2 pi with
-// t = step dt, formed in FP64 so that long runs keep full FP32 phase accuracy.
+// t = step dt.  The turns step x (f dt) are formed modulo 1 exactly in 64-bit
+// fixed point (integer products wrap modulo 2^64) and their top 24 bits give
+// the phase, so long runs keep full FP32 phase accuracy without FP64.
 __device__ __forceinline__ float clock_phase(const StepConst &c, long long step) {
-    double ph = c.act_omega * ((double)step * c.dt_d);
-    ph -= kTwoPi * floor(ph / kTwoPi);
-    return (float)ph;
+    const unsigned long long fr = (unsigned long long)step * c.act_turns;
+    return __fmul_rn((float)(fr >> 40), 3.74507028e-7f);      // 2 pi / 2^24
 }
 
 // Per-thread actuation clock for step `step`: mode 1 the phase 2 pi f t mod
-// 2 pi, mode 2 (the worm of Sec. V-B, Eq. 3) the time t mod t_p.
+// 2 pi, mode 2 (the worm of Sec. V-B, Eq. 3) the time t mod t_p (the same
+// fixed-point turns, of dt / t_p).
 __device__ __forceinline__ float actuation_clock(const StepConst &c, long long step) {
     if (c.act_mode == 2) {
-        const double t = (double)step * c.dt_d;
-        return (float)(t - c.worm_period * floor(t / c.worm_period));
+        const unsigned long long fr = (unsigned long long)step * c.worm_turns;
+        return __fmul_rn((float)(fr >> 40), c.worm_unit);
     }
     return clock_phase(c, step);
 }

@@ -285,8 +285,24 @@ bool uses_cube(const titan_sim *sim) { return sim->csr_kernel == 8; }
 
 
 // Uploads the per-entry actuation arrays of the current layout.
+// Brings act_amp / act_phase up to the values last set from device arrays.
+cudaError_t fetch_act_host(titan_sim *sim) {
+    if (!sim->act_host_stale) return cudaSuccess;
+    sim->act_amp.resize(sim->s);
+    sim->act_phase.resize(sim->s);
+    cudaError_t e = cudaMemcpyAsync(sim->act_amp.data(), sim->d_act_amp, (size_t)sim->s * 4, cudaMemcpyDeviceToHost,
+                                    sim->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(sim->act_phase.data(), sim->d_act_phase, (size_t)sim->s * 4, cudaMemcpyDeviceToHost,
+                            sim->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(sim->stream);
+    if (e == cudaSuccess) sim->act_host_stale = false;
+    return e;
+}
+
 cudaError_t upload_actuation(titan_sim *sim) {
     cudaError_t e;
+    if ((e = fetch_act_host(sim)) != cudaSuccess) return e;
     if (sim->accumulate == TITAN_ACCUM_CSR) {
         if (!sim->d_act && (e = dev_alloc(sim, &sim->d_act, sim->sell.entries + titan::kStreamTail)) != cudaSuccess)
             return e;
@@ -314,6 +330,59 @@ cudaError_t upload_actuation(titan_sim *sim) {
         a[r] = make_float2(sim->act_amp[q], sim->act_phase[q]);
     }
     return upload(sim->d_ract, a, sim->stream);
+}
+
+__global__ void k_count_nonfinite(const float *__restrict__ a, const float *__restrict__ b, uint32_t n,
+                                  int *__restrict__ bad) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && !(isfinite(a[i]) && isfinite(b[i]))) atomicAdd(bad, 1);
+}
+
+// out[i] = (amp, phase) of the spring behind entry i, zero for padding.
+__global__ void k_scatter_act(const uint32_t *__restrict__ spring_of, uint32_t n, const float *__restrict__ amp,
+                              const float *__restrict__ phase, float2 *__restrict__ out) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t q = spring_of[i];
+    out[i] = q != UINT32_MAX ? make_float2(amp[q], phase[q]) : make_float2(0.f, 0.f);
+}
+
+// Uploads the host map `map` into *dst once (spring of each entry).
+cudaError_t ensure_map(titan_sim *sim, uint32_t **dst, const std::vector<uint32_t> &map) {
+    if (*dst) return cudaSuccess;
+    cudaError_t e = dev_alloc(sim, dst, map.size());
+    if (e != cudaSuccess) return e;
+    return map.empty() ? cudaSuccess
+                       : cudaMemcpy(*dst, map.data(), map.size() * 4, cudaMemcpyHostToDevice);
+}
+
+// Fills the per-entry actuation arrays of the active layout from the
+// caller-order device arrays d_act_amp / d_act_phase.
+cudaError_t scatter_actuation_dev(titan_sim *sim) {
+    cudaError_t e;
+    auto run = [&](const uint32_t *map, uint32_t n, float2 *out) {
+        if (n) k_scatter_act<<<(n + 255) / 256, 256, 0, sim->stream>>>(map, n, sim->d_act_amp, sim->d_act_phase, out);
+        return cudaGetLastError();
+    };
+    if (sim->accumulate == TITAN_ACCUM_CSR) {
+        if (!sim->d_act) {
+            if ((e = dev_alloc(sim, &sim->d_act, sim->sell.entries + titan::kStreamTail)) != cudaSuccess) return e;
+            if ((e = cudaMemsetAsync(sim->d_act, 0, (sim->sell.entries + titan::kStreamTail) * sizeof(float2),
+                                     sim->stream)) != cudaSuccess)
+                return e;
+        }
+        if ((e = ensure_map(sim, &sim->d_entry_spring, sim->sell.spring)) != cudaSuccess) return e;
+        if ((e = run(sim->d_entry_spring, sim->sell.entries, sim->d_act)) != cudaSuccess) return e;
+        if (uses_cube(sim)) {
+            if (!sim->d_cact && (e = dev_alloc(sim, &sim->d_cact, sim->cube.entries)) != cudaSuccess) return e;
+            if ((e = ensure_map(sim, &sim->d_cube_spring, sim->cube.spring)) != cudaSuccess) return e;
+            if ((e = run(sim->d_cube_spring, sim->cube.entries, sim->d_cact)) != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+    if (!sim->d_ract && (e = dev_alloc(sim, &sim->d_ract, sim->s)) != cudaSuccess) return e;
+    if ((e = ensure_map(sim, &sim->d_rec_spring, sim->rec.order)) != cudaSuccess) return e;
+    return run(sim->d_rec_spring, sim->s, sim->d_ract);
 }
 
 // after_step: the operation just before this one on `st` is this
@@ -928,6 +997,7 @@ titan_status titan_set_actuation(titan_sim *sim, uint32_t n, const uint32_t *ids
         if (!std::isfinite(amp[q]) || !std::isfinite(phase[q])) return fail(sim, TITAN_E_INVALID, "non-finite amp or phase");
     }
     DeviceGuard dg(sim->device);
+    TITAN_CK(sim, fetch_act_host(sim));
     if (sim->act_amp.empty() || sim->act_mode != 1) {
         sim->act_amp.assign(sim->s, 0.f);
         sim->act_phase.assign(sim->s, 0.f);
@@ -936,13 +1006,69 @@ titan_status titan_set_actuation(titan_sim *sim, uint32_t n, const uint32_t *ids
         sim->act_amp[ids[q]] = amp[q];
         sim->act_phase[ids[q]] = phase[q];
     }
-    sim->c.act_omega = 2.0 * 3.14159265358979323846 * (double)freq_hz;
+    titan::set_act_clock(sim->c, (double)freq_hz);
     sim->c.act_mode = 1;
     sim->act_mode = 1;
     TITAN_CK(sim, upload_actuation(sim));
     sim->has_act = true;
     TITAN_CK(sim, entries_grew(sim));   // larger entries
     free_graphs(sim);       // kernel variant and constants changed
+    return TITAN_OK;
+}
+
+titan_status titan_set_actuation_dev(titan_sim *sim, uint32_t n, const float *amp_dev, const float *phase_dev,
+                                     float freq_hz) {
+    if (!sim) return fail(nullptr, TITAN_E_INVALID, "sim is null");
+    BusyGuard bg(sim);
+    if (!bg.acquired) return fail(sim, TITAN_E_BUSY, "another call on this handle is in progress");
+    if (!std::isfinite(freq_hz)) return fail(sim, TITAN_E_INVALID, "freq_hz must be finite");
+    {
+        titan_status es_ = titan::ensure_layout(sim);
+        if (es_ != TITAN_OK) return es_;
+    }
+    const uint32_t S = sim->s;
+    if (n != S)
+        return fail(sim, TITAN_E_INVALID, "n (" + std::to_string(n) + ") is not the spring count (" +
+                                              std::to_string(S) + ")");
+    if (S && (!amp_dev || !phase_dev)) return fail(sim, TITAN_E_INVALID, "amp and phase are required");
+    DeviceGuard dg(sim->device);
+    if (S) {
+        // the arguments are checked on the device before anything changes
+        if (!sim->d_check) TITAN_CK(sim, dev_alloc(sim, &sim->d_check, 1));
+        TITAN_CK(sim, cudaMemsetAsync(sim->d_check, 0, sizeof(int), sim->stream));
+        k_count_nonfinite<<<(S + 255) / 256, 256, 0, sim->stream>>>(amp_dev, phase_dev, S, sim->d_check);
+        TITAN_CK(sim, cudaGetLastError());
+        int bad = 0;
+        TITAN_CK(sim, cudaMemcpyAsync(&bad, sim->d_check, sizeof(int), cudaMemcpyDeviceToHost, sim->stream));
+        TITAN_CK(sim, cudaStreamSynchronize(sim->stream));
+        if (bad) return fail(sim, TITAN_E_INVALID, "non-finite amp or phase (" + std::to_string(bad) + " springs)");
+        if (!sim->d_act_amp) {
+            TITAN_CK(sim, dev_alloc(sim, &sim->d_act_amp, S));
+            TITAN_CK(sim, dev_alloc(sim, &sim->d_act_phase, S));
+        }
+        TITAN_CK(sim, cudaMemcpyAsync(sim->d_act_amp, amp_dev, (size_t)S * 4, cudaMemcpyDeviceToDevice, sim->stream));
+        TITAN_CK(sim, cudaMemcpyAsync(sim->d_act_phase, phase_dev, (size_t)S * 4, cudaMemcpyDeviceToDevice, sim->stream));
+        TITAN_CK(sim, cudaStreamSynchronize(sim->stream));   // the caller's arrays are free on return
+    }
+    titan::StepConst nc = sim->c;
+    titan::set_act_clock(nc, (double)freq_hz);
+    // captured step graphs hold the kernel variant and the clock constants
+    const bool same = sim->has_act && sim->act_mode == 1 && sim->c.act_turns == nc.act_turns &&
+                      sim->c.act_omega == nc.act_omega;
+    sim->c = nc;
+    sim->c.act_mode = 1;
+    sim->act_mode = 1;
+    sim->act_host_stale = S > 0;
+    if (!S) {
+        sim->act_amp.clear();
+        sim->act_phase.clear();
+    }
+    TITAN_CK(sim, scatter_actuation_dev(sim));
+    if (!same) {
+        sim->has_act = true;
+        TITAN_CK(sim, entries_grew(sim));
+        free_graphs(sim);
+    }
     return TITAN_OK;
 }
 
@@ -1112,6 +1238,10 @@ cudaError_t enable_per_spring_damping(titan_sim *sim) {
 
 // Pushes the current host parameters of device springs `ids` into the device layout.
 cudaError_t push_springs(titan_sim *sim, const std::vector<uint32_t> &ids, bool damping, bool actuation) {
+    if (actuation) {
+        cudaError_t fe = fetch_act_host(sim);
+        if (fe != cudaSuccess) return fe;
+    }
     std::vector<uint32_t> wi, wv, ci, cv, ai, av;
     std::vector<uint32_t> xwi, xwv, xci, xcv, xai, xav;      // the cube stream (cube kernel)
     for (uint32_t q : ids) {
@@ -1204,6 +1334,7 @@ titan_status titan::ensure_layout(titan_sim *sim) {
     titan_status st = titan_create(&ms, &ss, &p, &fresh);
     if (st != TITAN_OK) return fail(sim, st, std::string("rebuild after a topology edit: ") + titan_last_error(nullptr));
     // carry the clock and the actuation across
+    TITAN_CK(sim, fetch_act_host(sim));
     const uint64_t steps = sim->steps;
     std::vector<float> amp = sim->act_amp, phase = sim->act_phase;
     const int act_mode = sim->act_mode;
@@ -1224,8 +1355,11 @@ titan_status titan::ensure_layout(titan_sim *sim) {
         sim->act_mode = act_mode;
         sim->c.act_mode = oldc.act_mode;
         sim->c.act_omega = oldc.act_omega;
+        sim->c.act_turns = oldc.act_turns;
         sim->c.worm_omega = oldc.worm_omega;
         sim->c.worm_period = oldc.worm_period;
+        sim->c.worm_turns = oldc.worm_turns;
+        sim->c.worm_unit = oldc.worm_unit;
         TITAN_CK(sim, upload_actuation(sim));
         sim->has_act = true;
         TITAN_CK(sim, entries_grew(sim));
@@ -1278,6 +1412,7 @@ titan_status titan_remove_springs(titan_sim *sim, uint32_t n, const uint32_t *id
     for (uint32_t q = 0; q < n; ++q)
         if (ids[q] >= s_tot) return fail(sim, TITAN_E_INVALID, "spring id out of range: " + std::to_string(ids[q]));
     DeviceGuard dg(sim->device);
+    TITAN_CK(sim, fetch_act_host(sim));
     std::vector<uint32_t> live;
     for (uint32_t q = 0; q < n; ++q) {
         const uint32_t id = ids[q];
@@ -1390,6 +1525,7 @@ titan_status titan_set_worm_actuation(titan_sim *sim, uint32_t n, const uint32_t
             if (!std::isfinite(c[q]) || !std::isfinite(t_offset[q])) return fail(sim, TITAN_E_INVALID, "non-finite c or t_offset");
         }
         DeviceGuard dg(sim->device);
+        TITAN_CK(sim, fetch_act_host(sim));
         if (sim->act_amp.empty() || sim->act_mode != 2) {
             sim->act_amp.assign(sim->s, 0.f);
             sim->act_phase.assign(sim->s, 0.f);
@@ -1400,8 +1536,7 @@ titan_status titan_set_worm_actuation(titan_sim *sim, uint32_t n, const uint32_t
             sim->act_phase[ids[q]] = (float)(to - (double)period * std::floor(to / (double)period));   // in [0, t_p)
         }
         sim->c.act_mode = 2;
-        sim->c.worm_omega = omega;
-        sim->c.worm_period = period;
+        titan::set_worm_clock(sim->c, (double)omega, (double)period);
         sim->act_mode = 2;
         TITAN_CK(sim, upload_actuation(sim));
         sim->has_act = true;

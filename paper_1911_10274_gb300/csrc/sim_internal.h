@@ -112,6 +112,15 @@ struct SimCore {
     bool dirty = false;                   // masses or springs were added: rebuild before next use
     std::vector<double> pend_pos, pend_vel;   // initial state of masses added since the last rebuild
     int act_mode = 0;                     // 0 none, 1 sinusoid, 2 worm (Eqs. 3-4)
+    // actuation set from device arrays (titan_set_actuation_dev): the
+    // caller-order values stay on the device, and act_amp / act_phase follow
+    // them only when host code needs them (act_host_stale until then)
+    float *d_act_amp = nullptr, *d_act_phase = nullptr;
+    bool act_host_stale = false;
+    uint32_t *d_entry_spring = nullptr;   // spring of each SELL entry (UINT32_MAX: padding)
+    uint32_t *d_cube_spring = nullptr;    // spring of each cube-stream entry
+    uint32_t *d_rec_spring = nullptr;     // spring of each record (atomic path)
+    int *d_check = nullptr;               // non-finite count of the last device-array argument check
 };
 
 struct titan_sim : SimCore {

@@ -23,6 +23,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include <vector>
@@ -55,11 +56,38 @@ struct StepConst {
     float c_uniform;      // dashpot when there is no per-spring damping array
     int32_t ground;
     double act_omega;     // 2 pi f (rad/s) of the sinusoidal actuation
-    double dt_d;          // dt in FP64 for the phase of the actuation clock
+    double dt_d;          // dt in FP64
     int32_t act_mode;     // 1: L0 (1 + A sin(2 pi f t + phi)); 2: worm, L0 (1 + c sin(w tau))
     float worm_omega;     // mode 2: w (rad/s)
     double worm_period;   // mode 2: t_p (s); per-spring offsets are stored reduced to [0, t_p)
+    // the actuation clocks as fixed-point turns per step (fractional part, in
+    // units of 2^-64): step x turns wraps modulo 2^64 exactly, so the phase
+    // of any step costs one 64-bit integer product (no FP64 on the device)
+    unsigned long long act_turns;    // mode 1: f dt
+    unsigned long long worm_turns;   // mode 2: dt / t_p
+    float worm_unit;                 // mode 2: t_p / 2^24 (s per clock unit)
 };
+
+// The fractional part of x (turns per step, x >= 0) in units of 2^-64.
+inline unsigned long long turns_fraction(double x) {
+    const double f = x - floor(x);
+    const double q = ldexp(f, 64);
+    return q >= 18446744073709549568.0 ? 0xFFFFFFFFFFFFF800ull : (unsigned long long)q;
+}
+
+// Sets the sinusoidal clock (mode 1) of c for frequency freq_hz.
+inline void set_act_clock(StepConst &c, double freq_hz) {
+    c.act_omega = 2.0 * 3.14159265358979323846 * freq_hz;
+    c.act_turns = turns_fraction(freq_hz * c.dt_d);
+}
+
+// Sets the worm clock (mode 2) of c: w and t_p.
+inline void set_worm_clock(StepConst &c, double omega, double period) {
+    c.worm_omega = (float)omega;
+    c.worm_period = period;
+    c.worm_turns = turns_fraction(c.dt_d / period);
+    c.worm_unit = (float)(period / 16777216.0);
+}
 
 struct SellView {
     const uint32_t *slice_off;   // [n_slices + 1] entry offsets

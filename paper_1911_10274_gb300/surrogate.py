@@ -83,6 +83,22 @@ def mirrored(morphs: List[Morph], y: np.ndarray):
     return out_m, np.array(out_y)
 
 
+def mirrored_encoded(X: np.ndarray, y: np.ndarray):
+    """encode(mirrored(morphs, y)) from encode(morphs): the same four
+    reflections, rows in the same order (for each robot: as is, y -> -y,
+    x -> -x, both), formed on the encoded grids instead of re-encoding."""
+    n = len(X)
+    V = X.reshape(n, 2, GRID, GRID, GRID)          # (occupancy, phase) blocks, (z, y, x)
+    out = np.empty((n, 4) + V.shape[1:], X.dtype)
+    out[:, 0] = V
+    out[:, 1] = V[:, :, :, ::-1, :]
+    out[:, 2] = V[:, :, :, :, ::-1]
+    out[:, 3] = V[:, :, :, ::-1, ::-1]
+    yy = np.repeat(np.asarray(y, np.float64), 4).reshape(n, 4)
+    yy[:, 2:] *= -1.0
+    return out.reshape(4 * n, X.shape[1]), yy.ravel()
+
+
 def fitness(morphs: List[Morph], steps: int, freq: float = 2.0, chunk: int = 4096,
             device: int = 0) -> np.ndarray:
     """Centroid x-displacement of each robot after `steps` steps (simulated)."""
@@ -128,6 +144,9 @@ class Surrogate:
         self.mu, self.sd = 0.0, 1.0
 
     def _x(self, X):
+        """BF16 features on the device (a tensor already there is taken as is)."""
+        if isinstance(X, self.torch.Tensor):
+            return X
         return self.torch.as_tensor(X, dtype=self.torch.float32, device=f"cuda:{self.device}").bfloat16()
 
     def fit(self, X: np.ndarray, y: np.ndarray, epochs: int = 20, batch: int = 4096, lr: float = 1e-3,
@@ -208,9 +227,11 @@ class Ensemble:
 
     def refine(self, X: np.ndarray, y: np.ndarray, epochs: int = 3, batch: int = 1024, lr: float = 5e-4,
                seed: int = 0) -> None:
+        Xd = self.members[0]._x(X)               # uploaded once, each member's resample taken on the device
         for k, m in enumerate(self.members):
             idx = self._boot(len(X), k, 7919 + seed)
-            m.refine(X[idx], y[idx], epochs=epochs, batch=batch, lr=lr, seed=seed + k)
+            sel = m.torch.as_tensor(idx, device=Xd.device)
+            m.refine(Xd[sel], y[idx], epochs=epochs, batch=batch, lr=lr, seed=seed + k)
 
     def predict_stats(self, X: np.ndarray):
         P = np.stack([m.predict(X) for m in self.members])
@@ -253,7 +274,7 @@ def search(mode: str, start: List[Morph], start_fit: np.ndarray, generations: in
     pop = [start[i] for i in order]
     pop_fit = start_fit[order].copy()
     best, used, hist = float(pop_fit[0]), 0, []
-    seen_m, seen_f = [], np.zeros(0)
+    seen_X, seen_y = np.zeros((0, N_FEATURES), np.float32), np.zeros(0)   # encoded, mirrored
     gains = []
     for g in range(generations):
         if target is not None and best >= target:
@@ -273,12 +294,13 @@ def search(mode: str, start: List[Morph], start_fit: np.ndarray, generations: in
         used += len(chosen)
         gains.append(float(f.mean() - pop_fit.mean()))
         if mode == "surrogate":
-            seen_m = seen_m + chosen
-            seen_f = np.concatenate([seen_f, f])
+            # each simulated mutant is encoded (and mirrored) once, when simulated
+            Xn, yn = mirrored_encoded(encode(chosen), f)
+            seen_X = np.concatenate([seen_X, Xn])
+            seen_y = np.concatenate([seen_y, yn])
             if refine_window > 0:
-                seen_m, seen_f = seen_m[-refine_window:], seen_f[-refine_window:]
-            am, af = mirrored(seen_m, seen_f)
-            surrogate.refine(encode(am), af, epochs=refine_epochs, batch=512, seed=g)
+                seen_X, seen_y = seen_X[-4 * refine_window:], seen_y[-4 * refine_window:]
+            surrogate.refine(seen_X, seen_y, epochs=refine_epochs, batch=512, seed=g)
         allm = pop + chosen
         allf = np.concatenate([pop_fit, f])
         keep = np.argsort(-allf)[:parents]

@@ -77,6 +77,7 @@ def load(path: Optional[str] = None):
                 "titan_snapshot_wait": (S, [_P, u64, C.POINTER(C.POINTER(f32)),
                                             C.POINTER(C.POINTER(f32)), C.POINTER(C.c_double)]),
                 "titan_set_actuation": (S, [_P, u32, _P, _P, _P, f32]),
+                "titan_set_actuation_dev": (S, [_P, u32, _P, _P, f32]),
                 "titan_set_state": (S, [_P, _P, _P]),
                 "titan_read_state_dev": (S, [_P, _P, _P, _P]),
                 "titan_sync": (S, [_P]),
@@ -97,6 +98,7 @@ def load(path: Optional[str] = None):
                 "titan_set_fixed": (S, [_P, u32, _P, _P]),
                 "titan_adjoint": (S, [_P, u64, u32, _P, _P, _P, _P]),
                 "titan_gemm_bf16_tn": (S, [u32, u32, u32, _P, _P, _P, _P]),
+                "titan_gemm_check": (S, []),
                 "titan_mlp_create": (S, [u32, u32, u64, C.c_int32, _P, C.POINTER(_P)]),
                 "titan_mlp_param_count": (u64, [_P]),
                 "titan_mlp_get_params": (S, [_P, _P]),
@@ -186,6 +188,22 @@ def titan_set_actuation(sim: int, spring_ids, amp, phase, freq_hz: float) -> Non
     if not (ids.shape == a.shape == ph.shape):
         raise ValueError("spring_ids, amp and phase must have the same length")
     _check(load().titan_set_actuation(sim, ids.size, _ptr(ids), _ptr(a), _ptr(ph), float(freq_hz)), sim)
+
+
+def titan_set_actuation_dev(sim: int, amp_dev, phase_dev, freq_hz: float) -> None:
+    """Every spring's (amp, phase) from 1-D contiguous CUDA float32 tensors
+    of n_springs entries each (caller order), copied on the simulation's
+    stream; the library checks the length against its spring count."""
+    import torch
+    for name, t in (("amp_dev", amp_dev), ("phase_dev", phase_dev)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32:
+            raise TypeError(f"titan_set_actuation_dev: {name} must be a CUDA float32 tensor")
+        if t.dim() != 1 or not t.is_contiguous():
+            raise ValueError(f"titan_set_actuation_dev: {name} must be 1-D and contiguous")
+    if amp_dev.numel() != phase_dev.numel():
+        raise ValueError("titan_set_actuation_dev: amp_dev and phase_dev must have the same length")
+    _check(load().titan_set_actuation_dev(sim, amp_dev.numel(), _ptr(amp_dev), _ptr(phase_dev), float(freq_hz)),
+           sim)
 
 
 def titan_set_state(sim: int, pos, vel=None) -> None:
@@ -590,7 +608,7 @@ class CentroidRollout:
     of per-robot displacements; gradients flow back through the library's
     adjoint (titan_adjoint) with checkpoints every ``every`` steps."""
 
-    def __init__(self, robots, n_steps: int, every: int = 50, device: int = 0):
+    def __init__(self, robots, n_steps: int, every: int = 50, device: int = 0, order: int = ORDER_MORTON):
         import torch
         self.system, self.mass_off, self.spring_off = union_system(robots)
         self.n_steps, self.every = int(n_steps), int(every)
@@ -599,18 +617,32 @@ class CentroidRollout:
         self.counts = np.diff(self.mass_off).astype(np.float64)
         self.freq = float(self.system.act_freq)
         self.device = device
-        self.sim = Sim(self.system, device=device)
+        self.sim = Sim(self.system, device=device, order=order)
         self.pos0 = np.ascontiguousarray(self.system.pos)
         self.vel0 = np.ascontiguousarray(self.system.vel)
         self.x0 = np.array([self.pos0[self.mass_off[r]:self.mass_off[r + 1], 0].mean()
                             for r in range(self.n_robots)])
         self._fn = None
+        self._dev = None
         self._torch = torch
+
+    def _dev_tables(self):
+        """Robot of each mass, masses per robot and initial centroid x, kept
+        on the device after the first use."""
+        if self._dev is None:
+            T_ = self._torch
+            dev = T_.device("cuda", self.device)
+            self._dev = (T_.as_tensor(self.robot_of_mass, device=dev), T_.as_tensor(self.counts, device=dev),
+                         T_.as_tensor(self.x0, device=dev))
+        return self._dev
 
     def _prepare(self, amp, phase):
         T_ = self._torch
-        titan_set_actuation(self.sim.handle, np.arange(self.system.n_springs, dtype=np.uint32),
-                            amp.detach().float().cpu().numpy(), phase.detach().float().cpu().numpy(), self.freq)
+        dev = T_.device("cuda", self.device)
+        a = amp.detach().to(dev, T_.float32).contiguous()
+        p = phase.detach().to(dev, T_.float32).contiguous()
+        T_.cuda.current_stream(dev).synchronize()      # the library reads them on its own stream
+        titan_set_actuation_dev(self.sim.handle, a, p, self.freq)
         titan_set_step(self.sim.handle, 0)
         self.sim.set_state(self.pos0, self.vel0)
 
@@ -621,21 +653,21 @@ class CentroidRollout:
         pos = T_.empty((self.system.n_masses, 3), dtype=T_.float32, device=f"cuda:{self.device}")
         titan_read_state_dev(self.sim.handle, pos, None, None)
         self.sim.sync()
-        idx = T_.as_tensor(self.robot_of_mass, device=pos.device)
+        idx, cnt, x0 = self._dev_tables()
         sums = T_.zeros(self.n_robots, dtype=T_.float64, device=pos.device).index_add_(0, idx, pos[:, 0].double())
-        cnt = T_.as_tensor(self.counts, device=pos.device)
-        return (sums / cnt - T_.as_tensor(self.x0, device=pos.device)).float()
+        return (sums / cnt - x0).float()
 
     def gradients(self, amp, phase, grad_out):
         """dJ/dA and dJ/dphi for the objective sum_r grad_out[r] * J_r."""
         T_ = self._torch
         self._prepare(amp, phase)
         dev = f"cuda:{self.device}"
-        w = (grad_out.detach().double().cpu().numpy() / self.counts)[self.robot_of_mass]
+        idx, cnt, _ = self._dev_tables()
         seed = T_.zeros((self.system.n_masses, 3), dtype=T_.float32, device=dev)
-        seed[:, 0] = T_.as_tensor(w, dtype=T_.float32, device=dev)
+        seed[:, 0] = (grad_out.detach().to(dev).double() / cnt)[idx].float()
         ga = T_.empty(self.system.n_springs, dtype=T_.float32, device=dev)
         gp = T_.empty_like(ga)
+        T_.cuda.current_stream(dev).synchronize()      # seed is written on torch's stream
         titan_adjoint(self.sim.handle, self.n_steps, self.every, seed, None, ga, gp)
         self.sim.sync()
         return ga, gp
@@ -664,10 +696,20 @@ class CentroidRollout:
 # --------------------------------------------------------------------------- tensor-core surrogate MLP
 
 def titan_gemm_bf16_tn(A, B, C, stream: Optional[int] = None) -> None:
-    """C = A B^T on the tcgen05 tensor cores (A, B: CUDA bfloat16 tensors [M, K], [N, K]; C: float32 [M, N])."""
+    """C = A B^T on the tcgen05 tensor cores (A, B: CUDA bfloat16 tensors [M, K], [N, K]; C: float32 [M, N]),
+    enqueued on `stream` (default: torch's current stream of A's device); returns without waiting."""
     M, K = A.shape
     N = B.shape[0]
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream(A.device).cuda_stream
     _check_mlp(load().titan_gemm_bf16_tn(M, N, K, _ptr(A), _ptr(B), _ptr(C), stream))
+
+
+def titan_gemm_check() -> None:
+    """Raises TitanError (TITAN_E_TIMEOUT) if a GEMM kernel on the current
+    device gave up on a bounded wait since the last check."""
+    _check_mlp(load().titan_gemm_check())
 
 
 def _check_mlp(status: int, m=None):

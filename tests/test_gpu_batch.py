@@ -52,10 +52,12 @@ def test_batch_second_rollout_continues_the_actuation_clock():
             assert np.abs(xg - xo).max() <= POS_TOL_FRAC * sy.spacing
 
 
-@pytest.mark.parametrize("threads,tpm", [(128, 1), (512, 1), (128, 2), (256, 2), (512, 4), (64, 4)])
+@pytest.mark.parametrize("threads,tpm", [(128, 1), (512, 1), (128, 2), (256, 2), (512, 4), (64, 4), (1024, 1),
+                                         (1024, 8), (256, 8)])
 def test_every_launch_shape_matches_oracle(threads, tpm):
-    """Every shape the autotuner can pick (threads per CTA, threads per mass),
-    pinned by hand, against the oracle."""
+    """Every shape the autotuner can pick (threads per CTA, most threads per
+    mass; each CTA takes the most that fit its masses), pinned by hand,
+    against the oracle."""
     robots = _robots()
     with T.Batch(robots) as b:
         for g in range(len(b.groups())):
@@ -68,7 +70,8 @@ def test_batch_autotune_and_reset_keep_results():
     robots = _robots()[:4]
     with T.Batch(robots) as b:
         b.autotune(20)
-        assert all(x["threads"] in (128, 256, 512) and x["threads_per_mass"] in (1, 2, 4) for x in b.groups())
+        assert all(x["threads"] in (128, 256, 512, 1024) and x["threads_per_mass"] in (1, 2, 4, 8)
+                   for x in b.groups())
         b.rollout(400)
         a = [b.read(r)[0] for r in range(len(robots))]
         b.reset()

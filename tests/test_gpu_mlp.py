@@ -28,6 +28,27 @@ def test_tcgen05_gemm_matches_reference(M, N, K):
     ref_c = A.double() @ B.double().T
     err = (C.double() - ref_c).abs().max().item()
     assert err <= 1e-4 * ref_c.abs().max().item(), err
+    torch.cuda.synchronize()
+    T.titan_gemm_check()
+
+
+def test_gemm_calls_enqueue_without_waiting_and_follow_stream_order():
+    """Eight products enqueued back to back on a side stream, each output
+    then consumed on that stream: stream order alone orders them."""
+    g = torch.Generator(device="cuda").manual_seed(9)
+    s = torch.cuda.Stream()
+    As = [torch.randn(256, 512, device="cuda", generator=g).bfloat16() for _ in range(8)]
+    B = torch.randn(384, 512, device="cuda", generator=g).bfloat16()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        Cs = [torch.empty(256, 384, device="cuda") for _ in range(8)]
+        for A, C in zip(As, Cs):
+            T.titan_gemm_bf16_tn(A, B, C)                # torch's current stream: s
+        tot = sum(C.double() for C in Cs)
+    s.synchronize()
+    T.titan_gemm_check()
+    ref = sum(A.double() @ B.double().T for A in As)
+    assert (tot - ref).abs().max().item() <= 1e-4 * ref.abs().max().item()
 
 
 def test_gemm_rejects_unaligned_shapes():
@@ -43,7 +64,9 @@ def _bf16_round(a):
     return torch.as_tensor(a, dtype=torch.float32).bfloat16().float().numpy().astype(np.float64)
 
 
-@pytest.mark.parametrize("n_in,hidden,B", [(128, 128, 128), (1024, 512, 512)])
+# B = 4096 cuts the weight-gradient products into 4 (first layer) and 8 (hidden
+# layers) K slices; B = 512 into 2; B = 128 not at all
+@pytest.mark.parametrize("n_in,hidden,B", [(128, 128, 128), (1024, 512, 512), (1024, 512, 4096)])
 def test_mlp_forward_and_gradient_match_fp64_reference(n_in, hidden, B):
     net = T.MLP(n_in, hidden, seed=3)
     rng = np.random.default_rng(1)
@@ -92,3 +115,36 @@ def test_mlp_training_reduces_the_loss_on_a_learnable_target():
         net.train_step(x, tt, 1e-3, loss)
     net.sync()
     assert float(loss) < 0.2 * first
+
+
+def test_train_step_is_adam_on_the_gradient_with_the_device_step_count():
+    """Three training steps (the first two at one learning rate, the third at
+    another) against Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected)
+    written out in FP64 on the gradients the network reports at each step's
+    parameters: checks the step counter and learning rate the captured step
+    reads from device memory."""
+    n_in, hidden, B = 256, 128, 1024
+    net = T.MLP(n_in, hidden, seed=11)
+    rng = np.random.default_rng(2)
+    x = torch.as_tensor(rng.normal(0, 1, (B, n_in)), dtype=torch.float32).bfloat16().cuda()
+    t = torch.as_tensor(rng.normal(0, 0.3, B), dtype=torch.float32).cuda()
+    b1, b2, eps = 0.9, 0.999, 1e-8
+    m = np.zeros(net.n_params)
+    v = np.zeros(net.n_params)
+    loss = torch.empty(1, device="cuda")
+    grad = torch.empty(net.n_params, device="cuda")
+    for step, lr in enumerate([1e-3, 1e-3, 3e-4], start=1):
+        p0 = net.get_params().astype(np.float64)
+        net.gradient(x, t, loss, grad)
+        g = grad.cpu().numpy().astype(np.float64)
+        m = b1 * m + (1 - b1) * g
+        v = b2 * v + (1 - b2) * g * g
+        want = p0 - lr * (m / (1 - b1 ** step)) / (np.sqrt(v / (1 - b2 ** step)) + eps)
+        net.train_step(x, t, lr, loss)
+        net.sync()
+        got = net.get_params().astype(np.float64)
+        # FP32 arithmetic of a step of size <= lr (a few ulp of lr), plus
+        # entries whose gradient is near zero, where eps decides the step
+        err = np.abs(got - want)
+        assert np.median(err) <= 1e-3 * lr
+        assert np.quantile(err, 0.999) <= 2e-2 * lr + 1e-6 * np.abs(p0).max()
