@@ -56,6 +56,10 @@ k_batch_rollout(const BatchCta *__restrict__ ctas, const MassState *__restrict__
                 int *__restrict__ err) {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ uint64_t bar;
+    // sin and cos of the actuation phase, one pair per step parity: thread 0
+    // forms step k + 1's pair during step k (the end-of-step barrier publishes
+    // it; the slot it overwrites was last read before the previous barrier)
+    __shared__ float2 s_sc[2];
     const BatchCta d = ctas[blockIdx.x];
     const BatchSmem L = batch_smem_layout(d.slot_count, d.halo_slots, d.n_slices, d.edge_count, ACT);
     float4 *const a0s = reinterpret_cast<float4 *>(sm + L.a0), *const a1s = reinterpret_cast<float4 *>(sm + L.a1);
@@ -67,6 +71,11 @@ k_batch_rollout(const BatchCta *__restrict__ ctas, const MassState *__restrict__
     const uint16_t *s_nbr = reinterpret_cast<const uint16_t *>(sm + L.nbr);
     const uint32_t tid = threadIdx.x;
 
+    if (ACT && tid == 0) {
+        float sp, cp;
+        sincosf(titan::clock_phase(c, step0), &sp, &cp);
+        s_sc[0] = make_float2(sp, cp);
+    }
     if (tid == 0) {
         const uint32_t slice_bytes = 4 * ((d.n_slices + 1 + 3) & ~3u);
         const uint32_t bytes = slice_bytes + d.edge_count * (ACT ? 18 : 10);
@@ -112,7 +121,16 @@ k_batch_rollout(const BatchCta *__restrict__ ctas, const MassState *__restrict__
     int cur = 0;
     for (uint32_t k = 0; k < n_steps; ++k) {
         float sp = 0.f, cp = 1.f;
-        if (ACT) sincosf(titan::clock_phase(c, step0 + (long long)k), &sp, &cp);
+        if (ACT) {
+            const float2 sc = s_sc[k & 1];
+            sp = sc.x;
+            cp = sc.y;
+            if (tid == 0) {
+                float sn, cs;
+                sincosf(titan::clock_phase(c, step0 + (long long)k + 1), &sn, &cs);
+                s_sc[(k + 1) & 1] = make_float2(sn, cs);
+            }
+        }
         float4 *srcA = cur ? a1s : a0s;
         float2 *srcB = cur ? b1s : b0s;
         float4 *dstA = cur ? a0s : a1s;
@@ -249,6 +267,8 @@ struct titan_batch {
     uint64_t steps = 0;
     uint32_t spin_limit = 1u << 22;
     std::vector<uint32_t> mass_off, mass_cnt;   // per robot, into the global mass slots
+    std::vector<uint32_t> slot_of_mass;          // per robot's caller index (from caller_off): its slot - mass_off
+    std::vector<size_t> caller_off;              // per robot, into slot_of_mass
     std::vector<float> init_state;               // caller-provided initial state, [slots][8] (x y z 1/m vx vy vz 0)
     std::vector<Group> groups;
     std::vector<uint32_t> group_of;              // per system: the launch group holding its cluster
@@ -445,6 +465,14 @@ titan_status titan_batch_create(uint32_t n_systems, const titan_masses *masses, 
         return bail(bfail(b, TITAN_E_UNSUPPORTED, why));
     b->mass_off = L.mass_off;
     b->mass_cnt = L.mass_cnt;
+    b->caller_off.assign(n_systems + 1, 0);
+    for (uint32_t r = 0; r < n_systems; ++r) b->caller_off[r + 1] = b->caller_off[r] + L.mass_cnt[r];
+    b->slot_of_mass.assign(b->caller_off[n_systems], 0);
+    for (uint32_t r = 0; r < n_systems; ++r)
+        for (uint32_t k = 0; k < L.mass_cnt[r]; ++k) {
+            const uint32_t i = L.mass_of_slot[L.mass_off[r] + k];    // real masses fill the first n slots
+            b->slot_of_mass[b->caller_off[r] + i] = k;
+        }
     b->init_state = std::move(L.init_state);
     b->total_slots = L.total_slots;
     b->group_of.assign(n_systems, UINT32_MAX);
@@ -571,9 +599,11 @@ titan_status titan_batch_read(titan_batch *b, uint32_t system, float *pos, float
     std::vector<MassState> h(n);
     BATCH_CK(b, cudaMemcpy(h.data(), b->d_state[b->cur] + b->mass_off[system], n * sizeof(MassState),
                            cudaMemcpyDeviceToHost));
+    const uint32_t *slot = b->slot_of_mass.data() + b->caller_off[system];
     for (uint32_t i = 0; i < n; ++i) {
-        if (pos) { pos[3 * i] = h[i].p.x; pos[3 * i + 1] = h[i].p.y; pos[3 * i + 2] = h[i].p.z; }
-        if (vel) { vel[3 * i] = h[i].v.x; vel[3 * i + 1] = h[i].v.y; vel[3 * i + 2] = h[i].v.z; }
+        const MassState &x = h[slot[i]];
+        if (pos) { pos[3 * i] = x.p.x; pos[3 * i + 1] = x.p.y; pos[3 * i + 2] = x.p.z; }
+        if (vel) { vel[3 * i] = x.v.x; vel[3 * i + 1] = x.v.y; vel[3 * i + 2] = x.v.z; }
     }
     return TITAN_OK;
 }

@@ -745,11 +745,10 @@ bool build_batch(uint32_t n_systems, const titan_masses *masses, const titan_spr
             size_t worst = 0;
             for (uint32_t q0 = 0; q0 < m.n; q0 += per) {
                 uint32_t edges = 0, ns = 0;
-                for (uint32_t sl = q0; sl < std::min(m.n, q0 + per); sl += 32, ++ns) {
-                    uint32_t w = 0;
-                    for (uint32_t i = sl; i < std::min(m.n, sl + 32); ++i) w = std::max(w, deg[i]);
-                    edges += 32 * ((w + 1) & ~1u);
-                }
+                std::vector<uint32_t> dq(deg.begin() + q0, deg.begin() + std::min(m.n, q0 + per));
+                std::sort(dq.begin(), dq.end(), std::greater<uint32_t>());
+                for (uint32_t sl = 0; sl < (uint32_t)dq.size(); sl += 32, ++ns)
+                    edges += 32 * ((dq[sl] + 1) & ~1u);      // a slice's widest row is its first
                 edges = (edges + 63) & ~63u;
                 worst = std::max<size_t>(worst, batch_smem_layout(per, hc, ns, edges, any_act).total);
             }
@@ -759,34 +758,50 @@ bool build_batch(uint32_t n_systems, const titan_masses *masses, const titan_spr
         const uint32_t per = ((m.n + C - 1) / C + 31) & ~31u;
         out.mass_off.push_back(slot_cursor);
         out.mass_cnt.push_back(m.n);
+        // each CTA's masses by decreasing degree (ties in caller order):
+        // mass_at[q * per + p] is the mass in slot p of CTA q, pos_of[j] the slot of mass j in its CTA
+        std::vector<uint32_t> mass_at((size_t)C * per, UINT32_MAX), pos_of(m.n);
+        for (uint32_t q = 0; q < C; ++q) {
+            const uint32_t a0 = std::min(m.n, q * per), a1 = std::min(m.n, a0 + per);
+            std::vector<uint32_t> perm(a1 - a0);
+            std::iota(perm.begin(), perm.end(), a0);
+            std::stable_sort(perm.begin(), perm.end(), [&](uint32_t x, uint32_t y) { return deg[x] > deg[y]; });
+            for (uint32_t p = 0; p < (uint32_t)perm.size(); ++p) {
+                mass_at[(size_t)q * per + p] = perm[p];
+                pos_of[perm[p]] = p;
+            }
+        }
         for (uint32_t q = 0; q < C; ++q) {
             CtaHost h;
             const uint32_t m0 = std::min(m.n, q * per), m1 = std::min(m.n, m0 + per);
             h.d = BatchCta{slot_cursor + m0, m1 - m0, per, 0, 0, 0, 0, r, 0, 0, 0};
-            // neighbours as own slots (j - m0) or halo slots (per + h)
+            // neighbours as own slots (pos_of[j]) or halo slots (per + h)
             std::fill(mark.begin(), mark.end(), UINT32_MAX);      // here: halo slot of a mass
             auto slot_of = [&](uint32_t j) -> uint16_t {
-                if (j >= m0 && j < m1) return (uint16_t)(j - m0);
+                if (j >= m0 && j < m1) return (uint16_t)pos_of[j];
                 if (mark[j] == UINT32_MAX) {
                     mark[j] = per + (uint32_t)h.halo.size();
-                    h.halo.push_back(((j / per) << 16) | (j % per));
+                    h.halo.push_back(((j / per) << 16) | pos_of[j]);
                 }
                 return (uint16_t)mark[j];
             };
+            const uint32_t *at = mass_at.data() + (size_t)q * per;
+            const uint32_t count = m1 - m0;
             h.slices.push_back(0);
-            for (uint32_t sl = m0; sl < m0 + per; sl += 32) {
+            for (uint32_t sl = 0; sl < per; sl += 32) {
                 uint32_t w = 0;
-                for (uint32_t i = sl; i < std::min(m1, sl + 32); ++i) w = std::max(w, deg[i]);
+                for (uint32_t p = sl; p < std::min(count, sl + 32); ++p) w = std::max(w, deg[at[p]]);
                 w = (w + 1) & ~1u;
                 const uint32_t base = (uint32_t)h.nbr.size();
                 h.kl.resize(2 * (size_t)(base + 32 * w), 0.f);
                 h.act.resize(2 * (size_t)(base + 32 * w), 0.f);
                 h.nbr.resize(base + 32 * w, 0);
                 for (uint32_t l = 0; l < 32; ++l) {
-                    const uint32_t i = sl + l;
+                    const uint32_t p = sl + l;                          // slot of this row
+                    const uint32_t i = p < count ? at[p] : UINT32_MAX;   // its mass (none: padding slot)
                     for (uint32_t t = 0; t < w; ++t) {
                         const uint32_t e = base + 32 * t + l;
-                        if (i < m1 && t < deg[i]) {
+                        if (p < count && t < deg[i]) {
                             const auto &x = he[rowptr[i] + t];
                             const uint32_t j = x.first, q2 = x.second;
                             h.nbr[e] = slot_of(j);
@@ -807,8 +822,7 @@ bool build_batch(uint32_t n_systems, const titan_masses *masses, const titan_spr
                                 h.act[2 * (size_t)e + 1] = (float)(act[r].amp[q2] * std::sin(act[r].phase[q2]));
                             }
                         } else {
-                            const uint32_t self = std::min(i, m.n - 1);   // zero-parameter padding
-                            h.nbr[e] = slot_of(self);
+                            h.nbr[e] = (uint16_t)p;          // zero-parameter padding: the row's own slot
                         }
                     }
                 }
@@ -829,8 +843,11 @@ bool build_batch(uint32_t n_systems, const titan_masses *masses, const titan_spr
         slot_cursor += C * per;
         // initial state of every slot of this system (padding slots: fixed, at rest)
         out.init_state.resize(8 * (size_t)slot_cursor, 0.f);
+        out.mass_of_slot.resize(slot_cursor, UINT32_MAX);
+        for (size_t sl = 0; sl < mass_at.size(); ++sl) out.mass_of_slot[out.mass_off[r] + sl] = mass_at[sl];
         for (uint32_t k = 0; k < m.n; ++k) {
-            float *st = &out.init_state[8 * (size_t)(out.mass_off[r] + k)];
+            const uint32_t q = k / per;
+            float *st = &out.init_state[8 * (size_t)(out.mass_off[r] + (size_t)q * per + pos_of[k])];
             for (int a = 0; a < 3; ++a) {
                 st[a] = (float)m.pos[3 * (size_t)k + a];
                 st[4 + a] = m.vel ? (float)m.vel[3 * (size_t)k + a] : 0.f;

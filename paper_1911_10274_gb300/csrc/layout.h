@@ -279,6 +279,9 @@ struct BatchHost {
     std::vector<uint32_t> mass_off;      // [systems] first global state slot
     std::vector<uint32_t> mass_cnt;      // [systems] masses
     std::vector<float> init_state;       // [slots][8] x, y, z, 1/m, vx, vy, vz, 0 (FP32 of the caller's values)
+    std::vector<uint32_t> mass_of_slot;  // [slots] caller index (within its system) of the mass in each slot,
+                                         // UINT32_MAX for padding: each CTA holds its masses by decreasing
+                                         // degree, so that its SELL slices hold rows of similar length
     uint32_t total_slots = 0;
     bool any_act = false;
 };

@@ -46,7 +46,10 @@ namespace {
 // products: each A tile then feeds twice the columns, halving the A traffic
 // from L2 per FLOP).
 constexpr int BM = 128, BN = 128, BK = 64, STAGES = 4;
-constexpr int kGemmThreads = 128;
+// 8 warps: warps 0 and 1 issue the loads and the products; after the
+// mainloop all 8 run the epilogue, warp w on TMEM lanes 32 (w mod 4) ..
+// + 31 (the lanes its quarter may read) and on half w / 4 of the columns
+constexpr int kGemmThreads = 256;
 constexpr uint32_t kStageA = BM * BK * 2;
 template <int BN_> constexpr uint32_t stage_b() { return (uint32_t)BN_ * BK * 2; }
 template <int BN_> constexpr size_t gemm_smem() { return (size_t)STAGES * (kStageA + stage_b<BN_>()) + 1024; }
@@ -62,6 +65,7 @@ struct EpiArgs {
     const float *z;               // [M, ldc]       (GELU_GRAD: the forward pre-activation)
     __nv_bfloat16 *out_t = nullptr;   // [N, ldt] the transpose of out_bf16, if given (BIAS_GELU, GELU_GRAD)
     int ldt = 0;
+    float *colsum = nullptr;          // [M / 32, ldc] GELU_GRAD: per 32 rows, the column sums of out_bf16
 };
 
 __device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
@@ -170,40 +174,63 @@ k_gemm_tn(const __grid_constant__ CUtensorMap tma_a, const __grid_constant__ CUt
         }
         __syncthreads();
     } else {
-        const int row = m0 + warp * 32 + lane;
-        for (int c0 = 0; c0 < BN_; c0 += 32) {
+        // The accumulator comes out of TMEM one row per lane.  Each 32 x 32
+        // block goes through this warp's scratch in the (now idle) stage
+        // buffers so that global reads and writes run along rows (lane =
+        // column, 128-byte lines), and the transposed copy, if any, along
+        // its columns (lane = row).
+        float *scr = reinterpret_cast<float *>(gsm) + warp * (32 * 33);
+        const int quarter = (int)(warp & 3), half = (int)(warp >> 2);
+        const int row0 = m0 + quarter * 32;
+        const size_t zoff = (size_t)blockIdx.z * gridDim.y * BM * ep.ldc;   // split-K slice (EPI_F32)
+        for (int c0 = half * (BN_ / 2); c0 < (half + 1) * (BN_ / 2); c0 += 32) {
             float v[32];
-            titan::ptx::tmem_ld32(taddr + ((warp * 32u) << 16) + (uint32_t)c0, v);
-            const int col = n0 + c0;
-            const size_t off = (size_t)row * ep.ldc + col + (size_t)blockIdx.z * gridDim.y * BM * ep.ldc;
+            titan::ptx::tmem_ld32(taddr + (((uint32_t)quarter * 32u) << 16) + (uint32_t)c0, v);
+#pragma unroll
+            for (int k = 0; k < 32; ++k) scr[lane * 33 + k] = v[k];
+            __syncwarp();
+            const int col = n0 + c0 + lane;
             if (ep.mode == EPI_F32) {
-#pragma unroll
-                for (int k = 0; k < 32; k += 4)
-                    *reinterpret_cast<float4 *>(ep.out_f32 + off + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
-            } else if (ep.mode == EPI_BIAS_GELU) {
-#pragma unroll
-                for (int k = 0; k < 32; k += 2) {
-                    const float z0 = v[k] + ep.bias[col + k], z1 = v[k + 1] + ep.bias[col + k + 1];
-                    *reinterpret_cast<float2 *>(ep.out_f32 + off + k) = make_float2(z0, z1);
-                    const __nv_bfloat162 h = __floats2bfloat162_rn(gelu(z0), gelu(z1));
-                    *reinterpret_cast<__nv_bfloat162 *>(ep.out_bf16 + off + k) = h;
-                    if (ep.out_t) {       // the 32 lanes write 32 consecutive rows of one column
-                        ep.out_t[(size_t)(col + k) * ep.ldt + row] = h.x;
-                        ep.out_t[(size_t)(col + k + 1) * ep.ldt + row] = h.y;
-                    }
-                }
+#pragma unroll 8
+                for (int r = 0; r < 32; ++r) ep.out_f32[zoff + (size_t)(row0 + r) * ep.ldc + col] = scr[r * 33 + lane];
             } else {
-#pragma unroll
-                for (int k = 0; k < 32; k += 2) {
-                    const float2 z = *reinterpret_cast<const float2 *>(ep.z + off + k);
-                    const __nv_bfloat162 d = __floats2bfloat162_rn(v[k] * gelu_grad(z.x), v[k + 1] * gelu_grad(z.y));
-                    *reinterpret_cast<__nv_bfloat162 *>(ep.out_bf16 + off + k) = d;
-                    if (ep.out_t) {
-                        ep.out_t[(size_t)(col + k) * ep.ldt + row] = d.x;
-                        ep.out_t[(size_t)(col + k + 1) * ep.ldt + row] = d.y;
+                if (ep.mode == EPI_BIAS_GELU) {
+                    const float b = ep.bias[col];
+#pragma unroll 8
+                    for (int r = 0; r < 32; ++r) {
+                        const size_t o = (size_t)(row0 + r) * ep.ldc + col;
+                        const float z = scr[r * 33 + lane] + b;
+                        ep.out_f32[o] = z;
+                        const __nv_bfloat16 hb = __float2bfloat16_rn(gelu(z));
+                        ep.out_bf16[o] = hb;
+                        scr[r * 33 + lane] = __bfloat162float(hb);     // exact: read back for the transpose
                     }
+                } else {
+                    // the block's 32 rows of Z requested together, then the products;
+                    // the column sums of the BF16 results (rows in order) feed the bias gradient
+                    float zr[32];
+#pragma unroll
+                    for (int r = 0; r < 32; ++r) zr[r] = ep.z[(size_t)(row0 + r) * ep.ldc + col];
+                    float cs = 0.f;
+#pragma unroll
+                    for (int r = 0; r < 32; ++r) {
+                        const size_t o = (size_t)(row0 + r) * ep.ldc + col;
+                        const __nv_bfloat16 hb = __float2bfloat16_rn(scr[r * 33 + lane] * gelu_grad(zr[r]));
+                        ep.out_bf16[o] = hb;
+                        const float hf = __bfloat162float(hb);
+                        cs += hf;
+                        scr[r * 33 + lane] = hf;                        // exact: read back for the transpose
+                    }
+                    if (ep.colsum) ep.colsum[(size_t)(row0 >> 5) * ep.ldc + col] = cs;
+                }
+                if (ep.out_t) {
+                    __syncwarp();
+#pragma unroll 8
+                    for (int k = 0; k < 32; ++k)
+                        ep.out_t[(size_t)(n0 + c0 + k) * ep.ldt + row0 + lane] = __float2bfloat16_rn(scr[lane * 33 + k]);
                 }
             }
+            __syncwarp();
         }
     }
     titan::ptx::tc_fence_before();
@@ -229,6 +256,34 @@ __global__ void k_transpose_bf16(const __nv_bfloat16 *__restrict__ in, __nv_bflo
     }
 }
 
+// out[c][r] = in[r][c] for a rows x cols BF16 matrix, both multiples of 64
+// and 16-byte aligned: 64 x 64 tiles, 16-byte global loads and stores (256
+// threads).  Tile rows are 37 words apart in shared memory, so the eight
+// input rows a warp gathers for one output vector fall in different banks.
+__global__ void __launch_bounds__(256) k_transpose64_bf16(const __nv_bfloat16 *__restrict__ in,
+                                                          __nv_bfloat16 *__restrict__ out, int rows, int cols) {
+    constexpr int kW = 37;                              // words per tile row (64 values + 5 words pad)
+    __shared__ uint32_t t[64 * kW];
+    const int c0 = blockIdx.x * 64, r0 = blockIdx.y * 64, tid = threadIdx.x;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int q = tid + 256 * h, r = q >> 3, seg = (q & 7) * 8;
+        const uint4 v = *reinterpret_cast<const uint4 *>(in + (size_t)(r0 + r) * cols + c0 + seg);
+        uint32_t *d = t + r * kW + seg / 2;
+        d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
+    }
+    __syncthreads();
+    const __nv_bfloat16 *tb = reinterpret_cast<const __nv_bfloat16 *>(t);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int q = tid + 256 * h, c = q >> 3, seg = (q & 7) * 8;   // output row c, input rows seg..seg+7
+        __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) o[k] = tb[(seg + k) * (2 * kW) + c];
+        *reinterpret_cast<uint4 *>(out + (size_t)(c0 + c) * rows + r0 + seg) = *reinterpret_cast<const uint4 *>(o);
+    }
+}
+
 __global__ void k_f32_to_bf16(const float *__restrict__ in, __nv_bfloat16 *__restrict__ out, size_t n) {
     const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (i < n) out[i] = __float2bfloat16_rn(in[i]);
@@ -245,14 +300,18 @@ __global__ void k_out_layer(const __nv_bfloat16 *__restrict__ H, const float *__
     if (lane == 0) y[row] = s + b[0];
 }
 
+constexpr int kLossThreads = 1024;
+
 // dy = 2 (y - t) / B and the mean-squared error (one block, fixed order).
 // The output bias's gradient db = sum_b dy[b] is reduced alongside, in the
 // same fixed order.
+// tick (training steps only): the device Adam step counter, advanced here.
 __global__ void k_loss(const float *__restrict__ y, const float *__restrict__ t, float *__restrict__ dy,
-                       float *__restrict__ loss, int B, float *__restrict__ db) {
-    __shared__ float part[256], pdb[256];
+                       float *__restrict__ loss, int B, float *__restrict__ db, unsigned long long *__restrict__ tick) {
+    __shared__ float part[kLossThreads], pdb[kLossThreads];
     float s = 0.f, sd = 0.f;
-    for (int i = threadIdx.x; i < B; i += 256) {
+#pragma unroll 8
+    for (int i = threadIdx.x; i < B; i += kLossThreads) {
         const float d = y[i] - t[i];
         const float g = 2.f * d / (float)B;
         dy[i] = g;
@@ -262,7 +321,7 @@ __global__ void k_loss(const float *__restrict__ y, const float *__restrict__ t,
     part[threadIdx.x] = s;
     pdb[threadIdx.x] = sd;
     __syncthreads();
-    for (int o = 128; o; o >>= 1) {
+    for (int o = kLossThreads / 2; o; o >>= 1) {
         if (threadIdx.x < o) {
             part[threadIdx.x] += part[threadIdx.x + o];
             pdb[threadIdx.x] += pdb[threadIdx.x + o];
@@ -272,6 +331,7 @@ __global__ void k_loss(const float *__restrict__ y, const float *__restrict__ t,
     if (threadIdx.x == 0) {
         if (loss) *loss = part[0] / (float)B;
         if (db) *db = pdb[0];
+        if (tick) *tick += 1;
     }
 }
 
@@ -281,50 +341,69 @@ __global__ void k_loss(const float *__restrict__ y, const float *__restrict__ t,
 constexpr int kRowChunk = 32;
 
 // Output layer backward, stage one: per (chunk, column) the partial of
-// dw[c] = sum_b dy[b] H[b, c]; and, elementwise, dZ[b, c] = dy[b] w[c] GELU'(Z[b, c]) in BF16.
+// dw[c] = sum_b dy[b] H[b, c]; elementwise dZ[b, c] = dy[b] w[c] GELU'(Z[b, c])
+// in BF16; and per (chunk, column) the partial column sum of that BF16 dZ
+// (the last hidden layer's bias gradient).
 __global__ void k_out_backward(const __nv_bfloat16 *__restrict__ H, const float *__restrict__ Z, const float *__restrict__ dy,
                                const float *__restrict__ w, float *__restrict__ part, __nv_bfloat16 *__restrict__ dZ,
-                               int B, int cols) {
+                               float *__restrict__ part_b, int B, int cols) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;
     if (c >= cols) return;
-    const int b0 = k * kRowChunk, b1 = min(B, b0 + kRowChunk);
+    const int b0 = k * kRowChunk;               // B is a multiple of 128: every chunk is whole
     const float wc = w[c];
-    float s = 0.f;
-    for (int b = b0; b < b1; ++b) {
-        const size_t o = (size_t)b * cols + c;
-        const float d = dy[b];
-        s += d * __bfloat162float(H[o]);
-        dZ[o] = __float2bfloat16_rn(d * wc * gelu_grad(Z[o]));
+    // the chunk's loads first (all in flight together), then the arithmetic
+    float hv[kRowChunk], zv[kRowChunk];
+#pragma unroll
+    for (int r = 0; r < kRowChunk; ++r) {
+        const size_t o = (size_t)(b0 + r) * cols + c;
+        hv[r] = __bfloat162float(H[o]);
+        zv[r] = Z[o];
+    }
+    float s = 0.f, sb = 0.f;
+#pragma unroll
+    for (int r = 0; r < kRowChunk; ++r) {
+        const float d = dy[b0 + r];
+        s += d * hv[r];
+        const __nv_bfloat16 g = __float2bfloat16_rn(d * wc * gelu_grad(zv[r]));
+        dZ[(size_t)(b0 + r) * cols + c] = g;
+        sb += __bfloat162float(g);
     }
     part[(size_t)k * cols + c] = s;
+    part_b[(size_t)k * cols + c] = sb;
 }
 
-// Stage one of the bias gradients: per (chunk, column) the partial column sum of a BF16 [B, cols] matrix.
-__global__ void k_col_sum_part(const __nv_bfloat16 *__restrict__ M, float *__restrict__ part, int B, int cols) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;
-    if (c >= cols) return;
-    const int b0 = k * kRowChunk, b1 = min(B, b0 + kRowChunk);
+// Stage two: out[c] = the sum over chunks of part[k][c], in a fixed order:
+// thread (c, j) of a 32 x 32 block adds chunks j, j + 32, ... in turn, then
+// the 32 partial sums of a column are added pairwise in a fixed tree.
+__global__ void __launch_bounds__(1024) k_col_sum_final(const float *__restrict__ part, int chunks, int cols,
+                                                        float *__restrict__ out) {
+    __shared__ float t[32][33];
+    const int c = blockIdx.x * 32 + threadIdx.x, j = threadIdx.y;
     float s = 0.f;
-    for (int b = b0; b < b1; ++b) s += __bfloat162float(M[(size_t)b * cols + c]);
-    part[(size_t)k * cols + c] = s;
+    if (c < cols) {
+#pragma unroll 4
+        for (int k = j; k < chunks; k += 32) s += part[(size_t)k * cols + c];
+    }
+    t[j][threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 16; o; o >>= 1) {
+        if (j < o) t[j][threadIdx.x] += t[j + o][threadIdx.x];
+        __syncthreads();
+    }
+    if (j == 0 && c < cols) out[c] = t[0][threadIdx.x];
 }
 
-// Stage two: out[c] = sum over chunks, in chunk order.
-__global__ void k_col_sum_final(const float *__restrict__ part, int chunks, int cols, float *__restrict__ out) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= cols) return;
-    float s = 0.f;
-    for (int k = 0; k < chunks; ++k) s += part[(size_t)k * cols + c];
-    out[c] = s;
-}
-
-// out[i] = sum over z of part[z][i], z in order (a split-K product's slices).
+// out[i] = sum over z of part[z][i], z in order (a split-K product's
+// slices); four entries per thread (n a multiple of 4, arrays 16-byte aligned).
 __global__ void k_sum_splits(float *__restrict__ out, const float *__restrict__ part, int splits, size_t n) {
-    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    const size_t i = 4 * (blockIdx.x * (size_t)blockDim.x + threadIdx.x);
     if (i >= n) return;
-    float s = part[i];
-    for (int z = 1; z < splits; ++z) s += part[(size_t)z * n + i];
-    out[i] = s;
+    float4 s = *reinterpret_cast<const float4 *>(part + i);
+    for (int z = 1; z < splits; ++z) {
+        const float4 q = *reinterpret_cast<const float4 *>(part + (size_t)z * n + i);
+        s.x += q.x; s.y += q.y; s.z += q.z; s.w += q.w;
+    }
+    *reinterpret_cast<float4 *>(out + i) = s;
 }
 
 // Adam (beta1, beta2, eps; bias corrections c1 = 1 - b1^t, c2 = 1 - b2^t)
@@ -334,7 +413,7 @@ struct AdamArgs {
     const float *g;
     float *m, *v;
     const float *lr;                      // device: a captured step reads the current rate
-    unsigned long long *t;                // device step counter (advanced by k_adam_vec)
+    const unsigned long long *t;          // device step counter (advanced by k_loss of the same step)
     float b1, b2, eps;
 };
 
@@ -349,36 +428,32 @@ __device__ __forceinline__ float adam_one(const AdamArgs &a, size_t i, float c1,
     return pi;
 }
 
-// The vectors of the network (b1, b2, b3, w4, b4: three ranges of `lens`
-// parameters from `offs`), one block; the block first takes step t + 1 and,
-// when every thread has read t, stores it (the weight kernel that follows in
-// stream order reads the new value).
-__global__ void k_adam_vec(AdamArgs a, uint32_t off0, uint32_t len0, uint32_t off1, uint32_t len1, uint32_t off2,
-                           uint32_t len2) {
-    const unsigned long long t = *a.t + 1;
-    const float tf = (float)t;
-    const float c1 = 1.f - powf(a.b1, tf), c2 = 1.f - powf(a.b2, tf), lr = *a.lr;
-    for (uint32_t k = threadIdx.x; k < len0; k += blockDim.x) adam_one(a, off0 + k, c1, c2, lr);
-    for (uint32_t k = threadIdx.x; k < len1; k += blockDim.x) adam_one(a, off1 + k, c1, c2, lr);
-    for (uint32_t k = threadIdx.x; k < len2; k += blockDim.x) adam_one(a, off2 + k, c1, c2, lr);
-    __syncthreads();
-    if (threadIdx.x == 0) *a.t = t;
-}
-
 // The three weight matrices W_l^T ([hid][in_l] at off_w[l], blockIdx.z = l),
 // 32 x 32 tiles: Adam on every entry, then the BF16 copies the next step's
 // products read - W^T itself (wt, same layout) and W (w, [in_l][hid], the
-// tile transposed through shared memory) - written coalesced.
+// tile transposed through shared memory) - written coalesced.  Blocks of
+// blockIdx.z = 3 take the vectors (b1, b2, and b3, w4, b4: three ranges from
+// voff, of rows, rows and 2 rows + 1 entries), 256 entries per block.
 struct AdamW {
     uint32_t off[3], cols[3];
     __nv_bfloat16 *wt[3], *w[3];
     uint32_t rows;
+    uint32_t voff[3];
 };
 
 __global__ void k_adam_w(AdamArgs a, AdamW W) {
     __shared__ __nv_bfloat16 tile[32][34];
     // the layer's fields picked without indexing the parameter block at run time
     const uint32_t l = blockIdx.z, rows = W.rows;
+    if (l == 3) {
+        const uint32_t v = (blockIdx.y * gridDim.x + blockIdx.x) * 256 + threadIdx.y * 32 + threadIdx.x;
+        if (v >= 4 * rows + 1) return;
+        const float tf = (float)*a.t;
+        const float c1 = 1.f - powf(a.b1, tf), c2 = 1.f - powf(a.b2, tf);
+        const uint32_t i = v < rows ? W.voff[0] + v : (v < 2 * rows ? W.voff[1] + (v - rows) : W.voff[2] + (v - 2 * rows));
+        adam_one(a, i, c1, c2, *a.lr);
+        return;
+    }
     const uint32_t cols = l == 0 ? W.cols[0] : (l == 1 ? W.cols[1] : W.cols[2]);
     const uint32_t off = l == 0 ? W.off[0] : (l == 1 ? W.off[1] : W.off[2]);
     __nv_bfloat16 *const wt = l == 0 ? W.wt[0] : (l == 1 ? W.wt[1] : W.wt[2]);
@@ -496,6 +571,7 @@ struct titan_mlp {
     __nv_bfloat16 *xT = nullptr, *HT[2] = {nullptr, nullptr}, *bT = nullptr;
     float *y = nullptr, *dy = nullptr;
     float *part = nullptr;                                 // column-reduction chunk sums [B / kRowChunk][hidden]
+    float *partb = nullptr;                                // the same for the bias gradient of one layer
     float *wsk = nullptr;                                  // split-K partial weight gradients [splits][hid][in]
     size_t wsk_cap = 0;                                    // floats
     int *err = nullptr;
@@ -566,14 +642,15 @@ cudaError_t refresh_bf16(titan_mlp *m) {
     return cudaGetLastError();
 }
 
-// One Adam step on every parameter (the step counter advanced on the
-// device) and the BF16 copies of the new weights, in two launches.
+// One Adam step on every parameter (at the step count k_loss advanced on the
+// device) and the BF16 copies of the new weights, in one launch.
 cudaError_t adam_step(titan_mlp *m) {
     AdamArgs a{m->p, m->g, m->m, m->v, m->d_lr, m->d_step, 0.9f, 0.999f, 1e-8f};
-    // b1, b2 and (b3, w4, b4): the parameter layout keeps the last three contiguous
-    k_adam_vec<<<1, 1024, 0, m->stream>>>(a, (uint32_t)m->off_b[0], m->hid, (uint32_t)m->off_b[1], m->hid,
-                                          (uint32_t)m->off_b[2], 2 * m->hid + 1);
     AdamW W;
+    // b1, b2 and (b3, w4, b4): the parameter layout keeps the last three contiguous
+    W.voff[0] = (uint32_t)m->off_b[0];
+    W.voff[1] = (uint32_t)m->off_b[1];
+    W.voff[2] = (uint32_t)m->off_b[2];
     for (int l = 0; l < 3; ++l) {
         W.off[l] = (uint32_t)m->off_w[l];
         W.cols[l] = layer_in(m, l);
@@ -581,7 +658,7 @@ cudaError_t adam_step(titan_mlp *m) {
         W.w[l] = m->w[l];
     }
     W.rows = m->hid;
-    k_adam_w<<<dim3(std::max(m->in, m->hid) / 32, m->hid / 32, 3), dim3(32, 8), 0, m->stream>>>(a, W);
+    k_adam_w<<<dim3(std::max(m->in, m->hid) / 32, m->hid / 32, 4), dim3(32, 8), 0, m->stream>>>(a, W);
     return cudaGetLastError();
 }
 
@@ -600,6 +677,7 @@ cudaError_t ensure_batch(titan_mlp *m, uint32_t B) {
     if ((e = malloc_t(m, &m->y, B)) != cudaSuccess) return e;
     if ((e = malloc_t(m, &m->dy, B)) != cudaSuccess) return e;
     if ((e = malloc_t(m, &m->part, (size_t)((B + kRowChunk - 1) / kRowChunk) * m->hid)) != cudaSuccess) return e;
+    if ((e = malloc_t(m, &m->partb, (size_t)((B + kRowChunk - 1) / kRowChunk) * m->hid)) != cudaSuccess) return e;
     size_t ws = 0;
     for (int l = 0; l < 3; ++l)
         ws = std::max(ws, (size_t)wgrad_splits(m->hid, layer_in(m, l), B) * m->hid * layer_in(m, l));
@@ -629,24 +707,28 @@ cudaError_t forward_pass(titan_mlp *m, const __nv_bfloat16 *x, uint32_t B, float
     return cudaGetLastError();
 }
 
-cudaError_t backward_pass(titan_mlp *m, const __nv_bfloat16 *x, const float *t, uint32_t B, float *loss) {
+// train: a training step follows (k_loss advances the Adam step counter).
+cudaError_t backward_pass(titan_mlp *m, const __nv_bfloat16 *x, const float *t, uint32_t B, float *loss,
+                          bool train = false) {
     cudaError_t e = forward_pass(m, x, B, m->y, true);
     if (e != cudaSuccess) return e;
-    k_loss<<<1, 256, 0, m->stream>>>(m->y, t, m->dy, loss, (int)B, m->g + m->off_b4);
+    k_loss<<<1, kLossThreads, 0, m->stream>>>(m->y, t, m->dy, loss, (int)B, m->g + m->off_b4,
+                                              train ? m->d_step : nullptr);
     const int chunks = ((int)B + kRowChunk - 1) / kRowChunk;
     k_out_backward<<<dim3(nblk(m->hid, 128), chunks), 128, 0, m->stream>>>(m->H[2], m->Z[2], m->dy, m->p + m->off_w4,
-                                                                          m->part, m->dZ[2], (int)B, (int)m->hid);
-    k_col_sum_final<<<nblk(m->hid, 128), 128, 0, m->stream>>>(m->part, chunks, (int)m->hid, m->g + m->off_w4);
+                                                                          m->part, m->dZ[2], m->partb, (int)B,
+                                                                          (int)m->hid);
+    const dim3 cs_grid(nblk(m->hid, 32)), cs_block(32, 32);
+    k_col_sum_final<<<cs_grid, cs_block, 0, m->stream>>>(m->part, chunks, (int)m->hid, m->g + m->off_w4);
     for (int l = 2; l >= 0; --l) {
         // dW_l^T (hid x in_l) = dZ_l^T (hid x B) . A_{l-1}^T (in_l x B)^T
         const uint32_t in = layer_in(m, l);
         const __nv_bfloat16 *actT = l == 0 ? m->xT : m->HT[l - 1];
         // dZ_2^T here; dZ_1^T and dZ_0^T come from the epilogue of the product that forms them
         if (l == 2)
-            k_transpose_bf16<<<dim3(nblk(m->hid, 32), nblk(B, 32)), dim3(32, 8), 0, m->stream>>>(m->dZ[2], m->bT, (int)B,
-                                                                                                 (int)m->hid);
+            k_transpose64_bf16<<<dim3(m->hid / 64, B / 64), 256, 0, m->stream>>>(m->dZ[2], m->bT, (int)B, (int)m->hid);
         if (l == 0)
-            k_transpose_bf16<<<dim3(nblk(in, 32), nblk(B, 32)), dim3(32, 8), 0, m->stream>>>(x, m->xT, (int)B, (int)in);
+            k_transpose64_bf16<<<dim3(in / 64, B / 64), 256, 0, m->stream>>>(x, m->xT, (int)B, (int)in);
         const int splits = wgrad_splits(m->hid, in, B);
         EpiArgs ep{EPI_F32, (int)in, nullptr, splits > 1 ? m->wsk : m->g + m->off_w[l], nullptr, nullptr};
         if ((e = gemm_tn(m->bT, actT, (int)m->hid, (int)in, (int)B, ep, m->stream, m->spin_limit, m->err, splits)) !=
@@ -654,15 +736,17 @@ cudaError_t backward_pass(titan_mlp *m, const __nv_bfloat16 *x, const float *t, 
             return e;
         if (splits > 1) {
             const size_t n = (size_t)m->hid * in;
-            k_sum_splits<<<nblk(n, 256), 256, 0, m->stream>>>(m->g + m->off_w[l], m->wsk, splits, n);
+            k_sum_splits<<<nblk(n / 4, 256), 256, 0, m->stream>>>(m->g + m->off_w[l], m->wsk, splits, n);
         }
-        k_col_sum_part<<<dim3(nblk(m->hid, 128), chunks), 128, 0, m->stream>>>(m->dZ[l], m->part, (int)B, (int)m->hid);
-        k_col_sum_final<<<nblk(m->hid, 128), 128, 0, m->stream>>>(m->part, chunks, (int)m->hid, m->g + m->off_b[l]);
+        // db_l: the chunk sums of dZ_l's columns came with dZ_l (k_out_backward, or the
+        // epilogue of the product that formed it); the next product overwrites them
+        k_col_sum_final<<<cs_grid, cs_block, 0, m->stream>>>(m->partb, chunks, (int)m->hid, m->g + m->off_b[l]);
         if (l > 0) {
             // dZ_{l-1} = (dZ_l . W_l^T) * GELU'(Z_{l-1}):  A = dZ_l (B x hid), B operand = W_l (in x hid)
             EpiArgs ep2{EPI_GELU_GRAD, (int)m->hid, nullptr, nullptr, m->dZ[l - 1], m->Z[l - 1]};
             ep2.out_t = m->bT;            // this layer's weight-gradient product (above) has read bT
             ep2.ldt = (int)B;
+            ep2.colsum = m->partb;
             if ((e = gemm_tn(m->dZ[l], m->w[l], (int)B, (int)in, (int)m->hid, ep2, m->stream, m->spin_limit, m->err)) != cudaSuccess)
                 return e;
         }
@@ -678,7 +762,7 @@ cudaError_t capture_train(titan_mlp *m, uint32_t B, cudaGraphExec_t *out) {
     if (e != cudaSuccess) return e;
     cudaStream_t saved = m->stream;
     m->stream = m->capture;
-    cudaError_t le = backward_pass(m, m->gx, m->gt, B, m->gloss);
+    cudaError_t le = backward_pass(m, m->gx, m->gt, B, m->gloss, true);
     if (le == cudaSuccess) le = adam_step(m);
     m->stream = saved;
     cudaGraph_t g = nullptr;
@@ -928,7 +1012,7 @@ titan_status titan_mlp_train_step(titan_mlp *m, const uint16_t *x_dev, const flo
             return TITAN_OK;
         }
     }
-    MLP_CK(m, backward_pass(m, reinterpret_cast<const __nv_bfloat16 *>(x_dev), t_dev, batch, loss_dev));
+    MLP_CK(m, backward_pass(m, reinterpret_cast<const __nv_bfloat16 *>(x_dev), t_dev, batch, loss_dev, true));
     MLP_CK(m, adam_step(m));
     return TITAN_OK;
 }

@@ -178,7 +178,7 @@ uint64_t shim_batch_smem(uint32_t slots, uint32_t halo, uint32_t n_slices, uint3
 
 // Arrays: "ctas" as 11 uint32 per CTA (BatchCta field order), "groups" as 4
 // uint64 per group (cluster, cta_first, cta_count, smem), then slices, kl,
-// act, nbr, halo, mass_off, mass_cnt, init_state as stored.
+// act, nbr, halo, mass_off, mass_cnt, init_state, mass_of_slot as stored.
 uint64_t shim_batch_len(const char *name) {
     const std::string k(name);
     if (k == "ctas") return bh.ctas.size() * 11;
@@ -191,6 +191,7 @@ uint64_t shim_batch_len(const char *name) {
     if (k == "mass_off") return bh.mass_off.size();
     if (k == "mass_cnt") return bh.mass_cnt.size();
     if (k == "init_state") return bh.init_state.size();
+    if (k == "mass_of_slot") return bh.mass_of_slot.size();
     return 0;
 }
 
@@ -215,6 +216,7 @@ void shim_batch_get(const char *name, void *dst) {
     if (k == "mass_off") copy_out(bh.mass_off, dst);
     if (k == "mass_cnt") copy_out(bh.mass_cnt, dst);
     if (k == "init_state") copy_out(bh.init_state, dst);
+    if (k == "mass_of_slot") copy_out(bh.mass_of_slot, dst);
 }
 
 }  // extern "C"

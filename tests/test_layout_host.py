@@ -351,7 +351,7 @@ class BatchLayout:
     CTA_FIELDS = ("mass_begin", "mass_count", "slot_count", "edge_off", "edge_count", "slice_base", "n_slices",
                   "robot", "halo_off", "halo_count", "halo_slots")
     DT = {"ctas": np.uint32, "groups": np.uint64, "slices": np.uint32, "kl": np.float32, "act": np.float32,
-          "nbr": np.uint16, "halo": np.uint32, "mass_off": np.uint32, "mass_cnt": np.uint32,
+          "nbr": np.uint16, "halo": np.uint32, "mass_off": np.uint32, "mass_cnt": np.uint32, "mass_of_slot": np.uint32,
           "init_state": np.float32}
 
     def __init__(self, lib, systems):
@@ -401,7 +401,7 @@ def _batch_systems():
     rng = np.random.default_rng(5)
     out = [inputs.actuated_box(a, b, c, rng) for a, b, c in
            [(3, 3, 3), (12, 12, 12), (5, 4, 3), (14, 14, 14), (7, 3, 9), (10, 10, 10), (8, 8, 8), (4, 11, 6),
-            (3, 12, 3)]]
+            (3, 12, 3), (9, 9, 9)]]
     two = inputs.two_masses()
     two.act_amp, two.act_phase = None, None
     out.append(two)
@@ -421,14 +421,16 @@ def _batch_systems():
     return out
 
 
-def _decode_slot(L, c, rank, P, slot):
-    """Caller index (within its system) of the mass a table slot names."""
+def _decode_slot(L, c, rank, P, slot, base):
+    """Caller index (within its system) of the mass a table slot names
+    (base: the system's first global slot); -1 for a padding slot."""
     own = slot < P
-    j = np.where(own, rank * P + slot.astype(np.int64), 0)
+    g = np.where(own, rank * P + slot.astype(np.int64), 0)
     if (~own).any():
         code = L.halo[c["halo_off"] + slot[~own].astype(np.int64) - P].astype(np.int64)
-        j[~own] = (code >> 16) * P + (code & 0xFFFF)
-    return j
+        g[~own] = (code >> 16) * P + (code & 0xFFFF)
+    j = L.mass_of_slot[base + g].astype(np.int64)
+    return np.where(j == 0xFFFFFFFF, -1, j)
 
 
 def test_batch_layout_encodes_every_spring_and_every_index_stays_in_range(shim):
@@ -476,11 +478,18 @@ def test_batch_layout_encodes_every_spring_and_every_index_stays_in_range(shim):
                 assert c["halo_off"] + c["halo_count"] <= L.halo.size
                 assert shim.shim_batch_smem(P, c["halo_slots"], c["n_slices"], c["edge_count"],
                                             int(L.any_act)) <= smem
+                # slots: the CTA's own masses (caller range [m0, m1)) by decreasing degree, padding after
+                base = L.mass_off[r]
+                ms = L.mass_of_slot[base + rank * P:base + rank * P + P].astype(np.int64)
+                real = ms[:m1 - m0]
+                assert np.array_equal(np.sort(real), np.arange(m0, m1)) and np.all(ms[m1 - m0:] == 0xFFFFFFFF)
+                dg = np.diff(inc_ptr[r])
+                assert np.all(np.diff(dg[real]) <= 0)
                 # halo: other ranks of this cluster, masses that exist, no repeats
                 hl = L.halo[c["halo_off"]:c["halo_off"] + c["halo_count"]].astype(np.int64)
                 hr, hs = hl >> 16, hl & 0xFFFF
                 assert np.all(hr < cluster) and np.all(hr != rank) and np.all(hs < P)
-                assert np.all(hr * P + hs < n) and len(set(hl.tolist())) == hl.size
+                assert np.all(L.mass_of_slot[base + hr * P + hs] < n) and len(set(hl.tolist())) == hl.size
                 rel = L.slices[c["slice_base"]:c["slice_base"] + c["n_slices"] + 1].astype(np.int64)
                 assert rel[0] == 0 and np.all(np.diff(rel) % 64 == 0) and rel[-1] <= c["edge_count"]
                 nb = L.nbr[c["edge_off"]:c["edge_off"] + c["edge_count"]]
@@ -492,12 +501,13 @@ def test_batch_layout_encodes_every_spring_and_every_index_stays_in_range(shim):
                 for s_ in range(c["n_slices"]):
                     w = (rel[s_ + 1] - rel[s_]) // 32
                     for lane in range(32):
-                        i = rank * P + s_ * 32 + lane                   # caller index of the row's mass
+                        p_ = s_ * 32 + lane                               # the row's slot
+                        i = int(ms[p_]) if p_ < m1 - m0 else -1           # caller index of its mass
                         e = rel[s_] + 32 * np.arange(w) + lane
-                        j = _decode_slot(L, c, rank, P, nb[e])
+                        j = _decode_slot(L, c, rank, P, nb[e], base)
                         pad = (kl[e, 0] == 0) & (kl[e, 1] == 0)
-                        assert np.all(j[pad] == min(i, n - 1)), (r, i)
-                        if i >= n:
+                        assert np.all(nb[e][pad] == p_), (r, i)           # padding names the row's own slot
+                        if i < 0:
                             assert pad.all()
                             continue
                         assert not pad[:np.count_nonzero(~pad)].any()  # springs first, padding after
@@ -517,12 +527,14 @@ def test_batch_layout_encodes_every_spring_and_every_index_stays_in_range(shim):
                             A, ph = sy.act_amp[q], sy.act_phase[q]
                             np.testing.assert_array_equal(a[:, 0], (A * np.cos(ph)).astype(np.float32))
                             np.testing.assert_array_equal(a[:, 1], (A * np.sin(ph)).astype(np.float32))
-            # initial state: real masses in caller order, padding slots fixed and at rest
+            # initial state: every real mass in its slot (the first n slots), padding slots fixed and at rest
             st = L.init_state[L.mass_off[r]:L.mass_off[r] + cluster * P]
-            assert np.array_equal(st[:n, :3], sy.pos.astype(np.float32))
-            assert np.array_equal(st[:n, 4:7], sy.vel.astype(np.float32))
+            who = L.mass_of_slot[L.mass_off[r]:L.mass_off[r] + n].astype(np.int64)
+            assert np.array_equal(np.sort(who), np.arange(n))
+            assert np.array_equal(st[:n, :3], sy.pos[who].astype(np.float32))
+            assert np.array_equal(st[:n, 4:7], sy.vel[who].astype(np.float32))
             inv = np.where(sy.fixed.astype(bool), 0.0, 1.0 / sy.mass).astype(np.float32)
-            assert np.array_equal(st[:n, 3], inv) and not st[n:].any() and not st[:, 7].any()
+            assert np.array_equal(st[:n, 3], inv[who]) and not st[n:].any() and not st[:, 7].any()
     assert sorted(seen_robots) == list(range(len(systems)))
     assert L.total_slots == L.init_state.shape[0]
 
