@@ -52,7 +52,7 @@ QUEUE_FILL_CYCLES = 2_000_000
 # header and the build script with its flags).  Reported only while those are
 # unchanged.  Capture: profiles/k_step_box_lattice1m.md.
 NCU_TRAFFIC = {
-    ("lattice1m", "csr", "k_step_box", "f5caef2b84fe5671"): 251_618_304 + 12_401_664,
+    ("lattice1m", "csr", "k_step_box", "544b3a1b8dc37538"): 251_609_856 + 12_306_432,
 }
 KERNEL_INPUTS = ("paper_1911_10274_gb300/csrc/step_kernels.cu", "paper_1911_10274_gb300/csrc/physics.cuh",
                  "paper_1911_10274_gb300/build.py")
@@ -387,7 +387,7 @@ def adjoint_leg(device, n_robots=4096, steps=200, every=50):
             "note": "forward with checkpoints + per-segment recompute + two reverse kernels per step"}
 
 
-def mlp_leg(device, batch=4096, n_in=1024, hidden=512, reps=20):
+def mlp_leg(device, batch=4096, n_in=1024, hidden=512, reps=20, big=True):
     """The surrogate's tensor-core work: the largest forward GEMM
     (batch x in) . (hidden x in)^T alone, and a whole training step."""
     import torch
@@ -423,27 +423,35 @@ def mlp_leg(device, batch=4096, n_in=1024, hidden=512, reps=20):
     large_tflops = 2.0 * L ** 3 / large_s / 1e12
     del AL, BL, CL
     net = T.MLP(n_in, hidden, seed=0, device=device)
-    x = torch.randn(batch, n_in, device=dev).bfloat16()
-    t = torch.randn(batch, device=dev)
-    for _ in range(3):
-        net.train_step(x, t, 1e-3)
-    net.sync()
-    ts = torch.cuda.Event(enable_timing=True)
-    te = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(reps):
-        net.train_step(x, t, 1e-3)
-    net.sync()
-    step_s = (time.perf_counter() - t0) / reps
+
+    def train_time(bsz, n):
+        x = torch.randn(bsz, n_in, device=dev).bfloat16()
+        t = torch.randn(bsz, device=dev)
+        for _ in range(3):
+            net.train_step(x, t, 1e-3)
+        net.sync()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(n):
+            net.train_step(x, t, 1e-3)          # enqueued back to back (one captured graph each)
+        net.sync()
+        return (time.perf_counter() - t0) / n
+
     # forward: 3 products; backward: 3 weight-gradient products and the input
     # gradients of the two hidden layers (none for the network's input)
-    step_flops = 2.0 * batch * (3 * (n_in * hidden + 2 * hidden * hidden) - n_in * hidden)
+    def flops_of(bsz):
+        return 2.0 * bsz * (3 * (n_in * hidden + 2 * hidden * hidden) - n_in * hidden)
+
+    step_s = train_time(batch, reps)
+    step_flops = flops_of(batch)
+    big_batch = 8 * batch
+    big_s = train_time(big_batch, reps) if big else None
     peak = bf16_peak()
     return {"gemm": f"{batch}x{hidden}x{n_in} BF16, FP32 accumulate (tcgen05)",
             "gemm_tflops": flops / gemm_s / 1e12, "gemm_s": gemm_s,
             "train_step_s": step_s, "train_samples_per_s": batch / step_s,
             "train_tflops": step_flops / step_s / 1e12,
+            f"train_tflops_batch{big_batch}": flops_of(big_batch) / big_s / 1e12 if big else None,
             "gemm_8192_tflops": large_tflops, "gemm_8192_frac": large_tflops / peak[0],
             "roofline": {"bound": "tensor", "achieved": large_tflops, "peak": peak[0], "unit": "TFLOP/s",
                          "frac": large_tflops / peak[0], "peak_source": peak[1],
@@ -566,7 +574,7 @@ def run_leg(args):
     elif args.leg == "adjoint":
         out = adjoint_leg(local, n_robots=args.robots, steps=args.rollout_steps)
     elif args.leg == "mlp":
-        out = mlp_leg(local)
+        out = mlp_leg(local, reps=args.mlp_reps, big=not args.mlp_no_big)
     else:
         raise SystemExit(f"unknown leg {args.leg}")
     print(json.dumps({"leg": args.leg, **out}), flush=True)
@@ -588,6 +596,8 @@ def main():
     ap.add_argument("--robots", type=int, default=4096, help="robots of the --leg batched/adjoint run")
     ap.add_argument("--rollout-steps", type=int, default=2000, help="rollout steps of the --leg run")
     ap.add_argument("--untuned", action="store_true", help="--leg batched: keep the default launch shapes")
+    ap.add_argument("--mlp-reps", type=int, default=20, help="--leg mlp: timed training steps per batch size")
+    ap.add_argument("--mlp-no-big", action="store_true", help="--leg mlp: skip the 8x batch")
     ap.add_argument("--no-l2-persist", action="store_true",
                     help="do not keep the state buffers resident in L2 (access-policy window)")
     ap.add_argument("--order", choices=["morton", "input"], default="morton",

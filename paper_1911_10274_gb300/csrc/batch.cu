@@ -50,7 +50,7 @@ template <bool ACT, bool GROUND>
 __global__ void __launch_bounds__(1024)
 k_batch_rollout(const BatchCta *__restrict__ ctas, const MassState *__restrict__ state_in,
                 MassState *__restrict__ state_out, const uint32_t *__restrict__ slice_rel,
-                const float2 *__restrict__ kl, const float2 *__restrict__ act,
+                const float2 *__restrict__ kl, const float4 *__restrict__ kla,
                 const uint16_t *__restrict__ nbr, const uint32_t *__restrict__ halo, titan::StepConst c,
                 long long step0, uint32_t n_steps, uint32_t cluster_size, uint32_t tpm_max, uint32_t spin_limit,
                 int *__restrict__ err) {
@@ -66,8 +66,8 @@ k_batch_rollout(const BatchCta *__restrict__ ctas, const MassState *__restrict__
     float2 *const b0s = reinterpret_cast<float2 *>(sm + L.b0), *const b1s = reinterpret_cast<float2 *>(sm + L.b1);
     float *s_inv = reinterpret_cast<float *>(sm + L.inv);
     const uint32_t *s_slice = reinterpret_cast<const uint32_t *>(sm + L.slices);
-    const float2 *s_kl = reinterpret_cast<const float2 *>(sm + L.kl);
-    const float2 *s_act = reinterpret_cast<const float2 *>(sm + L.act);
+    const float2 *s_kl = reinterpret_cast<const float2 *>(sm + L.kl);      // not actuated
+    const float4 *s_kla = reinterpret_cast<const float4 *>(sm + L.kl);     // actuated: {k, L0, A cos, A sin}
     const uint16_t *s_nbr = reinterpret_cast<const uint16_t *>(sm + L.nbr);
     const uint32_t tid = threadIdx.x;
 
@@ -85,8 +85,8 @@ k_batch_rollout(const BatchCta *__restrict__ ctas, const MassState *__restrict__
         // every size is a multiple of 16 bytes; zero-size copies are not issued
         titan::ptx::bulk_g2s(sm + L.slices, slice_rel + d.slice_base, slice_bytes, &bar);
         if (d.edge_count) {
-            titan::ptx::bulk_g2s(sm + L.kl, kl + d.edge_off, d.edge_count * 8, &bar);
-            if (ACT) titan::ptx::bulk_g2s(sm + L.act, act + d.edge_off, d.edge_count * 8, &bar);
+            if (ACT) titan::ptx::bulk_g2s(sm + L.kl, kla + d.edge_off, d.edge_count * 16, &bar);
+            else titan::ptx::bulk_g2s(sm + L.kl, kl + d.edge_off, d.edge_count * 8, &bar);
             titan::ptx::bulk_g2s(sm + L.nbr, nbr + d.edge_off, d.edge_count * 2, &bar);
         }
     }
@@ -166,12 +166,14 @@ k_batch_rollout(const BatchCta *__restrict__ ctas, const MassState *__restrict__
                     const float2 qb = srcB[slot];
                     qp = make_float4(qa.x, qa.y, qa.z, 0.f);
                     qv = make_float4(qa.w, qb.x, qb.y, 0.f);
-                    const float2 a = s_kl[e];
-                    k = a.x;
-                    L0 = a.y;
                     if (ACT) {
-                        const float2 s = s_act[e];               // (A cos phi, A sin phi)
-                        L0 = a.y + a.y * (s.x * sp + s.y * cp);
+                        const float4 a = s_kla[e];
+                        k = a.x;
+                        L0 = a.y + a.y * (a.z * sp + a.w * cp);
+                    } else {
+                        const float2 a = s_kl[e];
+                        k = a.x;
+                        L0 = a.y;
                     }
                 };
                 // four entries in flight per thread (their shared-memory loads
@@ -277,7 +279,8 @@ struct titan_batch {
     MassState *d_state[2] = {nullptr, nullptr};
     int cur = 0;
     uint32_t *d_slice = nullptr;
-    float2 *d_kl = nullptr, *d_act = nullptr;
+    float2 *d_kl = nullptr;                      // not actuated: {k, L0} per entry
+    float4 *d_kla = nullptr;                     // actuated: {k, L0, A cos phi, A sin phi} per entry
     uint16_t *d_nbr = nullptr;
     uint32_t *d_halo = nullptr;
     uint32_t *d_moff = nullptr, *d_mcnt = nullptr;
@@ -355,14 +358,14 @@ cudaError_t launch_group(titan_batch *b, const Group &g, cudaStream_t st, long l
     const MassState *in = b->d_state[b->cur];
     MassState *out = b->d_state[b->cur ^ 1];
     void (*kern)(const BatchCta *, const MassState *, MassState *, const uint32_t *, const float2 *,
-                 const float2 *, const uint16_t *, const uint32_t *, titan::StepConst, long long, uint32_t, uint32_t,
+                 const float4 *, const uint16_t *, const uint32_t *, titan::StepConst, long long, uint32_t, uint32_t,
                  uint32_t, uint32_t, int *);
     if (b->has_act) kern = b->c.ground ? k_batch_rollout<true, true> : k_batch_rollout<true, false>;
     else kern = b->c.ground ? k_batch_rollout<false, true> : k_batch_rollout<false, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
     if (e != cudaSuccess) return e;
     return cudaLaunchKernelEx(&cfg, kern, ctas, in, out, (const uint32_t *)b->d_slice, (const float2 *)b->d_kl,
-                              (const float2 *)b->d_act, (const uint16_t *)b->d_nbr, (const uint32_t *)b->d_halo,
+                              (const float4 *)b->d_kla, (const uint16_t *)b->d_nbr, (const uint32_t *)b->d_halo,
                               b->c, step0, n_steps,
                               g.cluster, g.tpm, b->spin_limit, b->d_err);
 }
@@ -505,8 +508,8 @@ titan_status titan_batch_create(uint32_t n_systems, const titan_masses *masses, 
     CK(balloc(b, &b->d_state[0], b->total_slots));
     CK(balloc(b, &b->d_state[1], b->total_slots));
     CK(balloc(b, &b->d_slice, L.slices.size()));
-    CK(balloc(b, &b->d_kl, E));
-    if (L.any_act) CK(balloc(b, &b->d_act, E));
+    if (b->has_act) CK(balloc(b, &b->d_kla, E));
+    else CK(balloc(b, &b->d_kl, E));
     CK(balloc(b, &b->d_nbr, E));
     CK(balloc(b, &b->d_halo, std::max<size_t>(L.halo.size(), 1)));
     CK(balloc(b, &b->d_moff, n_systems));
@@ -516,8 +519,14 @@ titan_status titan_batch_create(uint32_t n_systems, const titan_masses *masses, 
     CK(cudaMemcpy(b->d_ctas, L.ctas.data(), L.ctas.size() * sizeof(BatchCta), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(b->d_state[0], b->init_state.data(), b->init_state.size() * sizeof(float), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(b->d_slice, L.slices.data(), L.slices.size() * 4, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(b->d_kl, L.kl.data(), L.kl.size() * sizeof(float), cudaMemcpyHostToDevice));
-    if (L.any_act) CK(cudaMemcpy(b->d_act, L.act.data(), L.act.size() * sizeof(float), cudaMemcpyHostToDevice));
+    if (b->has_act) {
+        std::vector<float4> kla(E);
+        for (size_t e = 0; e < E; ++e)
+            kla[e] = make_float4(L.kl[2 * e], L.kl[2 * e + 1], L.act[2 * e], L.act[2 * e + 1]);
+        CK(cudaMemcpy(b->d_kla, kla.data(), E * sizeof(float4), cudaMemcpyHostToDevice));
+    } else {
+        CK(cudaMemcpy(b->d_kl, L.kl.data(), L.kl.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
     CK(cudaMemcpy(b->d_nbr, L.nbr.data(), E * 2, cudaMemcpyHostToDevice));
     if (!L.halo.empty()) CK(cudaMemcpy(b->d_halo, L.halo.data(), L.halo.size() * 4, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(b->d_moff, b->mass_off.data(), n_systems * 4, cudaMemcpyHostToDevice));

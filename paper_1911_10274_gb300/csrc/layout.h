@@ -236,7 +236,9 @@ struct BatchCta {
 // Shared-memory image of one CTA (byte offsets, all 16-byte aligned): two
 // state buffers of (own + halo) slots split into (x, y, z, vx) float4 and
 // (vy, vz) float2 arrays, 1/m of the own slots, the relative slice offsets,
-// {k, L0} per entry, the actuation pair per entry (if any), the slot per entry.
+// per entry {k, L0} - or, when the batch is actuated, {k, L0, A cos phi,
+// A sin phi} (one 16-byte load) - then the slot per entry.  (`act` names the
+// same offset as `kl`: the actuation pair is interleaved there.)
 struct BatchSmem {
     uint32_t a0, b0, a1, b1, inv, slices, kl, act, nbr, total;
 };
@@ -252,8 +254,8 @@ TITAN_HD inline BatchSmem batch_smem_layout(uint32_t slots, uint32_t halo, uint3
     L.inv = al16(L.b1 + tab * 8);
     L.slices = al16(L.inv + slots * 4);
     L.kl = al16(L.slices + 4 * ((n_slices + 1 + 3) & ~3u));
-    L.act = L.kl + edges * 8;
-    L.nbr = L.act + (act ? edges * 8 : 0);
+    L.act = L.kl;
+    L.nbr = L.kl + edges * (act ? 16 : 8);
     L.total = al16(L.nbr + edges * 2);
     return L;
 }
