@@ -156,8 +156,12 @@ titan_status titan_create(const titan_masses *masses, const titan_springs *sprin
 
 /* Enqueues n_steps time steps on the simulation's stream and returns without
  * waiting for them (Sec. III-D: the GPU runs while the caller continues).
- * Each step is the spring pass and the mass pass of Sec. III-B.
- * n_steps == 0 is a no-op.  Errors: TITAN_E_CUDA, TITAN_E_TIMEOUT (a bounded
+ * Each step is the spring pass and the mass pass of Sec. III-B.  Steps are
+ * replayed from captured CUDA graphs (params.graph_chunk): a count that is
+ * not one graph of the ladder 64, 32, ..., 2 and is at most twice the chunk
+ * gets a graph of its own, captured on its first use (the four most
+ * recently used counts are kept), so a caller stepping by a fixed count
+ * pays the capture once.  n_steps == 0 is a no-op.  Errors: TITAN_E_CUDA, TITAN_E_TIMEOUT (a bounded
  * device wait in the persistent kernel expired; reported by this or a later
  * call once the GPU has run it). */
 titan_status titan_step(titan_sim *sim, uint64_t n_steps);

@@ -113,6 +113,10 @@ void free_graphs(titan_sim *sim) {
             if (g) cudaGraphExecDestroy(g);
             g = nullptr;
         }
+    for (auto &x : sim->exact) {
+        if (x.exec) cudaGraphExecDestroy(x.exec);
+        x = SimCore::ExactGraph();
+    }
     sim->graphs_built = false;
 }
 
@@ -527,20 +531,55 @@ cudaError_t titan::enqueue_sim_step_io(titan_sim *sim, cudaStream_t st, const Ma
 
 namespace {
 
-cudaError_t capture_graph(titan_sim *sim, int L, int b) {
+// Captures k_steps steps starting from state buffer b into *out.
+cudaError_t capture_steps(titan_sim *sim, uint64_t k_steps, int b, cudaGraphExec_t *out) {
     cudaError_t e = cudaStreamBeginCapture(sim->capture, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
     cudaError_t le = cudaSuccess;
-    const int k_steps = graph_steps(sim, L);
     // the graph's first step follows whatever precedes the graph launch: plain order
-    for (int k = 0; k < k_steps && le == cudaSuccess; ++k) le = enqueue_step(sim, sim->capture, b ^ (k & 1), k > 0);
+    for (uint64_t k = 0; k < k_steps && le == cudaSuccess; ++k)
+        le = enqueue_step(sim, sim->capture, b ^ (int)(k & 1), k > 0);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(sim->capture, &g);
     if (le != cudaSuccess) { if (g) cudaGraphDestroy(g); return le; }
     if (e != cudaSuccess) return e;
-    e = cudaGraphInstantiate(&sim->graph[L][b], g, 0);
+    e = cudaGraphInstantiate(out, g, 0);
     cudaGraphDestroy(g);
     return e;
+}
+
+cudaError_t capture_graph(titan_sim *sim, int L, int b) {
+    return capture_steps(sim, (uint64_t)graph_steps(sim, L), b, &sim->graph[L][b]);
+}
+
+// The graph of exactly n steps from buffer b, captured on first use (n from
+// 3 to twice the graph chunk that is not itself a ladder level); null if the
+// count does not qualify or the capture failed (the ladder then runs it).
+cudaGraphExec_t exact_graph(titan_sim *sim, uint64_t n, int b) {
+    if (n < 3 || n > 2 * (uint64_t)sim->graph_chunk) return nullptr;
+    for (int L = 0; L < kGraphLevels; ++L)
+        if ((uint64_t)graph_steps(sim, L) == n) return nullptr;
+    ++sim->exact_clock;
+    SimCore::ExactGraph *slot = &sim->exact[0];
+    for (auto &x : sim->exact) {
+        if (x.exec && x.n == n && x.b == b) {
+            x.last_use = sim->exact_clock;
+            return x.exec;
+        }
+        if (!x.exec || (slot->exec && x.last_use < slot->last_use)) slot = &x;
+    }
+    if (slot->exec) cudaGraphExecDestroy(slot->exec);
+    *slot = SimCore::ExactGraph();
+    cudaGraphExec_t g = nullptr;
+    if (capture_steps(sim, n, b, &g) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    slot->n = n;
+    slot->b = b;
+    slot->last_use = sim->exact_clock;
+    slot->exec = g;
+    return g;
 }
 
 // Captures every level's graph for both starting buffers at once (so that no
@@ -906,8 +945,17 @@ titan_status titan_step(titan_sim *sim, uint64_t n_steps) {
         sim->steps += k;
     }
     // whole graphs, largest level first (each an even step count: the buffer
-    // parity is unchanged), then at most one single launch
+    // parity is unchanged), then at most one single launch; a count of its
+    // own (up to twice the chunk) replays one graph captured for it
     if (n_steps >= 2 && sim->graph_chunk > 0) TITAN_CK(sim, ensure_graphs(sim));
+    if (sim->graph_chunk > 0 && sim->graphs_built) {
+        if (cudaGraphExec_t g = exact_graph(sim, n_steps, sim->cur)) {
+            TITAN_CK(sim, cudaGraphLaunch(g, sim->stream));
+            sim->cur ^= (int)(n_steps & 1);
+            sim->steps += n_steps;
+            n_steps = 0;
+        }
+    }
     for (int L = 0; L < kGraphLevels && n_steps >= 2; ++L) {
         const uint64_t k = (uint64_t)graph_steps(sim, L);
         if (!k) continue;

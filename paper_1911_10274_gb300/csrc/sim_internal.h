@@ -14,6 +14,7 @@ using titan::MassState;
 
 constexpr int kDefaultGraphChunk = 64;
 constexpr int kGraphLevels = 8;
+constexpr int kExactGraphs = 4;          // step counts with a graph of their own (least recently used replaced)
 constexpr uint32_t kDefaultSpinLimit = 1u << 22;
 
 // Everything a simulation owns; titan_sim adds the per-handle lock and error
@@ -86,6 +87,17 @@ struct SimCore {
     // that count is even and >= 2), one graph per starting buffer
     cudaGraphExec_t graph[kGraphLevels][2] = {};
     bool graphs_built = false;
+    // whole step counts that are not one ladder level (a caller stepping by a
+    // fixed count, e.g. 20 = 16 + 4), captured on first use: one graph
+    // replaces several, so one fewer step per call starts in plain order
+    struct ExactGraph {
+        uint64_t n = 0;
+        int b = 0;
+        uint64_t last_use = 0;
+        cudaGraphExec_t exec = nullptr;
+    };
+    ExactGraph exact[kExactGraphs];
+    uint64_t exact_clock = 0;
 
     // snapshots: slot = ticket & 1
     float *snap_dev[2] = {nullptr, nullptr};     // [2][n][3] pos then vel, caller order
