@@ -42,7 +42,7 @@ void set_thread_error(const std::string &msg);   // runtime.cu
 
 namespace {
 
-// BM x BN output tile per CTA; BN = 128 or 256 (wide tiles for large
+// BM x BN output tile per CTA; BN = 64, 128 or 256 (wide tiles for large
 // products: each A tile then feeds twice the columns, halving the A traffic
 // from L2 per FLOP).
 constexpr int BM = 128, BN = 128, BK = 64, STAGES = 4;
@@ -536,12 +536,19 @@ cudaError_t gemm_tn(const void *A, const void *B, int M, int N, int K, const Epi
     if (splits < 1 || (splits > 1 && (ep.mode != EPI_F32 || (K / splits) % BK || K % splits)))
         return cudaErrorInvalidValue;
     if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15) return cudaErrorInvalidValue;
-    // 256-wide tiles once there are at least two waves of them on 152 SMs
+    // 256-wide tiles once there are at least two waves of them on 152 SMs;
+    // 64-wide tiles when 128-wide ones (split-K slices included) would not
+    // fill one wave: twice the CTAs, two resident per SM (97 KB of shared
+    // memory each), so one CTA's epilogue overlaps another's products
+    const int64_t tiles128 = (int64_t)(N / 128) * (M / BM) * splits;
     const bool wide = splits == 1 && N % 256 == 0 && (int64_t)(N / 256) * (M / BM) >= 2 * 152;
+    const bool narrow = !wide && tiles128 <= 152;
     CUtensorMap ma, mb;
-    if (!make_map(&ma, A, M, K) || !make_map(&mb, B, N, K, wide ? 256 : 128)) return cudaErrorInvalidValue;
-    return wide ? gemm_tn_launch<256>(ma, mb, M, N, K, ep, st, spin_limit, err)
-                : gemm_tn_launch<128>(ma, mb, M, N, K, ep, st, spin_limit, err, splits);
+    if (!make_map(&ma, A, M, K) || !make_map(&mb, B, N, K, wide ? 256 : (narrow ? 64 : 128)))
+        return cudaErrorInvalidValue;
+    if (wide) return gemm_tn_launch<256>(ma, mb, M, N, K, ep, st, spin_limit, err);
+    if (narrow) return gemm_tn_launch<64>(ma, mb, M, N, K, ep, st, spin_limit, err, splits);
+    return gemm_tn_launch<128>(ma, mb, M, N, K, ep, st, spin_limit, err, splits);
 }
 
 inline unsigned nblk(size_t n, int t) { return (unsigned)((n + t - 1) / t); }

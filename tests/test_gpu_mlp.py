@@ -17,8 +17,10 @@ torch = pytest.importorskip("torch")
 
 
 # the last two shapes have at least two waves of 256-wide tiles: the wide-tile kernel
+# tile widths: 64 (up to one wave of 128-wide tiles), 128 (between), 256
+# (two waves of 256-wide tiles or more)
 @pytest.mark.parametrize("M,N,K", [(128, 128, 64), (256, 384, 512), (512, 512, 4096), (4096, 512, 1024),
-                                   (4096, 2560, 256), (2048, 5120, 192)])
+                                   (4096, 768, 256), (4096, 2560, 256), (2048, 5120, 192)])
 def test_tcgen05_gemm_matches_reference(M, N, K):
     g = torch.Generator(device="cuda").manual_seed(M + N + K)
     A = torch.randn(M, K, device="cuda", generator=g).bfloat16()
