@@ -458,7 +458,7 @@ def mlp_leg(device, batch=4096, n_in=1024, hidden=512, reps=20, big=True):
                          "kernel": "k_gemm_tn", "shape": f"{L}x{L}x{L}",
                          "note": "the kernel on a square product, 5 calls enqueued back to back and timed "
                                  "to the end of the last; at the MLP's own shapes (gemm_tflops) one call is a "
-                                 "128-CTA launch of 4.3 GFLOP"}}
+                                 "256-CTA launch (128 x 64 tiles, two per SM) of 4.3 GFLOP"}}
 
 
 def bf16_peak():
