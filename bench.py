@@ -315,7 +315,8 @@ def config_for(args, system, resolved=None):
     return cfg
 
 
-def batched_leg(stream_handle, device, n_robots=4096, steps=2000, plain_robots=32, plain_steps=200, tune=True):
+def batched_leg(stream_handle, device, n_robots=4096, steps=2000, plain_robots=32, plain_steps=200, tune=True,
+                robot_max=12):
     """Batched actuated robots (a, b, c ~ U{3..12}, 30% of springs actuated,
     ground contact): one rollout of `steps` steps for all robots in the
     persistent cluster launches, against plain per-robot launches (one kernel
@@ -323,7 +324,7 @@ def batched_leg(stream_handle, device, n_robots=4096, steps=2000, plain_robots=3
     import torch
     from paper_1911_10274_gb300 import inputs
     from paper_1911_10274_gb300 import titan as T
-    robots = inputs.robot_batch(n_robots, seed=0)
+    robots = inputs.robot_batch(n_robots, seed=0, hi=robot_max)
     springs = sum(r.n_springs for r in robots)
     with T.Batch(robots, device=device, stream=stream_handle) as b:
         if tune:
@@ -353,7 +354,7 @@ def batched_leg(stream_handle, device, n_robots=4096, steps=2000, plain_robots=3
     for sm in sims:
         sm.close()
     plain = 1.0 / (per_robot_step * steps)
-    return {"workload": f"{n_robots} actuated lattice robots, a,b,c ~ U{{3..12}}, {springs} springs, "
+    return {"workload": f"{n_robots} actuated lattice robots, a,b,c ~ U{{3..{robot_max}}}, {springs} springs, "
                         f"{steps}-step rollouts, ground contact, dt=1e-4",
             "rollouts_per_s": n_robots / t, "plain_rollouts_per_s": plain, "speedup": n_robots / t / plain,
             "spring_updates_per_s": springs * steps / t, "rollout_s": t,
@@ -573,7 +574,8 @@ def run_leg(args):
     torch.cuda.set_stream(stream)
     if args.leg == "batched":
         out = batched_leg(stream.cuda_stream, local, n_robots=args.robots, steps=args.rollout_steps,
-                          plain_robots=min(32, args.robots), plain_steps=20, tune=not args.untuned)
+                          plain_robots=min(32, args.robots), plain_steps=20, tune=not args.untuned,
+                          robot_max=args.robot_max)
     elif args.leg == "adjoint":
         out = adjoint_leg(local, n_robots=args.robots, steps=args.rollout_steps)
     elif args.leg == "mlp":
@@ -599,6 +601,7 @@ def main():
     ap.add_argument("--robots", type=int, default=4096, help="robots of the --leg batched/adjoint run")
     ap.add_argument("--rollout-steps", type=int, default=2000, help="rollout steps of the --leg run")
     ap.add_argument("--untuned", action="store_true", help="--leg batched: keep the default launch shapes")
+    ap.add_argument("--robot-max", type=int, default=12, help="--leg batched: largest robot edge (masses)")
     ap.add_argument("--mlp-reps", type=int, default=20, help="--leg mlp: timed training steps per batch size")
     ap.add_argument("--mlp-no-big", action="store_true", help="--leg mlp: skip the 8x batch")
     ap.add_argument("--no-l2-persist", action="store_true",

@@ -353,7 +353,7 @@ cudaError_t launch_group(titan_batch *b, const Group &g, cudaStream_t st, long l
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = g.cluster > 1 ? 1 : 0;       // one-CTA robots: a plain launch
     const BatchCta *ctas = b->d_ctas + g.cta_first;
     const MassState *in = b->d_state[b->cur];
     MassState *out = b->d_state[b->cur ^ 1];
