@@ -170,14 +170,20 @@ def titan_snapshot_async(sim: int, stream: Optional[int] = None) -> int:
     return t.value
 
 
-def titan_snapshot_wait(sim: int, ticket: int, n: int):
-    """Returns (pos, vel, t); pos/vel are numpy copies [n][3] float32."""
+def titan_snapshot_wait(sim: int, ticket: int, n: int, copy: bool = True):
+    """Returns (pos, vel, t): pos/vel [n][3] float32, numpy copies, or with
+    copy=False read-only views of the library's pinned snapshot buffers (no
+    host copy; valid until the second next titan_snapshot_async)."""
     p, v, t = C.POINTER(C.c_float)(), C.POINTER(C.c_float)(), C.c_double()
     _check(load().titan_snapshot_wait(sim, ticket, C.byref(p), C.byref(v), C.byref(t)), sim)
     if n == 0:
         return np.zeros((0, 3), np.float32), np.zeros((0, 3), np.float32), t.value
-    pos = np.ctypeslib.as_array(p, shape=(n, 3)).copy()
-    vel = np.ctypeslib.as_array(v, shape=(n, 3)).copy()
+    pos = np.ctypeslib.as_array(p, shape=(n, 3))
+    vel = np.ctypeslib.as_array(v, shape=(n, 3))
+    if copy:
+        return pos.copy(), vel.copy(), t.value
+    pos.flags.writeable = False
+    vel.flags.writeable = False
     return pos, vel, t.value
 
 
@@ -526,10 +532,12 @@ class Sim:
         titan_step(self.handle, n)
         return self
 
-    def snapshot(self):
-        """(pos, vel, t) after every step enqueued so far (float32, caller order)."""
+    def snapshot(self, copy: bool = True):
+        """(pos, vel, t) after every step enqueued so far (float32, caller order);
+        copy=False: read-only views of the pinned snapshot buffers, valid until
+        the second next snapshot."""
         t = titan_snapshot_async(self.handle)          # first: a pending rebuild changes n
-        return titan_snapshot_wait(self.handle, t, self.n)
+        return titan_snapshot_wait(self.handle, t, self.n, copy=copy)
 
     def add_masses(self, pos, mass, vel=None, fixed=None) -> int:
         first = titan_add_masses(self.handle, pos, mass, vel, fixed)

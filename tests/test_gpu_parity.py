@@ -488,3 +488,19 @@ def test_l2_persistence_changes_no_bit():
         a = gpu_run(sys, 200, l2_persist=True, **LAUNCH)
         b = gpu_run(sys, 200, l2_persist=False, **LAUNCH)
         assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_snapshot_views_equal_copies_and_outlive_the_next_snapshot():
+    """snapshot(copy=False) returns read-only views of the pinned snapshot
+    buffers: the same values as a copy, still intact after one more snapshot."""
+    sys = inputs.cube_drop(drop_height=0.02)
+    with T.Sim(sys, **LAUNCH) as sim:
+        sim.step(10)
+        a = sim.snapshot()
+        v = sim.snapshot(copy=False)
+        assert np.array_equal(a[0], v[0]) and np.array_equal(a[1], v[1]) and a[2] == v[2]
+        assert not v[0].flags.writeable and not v[1].flags.writeable
+        sim.step(10)
+        b = sim.snapshot()
+        assert not np.array_equal(b[0], a[0])
+        assert np.array_equal(v[0], a[0]) and np.array_equal(v[1], a[1])
