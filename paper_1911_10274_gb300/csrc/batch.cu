@@ -5,17 +5,20 @@
 //
 // The paper simulates hundreds of worms at once (Sec. V-B) and many agents in
 // parallel (Sec. I).  Here every robot is owned by one thread-block cluster of
-// C CTAs (C = 1, 2, 4 or 8, the smallest that holds it).  Each CTA owns a
-// contiguous range of the robot's masses: at launch it copies its masses'
-// state and their SELL-32 half-edge rows into shared memory with 1-D TMA bulk
-// copies (one mbarrier, bounded wait), then runs every time step of the
-// rollout without touching global memory: each step first copies the current
-// state of its halo - the masses of other CTAs of the cluster its rows touch -
-// out of their shared memory (distributed shared memory, one coalesced pass),
-// then reads every neighbour from its own shared memory; integration into the
-// other state buffer; one hardware cluster barrier per step.  The final state goes back to global
-// memory.  The step is the same as the single-system kernels' (Sec. III-B,
-// Eq. 1 with the Sec. III-A constraints), including sinusoidal actuation.
+// C CTAs (C = 1, 2, 4 or 8, the smallest that holds it; one-CTA robots are
+// plain launches).  Each CTA owns a contiguous range of the robot's masses,
+// held in its slots by decreasing degree (rows of similar length share a
+// SELL-32 slice): at launch it copies their state and half-edge rows into
+// shared memory with 1-D TMA bulk copies (one mbarrier, bounded wait), then
+// runs every time step of the rollout without touching global memory: each
+// step first copies the current state of its halo - the masses of other CTAs
+// of the cluster its rows touch - out of their shared memory (distributed
+// shared memory, one coalesced pass), then reads every neighbour from its own
+// shared memory; integration into the other state buffer; one hardware cluster
+// barrier per step.  The final state goes back to global memory.  The step is
+// the same as the single-system kernels' (Sec. III-B, Eq. 1 with the Sec. III-A
+// constraints), including sinusoidal actuation, whose sin and cos are formed
+// once per CTA and step.
 #include <cooperative_groups.h>
 #include <math.h>
 #include <string.h>
