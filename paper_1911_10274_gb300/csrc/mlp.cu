@@ -8,18 +8,27 @@
 // Network: in -> hidden -> hidden -> hidden -> 1, GELU after each hidden layer.
 //
 // GEMM kernel (k_gemm_tn): C[M, N] = A[M, K] * B[N, K]^T with A and B row-major
-// BF16 (K contiguous).  One CTA per 128 x 128 output tile, 128 threads:
+// BF16 (K contiguous).  One CTA per 128 x BN output tile (BN = 64, 128 or
+// 256), optionally one K slice of it (split K), 256 threads:
 //   warp 0 lane 0  - TMA producer: 2-D tiled loads (128-byte swizzle) of the
 //                    A and B K-blocks (64 wide) into a 4-stage ring;
-//   warp 1 lane 0  - MMA issuer: tcgen05.mma.kind::f16 (M = N = 128, K = 16)
-//                    into an FP32 accumulator in TMEM, releasing each stage
-//                    with tcgen05.commit;
-//   all 4 warps    - epilogue: tcgen05.ld of the accumulator (warp w owns TMEM
-//                    lanes 32w..32w+31 = output rows), fused bias + GELU, or
-//                    the GELU-derivative product of back-propagation, stored
-//                    to global memory.
+//   warp 1 lane 0  - MMA issuer: tcgen05.mma.kind::f16 (M = 128, N = BN,
+//                    K = 16) into an FP32 accumulator in TMEM, releasing each
+//                    stage with tcgen05.commit;
+//   all 8 warps    - epilogue: tcgen05.ld of the accumulator (warp w reads
+//                    TMEM lanes 32 (w mod 4) .. + 31 = output rows, half
+//                    w / 4 of the columns), each 32 x 32 block staged in the
+//                    idle stage buffers so that global traffic runs along rows:
+//                    FP32 output, fused bias + GELU, or the GELU-derivative
+//                    product of back-propagation, with optional transposed
+//                    BF16 copies and bias-gradient column partials.
 // Every mbarrier wait is bounded (spin_limit polls); on expiry the kernel sets
-// *err, skips the epilogue, frees its TMEM and returns.
+// *err, waits (bounded) for its own copies and products in flight, skips the
+// epilogue, frees its TMEM and returns.
+//
+// Training step: one CUDA graph per batch size (forward, loss, backward,
+// Adam), replayed by titan_mlp_train_step; the learning rate and the Adam
+// step counter live in device memory so the replay needs no host values.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <math.h>
