@@ -26,9 +26,10 @@
 // *err, waits (bounded) for its own copies and products in flight, skips the
 // epilogue, frees its TMEM and returns.
 //
-// Training step: one CUDA graph per batch size (forward, loss, backward,
-// Adam), replayed by titan_mlp_train_step; the learning rate and the Adam
-// step counter live in device memory so the replay needs no host values.
+// Training step: one CUDA graph per batch size (forward, loss, backward with
+// the weight-gradient products on a second stream, Adam), replayed by
+// titan_mlp_train_step; the learning rate and the Adam step counter live in
+// device memory so the replay needs no host values.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <math.h>
@@ -584,7 +585,11 @@ struct titan_mlp {
     __nv_bfloat16 *dZ[3] = {nullptr, nullptr, nullptr};
     // transposes for the weight gradients: x^T, H_0^T and H_1^T (written by
     // the forward products' epilogues), dZ_l^T (one buffer, layer by layer)
-    __nv_bfloat16 *xT = nullptr, *HT[2] = {nullptr, nullptr}, *bT = nullptr;
+    __nv_bfloat16 *xT = nullptr, *HT[2] = {nullptr, nullptr}, *bT = nullptr, *bT2 = nullptr;
+    // the weight-gradient products run on a second stream beside the
+    // input-gradient products (fork and join events per layer)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork[3] = {nullptr, nullptr, nullptr}, ev_join[3] = {nullptr, nullptr, nullptr};
     float *y = nullptr, *dy = nullptr;
     float *part = nullptr;                                 // column-reduction chunk sums [B / kRowChunk][hidden]
     float *partb = nullptr;                                // the same for the bias gradient of one layer
@@ -690,6 +695,7 @@ cudaError_t ensure_batch(titan_mlp *m, uint32_t B) {
     if ((e = malloc_t(m, &m->HT[0], (size_t)B * m->hid)) != cudaSuccess) return e;
     if ((e = malloc_t(m, &m->HT[1], (size_t)B * m->hid)) != cudaSuccess) return e;
     if ((e = malloc_t(m, &m->bT, (size_t)B * m->hid)) != cudaSuccess) return e;
+    if ((e = malloc_t(m, &m->bT2, (size_t)B * m->hid)) != cudaSuccess) return e;
     if ((e = malloc_t(m, &m->y, B)) != cudaSuccess) return e;
     if ((e = malloc_t(m, &m->dy, B)) != cudaSuccess) return e;
     if ((e = malloc_t(m, &m->part, (size_t)((B + kRowChunk - 1) / kRowChunk) * m->hid)) != cudaSuccess) return e;
@@ -736,37 +742,46 @@ cudaError_t backward_pass(titan_mlp *m, const __nv_bfloat16 *x, const float *t, 
                                                                           (int)m->hid);
     const dim3 cs_grid(nblk(m->hid, 32)), cs_block(32, 32);
     k_col_sum_final<<<cs_grid, cs_block, 0, m->stream>>>(m->part, chunks, (int)m->hid, m->g + m->off_w4);
+    // dZ_l^T alternates between two buffers (layer 2 and 0: bT, layer 1: bT2),
+    // so that layer l's weight-gradient product (second stream) can read its
+    // own while the input-gradient product (this stream) writes the next
+    __nv_bfloat16 *const bt[2] = {m->bT, m->bT2};
+    k_transpose64_bf16<<<dim3(m->hid / 64, B / 64), 256, 0, m->stream>>>(m->dZ[2], bt[0], (int)B, (int)m->hid);
     for (int l = 2; l >= 0; --l) {
-        // dW_l^T (hid x in_l) = dZ_l^T (hid x B) . A_{l-1}^T (in_l x B)^T
+        // dW_l^T (hid x in_l) = dZ_l^T (hid x B) . A_{l-1}^T (in_l x B)^T, on the second stream
         const uint32_t in = layer_in(m, l);
         const __nv_bfloat16 *actT = l == 0 ? m->xT : m->HT[l - 1];
-        // dZ_2^T here; dZ_1^T and dZ_0^T come from the epilogue of the product that forms them
-        if (l == 2)
-            k_transpose64_bf16<<<dim3(m->hid / 64, B / 64), 256, 0, m->stream>>>(m->dZ[2], m->bT, (int)B, (int)m->hid);
         if (l == 0)
             k_transpose64_bf16<<<dim3(in / 64, B / 64), 256, 0, m->stream>>>(x, m->xT, (int)B, (int)in);
+        if ((e = cudaEventRecord(m->ev_fork[l], m->stream)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(m->side, m->ev_fork[l], 0)) != cudaSuccess) return e;
         const int splits = wgrad_splits(m->hid, in, B);
         EpiArgs ep{EPI_F32, (int)in, nullptr, splits > 1 ? m->wsk : m->g + m->off_w[l], nullptr, nullptr};
-        if ((e = gemm_tn(m->bT, actT, (int)m->hid, (int)in, (int)B, ep, m->stream, m->spin_limit, m->err, splits)) !=
+        if ((e = gemm_tn(bt[l & 1], actT, (int)m->hid, (int)in, (int)B, ep, m->side, m->spin_limit, m->err, splits)) !=
             cudaSuccess)
             return e;
         if (splits > 1) {
             const size_t n = (size_t)m->hid * in;
-            k_sum_splits<<<nblk(n / 4, 256), 256, 0, m->stream>>>(m->g + m->off_w[l], m->wsk, splits, n);
+            k_sum_splits<<<nblk(n / 4, 256), 256, 0, m->side>>>(m->g + m->off_w[l], m->wsk, splits, n);
         }
+        if ((e = cudaEventRecord(m->ev_join[l], m->side)) != cudaSuccess) return e;
         // db_l: the chunk sums of dZ_l's columns came with dZ_l (k_out_backward, or the
         // epilogue of the product that formed it); the next product overwrites them
         k_col_sum_final<<<cs_grid, cs_block, 0, m->stream>>>(m->partb, chunks, (int)m->hid, m->g + m->off_b[l]);
         if (l > 0) {
-            // dZ_{l-1} = (dZ_l . W_l^T) * GELU'(Z_{l-1}):  A = dZ_l (B x hid), B operand = W_l (in x hid)
+            // dZ_{l-1} = (dZ_l . W_l^T) * GELU'(Z_{l-1}):  A = dZ_l (B x hid), B operand = W_l (in x hid);
+            // its transpose goes to the buffer layer l + 1's weight gradient read: wait for it
+            if (l == 1 && (e = cudaStreamWaitEvent(m->stream, m->ev_join[2], 0)) != cudaSuccess) return e;
             EpiArgs ep2{EPI_GELU_GRAD, (int)m->hid, nullptr, nullptr, m->dZ[l - 1], m->Z[l - 1]};
-            ep2.out_t = m->bT;            // this layer's weight-gradient product (above) has read bT
+            ep2.out_t = bt[(l - 1) & 1];
             ep2.ldt = (int)B;
             ep2.colsum = m->partb;
             if ((e = gemm_tn(m->dZ[l], m->w[l], (int)B, (int)in, (int)m->hid, ep2, m->stream, m->spin_limit, m->err)) != cudaSuccess)
                 return e;
         }
     }
+    // every weight gradient is in place before anything reads it (the side stream runs in order)
+    if ((e = cudaStreamWaitEvent(m->stream, m->ev_join[0], 0)) != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -901,6 +916,11 @@ titan_status titan_mlp_create(uint32_t in, uint32_t hidden, uint64_t seed, int32
     auto bail = [&](titan_status st) {
         titan::set_thread_error(m->error);
         for (void *p : m->allocs) cudaFree(p);
+        for (int l = 0; l < 3; ++l) {
+            if (m->ev_fork[l]) cudaEventDestroy(m->ev_fork[l]);
+            if (m->ev_join[l]) cudaEventDestroy(m->ev_join[l]);
+        }
+        if (m->side) cudaStreamDestroy(m->side);
         if (m->capture) cudaStreamDestroy(m->capture);
         if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
         delete m;
@@ -925,6 +945,11 @@ titan_status titan_mlp_create(uint32_t in, uint32_t hidden, uint64_t seed, int32
     C_CK(malloc_t(m, &m->d_step, 1));
     C_CK(cudaMemset(m->d_step, 0, sizeof(unsigned long long)));
     C_CK(cudaStreamCreateWithFlags(&m->capture, cudaStreamNonBlocking));
+    C_CK(cudaStreamCreateWithFlags(&m->side, cudaStreamNonBlocking));
+    for (int l = 0; l < 3; ++l) {
+        C_CK(cudaEventCreateWithFlags(&m->ev_fork[l], cudaEventDisableTiming));
+        C_CK(cudaEventCreateWithFlags(&m->ev_join[l], cudaEventDisableTiming));
+    }
     for (int l = 0; l < 3; ++l) {
         C_CK(malloc_t(m, &m->wt[l], (size_t)hidden * layer_in(m, l)));
         C_CK(malloc_t(m, &m->w[l], (size_t)hidden * layer_in(m, l)));
@@ -1040,7 +1065,13 @@ const char *titan_mlp_last_error(const titan_mlp *m) { return m ? m->error.c_str
 titan_status titan_mlp_destroy(titan_mlp *m) {
     if (!m) return TITAN_OK;
     cudaStreamSynchronize(m->stream);
+    if (m->side) cudaStreamSynchronize(m->side);
     drop_train_graphs(m);
+    for (int l = 0; l < 3; ++l) {
+        if (m->ev_fork[l]) cudaEventDestroy(m->ev_fork[l]);
+        if (m->ev_join[l]) cudaEventDestroy(m->ev_join[l]);
+    }
+    if (m->side) cudaStreamDestroy(m->side);
     if (m->capture) cudaStreamDestroy(m->capture);
     for (void *p : m->allocs) cudaFree(p);
     if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
