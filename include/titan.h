@@ -256,6 +256,27 @@ titan_status titan_set_state(titan_sim *sim, const double *pos, const double *ve
  * the host.  Errors: TITAN_E_CUDA. */
 titan_status titan_read_state_dev(titan_sim *sim, float *pos_dev, float *vel_dev, void *stream);
 
+/* Group centroids of the state after all steps enqueued so far (the objective
+ * of a swarm of robots simulated as one system, Sec. V-B: how far each moved).
+ * Group g is the masses with caller indices first_dev[g] .. first_dev[g+1] - 1
+ * (first_dev: DEVICE uint32 array of n_groups + 1 non-decreasing offsets, the
+ * last at most n_masses).  out_dev[g][0..2] (DEVICE float) = the mean
+ * position of the group, summed in FP64 mass by mass, minus origin_dev[g][..]
+ * when origin_dev (DEVICE float [n_groups][3]) is non-NULL; an empty group
+ * gives 0.  Enqueued on the simulation stream.  Offsets are not read on the
+ * host: out-of-range ones are clamped to n_masses.  Errors: TITAN_E_INVALID
+ * (null array with n_groups > 0), TITAN_E_CUDA. */
+titan_status titan_group_centroids(titan_sim *sim, uint32_t n_groups, const uint32_t *first_dev,
+                                   const float *origin_dev, float *out_dev);
+
+/* The adjoint seed of sum_g w[g] * (centroid of group g) . e_axis:
+ * seed_dev[i][axis] = w_dev[g] / (number of masses of group g) for every mass
+ * i of group g, every other entry of seed_dev ([n_masses][3], DEVICE float)
+ * 0.  Groups as for titan_group_centroids; axis 0, 1 or 2.  Enqueued on the
+ * simulation stream.  Errors: TITAN_E_INVALID, TITAN_E_CUDA. */
+titan_status titan_group_seed(titan_sim *sim, uint32_t n_groups, const uint32_t *first_dev, const float *w_dev,
+                              int32_t axis, float *seed_dev);
+
 /* Sets the step counter (the simulated time is steps * dt; the actuation
  * clock reads it) for the steps enqueued from now on.  Errors: TITAN_E_CUDA. */
 titan_status titan_set_step(titan_sim *sim, uint64_t step);

@@ -289,6 +289,39 @@ bool uses_cube(const titan_sim *sim) { return sim->csr_kernel == 8; }
 
 
 // Uploads the per-entry actuation arrays of the current layout.
+// Mean position of each group of masses (caller indices first[g] ..
+// first[g+1] - 1, clamped to n), summed in FP64 in caller order, minus the
+// group's origin if given (an empty group: 0); one thread per group.
+__global__ void k_group_centroid(const MassState *__restrict__ state, const uint32_t *__restrict__ dev_of_caller,
+                                 uint32_t n, const uint32_t *__restrict__ first, uint32_t n_groups,
+                                 const float *__restrict__ origin, float *__restrict__ out) {
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n_groups) return;
+    const uint32_t i0 = min(first[g], n), i1 = max(i0, min(first[g + 1], n));
+    double sx = 0, sy = 0, sz = 0;
+    for (uint32_t i = i0; i < i1; ++i) {
+        const float4 p = state[dev_of_caller[i]].p;
+        sx += p.x; sy += p.y; sz += p.z;
+    }
+    const double c = i1 > i0 ? 1.0 / (double)(i1 - i0) : 0.0;
+    float o[3] = {0.f, 0.f, 0.f};
+    if (origin && i1 > i0) { o[0] = origin[3 * g]; o[1] = origin[3 * g + 1]; o[2] = origin[3 * g + 2]; }
+    out[3 * g] = (float)(sx * c - (double)o[0]);
+    out[3 * g + 1] = (float)(sy * c - (double)o[1]);
+    out[3 * g + 2] = (float)(sz * c - (double)o[2]);
+}
+
+// seed[i][axis] = w[g] / |group g| for the masses of group g; a warp per group.
+__global__ void k_group_seed(const uint32_t *__restrict__ first, uint32_t n_groups, uint32_t n,
+                             const float *__restrict__ w, int axis, float *__restrict__ seed) {
+    const uint32_t g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (g >= n_groups) return;
+    const uint32_t i0 = min(first[g], n), i1 = max(i0, min(first[g + 1], n));
+    if (i1 == i0) return;
+    const float v = (float)((double)w[g] / (double)(i1 - i0));
+    for (uint32_t i = i0 + lane; i < i1; i += 32) seed[3 * (size_t)i + axis] = v;
+}
+
 // Brings act_amp / act_phase up to the values last set from device arrays.
 cudaError_t fetch_act_host(titan_sim *sim) {
     if (!sim->act_host_stale) return cudaSuccess;
@@ -1174,6 +1207,47 @@ titan_status titan_read_state_dev(titan_sim *sim, float *pos_dev, float *vel_dev
         if (e == cudaSuccess) e = cudaStreamWaitEvent(static_cast<cudaStream_t>(stream), ev, 0);
         cudaEventDestroy(ev);
         TITAN_CK(sim, e);
+    }
+    return TITAN_OK;
+}
+
+titan_status titan_group_centroids(titan_sim *sim, uint32_t n_groups, const uint32_t *first_dev,
+                                   const float *origin_dev, float *out_dev) {
+    if (!sim) return fail(nullptr, TITAN_E_INVALID, "sim is null");
+    BusyGuard bg(sim);
+    if (!bg.acquired) return fail(sim, TITAN_E_BUSY, "another call on this handle is in progress");
+    if (!n_groups) return TITAN_OK;
+    if (!first_dev || !out_dev) return fail(sim, TITAN_E_INVALID, "first_dev and out_dev are required");
+    DeviceGuard dg(sim->device);
+    {
+        titan_status es_ = titan::ensure_layout(sim);
+        if (es_ != TITAN_OK) return es_;
+    }
+    k_group_centroid<<<(n_groups + 127) / 128, 128, 0, sim->stream>>>(sim->state[sim->cur], sim->d_dev_of_caller,
+                                                                       sim->n, first_dev, n_groups, origin_dev,
+                                                                       out_dev);
+    TITAN_CK(sim, cudaGetLastError());
+    return TITAN_OK;
+}
+
+titan_status titan_group_seed(titan_sim *sim, uint32_t n_groups, const uint32_t *first_dev, const float *w_dev,
+                              int32_t axis, float *seed_dev) {
+    if (!sim) return fail(nullptr, TITAN_E_INVALID, "sim is null");
+    BusyGuard bg(sim);
+    if (!bg.acquired) return fail(sim, TITAN_E_BUSY, "another call on this handle is in progress");
+    if (axis < 0 || axis > 2) return fail(sim, TITAN_E_INVALID, "axis must be 0, 1 or 2");
+    if (!seed_dev || (n_groups && (!first_dev || !w_dev)))
+        return fail(sim, TITAN_E_INVALID, "seed_dev, first_dev and w_dev are required");
+    DeviceGuard dg(sim->device);
+    {
+        titan_status es_ = titan::ensure_layout(sim);
+        if (es_ != TITAN_OK) return es_;
+    }
+    if (!sim->n) return TITAN_OK;
+    TITAN_CK(sim, cudaMemsetAsync(seed_dev, 0, (size_t)sim->n * 3 * sizeof(float), sim->stream));
+    if (n_groups) {
+        k_group_seed<<<(n_groups + 3) / 4, 128, 0, sim->stream>>>(first_dev, n_groups, sim->n, w_dev, axis, seed_dev);
+        TITAN_CK(sim, cudaGetLastError());
     }
     return TITAN_OK;
 }

@@ -78,6 +78,8 @@ def load(path: Optional[str] = None):
                                             C.POINTER(C.POINTER(f32)), C.POINTER(C.c_double)]),
                 "titan_set_actuation": (S, [_P, u32, _P, _P, _P, f32]),
                 "titan_set_actuation_dev": (S, [_P, u32, _P, _P, f32]),
+                "titan_group_centroids": (S, [_P, u32, _P, _P, _P]),
+                "titan_group_seed": (S, [_P, u32, _P, _P, C.c_int32, _P]),
                 "titan_set_state": (S, [_P, _P, _P]),
                 "titan_read_state_dev": (S, [_P, _P, _P, _P]),
                 "titan_sync": (S, [_P]),
@@ -210,6 +212,21 @@ def titan_set_actuation_dev(sim: int, amp_dev, phase_dev, freq_hz: float) -> Non
         raise ValueError("titan_set_actuation_dev: amp_dev and phase_dev must have the same length")
     _check(load().titan_set_actuation_dev(sim, amp_dev.numel(), _ptr(amp_dev), _ptr(phase_dev), float(freq_hz)),
            sim)
+
+
+def titan_group_centroids(sim: int, first_dev, origin_dev, out_dev) -> None:
+    """out_dev[g] = mean position of masses first_dev[g] .. first_dev[g+1]-1
+    (minus origin_dev[g] if given); CUDA tensors: uint32/int32 [G+1], float32
+    [G][3]; enqueued on the simulation's stream."""
+    _check(load().titan_group_centroids(sim, first_dev.numel() - 1, _ptr(first_dev), _ptr(origin_dev),
+                                        _ptr(out_dev)), sim)
+
+
+def titan_group_seed(sim: int, first_dev, w_dev, axis: int, seed_dev) -> None:
+    """seed_dev[i][axis] = w_dev[g] / |group g| for the masses of group g, 0
+    elsewhere; enqueued on the simulation's stream."""
+    _check(load().titan_group_seed(sim, first_dev.numel() - 1, _ptr(first_dev), _ptr(w_dev), int(axis),
+                                   _ptr(seed_dev)), sim)
 
 
 def titan_set_state(sim: int, pos, vel=None) -> None:
@@ -621,8 +638,6 @@ class CentroidRollout:
         self.system, self.mass_off, self.spring_off = union_system(robots)
         self.n_steps, self.every = int(n_steps), int(every)
         self.n_robots = len(robots)
-        self.robot_of_mass = np.repeat(np.arange(self.n_robots), np.diff(self.mass_off))
-        self.counts = np.diff(self.mass_off).astype(np.float64)
         self.freq = float(self.system.act_freq)
         self.device = device
         self.sim = Sim(self.system, device=device, order=order)
@@ -635,13 +650,15 @@ class CentroidRollout:
         self._torch = torch
 
     def _dev_tables(self):
-        """Robot of each mass, masses per robot and initial centroid x, kept
-        on the device after the first use."""
+        """The robots' mass ranges (uint32 offsets) and initial centroids
+        (float32 [robots][3]), kept on the device after the first use."""
         if self._dev is None:
             T_ = self._torch
             dev = T_.device("cuda", self.device)
-            self._dev = (T_.as_tensor(self.robot_of_mass, device=dev), T_.as_tensor(self.counts, device=dev),
-                         T_.as_tensor(self.x0, device=dev))
+            first = T_.as_tensor(np.asarray(self.mass_off, np.int64).astype(np.int32), device=dev)
+            origin = np.zeros((self.n_robots, 3), np.float32)
+            origin[:, 0] = self.x0
+            self._dev = (first, T_.as_tensor(origin, device=dev))
         return self._dev
 
     def _prepare(self, amp, phase):
@@ -658,24 +675,24 @@ class CentroidRollout:
         T_ = self._torch
         self._prepare(amp, phase)
         self.sim.step(self.n_steps)
-        pos = T_.empty((self.system.n_masses, 3), dtype=T_.float32, device=f"cuda:{self.device}")
-        titan_read_state_dev(self.sim.handle, pos, None, None)
+        first, origin = self._dev_tables()
+        out = T_.empty((self.n_robots, 3), dtype=T_.float32, device=f"cuda:{self.device}")
+        titan_group_centroids(self.sim.handle, first, origin, out)     # displacement of every centroid
         self.sim.sync()
-        idx, cnt, x0 = self._dev_tables()
-        sums = T_.zeros(self.n_robots, dtype=T_.float64, device=pos.device).index_add_(0, idx, pos[:, 0].double())
-        return (sums / cnt - x0).float()
+        return out[:, 0].contiguous()
 
     def gradients(self, amp, phase, grad_out):
         """dJ/dA and dJ/dphi for the objective sum_r grad_out[r] * J_r."""
         T_ = self._torch
         self._prepare(amp, phase)
         dev = f"cuda:{self.device}"
-        idx, cnt, _ = self._dev_tables()
-        seed = T_.zeros((self.system.n_masses, 3), dtype=T_.float32, device=dev)
-        seed[:, 0] = (grad_out.detach().to(dev).double() / cnt)[idx].float()
+        first, _ = self._dev_tables()
+        w = grad_out.detach().to(dev, T_.float32).contiguous()
+        seed = T_.empty((self.system.n_masses, 3), dtype=T_.float32, device=dev)
         ga = T_.empty(self.system.n_springs, dtype=T_.float32, device=dev)
         gp = T_.empty_like(ga)
-        T_.cuda.current_stream(dev).synchronize()      # seed is written on torch's stream
+        T_.cuda.current_stream(dev).synchronize()      # w is written on torch's stream
+        titan_group_seed(self.sim.handle, first, w, 0, seed)
         titan_adjoint(self.sim.handle, self.n_steps, self.every, seed, None, ga, gp)
         self.sim.sync()
         return ga, gp

@@ -135,3 +135,38 @@ def test_torch_autograd_function_over_several_robots():
         s0, s1 = f.spring_off[r], f.spring_off[r + 1]
         _close(amp.grad[s0:s1].cpu().numpy() / float(w[r]), ra)
         _close(ph.grad[s0:s1].cpu().numpy() / float(w[r]), rp)
+
+
+def test_group_centroids_and_seed_match_numpy():
+    """titan_group_centroids (mean position per group of caller indices, minus
+    an origin) against the snapshot averaged in numpy; titan_group_seed
+    against w[g] / |g| written by hand; an empty group gives 0."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(3)
+    robots = [inputs.actuated_box(a, b, c, rng) for a, b, c in [(3, 3, 3), (4, 3, 2), (2, 2, 5)]]
+    sy, mo, _ = T.union_system(robots)
+    first = np.array([mo[0], mo[1], mo[1], mo[2], mo[3]], np.int32)      # group 1 is empty
+    with T.Sim(sy) as sim:
+        sim.step(57)
+        x, _, _ = sim.snapshot()
+        f = torch.as_tensor(first, device="cuda")
+        origin = torch.as_tensor(rng.normal(0, 0.1, (4, 3)).astype(np.float32), device="cuda")
+        out = torch.empty((4, 3), device="cuda")
+        T.titan_group_centroids(sim.handle, f, origin, out)
+        w = torch.tensor([0.5, 3.0, -1.0, 2.0], device="cuda")
+        seed = torch.full((sy.n_masses, 3), 7.0, device="cuda")
+        T.titan_group_seed(sim.handle, f, w, 1, seed)
+        sim.sync()
+    o = origin.cpu().numpy().astype(np.float64)
+    got = out.cpu().numpy()
+    for g in range(4):
+        i0, i1 = first[g], first[g + 1]
+        want = x[i0:i1].astype(np.float64).mean(axis=0) - o[g] if i1 > i0 else np.zeros(3)
+        np.testing.assert_allclose(got[g], want, rtol=0, atol=1e-6)
+    sd = seed.cpu().numpy()
+    assert not sd[:, [0, 2]].any()
+    wn = w.cpu().numpy().astype(np.float64)
+    for g in range(4):
+        i0, i1 = first[g], first[g + 1]
+        if i1 > i0:
+            np.testing.assert_array_equal(sd[i0:i1, 1], np.float32(wn[g] / (i1 - i0)))
